@@ -1,0 +1,1070 @@
+/*
+ * mrfv_oracle.c -- plain, slow CPU oracle of the adaptive multiresolution
+ * finite-volume method for the compressible Euler equations
+ * (Deiterding, Domingues, Gomes, Schneider, arXiv:1603.05211).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the bench may load this library.  It shares no code, header,
+ * table or helper with the CUDA path.  It is compiled with -ffp-contract=off so
+ * every floating-point operation is rounded where the source says it is.
+ *
+ * Data model: every level l = 0..L is a dense array of N_l^d cells per
+ * variable (layout [v][cell], cell = i + n0*(j + n1*k)) plus a dense byte map
+ * of which 8^d-cell blocks exist.  Cells of absent blocks hold NaN, so any read
+ * of an absent value poisons the result and shows up in the tests.
+ *
+ * What each part follows:
+ *   - Euler equations, ideal gas, gamma = 1.4 .............. Section 2, Eqs. 2.1-2.3
+ *   - cell averages, dQ/dt = -F(Q) ........................ Section 2 (FV semi-discretisation)
+ *   - MUSCL, van Albada limiter, AUSM+ flux, RK2 midpoint .. Section 2 (MR scheme paragraph)
+ *   - projection / 3rd-order prediction / details / eps ... Section 2.1
+ *   - refinement by one level, gradedness, coarsening ..... Section 2.1 (three basic operations)
+ *   - virtual leaves / conservative coarse-fine fluxes ..... Section 2.1, Fig. 1
+ *   - level-dependent time steps, time interpolation ....... Section 2.1 (MRLT), Section 2.2, Fig. 2
+ *   - flux correction at refinement boundaries ............. Section 2.2, Fig. 2
+ *   - scaled-gradient flags + one-cell buffer, clustering .. Section 2.2 (refinement indicators)
+ *   - L1 error by projection to the finest level .......... Section 3
+ * Readings where the paper is silent are stated beside the code that takes them.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OMAXL 12
+#define OB 8 /* cells per block edge */
+
+enum { O_BC_TRANSMISSIVE = 0, O_BC_PERIODIC = 1 };
+enum { O_CRIT_MR = 0, O_CRIT_GRAD = 1 };
+enum { O_IC_QUADRANTS = 0, O_IC_ELLIPSOID = 1, O_IC_SHOCKTUBE = 2, O_IC_UNIFORM = 3,
+       O_IC_WAVE = 4, O_IC_ROTATED_ELLIPSOID = 5 };
+
+typedef struct {
+  int dim, nv, L, bc;
+  double gamma;
+  double lo[3], hi[3];
+  int nb[OMAXL][3];   /* blocks per dimension (1 in unused dimensions) */
+  int n[OMAXL][3];    /* cells per dimension */
+  long ncell[OMAXL], nblk[OMAXL];
+  double dx[OMAXL][3];
+  uint8_t *ex[OMAXL]; /* block exists */
+  double *q[OMAXL];   /* state Q^n, [v][cell] */
+  double *qs[OMAXL];  /* RK stage state Q* */
+  double *q0[OMAXL];  /* state at the start of the level's own step (local time stepping) */
+  double *rc[OMAXL];  /* coarse-role flux record: dt*F on [side][dir][v][cell] */
+  double *rf[OMAXL];  /* fine-role flux record, summed over the sub-steps of the parent step */
+  uint8_t *sig[OMAXL];      /* last analysis: block significant / flagged */
+  double *maxdet[OMAXL];    /* last analysis: block max normalised detail */
+  double scale[5];          /* last analysis: normalisation s_v */
+} orc;
+
+/* ------------------------------------------------------------------------ */
+/* indexing                                                                   */
+
+static long cidx(const orc *o, int l, int i, int j, int k) {
+  return (long)i + (long)o->n[l][0] * ((long)j + (long)o->n[l][1] * (long)k);
+}
+static long bidx(const orc *o, int l, int bi, int bj, int bk) {
+  return (long)bi + (long)o->nb[l][0] * ((long)bj + (long)o->nb[l][1] * (long)bk);
+}
+/* boundary handling of a cell coordinate: transmissive = nearest interior cell
+   (zero-gradient copy into every ghost layer), periodic = wrap. */
+static int bc_cell(const orc *o, int l, int d, int i) {
+  int N = o->n[l][d];
+  if (d >= o->dim) return 0;
+  if (o->bc == O_BC_PERIODIC) { i %= N; if (i < 0) i += N; return i; }
+  return i < 0 ? 0 : (i >= N ? N - 1 : i);
+}
+/* neighbouring block coordinate, or -1 when it lies outside a transmissive domain */
+static int bc_block(const orc *o, int l, int d, int b) {
+  int N = o->nb[l][d];
+  if (d >= o->dim) return b == 0 ? 0 : -1;
+  if (o->bc == O_BC_PERIODIC) { b %= N; if (b < 0) b += N; return b; }
+  return (b < 0 || b >= N) ? -1 : b;
+}
+static int block_exists(const orc *o, int l, int bi, int bj, int bk) {
+  return o->ex[l][bidx(o, l, bi, bj, bk)] != 0;
+}
+static int block_is_leaf(const orc *o, int l, int bi, int bj, int bk) {
+  if (!block_exists(o, l, bi, bj, bk)) return 0;
+  if (l == o->L) return 1;
+  return !block_exists(o, l + 1, 2 * bi, 2 * bj, o->dim == 3 ? 2 * bk : 0);
+}
+static int cell_block_exists(const orc *o, int l, int i, int j, int k) {
+  return block_exists(o, l, i / OB, j / OB, k / OB);
+}
+static int cell_block_internal(const orc *o, int l, int i, int j, int k) {
+  return cell_block_exists(o, l, i, j, k) && !block_is_leaf(o, l, i / OB, j / OB, k / OB);
+}
+
+/* ------------------------------------------------------------------------ */
+/* equation of state (Section 2): p = (gamma-1) (rho e - rho |v|^2 / 2)       */
+
+/* conservative (rho, rho v_1..rho v_d, rho e) -> primitive (rho, v_1..v_3, p) */
+static void cons_to_prim(const orc *o, const double *Q, double *w) {
+  double rho = Q[0];
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < o->dim; d++) v[d] = Q[1 + d] / rho;
+  double vv = ((v[0] * v[0]) + (v[1] * v[1])) + (v[2] * v[2]);
+  double E = Q[o->dim + 1];
+  w[0] = rho;
+  w[1] = v[0]; w[2] = v[1]; w[3] = v[2];
+  w[4] = (o->gamma - 1.0) * (E - ((0.5 * rho) * vv));
+}
+static void prim_to_cons(const orc *o, const double *w, double *Q) {
+  double vv = ((w[1] * w[1]) + (w[2] * w[2])) + (w[3] * w[3]);
+  Q[0] = w[0];
+  for (int d = 0; d < o->dim; d++) Q[1 + d] = w[0] * w[1 + d];
+  Q[o->dim + 1] = (w[4] / (o->gamma - 1.0)) + ((0.5 * w[0]) * vv);
+}
+
+/* ------------------------------------------------------------------------ */
+/* MUSCL reconstruction with the van Albada limiter (Section 2).
+   Reading: primitive variables are reconstructed; the slope is
+   a*b*(a+b)/(a^2+b^2) when a*b > 0 and 0 otherwise (no epsilon).  This slope
+   never exceeds 1.21*min(|a|,|b|) in size, so w_i -/+ slope/2 stays positive
+   whenever the three cells are positive and no first-order fallback is needed. */
+static double van_albada(double a, double b) {
+  double ab = a * b;
+  if (ab > 0.0) return (ab * (a + b)) / ((a * a) + (b * b));
+  return 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* AUSM+ (Liou 1996, cited in Section 2).  Split Mach numbers and pressures with
+   beta = 1/8, alpha = 3/16; interface sound speed = arithmetic mean (reading);
+   |M| >= 1 takes the supersonic branch (both branches agree there). */
+static double mach4_plus(double M) {
+  if (fabs(M) >= 1.0) return 0.5 * (M + fabs(M));
+  double t = M + 1.0, u = (M * M) - 1.0;
+  return (0.25 * (t * t)) + (0.125 * (u * u));
+}
+static double mach4_minus(double M) {
+  if (fabs(M) >= 1.0) return 0.5 * (M - fabs(M));
+  double t = M - 1.0, u = (M * M) - 1.0;
+  return (-0.25 * (t * t)) - (0.125 * (u * u));
+}
+static double pres5_plus(double M) {
+  if (fabs(M) >= 1.0) return M > 0.0 ? 1.0 : 0.0;
+  double t = M + 1.0, u = (M * M) - 1.0;
+  return ((0.25 * (t * t)) * (2.0 - M)) + ((0.1875 * M) * (u * u));
+}
+static double pres5_minus(double M) {
+  if (fabs(M) >= 1.0) return M < 0.0 ? 1.0 : 0.0;
+  double t = M - 1.0, u = (M * M) - 1.0;
+  return ((0.25 * (t * t)) * (2.0 + M)) - ((0.1875 * M) * (u * u));
+}
+/* flux across a face with normal dir nd from primitive face states wl | wr */
+static void ausm_plus(const orc *o, int nd, const double *wl, const double *wr, double *F) {
+  double g = o->gamma;
+  double cl = sqrt((g * wl[4]) / wl[0]);
+  double cr = sqrt((g * wr[4]) / wr[0]);
+  double ch = 0.5 * (cl + cr);
+  double ml = wl[1 + nd] / ch;
+  double mr = wr[1 + nd] / ch;
+  double m = mach4_plus(ml) + mach4_minus(mr);
+  double ph = (pres5_plus(ml) * wl[4]) + (pres5_minus(mr) * wr[4]);
+  double a = ch * m;
+  const double *wu = (m >= 0.0) ? wl : wr;
+  double vv = ((wu[1] * wu[1]) + (wu[2] * wu[2])) + (wu[3] * wu[3]);
+  double rhoH = ((g / (g - 1.0)) * wu[4]) + ((0.5 * wu[0]) * vv);
+  double fr = a * wu[0];
+  F[0] = fr;
+  for (int d = 0; d < o->dim; d++) {
+    double f = fr * wu[1 + d];
+    if (d == nd) f = f + ph;
+    F[1 + d] = f;
+  }
+  F[o->dim + 1] = a * rhoH;
+}
+
+/* physical flux f_n(q) of Eq. 2.2, used only by the consistency check */
+static void physical_flux(const orc *o, int nd, const double *Q, double *F) {
+  double w[5];
+  cons_to_prim(o, Q, w);
+  double vn = w[1 + nd];
+  F[0] = Q[0] * vn;
+  for (int d = 0; d < o->dim; d++) F[1 + d] = Q[1 + d] * vn + (d == nd ? w[4] : 0.0);
+  F[o->dim + 1] = (Q[o->dim + 1] + w[4]) * vn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* helpers on dense level arrays                                             */
+
+static void get_cell(const orc *o, int l, const double *A, long c, double *Q) {
+  for (int v = 0; v < o->nv; v++) Q[v] = A[(long)v * o->ncell[l] + c];
+}
+static double *alloc_level(const orc *o, int l) {
+  double *a = (double *)malloc(sizeof(double) * (size_t)o->nv * (size_t)o->ncell[l]);
+  for (long m = 0; m < (long)o->nv * o->ncell[l]; m++) a[m] = NAN;
+  return a;
+}
+
+/* ------------------------------------------------------------------------ */
+/* MR projection (Section 2.1): a parent cell average is the mean of its 2^d
+   children, summed in lexicographic child order (x offset fastest).          */
+static double project_cell(const orc *o, int lf, const double *F, int v, int i, int j, int k) {
+  long nc = o->ncell[lf];
+  double s = 0.0;
+  int kz = (o->dim == 3) ? 2 : 1;
+  int first = 1;
+  for (int c = 0; c < kz; c++)
+    for (int b = 0; b < 2; b++)
+      for (int a = 0; a < 2; a++) {
+        double x = F[(long)v * nc + cidx(o, lf, 2 * i + a, 2 * j + b, o->dim == 3 ? 2 * k + c : 0)];
+        if (first) { s = x; first = 0; } else s = s + x;
+      }
+  return s * (o->dim == 3 ? 0.125 : 0.25);
+}
+
+/* restrict level l+1 onto the internal (refined) blocks of level l */
+static void restrict_level(orc *o, int l, double **arr) {
+  for (int bk = 0; bk < o->nb[l][2]; bk++)
+    for (int bj = 0; bj < o->nb[l][1]; bj++)
+      for (int bi = 0; bi < o->nb[l][0]; bi++) {
+        if (!block_exists(o, l, bi, bj, bk) || block_is_leaf(o, l, bi, bj, bk)) continue;
+        int kz = o->dim == 3 ? OB : 1;
+        for (int kk = 0; kk < kz; kk++)
+          for (int jj = 0; jj < OB; jj++)
+            for (int ii = 0; ii < OB; ii++) {
+              int i = bi * OB + ii, j = bj * OB + jj, k = (o->dim == 3) ? bk * OB + kk : 0;
+              long c = cidx(o, l, i, j, k);
+              for (int v = 0; v < o->nv; v++)
+                arr[l][(long)v * o->ncell[l] + c] = project_cell(o, l + 1, arr[l + 1], v, i, j, k);
+            }
+      }
+}
+static void restrict_all(orc *o, double **arr) {
+  for (int l = o->L - 1; l >= 0; l--) restrict_level(o, l, arr);
+}
+
+/* ------------------------------------------------------------------------ */
+/* MR prediction, third order (Section 2.1): quadratic interpolation of cell
+   averages, tensor product over directions.  In 1D the two children of coarse
+   cell k are Q_k +/- (Q_{k-1} - Q_{k+1})/8 (+ for the even child).  In d
+   dimensions the product of these operators adds the mixed differences of the
+   coarse 3^d neighbourhood with weights 1/64 and 1/512.  Coarse neighbours
+   outside the domain come from the same boundary rule.
+   Evaluation order (also fixes rounding): Q_k, then the first-order terms in
+   direction order, then the mixed pairs (12, 13, 23), then the triple term. */
+static double coarse_at(const orc *o, int lc, const double *C, int v, int i, int j, int k) {
+  i = bc_cell(o, lc, 0, i); j = bc_cell(o, lc, 1, j); k = bc_cell(o, lc, 2, k);
+  return C[(long)v * o->ncell[lc] + cidx(o, lc, i, j, k)];
+}
+static double predict_cell(const orc *o, int lf, const double *C, int v, int I, int J, int K) {
+  int lc = lf - 1;
+  int ki = I >> 1, kj = J >> 1, kk = K >> 1;
+  double si = (I & 1) ? -1.0 : 1.0, sj = (J & 1) ? -1.0 : 1.0, sk = (K & 1) ? -1.0 : 1.0;
+  if (o->dim == 2) {
+    double q = coarse_at(o, lc, C, v, ki, kj, 0);
+    double d1 = coarse_at(o, lc, C, v, ki - 1, kj, 0) - coarse_at(o, lc, C, v, ki + 1, kj, 0);
+    double d2 = coarse_at(o, lc, C, v, ki, kj - 1, 0) - coarse_at(o, lc, C, v, ki, kj + 1, 0);
+    double d12 = ((coarse_at(o, lc, C, v, ki - 1, kj - 1, 0) - coarse_at(o, lc, C, v, ki + 1, kj - 1, 0))
+                  - coarse_at(o, lc, C, v, ki - 1, kj + 1, 0)) + coarse_at(o, lc, C, v, ki + 1, kj + 1, 0);
+    double r = q + (si * 0.125) * d1;
+    r = r + (sj * 0.125) * d2;
+    r = r + ((si * sj) * 0.015625) * d12;
+    return r;
+  }
+  /* 3D */
+  double q = coarse_at(o, lc, C, v, ki, kj, kk);
+  double d1 = coarse_at(o, lc, C, v, ki - 1, kj, kk) - coarse_at(o, lc, C, v, ki + 1, kj, kk);
+  double d2 = coarse_at(o, lc, C, v, ki, kj - 1, kk) - coarse_at(o, lc, C, v, ki, kj + 1, kk);
+  double d3 = coarse_at(o, lc, C, v, ki, kj, kk - 1) - coarse_at(o, lc, C, v, ki, kj, kk + 1);
+  double d12 = ((coarse_at(o, lc, C, v, ki - 1, kj - 1, kk) - coarse_at(o, lc, C, v, ki + 1, kj - 1, kk))
+                - coarse_at(o, lc, C, v, ki - 1, kj + 1, kk)) + coarse_at(o, lc, C, v, ki + 1, kj + 1, kk);
+  double d13 = ((coarse_at(o, lc, C, v, ki - 1, kj, kk - 1) - coarse_at(o, lc, C, v, ki + 1, kj, kk - 1))
+                - coarse_at(o, lc, C, v, ki - 1, kj, kk + 1)) + coarse_at(o, lc, C, v, ki + 1, kj, kk + 1);
+  double d23 = ((coarse_at(o, lc, C, v, ki, kj - 1, kk - 1) - coarse_at(o, lc, C, v, ki, kj + 1, kk - 1))
+                - coarse_at(o, lc, C, v, ki, kj - 1, kk + 1)) + coarse_at(o, lc, C, v, ki, kj + 1, kk + 1);
+  double e_lo = ((coarse_at(o, lc, C, v, ki - 1, kj - 1, kk - 1) - coarse_at(o, lc, C, v, ki + 1, kj - 1, kk - 1))
+                 - coarse_at(o, lc, C, v, ki - 1, kj + 1, kk - 1)) + coarse_at(o, lc, C, v, ki + 1, kj + 1, kk - 1);
+  double e_hi = ((coarse_at(o, lc, C, v, ki - 1, kj - 1, kk + 1) - coarse_at(o, lc, C, v, ki + 1, kj - 1, kk + 1))
+                 - coarse_at(o, lc, C, v, ki - 1, kj + 1, kk + 1)) + coarse_at(o, lc, C, v, ki + 1, kj + 1, kk + 1);
+  double d123 = e_lo - e_hi;
+  double r = q + (si * 0.125) * d1;
+  r = r + (sj * 0.125) * d2;
+  r = r + (sk * 0.125) * d3;
+  r = r + ((si * sj) * 0.015625) * d12;
+  r = r + ((si * sk) * 0.015625) * d13;
+  r = r + ((sj * sk) * 0.015625) * d23;
+  r = r + (((si * sj) * sk) * 0.001953125) * d123;
+  return r;
+}
+
+/* The same prediction in single precision: used to take the thresholding
+   decision in the precision of a single-precision state. */
+static float coarse_at_f(const orc *o, int lc, const float *C, int v, int i, int j, int k) {
+  i = bc_cell(o, lc, 0, i); j = bc_cell(o, lc, 1, j); k = bc_cell(o, lc, 2, k);
+  return C[(long)v * o->ncell[lc] + cidx(o, lc, i, j, k)];
+}
+static float predict_cell_f(const orc *o, int lf, const float *C, int v, int I, int J, int K) {
+  int lc = lf - 1;
+  int ki = I >> 1, kj = J >> 1, kk = K >> 1;
+  float si = (I & 1) ? -1.0f : 1.0f, sj = (J & 1) ? -1.0f : 1.0f, sk = (K & 1) ? -1.0f : 1.0f;
+  if (o->dim == 2) {
+    float q = coarse_at_f(o, lc, C, v, ki, kj, 0);
+    float d1 = coarse_at_f(o, lc, C, v, ki - 1, kj, 0) - coarse_at_f(o, lc, C, v, ki + 1, kj, 0);
+    float d2 = coarse_at_f(o, lc, C, v, ki, kj - 1, 0) - coarse_at_f(o, lc, C, v, ki, kj + 1, 0);
+    float d12 = ((coarse_at_f(o, lc, C, v, ki - 1, kj - 1, 0) - coarse_at_f(o, lc, C, v, ki + 1, kj - 1, 0))
+                 - coarse_at_f(o, lc, C, v, ki - 1, kj + 1, 0)) + coarse_at_f(o, lc, C, v, ki + 1, kj + 1, 0);
+    float r = q + (si * 0.125f) * d1;
+    r = r + (sj * 0.125f) * d2;
+    r = r + ((si * sj) * 0.015625f) * d12;
+    return r;
+  }
+  float q = coarse_at_f(o, lc, C, v, ki, kj, kk);
+  float d1 = coarse_at_f(o, lc, C, v, ki - 1, kj, kk) - coarse_at_f(o, lc, C, v, ki + 1, kj, kk);
+  float d2 = coarse_at_f(o, lc, C, v, ki, kj - 1, kk) - coarse_at_f(o, lc, C, v, ki, kj + 1, kk);
+  float d3 = coarse_at_f(o, lc, C, v, ki, kj, kk - 1) - coarse_at_f(o, lc, C, v, ki, kj, kk + 1);
+  float d12 = ((coarse_at_f(o, lc, C, v, ki - 1, kj - 1, kk) - coarse_at_f(o, lc, C, v, ki + 1, kj - 1, kk))
+               - coarse_at_f(o, lc, C, v, ki - 1, kj + 1, kk)) + coarse_at_f(o, lc, C, v, ki + 1, kj + 1, kk);
+  float d13 = ((coarse_at_f(o, lc, C, v, ki - 1, kj, kk - 1) - coarse_at_f(o, lc, C, v, ki + 1, kj, kk - 1))
+               - coarse_at_f(o, lc, C, v, ki - 1, kj, kk + 1)) + coarse_at_f(o, lc, C, v, ki + 1, kj, kk + 1);
+  float d23 = ((coarse_at_f(o, lc, C, v, ki, kj - 1, kk - 1) - coarse_at_f(o, lc, C, v, ki, kj + 1, kk - 1))
+               - coarse_at_f(o, lc, C, v, ki, kj - 1, kk + 1)) + coarse_at_f(o, lc, C, v, ki, kj + 1, kk + 1);
+  float e_lo = ((coarse_at_f(o, lc, C, v, ki - 1, kj - 1, kk - 1) - coarse_at_f(o, lc, C, v, ki + 1, kj - 1, kk - 1))
+                - coarse_at_f(o, lc, C, v, ki - 1, kj + 1, kk - 1)) + coarse_at_f(o, lc, C, v, ki + 1, kj + 1, kk - 1);
+  float e_hi = ((coarse_at_f(o, lc, C, v, ki - 1, kj - 1, kk + 1) - coarse_at_f(o, lc, C, v, ki + 1, kj - 1, kk + 1))
+                - coarse_at_f(o, lc, C, v, ki - 1, kj + 1, kk + 1)) + coarse_at_f(o, lc, C, v, ki + 1, kj + 1, kk + 1);
+  float d123 = e_lo - e_hi;
+  float r = q + (si * 0.125f) * d1;
+  r = r + (sj * 0.125f) * d2;
+  r = r + (sk * 0.125f) * d3;
+  r = r + ((si * sj) * 0.015625f) * d12;
+  r = r + ((si * sk) * 0.015625f) * d13;
+  r = r + ((sj * sk) * 0.015625f) * d23;
+  r = r + (((si * sj) * sk) * 0.001953125f) * d123;
+  return r;
+}
+
+/* The level-l array the scheme sees: values of existing blocks from src, every
+   other cell predicted from the level l-1 array coarse (virtual cells).  By
+   gradedness every coarse value that a used virtual cell needs exists; absent
+   coarse values are NaN and would poison any result that used them. */
+static double *build_ext(const orc *o, int l, const double *src, const double *coarse) {
+  double *e = alloc_level(o, l);
+  for (int k = 0; k < o->n[l][2]; k++)
+    for (int j = 0; j < o->n[l][1]; j++)
+      for (int i = 0; i < o->n[l][0]; i++) {
+        long c = cidx(o, l, i, j, k);
+        if (cell_block_exists(o, l, i, j, k)) {
+          for (int v = 0; v < o->nv; v++) e[(long)v * o->ncell[l] + c] = src[(long)v * o->ncell[l] + c];
+        } else if (l > 0 && coarse) {
+          for (int v = 0; v < o->nv; v++) e[(long)v * o->ncell[l] + c] = predict_cell(o, l, coarse, v, i, j, k);
+        }
+      }
+  return e;
+}
+
+/* ------------------------------------------------------------------------ */
+/* numerical flux across the face between cell a = (i,j,k) and a + e_nd,
+   computed from the level array E (with boundary handling of indices)        */
+static void face_flux(const orc *o, int l, const double *E, int nd, int i, int j, int k, double *F) {
+  int c4[4][3];
+  for (int s = 0; s < 4; s++) {
+    int p[3] = {i, j, k};
+    p[nd] += s - 1; /* a-e, a, a+e, a+2e */
+    for (int d = 0; d < 3; d++) c4[s][d] = bc_cell(o, l, d, p[d]);
+  }
+  double w[4][5];
+  for (int s = 0; s < 4; s++) {
+    double Q[5];
+    get_cell(o, l, E, cidx(o, l, c4[s][0], c4[s][1], c4[s][2]), Q);
+    cons_to_prim(o, Q, w[s]);
+  }
+  double wl[5], wr[5];
+  for (int m = 0; m < 5; m++) {
+    if (m >= 1 + o->dim && m < 4) { wl[m] = 0.0; wr[m] = 0.0; continue; }
+    double sa = van_albada(w[1][m] - w[0][m], w[2][m] - w[1][m]);
+    double sb = van_albada(w[2][m] - w[1][m], w[3][m] - w[2][m]);
+    wl[m] = w[1][m] + 0.5 * sa;
+    wr[m] = w[2][m] - 0.5 * sb;
+  }
+  ausm_plus(o, nd, wl, wr, F);
+}
+
+/* ------------------------------------------------------------------------ */
+/* one RK stage on level l: out = q0 - coef*dt * F(E) on leaf blocks (or on all
+   existing blocks when all_blocks), F = sum_n (F_{n,+} - F_{n,-}) / dx_n.
+   When record is set, dt*F of both faces in every direction is stored per
+   cell: coarse role overwritten, fine role written (first sub-step) or added. */
+static void fv_level(orc *o, int l, const double *E, const double *q0, double *out,
+                     double coef, double dt, int all_blocks, int record, int accumulate) {
+  long nc = o->ncell[l];
+  double lam[3];
+  for (int d = 0; d < 3; d++) lam[d] = (coef * dt) / o->dx[l][d];
+  for (int bk = 0; bk < o->nb[l][2]; bk++)
+    for (int bj = 0; bj < o->nb[l][1]; bj++)
+      for (int bi = 0; bi < o->nb[l][0]; bi++) {
+        if (all_blocks ? !block_exists(o, l, bi, bj, bk) : !block_is_leaf(o, l, bi, bj, bk)) continue;
+        int kz = o->dim == 3 ? OB : 1;
+        for (int kk = 0; kk < kz; kk++)
+          for (int jj = 0; jj < OB; jj++)
+            for (int ii = 0; ii < OB; ii++) {
+              int i = bi * OB + ii, j = bj * OB + jj, k = (o->dim == 3) ? bk * OB + kk : 0;
+              long c = cidx(o, l, i, j, k);
+              double Fm[3][5], Fp[3][5];
+              for (int d = 0; d < o->dim; d++) {
+                int a[3] = {i, j, k};
+                a[d] -= 1;
+                face_flux(o, l, E, d, a[0], a[1], a[2], Fm[d]);
+                face_flux(o, l, E, d, i, j, k, Fp[d]);
+              }
+              for (int v = 0; v < o->nv; v++) {
+                double r = lam[0] * (Fp[0][v] - Fm[0][v]);
+                r = r + lam[1] * (Fp[1][v] - Fm[1][v]);
+                if (o->dim == 3) r = r + lam[2] * (Fp[2][v] - Fm[2][v]);
+                out[(long)v * nc + c] = q0[(long)v * nc + c] - r;
+              }
+              if (record) {
+                for (int d = 0; d < o->dim; d++)
+                  for (int v = 0; v < o->nv; v++) {
+                    long lo_i = ((long)(0 * 3 + d) * o->nv + v) * nc + c;
+                    long hi_i = ((long)(1 * 3 + d) * o->nv + v) * nc + c;
+                    double rm = dt * Fm[d][v], rp = dt * Fp[d][v];
+                    o->rc[l][lo_i] = rm;
+                    o->rc[l][hi_i] = rp;
+                    if (accumulate) { o->rf[l][lo_i] = o->rf[l][lo_i] + rm; o->rf[l][hi_i] = o->rf[l][hi_i] + rp; }
+                    else { o->rf[l][lo_i] = rm; o->rf[l][hi_i] = rp; }
+                  }
+              }
+            }
+      }
+}
+
+/* Flux correction (Section 2.2, Fig. 2; virtual leaves of Section 2.1): on every
+   leaf cell of level l whose face borders a refined block of level l, the
+   time-integrated coarse flux dt_l*F_c is replaced by the mean over the 2^{d-1}
+   fine faces of the time-integrated fine fluxes (summed over the fine sub-steps):
+   q += s * (R_c - mean R_f) / dx, s = +1 on the high face, -1 on the low face.
+   The fine faces are averaged in lexicographic order of their tangential
+   offsets (first tangential direction fastest). */
+static void reflux_level(orc *o, int l, double *q) {
+  if (l >= o->L) return;
+  long nc = o->ncell[l], ncf = o->ncell[l + 1];
+  for (int bk = 0; bk < o->nb[l][2]; bk++)
+    for (int bj = 0; bj < o->nb[l][1]; bj++)
+      for (int bi = 0; bi < o->nb[l][0]; bi++) {
+        if (!block_is_leaf(o, l, bi, bj, bk)) continue;
+        int kz = o->dim == 3 ? OB : 1;
+        for (int kk = 0; kk < kz; kk++)
+          for (int jj = 0; jj < OB; jj++)
+            for (int ii = 0; ii < OB; ii++) {
+              int i = bi * OB + ii, j = bj * OB + jj, k = (o->dim == 3) ? bk * OB + kk : 0;
+              long c = cidx(o, l, i, j, k);
+              for (int d = 0; d < o->dim; d++)
+                for (int side = 0; side < 2; side++) {
+                  int nbp[3] = {i, j, k};
+                  nbp[d] += side ? 1 : -1;
+                  /* neighbour cell across the face, with periodic wrap; none outside */
+                  int ok = 1;
+                  for (int e = 0; e < 3; e++) {
+                    if (e >= o->dim) continue;
+                    int N = o->n[l][e];
+                    if (nbp[e] < 0 || nbp[e] >= N) {
+                      if (o->bc == O_BC_PERIODIC) nbp[e] = (nbp[e] % N + N) % N; else ok = 0;
+                    }
+                  }
+                  if (!ok || !cell_block_internal(o, l, nbp[0], nbp[1], nbp[2])) continue;
+                  /* fine cells on the refined side adjacent to the face */
+                  int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+                  double mean[5] = {0, 0, 0, 0, 0};
+                  int nt2 = (o->dim == 3) ? 2 : 1;
+                  int first = 1;
+                  for (int b = 0; b < nt2; b++)
+                    for (int a = 0; a < 2; a++) {
+                      int f[3];
+                      f[d] = side ? 2 * nbp[d] : 2 * nbp[d] + 1;
+                      f[t1] = 2 * (t1 == 0 ? i : (t1 == 1 ? j : k)) + a;
+                      if (o->dim == 3) f[t2] = 2 * (t2 == 1 ? j : k) + b; else f[2] = 0;
+                      long fc = cidx(o, l + 1, f[0], f[1], f[2]);
+                      int fside = side ? 0 : 1; /* the fine cell's face toward the coarse cell */
+                      for (int v = 0; v < o->nv; v++) {
+                        double x = o->rf[l + 1][((long)(fside * 3 + d) * o->nv + v) * ncf + fc];
+                        if (first) mean[v] = x; else mean[v] = mean[v] + x;
+                      }
+                      first = 0;
+                    }
+                  for (int v = 0; v < o->nv; v++) {
+                    double m = mean[v] * (o->dim == 3 ? 0.25 : 0.5);
+                    double rcv = o->rc[l][((long)(side * 3 + d) * o->nv + v) * nc + c];
+                    double corr = (rcv - m) / o->dx[l][d];
+                    if (side) q[(long)v * nc + c] = q[(long)v * nc + c] + corr;
+                    else q[(long)v * nc + c] = q[(long)v * nc + c] - corr;
+                  }
+                }
+            }
+      }
+}
+
+/* copy the cells of existing (or leaf-only) blocks of level l from src to dst */
+static void copy_blocks(const orc *o, int l, const double *src, double *dst, int leaves_only) {
+  long nc = o->ncell[l];
+  for (int k = 0; k < o->n[l][2]; k++)
+    for (int j = 0; j < o->n[l][1]; j++)
+      for (int i = 0; i < o->n[l][0]; i++) {
+        int keep = leaves_only ? block_is_leaf(o, l, i / OB, j / OB, k / OB) : cell_block_exists(o, l, i, j, k);
+        if (!keep) continue;
+        long c = cidx(o, l, i, j, k);
+        for (int v = 0; v < o->nv; v++) dst[(long)v * nc + c] = src[(long)v * nc + c];
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* creation, initial data                                                    */
+
+orc *orc_create(int dim, int levels, const int *nb0, const double *lo, const double *hi,
+                double gamma, int bc) {
+  if (dim < 2 || dim > 3 || levels < 1 || levels > OMAXL) return NULL;
+  orc *o = (orc *)calloc(1, sizeof(orc));
+  o->dim = dim; o->nv = dim + 2; o->L = levels - 1; o->bc = bc; o->gamma = gamma;
+  for (int d = 0; d < 3; d++) { o->lo[d] = lo[d]; o->hi[d] = hi[d]; }
+  for (int l = 0; l <= o->L; l++) {
+    o->ncell[l] = 1; o->nblk[l] = 1;
+    for (int d = 0; d < 3; d++) {
+      if (d < dim) { o->nb[l][d] = nb0[d] << l; o->n[l][d] = o->nb[l][d] * OB; }
+      else { o->nb[l][d] = 1; o->n[l][d] = 1; }
+      o->dx[l][d] = (d < dim) ? (hi[d] - lo[d]) / (double)o->n[l][d] : 1.0;
+      o->ncell[l] *= o->n[l][d]; o->nblk[l] *= o->nb[l][d];
+    }
+    o->ex[l] = (uint8_t *)calloc((size_t)o->nblk[l], 1);
+    o->sig[l] = (uint8_t *)calloc((size_t)o->nblk[l], 1);
+    o->maxdet[l] = (double *)calloc((size_t)o->nblk[l], sizeof(double));
+    o->q[l] = alloc_level(o, l);
+    o->qs[l] = alloc_level(o, l);
+    o->q0[l] = alloc_level(o, l);
+    o->rc[l] = (double *)calloc((size_t)6 * o->nv * o->ncell[l], sizeof(double));
+    o->rf[l] = (double *)calloc((size_t)6 * o->nv * o->ncell[l], sizeof(double));
+  }
+  return o;
+}
+
+void orc_destroy(orc *o) {
+  if (!o) return;
+  for (int l = 0; l <= o->L; l++) {
+    free(o->ex[l]); free(o->sig[l]); free(o->maxdet[l]); free(o->q[l]); free(o->qs[l]);
+    free(o->q0[l]); free(o->rc[l]); free(o->rf[l]);
+  }
+  free(o);
+}
+
+/* primitive initial state at a point */
+static void ic_point(const orc *o, int kind, const double *P, const double *x, double *w) {
+  w[0] = 1.0; w[1] = w[2] = w[3] = 0.0; w[4] = 1.0;
+  if (kind == O_IC_QUADRANTS) {
+    double xc = 0.5 * (o->lo[0] + o->hi[0]), yc = 0.5 * (o->lo[1] + o->hi[1]);
+    int quad; /* I top-right, II top-left, III bottom-left, IV bottom-right (Table 1) */
+    if (x[1] >= yc) quad = (x[0] >= xc) ? 0 : 1; else quad = (x[0] >= xc) ? 3 : 2;
+    w[0] = P[4 * quad + 0]; w[1] = P[4 * quad + 1]; w[2] = P[4 * quad + 2]; w[4] = P[4 * quad + 3];
+  } else if (kind == O_IC_ELLIPSOID) {
+    double r2 = 0.0;
+    for (int d = 0; d < 3; d++) { double t = (x[d] - P[d]) / P[3 + d]; r2 = r2 + t * t; }
+    if (r2 < 1.0) { w[0] = P[6]; w[4] = P[7]; } else { w[0] = P[8]; w[4] = P[9]; }
+  } else if (kind == O_IC_SHOCKTUBE) {
+    int ax = (int)P[0];
+    int left = x[ax] < P[1];
+    w[0] = left ? P[2] : P[5];
+    w[1 + ax] = left ? P[3] : P[6];
+    w[4] = left ? P[4] : P[7];
+  } else if (kind == O_IC_UNIFORM) {
+    w[0] = P[0]; w[1] = P[1]; w[2] = P[2]; w[3] = P[3]; w[4] = P[4];
+  } else if (kind == O_IC_WAVE) {
+    double s = x[0] + x[1];
+    if (o->dim == 3) s = s + x[2];
+    w[0] = 1.0 + P[0] * sin(2.0 * M_PI * s);
+    w[1] = P[1]; w[2] = P[2]; w[3] = P[3]; w[4] = P[4];
+  } else if (kind == O_IC_ROTATED_ELLIPSOID) {
+    double a = P[0], b = P[1], c = P[2], rc = P[3], th = P[4], ph = P[5];
+    double x1 = x[0] * cos(th) - x[1] * sin(th);
+    double t = x[0] * sin(th) + x[1] * cos(th);
+    double x2 = t * cos(ph) - x[2] * sin(ph);
+    double x3 = t * sin(ph) + x[2] * cos(ph);
+    double r = sqrt((x1 / a) * (x1 / a) + (x2 / b) * (x2 / b) + (x3 / c) * (x3 / c));
+    int in = r < rc;
+    w[0] = in ? P[6] : P[8];
+    w[4] = (o->gamma - 1.0) * (in ? P[7] : P[9]); /* at rest: p = (gamma-1) rho e */
+  }
+  if (o->dim == 2) w[3] = 0.0;
+}
+
+/* sample the finest level at cell centres (reading: no quadrature), project
+   down to every coarser level; every block of every level exists */
+int orc_init(orc *o, int kind, const double *P, int np) {
+  (void)np;
+  int L = o->L;
+  for (int l = 0; l <= L; l++) memset(o->ex[l], 1, (size_t)o->nblk[l]);
+  long nc = o->ncell[L];
+  for (int k = 0; k < o->n[L][2]; k++)
+    for (int j = 0; j < o->n[L][1]; j++)
+      for (int i = 0; i < o->n[L][0]; i++) {
+        double x[3] = {0.0, 0.0, 0.0};
+        int id[3] = {i, j, k};
+        for (int d = 0; d < o->dim; d++) x[d] = o->lo[d] + ((double)id[d] + 0.5) * o->dx[L][d];
+        double w[5], Q[5];
+        ic_point(o, kind, P, x, w);
+        prim_to_cons(o, w, Q);
+        long c = cidx(o, L, i, j, k);
+        for (int v = 0; v < o->nv; v++) o->q[L][(long)v * nc + c] = Q[v];
+      }
+  restrict_all(o, o->q);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* dense access for the tests                                                */
+
+long orc_level_cells(const orc *o, int l) { return o->ncell[l]; }
+long orc_level_blocks(const orc *o, int l) { return o->nblk[l]; }
+void orc_get_level(const orc *o, int l, double *out) {
+  memcpy(out, o->q[l], sizeof(double) * (size_t)o->nv * (size_t)o->ncell[l]);
+}
+void orc_set_level(orc *o, int l, const double *in) {
+  long nc = o->ncell[l];
+  for (int k = 0; k < o->n[l][2]; k++)
+    for (int j = 0; j < o->n[l][1]; j++)
+      for (int i = 0; i < o->n[l][0]; i++) {
+        long c = cidx(o, l, i, j, k);
+        int e = cell_block_exists(o, l, i, j, k);
+        for (int v = 0; v < o->nv; v++) o->q[l][(long)v * nc + c] = e ? in[(long)v * nc + c] : NAN;
+      }
+}
+void orc_get_exist(const orc *o, int l, uint8_t *out) { memcpy(out, o->ex[l], (size_t)o->nblk[l]); }
+/* replace the tree; cells of blocks that become absent turn NaN; cells of new
+   blocks must be set by the caller (orc_set_level) */
+void orc_set_exist(orc *o, int l, const uint8_t *in) {
+  long nc = o->ncell[l];
+  memcpy(o->ex[l], in, (size_t)o->nblk[l]);
+  for (int k = 0; k < o->n[l][2]; k++)
+    for (int j = 0; j < o->n[l][1]; j++)
+      for (int i = 0; i < o->n[l][0]; i++)
+        if (!cell_block_exists(o, l, i, j, k))
+          for (int v = 0; v < o->nv; v++) o->q[l][(long)v * nc + cidx(o, l, i, j, k)] = NAN;
+}
+void orc_get_sig(const orc *o, int l, uint8_t *sig, double *maxdet) {
+  memcpy(sig, o->sig[l], (size_t)o->nblk[l]);
+  if (maxdet) memcpy(maxdet, o->maxdet[l], sizeof(double) * (size_t)o->nblk[l]);
+}
+void orc_get_scale(const orc *o, double *s) { for (int v = 0; v < o->nv; v++) s[v] = o->scale[v]; }
+void orc_restrict_all(orc *o) { restrict_all(o, o->q); }
+
+/* ------------------------------------------------------------------------ */
+/* CFL time step (Section 2.2 "CFL-type condition"; readings: maximum over
+   directions of |v_n| + c, minimum over the leaf cells).  With level-dependent
+   steps the finest step is returned: each leaf's limit is scaled by 2^(l-L). */
+double orc_dt(const orc *o, double cfl, int lts) {
+  double best = INFINITY;
+  for (int l = 0; l <= o->L; l++) {
+    for (int k = 0; k < o->n[l][2]; k++)
+      for (int j = 0; j < o->n[l][1]; j++)
+        for (int i = 0; i < o->n[l][0]; i++) {
+          if (!block_is_leaf(o, l, i / OB, j / OB, k / OB)) continue;
+          double Q[5], w[5];
+          get_cell(o, l, o->q[l], cidx(o, l, i, j, k), Q);
+          cons_to_prim(o, Q, w);
+          if (!(w[0] > 0.0) || !(w[4] > 0.0)) return -1.0;
+          double c = sqrt((o->gamma * w[4]) / w[0]);
+          for (int d = 0; d < o->dim; d++) {
+            double r = o->dx[l][d] / (fabs(w[1 + d]) + c);
+            if (lts) r = ldexp(r, l - o->L);
+            if (r < best) best = r;
+          }
+        }
+  }
+  return cfl * best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* time stepping                                                             */
+
+/* one step of explicit midpoint RK2 (Section 2) with one time step for all
+   leaves: Q* = Q^n - dt/2 F(Q^n), Q^{n+1} = Q^n - dt F(Q*).  Virtual cells are
+   predicted from the next coarser level of the same stage; refined blocks hold
+   the projection of their children; the stage-2 fluxes at coarse-fine faces
+   are corrected as in Fig. 2. */
+static void step_global(orc *o, double dt) {
+  int L = o->L;
+  /* stage 1 */
+  for (int l = 0; l <= L; l++) {
+    double *E = build_ext(o, l, o->q[l], l > 0 ? o->q[l - 1] : NULL);
+    fv_level(o, l, E, o->q[l], o->qs[l], 0.5, dt, 0, 0, 0);
+    free(E);
+  }
+  restrict_all(o, o->qs);
+  /* stage 2 */
+  double *qn[OMAXL];
+  for (int l = 0; l <= L; l++) {
+    qn[l] = alloc_level(o, l);
+    double *E = build_ext(o, l, o->qs[l], l > 0 ? o->qs[l - 1] : NULL);
+    fv_level(o, l, E, o->q[l], qn[l], 1.0, dt, 0, 1, 0);
+    free(E);
+  }
+  for (int l = 0; l <= L; l++) {
+    copy_blocks(o, l, qn[l], o->q[l], 1);
+    free(qn[l]);
+  }
+  for (int l = 0; l < L; l++) reflux_level(o, l, o->q[l]);
+  restrict_all(o, o->q);
+}
+
+/* q0 + theta*(q - q0) on existing blocks of level l (linear time interpolation) */
+static double *time_interp(const orc *o, int l, double theta) {
+  double *r = alloc_level(o, l);
+  long nc = o->ncell[l];
+  for (long m = 0; m < (long)o->nv * nc; m++) r[m] = o->q0[l][m] + theta * (o->q[l][m] - o->q0[l][m]);
+  return r;
+}
+
+static int level_has_blocks(const orc *o, int l) {
+  for (long b = 0; b < o->nblk[l]; b++) if (o->ex[l][b]) return 1;
+  return 0;
+}
+
+/* Recursive level advance with level-dependent steps dt_l = 2^(L-l) dt_L
+   (Section 2.1 MRLT, Section 2.2 Fig. 2): every existing block of level l is
+   updated (refined ones are overwritten by the projection afterwards); virtual
+   cells of level l are predicted from level l-1 interpolated linearly in time
+   (stage 1 at the sub-step start, stage 2 at its midpoint); then level l+1 takes
+   two sub-steps, is averaged onto level l, and the level-l leaves bordering it
+   get the flux correction. */
+static void advance_level(orc *o, int l, int sub, double dtL) {
+  int L = o->L;
+  double dtl = ldexp(dtL, L - l);
+  double th1 = 0.5 * (double)sub, th2 = th1 + 0.25;
+  copy_blocks(o, l, o->q[l], o->q0[l], 0);
+  double *C1 = l > 0 ? time_interp(o, l - 1, th1) : NULL;
+  double *E = build_ext(o, l, o->q[l], C1);
+  fv_level(o, l, E, o->q[l], o->qs[l], 0.5, dtl, 1, 0, 0);
+  free(E); free(C1);
+  double *C2 = l > 0 ? time_interp(o, l - 1, th2) : NULL;
+  E = build_ext(o, l, o->qs[l], C2);
+  double *qn = alloc_level(o, l);
+  fv_level(o, l, E, o->q[l], qn, 1.0, dtl, 1, 1, sub == 1);
+  free(E); free(C2);
+  copy_blocks(o, l, qn, o->q[l], 0);
+  free(qn);
+  if (l < L && level_has_blocks(o, l + 1)) {
+    advance_level(o, l + 1, 0, dtL);
+    advance_level(o, l + 1, 1, dtL);
+    restrict_level(o, l, o->q);
+    reflux_level(o, l, o->q[l]);
+  }
+}
+
+/* one time step: global (lts = 0, dt for every leaf) or one coarse step of
+   the level recursion (lts = 1, dt = finest-level step) */
+void orc_step(orc *o, double dt, int lts) {
+  if (lts) advance_level(o, 0, 0, dt);
+  else step_global(o, dt);
+}
+
+/* ------------------------------------------------------------------------ */
+/* MR analysis (Section 2.1): details d = Q_{l} - prediction from level l-1 on
+   every existing block of level >= 1; a block is significant when
+   max over cells and variables of |d_v| / s_v exceeds eps (strict), with the
+   same eps on all levels.  Reading for the normalisation s_v (maxima over the
+   level-0 field): s_rho = max|rho|, s_E = max|E|, s_m = max|rho| * max|v_n|,
+   each at least 1e-14 * max|rho|.  precision 1: the state is rounded to single
+   precision and the whole decision is taken in single precision. */
+int orc_analyse(orc *o, double eps, int precision, long *n_sig) {
+  int L = o->L, nv = o->nv, dim = o->dim;
+  long total = 0;
+  /* scales */
+  double mr = 0.0, mE = 0.0, mv = 0.0;
+  float fr = 0.0f, fE = 0.0f, fv = 0.0f;
+  long nc0 = o->ncell[0];
+  for (long c = 0; c < nc0; c++) {
+    double rho = o->q[0][c], E = o->q[0][(long)(dim + 1) * nc0 + c];
+    if (precision == 0) {
+      if (fabs(rho) > mr) mr = fabs(rho);
+      if (fabs(E) > mE) mE = fabs(E);
+      for (int d = 0; d < dim; d++) {
+        double v = fabs(o->q[0][(long)(1 + d) * nc0 + c] / rho);
+        if (v > mv) mv = v;
+      }
+    } else {
+      float rf = (float)rho, Ef = (float)E;
+      if (fabsf(rf) > fr) fr = fabsf(rf);
+      if (fabsf(Ef) > fE) fE = fabsf(Ef);
+      for (int d = 0; d < dim; d++) {
+        float v = fabsf((float)o->q[0][(long)(1 + d) * nc0 + c] / rf);
+        if (v > fv) fv = v;
+      }
+    }
+  }
+  double s[5];
+  float sf[5];
+  if (precision == 0) {
+    double fl = 1e-14 * mr;
+    double sm = mr * mv;
+    s[0] = mr > fl ? mr : fl;
+    for (int d = 0; d < dim; d++) s[1 + d] = sm > fl ? sm : fl;
+    s[dim + 1] = mE > fl ? mE : fl;
+    for (int v = 0; v < nv; v++) o->scale[v] = s[v];
+  } else {
+    float fl = 1e-14f * fr;
+    float sm = fr * fv;
+    sf[0] = fr > fl ? fr : fl;
+    for (int d = 0; d < dim; d++) sf[1 + d] = sm > fl ? sm : fl;
+    sf[dim + 1] = fE > fl ? fE : fl;
+    for (int v = 0; v < nv; v++) o->scale[v] = (double)sf[v];
+  }
+  memset(o->sig[0], 0, (size_t)o->nblk[0]);
+  for (long b = 0; b < o->nblk[0]; b++) o->maxdet[0][b] = 0.0;
+  float *qf[OMAXL] = {0};
+  if (precision == 1)
+    for (int l = 0; l <= L; l++) {
+      qf[l] = (float *)malloc(sizeof(float) * (size_t)nv * (size_t)o->ncell[l]);
+      for (long m = 0; m < (long)nv * o->ncell[l]; m++) qf[l][m] = (float)o->q[l][m];
+    }
+  for (int l = 1; l <= L; l++) {
+    long nc = o->ncell[l];
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++)
+        for (int bi = 0; bi < o->nb[l][0]; bi++) {
+          long b = bidx(o, l, bi, bj, bk);
+          o->sig[l][b] = 0;
+          o->maxdet[l][b] = 0.0;
+          if (!o->ex[l][b]) continue;
+          double md = 0.0;
+          float mdf = 0.0f;
+          int kz = dim == 3 ? OB : 1;
+          for (int kk = 0; kk < kz; kk++)
+            for (int jj = 0; jj < OB; jj++)
+              for (int ii = 0; ii < OB; ii++) {
+                int i = bi * OB + ii, j = bj * OB + jj, k = (dim == 3) ? bk * OB + kk : 0;
+                long c = cidx(o, l, i, j, k);
+                for (int v = 0; v < nv; v++) {
+                  if (precision == 0) {
+                    double d = o->q[l][(long)v * nc + c] - predict_cell(o, l, o->q[l - 1], v, i, j, k);
+                    double r = fabs(d) / s[v];
+                    if (r > md) md = r;
+                  } else {
+                    float d = qf[l][(long)v * nc + c] - predict_cell_f(o, l, qf[l - 1], v, i, j, k);
+                    float r = fabsf(d) / sf[v];
+                    if (r > mdf) mdf = r;
+                  }
+                }
+              }
+          if (precision == 0) { o->maxdet[l][b] = md; o->sig[l][b] = md > eps; }
+          else { o->maxdet[l][b] = (double)mdf; o->sig[l][b] = mdf > (float)eps; }
+          total += o->sig[l][b];
+        }
+  }
+  for (int l = 0; l <= L; l++) free(qf[l]);
+  if (n_sig) *n_sig = total;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* scaled-gradient refinement flags with a one-cell buffer (Section 2.2):
+   cell i is flagged when |rho(Q_{i+alpha}) - rho(Q_i)| > eps_w for some
+   alpha in {0,1}^d \ {0} (reading: unscaled, density only); a block of level
+   l < L is flagged when a flagged cell lies within one cell of it.  Blocks are
+   then grouped per row of the level's block grid into runs of at most 8 blocks
+   (64 cells) whose flagged fraction stays >= eta_tol (reading of the
+   clustering step); every block of a run is flagged for refinement. */
+static int grad_flag_cell(const orc *o, int l, const double *E, int i, int j, int k, double epsw) {
+  double r0 = E[cidx(o, l, i, j, k)];
+  int kz = o->dim == 3 ? 2 : 1;
+  for (int c = 0; c < kz; c++)
+    for (int b = 0; b < 2; b++)
+      for (int a = 0; a < 2; a++) {
+        if (a == 0 && b == 0 && c == 0) continue;
+        int ii = bc_cell(o, l, 0, i + a), jj = bc_cell(o, l, 1, j + b), kk = bc_cell(o, l, 2, k + c);
+        double r1 = E[cidx(o, l, ii, jj, kk)];
+        if (fabs(r1 - r0) > epsw) return 1;
+      }
+  return 0;
+}
+
+static void grad_flags(orc *o, double epsw, double eta) {
+  int L = o->L, dim = o->dim;
+  for (int l = 0; l <= L; l++) { memset(o->sig[l], 0, (size_t)o->nblk[l]); }
+  for (int l = 0; l < L; l++) {
+    double *E = build_ext(o, l, o->q[l], l > 0 ? o->q[l - 1] : NULL);
+    uint8_t *fl = (uint8_t *)calloc((size_t)o->nblk[l], 1);
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++)
+        for (int bi = 0; bi < o->nb[l][0]; bi++) {
+          if (!block_exists(o, l, bi, bj, bk)) continue;
+          int hit = 0;
+          int k0 = dim == 3 ? bk * OB - 1 : 0, k1 = dim == 3 ? bk * OB + OB : 0;
+          for (int k = k0; k <= k1 && !hit; k++)
+            for (int j = bj * OB - 1; j <= bj * OB + OB && !hit; j++)
+              for (int i = bi * OB - 1; i <= bi * OB + OB && !hit; i++) {
+                int id[3] = {i, j, k}, ok = 1;
+                for (int d = 0; d < dim; d++) {
+                  if (id[d] < 0 || id[d] >= o->n[l][d]) {
+                    if (o->bc == O_BC_PERIODIC) id[d] = bc_cell(o, l, d, id[d]); else ok = 0;
+                  }
+                }
+                if (ok && grad_flag_cell(o, l, E, id[0], id[1], id[2], epsw)) hit = 1;
+              }
+          fl[bidx(o, l, bi, bj, bk)] = (uint8_t)hit;
+        }
+    /* row clustering along the first direction */
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++) {
+        int nx = o->nb[l][0];
+        int x = 0;
+        while (x < nx) {
+          if (!fl[bidx(o, l, x, bj, bk)]) { x++; continue; }
+          int best = x, cnt = 0;
+          for (int e = x; e < nx && e - x < 8; e++) {
+            if (fl[bidx(o, l, e, bj, bk)]) {
+              cnt++;
+              if ((double)cnt >= eta * (double)(e - x + 1)) best = e;
+            }
+          }
+          for (int e = x; e <= best; e++) o->sig[l][bidx(o, l, e, bj, bk)] = 1;
+          x = best + 1;
+        }
+      }
+    free(fl);
+    free(E);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* tree update (Section 2.1 refinement / coarsening, gradedness).  Block reading
+   of the cell rules:
+     MR:   a significant block B of level l >= 1 is kept, its 3^d-1 same-level
+           neighbours are kept (safety zone), and for l < L its 2^d children are
+           added (refinement by one level);
+     GRAD: the children of every flagged block of level l < L are added;
+   closure, level by level from the finest: a needed block brings its siblings
+   (complete child sets), its parent, and the 3^d-1 neighbours of its parent
+   (gradedness: at most one level between neighbouring leaves).  Blocks that
+   leave the tree are dropped (the parent holds their projection); blocks that
+   enter it are filled by the prediction from their parent level, coarse to
+   fine.  Level 0 always exists. */
+static void mark_nbrs(orc *o, uint8_t **need, int l, int bi, int bj, int bk) {
+  int kz0 = o->dim == 3 ? -1 : 0, kz1 = o->dim == 3 ? 1 : 0;
+  for (int c = kz0; c <= kz1; c++)
+    for (int b = -1; b <= 1; b++)
+      for (int a = -1; a <= 1; a++) {
+        int x = bc_block(o, l, 0, bi + a), y = bc_block(o, l, 1, bj + b), z = bc_block(o, l, 2, bk + c);
+        if (x < 0 || y < 0 || z < 0) continue;
+        need[l][bidx(o, l, x, y, z)] = 1;
+      }
+}
+
+int orc_adapt(orc *o, int crit, double eps, double epsw, double eta, int precision) {
+  int L = o->L, dim = o->dim;
+  if (crit == O_CRIT_MR) orc_analyse(o, eps, precision, NULL);
+  else grad_flags(o, epsw, eta);
+  uint8_t *need[OMAXL] = {0};
+  for (int l = 0; l <= L; l++) need[l] = (uint8_t *)calloc((size_t)o->nblk[l], 1);
+  memset(need[0], 1, (size_t)o->nblk[0]);
+  for (int l = 0; l <= L; l++)
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++)
+        for (int bi = 0; bi < o->nb[l][0]; bi++) {
+          long b = bidx(o, l, bi, bj, bk);
+          if (!o->ex[l][b] || !o->sig[l][b]) continue;
+          if (crit == O_CRIT_MR) {
+            if (l == 0) continue;
+            need[l][b] = 1;
+            mark_nbrs(o, need, l, bi, bj, bk);
+          }
+          if (l < L) {
+            int kz = dim == 3 ? 2 : 1;
+            for (int c = 0; c < kz; c++)
+              for (int bb = 0; bb < 2; bb++)
+                for (int a = 0; a < 2; a++)
+                  need[l + 1][bidx(o, l + 1, 2 * bi + a, 2 * bj + bb, dim == 3 ? 2 * bk + c : 0)] = 1;
+          }
+        }
+  for (int l = L; l >= 1; l--)
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++)
+        for (int bi = 0; bi < o->nb[l][0]; bi++) {
+          if (!need[l][bidx(o, l, bi, bj, bk)]) continue;
+          int pi = bi >> 1, pj = bj >> 1, pk = bk >> 1;
+          int kz = dim == 3 ? 2 : 1;
+          for (int c = 0; c < kz; c++)
+            for (int bb = 0; bb < 2; bb++)
+              for (int a = 0; a < 2; a++)
+                need[l][bidx(o, l, 2 * pi + a, 2 * pj + bb, dim == 3 ? 2 * pk + c : 0)] = 1;
+          need[l - 1][bidx(o, l - 1, pi, pj, pk)] = 1;
+          mark_nbrs(o, need, l - 1, pi, pj, pk);
+        }
+  /* apply, coarse to fine: drop, then predict new blocks from the level below */
+  for (int l = 1; l <= L; l++) {
+    long nc = o->ncell[l];
+    uint8_t *old = (uint8_t *)malloc((size_t)o->nblk[l]);
+    memcpy(old, o->ex[l], (size_t)o->nblk[l]);
+    memcpy(o->ex[l], need[l], (size_t)o->nblk[l]);
+    for (int k = 0; k < o->n[l][2]; k++)
+      for (int j = 0; j < o->n[l][1]; j++)
+        for (int i = 0; i < o->n[l][0]; i++) {
+          long b = bidx(o, l, i / OB, j / OB, k / OB), c = cidx(o, l, i, j, k);
+          if (!need[l][b]) {
+            for (int v = 0; v < o->nv; v++) o->q[l][(long)v * nc + c] = NAN;
+          } else if (!old[b]) {
+            for (int v = 0; v < o->nv; v++) o->q[l][(long)v * nc + c] = predict_cell(o, l, o->q[l - 1], v, i, j, k);
+          }
+        }
+    free(old);
+  }
+  for (int l = 0; l <= L; l++) free(need[l]);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* diagnostics                                                               */
+
+/* conserved totals: sum over leaf cells of Q_v times the cell volume */
+void orc_totals(const orc *o, double *out) {
+  for (int v = 0; v < o->nv; v++) out[v] = 0.0;
+  for (int l = 0; l <= o->L; l++) {
+    long nc = o->ncell[l];
+    double vol = o->dx[l][0] * o->dx[l][1];
+    if (o->dim == 3) vol = vol * o->dx[l][2];
+    for (int k = 0; k < o->n[l][2]; k++)
+      for (int j = 0; j < o->n[l][1]; j++)
+        for (int i = 0; i < o->n[l][0]; i++) {
+          if (!block_is_leaf(o, l, i / OB, j / OB, k / OB)) continue;
+          long c = cidx(o, l, i, j, k);
+          for (int v = 0; v < o->nv; v++) out[v] += o->q[l][(long)v * nc + c] * vol;
+        }
+  }
+}
+
+/* leaf representation projected to the finest level by repeated third-order
+   prediction (Section 3, error assessment for MR) */
+void orc_project_finest(const orc *o, double *out) {
+  double *prev = NULL;
+  for (int l = 0; l <= o->L; l++) {
+    double *E = alloc_level(o, l);
+    long nc = o->ncell[l];
+    for (int k = 0; k < o->n[l][2]; k++)
+      for (int j = 0; j < o->n[l][1]; j++)
+        for (int i = 0; i < o->n[l][0]; i++) {
+          long c = cidx(o, l, i, j, k);
+          int ex = cell_block_exists(o, l, i, j, k);
+          for (int v = 0; v < o->nv; v++)
+            E[(long)v * nc + c] = ex ? o->q[l][(long)v * nc + c] : predict_cell(o, l, prev, v, i, j, k);
+        }
+    free(prev);
+    prev = E;
+  }
+  memcpy(out, prev, sizeof(double) * (size_t)o->nv * (size_t)o->ncell[o->L]);
+  free(prev);
+}
+
+/* AUSM+ flux of two conservative states (consistency checks) */
+void orc_flux(orc *o, int nd, const double *Ql, const double *Qr, double *F) {
+  double wl[5], wr[5];
+  cons_to_prim(o, Ql, wl);
+  cons_to_prim(o, Qr, wr);
+  if (o->dim == 2) { wl[3] = 0.0; wr[3] = 0.0; }
+  ausm_plus(o, nd, wl, wr, F);
+}
+void orc_physical_flux(orc *o, int nd, const double *Q, double *F) { physical_flux(o, nd, Q, F); }
+
+/* one cell's prediction from a given coarse level array (tests of the operator) */
+double orc_predict(orc *o, int lf, const double *coarse, int v, int i, int j, int k) {
+  return predict_cell(o, lf, coarse, v, i, j, k);
+}
