@@ -1,0 +1,217 @@
+/*
+ * mrfv.h -- C interface of the GB300 (sm_103a) adaptive multiresolution
+ * finite-volume solver for the compressible Euler equations.
+ *
+ * Method (arXiv:1603.05211): cell averages Q = (rho, rho v, rho e) of the Euler
+ * equations (Section 2, Eqs. 2.1-2.3) advanced by dQ/dt = -F(Q) with MUSCL
+ * reconstruction (van Albada limiter), the AUSM+ flux and the explicit midpoint
+ * RK2 rule (Section 2), on the leaves of a graded tree of 8^d-cell blocks that a
+ * multiresolution analysis (projection, third-order prediction, details,
+ * eps-thresholding; Section 2.1) or a scaled-gradient criterion (Section 2.2)
+ * adapts every step; coarse-fine faces are made conservative by flux
+ * correction (Section 2.1 virtual leaves, Section 2.2 / Fig. 2), and levels can
+ * advance with their own step 2^(L-l) dt (Section 2.1 MRLT, Fig. 2).
+ *
+ * Conventions for every entry point:
+ *   - return value: MRFV_OK (0) or a negative MRFV_ERR_* code; the text of the
+ *     last error of a context is given by mrfv_last_error();
+ *   - host pointers are owned by the caller and only read or written during the
+ *     call; the library keeps no reference to them;
+ *   - all device state is owned by the context (allocated by the library with
+ *     cudaMalloc, or placed in a caller-provided device arena that must outlive
+ *     the context);
+ *   - work is issued on the configured CUDA stream.  Entry points that return
+ *     host data synchronise that stream; the others only enqueue work;
+ *   - after MRFV_ERR_CUDA, MRFV_ERR_POOL_FULL or MRFV_ERR_TIMEOUT the context's
+ *     state is undefined and it must be destroyed;
+ *   - there is no CPU fallback: without a usable GPU mrfv_create fails.
+ *
+ * Dense level layout used by download/upload: level l has N_l = base_blocks*8*2^l
+ * cells per dimension; a level array is [v][k][j][i] (i fastest), nv = dim+2
+ * conserved variables (rho, rho v_1..rho v_d, rho e), always in double.
+ * Block maps are [bk][bj][bi] bytes, base_blocks*2^l blocks per dimension.
+ */
+#ifndef MRFV_H
+#define MRFV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRFV_OK 0
+#define MRFV_ERR_ARG (-1)         /* invalid argument or configuration */
+#define MRFV_ERR_POOL_FULL (-2)   /* block pool capacity exceeded */
+#define MRFV_ERR_NONPHYSICAL (-3) /* rho <= 0, p <= 0 or NaN met by the time-step reduction */
+#define MRFV_ERR_TIMEOUT (-4)     /* a bounded device wait expired */
+#define MRFV_ERR_CUDA (-5)        /* CUDA runtime error */
+#define MRFV_ERR_STATE (-6)       /* call out of order (e.g. step before init) */
+#define MRFV_ERR_TREE (-7)        /* a kernel met a tree that is not graded */
+
+enum { MRFV_FP64 = 0, MRFV_FP32 = 1 };
+enum { MRFV_BC_TRANSMISSIVE = 0, MRFV_BC_PERIODIC = 1 };
+enum { MRFV_CRIT_MR = 0, MRFV_CRIT_GRAD = 1 };
+/* initial data (parameter lists as in the Python module mrfv_inputs) */
+enum {
+  MRFV_IC_QUADRANTS = 0,         /* 16: (rho, v1, v2, p) of quadrants I, II, III, IV (Table 1 order) */
+  MRFV_IC_ELLIPSOID = 1,         /* 10: cx, cy, cz, a, b, c, rho_in, p_in, rho_out, p_out */
+  MRFV_IC_SHOCKTUBE = 2,         /* 8: axis, x0, rho_L, u_L, p_L, rho_R, u_R, p_R */
+  MRFV_IC_UNIFORM = 3,           /* 5: rho, v1, v2, v3, p */
+  MRFV_IC_WAVE = 4,              /* 5: amp, v1, v2, v3, p; rho = 1 + amp sin(2 pi sum x) */
+  MRFV_IC_ROTATED_ELLIPSOID = 5  /* 10: a, b, c, r_c, theta, phi, rho_in, rhoe_in, rho_out, rhoe_out */
+};
+
+#define MRFV_MAX_LEVELS 12
+
+/* Solver configuration; plain data, copied by mrfv_create. */
+typedef struct {
+  int dim;              /* 2 or 3 */
+  int precision;        /* MRFV_FP64 (parity mode) or MRFV_FP32 (state and flux in single precision) */
+  int levels;           /* number of levels L+1 (1..MRFV_MAX_LEVELS); level l has base_blocks*2^l blocks per dim */
+  int base_blocks[3];   /* blocks of 8 cells per dimension on level 0 (unused dimensions: 1) */
+  double lo[3], hi[3];  /* domain box */
+  int bc;               /* MRFV_BC_TRANSMISSIVE (outflow, Section 4) or MRFV_BC_PERIODIC */
+  double gamma;         /* ratio of specific heats (1.4, Section 2) */
+  double cfl;           /* CFL number of the time-step rule */
+  double t_end;         /* > 0: steps with a CFL-computed dt are clipped to end at t_end */
+  int adapt;            /* 1: analyse and adapt the tree after every (coarse) step */
+  int criterion;        /* MRFV_CRIT_MR (details vs eps) or MRFV_CRIT_GRAD (density gradient vs eps_w) */
+  double eps;           /* MR threshold, the same on every level (Section 2.1) */
+  double eps_w;         /* gradient threshold (Section 2.2) */
+  double eta_tol;       /* clustering efficiency (Section 2.2) */
+  int lts;              /* 1: level-dependent time steps 2^(L-l) dt (Section 2.1 MRLT, Fig. 2) */
+  int64_t pool_blocks;  /* block pool capacity; 0 = every block of every level (never full) */
+  void *stream;         /* cudaStream_t to issue work on; NULL = the legacy default stream */
+  void *device_arena;   /* optional device memory for all state (e.g. from a PyTorch tensor) */
+  size_t arena_bytes;   /* its size; must be >= mrfv_arena_bytes(config) */
+} mrfv_config;
+
+typedef struct {
+  int levels;
+  int64_t blocks[MRFV_MAX_LEVELS];  /* existing blocks per level */
+  int64_t leaves[MRFV_MAX_LEVELS];  /* leaf blocks per level */
+  int64_t total_blocks, total_leaves;
+  int64_t leaf_cells;               /* cells advanced per step (leaves x 8^d) */
+  int64_t pool_capacity;
+  double t;                         /* simulated time */
+  double last_dt;                   /* last (finest-level) time step */
+  int64_t steps;                    /* steps taken */
+  int64_t cell_updates;             /* sum over steps of the leaf cells advanced */
+} mrfv_stats;
+
+typedef struct mrfv_ctx mrfv_ctx;
+
+/* Fill *cfg with defaults: 2D, FP64, one level of 1x1 blocks on [0,1]^2,
+   transmissive, gamma 1.4, CFL 0.5, eps 1e-3, eps_w 0.05, eta_tol 0.8. */
+int mrfv_config_default(mrfv_config *cfg);
+
+/* Device bytes the context needs for cfg (pool, maps, lists, scratch). */
+size_t mrfv_arena_bytes(const mrfv_config *cfg);
+
+/* Create a context on the current CUDA device.  Validates cfg (MRFV_ERR_ARG)
+   and allocates the block pool (MRFV_ERR_CUDA when memory is short). */
+int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out);
+int mrfv_destroy(mrfv_ctx *ctx);
+/* Text of the last error of ctx (valid until the next call on ctx); for a NULL
+   ctx, the last error of mrfv_create on this thread. */
+const char *mrfv_last_error(const mrfv_ctx *ctx);
+
+/* Initial data (Section 4.1 / 4.2 set-ups): every block of every level is
+   created, the finest level is sampled at cell centres, coarser levels are its
+   projections (Section 2.1), t = 0.  With cfg.adapt the tree is then adapted
+   (analysis + thresholding), so only the blocks the threshold keeps remain. */
+int mrfv_init_state(mrfv_ctx *ctx, int ic_kind, const double *params, int n_params);
+
+/* MR analysis (Section 2.1): projection onto refined blocks, details of every
+   block of level >= 1 against the third-order prediction from its parent level,
+   normalised by the level-0 maxima, thresholded with eps (strict >).
+   *n_significant (may be NULL) = significant blocks.  Synchronises. */
+int mrfv_analyse(mrfv_ctx *ctx, double eps, int64_t *n_significant);
+
+/* Tree update from the current flags/state with cfg.criterion: refinement by
+   one level and safety zone (MR) or gradient flags + clustering (GRAD),
+   gradedness closure, removal of blocks that are no longer needed, prediction
+   of new blocks from their parent level, rebuild of neighbour tables and work
+   lists.  use_proposer is reserved and must be 0.  *n_blocks (may be NULL)
+   receives the number of existing blocks (synchronises when non-NULL). */
+int mrfv_adapt(mrfv_ctx *ctx, int use_proposer, int64_t *n_blocks);
+
+/* CFL time step over the leaves: cfl * min over leaf cells and directions of
+   dx_{l,n} / (|v_n| + c); with cfg.lts the finest step (each leaf's limit scaled
+   by 2^(l-L)).  Returns MRFV_ERR_NONPHYSICAL on rho <= 0, p <= 0 or NaN. */
+int mrfv_compute_dt(mrfv_ctx *ctx, double *dt_out);
+
+/* Ghost strips of level l (Section 2.2 ghost cells; Section 2.1 virtual
+   leaves): every face of a leaf block of level l whose same-level neighbour is
+   absent gets its two cell layers predicted (third order) from level l-1 of the
+   chosen buffer (0 = state Q^n, 1 = RK stage Q*).  Same-level neighbours and
+   domain boundaries need no strip: the flux kernel reads them directly. */
+int mrfv_fill_ghosts(mrfv_ctx *ctx, int level, int buffer);
+
+/* One step.  dt > 0: that (finest-level) step; dt <= 0: the CFL step, clipped
+   to cfg.t_end when set.  Global stepping: one midpoint-RK2 step of every leaf
+   (stage fluxes at coarse-fine faces corrected as in Fig. 2).  cfg.lts: one
+   coarse step of the level recursion of Fig. 2 (2^L finest sub-steps).  With
+   cfg.adapt the tree is adapted after the step.  *dt_out (may be NULL; then
+   nothing synchronises) receives the finest-level dt used. */
+int mrfv_step(mrfv_ctx *ctx, double dt, double *dt_out);
+
+/* The level recursion of Fig. 2 from level l (levels l..L advance by one step
+   of level l, dt_l = 2^(L-l) dt_finest), without adaptation. */
+int mrfv_step_level(mrfv_ctx *ctx, int level, double dt_finest);
+
+/* Projection (Section 2.1) of level fine_level onto the refined blocks of
+   fine_level-1; fine_level <= 0 restricts every level, finest first. */
+int mrfv_restrict(mrfv_ctx *ctx, int fine_level);
+
+/* Conserved totals: sum over leaf cells of Q_v times the cell volume, in double
+   (nv values).  Synchronises. */
+int mrfv_conserved_totals(mrfv_ctx *ctx, double *out, int n);
+
+int mrfv_get_stats(mrfv_ctx *ctx, mrfv_stats *out);
+
+/* Dense copy of level l into host[nv * cells(l)] (double; NaN in absent
+   blocks); exist (may be NULL) receives the block map of level l. */
+int mrfv_download_level(mrfv_ctx *ctx, int level, double *host, int64_t n, uint8_t *exist);
+/* Write host[nv * cells(l)] into the existing blocks of level l. */
+int mrfv_upload_level(mrfv_ctx *ctx, int level, const double *host, int64_t n);
+
+/* Block map of level l (1 = block exists). */
+int mrfv_get_tree(mrfv_ctx *ctx, int level, uint8_t *exist, int64_t n);
+/* Replace the tree: exist_all = the block maps of levels 0..L concatenated.
+   The tree must hold every level-0 block, complete child sets, parents and the
+   gradedness rule (MRFV_ERR_ARG otherwise).  New blocks are predicted from
+   their parent level; removed blocks are dropped. */
+int mrfv_set_tree(mrfv_ctx *ctx, const uint8_t *exist_all, int64_t n);
+
+/* Last analysis of level l: flags[b] = 1 when block b was significant (MR) or
+   flagged for refinement (GRAD); maxdet[b] (may be NULL) = its largest
+   normalised detail, in the state precision widened to double. */
+int mrfv_get_flags(mrfv_ctx *ctx, int level, uint8_t *flags, double *maxdet, int64_t n);
+
+/* Wait for all work issued on the context's stream. */
+int mrfv_synchronize(mrfv_ctx *ctx);
+
+/* Diagnostics (no counterpart in the paper, which profiled its CPU codes with
+   perf, Section 4.1 Table 5): kernel launch count and CUDA-event timing of the
+   finite-volume stage launches. */
+typedef struct {
+  int64_t launches;     /* kernels this context launched since profiling was enabled */
+  int64_t fv_launches;  /* finite-volume stage launches timed */
+  double fv_ms;         /* sum of their CUDA-event durations on the context stream */
+  double fv_bytes;      /* algorithmic bytes of those launches: per cell, stage 1 reads
+                           Q^n and writes Q* (2 nv words), stage 2 reads Q^n and Q* and
+                           writes Q^{n+1} (3 nv words) */
+} mrfv_profile;
+/* enable != 0: reset the counters and bracket every finite-volume stage launch
+   with CUDA events on the context stream; 0: stop. */
+int mrfv_profile_enable(mrfv_ctx *ctx, int enable);
+/* Read the counters (synchronises the stream). */
+int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRFV_H */

@@ -1,0 +1,733 @@
+// C interface (include/mrfv.h): context, device arena, and the host-side
+// sequencing of the kernels for the time step of arXiv:1603.05211
+// (Section 2 RK2 step, Section 2.1 adaptation cycle, Fig. 2 level recursion).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "launch.h"
+#include "mrfv.h"
+
+using namespace mrfv;
+
+struct mrfv_ctx {
+  mrfv_config cfg;
+  Geo g;
+  int prec;         // MRFV_FP64 / MRFV_FP32
+  size_t tsize;     // bytes per state value
+  cudaStream_t st;
+  int nsm, grid, bgrid, fvgrid;
+  char *arena;
+  size_t arena_bytes;
+  bool own_arena;
+  void *U, *Us, *U0, *G, *FR, *scale;
+  uint8_t *sig, *need, *gflag, *kbits;
+  double *maxdet;
+  int32_t *freestack, *newlist, *tcount, *toff;
+  int *freetop, *nnew;
+  double *dsc;              // [0] dt of the finest level, [1] t
+  unsigned long long *red;  // reductions
+  long long *counter;       // [0] cell updates, [1] steps
+  double *totals;
+  int ntiles;
+  long long maptotal, mtotal;
+  bool initialized;
+  std::string err;
+  // diagnostics
+  long long nlaunch;
+  bool prof;
+  std::vector<cudaEvent_t> evs;  // start/end pairs of timed stage launches
+  size_t ev_used;
+  unsigned long long *dbytes;
+};
+
+static thread_local std::string g_create_error;
+
+namespace {
+
+int fail(mrfv_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int check_launch(mrfv_ctx *c, const char *where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, MRFV_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return MRFV_OK;
+}
+
+// synchronise the stream and turn the device error word into a status
+int check_device(mrfv_ctx *c, const char *where) {
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return fail(c, MRFV_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  int bits = 0;
+  e = cudaMemcpy(&bits, c->g.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(c, MRFV_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  if (bits) {
+    cudaMemset(c->g.err, 0, sizeof(int));
+    if (bits & EB_POOL) return fail(c, MRFV_ERR_POOL_FULL, std::string(where) + ": block pool capacity exceeded");
+    if (bits & EB_TREE) return fail(c, MRFV_ERR_TREE, std::string(where) + ": a kernel met a block tree that is not graded");
+    if (bits & EB_NONPHYS)
+      return fail(c, MRFV_ERR_NONPHYSICAL, std::string(where) + ": non-physical state (rho <= 0, p <= 0 or NaN)");
+  }
+  return MRFV_OK;
+}
+
+int ilog2_ceil(int x) {
+  int b = 0;
+  while ((1 << b) < x) b++;
+  return b;
+}
+
+bool fill_geo(const mrfv_config *cfg, Geo &g, long long &maptotal, long long &mtotal, long long &full) {
+  memset(&g, 0, sizeof(g));
+  if (cfg->dim != 2 && cfg->dim != 3) return false;
+  if (cfg->levels < 1 || cfg->levels > MAXL) return false;
+  g.dim = cfg->dim;
+  g.nv = cfg->dim + 2;
+  g.L = cfg->levels - 1;
+  g.bc = cfg->bc;
+  g.gamma = cfg->gamma;
+  for (int d = 0; d < 3; d++) g.lo[d] = cfg->lo[d];
+  maptotal = 0;
+  mtotal = 0;
+  for (int l = 0; l <= g.L; l++) {
+    long long nblk = 1;
+    int mx = 1;
+    for (int d = 0; d < 3; d++) {
+      if (d < g.dim) {
+        long long n = (long long)cfg->base_blocks[d] << l;
+        if (cfg->base_blocks[d] < 1 || n > (1 << 20)) return false;
+        g.nb[l][d] = (int)n;
+        g.dx[l][d] = (cfg->hi[d] - cfg->lo[d]) / (double)(n * BS);
+        if (!(g.dx[l][d] > 0.0)) return false;
+        if (g.nb[l][d] > mx) mx = g.nb[l][d];
+      } else {
+        g.nb[l][d] = 1;
+        g.dx[l][d] = 1.0;
+      }
+      nblk *= g.nb[l][d];
+    }
+    g.mapoff[l] = maptotal;
+    maptotal += nblk;
+    g.mbits[l] = ilog2_ceil(mx);
+    g.moff[l] = mtotal;
+    mtotal += 1ll << (g.mbits[l] * g.dim);
+  }
+  g.mapoff[g.L + 1] = maptotal;
+  g.moff[g.L + 1] = mtotal;
+  full = maptotal;
+  return true;
+}
+
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = (off + 255) & ~(size_t)255;
+    off = o + bytes;
+    return o;
+  }
+};
+
+// Assign every device buffer an offset in the arena; returns the total size.
+size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long maptotal, long long mtotal, int ntiles,
+              mrfv_ctx *c) {
+  size_t ts = cfg->precision == MRFV_FP32 ? 4 : 8;
+  int nv = g.nv, B = block_cells(g.dim), TF = face_cells(g.dim);
+  Layout L;
+  size_t state = (size_t)nv * cap * B * ts;
+  size_t oU = L.take(state), oUs = L.take(state), oU0 = L.take(state);
+  size_t oG = L.take((size_t)nv * cap * 2 * g.dim * 2 * TF * ts);
+  size_t oFR = L.take((size_t)nv * cap * 2 * g.dim * TF * ts);
+  size_t oidx = L.take(maptotal * 4), olev = L.take(cap * 4), ocoord = L.take(cap * 12), onbr = L.take(cap * 24);
+  size_t ocm = L.take(cap), oloff = L.take(LK_NUM * (MAXL + 2) * 4), olists = L.take((size_t)LK_NUM * cap * 4);
+  size_t oerr = L.take(4);
+  size_t osig = L.take(maptotal), oneed = L.take(maptotal), ogf = L.take(maptotal), omd = L.take(maptotal * 8);
+  size_t okb = L.take(mtotal), otc = L.take((size_t)LK_NUM * ntiles * 4), oto = L.take((size_t)LK_NUM * ntiles * 4);
+  size_t ofs = L.take(cap * 4), oft = L.take(4), onl = L.take(cap * 4), onn = L.take(4);
+  size_t odsc = L.take(4 * 8), ored = L.take(4 * 8), ocnt = L.take(2 * 8), otot = L.take(5 * 8), osc = L.take(5 * ts);
+  size_t obyt = L.take(8);
+  if (c) {
+    char *a = c->arena;
+    c->U = a + oU; c->Us = a + oUs; c->U0 = a + oU0; c->G = a + oG; c->FR = a + oFR;
+    c->g.idx = (int32_t *)(a + oidx); c->g.slot_level = (int32_t *)(a + olev);
+    c->g.slot_coord = (int32_t *)(a + ocoord); c->g.nbr = (int32_t *)(a + onbr);
+    c->g.cmask = (uint8_t *)(a + ocm); c->g.loff = (int32_t *)(a + oloff); c->g.lists = (int32_t *)(a + olists);
+    c->g.err = (int *)(a + oerr);
+    c->sig = (uint8_t *)(a + osig); c->need = (uint8_t *)(a + oneed); c->gflag = (uint8_t *)(a + ogf);
+    c->maxdet = (double *)(a + omd); c->kbits = (uint8_t *)(a + okb);
+    c->tcount = (int32_t *)(a + otc); c->toff = (int32_t *)(a + oto);
+    c->freestack = (int32_t *)(a + ofs); c->freetop = (int *)(a + oft);
+    c->newlist = (int32_t *)(a + onl); c->nnew = (int *)(a + onn);
+    c->dsc = (double *)(a + odsc); c->red = (unsigned long long *)(a + ored);
+    c->counter = (long long *)(a + ocnt); c->totals = (double *)(a + otot); c->scale = a + osc;
+    c->dbytes = (unsigned long long *)(a + obyt);
+  }
+  return L.off + 256;
+}
+
+long long capacity_of(const mrfv_config *cfg, long long full) {
+  return cfg->pool_blocks > 0 ? (long long)cfg->pool_blocks : full;
+}
+
+int ntiles_of(long long mtotal) { return (int)((mtotal + scan_tile_entries() - 1) / scan_tile_entries()); }
+
+// ---------------------------------------------------------------- typed sequencing
+template <typename T>
+struct Seq {
+  mrfv_ctx *c;
+  T *U() { return (T *)c->U; }
+  T *Us() { return (T *)c->Us; }
+  T *U0() { return (T *)c->U0; }
+  T *G() { return (T *)c->G; }
+  T *FR() { return (T *)c->FR; }
+
+  void restrict_all(T *A) {
+    for (int l = c->g.L - 1; l >= 0; l--) launch_restrict<T>(c->g, l, A, c->grid, c->st);
+    c->nlaunch += c->g.L;
+  }
+  void fv(int kind, int l0, int l1, const T *Uin, const T *U0b, T *Uout, double coef, int lts, int record) {
+    FVArgs<T> a;
+    a.Uin = Uin; a.U0 = U0b; a.Uout = Uout; a.G = G(); a.FR = FR();
+    a.kind = kind; a.l0 = l0; a.l1 = l1; a.coef = coef; a.dt = c->dsc; a.lts = lts; a.record = record;
+    a.words = (coef == 0.5 ? 2 : 3) * c->g.nv;
+    a.bytes = c->prof ? c->dbytes : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+      if (c->ev_used + 2 > c->evs.size()) {
+        for (int k = 0; k < 64; k++) {
+          cudaEvent_t e;
+          cudaEventCreate(&e);
+          c->evs.push_back(e);
+        }
+      }
+      e0 = c->evs[c->ev_used];
+      e1 = c->evs[c->ev_used + 1];
+      c->ev_used += 2;
+      cudaEventRecord(e0, c->st);
+    }
+    launch_fv<T>(c->g, a, c->fvgrid, c->st);
+    if (c->prof) cudaEventRecord(e1, c->st);
+    c->nlaunch += 1;
+  }
+  void ghost(int l0, int l1, const T *A, const T *A0, double theta) {
+    if (l1 < 1) return;
+    launch_ghost<T>(c->g, l0 < 1 ? 1 : l0, l1, A, A0, theta, G(), c->bgrid, c->st);
+    c->nlaunch += 1;
+  }
+  // one midpoint-RK2 step of every leaf with the same dt (Section 2)
+  void step_global() {
+    int L = c->g.L;
+    ghost(1, L, U(), nullptr, 0.0);
+    fv(LK_LEAF, 0, L, U(), U(), Us(), 0.5, 0, 0);
+    restrict_all(Us());
+    ghost(1, L, Us(), nullptr, 0.0);
+    fv(LK_LEAF, 0, L, Us(), U(), U(), 1.0, 0, 1);
+    if (L > 0) {
+      launch_reflux<T>(c->g, 0, L - 1, U(), FR(), c->grid, c->st);
+      c->nlaunch += 1;
+    }
+    restrict_all(U());
+  }
+  // Fig. 2 recursion: level l takes one step of dt_l = 2^(L-l) dt (all its blocks),
+  // then level l+1 two steps, then projection and flux correction of level l.
+  void advance(int l, int sub) {
+    int L = c->g.L;
+    double th1 = 0.5 * sub, th2 = th1 + 0.25;
+    launch_copy_level<T>(c->g, l, U(), U0(), c->grid, c->st);
+    c->nlaunch += 1;
+    if (l >= 1) ghost(l, l, U(), U0(), th1);
+    fv(LK_EXIST, l, l, U(), U(), Us(), 0.5, 1, 0);
+    if (l >= 1) ghost(l, l, U(), U0(), th2);
+    fv(LK_EXIST, l, l, Us(), U(), U(), 1.0, 1, sub == 1 ? 2 : 1);
+    if (l < L) {
+      advance(l + 1, 0);
+      advance(l + 1, 1);
+      launch_restrict<T>(c->g, l, U(), c->grid, c->st);
+      launch_reflux<T>(c->g, l, l, U(), FR(), c->grid, c->st);
+      c->nlaunch += 2;
+    }
+  }
+  void analyse(double eps) {
+    launch_scales<T>(c->g, U(), c->red + 0, (T *)c->scale, c->grid, c->st);
+    cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
+    cudaMemsetAsync(c->maxdet, 0, c->maptotal * 8, c->st);
+    launch_details<T>(c->g, U(), (const T *)c->scale, eps, c->sig, c->maxdet, c->bgrid, c->st);
+    c->nlaunch += 3;
+  }
+  void prolong_new() {
+    for (int l = 1; l <= c->g.L; l++) launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(), c->bgrid, c->st);
+    c->nlaunch += c->g.L;
+  }
+  void compute_dt(int lts) {
+    launch_dt<T>(c->g, U(), lts, c->red + 3, c->grid, c->st);
+    launch_dt_final(c->red + 3, c->cfg.cfl, c->cfg.t_end, c->dsc, c->dsc + 1, c->st);
+    c->nlaunch += 2;
+  }
+  void init_level(const ICParams &ic) {
+    launch_init<T>(c->g, ic, c->cfg.hi, U(), c->grid, c->st);
+    c->nlaunch += 1;
+    restrict_all(U());
+  }
+  void gradflags() {
+    cudaMemsetAsync(c->gflag, 0, c->maptotal, c->st);
+    cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
+    launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->gflag, c->bgrid, c->st);
+    launch_cluster(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->grid, c->st);
+    c->nlaunch += 2;
+  }
+};
+
+template <typename F>
+void dispatch(mrfv_ctx *c, F f) {
+  if (c->prec == MRFV_FP32) {
+    Seq<float> s{c};
+    f(s);
+  } else {
+    Seq<double> s{c};
+    f(s);
+  }
+}
+
+// free, allocate, rebuild neighbour tables and lists, optionally predict new blocks
+void apply_need(mrfv_ctx *c, bool prolong) {
+  cudaMemsetAsync(c->nnew, 0, sizeof(int), c->st);
+  launch_free(c->g, c->need, c->freestack, c->freetop, c->grid, c->st);
+  launch_alloc(c->g, c->need, c->freestack, c->freetop, c->newlist, c->nnew, c->grid, c->st);
+  launch_rebuild_lists(c->g, c->kbits, c->tcount, c->toff, c->ntiles, c->grid, c->st);
+  c->nlaunch += 6;
+  if (prolong) dispatch(c, [&](auto &s) { s.prolong_new(); });
+}
+
+// analysis / flags -> needed blocks -> closure -> apply
+void adapt_tree(mrfv_ctx *c) {
+  const Geo &g = c->g;
+  if (c->cfg.criterion == MRFV_CRIT_MR) dispatch(c, [&](auto &s) { s.analyse(c->cfg.eps); });
+  else dispatch(c, [&](auto &s) { s.gradflags(); });
+  cudaMemsetAsync(c->need, 0, c->maptotal, c->st);
+  cudaMemsetAsync(c->need, 1, g.mapoff[1], c->st);
+  launch_need_mark(g, c->sig, c->need, c->cfg.criterion, c->grid, c->st);
+  for (int l = g.L; l >= 1; l--) launch_need_close(g, l, c->need, c->grid, c->st);
+  c->nlaunch += 1 + g.L;
+  apply_need(c, true);
+}
+
+bool valid_tree(const mrfv_ctx *c, const uint8_t *ex) {
+  const Geo &g = c->g;
+  auto at = [&](int l, int x, int y, int z) -> bool {
+    return ex[g.mapoff[l] + x + (long long)g.nb[l][0] * (y + (long long)g.nb[l][1] * z)] != 0;
+  };
+  for (long long t = 0; t < g.mapoff[1]; t++)
+    if (!ex[t]) return false;
+  for (int l = 1; l <= g.L; l++)
+    for (int z = 0; z < g.nb[l][2]; z++)
+      for (int y = 0; y < g.nb[l][1]; y++)
+        for (int x = 0; x < g.nb[l][0]; x++) {
+          if (!at(l, x, y, z)) continue;
+          int px = x >> 1, py = y >> 1, pz = g.dim == 3 ? z >> 1 : 0;
+          for (int cz = 0; cz < (g.dim == 3 ? 2 : 1); cz++)
+            for (int cy = 0; cy < 2; cy++)
+              for (int cx = 0; cx < 2; cx++)
+                if (!at(l, 2 * px + cx, 2 * py + cy, g.dim == 3 ? 2 * pz + cz : 0)) return false;
+          for (int c3 = (g.dim == 3 ? -1 : 0); c3 <= (g.dim == 3 ? 1 : 0); c3++)
+            for (int b = -1; b <= 1; b++)
+              for (int a = -1; a <= 1; a++) {
+                int q[3] = {px + a, py + b, pz + c3};
+                bool in = true;
+                for (int d = 0; d < g.dim; d++) {
+                  int N = g.nb[l - 1][d];
+                  if (q[d] < 0 || q[d] >= N) {
+                    if (g.bc == MRFV_BC_PERIODIC) q[d] = (q[d] % N + N) % N;
+                    else in = false;
+                  }
+                }
+                if (in && !at(l - 1, q[0], q[1], q[2])) return false;
+              }
+        }
+  return true;
+}
+
+long long level_cells(const Geo &g, int l) {
+  long long n = 1;
+  for (int d = 0; d < g.dim; d++) n *= (long long)g.nb[l][d] * BS;
+  return n;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int mrfv_config_default(mrfv_config *cfg) {
+  if (!cfg) return MRFV_ERR_ARG;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->dim = 2;
+  cfg->precision = MRFV_FP64;
+  cfg->levels = 1;
+  cfg->base_blocks[0] = cfg->base_blocks[1] = cfg->base_blocks[2] = 1;
+  cfg->hi[0] = cfg->hi[1] = cfg->hi[2] = 1.0;
+  cfg->bc = MRFV_BC_TRANSMISSIVE;
+  cfg->gamma = 1.4;
+  cfg->cfl = 0.5;
+  cfg->eps = 1e-3;
+  cfg->eps_w = 0.05;
+  cfg->eta_tol = 0.8;
+  return MRFV_OK;
+}
+
+size_t mrfv_arena_bytes(const mrfv_config *cfg) {
+  if (!cfg) return 0;
+  Geo g;
+  long long mt, mo, full;
+  if (!fill_geo(cfg, g, mt, mo, full)) return 0;
+  return layout(cfg, g, capacity_of(cfg, full), mt, mo, ntiles_of(mo), nullptr);
+}
+
+int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
+  if (!cfg || !out) return fail(nullptr, MRFV_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (cfg->precision != MRFV_FP32 && cfg->precision != MRFV_FP64) return fail(nullptr, MRFV_ERR_ARG, "precision");
+  if (cfg->bc != MRFV_BC_TRANSMISSIVE && cfg->bc != MRFV_BC_PERIODIC) return fail(nullptr, MRFV_ERR_ARG, "bc");
+  if (cfg->criterion != MRFV_CRIT_MR && cfg->criterion != MRFV_CRIT_GRAD) return fail(nullptr, MRFV_ERR_ARG, "criterion");
+  if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0)) return fail(nullptr, MRFV_ERR_ARG, "gamma/cfl");
+  if (cfg->pool_blocks < 0) return fail(nullptr, MRFV_ERR_ARG, "pool_blocks");
+  {
+    Geo gg;
+    long long a, b, f;
+    if (!fill_geo(cfg, gg, a, b, f)) return fail(nullptr, MRFV_ERR_ARG, "dim/levels/base_blocks/domain");
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(nullptr, MRFV_ERR_CUDA, "no CUDA device: this library has no CPU path");
+  }
+  mrfv_ctx *c = new mrfv_ctx();
+  c->cfg = *cfg;
+  c->prec = cfg->precision;
+  c->tsize = c->prec == MRFV_FP32 ? 4 : 8;
+  c->st = (cudaStream_t)cfg->stream;
+  long long full;
+  fill_geo(cfg, c->g, c->maptotal, c->mtotal, full);
+  c->g.cap = capacity_of(cfg, full);
+  if (c->g.cap > (1ll << 30)) {
+    delete c;
+    return fail(nullptr, MRFV_ERR_ARG, "pool capacity too large");
+  }
+  c->ntiles = ntiles_of(c->mtotal);
+  if (c->ntiles > 65535) {
+    delete c;
+    return fail(nullptr, MRFV_ERR_ARG, "hierarchy too large");
+  }
+  size_t bytes = layout(cfg, c->g, c->g.cap, c->maptotal, c->mtotal, c->ntiles, nullptr);
+  if (cfg->device_arena) {
+    if (cfg->arena_bytes < bytes) {
+      delete c;
+      return fail(nullptr, MRFV_ERR_ARG, "device_arena smaller than mrfv_arena_bytes()");
+    }
+    c->arena = (char *)cfg->device_arena;
+    c->own_arena = false;
+  } else {
+    if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return fail(nullptr, MRFV_ERR_CUDA, "cudaMalloc of the device arena failed");
+    }
+    c->own_arena = true;
+  }
+  c->arena_bytes = bytes;
+  layout(cfg, c->g, c->g.cap, c->maptotal, c->mtotal, c->ntiles, c);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+  c->grid = c->nsm * 8;
+  c->bgrid = c->nsm * 16;
+  c->fvgrid = c->nsm * (c->prec == MRFV_FP32 ? fv_ctas_per_sm<float>(cfg->dim) : fv_ctas_per_sm<double>(cfg->dim));
+  cudaMemsetAsync(c->g.idx, 0xff, c->maptotal * 4, c->st);
+  cudaMemsetAsync(c->g.slot_level, 0xff, c->g.cap * 4, c->st);
+  cudaMemsetAsync(c->g.loff, 0, LK_NUM * (MAXL + 2) * 4, c->st);
+  cudaMemsetAsync(c->g.err, 0, 4, c->st);
+  cudaMemsetAsync(c->dsc, 0, 4 * 8, c->st);
+  cudaMemsetAsync(c->counter, 0, 2 * 8, c->st);
+  launch_init_freestack(c->freestack, c->freetop, c->g.cap, c->grid, c->st);
+  int rc = check_launch(c, "mrfv_create");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_create");
+  if (rc != MRFV_OK) {
+    g_create_error = c->err;
+    mrfv_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MRFV_OK;
+}
+
+int mrfv_destroy(mrfv_ctx *c) {
+  if (!c) return MRFV_OK;
+  cudaStreamSynchronize(c->st);
+  for (cudaEvent_t e : c->evs) cudaEventDestroy(e);
+  if (c->own_arena && c->arena) cudaFree(c->arena);
+  delete c;
+  return MRFV_OK;
+}
+
+const char *mrfv_last_error(const mrfv_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int mrfv_init_state(mrfv_ctx *c, int kind, const double *params, int n) {
+  if (!c || n < 0 || n > 16 || (n > 0 && !params) || kind < 0 || kind > 5) return fail(c, MRFV_ERR_ARG, "init: arguments");
+  if (c->g.cap < c->maptotal) return fail(c, MRFV_ERR_POOL_FULL, "init needs a pool that holds every block of every level");
+  ICParams ic;
+  memset(&ic, 0, sizeof(ic));
+  ic.kind = kind;
+  for (int i = 0; i < n; i++) ic.p[i] = params[i];
+  cudaMemsetAsync(c->need, 1, c->maptotal, c->st);
+  apply_need(c, false);
+  dispatch(c, [&](auto &s) { s.init_level(ic); });
+  cudaMemsetAsync(c->dsc, 0, 4 * 8, c->st);
+  cudaMemsetAsync(c->counter, 0, 2 * 8, c->st);
+  if (c->cfg.adapt) adapt_tree(c);
+  int rc = check_launch(c, "mrfv_init_state");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_init_state");
+  c->initialized = rc == MRFV_OK;
+  return rc;
+}
+
+int mrfv_analyse(mrfv_ctx *c, double eps, int64_t *n_sig) {
+  if (!c) return MRFV_ERR_ARG;
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "analyse before init");
+  dispatch(c, [&](auto &s) {
+    s.restrict_all(s.U());
+    s.analyse(eps);
+  });
+  int rc = check_launch(c, "mrfv_analyse");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_analyse");
+  if (rc != MRFV_OK) return rc;
+  if (n_sig) {
+    std::vector<uint8_t> h(c->maptotal);
+    cudaMemcpy(h.data(), c->sig, c->maptotal, cudaMemcpyDeviceToHost);
+    int64_t k = 0;
+    for (uint8_t b : h) k += b;
+    *n_sig = k;
+  }
+  return MRFV_OK;
+}
+
+int mrfv_adapt(mrfv_ctx *c, int use_proposer, int64_t *n_blocks) {
+  if (!c || use_proposer != 0) return fail(c, MRFV_ERR_ARG, "adapt: use_proposer must be 0");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "adapt before init");
+  adapt_tree(c);
+  int rc = check_launch(c, "mrfv_adapt");
+  if (rc != MRFV_OK) return rc;
+  if (n_blocks) {
+    rc = check_device(c, "mrfv_adapt");
+    if (rc != MRFV_OK) return rc;
+    int32_t e = 0;
+    cudaMemcpy(&e, c->g.loff + LK_EXIST * (MAXL + 2) + c->g.L + 1, 4, cudaMemcpyDeviceToHost);
+    *n_blocks = e;
+  }
+  return MRFV_OK;
+}
+
+int mrfv_compute_dt(mrfv_ctx *c, double *dt_out) {
+  if (!c) return MRFV_ERR_ARG;
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "dt before init");
+  dispatch(c, [&](auto &s) { s.compute_dt(c->cfg.lts); });
+  int rc = check_launch(c, "mrfv_compute_dt");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_compute_dt");
+  if (rc == MRFV_OK && dt_out) cudaMemcpy(dt_out, c->dsc, 8, cudaMemcpyDeviceToHost);
+  return rc;
+}
+
+int mrfv_fill_ghosts(mrfv_ctx *c, int level, int buffer) {
+  if (!c || level < 1 || level > c->g.L || buffer < 0 || buffer > 1) return fail(c, MRFV_ERR_ARG, "fill_ghosts: arguments");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "fill_ghosts before init");
+  dispatch(c, [&](auto &s) { s.ghost(level, level, buffer ? s.Us() : s.U(), nullptr, 0.0); });
+  return check_launch(c, "mrfv_fill_ghosts");
+}
+
+int mrfv_step(mrfv_ctx *c, double dt, double *dt_out) {
+  if (!c) return MRFV_ERR_ARG;
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "step before init");
+  int lts = c->cfg.lts;
+  dispatch(c, [&](auto &s) {
+    if (dt > 0.0) {
+      launch_set_double(c->dsc, dt, c->st);
+      c->nlaunch += 1;
+    } else {
+      s.compute_dt(lts);
+    }
+    if (lts) s.advance(0, 0);
+    else s.step_global();
+  });
+  launch_advance(c->g, c->dsc + 1, c->dsc, lts ? ldexp(1.0, c->g.L) : 1.0, c->counter, lts, c->st);
+  c->nlaunch += 1;
+  if (c->cfg.adapt) adapt_tree(c);
+  int rc = check_launch(c, "mrfv_step");
+  if (rc != MRFV_OK) return rc;
+  if (dt_out) {
+    rc = check_device(c, "mrfv_step");
+    if (rc != MRFV_OK) return rc;
+    cudaMemcpy(dt_out, c->dsc, 8, cudaMemcpyDeviceToHost);
+  }
+  return MRFV_OK;
+}
+
+int mrfv_step_level(mrfv_ctx *c, int level, double dt) {
+  if (!c || level < 0 || level > c->g.L || !(dt > 0.0)) return fail(c, MRFV_ERR_ARG, "step_level: arguments");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "step_level before init");
+  launch_set_double(c->dsc, dt, c->st);
+  dispatch(c, [&](auto &s) { s.advance(level, 0); });
+  return check_launch(c, "mrfv_step_level");
+}
+
+int mrfv_restrict(mrfv_ctx *c, int fine_level) {
+  if (!c || fine_level > c->g.L) return fail(c, MRFV_ERR_ARG, "restrict: level");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "restrict before init");
+  dispatch(c, [&](auto &s) {
+    if (fine_level <= 0) s.restrict_all(s.U());
+    else launch_restrict(c->g, fine_level - 1, s.U(), c->grid, c->st);
+  });
+  return check_launch(c, "mrfv_restrict");
+}
+
+int mrfv_conserved_totals(mrfv_ctx *c, double *out, int n) {
+  if (!c || !out || n < c->g.nv) return fail(c, MRFV_ERR_ARG, "totals: buffer");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "totals before init");
+  dispatch(c, [&](auto &s) { launch_totals(c->g, s.U(), c->totals, c->grid, c->st); });
+  c->nlaunch += 1;
+  int rc = check_launch(c, "mrfv_conserved_totals");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_conserved_totals");
+  if (rc == MRFV_OK) cudaMemcpy(out, c->totals, c->g.nv * 8, cudaMemcpyDeviceToHost);
+  return rc;
+}
+
+int mrfv_get_stats(mrfv_ctx *c, mrfv_stats *o) {
+  if (!c || !o) return MRFV_ERR_ARG;
+  int rc = check_device(c, "mrfv_get_stats");
+  if (rc != MRFV_OK) return rc;
+  memset(o, 0, sizeof(*o));
+  std::vector<int32_t> loff(LK_NUM * (MAXL + 2));
+  cudaMemcpy(loff.data(), c->g.loff, loff.size() * 4, cudaMemcpyDeviceToHost);
+  double d[2];
+  long long cnt[2];
+  cudaMemcpy(d, c->dsc, 16, cudaMemcpyDeviceToHost);
+  cudaMemcpy(cnt, c->counter, 16, cudaMemcpyDeviceToHost);
+  o->levels = c->g.L + 1;
+  for (int l = 0; l <= c->g.L; l++) {
+    o->blocks[l] = loff[LK_EXIST * (MAXL + 2) + l + 1] - loff[LK_EXIST * (MAXL + 2) + l];
+    o->leaves[l] = loff[LK_LEAF * (MAXL + 2) + l + 1] - loff[LK_LEAF * (MAXL + 2) + l];
+    o->total_blocks += o->blocks[l];
+    o->total_leaves += o->leaves[l];
+  }
+  o->leaf_cells = o->total_leaves * block_cells(c->g.dim);
+  o->pool_capacity = c->g.cap;
+  o->last_dt = d[0];
+  o->t = d[1];
+  o->cell_updates = cnt[0];
+  o->steps = cnt[1];
+  return check_launch(c, "mrfv_get_stats");
+}
+
+int mrfv_download_level(mrfv_ctx *c, int level, double *host, int64_t n, uint8_t *exist) {
+  if (!c || level < 0 || level > c->g.L || !host) return fail(c, MRFV_ERR_ARG, "download: arguments");
+  long long nc = level_cells(c->g, level);
+  if (n != nc * c->g.nv) return fail(c, MRFV_ERR_ARG, "download: n must be nv * cells(level)");
+  double *buf = nullptr;
+  if (cudaMalloc(&buf, n * 8) != cudaSuccess) return fail(c, MRFV_ERR_CUDA, "download: staging allocation");
+  dispatch(c, [&](auto &s) { launch_gather(c->g, level, s.U(), buf, c->st); });
+  int rc = check_launch(c, "mrfv_download_level");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_download_level");
+  if (rc == MRFV_OK) cudaMemcpy(host, buf, n * 8, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (rc == MRFV_OK && exist) rc = mrfv_get_tree(c, level, exist, c->g.mapoff[level + 1] - c->g.mapoff[level]);
+  return rc;
+}
+
+int mrfv_upload_level(mrfv_ctx *c, int level, const double *host, int64_t n) {
+  if (!c || level < 0 || level > c->g.L || !host) return fail(c, MRFV_ERR_ARG, "upload: arguments");
+  long long nc = level_cells(c->g, level);
+  if (n != nc * c->g.nv) return fail(c, MRFV_ERR_ARG, "upload: n must be nv * cells(level)");
+  double *buf = nullptr;
+  if (cudaMalloc(&buf, n * 8) != cudaSuccess) return fail(c, MRFV_ERR_CUDA, "upload: staging allocation");
+  cudaMemcpy(buf, host, n * 8, cudaMemcpyHostToDevice);
+  dispatch(c, [&](auto &s) { launch_scatter(c->g, level, buf, s.U(), c->st); });
+  int rc = check_launch(c, "mrfv_upload_level");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_upload_level");
+  cudaFree(buf);
+  return rc;
+}
+
+int mrfv_get_tree(mrfv_ctx *c, int level, uint8_t *exist, int64_t n) {
+  if (!c || level < 0 || level > c->g.L || !exist) return fail(c, MRFV_ERR_ARG, "get_tree: arguments");
+  long long nb = c->g.mapoff[level + 1] - c->g.mapoff[level];
+  if (n != nb) return fail(c, MRFV_ERR_ARG, "get_tree: n must be the number of blocks of the level");
+  int rc = check_device(c, "mrfv_get_tree");
+  if (rc != MRFV_OK) return rc;
+  std::vector<int32_t> h(nb);
+  cudaMemcpy(h.data(), c->g.idx + c->g.mapoff[level], nb * 4, cudaMemcpyDeviceToHost);
+  for (long long i = 0; i < nb; i++) exist[i] = h[i] >= 0;
+  return check_launch(c, "mrfv_get_tree");
+}
+
+int mrfv_set_tree(mrfv_ctx *c, const uint8_t *ex, int64_t n) {
+  if (!c || !ex || n != c->maptotal) return fail(c, MRFV_ERR_ARG, "set_tree: n must be the total number of block positions");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "set_tree before init");
+  if (!valid_tree(c, ex)) return fail(c, MRFV_ERR_ARG, "set_tree: tree is not complete, nested and graded");
+  cudaMemcpyAsync(c->need, ex, n, cudaMemcpyHostToDevice, c->st);
+  apply_need(c, true);
+  int rc = check_launch(c, "mrfv_set_tree");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_set_tree");
+  return rc;
+}
+
+int mrfv_get_flags(mrfv_ctx *c, int level, uint8_t *flags, double *maxdet, int64_t n) {
+  if (!c || level < 0 || level > c->g.L || !flags) return fail(c, MRFV_ERR_ARG, "get_flags: arguments");
+  long long nb = c->g.mapoff[level + 1] - c->g.mapoff[level];
+  if (n != nb) return fail(c, MRFV_ERR_ARG, "get_flags: n must be the number of blocks of the level");
+  int rc = check_device(c, "mrfv_get_flags");
+  if (rc != MRFV_OK) return rc;
+  cudaMemcpy(flags, c->sig + c->g.mapoff[level], nb, cudaMemcpyDeviceToHost);
+  if (maxdet) cudaMemcpy(maxdet, c->maxdet + c->g.mapoff[level], nb * 8, cudaMemcpyDeviceToHost);
+  return check_launch(c, "mrfv_get_flags");
+}
+
+int mrfv_synchronize(mrfv_ctx *c) {
+  if (!c) return MRFV_ERR_ARG;
+  return check_device(c, "mrfv_synchronize");
+}
+
+int mrfv_profile_enable(mrfv_ctx *c, int enable) {
+  if (!c) return MRFV_ERR_ARG;
+  int rc = check_device(c, "mrfv_profile_enable");
+  if (rc != MRFV_OK) return rc;
+  c->prof = enable != 0;
+  c->ev_used = 0;
+  c->nlaunch = 0;
+  cudaMemsetAsync(c->dbytes, 0, 8, c->st);
+  return check_launch(c, "mrfv_profile_enable");
+}
+
+int mrfv_profile_read(mrfv_ctx *c, mrfv_profile *o) {
+  if (!c || !o) return MRFV_ERR_ARG;
+  int rc = check_device(c, "mrfv_profile_read");
+  if (rc != MRFV_OK) return rc;
+  memset(o, 0, sizeof(*o));
+  o->launches = c->nlaunch;
+  o->fv_launches = (int64_t)(c->ev_used / 2);
+  double ms = 0.0;
+  for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->evs[k], c->evs[k + 1]) == cudaSuccess) ms += t;
+  }
+  o->fv_ms = ms;
+  unsigned long long b = 0;
+  cudaMemcpy(&b, c->dbytes, 8, cudaMemcpyDeviceToHost);
+  o->fv_bytes = (double)b;
+  return check_launch(c, "mrfv_profile_read");
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// Device helpers: indexing, boundary rule, list ranges, coarse patches and the
+// third-order multiresolution prediction (Section 2.1 of arXiv:1603.05211).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.h"
+
+namespace mrfv {
+
+__device__ __forceinline__ long long map_index(const Geo &g, int l, int bx, int by, int bz) {
+  return g.mapoff[l] + (long long)bx + (long long)g.nb[l][0] * ((long long)by + (long long)g.nb[l][1] * bz);
+}
+
+// Boundary rule on a cell coordinate of level l: transmissive = nearest interior
+// cell (zero-gradient copy into every ghost layer), periodic = wrap.
+__device__ __forceinline__ int bc_cell(const Geo &g, int l, int d, int i) {
+  int N = g.nb[l][d] * BS;
+  if (g.bc == 1) {
+    i %= N;
+    if (i < 0) i += N;
+    return i;
+  }
+  return i < 0 ? 0 : (i >= N ? N - 1 : i);
+}
+
+// Range [begin, end) of list `kind` over levels l0..l1.
+__device__ __forceinline__ void list_range(const Geo &g, int kind, int l0, int l1, int &b, int &e) {
+  b = g.loff[kind * (MAXL + 2) + l0];
+  e = g.loff[kind * (MAXL + 2) + l1 + 1];
+}
+
+__device__ __forceinline__ void set_err(const Geo &g, int bits) { atomicOr(g.err, bits); }
+
+// Gather the coarse cells [o_d, o_d + EXT) (per dimension, level lc) of the
+// buffer A into patch[v][p], p = x + EXT*(y + EXT*z).  With A0 != null the
+// value is the linear time interpolation A0 + theta*(A - A0).  A coarse cell
+// whose block does not exist marks the tree error and reads NaN.
+template <typename T, int D, int EXT>
+__device__ void gather_patch(const Geo &g, int lc, const T *__restrict__ A, const T *__restrict__ A0, T theta,
+                             int o0, int o1, int o2, T *patch, int tid, int nthr) {
+  constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
+  constexpr int NB = (D == 2) ? 64 : 512;
+  const long long cap = g.cap;
+  for (int p = tid; p < NP; p += nthr) {
+    int x = p % EXT, y = (p / EXT) % EXT, z = (D == 3) ? p / (EXT * EXT) : 0;
+    int cx = bc_cell(g, lc, 0, o0 + x), cy = bc_cell(g, lc, 1, o1 + y), cz = (D == 3) ? bc_cell(g, lc, 2, o2 + z) : 0;
+    int32_t s = g.idx[map_index(g, lc, cx >> 3, cy >> 3, cz >> 3)];
+    int c = (cx & 7) + 8 * (cy & 7) + (D == 3 ? 64 * (cz & 7) : 0);
+    for (int v = 0; v < D + 2; v++) {
+      T val;
+      if (s < 0) {
+        val = T(__int_as_float(0x7fc00000));
+        if (v == 0) set_err(g, EB_TREE);
+      } else {
+        long long off = ((long long)v * cap + s) * NB + c;
+        val = A[off];
+        if (A0) {
+          T a0 = A0[off];
+          val = a0 + theta * (val - a0);
+        }
+      }
+      patch[v * NP + p] = val;
+    }
+  }
+}
+
+// Third-order prediction of the fine cell whose parent is patch cell
+// (x, y, z): tensor product of the 1D rule Q_k +/- (Q_{k-1} - Q_{k+1})/8 (+ for
+// the even child).  Evaluation order: Q_k, the first-order terms in direction
+// order, the mixed pairs 12, 13, 23, then the triple term; each difference is
+// formed left to right as written.  P points at one variable of the patch.
+template <typename T, int D, int EXT>
+__device__ __forceinline__ T predict(const T *P, int x, int y, int z, T si, T sj, T sk) {
+  auto at = [&](int a, int b, int c) -> T {
+    return (D == 2) ? P[(x + a) + EXT * (y + b)] : P[(x + a) + EXT * ((y + b) + EXT * (z + c))];
+  };
+  const T e1 = T(0.125), e2 = T(0.015625), e3 = T(0.001953125);
+  if (D == 2) {
+    T q = at(0, 0, 0);
+    T d1 = at(-1, 0, 0) - at(1, 0, 0);
+    T d2 = at(0, -1, 0) - at(0, 1, 0);
+    T d12 = ((at(-1, -1, 0) - at(1, -1, 0)) - at(-1, 1, 0)) + at(1, 1, 0);
+    T r = q + (si * e1) * d1;
+    r = r + (sj * e1) * d2;
+    r = r + ((si * sj) * e2) * d12;
+    return r;
+  } else {
+    T q = at(0, 0, 0);
+    T d1 = at(-1, 0, 0) - at(1, 0, 0);
+    T d2 = at(0, -1, 0) - at(0, 1, 0);
+    T d3 = at(0, 0, -1) - at(0, 0, 1);
+    T d12 = ((at(-1, -1, 0) - at(1, -1, 0)) - at(-1, 1, 0)) + at(1, 1, 0);
+    T d13 = ((at(-1, 0, -1) - at(1, 0, -1)) - at(-1, 0, 1)) + at(1, 0, 1);
+    T d23 = ((at(0, -1, -1) - at(0, 1, -1)) - at(0, -1, 1)) + at(0, 1, 1);
+    T elo = ((at(-1, -1, -1) - at(1, -1, -1)) - at(-1, 1, -1)) + at(1, 1, -1);
+    T ehi = ((at(-1, -1, 1) - at(1, -1, 1)) - at(-1, 1, 1)) + at(1, 1, 1);
+    T d123 = elo - ehi;
+    T r = q + (si * e1) * d1;
+    r = r + (sj * e1) * d2;
+    r = r + (sk * e1) * d3;
+    r = r + ((si * sj) * e2) * d12;
+    r = r + ((si * sk) * e2) * d13;
+    r = r + ((sj * sk) * e2) * d23;
+    r = r + (((si * sj) * sk) * e3) * d123;
+    return r;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T nan_val() {
+  return T(__int_as_float(0x7fc00000));
+}
+
+}  // namespace mrfv

@@ -1,0 +1,5 @@
+// Finite-volume stage and CFL kernels instantiated for double state.
+#include "fv_inst.cuh"
+namespace mrfv {
+MRFV_INSTANTIATE_FV(double)
+}

@@ -1,0 +1,49 @@
+// Launchers of the finite-volume stage and CFL kernels for one precision
+// (included by fv_f32.cu and fv_f64.cu).
+#pragma once
+#include "fv.cuh"
+#include "launch.h"
+
+namespace mrfv {
+
+template <typename T>
+void launch_fv(const Geo &g, const FVArgs<T> &a, int grid, cudaStream_t st) {
+  if (g.dim == 2) {
+    constexpr size_t sm = fv_smem_bytes<T, 2>();
+    k_fv<T, 2><<<grid, FVShape<2>::NT, sm, st>>>(g, a);
+  } else {
+    constexpr size_t sm = fv_smem_bytes<T, 3>();
+    k_fv<T, 3><<<grid, FVShape<3>::NT, sm, st>>>(g, a);
+  }
+}
+
+// Opt in to the dynamic shared memory the stage kernel needs and report how
+// many CTAs fit on one SM (sizes the persistent grid).
+template <typename T>
+int fv_ctas_per_sm(int dim) {
+  int n = 0;
+  if (dim == 2) {
+    constexpr size_t sm = fv_smem_bytes<T, 2>();
+    cudaFuncSetAttribute(k_fv<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, 2>, FVShape<2>::NT, sm);
+  } else {
+    constexpr size_t sm = fv_smem_bytes<T, 3>();
+    cudaFuncSetAttribute(k_fv<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, 3>, FVShape<3>::NT, sm);
+  }
+  return n > 0 ? n : 1;
+}
+
+template <typename T>
+void launch_dt(const Geo &g, const T *A, int lts, unsigned long long *red, int grid, cudaStream_t st) {
+  cudaMemsetAsync(red, 0x7f, sizeof(unsigned long long), st);  // a huge positive double
+  if (g.dim == 2) k_dt<T, 2><<<grid, 256, 0, st>>>(g, A, lts, red);
+  else k_dt<T, 3><<<grid, 256, 0, st>>>(g, A, lts, red);
+}
+
+#define MRFV_INSTANTIATE_FV(T)                                                                  \
+  template void launch_fv<T>(const Geo &, const FVArgs<T> &, int, cudaStream_t);                \
+  template int fv_ctas_per_sm<T>(int);                                                          \
+  template void launch_dt<T>(const Geo &, const T *, int, unsigned long long *, int, cudaStream_t);
+
+}  // namespace mrfv

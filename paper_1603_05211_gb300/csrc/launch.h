@@ -1,0 +1,42 @@
+// Host-side launchers of the kernels (one definition per precision, see the
+// *_f32.cu / *_f64.cu translation units).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.h"
+
+namespace mrfv {
+
+// multiresolution / bookkeeping kernels (mr_f32.cu, mr_f64.cu)
+template <typename T> void launch_restrict(const Geo &, int l, T *A, int grid, cudaStream_t);
+template <typename T> void launch_scales(const Geo &, const T *A, unsigned long long *red, T *scale, int grid, cudaStream_t);
+template <typename T> void launch_details(const Geo &, const T *A, const T *scale, double eps, uint8_t *sig, double *maxdet, int grid, cudaStream_t);
+template <typename T> void launch_prolong(const Geo &, int l, const int32_t *newlist, const int *nnew, T *A, int grid, cudaStream_t);
+template <typename T> void launch_ghost(const Geo &, int l0, int l1, const T *A, const T *A0, double theta, T *G, int grid, cudaStream_t);
+template <typename T> void launch_init(const Geo &, const ICParams &, const double *hi, T *A, int grid, cudaStream_t);
+template <typename T> void launch_gather(const Geo &, int l, const T *A, double *out, cudaStream_t);
+template <typename T> void launch_scatter(const Geo &, int l, const double *in, T *A, cudaStream_t);
+template <typename T> void launch_totals(const Geo &, const T *A, double *out, int grid, cudaStream_t);
+template <typename T> void launch_reflux(const Geo &, int l0, int l1, T *A, const T *FR, int grid, cudaStream_t);
+template <typename T> void launch_copy_level(const Geo &, int l, const T *src, T *dst, int grid, cudaStream_t);
+template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw, uint8_t *gflag, int grid, cudaStream_t);
+// finite-volume stage and CFL reduction (fv_f32.cu, fv_f64.cu)
+template <typename T> void launch_fv(const Geo &, const FVArgs<T> &, int grid, cudaStream_t);
+template <typename T> void launch_dt(const Geo &, const T *A, int lts, unsigned long long *red, int grid, cudaStream_t);
+template <typename T> int fv_ctas_per_sm(int dim);
+
+// integer tree work (tree.cu)
+void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t);
+void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t);
+void launch_free(const Geo &, const uint8_t *need, int32_t *fs, int *ft, int grid, cudaStream_t);
+void launch_alloc(const Geo &, const uint8_t *need, int32_t *fs, int *ft, int32_t *nl, int *nn, int grid, cudaStream_t);
+void launch_init_freestack(int32_t *fs, int *ft, long long cap, int grid, cudaStream_t);
+void launch_rebuild_lists(const Geo &, uint8_t *kbits, int32_t *tcount, int32_t *toff, int ntiles, int grid, cudaStream_t);
+int scan_tile_entries();
+void launch_cluster(const Geo &, const uint8_t *gflag, uint8_t *sig, double eta, int grid, cudaStream_t);
+void launch_set_double(double *p, double v, cudaStream_t);
+void launch_dt_final(const unsigned long long *red, double cfl, double t_end, double *dt, const double *t, cudaStream_t);
+void launch_advance(const Geo &, double *t, const double *dt, double factor, long long *counter, int lts, cudaStream_t);
+
+}  // namespace mrfv

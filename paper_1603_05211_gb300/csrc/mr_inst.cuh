@@ -1,0 +1,95 @@
+// Launchers of the multiresolution kernels for one precision (included by
+// mr_f32.cu and mr_f64.cu, which are compiled without FMA contraction so the
+// prediction, details and projection round exactly as written).
+#pragma once
+#include "launch.h"
+#include "mr.cuh"
+
+namespace mrfv {
+
+template <typename T>
+void launch_restrict(const Geo &g, int l, T *A, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_restrict<T, 2><<<grid, 256, 0, st>>>(g, l, A);
+  else k_restrict<T, 3><<<grid, 512, 0, st>>>(g, l, A);
+}
+template <typename T>
+void launch_scales(const Geo &g, const T *A, unsigned long long *red, T *scale, int grid, cudaStream_t st) {
+  cudaMemsetAsync(red, 0, 3 * sizeof(unsigned long long), st);
+  if (g.dim == 2) {
+    k_scale_max<T, 2><<<grid, 256, 0, st>>>(g, A, red);
+    k_scale_final<T, 2><<<1, 1, 0, st>>>(red, scale);
+  } else {
+    k_scale_max<T, 3><<<grid, 256, 0, st>>>(g, A, red);
+    k_scale_final<T, 3><<<1, 1, 0, st>>>(red, scale);
+  }
+}
+template <typename T>
+void launch_details(const Geo &g, const T *A, const T *scale, double eps, uint8_t *sig, double *maxdet, int grid,
+                    cudaStream_t st) {
+  if (g.dim == 2) k_details<T, 2><<<grid, 64, 0, st>>>(g, A, scale, T(eps), sig, maxdet);
+  else k_details<T, 3><<<grid, 512, 0, st>>>(g, A, scale, T(eps), sig, maxdet);
+}
+template <typename T>
+void launch_prolong(const Geo &g, int l, const int32_t *newlist, const int *nnew, T *A, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_prolong<T, 2><<<grid, 64, 0, st>>>(g, l, newlist, nnew, A);
+  else k_prolong<T, 3><<<grid, 512, 0, st>>>(g, l, newlist, nnew, A);
+}
+template <typename T>
+void launch_ghost(const Geo &g, int l0, int l1, const T *A, const T *A0, double theta, T *G, int grid,
+                  cudaStream_t st) {
+  if (g.dim == 2) k_ghost<T, 2><<<grid, 64, 4 * 64 * sizeof(T), st>>>(g, l0, l1, A, A0, T(theta), G);
+  else k_ghost<T, 3><<<grid, 256, 5 * 512 * sizeof(T), st>>>(g, l0, l1, A, A0, T(theta), G);
+}
+template <typename T>
+void launch_init(const Geo &g, const ICParams &ic, const double *hi, T *A, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_init<T, 2><<<grid, 256, 0, st>>>(g, ic, hi[0], hi[1], hi[2], A);
+  else k_init<T, 3><<<grid, 256, 0, st>>>(g, ic, hi[0], hi[1], hi[2], A);
+}
+template <typename T>
+void launch_gather(const Geo &g, int l, const T *A, double *out, cudaStream_t st) {
+  if (g.dim == 2) k_gather_level<T, 2><<<1024, 256, 0, st>>>(g, l, A, out);
+  else k_gather_level<T, 3><<<1024, 256, 0, st>>>(g, l, A, out);
+}
+template <typename T>
+void launch_scatter(const Geo &g, int l, const double *in, T *A, cudaStream_t st) {
+  if (g.dim == 2) k_scatter_level<T, 2><<<1024, 256, 0, st>>>(g, l, in, A);
+  else k_scatter_level<T, 3><<<1024, 256, 0, st>>>(g, l, in, A);
+}
+template <typename T>
+void launch_totals(const Geo &g, const T *A, double *out, int grid, cudaStream_t st) {
+  cudaMemsetAsync(out, 0, 5 * sizeof(double), st);
+  if (g.dim == 2) k_totals<T, 2><<<grid, 256, 0, st>>>(g, A, out);
+  else k_totals<T, 3><<<grid, 256, 0, st>>>(g, A, out);
+}
+template <typename T>
+void launch_reflux(const Geo &g, int l0, int l1, T *A, const T *FR, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_reflux<T, 2><<<grid, 256, 0, st>>>(g, l0, l1, A, FR);
+  else k_reflux<T, 3><<<grid, 256, 0, st>>>(g, l0, l1, A, FR);
+}
+template <typename T>
+void launch_copy_level(const Geo &g, int l, const T *src, T *dst, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_copy_level<T, 2><<<grid, 256, 0, st>>>(g, l, src, dst);
+  else k_copy_level<T, 3><<<grid, 256, 0, st>>>(g, l, src, dst);
+}
+template <typename T>
+void launch_gradflags(const Geo &g, const T *A, double epsw, uint8_t *gflag, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_gradflags<T, 2><<<grid, 128, 0, st>>>(g, A, T(epsw), gflag);
+  else k_gradflags<T, 3><<<grid, 256, 0, st>>>(g, A, T(epsw), gflag);
+}
+
+#define MRFV_INSTANTIATE_MR(T)                                                                              \
+  template void launch_restrict<T>(const Geo &, int, T *, int, cudaStream_t);                               \
+  template void launch_scales<T>(const Geo &, const T *, unsigned long long *, T *, int, cudaStream_t);     \
+  template void launch_details<T>(const Geo &, const T *, const T *, double, uint8_t *, double *, int,      \
+                                  cudaStream_t);                                                            \
+  template void launch_prolong<T>(const Geo &, int, const int32_t *, const int *, T *, int, cudaStream_t);  \
+  template void launch_ghost<T>(const Geo &, int, int, const T *, const T *, double, T *, int, cudaStream_t); \
+  template void launch_init<T>(const Geo &, const ICParams &, const double *, T *, int, cudaStream_t);      \
+  template void launch_gather<T>(const Geo &, int, const T *, double *, cudaStream_t);                      \
+  template void launch_scatter<T>(const Geo &, int, const double *, T *, cudaStream_t);                     \
+  template void launch_totals<T>(const Geo &, const T *, double *, int, cudaStream_t);                      \
+  template void launch_reflux<T>(const Geo &, int, int, T *, const T *, int, cudaStream_t);                 \
+  template void launch_copy_level<T>(const Geo &, int, const T *, T *, int, cudaStream_t);                  \
+  template void launch_gradflags<T>(const Geo &, const T *, double, uint8_t *, int, cudaStream_t);
+
+}  // namespace mrfv

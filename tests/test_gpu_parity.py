@@ -1,0 +1,276 @@
+"""GPU path (through the C interface) against the CPU oracle, element by element.
+
+Bars: FP64 mode per cell <= 1e-12 relative (the kernels evaluate the same
+expressions in the same order without contraction, so most cases are bit-exact);
+thresholding flags bit-exact on identical input state; FP32 mode <= 2e-4 relative
+L1 density error and conserved totals within 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import mrfv_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def mrfv():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    return m
+
+
+def pair(m, dim, levels, base, lo=(0, 0, 0), hi=(1, 1, 1), bc=0, precision="fp64", adapt=False,
+         criterion="mr", eps=1e-3, lts=False, ic=mi.IC_QUADRANTS, params=None, cfl=0.5):
+    params = params if params is not None else mi.quadrant_params(0)
+    s = m.Solver(dim=dim, precision=precision, levels=levels, base_blocks=base, lo=lo, hi=hi, bc=bc,
+                 adapt=adapt, criterion=criterion, eps=eps, lts=lts, cfl=cfl)
+    s.init_state(ic, params)
+    o = oracle.Oracle(dim, levels, base, lo=lo, hi=hi, bc=bc)
+    o.init(ic, params)
+    if adapt:
+        o.adapt(oracle.CRIT_GRAD if criterion == "grad" else oracle.CRIT_MR, eps=eps,
+                precision=1 if precision == "fp32" else 0)
+    return s, o
+
+
+def assert_same_tree(s, o):
+    for l in range(o.levels):
+        assert np.array_equal(s.get_tree(l), o.get_exist(l)), f"tree differs on level {l}"
+
+
+def assert_levels_close(s, o, rel=REL64):
+    for l in range(o.levels):
+        g, ex = s.download_level(l)
+        r = o.get_level(l)
+        assert np.array_equal(np.isnan(g), np.isnan(r)), f"existence differs on level {l}"
+        m = ~np.isnan(r)
+        if not m.any():
+            continue
+        scale = np.abs(r[m]).max()
+        err = np.abs(g[m] - r[m]).max()
+        assert err <= rel * scale, f"level {l}: max abs err {err:.3e} (scale {scale:.3e})"
+
+
+def run_pair(s, o, steps, lts=False, adapt_crit=None, eps=1e-3, check_dt=True, precision=0):
+    for _ in range(steps):
+        dt_o = o.dt(0.5, lts)
+        dt_g = s.step(0.0)
+        if check_dt:
+            assert dt_g == dt_o
+        o.step(dt_o, lts)
+        if adapt_crit is not None:
+            o.adapt(adapt_crit, eps=eps, precision=precision)
+
+
+# ----------------------------------------------------------------------------- uniform
+
+def test_uniform_128_fp64_200_steps_then_analysis(mrfv):
+    """128^2 four-quadrant Riemann data, CFL 0.5, 200 steps, then a 4-level MR analysis (eps 1e-3)."""
+    s, o = pair(mrfv, 2, 4, (2, 2, 1), params=mi.quadrant_params(0))
+    run_pair(s, o, 200)
+    g, _ = s.download_level(3)
+    r = o.get_level(3)
+    assert np.abs(g - r).max() <= REL64 * np.abs(r).max()
+    n_g = s.analyse(1e-3)
+    n_o = o.analyse(1e-3)
+    assert n_g == n_o
+    for l in range(1, 4):
+        fg, mg = s.get_flags(l)
+        fo, mo = o.get_sig(l)
+        assert np.array_equal(fg, fo)
+        assert np.array_equal(mg, mo)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_uniform_ragged_single_level(mrfv, bc):
+    """Non-power-of-two block grid (3 x 5 blocks), both boundary rules."""
+    s, o = pair(mrfv, 2, 1, (3, 5, 1), hi=(0.6, 1.0, 1.0), bc=bc, params=mi.quadrant_params(3))
+    run_pair(s, o, 30)
+    assert_levels_close(s, o)
+
+
+def test_single_block_domain(mrfv):
+    s, o = pair(mrfv, 2, 1, (1, 1, 1), params=mi.laxliu6_params())
+    run_pair(s, o, 10)
+    assert_levels_close(s, o)
+
+
+def test_free_stream_bit_exact_gpu(mrfv):
+    s, _ = pair(mrfv, 2, 5, (1, 1, 1), ic=mi.IC_UNIFORM, params=[1.3, 0.4, -0.2, 0.0, 0.8], adapt=True)
+    ref = [s.download_level(l)[0] for l in range(5)]
+    for _ in range(5):
+        s.step(0.001)
+    for l in range(5):
+        g = s.download_level(l)[0]
+        m = ~np.isnan(ref[l])
+        assert np.array_equal(g[m], ref[l][m])
+
+
+# ----------------------------------------------------------------------------- adaptive
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_adaptive_mr_fp64(mrfv, seed):
+    s, o = pair(mrfv, 2, 5, (1, 1, 1), adapt=True, params=mi.quadrant_params(seed))
+    assert_same_tree(s, o)
+    for _ in range(25):
+        run_pair(s, o, 1, adapt_crit=oracle.CRIT_MR)
+        assert_same_tree(s, o)
+    assert_levels_close(s, o)
+    st = s.stats()
+    assert len([x for x in st["leaves"] if x]) >= 2
+
+
+def test_adaptive_mr_fp64_periodic_conservation(mrfv):
+    s, o = pair(mrfv, 2, 5, (1, 1, 1), bc=1, adapt=True, params=mi.quadrant_params(5))
+    T0 = s.totals()
+    assert np.allclose(T0, o.totals(), rtol=1e-13)
+    run_pair(s, o, 15, adapt_crit=oracle.CRIT_MR)
+    assert_same_tree(s, o)
+    assert_levels_close(s, o)
+    T1 = s.totals()
+    assert np.all(np.abs(T1 - T0) <= 1e-12 * np.abs(T0).max())
+
+
+def test_mrlt_fp64(mrfv):
+    s, o = pair(mrfv, 2, 4, (2, 2, 1), adapt=True, lts=True, params=mi.quadrant_params(2))
+    for _ in range(3):
+        run_pair(s, o, 1, lts=True, adapt_crit=oracle.CRIT_MR)
+        assert_same_tree(s, o)
+    assert_levels_close(s, o)
+
+
+def test_amr_gradient_lts_fp64(mrfv):
+    s, o = pair(mrfv, 2, 3, (4, 4, 1), adapt=True, criterion="grad", lts=True, params=mi.quadrant_params(3))
+    assert_same_tree(s, o)
+    for l in range(2):
+        assert np.array_equal(s.get_flags(l)[0], o.get_sig(l)[0])
+    for _ in range(3):
+        run_pair(s, o, 1, lts=True, adapt_crit=oracle.CRIT_GRAD)
+        assert_same_tree(s, o)
+    assert_levels_close(s, o)
+
+
+def test_adaptive_3d_fp64(mrfv):
+    s, o = pair(mrfv, 3, 3, (2, 2, 2), lo=(-1, -1, -1), hi=(1, 1, 1), adapt=True, ic=mi.IC_ELLIPSOID,
+                params=mi.ellipsoid_params(1))
+    assert_same_tree(s, o)
+    for _ in range(4):
+        run_pair(s, o, 1, adapt_crit=oracle.CRIT_MR)
+        assert_same_tree(s, o)
+    assert_levels_close(s, o)
+
+
+def test_flags_bit_exact_on_identical_fp32_state(mrfv):
+    """Upload the GPU's single-precision state into the oracle and take the
+    thresholding decision on both sides in single precision."""
+    s = mrfv.Solver(dim=2, precision="fp32", levels=5, base_blocks=(1, 1, 1), adapt=True, eps=1e-3)
+    s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(4))
+    for _ in range(10):
+        s.step(0.0)
+    o = oracle.Oracle(2, 5, (1, 1, 1))
+    o.init(mi.IC_QUADRANTS, mi.quadrant_params(4))
+    for l in range(5):
+        o.set_exist(l, s.get_tree(l))
+    for l in range(5):
+        o.set_level(l, s.download_level(l)[0])
+    n_g = s.analyse(1e-3)
+    n_o = o.analyse(1e-3, precision=1)
+    assert n_g == n_o
+    for l in range(1, 5):
+        assert np.array_equal(s.get_flags(l)[0], o.get_sig(l)[0])
+        assert np.array_equal(s.get_flags(l)[1], o.get_sig(l)[1])
+
+
+# ----------------------------------------------------------------------------- FP32
+
+def test_fp32_adaptive_l1_and_totals(mrfv):
+    s, o = pair(mrfv, 2, 5, (1, 1, 1), bc=1, precision="fp32", adapt=True, params=mi.quadrant_params(6))
+    T0 = o.totals()
+    for _ in range(100):
+        dt = o.dt(0.5)
+        s.step(dt)
+        o.step(dt)
+        o.adapt(oracle.CRIT_MR, 1e-3, precision=1)
+    # compare on the finest level (trees may differ where a detail sits at eps)
+    gs = [s.download_level(l)[0] for l in range(5)]
+    o2 = oracle.Oracle(2, 5, (1, 1, 1), bc=1)
+    o2.init(mi.IC_QUADRANTS, mi.quadrant_params(6))
+    for l in range(5):
+        o2.set_exist(l, s.get_tree(l))
+    for l in range(5):
+        o2.set_level(l, gs[l])
+    fg = o2.project_finest()[0]
+    fo = o.project_finest()[0]
+    rel_l1 = np.abs(fg - fo).sum() / np.abs(fo).sum()
+    assert rel_l1 <= 2e-4, rel_l1
+    Tg = s.totals()
+    assert np.all(np.abs(Tg - o.totals()) <= 1e-6 * np.abs(T0).max())
+
+
+def test_fp32_uniform_l1(mrfv):
+    s, o = pair(mrfv, 2, 1, (8, 8, 1), precision="fp32", params=mi.quadrant_params(7))
+    for _ in range(100):
+        dt = o.dt(0.5)
+        s.step(dt)
+        o.step(dt)
+    g = s.download_level(0)[0][0]
+    r = o.get_level(0)[0]
+    assert np.abs(g - r).sum() / np.abs(r).sum() <= 2e-4
+
+
+def test_cfl_dt_fp32_close(mrfv):
+    s, o = pair(mrfv, 2, 1, (4, 4, 1), precision="fp32")
+    assert s.compute_dt() == pytest.approx(o.dt(0.5), rel=1e-6)
+
+
+# ----------------------------------------------------------------------------- full size
+
+def test_mr2d_fp32_levels8_full_size_steps(mrfv):
+    """The 8-level (1024^2 finest) adaptive FP32 workload for a few steps, as timed by the bench."""
+    P = mi.quadrant_params(0)
+    s = mrfv.Solver(dim=2, precision="fp32", levels=8, base_blocks=(1, 1, 1), adapt=True, eps=1e-3, t_end=0.25)
+    s.init_state(mi.IC_QUADRANTS, P)
+    o = oracle.Oracle(2, 8, (1, 1, 1))
+    o.init(mi.IC_QUADRANTS, P)
+    o.adapt(oracle.CRIT_MR, 1e-3, precision=1)
+    for _ in range(3):
+        dt = o.dt(0.5)
+        s.step(dt)
+        o.step(dt)
+        o.adapt(oracle.CRIT_MR, 1e-3, precision=1)
+    st = s.stats()
+    assert st["total_leaves"] > 0
+    gs = [s.download_level(l)[0] for l in range(8)]
+    o2 = oracle.Oracle(2, 8, (1, 1, 1))
+    o2.init(mi.IC_QUADRANTS, P)
+    for l in range(8):
+        o2.set_exist(l, s.get_tree(l))
+    for l in range(8):
+        o2.set_level(l, gs[l])
+    fg = o2.project_finest()[0]
+    fo = o.project_finest()[0]
+    assert np.abs(fg - fo).sum() / np.abs(fo).sum() <= 2e-4
+
+
+def test_errors_are_reported(mrfv):
+    s = mrfv.Solver(dim=2, levels=2, base_blocks=(1, 1, 1))
+    with pytest.raises(mrfv.MRFVError) as e:
+        s.step(0.0)
+    assert e.value.code == mrfv.ERR_STATE
+    with pytest.raises(mrfv.MRFVError):
+        s.init_state(99, [])
+    s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(0))
+    bad = [np.ones(s.blocks_shape(0), np.uint8), np.zeros(s.blocks_shape(1), np.uint8)]
+    bad[1][0, 0] = 1  # incomplete child set
+    with pytest.raises(mrfv.MRFVError) as e:
+        s.set_tree(bad)
+    assert e.value.code == mrfv.ERR_ARG
