@@ -321,16 +321,53 @@ def run_e2e(m, torch, stream, steps):
             "d2h_bytes_per_step": (out_bytes + 8 * steps) / steps}
 
 
+def run_case(args):
+    """Single uniform-grid case (the profiling workload): levels=1, n^d cells, CFL steps only."""
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    nb = args.n // 8
+    prec = args.precision
+    if args.dim == 2:
+        s = m.Solver(dim=2, precision=prec, levels=1, base_blocks=(nb, nb, 1), cfl=0.5)
+        s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(SEED))
+    else:
+        s = m.Solver(dim=3, precision=prec, levels=1, base_blocks=(nb, nb, nb), lo=(-1, -1, -1), hi=(1, 1, 1), cfl=0.5)
+        s.init_state(mi.IC_ELLIPSOID, mi.ellipsoid_params(SEED))
+    for _ in range(args.warmup):
+        s.step(0.0, sync=False)
+    s.profile_enable(True)
+    for _ in range(args.steps):
+        s.step(0.0, sync=False)
+    p = s.profile_read()
+    hbm_peak, _ = measured_peaks()
+    ach = p["fv_bytes"] / (p["fv_ms"] * 1e-3) / 1e9
+    cells = args.n ** args.dim * args.steps
+    print(json.dumps({"case": f"uniform{args.dim}d_{prec}_{args.n}", "fv_launches": p["fv_launches"],
+                      "fv_avg_ms": p["fv_ms"] / max(1, p["fv_launches"]), "fv_GBps": ach,
+                      "fv_frac_hbm": ach / hbm_peak, "cell_updates_per_s_fv_only": cells / (p["fv_ms"] * 1e-3)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default="adaptive", choices=["adaptive", "uniform"],
+                    help="uniform: only the stage kernel on an n^d grid (profiling workload)")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--dim", type=int, default=2)
+    ap.add_argument("--precision", default="fp32")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.case == "uniform":
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -31,6 +31,7 @@ struct mrfv_ctx {
   int32_t *freestack, *newlist, *tcount, *toff;
   int *freetop, *nnew;
   double *dsc;              // [0] dt of the finest level, [1] t
+  double *lev;              // per-level step table (lev_index)
   unsigned long long *red;  // reductions
   long long *counter;       // [0] cell updates, [1] steps
   double *totals;
@@ -152,7 +153,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t okb = L.take(mtotal), otc = L.take((size_t)LK_NUM * ntiles * 4), oto = L.take((size_t)LK_NUM * ntiles * 4);
   size_t ofs = L.take(cap * 4), oft = L.take(4), onl = L.take(cap * 4), onn = L.take(4);
   size_t odsc = L.take(4 * 8), ored = L.take(4 * 8), ocnt = L.take(2 * 8), otot = L.take(5 * 8), osc = L.take(5 * ts);
-  size_t obyt = L.take(8);
+  size_t obyt = L.take(8), olevp = L.take(2 * MAXL * 4 * 8);
   if (c) {
     char *a = c->arena;
     c->U = a + oU; c->Us = a + oUs; c->U0 = a + oU0; c->G = a + oG; c->FR = a + oFR;
@@ -168,6 +169,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->dsc = (double *)(a + odsc); c->red = (unsigned long long *)(a + ored);
     c->counter = (long long *)(a + ocnt); c->totals = (double *)(a + otot); c->scale = a + osc;
     c->dbytes = (unsigned long long *)(a + obyt);
+    c->lev = (double *)(a + olevp);
   }
   return L.off + 256;
 }
@@ -195,7 +197,8 @@ struct Seq {
   void fv(int kind, int l0, int l1, const T *Uin, const T *U0b, T *Uout, double coef, int lts, int record) {
     FVArgs<T> a;
     a.Uin = Uin; a.U0 = U0b; a.Uout = Uout; a.G = G(); a.FR = FR();
-    a.kind = kind; a.l0 = l0; a.l1 = l1; a.coef = coef; a.dt = c->dsc; a.lts = lts; a.record = record;
+    a.kind = kind; a.l0 = l0; a.l1 = l1; a.coef = coef; a.lev = c->lev; a.record = record;
+    (void)lts;
     a.words = (coef == 0.5 ? 2 : 3) * c->g.nv;
     a.bytes = c->prof ? c->dbytes : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -560,6 +563,8 @@ int mrfv_step(mrfv_ctx *c, double dt, double *dt_out) {
     } else {
       s.compute_dt(lts);
     }
+    launch_level_params(c->g, c->dsc, lts, c->lev, c->st);
+    c->nlaunch += 1;
     if (lts) s.advance(0, 0);
     else s.step_global();
   });
@@ -580,6 +585,8 @@ int mrfv_step_level(mrfv_ctx *c, int level, double dt) {
   if (!c || level < 0 || level > c->g.L || !(dt > 0.0)) return fail(c, MRFV_ERR_ARG, "step_level: arguments");
   if (!c->initialized) return fail(c, MRFV_ERR_STATE, "step_level before init");
   launch_set_double(c->dsc, dt, c->st);
+  launch_level_params(c->g, c->dsc, 1, c->lev, c->st);
+  c->nlaunch += 2;
   dispatch(c, [&](auto &s) { s.advance(level, 0); });
   return check_launch(c, "mrfv_step_level");
 }

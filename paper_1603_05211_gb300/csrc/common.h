@@ -54,12 +54,14 @@ struct FVArgs {
   int kind;       // work list
   int l0, l1;     // level range of the list
   double coef;    // stage coefficient: 1/2 (stage 1) or 1 (stage 2)
-  const double *dt;  // device time step of the finest level (global stepping: of every level)
-  int lts;        // 1: dt_l = dt * 2^(L-l)
+  const double *lev;  // per-level step table: [(stage*MAXL + l)*4 + n] = (coef dt_l)/dx_{l,n}, [.. + 3] = dt_l
   int record;     // 0: no registers; 1: store dt_l F on marked faces; 2: add on fine-role faces
   int words;      // algorithmic state words moved per cell (for the byte counter)
   unsigned long long *bytes;  // optional: += algorithmic bytes of this launch
 };
+
+// rows of the per-level step table (see FVArgs::lev): stage 0 has coef 1/2, stage 1 coef 1
+__host__ __device__ inline int lev_index(int stage, int l, int k) { return (stage * MAXL + l) * 4 + k; }
 
 struct ICParams {
   int kind;

@@ -99,174 +99,196 @@ __device__ __forceinline__ void cons_to_prim(const T *Q, T gm1, T *w) {
 template <int D>
 struct FVShape {
   static constexpr int B = (D == 2) ? 64 : 512;        // interior cells
-  static constexpr int TF = (D == 2) ? 8 : 64;         // cells of one face layer
+  static constexpr int TF = (D == 2) ? 8 : 64;         // cells of one face layer = pencils per direction
   static constexpr int NV = D + 2;
-  static constexpr int TILE = (D == 2) ? 144 : 1728;   // 12^d staging box (corners unused)
-  static constexpr int NF = 9 * TF;                    // faces per direction
   static constexpr int STRIP = 2 * D * 2 * TF;         // ghost cells (two layers per face)
-  static constexpr int BPC = (D == 2) ? 4 : 1;         // blocks per CTA
-  static constexpr int NT = B * BPC;                   // threads per CTA
+  static constexpr int BPC = (D == 2) ? 16 : 1;        // blocks per CTA
+  static constexpr int NPEN = D * TF;                  // pencils per block
+  static constexpr int NT = NPEN * BPC;                // threads per CTA (one pencil each)
+  static constexpr int PY = (D == 2) ? 9 : 8;          // padded shared-memory cell index x + PY y + PZ z
+  static constexpr int PZ = (D == 2) ? 0 : 69;         // (bank-conflict free pencil stores in 2D, 2-way in 3D)
+  static constexpr int RS = (D == 2) ? 74 : 552;       // padded cells per (block, variable) in shared memory
+};
+
+// CTAs per SM the register allocation must allow (single precision: 4, the
+// double-precision parity mode: 2); overridable at build time for tuning.
+#ifndef MRFV_FV_MINB32
+#define MRFV_FV_MINB32 4
+#endif
+#ifndef MRFV_FV_MINB64
+#define MRFV_FV_MINB64 2
+#endif
+template <typename T>
+struct FVMinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? MRFV_FV_MINB32 : MRFV_FV_MINB64;
 };
 
 template <typename T, int D>
 constexpr size_t fv_smem_bytes() {
   using S = FVShape<D>;
-  return (size_t)S::BPC * (S::NV * S::TILE + 3 * S::NV * S::NF) * sizeof(T);
+  return (size_t)D * S::BPC * S::NV * S::RS * sizeof(T);
 }
 
-__device__ __forceinline__ int tile_pos(int D, int x, int y, int z) {
-  return (D == 2) ? (x + 2) + 12 * (y + 2) : (x + 2) + 12 * ((y + 2) + 12 * (z + 2));
-}
-
+// Conservative state of pencil position p (-2..9) of the pencil (n, tangential t)
+// of block s: own cells, the same-level neighbour's cells, the ghost strip, or the
+// block's own edge cell at a transmissive wall.
 template <typename T, int D>
-__global__ void __launch_bounds__(FVShape<D>::NT) k_fv(Geo g, FVArgs<T> a) {
+__device__ __forceinline__ void pencil_load(const Geo &g, const T *__restrict__ U, const T *__restrict__ G, int s,
+                                            int n, int t, int nb_lo, int nb_hi, int p, T *Q) {
   using S = FVShape<D>;
-  constexpr int B = S::B, TF = S::TF, NV = S::NV, TILE = S::TILE, NF = S::NF, BPC = S::BPC;
+  constexpr int B = S::B, TF = S::TF, NV = S::NV;
+  const long long cap = g.cap;
+  const int stride = (n == 0) ? 1 : (n == 1 ? 8 : 64);
+  // cell index of tangential position t with coordinate 0 along n
+  const int t1 = t & 7, t2 = t >> 3;
+  const int base = (n == 0) ? (8 * t1 + 64 * t2) : (n == 1 ? (t1 + 64 * t2) : (t1 + 8 * t2));
+  int from = s, c;
+  if (p >= 0 && p <= 7) {
+    c = base + p * stride;
+  } else {
+    const int side = p > 7 ? 1 : 0;
+    const int dd = side ? p - 8 : -1 - p;  // 0 touches the block
+    const int nb = side ? nb_hi : nb_lo;
+    if (nb == NBR_MISSING) {
+      const int q = (2 * n + side) * 2 * TF + dd * TF + t;
+#pragma unroll
+      for (int v = 0; v < NV; v++) Q[v] = G[((long long)v * cap + s) * S::STRIP + q];
+      return;
+    }
+    if (nb >= 0) {
+      from = nb;
+      c = base + (side ? dd : 7 - dd) * stride;
+    } else {
+      c = base + (side ? 7 : 0) * stride;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; v++) Q[v] = U[((long long)v * cap + from) * B + c];
+}
+
+// One thread per pencil: the 12 cells of a line along direction n (two beyond
+// each face of the block) are converted to primitives once; a sliding window then
+// forms the limited slope of each cell, the two face states and the AUSM+ flux of
+// each of the 9 faces, and stores the flux difference F_{k+1} - F_k of every
+// interior cell in shared memory.  A second pass applies
+// Q_out = Q_0 - (lambda_1 dF_1 + lambda_2 dF_2 [+ lambda_3 dF_3]), summed in
+// direction order, to every cell.
+template <typename T, int D>
+__global__ void __launch_bounds__(FVShape<D>::NT, FVMinBlocks<T>::value) k_fv(Geo g, FVArgs<T> a) {
+  using S = FVShape<D>;
+  constexpr int B = S::B, TF = S::TF, NV = S::NV, BPC = S::BPC, RS = S::RS, NT = S::NT;
   extern __shared__ unsigned char smem_raw[];
-  const int sub = threadIdx.x / B, tid = threadIdx.x % B;
-  T *tile = reinterpret_cast<T *>(smem_raw) + (size_t)sub * (NV * TILE + 3 * NV * NF);
-  T *WL = tile + NV * TILE;
-  T *WR = WL + NV * NF;
-  T *FX = WR + NV * NF;
+  T *dFs = reinterpret_cast<T *>(smem_raw);  // [dir][block][v][RS]
   const long long cap = g.cap;
   const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
-  const int cx = tid & 7, cy = (tid >> 3) & 7, cz = (D == 3) ? (tid >> 6) : 0;
-  const double dtf = *a.dt;
+  const int stage = (a.coef == 0.5) ? 0 : 1;
+  // pencil of this thread: direction-major so a warp shares one direction
+  const int n = threadIdx.x / (TF * BPC);
+  const int j = (threadIdx.x / TF) % BPC;
+  const int t = threadIdx.x % TF;
   int lb, le;
   list_range(g, a.kind, a.l0, a.l1, lb, le);
   if (a.bytes && blockIdx.x == 0 && threadIdx.x == 0)
     atomicAdd(a.bytes, (unsigned long long)(le - lb) * B * a.words * sizeof(T));
 
   for (int i0 = lb + blockIdx.x * BPC; i0 < le; i0 += gridDim.x * BPC) {
-    const int i = i0 + sub;
-    const bool active = i < le;
-    const int s = active ? g.lists[a.kind * cap + i] : 0;
-    const int l = active ? g.slot_level[s] : 0;
-    const double dtl = a.lts ? ldexp(dtf, g.L - l) : dtf;
-    __syncthreads();
-    // ---- stage the block and its face layers as primitive variables
-    if (active) {
-      for (int it = tid; it < B + S::STRIP; it += B) {
-        T Q[NV], w[NV];
-        int pos;
-        if (it < B) {
-          int x = it & 7, y = (it >> 3) & 7, z = (D == 3) ? (it >> 6) : 0;
-          pos = tile_pos(D, x, y, z);
+    // ---------------- pencil pass
+    {
+      const int i = i0 + j;
+      if (i < le) {
+        const int s = g.lists[a.kind * cap + i];
+        const int l = g.slot_level[s];
+        const int nb_lo = g.nbr[6 * s + 2 * n], nb_hi = g.nbr[6 * s + 2 * n + 1];
+        const bool rec_lo = a.record && (nb_lo == NBR_MISSING || ((g.cmask[s] >> (2 * n)) & 1));
+        const bool rec_hi = a.record && (nb_hi == NBR_MISSING || ((g.cmask[s] >> (2 * n + 1)) & 1));
+        const bool add_lo = a.record == 2 && nb_lo == NBR_MISSING;
+        const bool add_hi = a.record == 2 && nb_hi == NBR_MISSING;
+        const T dtT = T(a.lev[lev_index(stage, l, 3)]);
+        // padded shared-memory index of this pencil's position 0 and the stride along n
+        const int t1 = t & 7, t2 = t >> 3;
+        const int base = (n == 0) ? (S::PY * t1 + S::PZ * t2) : (n == 1 ? (t1 + S::PZ * t2) : (t1 + S::PY * t2));
+        const int stride = (n == 0) ? 1 : (n == 1 ? S::PY : S::PZ);
+        T *dF = dFs + ((size_t)(n * BPC + j) * NV) * RS;
+        // sliding window of primitives: wb = cell k-1, wc = cell k (face k lies between them)
+        T wb[NV], wc[NV], slo[NV], Fprev[NV];
+        {
+          T Q[NV], wa[NV];
+          pencil_load<T, D>(g, a.Uin, a.G, s, n, t, nb_lo, nb_hi, -2, Q);
+          cons_to_prim<T, D>(Q, gm1, wa);
+          pencil_load<T, D>(g, a.Uin, a.G, s, n, t, nb_lo, nb_hi, -1, Q);
+          cons_to_prim<T, D>(Q, gm1, wb);
+          pencil_load<T, D>(g, a.Uin, a.G, s, n, t, nb_lo, nb_hi, 0, Q);
+          cons_to_prim<T, D>(Q, gm1, wc);
+          // slope of cell -1
 #pragma unroll
-          for (int v = 0; v < NV; v++) Q[v] = a.Uin[((long long)v * cap + s) * B + it];
-        } else {
-          int q = it - B;
-          int f = q / (2 * TF), dd = (q / TF) & 1, t = q % TF;
-          int n = f >> 1, side = f & 1;
-          int t1 = (n == 0) ? 1 : 0, t2 = (n == 2) ? 1 : 2;
-          int rel[3], src[3];
-          rel[t1] = t & 7;
-          rel[t2] = (D == 3) ? (t >> 3) : 0;
-          src[t1] = rel[t1];
-          src[t2] = rel[t2];
-          rel[n] = side ? 8 + dd : -1 - dd;
-          pos = tile_pos(D, rel[0], rel[1], rel[2]);
-          int nb = g.nbr[6 * s + f];
-          if (nb == NBR_MISSING) {
-#pragma unroll
-            for (int v = 0; v < NV; v++) Q[v] = a.G[((long long)v * cap + s) * S::STRIP + q];
-          } else {
-            int from;
-            if (nb >= 0) {
-              src[n] = side ? dd : 7 - dd;
-              from = nb;
-            } else {  // transmissive wall: the block's own edge cell
-              src[n] = side ? 7 : 0;
-              from = s;
-            }
-            int c = src[0] + 8 * src[1] + (D == 3 ? 64 * src[2] : 0);
-#pragma unroll
-            for (int v = 0; v < NV; v++) Q[v] = a.Uin[((long long)v * cap + from) * B + c];
-          }
+          for (int v = 0; v < NV; v++) slo[v] = van_albada<T>(wb[v] - wa[v], wc[v] - wb[v]);
         }
-        cons_to_prim<T, D>(Q, gm1, w);
 #pragma unroll
-        for (int v = 0; v < NV; v++) tile[v * TILE + pos] = w[v];
-      }
-    }
-    __syncthreads();
-
-    T r[NV];
-#pragma unroll
-    for (int n = 0; n < D; n++) {
-      const int t1 = (n == 0) ? 1 : 0, t2 = (n == 2) ? 1 : 2;
-      const int stride = (n == 0) ? 1 : (n == 1 ? 12 : 144);
-      // ---- limited slopes -> face states; pencil cell p in [-1, 8] along n
-      if (active) {
-        for (int it = tid; it < 10 * TF; it += B) {
-          int p = it % 10 - 1, t = it / 10;
-          int c3[3];
-          c3[n] = p;
-          c3[t1] = t & 7;
-          c3[t2] = (D == 3) ? (t >> 3) : 0;
-          int pos = tile_pos(D, c3[0], c3[1], c3[2]);
+        for (int k = 0; k < 9; k++) {
+          T wd[NV], wl[NV], wr[NV], shi[NV], F[NV];
+          {
+            T Q[NV];
+            pencil_load<T, D>(g, a.Uin, a.G, s, n, t, nb_lo, nb_hi, k + 1, Q);
+            cons_to_prim<T, D>(Q, gm1, wd);
+          }
 #pragma unroll
           for (int v = 0; v < NV; v++) {
-            T wm = tile[v * TILE + pos - stride], w0 = tile[v * TILE + pos], wp = tile[v * TILE + pos + stride];
-            T sl = van_albada<T>(w0 - wm, wp - w0);
-            if (p >= 0) WR[v * NF + p + 9 * t] = w0 - T(0.5) * sl;
-            if (p <= 7) WL[v * NF + (p + 1) + 9 * t] = w0 + T(0.5) * sl;
-          }
-        }
-      }
-      __syncthreads();
-      // ---- AUSM+ on every face of direction n; face k lies between cells k-1 and k
-      if (active) {
-        for (int it = tid; it < NF; it += B) {
-          T wl[NV], wr[NV], F[NV];
-#pragma unroll
-          for (int v = 0; v < NV; v++) {
-            wl[v] = WL[v * NF + it];
-            wr[v] = WR[v * NF + it];
+            shi[v] = van_albada<T>(wc[v] - wb[v], wd[v] - wc[v]);
+            wl[v] = wb[v] + T(0.5) * slo[v];
+            wr[v] = wc[v] - T(0.5) * shi[v];
           }
           ausm_plus<T, D>(n, wl, wr, gam, goverg1, F);
+          if (k == 0 && rec_lo) {
 #pragma unroll
-          for (int v = 0; v < NV; v++) FX[v * NF + it] = F[v];
-          int k = it % 9;
-          if (a.record && (k == 0 || k == 8)) {
-            int f = 2 * n + (k == 8 ? 1 : 0), t = it / 9;
-            bool fine = g.nbr[6 * s + f] == NBR_MISSING;
-            bool coarse = (g.cmask[s] >> f) & 1;
-            if (fine || coarse) {
-              T dtT = T(dtl);
-              T *R = a.FR + (long long)f * TF + t;
-              bool add = fine && a.record == 2;
-#pragma unroll
-              for (int v = 0; v < NV; v++) {
-                long long o = ((long long)v * cap + s) * (2 * D * TF);
-                T val = dtT * F[v];
-                R[o] = add ? R[o] + val : val;
-              }
+            for (int v = 0; v < NV; v++) {
+              T *R = a.FR + ((long long)v * cap + s) * (2 * D * TF) + (2 * n) * TF + t;
+              T val = dtT * F[v];
+              *R = add_lo ? *R + val : val;
             }
+          }
+          if (k == 8 && rec_hi) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+              T *R = a.FR + ((long long)v * cap + s) * (2 * D * TF) + (2 * n + 1) * TF + t;
+              T val = dtT * F[v];
+              *R = add_hi ? *R + val : val;
+            }
+          }
+          if (k > 0) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) dF[v * RS + base + (k - 1) * stride] = F[v] - Fprev[v];
+          }
+#pragma unroll
+          for (int v = 0; v < NV; v++) {
+            Fprev[v] = F[v];
+            slo[v] = shi[v];
+            wb[v] = wc[v];
+            wc[v] = wd[v];
           }
         }
       }
-      __syncthreads();
-      // ---- residual of this thread's cell: lambda_n (F_{k+1} - F_k)
-      if (active) {
-        const T lam = T((a.coef * dtl) / g.dx[l][n]);
-        int c3[3] = {cx, cy, cz};
-        int p = c3[n];
-        int t = c3[t1] + ((D == 3) ? 8 * c3[t2] : 0);
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-          T dF = FX[v * NF + (p + 1) + 9 * t] - FX[v * NF + p + 9 * t];
-          r[v] = (n == 0) ? lam * dF : r[v] + lam * dF;
-        }
-      }
     }
-    if (active) {
+    __syncthreads();
+    // ---------------- update pass
+    for (int q = threadIdx.x; q < BPC * B; q += NT) {
+      const int jj = q / B, c = q % B;
+      const int i = i0 + jj;
+      if (i >= le) break;
+      const int s = g.lists[a.kind * cap + i];
+      const int l = g.slot_level[s];
+      const int cp = (c & 7) + S::PY * ((c >> 3) & 7) + S::PZ * (c >> 6);
+      const T lam0 = T(a.lev[lev_index(stage, l, 0)]), lam1 = T(a.lev[lev_index(stage, l, 1)]);
+      const T lam2 = T(a.lev[lev_index(stage, l, 2)]);
 #pragma unroll
       for (int v = 0; v < NV; v++) {
-        long long o = ((long long)v * cap + s) * B + tid;
-        a.Uout[o] = a.U0[o] - r[v];
+        T r = lam0 * dFs[((size_t)(0 * BPC + jj) * NV + v) * RS + cp];
+        r = r + lam1 * dFs[((size_t)(1 * BPC + jj) * NV + v) * RS + cp];
+        if (D == 3) r = r + lam2 * dFs[((size_t)(2 * BPC + jj) * NV + v) * RS + cp];
+        long long o = ((long long)v * cap + s) * B + c;
+        a.Uout[o] = a.U0[o] - r;
       }
     }
+    __syncthreads();
   }
 }
 

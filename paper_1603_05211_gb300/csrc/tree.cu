@@ -361,6 +361,20 @@ __global__ void k_dt_final(const unsigned long long *red, double cfl, double t_e
   *dt = d;
 }
 
+// Per-level step table for the stage kernels, computed once per step in double:
+// dt_l = dt (global) or dt * 2^(L-l) (level-dependent steps), and for each stage
+// coefficient c (1/2, 1) the ratios (c dt_l) / dx_{l,n}.
+__global__ void k_level_params(Geo g, const double *dt, int lts, double *lev) {
+  int l = threadIdx.x;
+  if (l > g.L) return;
+  double dtl = lts ? ldexp(*dt, g.L - l) : *dt;
+  for (int st = 0; st < 2; st++) {
+    double coef = st == 0 ? 0.5 : 1.0;
+    for (int n = 0; n < 3; n++) lev[lev_index(st, l, n)] = (coef * dtl) / g.dx[l][n];
+    lev[lev_index(st, l, 3)] = dtl;
+  }
+}
+
 // t += factor * dt; cell-update counter += leaf cells (weighted per level for
 // level-dependent steps: a leaf of level l takes 2^l steps per coarse step)
 __global__ void k_advance(Geo g, double *t, const double *dt, double factor, long long *counter, int lts) {
@@ -407,6 +421,9 @@ void launch_set_double(double *p, double v, cudaStream_t st) { k_set_double<<<1,
 void launch_dt_final(const unsigned long long *red, double cfl, double t_end, double *dt, const double *t,
                      cudaStream_t st) {
   k_dt_final<<<1, 1, 0, st>>>(red, cfl, t_end, dt, t);
+}
+void launch_level_params(const Geo &g, const double *dt, int lts, double *lev, cudaStream_t st) {
+  k_level_params<<<1, 32, 0, st>>>(g, dt, lts, lev);
 }
 void launch_advance(const Geo &g, double *t, const double *dt, double factor, long long *counter, int lts,
                     cudaStream_t st) {
