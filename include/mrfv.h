@@ -211,6 +211,35 @@ int mrfv_profile_enable(mrfv_ctx *ctx, int enable);
 /* Read the counters (synchronises the stream). */
 int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
 
+/* Allocation-free CFL time step of a caller-owned dense array of cells (no
+   counterpart in the paper).  Some callers cannot call cudaMalloc: work issued
+   while a CUDA stream is being captured into a graph may not allocate, some host
+   frameworks own all device memory through their own pool, and latency-critical
+   loops cannot afford cudaMalloc's implicit device synchronisation.  This entry
+   point allocates nothing; its scratch (one partial minimum per tile of
+   MRFV_NOALLOC_DT_TILE_CELLS cells) is a file-scope device array of
+   MRFV_NOALLOC_DT_MAX_TILES doubles (512 KiB), held by every GPU that loads the
+   library until the process exits.
+     state   device pointer, [v][k][j][i] with nv = dim+2 conserved variables
+             (rho, rho v_1..rho v_d, rho e), float (MRFV_FP32) or double (MRFV_FP64);
+     n0,n1,n2 cells per dimension (n2 = 1 in 2D); at most MRFV_NOALLOC_DT_MAX_CELLS
+             cells in total, larger arrays return MRFV_ERR_ARG;
+     dx      host pointer to the 3 cell widths;
+     dt_out  device pointer to one double: cfl * min over cells and directions of
+             dx_n / (|v_n| + c) (the rule of mrfv_compute_dt on one uniform level),
+             or -1.0 when a cell has rho <= 0, p <= 0 or NaN;
+     stream  cudaStream_t (NULL = legacy default stream); the call only enqueues.
+   The first call on a device looks up the scratch array's device address (with
+   that device current) and caches it: make that first call before any stream
+   capture.  Every call shares the scratch array, which keeps the last call's
+   contents; calls that overlap on the GPU (on different streams, or from several
+   threads) race on it and must be serialised by the caller. */
+#define MRFV_NOALLOC_DT_TILE_CELLS 4096
+#define MRFV_NOALLOC_DT_MAX_TILES 65536
+#define MRFV_NOALLOC_DT_MAX_CELLS ((int64_t)MRFV_NOALLOC_DT_TILE_CELLS * MRFV_NOALLOC_DT_MAX_TILES)
+int mrfv_cfl_dt_noalloc(int dim, int precision, const void *state, int64_t n0, int64_t n1, int64_t n2,
+                        const double *dx, double gamma, double cfl, double *dt_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,7 @@ SIGNATURES = {
     "mrfv_synchronize": (_I, [_P]),
     "mrfv_profile_enable": (_I, [_P, _I]),
     "mrfv_profile_read": (_I, [_P, ctypes.POINTER(Profile)]),
+    "mrfv_cfl_dt_noalloc": (_I, [_I, _I, _P, _I64, _I64, _I64, _DP, _D, _D, _P, _P]),
 }
 
 _lib = None

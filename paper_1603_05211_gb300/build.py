@@ -5,7 +5,9 @@ Translation units and their floating-point flags:
       the double-precision step and every multiresolution operation round exactly
       where the source says (parity with the CPU oracle; bit-exact thresholding);
   fv_f32.cu : --use_fast_math (single-precision throughput path);
-  tree.cu, api.cu : integer work and host sequencing.
+  tree.cu, api.cu : integer work and host sequencing;
+  noalloc.cu : -fmad=false (the allocation-free CFL reduction rounds like the
+      double-precision one in fv_f64.cu).
 """
 from __future__ import annotations
 
@@ -31,6 +33,7 @@ UNITS = {
     "mr_f64.cu": ["-fmad=false"],
     "tree.cu": [],
     "api.cu": [],
+    "noalloc.cu": ["-fmad=false"],
 }
 
 
