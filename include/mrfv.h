@@ -86,6 +86,8 @@ typedef struct {
   void *stream;         /* cudaStream_t to issue work on; NULL = the legacy default stream */
   void *device_arena;   /* optional device memory for all state (e.g. from a PyTorch tensor) */
   size_t arena_bytes;   /* its size; must be >= mrfv_arena_bytes(config) */
+  int use_graph;        /* 1 (default): the first mrfv_step captures the step's launch sequence into a
+                           CUDA graph (on a private stream) and every step replays it on `stream` */
 } mrfv_config;
 
 typedef struct {
@@ -104,7 +106,8 @@ typedef struct {
 typedef struct mrfv_ctx mrfv_ctx;
 
 /* Fill *cfg with defaults: 2D, FP64, one level of 1x1 blocks on [0,1]^2,
-   transmissive, gamma 1.4, CFL 0.5, eps 1e-3, eps_w 0.05, eta_tol 0.8. */
+   transmissive, gamma 1.4, CFL 0.5, eps 1e-3, eps_w 0.05, eta_tol 0.8,
+   CUDA graph replay on. */
 int mrfv_config_default(mrfv_config *cfg);
 
 /* Device bytes the context needs for cfg (pool, maps, lists, scratch). */
@@ -206,7 +209,8 @@ typedef struct {
                            writes Q^{n+1} (3 nv words) */
 } mrfv_profile;
 /* enable != 0: reset the counters and bracket every finite-volume stage launch
-   with CUDA events on the context stream; 0: stop. */
+   with CUDA events on the context stream (steps then launch eagerly instead of
+   replaying the captured graph); 0: stop. */
 int mrfv_profile_enable(mrfv_ctx *ctx, int enable);
 /* Read the counters (synchronises the stream). */
 int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);

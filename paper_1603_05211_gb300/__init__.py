@@ -42,6 +42,7 @@ class Config(ctypes.Structure):
         ("eps", ctypes.c_double), ("eps_w", ctypes.c_double), ("eta_tol", ctypes.c_double),
         ("lts", ctypes.c_int), ("pool_blocks", ctypes.c_int64),
         ("stream", ctypes.c_void_p), ("device_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
+        ("use_graph", ctypes.c_int),
     ]
 
 
@@ -134,7 +135,8 @@ class Solver:
 
     def __init__(self, dim=2, precision="fp64", levels=1, base_blocks=(1, 1, 1), lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), bc=BC_TRANSMISSIVE, gamma=1.4, cfl=0.5, t_end=0.0, adapt=False,
-                 criterion="mr", eps=1e-3, eps_w=0.05, eta_tol=0.8, lts=False, pool_blocks=0, stream=None):
+                 criterion="mr", eps=1e-3, eps_w=0.05, eta_tol=0.8, lts=False, pool_blocks=0, stream=None,
+                 use_graph=True):
         import torch
 
         if not torch.cuda.is_available():
@@ -158,6 +160,7 @@ class Solver:
         cfg.eps, cfg.eps_w, cfg.eta_tol = eps, eps_w, eta_tol
         cfg.lts = int(bool(lts))
         cfg.pool_blocks = int(pool_blocks)
+        cfg.use_graph = int(bool(use_graph))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         cfg.stream = self.stream.cuda_stream
         nbytes = lib.mrfv_arena_bytes(ctypes.byref(cfg))

@@ -32,6 +32,7 @@ struct mrfv_ctx {
   int *freetop, *nnew;
   double *dsc;              // [0] dt of the finest level, [1] t
   double *lev;              // per-level step table (lev_index)
+  float *levf;              // its single-precision copy
   unsigned long long *red;  // reductions
   long long *counter;       // [0] cell updates, [1] steps
   double *totals;
@@ -45,6 +46,10 @@ struct mrfv_ctx {
   std::vector<cudaEvent_t> evs;  // start/end pairs of timed stage launches
   size_t ev_used;
   unsigned long long *dbytes;
+  // CUDA graph of one step: [0] with the CFL reduction, [1] with a preset dt
+  cudaStream_t cap_st;
+  cudaGraphExec_t gexec[2];
+  long long glaunch[2];  // kernels in each captured step
 };
 
 static thread_local std::string g_create_error;
@@ -151,9 +156,9 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t oerr = L.take(4);
   size_t osig = L.take(maptotal), oneed = L.take(maptotal), ogf = L.take(maptotal), omd = L.take(maptotal * 8);
   size_t okb = L.take(mtotal), otc = L.take((size_t)LK_NUM * ntiles * 4), oto = L.take((size_t)LK_NUM * ntiles * 4);
-  size_t ofs = L.take(cap * 4), oft = L.take(4), onl = L.take(cap * 4), onn = L.take(4);
+  size_t ofs = L.take(cap * 4), oft = L.take(4), onl = L.take(maptotal * 4), onn = L.take(MAXL * 4);
   size_t odsc = L.take(4 * 8), ored = L.take(4 * 8), ocnt = L.take(2 * 8), otot = L.take(5 * 8), osc = L.take(5 * ts);
-  size_t obyt = L.take(8), olevp = L.take(2 * MAXL * 4 * 8);
+  size_t obyt = L.take(8), olevp = L.take(2 * MAXL * 4 * 8), olevf = L.take(2 * MAXL * 4 * 4);
   if (c) {
     char *a = c->arena;
     c->U = a + oU; c->Us = a + oUs; c->U0 = a + oU0; c->G = a + oG; c->FR = a + oFR;
@@ -170,6 +175,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->counter = (long long *)(a + ocnt); c->totals = (double *)(a + otot); c->scale = a + osc;
     c->dbytes = (unsigned long long *)(a + obyt);
     c->lev = (double *)(a + olevp);
+    c->levf = (float *)(a + olevf);
   }
   return L.off + 256;
 }
@@ -179,6 +185,13 @@ long long capacity_of(const mrfv_config *cfg, long long full) {
 }
 
 int ntiles_of(long long mtotal) { return (int)((mtotal + scan_tile_entries() - 1) / scan_tile_entries()); }
+
+long long level_blocks(const Geo &g, int l) { return g.mapoff[l + 1] - g.mapoff[l]; }
+int grid_for(long long items, int per_cta, int cap_grid) {
+  long long n = (items + per_cta - 1) / per_cta;
+  if (n < 1) n = 1;
+  return (int)(n < cap_grid ? n : cap_grid);
+}
 
 // ---------------------------------------------------------------- typed sequencing
 template <typename T>
@@ -190,15 +203,20 @@ struct Seq {
   T *G() { return (T *)c->G; }
   T *FR() { return (T *)c->FR; }
 
+  void restrict_level(int l, T *A) {
+    // at most the blocks of level l are refined
+    launch_restrict<T>(c->g, l, A, grid_for(level_blocks(c->g, l), c->g.dim == 2 ? 4 : 1, c->grid), c->st);
+  }
   void restrict_all(T *A) {
-    for (int l = c->g.L - 1; l >= 0; l--) launch_restrict<T>(c->g, l, A, c->grid, c->st);
+    for (int l = c->g.L - 1; l >= 0; l--) restrict_level(l, A);
     c->nlaunch += c->g.L;
   }
   void fv(int kind, int l0, int l1, const T *Uin, const T *U0b, T *Uout, double coef, int lts, int record) {
     FVArgs<T> a;
     a.Uin = Uin; a.U0 = U0b; a.Uout = Uout; a.G = G(); a.FR = FR();
-    a.kind = kind; a.l0 = l0; a.l1 = l1; a.coef = coef; a.lev = c->lev; a.record = record;
+    a.kind = kind; a.l0 = l0; a.l1 = l1; a.coef = coef; a.lev = c->lev; a.levf = c->levf; a.record = record;
     (void)lts;
+    a.stage = coef == 0.5 ? 0 : 1;
     a.words = (coef == 0.5 ? 2 : 3) * c->g.nv;
     a.bytes = c->prof ? c->dbytes : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -252,20 +270,22 @@ struct Seq {
     if (l < L) {
       advance(l + 1, 0);
       advance(l + 1, 1);
-      launch_restrict<T>(c->g, l, U(), c->grid, c->st);
+      restrict_level(l, U());
       launch_reflux<T>(c->g, l, l, U(), FR(), c->grid, c->st);
       c->nlaunch += 2;
     }
   }
   void analyse(double eps) {
-    launch_scales<T>(c->g, U(), c->red + 0, (T *)c->scale, c->grid, c->st);
+    launch_scales<T>(c->g, U(), c->red + 0, (T *)c->scale,
+                     grid_for(level_blocks(c->g, 0) * block_cells(c->g.dim), 256, c->grid), c->st);
     cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
     cudaMemsetAsync(c->maxdet, 0, c->maptotal * 8, c->st);
     launch_details<T>(c->g, U(), (const T *)c->scale, eps, c->sig, c->maxdet, c->bgrid, c->st);
     c->nlaunch += 3;
   }
   void prolong_new() {
-    for (int l = 1; l <= c->g.L; l++) launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(), c->bgrid, c->st);
+    for (int l = 1; l <= c->g.L; l++)
+      launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(), grid_for(level_blocks(c->g, l), 1, c->bgrid), c->st);
     c->nlaunch += c->g.L;
   }
   void compute_dt(int lts) {
@@ -300,7 +320,7 @@ void dispatch(mrfv_ctx *c, F f) {
 
 // free, allocate, rebuild neighbour tables and lists, optionally predict new blocks
 void apply_need(mrfv_ctx *c, bool prolong) {
-  cudaMemsetAsync(c->nnew, 0, sizeof(int), c->st);
+  cudaMemsetAsync(c->nnew, 0, MAXL * sizeof(int), c->st);
   launch_free(c->g, c->need, c->freestack, c->freetop, c->grid, c->st);
   launch_alloc(c->g, c->need, c->freestack, c->freetop, c->newlist, c->nnew, c->grid, c->st);
   launch_rebuild_lists(c->g, c->kbits, c->tcount, c->toff, c->ntiles, c->grid, c->st);
@@ -316,7 +336,7 @@ void adapt_tree(mrfv_ctx *c) {
   cudaMemsetAsync(c->need, 0, c->maptotal, c->st);
   cudaMemsetAsync(c->need, 1, g.mapoff[1], c->st);
   launch_need_mark(g, c->sig, c->need, c->cfg.criterion, c->grid, c->st);
-  for (int l = g.L; l >= 1; l--) launch_need_close(g, l, c->need, c->grid, c->st);
+  for (int l = g.L; l >= 1; l--) launch_need_close(g, l, c->need, grid_for(level_blocks(g, l), 256, c->grid), c->st);
   c->nlaunch += 1 + g.L;
   apply_need(c, true);
 }
@@ -381,6 +401,7 @@ int mrfv_config_default(mrfv_config *cfg) {
   cfg->eps = 1e-3;
   cfg->eps_w = 0.05;
   cfg->eta_tol = 0.8;
+  cfg->use_graph = 1;
   return MRFV_OK;
 }
 
@@ -458,6 +479,7 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   cudaMemsetAsync(c->dsc, 0, 4 * 8, c->st);
   cudaMemsetAsync(c->counter, 0, 2 * 8, c->st);
   launch_init_freestack(c->freestack, c->freetop, c->g.cap, c->grid, c->st);
+  if (cfg->use_graph && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) c->cap_st = nullptr;
   int rc = check_launch(c, "mrfv_create");
   if (rc == MRFV_OK) rc = check_device(c, "mrfv_create");
   if (rc != MRFV_OK) {
@@ -473,6 +495,9 @@ int mrfv_destroy(mrfv_ctx *c) {
   if (!c) return MRFV_OK;
   cudaStreamSynchronize(c->st);
   for (cudaEvent_t e : c->evs) cudaEventDestroy(e);
+  for (int v = 0; v < 2; v++)
+    if (c->gexec[v]) cudaGraphExecDestroy(c->gexec[v]);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->own_arena && c->arena) cudaFree(c->arena);
   delete c;
   return MRFV_OK;
@@ -552,18 +577,16 @@ int mrfv_fill_ghosts(mrfv_ctx *c, int level, int buffer) {
   return check_launch(c, "mrfv_fill_ghosts");
 }
 
-int mrfv_step(mrfv_ctx *c, double dt, double *dt_out) {
-  if (!c) return MRFV_ERR_ARG;
-  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "step before init");
+}  // extern "C"
+
+namespace {
+// Every launch of one step after dt is set (preset) or with the CFL reduction;
+// nothing here synchronises, so the sequence can be captured into a graph.
+void issue_step(mrfv_ctx *c, bool preset) {
   int lts = c->cfg.lts;
   dispatch(c, [&](auto &s) {
-    if (dt > 0.0) {
-      launch_set_double(c->dsc, dt, c->st);
-      c->nlaunch += 1;
-    } else {
-      s.compute_dt(lts);
-    }
-    launch_level_params(c->g, c->dsc, lts, c->lev, c->st);
+    if (!preset) s.compute_dt(lts);
+    launch_level_params(c->g, c->dsc, lts, c->lev, c->levf, c->st);
     c->nlaunch += 1;
     if (lts) s.advance(0, 0);
     else s.step_global();
@@ -571,6 +594,56 @@ int mrfv_step(mrfv_ctx *c, double dt, double *dt_out) {
   launch_advance(c->g, c->dsc + 1, c->dsc, lts ? ldexp(1.0, c->g.L) : 1.0, c->counter, lts, c->st);
   c->nlaunch += 1;
   if (c->cfg.adapt) adapt_tree(c);
+}
+
+// Capture one step into graph variant v (once per context: every kernel argument
+// is a fixed device pointer or a configuration constant, and every work-list
+// length is read on the device).
+int capture_step(mrfv_ctx *c, int v) {
+  cudaStream_t user = c->st;
+  c->st = c->cap_st;
+  long long before = c->nlaunch;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    issue_step(c, v == 1);
+    e = cudaStreamEndCapture(c->cap_st, &graph);
+  }
+  c->st = user;
+  c->glaunch[v] = c->nlaunch - before;
+  c->nlaunch = before;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[v], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->gexec[v] = nullptr;
+    return fail(c, MRFV_ERR_CUDA, std::string("mrfv_step: graph capture: ") + cudaGetErrorString(e));
+  }
+  return MRFV_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mrfv_step(mrfv_ctx *c, double dt, double *dt_out) {
+  if (!c) return MRFV_ERR_ARG;
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "step before init");
+  bool preset = dt > 0.0;
+  if (preset) {
+    launch_set_double(c->dsc, dt, c->st);
+    c->nlaunch += 1;
+  }
+  if (c->cfg.use_graph && c->cap_st && !c->prof) {
+    int v = preset ? 1 : 0;
+    if (!c->gexec[v]) {
+      int rc = capture_step(c, v);
+      if (rc != MRFV_OK) return rc;
+    }
+    if (cudaGraphLaunch(c->gexec[v], c->st) != cudaSuccess) return check_launch(c, "mrfv_step: graph launch");
+    c->nlaunch += c->glaunch[v];
+  } else {
+    issue_step(c, preset);
+  }
   int rc = check_launch(c, "mrfv_step");
   if (rc != MRFV_OK) return rc;
   if (dt_out) {
@@ -585,7 +658,7 @@ int mrfv_step_level(mrfv_ctx *c, int level, double dt) {
   if (!c || level < 0 || level > c->g.L || !(dt > 0.0)) return fail(c, MRFV_ERR_ARG, "step_level: arguments");
   if (!c->initialized) return fail(c, MRFV_ERR_STATE, "step_level before init");
   launch_set_double(c->dsc, dt, c->st);
-  launch_level_params(c->g, c->dsc, 1, c->lev, c->st);
+  launch_level_params(c->g, c->dsc, 1, c->lev, c->levf, c->st);
   c->nlaunch += 2;
   dispatch(c, [&](auto &s) { s.advance(level, 0); });
   return check_launch(c, "mrfv_step_level");
@@ -596,7 +669,7 @@ int mrfv_restrict(mrfv_ctx *c, int fine_level) {
   if (!c->initialized) return fail(c, MRFV_ERR_STATE, "restrict before init");
   dispatch(c, [&](auto &s) {
     if (fine_level <= 0) s.restrict_all(s.U());
-    else launch_restrict(c->g, fine_level - 1, s.U(), c->grid, c->st);
+    else s.restrict_level(fine_level - 1, s.U());
   });
   return check_launch(c, "mrfv_restrict");
 }

@@ -54,7 +54,9 @@ struct FVArgs {
   int kind;       // work list
   int l0, l1;     // level range of the list
   double coef;    // stage coefficient: 1/2 (stage 1) or 1 (stage 2)
+  int stage;      // 0 (coef 1/2) or 1 (coef 1): row of the step table
   const double *lev;  // per-level step table: [(stage*MAXL + l)*4 + n] = (coef dt_l)/dx_{l,n}, [.. + 3] = dt_l
+  const float *levf;  // the same table rounded to single precision (read by the single-precision kernel)
   int record;     // 0: no registers; 1: store dt_l F on marked faces; 2: add on fine-role faces
   int words;      // algorithmic state words moved per cell (for the byte counter)
   unsigned long long *bytes;  // optional: += algorithmic bytes of this launch

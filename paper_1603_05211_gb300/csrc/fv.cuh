@@ -96,13 +96,16 @@ __device__ __forceinline__ void cons_to_prim(const T *Q, T gm1, T *w) {
   w[D + 1] = gm1 * (Q[D + 1] - ((T(0.5) * rho) * vv));
 }
 
+#ifndef MRFV_FV_BPC2
+#define MRFV_FV_BPC2 16
+#endif
 template <int D>
 struct FVShape {
   static constexpr int B = (D == 2) ? 64 : 512;        // interior cells
   static constexpr int TF = (D == 2) ? 8 : 64;         // cells of one face layer = pencils per direction
   static constexpr int NV = D + 2;
   static constexpr int STRIP = 2 * D * 2 * TF;         // ghost cells (two layers per face)
-  static constexpr int BPC = (D == 2) ? 16 : 1;        // blocks per CTA
+  static constexpr int BPC = (D == 2) ? MRFV_FV_BPC2 : 1;  // blocks per CTA
   static constexpr int NPEN = D * TF;                  // pencils per block
   static constexpr int NT = NPEN * BPC;                // threads per CTA (one pencil each)
   static constexpr int PY = (D == 2) ? 9 : 8;          // padded shared-memory cell index x + PY y + PZ z
@@ -122,6 +125,13 @@ template <typename T>
 struct FVMinBlocks {
   static constexpr int value = sizeof(T) == 4 ? MRFV_FV_MINB32 : MRFV_FV_MINB64;
 };
+
+// step-table entry in the kernel's precision (no double -> float conversion per cell)
+template <typename T>
+__device__ __forceinline__ T lev_at(const FVArgs<T> &a, int i) {
+  if constexpr (sizeof(T) == 4) return a.levf[i];
+  else return a.lev[i];
+}
 
 template <typename T, int D>
 constexpr size_t fv_smem_bytes() {
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(FVShape<D>::NT, FVMinBlocks<T>::value) k_fv(Ge
   T *dFs = reinterpret_cast<T *>(smem_raw);  // [dir][block][v][RS]
   const long long cap = g.cap;
   const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
-  const int stage = (a.coef == 0.5) ? 0 : 1;
+  const int stage = a.stage;
   // pencil of this thread: direction-major so a warp shares one direction
   const int n = threadIdx.x / (TF * BPC);
   const int j = (threadIdx.x / TF) % BPC;
@@ -203,7 +213,7 @@ __global__ void __launch_bounds__(FVShape<D>::NT, FVMinBlocks<T>::value) k_fv(Ge
         const bool rec_hi = a.record && (nb_hi == NBR_MISSING || ((g.cmask[s] >> (2 * n + 1)) & 1));
         const bool add_lo = a.record == 2 && nb_lo == NBR_MISSING;
         const bool add_hi = a.record == 2 && nb_hi == NBR_MISSING;
-        const T dtT = T(a.lev[lev_index(stage, l, 3)]);
+        const T dtT = lev_at(a, lev_index(stage, l, 3));
         // padded shared-memory index of this pencil's position 0 and the stride along n
         const int t1 = t & 7, t2 = t >> 3;
         const int base = (n == 0) ? (S::PY * t1 + S::PZ * t2) : (n == 1 ? (t1 + S::PZ * t2) : (t1 + S::PY * t2));
@@ -277,8 +287,8 @@ __global__ void __launch_bounds__(FVShape<D>::NT, FVMinBlocks<T>::value) k_fv(Ge
       const int s = g.lists[a.kind * cap + i];
       const int l = g.slot_level[s];
       const int cp = (c & 7) + S::PY * ((c >> 3) & 7) + S::PZ * (c >> 6);
-      const T lam0 = T(a.lev[lev_index(stage, l, 0)]), lam1 = T(a.lev[lev_index(stage, l, 1)]);
-      const T lam2 = T(a.lev[lev_index(stage, l, 2)]);
+      const T lam0 = lev_at(a, lev_index(stage, l, 0)), lam1 = lev_at(a, lev_index(stage, l, 1));
+      const T lam2 = lev_at(a, lev_index(stage, l, 2));
 #pragma unroll
       for (int v = 0; v < NV; v++) {
         T r = lam0 * dFs[((size_t)(0 * BPC + jj) * NV + v) * RS + cp];

@@ -37,7 +37,7 @@ int scan_tile_entries();
 void launch_cluster(const Geo &, const uint8_t *gflag, uint8_t *sig, double eta, int grid, cudaStream_t);
 void launch_set_double(double *p, double v, cudaStream_t);
 void launch_dt_final(const unsigned long long *red, double cfl, double t_end, double *dt, const double *t, cudaStream_t);
-void launch_level_params(const Geo &, const double *dt, int lts, double *lev, cudaStream_t);
+void launch_level_params(const Geo &, const double *dt, int lts, double *lev, float *levf, cudaStream_t);
 void launch_advance(const Geo &, double *t, const double *dt, double factor, long long *counter, int lts, cudaStream_t);
 
 }  // namespace mrfv

@@ -163,12 +163,11 @@ __global__ void k_prolong(Geo g, int l, const int32_t *__restrict__ newlist, con
   constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
   __shared__ T patch[(D + 2) * NP];
   const long long cap = g.cap;
-  const int n = *nnew;
+  const int n = nnew[l];
   const int c = threadIdx.x;
   const int x = c & 7, y = (c >> 3) & 7, z = (D == 3) ? (c >> 6) : 0;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    int s = newlist[i];
-    if (g.slot_level[s] != l) continue;  // uniform over the CTA
+    int s = newlist[g.mapoff[l] + i];
     int bx = g.slot_coord[3 * s], by = g.slot_coord[3 * s + 1], bz = g.slot_coord[3 * s + 2];
     __syncthreads();
     gather_patch<T, D, EXT>(g, l - 1, A, (const T *)nullptr, T(0), 4 * bx - 1, 4 * by - 1, 4 * bz - 1, patch, c, B);
@@ -188,7 +187,6 @@ __global__ void k_prolong(Geo g, int l, const int32_t *__restrict__ newlist, con
 template <typename T, int D>
 __global__ void k_ghost(Geo g, int l0, int l1, const T *__restrict__ A, const T *__restrict__ A0, T theta,
                         T *__restrict__ G) {
-  constexpr int B = (D == 2) ? 64 : 512;
   constexpr int TF = (D == 2) ? 8 : 64;
   constexpr int GS = 2 * D * 2 * TF;
   constexpr int EXT = 8;

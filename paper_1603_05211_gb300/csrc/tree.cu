@@ -117,7 +117,7 @@ __global__ void k_alloc(Geo g, const uint8_t *need, int32_t *freestack, int *fre
     g.slot_coord[3 * s] = bx;
     g.slot_coord[3 * s + 1] = by;
     g.slot_coord[3 * s + 2] = bz;
-    newlist[atomicAdd(nnew, 1)] = s;
+    newlist[g.mapoff[l] + atomicAdd(nnew + l, 1)] = s;  // per-level segment of the new-block list
   }
 }
 
@@ -235,32 +235,46 @@ __global__ void k_tile_count(Geo g, const uint8_t *kbits, int32_t *tcount, int n
   }
 }
 
-// single CTA: exclusive scan of the tile counts of each kind; totals -> loff[kind][L+1]
+// single CTA (1024 threads): exclusive scan of the tile counts of each kind;
+// totals -> loff[kind][L+1].  Each thread sums a run of tiles, the runs are
+// scanned with warp shuffles, then each thread writes its tiles' offsets.
 __global__ void k_tile_scan(Geo g, const int32_t *tcount, int32_t *toff, int ntiles) {
-  __shared__ int32_t part[1024];
+  __shared__ int32_t wsum[LK_NUM][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+  const int b = threadIdx.x * per, e = min(ntiles, b + per);
+  int run[LK_NUM];
   for (int k = 0; k < LK_NUM; k++) {
-    int per = (ntiles + blockDim.x - 1) / blockDim.x;
-    int b = threadIdx.x * per, e = min(ntiles, b + per);
-    int s = 0;
-    for (int t = b; t < e; t++) s += tcount[k * ntiles + t];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int run = 0;
-      for (int i = 0; i < (int)blockDim.x; i++) {
-        int x = part[i];
-        part[i] = run;
-        run += x;
+    int x = 0;
+    for (int t = b; t < e; t++) x += tcount[k * ntiles + t];
+    int incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[k][warp] = incl;
+    run[k] = incl - x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int k = 0; k < LK_NUM; k++) {
+      int x = lane < nw ? wsum[k][lane] : 0;
+      int incl = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      g.loff[k * (MAXL + 2) + g.L + 1] = run;
+      if (lane < nw) wsum[k][lane] = incl - x;
+      if (lane == 31) g.loff[k * (MAXL + 2) + g.L + 1] = incl;
     }
-    __syncthreads();
-    int run = part[threadIdx.x];
+  }
+  __syncthreads();
+  for (int k = 0; k < LK_NUM; k++) {
+    int r = run[k] + wsum[k][warp];
     for (int t = b; t < e; t++) {
-      toff[k * ntiles + t] = run;
-      run += tcount[k * ntiles + t];
+      toff[k * ntiles + t] = r;
+      r += tcount[k * ntiles + t];
     }
-    __syncthreads();
   }
 }
 
@@ -364,7 +378,7 @@ __global__ void k_dt_final(const unsigned long long *red, double cfl, double t_e
 // Per-level step table for the stage kernels, computed once per step in double:
 // dt_l = dt (global) or dt * 2^(L-l) (level-dependent steps), and for each stage
 // coefficient c (1/2, 1) the ratios (c dt_l) / dx_{l,n}.
-__global__ void k_level_params(Geo g, const double *dt, int lts, double *lev) {
+__global__ void k_level_params(Geo g, const double *dt, int lts, double *lev, float *levf) {
   int l = threadIdx.x;
   if (l > g.L) return;
   double dtl = lts ? ldexp(*dt, g.L - l) : *dt;
@@ -372,6 +386,7 @@ __global__ void k_level_params(Geo g, const double *dt, int lts, double *lev) {
     double coef = st == 0 ? 0.5 : 1.0;
     for (int n = 0; n < 3; n++) lev[lev_index(st, l, n)] = (coef * dtl) / g.dx[l][n];
     lev[lev_index(st, l, 3)] = dtl;
+    for (int k = 0; k < 4; k++) levf[lev_index(st, l, k)] = (float)lev[lev_index(st, l, k)];
   }
 }
 
@@ -422,8 +437,8 @@ void launch_dt_final(const unsigned long long *red, double cfl, double t_end, do
                      cudaStream_t st) {
   k_dt_final<<<1, 1, 0, st>>>(red, cfl, t_end, dt, t);
 }
-void launch_level_params(const Geo &g, const double *dt, int lts, double *lev, cudaStream_t st) {
-  k_level_params<<<1, 32, 0, st>>>(g, dt, lts, lev);
+void launch_level_params(const Geo &g, const double *dt, int lts, double *lev, float *levf, cudaStream_t st) {
+  k_level_params<<<1, 32, 0, st>>>(g, dt, lts, lev, levf);
 }
 void launch_advance(const Geo &g, double *t, const double *dt, double factor, long long *counter, int lts,
                     cudaStream_t st) {
