@@ -46,6 +46,7 @@ struct mrfv_ctx {
   std::vector<cudaEvent_t> evs;  // start/end pairs of timed stage launches
   size_t ev_used;
   unsigned long long *dbytes;
+  unsigned *done;  // last-CTA counter of the CFL reduction
   // CUDA graph of one step: [0] with the CFL reduction, [1] with a preset dt
   cudaStream_t cap_st;
   cudaGraphExec_t gexec[2];
@@ -159,6 +160,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t ofs = L.take(cap * 4), oft = L.take(4), onl = L.take(maptotal * 4), onn = L.take(MAXL * 4);
   size_t odsc = L.take(4 * 8), ored = L.take(4 * 8), ocnt = L.take(2 * 8), otot = L.take(5 * 8), osc = L.take(5 * ts);
   size_t obyt = L.take(8), olevp = L.take(2 * MAXL * 4 * 8), olevf = L.take(2 * MAXL * 4 * 4);
+  size_t odone = L.take(8);
   if (c) {
     char *a = c->arena;
     c->U = a + oU; c->Us = a + oUs; c->U0 = a + oU0; c->G = a + oG; c->FR = a + oFR;
@@ -176,6 +178,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->dbytes = (unsigned long long *)(a + obyt);
     c->lev = (double *)(a + olevp);
     c->levf = (float *)(a + olevf);
+    c->done = (unsigned *)(a + odone);
   }
   return L.off + 256;
 }
@@ -288,10 +291,11 @@ struct Seq {
       launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(), grid_for(level_blocks(c->g, l), 1, c->bgrid), c->st);
     c->nlaunch += c->g.L;
   }
+  // CFL reduction; its last CTA sets dt and the per-level step table
   void compute_dt(int lts) {
-    launch_dt<T>(c->g, U(), lts, c->red + 3, c->grid, c->st);
-    launch_dt_final(c->red + 3, c->cfg.cfl, c->cfg.t_end, c->dsc, c->dsc + 1, c->st);
-    c->nlaunch += 2;
+    launch_dt<T>(c->g, U(), lts, c->red + 3, c->done, c->cfg.cfl, c->cfg.t_end, c->dsc, c->lev, c->levf, c->grid,
+                 c->st);
+    c->nlaunch += 1;
   }
   void init_level(const ICParams &ic) {
     launch_init<T>(c->g, ic, c->cfg.hi, U(), c->grid, c->st);
@@ -585,9 +589,12 @@ namespace {
 void issue_step(mrfv_ctx *c, bool preset) {
   int lts = c->cfg.lts;
   dispatch(c, [&](auto &s) {
-    if (!preset) s.compute_dt(lts);
-    launch_level_params(c->g, c->dsc, lts, c->lev, c->levf, c->st);
-    c->nlaunch += 1;
+    if (!preset) {
+      s.compute_dt(lts);
+    } else {
+      launch_level_params(c->g, c->dsc, lts, c->lev, c->levf, c->st);
+      c->nlaunch += 1;
+    }
     if (lts) s.advance(0, 0);
     else s.step_global();
   });

@@ -107,6 +107,21 @@ __device__ __forceinline__ T predict(const T *P, int x, int y, int z, T si, T sj
   }
 }
 
+// Per-level step table (computed once per step, in double): dt_l = dt (global) or
+// dt * 2^(L-l) (level-dependent steps); for each stage coefficient c (1/2, 1)
+// (c dt_l) / dx_{l,n}; and its single-precision copy.
+__device__ inline void level_params_dev(const Geo &g, double dt, int lts, double *lev, float *levf) {
+  for (int l = 0; l <= g.L; l++) {
+    double dtl = lts ? ldexp(dt, g.L - l) : dt;
+    for (int st = 0; st < 2; st++) {
+      double coef = st == 0 ? 0.5 : 1.0;
+      for (int n = 0; n < 3; n++) lev[lev_index(st, l, n)] = (coef * dtl) / g.dx[l][n];
+      lev[lev_index(st, l, 3)] = dtl;
+      for (int k = 0; k < 4; k++) levf[lev_index(st, l, k)] = (float)lev[lev_index(st, l, k)];
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T nan_val() {
   return T(__int_as_float(0x7fc00000));

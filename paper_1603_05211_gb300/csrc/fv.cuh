@@ -303,9 +303,12 @@ __global__ void __launch_bounds__(FVShape<D>::NT, FVMinBlocks<T>::value) k_fv(Ge
 }
 
 // CFL limit over the leaves: min over cells and directions of dx_{l,n} / (|v_n| + c),
-// scaled by 2^(l-L) with level-dependent steps; rho <= 0, p <= 0 or NaN flags an error.
+// scaled by 2^(l-L) with level-dependent steps; rho <= 0, p <= 0 or NaN flags an
+// error.  The last CTA to finish sets dt = cfl * min (clipped to t_end - t) and
+// fills the per-level step table.
 template <typename T, int D>
-__global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long *red) {
+__global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long *red, unsigned *done, double cfl,
+                     double t_end, double *dsc, double *lev, float *levf) {
   constexpr int B = (D == 2) ? 64 : 512;
   int b, e;
   list_range(g, LK_LEAF, 0, g.L, b, e);
@@ -341,6 +344,21 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
   }
   if ((threadIdx.x & 31) == 0 && best < T(INFINITY))
     atomicMin(red, (unsigned long long)__double_as_longlong((double)best));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(done, 1u) == gridDim.x - 1) {
+      __threadfence();
+      double m = __longlong_as_double((long long)atomicAdd(red, 0ull));
+      double d = cfl * m;
+      if (t_end > 0.0) {
+        double rest = t_end - dsc[1];
+        if (rest < d) d = rest;
+      }
+      dsc[0] = d;
+      level_params_dev(g, d, lts, lev, levf);
+    }
+  }
 }
 
 }  // namespace mrfv

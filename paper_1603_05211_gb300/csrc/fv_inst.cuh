@@ -35,15 +35,18 @@ int fv_ctas_per_sm(int dim) {
 }
 
 template <typename T>
-void launch_dt(const Geo &g, const T *A, int lts, unsigned long long *red, int grid, cudaStream_t st) {
+void launch_dt(const Geo &g, const T *A, int lts, unsigned long long *red, unsigned *done, double cfl, double t_end,
+               double *dsc, double *lev, float *levf, int grid, cudaStream_t st) {
   cudaMemsetAsync(red, 0x7f, sizeof(unsigned long long), st);  // a huge positive double
-  if (g.dim == 2) k_dt<T, 2><<<grid, 256, 0, st>>>(g, A, lts, red);
-  else k_dt<T, 3><<<grid, 256, 0, st>>>(g, A, lts, red);
+  cudaMemsetAsync(done, 0, sizeof(unsigned), st);
+  if (g.dim == 2) k_dt<T, 2><<<grid, 256, 0, st>>>(g, A, lts, red, done, cfl, t_end, dsc, lev, levf);
+  else k_dt<T, 3><<<grid, 256, 0, st>>>(g, A, lts, red, done, cfl, t_end, dsc, lev, levf);
 }
 
 #define MRFV_INSTANTIATE_FV(T)                                                                  \
   template void launch_fv<T>(const Geo &, const FVArgs<T> &, int, cudaStream_t);                \
   template int fv_ctas_per_sm<T>(int);                                                          \
-  template void launch_dt<T>(const Geo &, const T *, int, unsigned long long *, int, cudaStream_t);
+  template void launch_dt<T>(const Geo &, const T *, int, unsigned long long *, unsigned *, double, double, double *, \
+                             double *, float *, int, cudaStream_t);
 
 }  // namespace mrfv

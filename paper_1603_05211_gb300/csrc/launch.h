@@ -23,7 +23,8 @@ template <typename T> void launch_copy_level(const Geo &, int l, const T *src, T
 template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw, uint8_t *gflag, int grid, cudaStream_t);
 // finite-volume stage and CFL reduction (fv_f32.cu, fv_f64.cu)
 template <typename T> void launch_fv(const Geo &, const FVArgs<T> &, int grid, cudaStream_t);
-template <typename T> void launch_dt(const Geo &, const T *A, int lts, unsigned long long *red, int grid, cudaStream_t);
+template <typename T> void launch_dt(const Geo &, const T *A, int lts, unsigned long long *red, unsigned *done, double cfl,
+                                     double t_end, double *dsc, double *lev, float *levf, int grid, cudaStream_t);
 template <typename T> int fv_ctas_per_sm(int dim);
 
 // integer tree work (tree.cu)
@@ -36,7 +37,6 @@ void launch_rebuild_lists(const Geo &, uint8_t *kbits, int32_t *tcount, int32_t 
 int scan_tile_entries();
 void launch_cluster(const Geo &, const uint8_t *gflag, uint8_t *sig, double eta, int grid, cudaStream_t);
 void launch_set_double(double *p, double v, cudaStream_t);
-void launch_dt_final(const unsigned long long *red, double cfl, double t_end, double *dt, const double *t, cudaStream_t);
 void launch_level_params(const Geo &, const double *dt, int lts, double *lev, float *levf, cudaStream_t);
 void launch_advance(const Geo &, double *t, const double *dt, double factor, long long *counter, int lts, cudaStream_t);
 

@@ -20,7 +20,7 @@ namespace mrfv {
 // Parent cell = mean of its 2^d children, summed in lexicographic child order
 // (x offset fastest), on every refined block of level l.
 template <typename T, int D>
-__global__ void k_restrict(Geo g, int l, T *__restrict__ A) {
+__device__ __forceinline__ void restrict_level_dev(const Geo &g, int l, T *__restrict__ A) {
   constexpr int B = (D == 2) ? 64 : 512;
   constexpr int BPC = (D == 2) ? 4 : 1;
   int b, e;
@@ -54,11 +54,16 @@ __global__ void k_restrict(Geo g, int l, T *__restrict__ A) {
   }
 }
 
+template <typename T, int D>
+__global__ void k_restrict(Geo g, int l, T *__restrict__ A) {
+  restrict_level_dev<T, D>(g, l, A);
+}
+
 // ---------------------------------------------------------------- MR analysis
 // Normalisation maxima over level 0: |rho|, |rho e|, max_n |v_n| (as the bit
 // patterns of non-negative doubles, so atomicMax on the integer orders them).
 template <typename T, int D>
-__global__ void k_scale_max(Geo g, const T *__restrict__ A, unsigned long long *red) {
+__device__ __forceinline__ void scale_max_dev(const Geo &g, const T *__restrict__ A, unsigned long long *red) {
   constexpr int B = (D == 2) ? 64 : 512;
   int b, e;
   list_range(g, LK_EXIST, 0, 0, b, e);
@@ -89,10 +94,15 @@ __global__ void k_scale_max(Geo g, const T *__restrict__ A, unsigned long long *
   }
 }
 
+template <typename T, int D>
+__global__ void k_scale_max(Geo g, const T *__restrict__ A, unsigned long long *red) {
+  scale_max_dev<T, D>(g, A, red);
+}
+
 // s_rho = max|rho|, s_E = max|rho e|, s_m = max|rho| * max|v_n|, each at least
 // 1e-14 * max|rho| (reading of the paper's unstated normalisation), in T.
 template <typename T, int D>
-__global__ void k_scale_final(const unsigned long long *red, T *scale) {
+__device__ __forceinline__ void scale_final_dev(const unsigned long long *red, T *scale) {
   T mr = (T)__longlong_as_double((long long)red[0]);
   T mE = (T)__longlong_as_double((long long)red[1]);
   T mv = (T)__longlong_as_double((long long)red[2]);
@@ -103,16 +113,19 @@ __global__ void k_scale_final(const unsigned long long *red, T *scale) {
   scale[D + 1] = mE > fl ? mE : fl;
 }
 
+template <typename T, int D>
+__global__ void k_scale_final(const unsigned long long *red, T *scale) {
+  scale_final_dev<T, D>(red, scale);
+}
+
 // Details of every existing block of levels 1..L against the prediction from
 // its parent level; block flag = max over cells and variables of |d_v|/s_v > eps.
 template <typename T, int D>
-__global__ void k_details(Geo g, const T *__restrict__ A, const T *__restrict__ scale, T eps, uint8_t *sig,
-                          double *maxdet) {
+__device__ __forceinline__ void details_dev(const Geo &g, const T *__restrict__ A, const T *__restrict__ scale,
+                                            T eps, uint8_t *sig, double *maxdet, T *patch, T *wmax) {
   constexpr int B = (D == 2) ? 64 : 512;
   constexpr int EXT = 6;
   constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
-  __shared__ T patch[(D + 2) * NP];
-  __shared__ T wmax[32];
   int b, e;
   list_range(g, LK_EXIST, 1, g.L, b, e);
   const long long cap = g.cap;
@@ -154,14 +167,21 @@ __global__ void k_details(Geo g, const T *__restrict__ A, const T *__restrict__ 
   }
 }
 
+template <typename T, int D>
+__global__ void k_details(Geo g, const T *__restrict__ A, const T *__restrict__ scale, T eps, uint8_t *sig,
+                          double *maxdet) {
+  __shared__ T patch[(D + 2) * ((D == 2) ? 36 : 216)];
+  __shared__ T wmax[32];
+  details_dev<T, D>(g, A, scale, eps, sig, maxdet, patch, wmax);
+}
+
 // ---------------------------------------------------------------- prediction of new blocks
 template <typename T, int D>
-__global__ void k_prolong(Geo g, int l, const int32_t *__restrict__ newlist, const int *__restrict__ nnew,
-                          T *__restrict__ A) {
+__device__ __forceinline__ void prolong_level_dev(const Geo &g, int l, const int32_t *__restrict__ newlist,
+                                                  const int *__restrict__ nnew, T *__restrict__ A, T *patch) {
   constexpr int B = (D == 2) ? 64 : 512;
   constexpr int EXT = 6;
   constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
-  __shared__ T patch[(D + 2) * NP];
   const long long cap = g.cap;
   const int n = nnew[l];
   const int c = threadIdx.x;
@@ -177,6 +197,13 @@ __global__ void k_prolong(Geo g, int l, const int32_t *__restrict__ newlist, con
     for (int v = 0; v < D + 2; v++)
       A[((long long)v * cap + s) * B + c] = predict<T, D, EXT>(patch + v * NP, px, py, pz, si, sj, sk);
   }
+}
+
+template <typename T, int D>
+__global__ void k_prolong(Geo g, int l, const int32_t *__restrict__ newlist, const int *__restrict__ nnew,
+                          T *__restrict__ A) {
+  __shared__ T patch[(D + 2) * ((D == 2) ? 36 : 216)];
+  prolong_level_dev<T, D>(g, l, newlist, nnew, A, patch);
 }
 
 // ---------------------------------------------------------------- ghost strips

@@ -1,5 +1,5 @@
 // Allocation-free CFL time step (mrfv_cfl_dt_noalloc): the reduction of
-// k_dt / k_dt_final over a caller-owned dense array of cells, with its scratch
+// k_dt (with its last-CTA finalisation) over a caller-owned dense array of cells, with its scratch
 // in a file-scope device array instead of the context arena.
 //
 // Some callers cannot allocate device memory: code that issues its work while a

@@ -56,7 +56,7 @@ __device__ void mark_children(const Geo &g, uint8_t *need, int l, int bx, int by
 // MR: a significant block of level >= 1 is kept with its 3^d-1 neighbours and,
 // below the finest level, its children are added.  GRAD: the children of every
 // flagged block are added.
-__global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit) {
+__device__ __forceinline__ void k_need_mark_dev(Geo g, const uint8_t *sig, uint8_t *need, int crit) {
   long long total = g.mapoff[g.L + 1];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     if (g.idx[t] < 0 || !sig[t]) continue;
@@ -73,7 +73,7 @@ __global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit) 
 
 // Closure on level l (run from the finest level down): a needed block needs its
 // siblings, its parent and the 3^d-1 neighbours of its parent (gradedness).
-__global__ void k_need_close(Geo g, int l, uint8_t *need) {
+__device__ __forceinline__ void k_need_close_dev(Geo g, int l, uint8_t *need) {
   long long n = g.mapoff[l + 1] - g.mapoff[l];
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
     long long t = g.mapoff[l] + u;
@@ -87,7 +87,7 @@ __global__ void k_need_close(Geo g, int l, uint8_t *need) {
   }
 }
 
-__global__ void k_free(Geo g, const uint8_t *need, int32_t *freestack, int *freetop) {
+__device__ __forceinline__ void k_free_dev(Geo g, const uint8_t *need, int32_t *freestack, int *freetop) {
   long long total = g.mapoff[g.L + 1];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     int32_t s = g.idx[t];
@@ -99,7 +99,7 @@ __global__ void k_free(Geo g, const uint8_t *need, int32_t *freestack, int *free
   }
 }
 
-__global__ void k_alloc(Geo g, const uint8_t *need, int32_t *freestack, int *freetop, int32_t *newlist, int *nnew) {
+__device__ __forceinline__ void k_alloc_dev(Geo g, const uint8_t *need, int32_t *freestack, int *freetop, int32_t *newlist, int *nnew) {
   long long total = g.mapoff[g.L + 1];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     if (g.idx[t] >= 0 || !need[t]) continue;
@@ -159,7 +159,7 @@ __device__ __forceinline__ bool has_children(const Geo &g, int l, int bx, int by
 // One thread per Morton position of every level: kind bits of the block there
 // (exist / leaf / refined / needs ghost strips / needs flux correction), its face
 // neighbour table and its refined-neighbour mask.
-__global__ void k_classify(Geo g, uint8_t *kbits) {
+__device__ __forceinline__ void k_classify_dev(Geo g, uint8_t *kbits) {
   long long total = g.moff[g.L + 1];
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < total; m += (long long)gridDim.x * blockDim.x) {
     int l, bx, by, bz;
@@ -207,7 +207,7 @@ constexpr int SCAN_PER = 8;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_PER;
 
 // per tile: number of entries of each kind
-__global__ void k_tile_count(Geo g, const uint8_t *kbits, int32_t *tcount, int ntiles) {
+__device__ __forceinline__ void k_tile_count_dev(Geo g, const uint8_t *kbits, int32_t *tcount, int ntiles) {
   __shared__ int32_t red[LK_NUM][SCAN_NT / 32];
   long long total = g.moff[g.L + 1];
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -238,7 +238,7 @@ __global__ void k_tile_count(Geo g, const uint8_t *kbits, int32_t *tcount, int n
 // single CTA (1024 threads): exclusive scan of the tile counts of each kind;
 // totals -> loff[kind][L+1].  Each thread sums a run of tiles, the runs are
 // scanned with warp shuffles, then each thread writes its tiles' offsets.
-__global__ void k_tile_scan(Geo g, const int32_t *tcount, int32_t *toff, int ntiles) {
+__device__ __forceinline__ void k_tile_scan_dev(Geo g, const int32_t *tcount, int32_t *toff, int ntiles) {
   __shared__ int32_t wsum[LK_NUM][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int per = (ntiles + blockDim.x - 1) / blockDim.x;
@@ -280,7 +280,7 @@ __global__ void k_tile_scan(Geo g, const int32_t *tcount, int32_t *toff, int nti
 
 // per tile: local exclusive scan, scatter slots into the lists; the thread that
 // owns the first Morton position of a level writes that level's list offsets
-__global__ void k_scatter(Geo g, const uint8_t *kbits, const int32_t *toff, int ntiles) {
+__device__ __forceinline__ void k_scatter_dev(Geo g, const uint8_t *kbits, const int32_t *toff, int ntiles) {
   __shared__ int32_t wsum[LK_NUM][SCAN_NT / 32];
   long long total = g.moff[g.L + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -327,6 +327,24 @@ __global__ void k_scatter(Geo g, const uint8_t *kbits, const int32_t *toff, int 
   }
 }
 
+// ---------------------------------------------------------------- kernels
+__global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit) { k_need_mark_dev(g, sig, need, crit); }
+__global__ void k_need_close(Geo g, int l, uint8_t *need) { k_need_close_dev(g, l, need); }
+__global__ void k_free(Geo g, const uint8_t *need, int32_t *fs, int *ft) { k_free_dev(g, need, fs, ft); }
+__global__ void k_alloc(Geo g, const uint8_t *need, int32_t *fs, int *ft, int32_t *nl, int *nn) {
+  k_alloc_dev(g, need, fs, ft, nl, nn);
+}
+__global__ void k_classify(Geo g, uint8_t *kbits) { k_classify_dev(g, kbits); }
+__global__ void k_tile_count(Geo g, const uint8_t *kbits, int32_t *tcount, int ntiles) {
+  k_tile_count_dev(g, kbits, tcount, ntiles);
+}
+__global__ void k_tile_scan(Geo g, const int32_t *tcount, int32_t *toff, int ntiles) {
+  k_tile_scan_dev(g, tcount, toff, ntiles);
+}
+__global__ void k_scatter(Geo g, const uint8_t *kbits, const int32_t *toff, int ntiles) {
+  k_scatter_dev(g, kbits, toff, ntiles);
+}
+
 // ---------------------------------------------------------------- gradient flags: row clustering
 // Per row of a level's block grid (first direction), runs of at most 8 blocks
 // whose flagged fraction stays >= eta; every block of a run is flagged.
@@ -364,30 +382,9 @@ __global__ void k_cluster(Geo g, const uint8_t *gflag, uint8_t *sig, double eta)
 // ---------------------------------------------------------------- scalars
 __global__ void k_set_double(double *p, double v) { *p = v; }
 
-// dt = cfl * (reduced minimum), clipped to t_end - t when t_end > 0
-__global__ void k_dt_final(const unsigned long long *red, double cfl, double t_end, double *dt, const double *t) {
-  double m = __longlong_as_double((long long)*red);
-  double d = cfl * m;
-  if (t_end > 0.0) {
-    double rest = t_end - *t;
-    if (rest < d) d = rest;
-  }
-  *dt = d;
-}
-
-// Per-level step table for the stage kernels, computed once per step in double:
-// dt_l = dt (global) or dt * 2^(L-l) (level-dependent steps), and for each stage
-// coefficient c (1/2, 1) the ratios (c dt_l) / dx_{l,n}.
+// per-level step table of a preset dt (the CFL path fills it in k_dt's last CTA)
 __global__ void k_level_params(Geo g, const double *dt, int lts, double *lev, float *levf) {
-  int l = threadIdx.x;
-  if (l > g.L) return;
-  double dtl = lts ? ldexp(*dt, g.L - l) : *dt;
-  for (int st = 0; st < 2; st++) {
-    double coef = st == 0 ? 0.5 : 1.0;
-    for (int n = 0; n < 3; n++) lev[lev_index(st, l, n)] = (coef * dtl) / g.dx[l][n];
-    lev[lev_index(st, l, 3)] = dtl;
-    for (int k = 0; k < 4; k++) levf[lev_index(st, l, k)] = (float)lev[lev_index(st, l, k)];
-  }
+  if (threadIdx.x == 0) level_params_dev(g, *dt, lts, lev, levf);
 }
 
 // t += factor * dt; cell-update counter += leaf cells (weighted per level for
@@ -429,14 +426,11 @@ void launch_rebuild_lists(const Geo &g, uint8_t *kbits, int32_t *tcount, int32_t
   k_scatter<<<grid, SCAN_NT, 0, st>>>(g, kbits, toff, ntiles);
 }
 int scan_tile_entries() { return SCAN_TILE; }
+
 void launch_cluster(const Geo &g, const uint8_t *gflag, uint8_t *sig, double eta, int grid, cudaStream_t st) {
   k_cluster<<<grid, 128, 0, st>>>(g, gflag, sig, eta);
 }
 void launch_set_double(double *p, double v, cudaStream_t st) { k_set_double<<<1, 1, 0, st>>>(p, v); }
-void launch_dt_final(const unsigned long long *red, double cfl, double t_end, double *dt, const double *t,
-                     cudaStream_t st) {
-  k_dt_final<<<1, 1, 0, st>>>(red, cfl, t_end, dt, t);
-}
 void launch_level_params(const Geo &g, const double *dt, int lts, double *lev, float *levf, cudaStream_t st) {
   k_level_params<<<1, 32, 0, st>>>(g, dt, lts, lev, levf);
 }
