@@ -88,6 +88,8 @@ typedef struct {
   size_t arena_bytes;   /* its size; must be >= mrfv_arena_bytes(config) */
   int use_graph;        /* 1 (default): the first mrfv_step captures the step's launch sequence into a
                            CUDA graph (on a private stream) and every step replays it on `stream` */
+  int proposer;         /* 1: MR adaptation takes the learned proposer's blocks instead of the safety
+                           zone, once weights are set (mrfv_proposer_set_weights) */
 } mrfv_config;
 
 typedef struct {
@@ -137,8 +139,9 @@ int mrfv_analyse(mrfv_ctx *ctx, double eps, int64_t *n_significant);
    one level and safety zone (MR) or gradient flags + clustering (GRAD),
    gradedness closure, removal of blocks that are no longer needed, prediction
    of new blocks from their parent level, rebuild of neighbour tables and work
-   lists.  use_proposer is reserved and must be 0.  *n_blocks (may be NULL)
-   receives the number of existing blocks (synchronises when non-NULL). */
+   lists.  use_proposer = 1 takes the learned proposer's blocks instead of the MR
+   safety zone (weights must be set).  *n_blocks (may be NULL) receives the
+   number of existing blocks (synchronises when non-NULL). */
 int mrfv_adapt(mrfv_ctx *ctx, int use_proposer, int64_t *n_blocks);
 
 /* CFL time step over the leaves: cfl * min over leaf cells and directions of
@@ -214,6 +217,34 @@ typedef struct {
 int mrfv_profile_enable(mrfv_ctx *ctx, int enable);
 /* Read the counters (synchronises the stream). */
 int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
+
+/* Learned refinement proposer (no counterpart in the paper, which refines by
+   the heuristic of Section 2.1): a 3-layer 3D convolutional net (16 channels,
+   3^3 kernels, zero padding, ReLU between layers; BF16 weights and activations,
+   FP32 accumulation, inference on the tensor cores) over three features of every
+   block position of every level (block-mean density / s_rho, block-mean pressure
+   / ((gamma-1) s_E), min(max normalised detail / eps, 8) / 8; absent blocks take
+   the means of their parent's covering octant).  A position of level >= 1 with a
+   positive logit and an existing parent is added to the tree; with cfg.proposer
+   this replaces the safety zone of the MR rule, and the MR thresholding of the
+   next analysis re-refines anything it missed.
+   "positions" = sum over levels of the level's block count.
+   Weight layout (FP32): W1[16][3][27], b1[16], W2[16][16][27], b2[16],
+   W3[1][16][27], b3[1]; tap index (dz+1)*9 + (dy+1)*3 + (dx+1). */
+#define MRFV_PROPOSER_NWEIGHTS 8673
+/* Set the FP32 master weights (n = MRFV_PROPOSER_NWEIGHTS) and reset the Adam state. */
+int mrfv_proposer_set_weights(mrfv_ctx *ctx, const float *w, int64_t n);
+int mrfv_proposer_get_weights(mrfv_ctx *ctx, float *w, int64_t n);
+/* Features of the current state and last analysis: feat[3][positions] (n = 3 * positions). */
+int mrfv_proposer_features(mrfv_ctx *ctx, float *feat, int64_t n);
+/* Logits of the current features (n = positions), through the tensor-core kernels. */
+int mrfv_proposer_infer(mrfv_ctx *ctx, float *logits, int64_t n);
+/* `steps` Adam steps (learning rate lr) on nsnap snapshots: feat[nsnap][3][positions],
+   target[nsnap][positions] (1 = block needed at the next step); binary
+   cross-entropy over positions of level >= 1 with an existing parent (in the
+   current tree).  *loss = loss of the last step. */
+int mrfv_proposer_train(mrfv_ctx *ctx, const float *feat, const uint8_t *target, int nsnap, int steps, float lr,
+                        double *loss);
 
 /* Allocation-free CFL time step of a caller-owned dense array of cells (no
    counterpart in the paper).  Some callers cannot call cudaMalloc: work issued

@@ -42,7 +42,7 @@ class Config(ctypes.Structure):
         ("eps", ctypes.c_double), ("eps_w", ctypes.c_double), ("eta_tol", ctypes.c_double),
         ("lts", ctypes.c_int), ("pool_blocks", ctypes.c_int64),
         ("stream", ctypes.c_void_p), ("device_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
-        ("use_graph", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("proposer", ctypes.c_int),
     ]
 
 
@@ -91,7 +91,14 @@ SIGNATURES = {
     "mrfv_profile_enable": (_I, [_P, _I]),
     "mrfv_profile_read": (_I, [_P, ctypes.POINTER(Profile)]),
     "mrfv_cfl_dt_noalloc": (_I, [_I, _I, _P, _I64, _I64, _I64, _DP, _D, _D, _P, _P]),
+    "mrfv_proposer_set_weights": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I64]),
+    "mrfv_proposer_get_weights": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I64]),
+    "mrfv_proposer_features": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I64]),
+    "mrfv_proposer_infer": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I64]),
+    "mrfv_proposer_train": (_I, [_P, ctypes.POINTER(ctypes.c_float), _U8, _I, _I, ctypes.c_float,
+                                 ctypes.POINTER(ctypes.c_double)]),
 }
+PROPOSER_NWEIGHTS = 8673
 
 _lib = None
 
@@ -136,7 +143,7 @@ class Solver:
     def __init__(self, dim=2, precision="fp64", levels=1, base_blocks=(1, 1, 1), lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), bc=BC_TRANSMISSIVE, gamma=1.4, cfl=0.5, t_end=0.0, adapt=False,
                  criterion="mr", eps=1e-3, eps_w=0.05, eta_tol=0.8, lts=False, pool_blocks=0, stream=None,
-                 use_graph=True):
+                 use_graph=True, proposer=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -161,6 +168,7 @@ class Solver:
         cfg.lts = int(bool(lts))
         cfg.pool_blocks = int(pool_blocks)
         cfg.use_graph = int(bool(use_graph))
+        cfg.proposer = int(bool(proposer))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         cfg.stream = self.stream.cuda_stream
         nbytes = lib.mrfv_arena_bytes(ctypes.byref(cfg))
@@ -278,6 +286,45 @@ class Solver:
 
     def synchronize(self) -> None:
         self._check(self.lib.mrfv_synchronize(self._h))
+
+    # ------------------------------------------------------------------ learned proposer
+    @property
+    def positions(self) -> int:
+        """Block positions of every level (the proposer's grid)."""
+        return sum(int(np.prod(self.blocks_shape(l))) for l in range(self.levels))
+
+    def adapt_with(self, use_proposer: bool) -> int:
+        n = ctypes.c_int64(0)
+        self._check(self.lib.mrfv_adapt(self._h, int(bool(use_proposer)), ctypes.byref(n)))
+        return n.value
+
+    def proposer_set_weights(self, w) -> None:
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        self._check(self.lib.mrfv_proposer_set_weights(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+
+    def proposer_get_weights(self) -> np.ndarray:
+        a = np.empty(PROPOSER_NWEIGHTS, dtype=np.float32)
+        self._check(self.lib.mrfv_proposer_get_weights(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+        return a
+
+    def proposer_features(self) -> np.ndarray:
+        a = np.empty((3, self.positions), dtype=np.float32)
+        self._check(self.lib.mrfv_proposer_features(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+        return a
+
+    def proposer_infer(self) -> np.ndarray:
+        a = np.empty(self.positions, dtype=np.float32)
+        self._check(self.lib.mrfv_proposer_infer(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+        return a
+
+    def proposer_train(self, feats, targets, steps: int, lr: float) -> float:
+        f = np.ascontiguousarray(feats, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.uint8)
+        ns = f.shape[0]
+        loss = ctypes.c_double(0.0)
+        self._check(self.lib.mrfv_proposer_train(self._h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _u8(t),
+                                                 ns, steps, lr, ctypes.byref(loss)))
+        return loss.value
 
     def profile_enable(self, enable: bool = True) -> None:
         self._check(self.lib.mrfv_profile_enable(self._h, int(bool(enable))))

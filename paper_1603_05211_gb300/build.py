@@ -7,7 +7,8 @@ Translation units and their floating-point flags:
   fv_f32.cu : --use_fast_math (single-precision throughput path);
   tree.cu, api.cu : integer work and host sequencing;
   noalloc.cu : -fmad=false (the allocation-free CFL reduction rounds like the
-      double-precision one in fv_f64.cu).
+      double-precision one in fv_f64.cu);
+  proposer.cu : the learned refinement proposer (tcgen05 inference, FP32 training).
 """
 from __future__ import annotations
 
@@ -34,6 +35,7 @@ UNITS = {
     "tree.cu": [],
     "api.cu": [],
     "noalloc.cu": ["-fmad=false"],
+    "proposer.cu": [],
 }
 
 

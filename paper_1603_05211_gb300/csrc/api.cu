@@ -12,6 +12,7 @@
 #include "common.h"
 #include "launch.h"
 #include "mrfv.h"
+#include <cuda_bf16.h>
 
 using namespace mrfv;
 
@@ -47,6 +48,12 @@ struct mrfv_ctx {
   size_t ev_used;
   unsigned long long *dbytes;
   unsigned *done;  // last-CTA counter of the CFL reduction
+  // learned proposer
+  float *pfeat, *plogit, *pb1, *pb2, *pb3, *pblob, *pgrad, *pm1, *pm2, *pwork;
+  __nv_bfloat16 *pa0, *pa1, *pa2, *pw1, *pw2, *pw3;
+  double *ploss;
+  bool has_weights;
+  int adam_t;
   // CUDA graph of one step: [0] with the CFL reduction, [1] with a preset dt
   cudaStream_t cap_st;
   cudaGraphExec_t gexec[2];
@@ -78,6 +85,7 @@ int check_device(mrfv_ctx *c, const char *where) {
   if (e != cudaSuccess) return fail(c, MRFV_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
   if (bits) {
     cudaMemset(c->g.err, 0, sizeof(int));
+    if (bits & EB_TIMEOUT) return fail(c, MRFV_ERR_TIMEOUT, std::string(where) + ": a bounded device wait expired");
     if (bits & EB_POOL) return fail(c, MRFV_ERR_POOL_FULL, std::string(where) + ": block pool capacity exceeded");
     if (bits & EB_TREE) return fail(c, MRFV_ERR_TREE, std::string(where) + ": a kernel met a block tree that is not graded");
     if (bits & EB_NONPHYS)
@@ -161,6 +169,11 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t odsc = L.take(4 * 8), ored = L.take(4 * 8), ocnt = L.take(2 * 8), otot = L.take(5 * 8), osc = L.take(5 * ts);
   size_t obyt = L.take(8), olevp = L.take(2 * MAXL * 4 * 8), olevf = L.take(2 * MAXL * 4 * 4);
   size_t odone = L.take(8);
+  const size_t NW = MRFV_PROPOSER_NWEIGHTS;
+  size_t opf = L.take(3 * maptotal * 4), opl = L.take(maptotal * 4), opa0 = L.take(3 * maptotal * 2);
+  size_t opa1 = L.take(16 * maptotal * 2), opa2 = L.take(16 * maptotal * 2);
+  size_t opw1 = L.take(16 * 96 * 2), opw2 = L.take(16 * 432 * 2), opw3 = L.take(16 * 432 * 2);
+  size_t opb = L.take(3 * 16 * 4), opblob = L.take(4 * NW * 4), opwork = L.take(50 * maptotal * 4), oploss = L.take(8);
   if (c) {
     char *a = c->arena;
     c->U = a + oU; c->Us = a + oUs; c->U0 = a + oU0; c->G = a + oG; c->FR = a + oFR;
@@ -179,6 +192,23 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->lev = (double *)(a + olevp);
     c->levf = (float *)(a + olevf);
     c->done = (unsigned *)(a + odone);
+    c->pfeat = (float *)(a + opf);
+    c->plogit = (float *)(a + opl);
+    c->pa0 = (__nv_bfloat16 *)(a + opa0);
+    c->pa1 = (__nv_bfloat16 *)(a + opa1);
+    c->pa2 = (__nv_bfloat16 *)(a + opa2);
+    c->pw1 = (__nv_bfloat16 *)(a + opw1);
+    c->pw2 = (__nv_bfloat16 *)(a + opw2);
+    c->pw3 = (__nv_bfloat16 *)(a + opw3);
+    c->pb1 = (float *)(a + opb);
+    c->pb2 = c->pb1 + 16;
+    c->pb3 = c->pb2 + 16;
+    c->pblob = (float *)(a + opblob);
+    c->pgrad = c->pblob + NW;
+    c->pm1 = c->pgrad + NW;
+    c->pm2 = c->pm1 + NW;
+    c->pwork = (float *)(a + opwork);
+    c->ploss = (double *)(a + oploss);
   }
   return L.off + 256;
 }
@@ -302,6 +332,10 @@ struct Seq {
     c->nlaunch += 1;
     restrict_all(U());
   }
+  void prop_features() {
+    launch_prop_features<T>(c->g, U(), c->maxdet, (const T *)c->scale, c->cfg.eps, c->pfeat, c->grid, c->st);
+    c->nlaunch += 1;
+  }
   void gradflags() {
     cudaMemsetAsync(c->gflag, 0, c->maptotal, c->st);
     cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
@@ -332,14 +366,29 @@ void apply_need(mrfv_ctx *c, bool prolong) {
   if (prolong) dispatch(c, [&](auto &s) { s.prolong_new(); });
 }
 
+void prop_infer(mrfv_ctx *c) {
+  launch_prop_infer(c->g, c->pfeat, c->pa0, c->pa1, c->pa2, c->pw1, c->pb1, c->pw2, c->pb2, c->pw3, c->pb3, c->plogit,
+                    c->nsm, c->st);
+  c->nlaunch += 4;
+}
+
 // analysis / flags -> needed blocks -> closure -> apply
 void adapt_tree(mrfv_ctx *c) {
   const Geo &g = c->g;
+  bool use_prop = c->cfg.proposer && c->has_weights && c->cfg.criterion == MRFV_CRIT_MR;
   if (c->cfg.criterion == MRFV_CRIT_MR) dispatch(c, [&](auto &s) { s.analyse(c->cfg.eps); });
   else dispatch(c, [&](auto &s) { s.gradflags(); });
+  if (use_prop) {
+    dispatch(c, [&](auto &s) { s.prop_features(); });
+    prop_infer(c);
+  }
   cudaMemsetAsync(c->need, 0, c->maptotal, c->st);
   cudaMemsetAsync(c->need, 1, g.mapoff[1], c->st);
-  launch_need_mark(g, c->sig, c->need, c->cfg.criterion, c->grid, c->st);
+  launch_need_mark(g, c->sig, c->need, use_prop ? 2 : c->cfg.criterion, c->grid, c->st);
+  if (use_prop) {
+    launch_prop_mark(g, c->plogit, c->need, c->grid, c->st);
+    c->nlaunch += 1;
+  }
   for (int l = g.L; l >= 1; l--) launch_need_close(g, l, c->need, grid_for(level_blocks(g, l), 256, c->grid), c->st);
   c->nlaunch += 1 + g.L;
   apply_need(c, true);
@@ -484,6 +533,7 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   cudaMemsetAsync(c->counter, 0, 2 * 8, c->st);
   launch_init_freestack(c->freestack, c->freetop, c->g.cap, c->grid, c->st);
   if (cfg->use_graph && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) c->cap_st = nullptr;
+  prop_setup();
   int rc = check_launch(c, "mrfv_create");
   if (rc == MRFV_OK) rc = check_device(c, "mrfv_create");
   if (rc != MRFV_OK) {
@@ -549,9 +599,13 @@ int mrfv_analyse(mrfv_ctx *c, double eps, int64_t *n_sig) {
 }
 
 int mrfv_adapt(mrfv_ctx *c, int use_proposer, int64_t *n_blocks) {
-  if (!c || use_proposer != 0) return fail(c, MRFV_ERR_ARG, "adapt: use_proposer must be 0");
+  if (!c || (use_proposer != 0 && use_proposer != 1)) return fail(c, MRFV_ERR_ARG, "adapt: use_proposer is 0 or 1");
   if (!c->initialized) return fail(c, MRFV_ERR_STATE, "adapt before init");
+  if (use_proposer && !c->has_weights) return fail(c, MRFV_ERR_STATE, "adapt: proposer without weights");
+  int saved = c->cfg.proposer;
+  c->cfg.proposer = use_proposer;
   adapt_tree(c);
+  c->cfg.proposer = saved;
   int rc = check_launch(c, "mrfv_adapt");
   if (rc != MRFV_OK) return rc;
   if (n_blocks) {
@@ -785,6 +839,90 @@ int mrfv_get_flags(mrfv_ctx *c, int level, uint8_t *flags, double *maxdet, int64
 int mrfv_synchronize(mrfv_ctx *c) {
   if (!c) return MRFV_ERR_ARG;
   return check_device(c, "mrfv_synchronize");
+}
+
+int mrfv_proposer_set_weights(mrfv_ctx *c, const float *w, int64_t n) {
+  if (!c || !w || n != MRFV_PROPOSER_NWEIGHTS) return fail(c, MRFV_ERR_ARG, "proposer_set_weights: n");
+  const size_t NW = MRFV_PROPOSER_NWEIGHTS;
+  cudaMemcpyAsync(c->pblob, w, NW * 4, cudaMemcpyHostToDevice, c->st);
+  cudaMemsetAsync(c->pm1, 0, 2 * NW * 4, c->st);
+  launch_pack_weights(c->pblob, c->pw1, c->pb1, c->pw2, c->pb2, c->pw3, c->pb3, c->st);
+  int rc = check_launch(c, "mrfv_proposer_set_weights");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_proposer_set_weights");
+  if (rc == MRFV_OK) {
+    c->has_weights = true;
+    c->adam_t = 0;
+    // a captured step graph does not contain the proposer path yet
+    for (int v = 0; v < 2; v++)
+      if (c->gexec[v]) {
+        cudaGraphExecDestroy(c->gexec[v]);
+        c->gexec[v] = nullptr;
+      }
+  }
+  return rc;
+}
+
+int mrfv_proposer_get_weights(mrfv_ctx *c, float *w, int64_t n) {
+  if (!c || !w || n != MRFV_PROPOSER_NWEIGHTS) return fail(c, MRFV_ERR_ARG, "proposer_get_weights: n");
+  int rc = check_device(c, "mrfv_proposer_get_weights");
+  if (rc == MRFV_OK) cudaMemcpy(w, c->pblob, n * 4, cudaMemcpyDeviceToHost);
+  return rc;
+}
+
+int mrfv_proposer_features(mrfv_ctx *c, float *feat, int64_t n) {
+  if (!c || !feat || n != 3 * c->maptotal) return fail(c, MRFV_ERR_ARG, "proposer_features: n = 3 * positions");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "proposer_features before init");
+  dispatch(c, [&](auto &s) { s.prop_features(); });
+  int rc = check_launch(c, "mrfv_proposer_features");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_proposer_features");
+  if (rc == MRFV_OK) cudaMemcpy(feat, c->pfeat, n * 4, cudaMemcpyDeviceToHost);
+  return rc;
+}
+
+int mrfv_proposer_infer(mrfv_ctx *c, float *logits, int64_t n) {
+  if (!c || !logits || n != c->maptotal) return fail(c, MRFV_ERR_ARG, "proposer_infer: n = positions");
+  if (!c->initialized || !c->has_weights) return fail(c, MRFV_ERR_STATE, "proposer_infer before init / weights");
+  dispatch(c, [&](auto &s) { s.prop_features(); });
+  prop_infer(c);
+  int rc = check_launch(c, "mrfv_proposer_infer");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_proposer_infer");
+  if (rc == MRFV_OK) cudaMemcpy(logits, c->plogit, n * 4, cudaMemcpyDeviceToHost);
+  return rc;
+}
+
+int mrfv_proposer_train(mrfv_ctx *c, const float *feat, const uint8_t *target, int nsnap, int steps, float lr,
+                        double *loss) {
+  if (!c || !feat || !target || nsnap < 1 || steps < 0 || !(lr > 0.f))
+    return fail(c, MRFV_ERR_ARG, "proposer_train: arguments");
+  if (!c->initialized || !c->has_weights) return fail(c, MRFV_ERR_STATE, "proposer_train before init / weights");
+  long long n = c->maptotal;
+  float *df = nullptr;
+  uint8_t *dt = nullptr;
+  if (cudaMalloc(&df, (size_t)nsnap * 3 * n * 4) != cudaSuccess || cudaMalloc(&dt, (size_t)nsnap * n) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(df);
+    return fail(c, MRFV_ERR_CUDA, "proposer_train: staging allocation");
+  }
+  cudaMemcpy(df, feat, (size_t)nsnap * 3 * n * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dt, target, (size_t)nsnap * n, cudaMemcpyHostToDevice);
+  double last = 0.0;
+  int rc = MRFV_OK;
+  for (int k = 0; k < steps && rc == MRFV_OK; k++) {
+    cudaMemsetAsync(c->ploss, 0, 8, c->st);
+    launch_prop_train_step(c->g, df, dt, nsnap, c->pblob, c->pgrad, c->pm1, c->pm2, ++c->adam_t, lr, c->pwork,
+                           c->ploss, c->st);
+    rc = check_launch(c, "mrfv_proposer_train");
+    if (rc == MRFV_OK && k == steps - 1) {
+      rc = check_device(c, "mrfv_proposer_train");
+      cudaMemcpy(&last, c->ploss, 8, cudaMemcpyDeviceToHost);
+    }
+  }
+  launch_pack_weights(c->pblob, c->pw1, c->pb1, c->pw2, c->pb2, c->pw3, c->pb3, c->st);
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_proposer_train");
+  cudaFree(df);
+  cudaFree(dt);
+  if (loss) *loss = last;
+  return rc;
 }
 
 int mrfv_profile_enable(mrfv_ctx *c, int enable) {

@@ -21,7 +21,7 @@ constexpr int NBR_MISSING = -1;  // same-level neighbour absent: read the ghost 
 constexpr int NBR_WALL = -2;     // outside a transmissive domain: zero-gradient copy
 
 enum ListKind { LK_EXIST = 0, LK_LEAF = 1, LK_INTERNAL = 2, LK_GHOST = 3, LK_REFLUX = 4, LK_NUM = 5 };
-enum ErrBits { EB_TREE = 1, EB_NONPHYS = 2, EB_POOL = 4 };
+enum ErrBits { EB_TREE = 1, EB_NONPHYS = 2, EB_POOL = 4, EB_TIMEOUT = 8 };
 
 // Geometry and tree pointers, passed to kernels by value.
 struct Geo {

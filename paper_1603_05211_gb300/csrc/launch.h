@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "common.h"
 
 namespace mrfv {
@@ -39,5 +41,18 @@ void launch_cluster(const Geo &, const uint8_t *gflag, uint8_t *sig, double eta,
 void launch_set_double(double *p, double v, cudaStream_t);
 void launch_level_params(const Geo &, const double *dt, int lts, double *lev, float *levf, cudaStream_t);
 void launch_advance(const Geo &, double *t, const double *dt, double factor, long long *counter, int lts, cudaStream_t);
+
+// learned refinement proposer (proposer.cu)
+template <typename T> void launch_prop_features(const Geo &, const T *U, const double *maxdet, const T *scale, double eps,
+                                                float *feat, int grid, cudaStream_t);
+void prop_setup();
+void launch_prop_infer(const Geo &, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
+                       const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
+                       const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaStream_t);
+void launch_prop_mark(const Geo &, const float *logits, uint8_t *need, int grid, cudaStream_t);
+void launch_pack_weights(const float *blob, __nv_bfloat16 *w1, float *b1, __nv_bfloat16 *w2, float *b2,
+                         __nv_bfloat16 *w3, float *b3, cudaStream_t);
+void launch_prop_train_step(const Geo &, const float *feat, const uint8_t *target, int ns, float *blob, float *grad,
+                            float *m1, float *m2, int t, float lr, float *work, double *loss, cudaStream_t);
 
 }  // namespace mrfv

@@ -1,0 +1,524 @@
+// Learned refinement proposer: a 3-layer 3D convolutional net over per-block
+// features of every level (16 channels, 3^3 kernels, zero padding, ReLU between
+// layers; BF16 weights and activations, FP32 accumulation) whose logits mark
+// the blocks to add before the next step.  It replaces the safety zone of the
+// MR refinement rule; the MR thresholding at the next analysis still keeps and
+// refines every significant block, so a missed block is re-refined one step
+// later.  No counterpart in the paper (its refinement is Section 2.1's
+// heuristic).
+//
+// Inference: implicit-GEMM convolution on the 5th-generation tensor cores.  A
+// CTA takes 128 output positions (rows, M = 128) x 16 output channels
+// (N = 16) x K = Cin * 27 taps; the im2col rows and the weights are staged in
+// shared memory in the no-swizzle K-major core-matrix layout (8 x 16 B core
+// matrices), one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32)
+// per K = 16 slice into a TMEM accumulator of 128 lanes x 16 columns, commits
+// to an mbarrier, and the four warps read the accumulator back with tcgen05.ld.
+// Every wait is bounded; on expiry the kernel records EB_TIMEOUT, frees its TMEM
+// and returns.
+//
+// Training: FP32 CUDA-core kernels (direct convolution forward, binary
+// cross-entropy gradient, backward convolution for weights and inputs, Adam).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.h"
+#include "dev.cuh"
+#include "launch.h"
+
+namespace mrfv {
+
+// ---------------------------------------------------------------- geometry of positions
+// Positions are the block positions of every level (dense maps, levels
+// concatenated); a 3^3 neighbourhood stays inside the level (zero outside).
+__device__ __forceinline__ int pos_level(const Geo &g, long long p) {
+  int l = 0;
+  while (l < g.L && p >= g.mapoff[l + 1]) l++;
+  return l;
+}
+__device__ __forceinline__ long long pos_neighbour(const Geo &g, int l, long long p, int dx, int dy, int dz) {
+  long long u = p - g.mapoff[l];
+  int nx = g.nb[l][0], ny = g.nb[l][1], nz = g.nb[l][2];
+  int x = (int)(u % nx) + dx, y = (int)((u / nx) % ny) + dy, z = (int)(u / ((long long)nx * ny)) + dz;
+  if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) return -1;
+  return g.mapoff[l] + x + (long long)nx * (y + (long long)ny * z);
+}
+
+// ---------------------------------------------------------------- features
+// Per position of level l: block-mean density / s_rho, block-mean pressure /
+// ((gamma-1) s_E), and min(max normalised detail / eps, 8) / 8.  An absent block
+// takes its means from the octant (quadrant) of its parent that covers it, and
+// detail 0; without a parent all three are 0.
+template <typename T, int D>
+__global__ void k_prop_features(Geo g, const T *__restrict__ U, const double *__restrict__ maxdet,
+                                const T *__restrict__ scale, double eps, float *__restrict__ feat) {
+  constexpr int B = (D == 2) ? 64 : 512;
+  const long long n = g.mapoff[g.L + 1];
+  const long long cap = g.cap;
+  const float srho = (float)scale[0], sp = (float)((g.gamma - 1.0) * (double)scale[D + 1]);
+  const float gm1 = (float)(g.gamma - 1.0);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int l = pos_level(g, p);
+    long long u = p - g.mapoff[l];
+    int bx = (int)(u % g.nb[l][0]), by = (int)((u / g.nb[l][0]) % g.nb[l][1]);
+    int bz = (int)(u / ((long long)g.nb[l][0] * g.nb[l][1]));
+    int32_t s = g.idx[p];
+    int c0[3] = {0, 0, 0}, ext = 8;
+    float f2 = 0.f;
+    if (s < 0 && l > 0) {
+      s = g.idx[map_index(g, l - 1, bx >> 1, by >> 1, bz >> 1)];
+      c0[0] = 4 * (bx & 1);
+      c0[1] = 4 * (by & 1);
+      c0[2] = (D == 3) ? 4 * (bz & 1) : 0;
+      ext = 4;
+    } else if (s >= 0) {
+      float m = (float)(maxdet[p] / eps);
+      f2 = fminf(m, 8.f) / 8.f;
+    }
+    float f0 = 0.f, f1 = 0.f;
+    if (s >= 0) {
+      double sr = 0.0, spp = 0.0;
+      int kz = (D == 3) ? ext : 1;
+      for (int k = 0; k < kz; k++)
+        for (int j = 0; j < ext; j++)
+          for (int i = 0; i < ext; i++) {
+            int c = (c0[0] + i) + 8 * (c0[1] + j) + ((D == 3) ? 64 * (c0[2] + k) : 0);
+            float rho = (float)U[((long long)0 * cap + s) * B + c];
+            float vv = 0.f;
+            for (int d = 0; d < D; d++) {
+              float m = (float)U[((long long)(1 + d) * cap + s) * B + c];
+              vv += m * m;
+            }
+            float E = (float)U[((long long)(D + 1) * cap + s) * B + c];
+            sr += rho;
+            spp += gm1 * (E - 0.5f * vv / rho);
+          }
+      double cnt = (double)(ext * ext * ((D == 3) ? ext : 1));
+      f0 = (float)(sr / cnt) / srho;
+      f1 = (float)(spp / cnt) / sp;
+    }
+    feat[p] = f0;
+    feat[n + p] = f1;
+    feat[2 * n + p] = f2;
+  }
+}
+
+__global__ void k_to_bf16(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16_rn(in[i]);
+}
+
+// ---------------------------------------------------------------- tcgen05 helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading-dimension byte offset
+// (between core matrices adjacent along K), stride byte offset (between 8-row
+// groups along M or N), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of element (r, k) of a K-major tile with KP columns, core-matrix layout
+__device__ __forceinline__ uint32_t cm_offset(int r, int k, int KP) {
+  return (uint32_t)((((r >> 3) * (KP >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+constexpr unsigned kWaitLimit = 1u << 24;
+
+// bounded wait for the mbarrier phase `parity`; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (unsigned it = 0; it < kWaitLimit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- convolution layer on tensor cores
+// in: BF16 [CIN][npos]; W: BF16 [16][KP] (row = output channel, K index
+// cin*27 + tap, tap = (dz+1)*9 + (dy+1)*3 + (dx+1), zero padded); bias FP32 [16].
+// LAST: logits[p] = acc[0] + bias[0]; otherwise out[n][p] = bf16(relu(acc + bias)).
+template <int CIN, int KP, bool LAST>
+__global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16 *__restrict__ in,
+                                                      const __nv_bfloat16 *__restrict__ W,
+                                                      const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out,
+                                                      float *__restrict__ logits) {
+  constexpr int M = 128, N = 16;
+  constexpr int KREAL = CIN * 27;
+  static_assert(KP % 16 == 0 && KP >= KREAL, "K padding");
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char *sA = sm;                       // M x KP bf16
+  unsigned char *sB = sm + M * KP * 2;          // N x KP bf16
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + (M + N) * KP * 2);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long npos = g.mapoff[g.L + 1];
+  const int dim3d = g.dim == 3;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(32)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
+  }
+  // weights -> shared (core-matrix layout)
+  for (int i = tid; i < N * KP; i += blockDim.x) {
+    int n = i / KP, k = i % KP;
+    *reinterpret_cast<__nv_bfloat16 *>(sB + cm_offset(n, k, KP)) = W[i];
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t mb = smem_u32(mbar);
+  const uint32_t aaddr = smem_u32(sA), baddr = smem_u32(sB);
+  constexpr uint32_t LBO = 128, SBO = (KP / 8) * 128;
+  constexpr uint32_t IDESC = idesc_bf16(M, N);
+  uint32_t phase = 0;
+  bool ok = true;
+
+  const long long ntiles = (npos + M - 1) / M;
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    // im2col rows of this tile -> shared
+    for (int i = tid; i < M * KP; i += blockDim.x) {
+      int m = i / KP, k = i % KP;
+      long long p = tile * M + m;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (p < npos && k < KREAL) {
+        int ci = k / 27, t = k % 27;
+        int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        if (dim3d || dz == 0) {
+          long long q = pos_neighbour(g, pos_level(g, p), p, dx, dy, dz);
+          if (q >= 0) v = in[(long long)ci * npos + q];
+        }
+      }
+      *reinterpret_cast<__nv_bfloat16 *>(sA + cm_offset(m, k, KP)) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+#pragma unroll 1
+      for (int ks = 0; ks < KP / 16; ks++) {
+        uint64_t ad = smem_desc(aaddr + ks * 256, LBO, SBO);
+        uint64_t bd = smem_desc(baddr + ks * 256, LBO, SBO);
+        uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                   : "memory");
+    }
+    __syncwarp();
+    ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;  // one decision for the whole CTA
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+      if (tid == 0) atomicOr(g.err, EB_TIMEOUT);
+      break;
+    }
+    // accumulator rows 32*warp .. 32*warp+31 (one per lane), 16 columns
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    long long p = tile * M + 32 * warp + lane;
+    if (p < npos) {
+      if (LAST) {
+        logits[p] = __uint_as_float(r[0]) + bias[0];
+      } else {
+#pragma unroll
+        for (int n = 0; n < N; n++) {
+          float v = __uint_as_float(r[n]) + bias[n];
+          out[(long long)n * npos + p] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
+  }
+}
+
+template <int KP>
+constexpr size_t conv_smem() {
+  return (size_t)(128 + 16) * KP * 2 + 16;
+}
+
+// ---------------------------------------------------------------- marking
+// Positions of level >= 1 whose parent exists and whose logit is positive are
+// needed (the closure then adds their siblings, parents and grading).
+__global__ void k_prop_mark(Geo g, const float *__restrict__ logits, uint8_t *need) {
+  const long long n = g.mapoff[g.L + 1];
+  for (long long p = g.mapoff[1] + blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (!(logits[p] > 0.f)) continue;
+    int l = pos_level(g, p);
+    long long u = p - g.mapoff[l];
+    int bx = (int)(u % g.nb[l][0]), by = (int)((u / g.nb[l][0]) % g.nb[l][1]);
+    int bz = (int)(u / ((long long)g.nb[l][0] * g.nb[l][1]));
+    if (g.idx[map_index(g, l - 1, bx >> 1, by >> 1, bz >> 1)] < 0) continue;
+    need[p] = 1;
+  }
+}
+
+// ---------------------------------------------------------------- training (FP32, CUDA cores)
+// direct convolution: y[co][p] = b[co] + sum_{ci,tap} w[co][ci][tap] * x[ci][p+tap]
+__global__ void k_conv_fwd_f32(Geo g, const float *__restrict__ x, int cin, const float *__restrict__ w,
+                               const float *__restrict__ b, int cout, float *__restrict__ y, int relu) {
+  const long long n = g.mapoff[g.L + 1];
+  const int dim3d = g.dim == 3;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n * cout;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int co = (int)(idx / n);
+    long long p = idx % n;
+    int l = pos_level(g, p);
+    float acc = b[co];
+    for (int t = 0; t < 27; t++) {
+      int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+      if (!dim3d && dz != 0) continue;
+      long long q = pos_neighbour(g, l, p, dx, dy, dz);
+      if (q < 0) continue;
+      for (int ci = 0; ci < cin; ci++) acc += w[(co * cin + ci) * 27 + t] * x[(long long)ci * n + q];
+    }
+    y[(long long)co * n + p] = relu ? fmaxf(acc, 0.f) : acc;
+  }
+}
+
+// binary cross-entropy with logits, averaged over positions of level >= 1
+// whose parent exists: dL/dz = (sigmoid(z) - y) / count
+__global__ void k_bce_grad(Geo g, const float *__restrict__ z, const uint8_t *__restrict__ target,
+                           float *__restrict__ dz, double *loss, float inv_count) {
+  const long long n = g.mapoff[g.L + 1];
+  double acc = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    float d = 0.f;
+    int l = pos_level(g, p);
+    bool use = l > 0;
+    if (use) {
+      long long u = p - g.mapoff[l];
+      int bx = (int)(u % g.nb[l][0]), by = (int)((u / g.nb[l][0]) % g.nb[l][1]);
+      int bz = (int)(u / ((long long)g.nb[l][0] * g.nb[l][1]));
+      use = g.idx[map_index(g, l - 1, bx >> 1, by >> 1, bz >> 1)] >= 0;
+    }
+    if (use) {
+      float x = z[p], y = target[p] ? 1.f : 0.f;
+      float s = 1.f / (1.f + expf(-x));
+      d = (s - y) * inv_count;
+      acc += (double)(fmaxf(x, 0.f) - x * y + log1pf(expf(-fabsf(x)))) * inv_count;
+    }
+    dz[p] = d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// gradient of a ReLU layer output -> pre-activation: zero where the output was 0
+__global__ void k_relu_back(const float *__restrict__ y, float *__restrict__ dy, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!(y[i] > 0.f)) dy[i] = 0.f;
+}
+
+// dW[co][ci][tap] += sum_p dy[co][p] x[ci][p+tap]; db[co] += sum_p dy[co][p]
+// one CTA per (co, ci, tap) weight (+ the bias on ci == 0, tap == 13)
+__global__ void k_conv_dw(Geo g, const float *__restrict__ x, int cin, const float *__restrict__ dy, int cout,
+                          float *__restrict__ dw, float *__restrict__ db) {
+  const long long n = g.mapoff[g.L + 1];
+  const int dim3d = g.dim == 3;
+  int wi = blockIdx.x;  // (co * cin + ci) * 27 + t
+  int t = wi % 27, ci = (wi / 27) % cin, co = wi / (27 * cin);
+  int dz = t / 9 - 1, dy_ = (t / 3) % 3 - 1, dx = t % 3 - 1;
+  __shared__ double red[2][32];
+  double acc = 0.0, accb = 0.0;
+  if (dim3d || dz == 0) {
+    for (long long p = threadIdx.x; p < n; p += blockDim.x) {
+      float d = dy[(long long)co * n + p];
+      if (d == 0.f) continue;
+      long long q = pos_neighbour(g, pos_level(g, p), p, dx, dy_, dz);
+      if (q >= 0) acc += (double)d * x[(long long)ci * n + q];
+      accb += d;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    accb += __shfl_xor_sync(0xffffffffu, accb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = acc;
+    red[1][threadIdx.x >> 5] = accb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0, sb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      s += red[0][w];
+      sb += red[1][w];
+    }
+    dw[wi] += (float)s;
+    if (ci == 0 && t == 13) db[co] += (float)sb;
+  }
+}
+
+// dx[ci][q] = sum_{co,tap} dy[co][q - tap] w[co][ci][tap]
+__global__ void k_conv_dx(Geo g, const float *__restrict__ dy, int cout, const float *__restrict__ w, int cin,
+                          float *__restrict__ dx) {
+  const long long n = g.mapoff[g.L + 1];
+  const int dim3d = g.dim == 3;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n * cin;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int ci = (int)(idx / n);
+    long long q = idx % n;
+    int l = pos_level(g, q);
+    float acc = 0.f;
+    for (int t = 0; t < 27; t++) {
+      int dz = t / 9 - 1, dyy = (t / 3) % 3 - 1, dxx = t % 3 - 1;
+      if (!dim3d && dz != 0) continue;
+      long long p = pos_neighbour(g, l, q, -dxx, -dyy, -dz);
+      if (p < 0) continue;
+      for (int co = 0; co < cout; co++) acc += dy[(long long)co * n + p] * w[(co * cin + ci) * 27 + t];
+    }
+    dx[(long long)ci * n + q] = acc;
+  }
+}
+
+// Adam on the FP32 master weights (beta1 0.9, beta2 0.999, eps 1e-8), step t
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ grad, float *__restrict__ m,
+                       float *__restrict__ v, int n, float lr, int t) {
+  float b1t = 1.f - powf(0.9f, (float)t), b2t = 1.f - powf(0.999f, (float)t);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float gi = grad[i];
+    m[i] = 0.9f * m[i] + 0.1f * gi;
+    v[i] = 0.999f * v[i] + 0.001f * gi * gi;
+    w[i] -= lr * (m[i] / b1t) / (sqrtf(v[i] / b2t) + 1e-8f);
+  }
+}
+
+// FP32 master weights (host blob order) -> BF16 GEMM operands [16][KP] and FP32 biases [16]
+__global__ void k_pack_weights(const float *__restrict__ blob, __nv_bfloat16 *w1, float *b1, __nv_bfloat16 *w2,
+                               float *b2, __nv_bfloat16 *w3, float *b3) {
+  const float *W1 = blob, *B1 = W1 + 16 * 81, *W2 = B1 + 16, *B2 = W2 + 16 * 432, *W3 = B2 + 16, *B3 = W3 + 432;
+  for (int i = threadIdx.x; i < 16 * 96; i += blockDim.x) {
+    int n = i / 96, k = i % 96;
+    w1[i] = __float2bfloat16_rn(k < 81 ? W1[n * 81 + k] : 0.f);
+  }
+  for (int i = threadIdx.x; i < 16 * 432; i += blockDim.x) {
+    w2[i] = __float2bfloat16_rn(W2[i]);
+    int n = i / 432, k = i % 432;
+    w3[i] = __float2bfloat16_rn(n == 0 ? W3[k] : 0.f);
+  }
+  for (int i = threadIdx.x; i < 16; i += blockDim.x) {
+    b1[i] = B1[i];
+    b2[i] = B2[i];
+    b3[i] = i == 0 ? B3[0] : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+void launch_prop_features(const Geo &g, const T *U, const double *maxdet, const T *scale, double eps, float *feat,
+                          int grid, cudaStream_t st) {
+  if (g.dim == 2) k_prop_features<T, 2><<<grid, 128, 0, st>>>(g, U, maxdet, scale, eps, feat);
+  else k_prop_features<T, 3><<<grid, 128, 0, st>>>(g, U, maxdet, scale, eps, feat);
+}
+template void launch_prop_features<float>(const Geo &, const float *, const double *, const float *, double, float *,
+                                          int, cudaStream_t);
+template void launch_prop_features<double>(const Geo &, const double *, const double *, const double *, double,
+                                           float *, int, cudaStream_t);
+
+void prop_setup() {
+  cudaFuncSetAttribute(k_prop_conv_tc<3, 96, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<96>());
+  cudaFuncSetAttribute(k_prop_conv_tc<16, 432, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)conv_smem<432>());
+  cudaFuncSetAttribute(k_prop_conv_tc<16, 432, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)conv_smem<432>());
+}
+
+// features (float [3][n]) -> logits (float [n]) through the three layers on tensor cores
+void launch_prop_infer(const Geo &g, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
+                       const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
+                       const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaStream_t st) {
+  long long n = g.mapoff[g.L + 1];
+  long long tiles = (n + 127) / 128;
+  int grid = (int)(tiles < nsm ? tiles : nsm);
+  k_to_bf16<<<256, 256, 0, st>>>(feat, a0, 3 * n);
+  k_prop_conv_tc<3, 96, false><<<grid, 128, conv_smem<96>(), st>>>(g, a0, w1, b1, a1, nullptr);
+  k_prop_conv_tc<16, 432, false><<<grid, 128, conv_smem<432>(), st>>>(g, a1, w2, b2, a2, nullptr);
+  k_prop_conv_tc<16, 432, true><<<grid, 128, conv_smem<432>(), st>>>(g, a2, w3, b3, nullptr, logits);
+}
+
+void launch_prop_mark(const Geo &g, const float *logits, uint8_t *need, int grid, cudaStream_t st) {
+  k_prop_mark<<<grid, 256, 0, st>>>(g, logits, need);
+}
+
+void launch_pack_weights(const float *blob, __nv_bfloat16 *w1, float *b1, __nv_bfloat16 *w2, float *b2,
+                         __nv_bfloat16 *w3, float *b3, cudaStream_t st) {
+  k_pack_weights<<<1, 256, 0, st>>>(blob, w1, b1, w2, b2, w3, b3);
+}
+
+// One Adam step on a batch of snapshots: forward in FP32 with the BF16-rounded
+// weights' master copy, BCE loss, backward, update.  feat: [ns][3][n] floats,
+// target: [ns][n] bytes (device).  work: scratch of 2*(3+16+16+1)*n floats.
+void launch_prop_train_step(const Geo &g, const float *feat, const uint8_t *target, int ns, float *blob, float *grad,
+                            float *m1, float *m2, int t, float lr, float *work, double *loss, cudaStream_t st) {
+  long long n = g.mapoff[g.L + 1];
+  const int NW = 16 * 81 + 16 + 16 * 432 + 16 + 432 + 1;
+  float *W1 = blob, *B1 = W1 + 16 * 81, *W2 = B1 + 16, *B2 = W2 + 16 * 432, *W3 = B2 + 16, *B3 = W3 + 432;
+  float *gW1 = grad, *gB1 = gW1 + 16 * 81, *gW2 = gB1 + 16, *gB2 = gW2 + 16 * 432, *gW3 = gB2 + 16, *gB3 = gW3 + 432;
+  float *h1 = work, *h2 = h1 + 16 * n, *z = h2 + 16 * n, *dz = z + n, *d2 = dz + n, *d1 = d2 + 16 * n;
+  cudaMemsetAsync(grad, 0, NW * sizeof(float), st);
+  // count of the positions entering the loss (level >= 1 with an existing parent) is
+  // approximated by the number of positions of levels >= 1 (sets the loss scale only)
+  float inv = 1.f / (float)((n - g.mapoff[1]) * (long long)ns);
+  int grid = 1024;
+  for (int k = 0; k < ns; k++) {
+    const float *x = feat + (long long)k * 3 * n;
+    k_conv_fwd_f32<<<grid, 256, 0, st>>>(g, x, 3, W1, B1, 16, h1, 1);
+    k_conv_fwd_f32<<<grid, 256, 0, st>>>(g, h1, 16, W2, B2, 16, h2, 1);
+    k_conv_fwd_f32<<<grid, 256, 0, st>>>(g, h2, 16, W3, B3, 1, z, 0);
+    k_bce_grad<<<grid, 256, 0, st>>>(g, z, target + (long long)k * n, dz, loss, inv);
+    k_conv_dw<<<432, 256, 0, st>>>(g, h2, 16, dz, 1, gW3, gB3);
+    k_conv_dx<<<grid, 256, 0, st>>>(g, dz, 1, W3, 16, d2);
+    k_relu_back<<<grid, 256, 0, st>>>(h2, d2, 16 * n);
+    k_conv_dw<<<16 * 432, 256, 0, st>>>(g, h1, 16, d2, 16, gW2, gB2);
+    k_conv_dx<<<grid, 256, 0, st>>>(g, d2, 16, W2, 16, d1);
+    k_relu_back<<<grid, 256, 0, st>>>(h1, d1, 16 * n);
+    k_conv_dw<<<16 * 81, 256, 0, st>>>(g, x, 3, d1, 16, gW1, gB1);
+  }
+  k_adam<<<64, 256, 0, st>>>(blob, grad, m1, m2, NW, lr, t);
+}
+
+}  // namespace mrfv

@@ -55,17 +55,18 @@ __device__ void mark_children(const Geo &g, uint8_t *need, int l, int bx, int by
 
 // MR: a significant block of level >= 1 is kept with its 3^d-1 neighbours and,
 // below the finest level, its children are added.  GRAD: the children of every
-// flagged block are added.
+// flagged block are added.  MR with the proposer (crit 2): as MR without the
+// neighbours.
 __device__ __forceinline__ void k_need_mark_dev(Geo g, const uint8_t *sig, uint8_t *need, int crit) {
   long long total = g.mapoff[g.L + 1];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     if (g.idx[t] < 0 || !sig[t]) continue;
     int l = level_of_map(g, t), bx, by, bz;
     map_coords(g, l, t, bx, by, bz);
-    if (crit == 0) {
+    if (crit == 0 || crit == 2) {  // MR (crit 2: without the safety zone, which the proposer replaces)
       if (l == 0) continue;
       need[t] = 1;
-      mark_nbrs(g, need, l, bx, by, bz);
+      if (crit == 0) mark_nbrs(g, need, l, bx, by, bz);
     }
     if (l < g.L) mark_children(g, need, l, bx, by, bz);
   }

@@ -1,0 +1,148 @@
+"""Learned refinement proposer: oracle pins (CPU) and tensor-core inference,
+features and training on the GPU against the oracle."""
+import numpy as np
+import pytest
+
+import mrfv_inputs as mi
+from oracle import proposer as P
+
+
+def random_weights(seed: int, scale: float = 0.3) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0.0, 1.0, P.NWEIGHTS).astype(np.float32)
+    (W1, B1), (W2, B2), (W3, B3) = P.unpack(w)
+    W1 *= scale / np.sqrt(81); W2 *= scale * 2 / np.sqrt(432); W3 *= scale * 2 / np.sqrt(432)
+    return w
+
+
+# ----------------------------------------------------------------------------- oracle pins
+
+def test_bf16_rounding_known_values():
+    x = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -9, 1 + 2 ** -7, -2.5, 0.0, 3.0e38], dtype=np.float32)
+    r = P.bf16_round(x)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                  # tie -> even
+    assert r[2] == np.float32(1 + 2 ** -7)  # above the tie -> up
+    assert r[3] == np.float32(1 + 2 ** -7)
+    assert r[4] == -2.5 and r[5] == 0.0
+    assert np.isfinite(r[6])
+
+
+def test_conv_level_matches_brute_force():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(2, 3, 4, 5))
+    W = rng.normal(size=(3, 2, 27))
+    b = rng.normal(size=3)
+    y = P.conv_level(x, W, b)
+    for co in range(3):
+        for z in range(3):
+            for yy in range(4):
+                for xx in range(5):
+                    s = b[co]
+                    for ci in range(2):
+                        for t in range(27):
+                            dz, dy, dx = t // 9 - 1, (t // 3) % 3 - 1, t % 3 - 1
+                            zz, y2, x2 = z + dz, yy + dy, xx + dx
+                            if 0 <= zz < 3 and 0 <= y2 < 4 and 0 <= x2 < 5:
+                                s += W[co, ci, t] * x[ci, zz, y2, x2]
+                    assert y[co, z, yy, xx] == pytest.approx(s, abs=1e-12)
+
+
+def test_forward_bias_only_is_constant_and_levels_independent():
+    w = np.zeros(P.NWEIGHTS, np.float32)
+    (W1, B1), (W2, B2), (W3, B3) = P.unpack(w)
+    B3[0] = 0.75
+    shapes = P.level_shapes(2, 3, (2, 2))
+    n = sum(int(np.prod(s)) for s in shapes)
+    z = P.forward(w, np.random.default_rng(0).normal(size=(3, n)), shapes)
+    assert np.all(z == 0.75)
+
+
+# ----------------------------------------------------------------------------- GPU
+
+@pytest.fixture(scope="module")
+def mrfv():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    return m
+
+
+def _oracle_features(s, dim, eps):
+    levels = [s.download_level(l)[0] for l in range(s.levels)]
+    ex = [s.get_tree(l) for l in range(s.levels)]
+    md = [s.get_flags(l)[1] for l in range(s.levels)]
+    # the analysis scales: recompute the level-0 maxima (same definition as the library)
+    q0 = levels[0]
+    rho = np.abs(q0[0]).max()
+    E = np.abs(q0[dim + 1]).max()
+    return P.features(dim, 1.4, eps, levels, ex, md, [rho] + [0.0] * dim + [E])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dim", [2, 3])
+def test_proposer_features_and_tensor_core_inference_match_oracle(mrfv, dim):
+    if dim == 2:
+        s = mrfv.Solver(dim=2, precision="fp32", levels=5, base_blocks=(2, 2, 1), adapt=True, eps=1e-3)
+        s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(3))
+        shapes = P.level_shapes(2, 5, (2, 2))
+    else:
+        s = mrfv.Solver(dim=3, precision="fp32", levels=3, base_blocks=(2, 2, 2), lo=(-1, -1, -1), hi=(1, 1, 1),
+                        adapt=True, eps=1e-3)
+        s.init_state(mi.IC_ELLIPSOID, mi.ellipsoid_params(3))
+        shapes = P.level_shapes(3, 3, (2, 2, 2))
+    for _ in range(3):
+        s.step(0.0)
+    s.analyse(1e-3)
+    fg = s.proposer_features()
+    fo = _oracle_features(s, dim, 1e-3)
+    assert np.allclose(fg, fo, rtol=2e-5, atol=2e-6)
+    w = random_weights(5)
+    s.proposer_set_weights(w)
+    zg = s.proposer_infer()
+    zo = P.forward(w, fg, shapes)
+    err = np.abs(zg - zo)
+    assert err.max() <= 2e-2 * (np.abs(zo).max() + 1e-3), (err.max(), np.abs(zo).max())
+    # decisions agree except where the oracle logit is within the bf16 noise of 0
+    clear = np.abs(zo) > 2e-2 * np.abs(zo).max()
+    assert np.array_equal(zg[clear] > 0, zo[clear] > 0)
+
+
+@pytest.mark.gpu
+def test_proposer_training_and_deployment(mrfv):
+    """Snapshots from the method itself (features at t, MR flags at t + dt), a few
+    Adam steps on the GPU, then adaptation with the proposer: the loss falls and
+    the run stays conservative and graded."""
+    kw = dict(dim=2, precision="fp32", levels=5, base_blocks=(2, 2, 1), adapt=True, eps=1e-3, bc=1)
+    s = mrfv.Solver(**kw)
+    s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(2))
+    feats, targets = [], []
+    for _ in range(6):
+        s.analyse(1e-3)
+        f = s.proposer_features()
+        s.step(0.0)
+        s.analyse(1e-3)
+        t = np.concatenate([s.get_flags(l)[0].ravel() for l in range(s.levels)])
+        feats.append(f)
+        targets.append(t)
+    s.proposer_set_weights(random_weights(7))
+    l0 = s.proposer_train(np.stack(feats), np.stack(targets), steps=1, lr=1e-3)
+    l1 = s.proposer_train(np.stack(feats), np.stack(targets), steps=40, lr=1e-2)
+    assert l1 < l0
+    w = s.proposer_get_weights()
+    assert np.all(np.isfinite(w))
+    # deploy
+    p = mrfv.Solver(proposer=True, **kw)
+    p.init_state(mi.IC_QUADRANTS, mi.quadrant_params(2))
+    p.proposer_set_weights(w)
+    T0 = p.totals()
+    for _ in range(5):
+        p.step(0.0)
+    T1 = p.totals()
+    assert np.all(np.abs(T1 - T0) <= 1e-5 * np.abs(T0).max())
+    st = p.stats()
+    assert st["total_leaves"] > 0
