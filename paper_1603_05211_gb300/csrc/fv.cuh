@@ -21,100 +21,150 @@
 namespace mrfv {
 
 
+// ---------------------------------------------------------------- lanes
+// The stage arithmetic is written once for a "lane" type L: a scalar (float,
+// double: one pencil per thread) or vf2 (two single-precision pencils per
+// thread in the packed FP32x2 instructions of sm_100+).  Branches are written as
+// selects of both sides, which gives the same values as the branches.
+struct vf2 {
+  float2 v;
+  __device__ __forceinline__ vf2() {}
+  __device__ __forceinline__ vf2(float a) : v(make_float2(a, a)) {}
+  __device__ __forceinline__ vf2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ explicit vf2(float2 x) : v(x) {}
+};
+struct mask2 {
+  bool x, y;
+};
+__device__ __forceinline__ vf2 operator+(vf2 a, vf2 b) { return vf2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ vf2 operator-(vf2 a, vf2 b) { return vf2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))); }
+__device__ __forceinline__ vf2 operator*(vf2 a, vf2 b) { return vf2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ vf2 operator/(vf2 a, vf2 b) { return vf2(a.v.x / b.v.x, a.v.y / b.v.y); }
+__device__ __forceinline__ mask2 operator>(vf2 a, vf2 b) { return {a.v.x > b.v.x, a.v.y > b.v.y}; }
+__device__ __forceinline__ mask2 operator>=(vf2 a, vf2 b) { return {a.v.x >= b.v.x, a.v.y >= b.v.y}; }
+__device__ __forceinline__ mask2 operator<(vf2 a, vf2 b) { return {a.v.x < b.v.x, a.v.y < b.v.y}; }
+__device__ __forceinline__ vf2 lsel(mask2 m, vf2 a, vf2 b) { return vf2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y); }
+__device__ __forceinline__ vf2 labs(vf2 a) { return vf2(fabsf(a.v.x), fabsf(a.v.y)); }
+__device__ __forceinline__ vf2 lsqrt(vf2 a) { return vf2(sqrtf(a.v.x), sqrtf(a.v.y)); }
+// a * b + c: fused for vf2; for scalars written as the product then the sum (the
+// double-precision unit is built without contraction, so it rounds both)
+__device__ __forceinline__ vf2 lfma(vf2 a, vf2 b, vf2 c) { return vf2(__ffma2_rn(a.v, b.v, c.v)); }
+
+template <typename L>
+__device__ __forceinline__ L lsel(bool m, L a, L b) { return m ? a : b; }
+__device__ __forceinline__ float labs(float a) { return fabsf(a); }
+__device__ __forceinline__ double labs(double a) { return fabs(a); }
+__device__ __forceinline__ float lsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double lsqrt(double a) { return sqrt(a); }
+template <typename L>
+__device__ __forceinline__ L lfma(L a, L b, L c) { return (a * b) + c; }
+
 // van Albada slope with the TVD clip: a b (a + b) / (a^2 + b^2) when a b > 0, else 0.
-template <typename T>
-__device__ __forceinline__ T van_albada(T a, T b) {
-  T ab = a * b;
-  if (ab > T(0)) return (ab * (a + b)) / ((a * a) + (b * b));
-  return T(0);
+template <typename L>
+__device__ __forceinline__ L van_albada(L a, L b) {
+  L ab = a * b;
+  L r = (ab * (a + b)) / lfma(a, a, b * b);
+  return lsel(ab > L(0.0f), r, L(0.0f));
 }
 
-// AUSM+ split Mach numbers (beta = 1/8) and pressures (alpha = 3/16), Liou 1996.
-template <typename T>
-__device__ __forceinline__ T mach4_plus(T M) {
-  if (fabs(M) >= T(1)) return T(0.5) * (M + fabs(M));
-  T t = M + T(1), u = (M * M) - T(1);
-  return (T(0.25) * (t * t)) + (T(0.125) * (u * u));
+// AUSM+ split Mach numbers (beta = 1/8) and pressures (alpha = 3/16), Liou 1996;
+// |M| >= 1 takes the supersonic form.
+template <typename L>
+__device__ __forceinline__ L mach4_plus(L M) {
+  L aM = labs(M);
+  L sup = L(0.5f) * (M + aM);
+  L t = M + L(1.0f), u = lfma(M, M, L(-1.0f));
+  L sub = lfma(L(0.25f), t * t, L(0.125f) * (u * u));
+  return lsel(aM >= L(1.0f), sup, sub);
 }
-template <typename T>
-__device__ __forceinline__ T mach4_minus(T M) {
-  if (fabs(M) >= T(1)) return T(0.5) * (M - fabs(M));
-  T t = M - T(1), u = (M * M) - T(1);
-  return (T(-0.25) * (t * t)) - (T(0.125) * (u * u));
+template <typename L>
+__device__ __forceinline__ L mach4_minus(L M) {
+  L aM = labs(M);
+  L sup = L(0.5f) * (M - aM);
+  L t = M - L(1.0f), u = lfma(M, M, L(-1.0f));
+  L sub = (L(-0.25f) * (t * t)) - (L(0.125f) * (u * u));
+  return lsel(aM >= L(1.0f), sup, sub);
 }
-template <typename T>
-__device__ __forceinline__ T pres5_plus(T M) {
-  if (fabs(M) >= T(1)) return M > T(0) ? T(1) : T(0);
-  T t = M + T(1), u = (M * M) - T(1);
-  return ((T(0.25) * (t * t)) * (T(2) - M)) + ((T(0.1875) * M) * (u * u));
+template <typename L>
+__device__ __forceinline__ L pres5_plus(L M) {
+  L aM = labs(M);
+  L sup = lsel(M > L(0.0f), L(1.0f), L(0.0f));
+  L t = M + L(1.0f), u = lfma(M, M, L(-1.0f));
+  L sub = lfma((L(0.25f) * (t * t)), (L(2.0f) - M), (L(0.1875f) * M) * (u * u));
+  return lsel(aM >= L(1.0f), sup, sub);
 }
-template <typename T>
-__device__ __forceinline__ T pres5_minus(T M) {
-  if (fabs(M) >= T(1)) return M < T(0) ? T(1) : T(0);
-  T t = M - T(1), u = (M * M) - T(1);
-  return ((T(0.25) * (t * t)) * (T(2) + M)) - ((T(0.1875) * M) * (u * u));
+template <typename L>
+__device__ __forceinline__ L pres5_minus(L M) {
+  L aM = labs(M);
+  L sup = lsel(M < L(0.0f), L(1.0f), L(0.0f));
+  L t = M - L(1.0f), u = lfma(M, M, L(-1.0f));
+  L sub = ((L(0.25f) * (t * t)) * (L(2.0f) + M)) - ((L(0.1875f) * M) * (u * u));
+  return lsel(aM >= L(1.0f), sup, sub);
 }
 
 // AUSM+ flux across a face with normal n from primitive face states
 // (rho, v_1..v_D, p); interface sound speed = arithmetic mean.
-template <typename T, int D>
-__device__ __forceinline__ void ausm_plus(int n, const T *wl, const T *wr, T g, T goverg1, T *F) {
-  T cl = sqrt((g * wl[D + 1]) / wl[0]);
-  T cr = sqrt((g * wr[D + 1]) / wr[0]);
-  T ch = T(0.5) * (cl + cr);
-  T ml = wl[1 + n] / ch;
-  T mr = wr[1 + n] / ch;
-  T m = mach4_plus(ml) + mach4_minus(mr);
-  T ph = (pres5_plus(ml) * wl[D + 1]) + (pres5_minus(mr) * wr[D + 1]);
-  T a = ch * m;
-  const T *wu = (m >= T(0)) ? wl : wr;
-  T vv = (wu[1] * wu[1]) + (wu[2] * wu[2]);
-  if (D == 3) vv = vv + (wu[3] * wu[3]);
-  T rhoH = (goverg1 * wu[D + 1]) + ((T(0.5) * wu[0]) * vv);
-  T fr = a * wu[0];
+template <typename L, int D>
+__device__ __forceinline__ void ausm_plus(int n, const L *wl, const L *wr, L g, L goverg1, L *F) {
+  L cl = lsqrt((g * wl[D + 1]) / wl[0]);
+  L cr = lsqrt((g * wr[D + 1]) / wr[0]);
+  L ch = L(0.5f) * (cl + cr);
+  L ml = wl[1 + n] / ch;
+  L mr = wr[1 + n] / ch;
+  L m = mach4_plus(ml) + mach4_minus(mr);
+  L ph = lfma(pres5_plus(ml), wl[D + 1], pres5_minus(mr) * wr[D + 1]);
+  L a = ch * m;
+  const auto up = m >= L(0.0f);
+  L wu[D + 2];
+#pragma unroll
+  for (int v = 0; v < D + 2; v++) wu[v] = lsel(up, wl[v], wr[v]);
+  L vv = lfma(wu[1], wu[1], wu[2] * wu[2]);
+  if (D == 3) vv = lfma(wu[3], wu[3], vv);
+  L rhoH = lfma(goverg1, wu[D + 1], (L(0.5f) * wu[0]) * vv);
+  L fr = a * wu[0];
   F[0] = fr;
 #pragma unroll
-  for (int d = 0; d < D; d++) {
-    T f = fr * wu[1 + d];
-    if (d == n) f = f + ph;
-    F[1 + d] = f;
-  }
+  for (int d = 0; d < D; d++) F[1 + d] = (d == n) ? lfma(fr, wu[1 + d], ph) : fr * wu[1 + d];
   F[D + 1] = a * rhoH;
 }
 
-template <typename T, int D>
-__device__ __forceinline__ void cons_to_prim(const T *Q, T gm1, T *w) {
-  T rho = Q[0];
-  T v[3] = {T(0), T(0), T(0)};
+template <typename L, int D>
+__device__ __forceinline__ void cons_to_prim(const L *Q, L gm1, L *w) {
+  L rho = Q[0];
+  L v[3] = {L(0.0f), L(0.0f), L(0.0f)};
 #pragma unroll
   for (int d = 0; d < D; d++) v[d] = Q[1 + d] / rho;
-  T vv = (v[0] * v[0]) + (v[1] * v[1]);
-  if (D == 3) vv = vv + (v[2] * v[2]);
+  L vv = lfma(v[0], v[0], v[1] * v[1]);
+  if (D == 3) vv = lfma(v[2], v[2], vv);
   w[0] = rho;
 #pragma unroll
   for (int d = 0; d < D; d++) w[1 + d] = v[d];
-  w[D + 1] = gm1 * (Q[D + 1] - ((T(0.5) * rho) * vv));
+  w[D + 1] = gm1 * (Q[D + 1] - ((L(0.5f) * rho) * vv));
 }
 
-#ifndef MRFV_FV_BPC2
-#define MRFV_FV_BPC2 16
+// Launch shape of the stage kernel for state type T in dimension D: P pencils per
+// thread, BPC blocks per CTA.  Two single-precision pencils per thread in packed
+// FP32x2 lanes (MRFV_FV_PPT32=1) measured slower on GB300 than one pencil per
+// thread (fewer warps to hide latency), so one is the default.
+#ifndef MRFV_FV_PPT32
+#define MRFV_FV_PPT32 0
 #endif
-template <int D>
+template <typename T, int D>
 struct FVShape {
   static constexpr int B = (D == 2) ? 64 : 512;        // interior cells
   static constexpr int TF = (D == 2) ? 8 : 64;         // cells of one face layer = pencils per direction
   static constexpr int NV = D + 2;
   static constexpr int STRIP = 2 * D * 2 * TF;         // ghost cells (two layers per face)
-  static constexpr int BPC = (D == 2) ? MRFV_FV_BPC2 : 1;  // blocks per CTA
-  static constexpr int NPEN = D * TF;                  // pencils per block
-  static constexpr int NT = NPEN * BPC;                // threads per CTA (one pencil each)
+  static constexpr int P = MRFV_FV_PPT32 && sizeof(T) == 4 ? 2 : 1;  // pencils per thread
+  static constexpr int BPC = (D == 2) ? (P == 2 ? 32 : 16) : (P == 2 ? 2 : 1);  // blocks per CTA
+  static constexpr int TPD = TF / P;                   // threads per block and direction
+  static constexpr int NT = D * TPD * BPC;             // threads per CTA
   static constexpr int PY = (D == 2) ? 9 : 8;          // padded shared-memory cell index x + PY y + PZ z
   static constexpr int PZ = (D == 2) ? 0 : 69;         // (bank-conflict free pencil stores in 2D, 2-way in 3D)
   static constexpr int RS = (D == 2) ? 74 : 552;       // padded cells per (block, variable) in shared memory
 };
 
-// CTAs per SM the register allocation must allow (single precision: 4, the
-// double-precision parity mode: 2); overridable at build time for tuning.
+// CTAs per SM the register allocation must allow (overridable for tuning)
 #ifndef MRFV_FV_MINB32
 #define MRFV_FV_MINB32 4
 #endif
@@ -135,23 +185,37 @@ __device__ __forceinline__ T lev_at(const FVArgs<T> &a, int i) {
 
 template <typename T, int D>
 constexpr size_t fv_smem_bytes() {
-  using S = FVShape<D>;
+  using S = FVShape<T, D>;
   return (size_t)D * S::BPC * S::NV * S::RS * sizeof(T);
 }
 
-// Conservative state of pencil position p (-2..9) of the pencil (n, tangential t)
+template <typename T, int P>
+struct Lane;
+template <typename T>
+struct Lane<T, 1> {
+  using type = T;
+};
+template <>
+struct Lane<float, 2> {
+  using type = vf2;
+};
+
+// Conservative state of pencil position p (-2..9) of the P pencils (n, t0 .. t0+P-1)
 // of block s: own cells, the same-level neighbour's cells, the ghost strip, or the
 // block's own edge cell at a transmissive wall.
-template <typename T, int D>
+template <typename T, int D, int P>
 __device__ __forceinline__ void pencil_load(const Geo &g, const T *__restrict__ U, const T *__restrict__ G, int s,
-                                            int n, int t, int nb_lo, int nb_hi, int p, T *Q) {
-  using S = FVShape<D>;
+                                            int n, int t0, int nb_lo, int nb_hi, int p,
+                                            typename Lane<T, P>::type *Q) {
+  using S = FVShape<T, D>;
   constexpr int B = S::B, TF = S::TF, NV = S::NV;
   const long long cap = g.cap;
   const int stride = (n == 0) ? 1 : (n == 1 ? 8 : 64);
-  // cell index of tangential position t with coordinate 0 along n
-  const int t1 = t & 7, t2 = t >> 3;
+  const int t1 = t0 & 7, t2 = t0 >> 3;
+  // cell index of tangential position t0 with coordinate 0 along n; the next
+  // pencil of the thread is one cell further in the first tangential direction
   const int base = (n == 0) ? (8 * t1 + 64 * t2) : (n == 1 ? (t1 + 64 * t2) : (t1 + 8 * t2));
+  const int tstep = (n == 0) ? 8 : 1;
   int from = s, c;
   if (p >= 0 && p <= 7) {
     c = base + p * stride;
@@ -160,9 +224,13 @@ __device__ __forceinline__ void pencil_load(const Geo &g, const T *__restrict__ 
     const int dd = side ? p - 8 : -1 - p;  // 0 touches the block
     const int nb = side ? nb_hi : nb_lo;
     if (nb == NBR_MISSING) {
-      const int q = (2 * n + side) * 2 * TF + dd * TF + t;
+      const T *Gp = G + (long long)s * S::STRIP + (2 * n + side) * 2 * TF + dd * TF + t0;
 #pragma unroll
-      for (int v = 0; v < NV; v++) Q[v] = G[((long long)v * cap + s) * S::STRIP + q];
+      for (int v = 0; v < NV; v++) {
+        const T *q = Gp + (long long)v * cap * S::STRIP;
+        if constexpr (P == 2) Q[v] = vf2(*reinterpret_cast<const float2 *>(q));
+        else Q[v] = q[0];
+      }
       return;
     }
     if (nb >= 0) {
@@ -172,30 +240,40 @@ __device__ __forceinline__ void pencil_load(const Geo &g, const T *__restrict__ 
       c = base + (side ? 7 : 0) * stride;
     }
   }
+  const T *Up = U + (long long)from * B + c;
 #pragma unroll
-  for (int v = 0; v < NV; v++) Q[v] = U[((long long)v * cap + from) * B + c];
+  for (int v = 0; v < NV; v++) {
+    const T *q = Up + (long long)v * cap * B;
+    if constexpr (P == 2) {
+      if (tstep == 1) Q[v] = vf2(*reinterpret_cast<const float2 *>(q));
+      else Q[v] = vf2(q[0], q[8]);
+    } else {
+      Q[v] = q[0];
+    }
+  }
 }
 
-// One thread per pencil: the 12 cells of a line along direction n (two beyond
-// each face of the block) are converted to primitives once; a sliding window then
-// forms the limited slope of each cell, the two face states and the AUSM+ flux of
-// each of the 9 faces, and stores the flux difference F_{k+1} - F_k of every
-// interior cell in shared memory.  A second pass applies
+// One thread per group of P pencils: the 12 cells of a line along direction n (two
+// beyond each face of the block) are converted to primitives in a sliding window;
+// each cell's limited slope is formed once, then the two face states and the
+// AUSM+ flux of each of the 9 faces, and the flux difference F_{k+1} - F_k of every
+// interior cell goes to shared memory.  A second pass applies
 // Q_out = Q_0 - (lambda_1 dF_1 + lambda_2 dF_2 [+ lambda_3 dF_3]), summed in
 // direction order, to every cell.
 template <typename T, int D>
-__global__ void __launch_bounds__(FVShape<D>::NT, FVMinBlocks<T>::value) k_fv(Geo g, FVArgs<T> a) {
-  using S = FVShape<D>;
-  constexpr int B = S::B, TF = S::TF, NV = S::NV, BPC = S::BPC, RS = S::RS, NT = S::NT;
+__global__ void __launch_bounds__(FVShape<T, D>::NT, FVMinBlocks<T>::value) k_fv(Geo g, FVArgs<T> a) {
+  using S = FVShape<T, D>;
+  constexpr int B = S::B, TF = S::TF, NV = S::NV, BPC = S::BPC, RS = S::RS, NT = S::NT, P = S::P, TPD = S::TPD;
+  using L = typename Lane<T, P>::type;
   extern __shared__ unsigned char smem_raw[];
   T *dFs = reinterpret_cast<T *>(smem_raw);  // [dir][block][v][RS]
   const long long cap = g.cap;
-  const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
+  const L gam = L(T(g.gamma)), gm1 = L(T(g.gamma - 1.0)), goverg1 = L(T(g.gamma / (g.gamma - 1.0)));
   const int stage = a.stage;
-  // pencil of this thread: direction-major so a warp shares one direction
-  const int n = threadIdx.x / (TF * BPC);
-  const int j = (threadIdx.x / TF) % BPC;
-  const int t = threadIdx.x % TF;
+  // pencil group of this thread: direction-major so a warp shares one direction
+  const int n = threadIdx.x / (TPD * BPC);
+  const int j = (threadIdx.x / TPD) % BPC;
+  const int t0 = (threadIdx.x % TPD) * P;
   int lb, le;
   list_range(g, a.kind, a.l0, a.l1, lb, le);
   if (a.bytes && blockIdx.x == 0 && threadIdx.x == 0)
@@ -214,59 +292,71 @@ __global__ void __launch_bounds__(FVShape<D>::NT, FVMinBlocks<T>::value) k_fv(Ge
         const bool add_lo = a.record == 2 && nb_lo == NBR_MISSING;
         const bool add_hi = a.record == 2 && nb_hi == NBR_MISSING;
         const T dtT = lev_at(a, lev_index(stage, l, 3));
-        // padded shared-memory index of this pencil's position 0 and the stride along n
-        const int t1 = t & 7, t2 = t >> 3;
+        // padded shared-memory index of the first pencil's position 0, stride along n,
+        // step to the next pencil of the thread
+        const int t1 = t0 & 7, t2 = t0 >> 3;
         const int base = (n == 0) ? (S::PY * t1 + S::PZ * t2) : (n == 1 ? (t1 + S::PZ * t2) : (t1 + S::PY * t2));
         const int stride = (n == 0) ? 1 : (n == 1 ? S::PY : S::PZ);
+        const int pstep = (n == 0) ? S::PY : 1;
         T *dF = dFs + ((size_t)(n * BPC + j) * NV) * RS;
         // sliding window of primitives: wb = cell k-1, wc = cell k (face k lies between them)
-        T wb[NV], wc[NV], slo[NV], Fprev[NV];
+        L wb[NV], wc[NV], slo[NV], Fprev[NV];
         {
-          T Q[NV], wa[NV];
-          pencil_load<T, D>(g, a.Uin, a.G, s, n, t, nb_lo, nb_hi, -2, Q);
-          cons_to_prim<T, D>(Q, gm1, wa);
-          pencil_load<T, D>(g, a.Uin, a.G, s, n, t, nb_lo, nb_hi, -1, Q);
-          cons_to_prim<T, D>(Q, gm1, wb);
-          pencil_load<T, D>(g, a.Uin, a.G, s, n, t, nb_lo, nb_hi, 0, Q);
-          cons_to_prim<T, D>(Q, gm1, wc);
+          L Q[NV], wa[NV];
+          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, -2, Q);
+          cons_to_prim<L, D>(Q, gm1, wa);
+          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, -1, Q);
+          cons_to_prim<L, D>(Q, gm1, wb);
+          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, 0, Q);
+          cons_to_prim<L, D>(Q, gm1, wc);
           // slope of cell -1
 #pragma unroll
-          for (int v = 0; v < NV; v++) slo[v] = van_albada<T>(wb[v] - wa[v], wc[v] - wb[v]);
+          for (int v = 0; v < NV; v++) slo[v] = van_albada<L>(wb[v] - wa[v], wc[v] - wb[v]);
         }
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-          T wd[NV], wl[NV], wr[NV], shi[NV], F[NV];
+          L wd[NV], wl[NV], wr[NV], shi[NV], F[NV];
           {
-            T Q[NV];
-            pencil_load<T, D>(g, a.Uin, a.G, s, n, t, nb_lo, nb_hi, k + 1, Q);
-            cons_to_prim<T, D>(Q, gm1, wd);
+            L Q[NV];
+            pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, k + 1, Q);
+            cons_to_prim<L, D>(Q, gm1, wd);
           }
 #pragma unroll
           for (int v = 0; v < NV; v++) {
-            shi[v] = van_albada<T>(wc[v] - wb[v], wd[v] - wc[v]);
-            wl[v] = wb[v] + T(0.5) * slo[v];
-            wr[v] = wc[v] - T(0.5) * shi[v];
+            shi[v] = van_albada<L>(wc[v] - wb[v], wd[v] - wc[v]);
+            wl[v] = lfma(L(T(0.5)), slo[v], wb[v]);
+            wr[v] = wc[v] - L(T(0.5)) * shi[v];
           }
-          ausm_plus<T, D>(n, wl, wr, gam, goverg1, F);
-          if (k == 0 && rec_lo) {
+          ausm_plus<L, D>(n, wl, wr, gam, goverg1, F);
+          if ((k == 0 && rec_lo) || (k == 8 && rec_hi)) {
+            const int side = k == 8 ? 1 : 0;
+            const bool add = side ? add_hi : add_lo;
 #pragma unroll
             for (int v = 0; v < NV; v++) {
-              T *R = a.FR + ((long long)v * cap + s) * (2 * D * TF) + (2 * n) * TF + t;
-              T val = dtT * F[v];
-              *R = add_lo ? *R + val : val;
-            }
-          }
-          if (k == 8 && rec_hi) {
-#pragma unroll
-            for (int v = 0; v < NV; v++) {
-              T *R = a.FR + ((long long)v * cap + s) * (2 * D * TF) + (2 * n + 1) * TF + t;
-              T val = dtT * F[v];
-              *R = add_hi ? *R + val : val;
+              T *R = a.FR + ((long long)v * cap + s) * (2 * D * TF) + (2 * n + side) * TF + t0;
+              if constexpr (P == 2) {
+                float2 val = __fmul2_rn(make_float2(dtT, dtT), F[v].v);
+                float2 *R2 = reinterpret_cast<float2 *>(R);
+                if (add) val = __fadd2_rn(*R2, val);
+                *R2 = val;
+              } else {
+                T val = dtT * F[v];
+                *R = add ? *R + val : val;
+              }
             }
           }
           if (k > 0) {
 #pragma unroll
-            for (int v = 0; v < NV; v++) dF[v * RS + base + (k - 1) * stride] = F[v] - Fprev[v];
+            for (int v = 0; v < NV; v++) {
+              L d = F[v] - Fprev[v];
+              T *dst = dF + v * RS + base + (k - 1) * stride;
+              if constexpr (P == 2) {
+                dst[0] = d.v.x;
+                dst[pstep] = d.v.y;
+              } else {
+                dst[0] = d;
+              }
+            }
           }
 #pragma unroll
           for (int v = 0; v < NV; v++) {

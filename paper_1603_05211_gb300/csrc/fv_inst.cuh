@@ -10,10 +10,10 @@ template <typename T>
 void launch_fv(const Geo &g, const FVArgs<T> &a, int grid, cudaStream_t st) {
   if (g.dim == 2) {
     constexpr size_t sm = fv_smem_bytes<T, 2>();
-    k_fv<T, 2><<<grid, FVShape<2>::NT, sm, st>>>(g, a);
+    k_fv<T, 2><<<grid, FVShape<T, 2>::NT, sm, st>>>(g, a);
   } else {
     constexpr size_t sm = fv_smem_bytes<T, 3>();
-    k_fv<T, 3><<<grid, FVShape<3>::NT, sm, st>>>(g, a);
+    k_fv<T, 3><<<grid, FVShape<T, 3>::NT, sm, st>>>(g, a);
   }
 }
 
@@ -25,11 +25,11 @@ int fv_ctas_per_sm(int dim) {
   if (dim == 2) {
     constexpr size_t sm = fv_smem_bytes<T, 2>();
     cudaFuncSetAttribute(k_fv<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, 2>, FVShape<2>::NT, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, 2>, FVShape<T, 2>::NT, sm);
   } else {
     constexpr size_t sm = fv_smem_bytes<T, 3>();
     cudaFuncSetAttribute(k_fv<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, 3>, FVShape<3>::NT, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, 3>, FVShape<T, 3>::NT, sm);
   }
   return n > 0 ? n : 1;
 }
