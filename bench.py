@@ -140,6 +140,229 @@ def uniform_roofline(m, torch, hbm_peak, steps=6):
     return out
 
 
+def timed_steps(s, n: int, torch, stream) -> float:
+    """GPU time (ms) of n asynchronous steps, CUDA events on the solver's stream."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(n):
+        s.step(0.0, sync=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def count_steps_to_end(make, t_end: float) -> int:
+    s = make()
+    n = 0
+    while True:
+        dt = s.step(0.0, sync=True)
+        n += 1
+        if dt <= 0.0 or s.stats()["t"] >= t_end * (1 - 1e-12):
+            break
+    s.close()
+    return n
+
+
+def matched_l1_2d(m, torch, stream, t_end=0.25):
+    """Adaptive MR (8 levels, 1024^2 finest) vs the uniform 1024^2 solve, both to
+    t_end, each L1(rho) measured against a uniform 2048^2 solve restricted to
+    1024^2 (Section 3); GPU time of each (CUDA events, steps counted beforehand)."""
+    import numpy as np
+
+    P = mi.quadrant_params(SEED)
+
+    def uniform(n):
+        s = m.Solver(dim=2, precision="fp32", levels=1, base_blocks=(n // 8, n // 8, 1), cfl=0.5, t_end=t_end,
+                     stream=stream)
+        s.init_state(mi.IC_QUADRANTS, P)
+        return s
+
+    def adaptive():
+        s = m.Solver(dim=2, precision="fp32", levels=8, base_blocks=(1, 1, 1), adapt=True, eps=WL["eps"], cfl=0.5,
+                     t_end=t_end, stream=stream)
+        s.init_state(mi.IC_QUADRANTS, P)
+        return s
+
+    # reference 2048^2, restricted to 1024^2
+    nref = count_steps_to_end(lambda: uniform(2048), t_end)
+    r = uniform(2048)
+    for _ in range(nref):
+        r.step(0.0, sync=False)
+    rho = r.download_level(0)[0][0]
+    r.close()
+    ref = rho.reshape(1024, 2, 1024, 2).mean(axis=(1, 3))
+    h2 = (1.0 / 1024) ** 2
+    out = {"t_end": t_end, "reference": "uniform 2048^2 FP32 restricted to 1024^2", "reference_steps": nref}
+    # uniform fine
+    nu = count_steps_to_end(lambda: uniform(1024), t_end)
+    u = uniform(1024)
+    ms_u = timed_steps(u, nu, torch, stream)
+    l1_u = float(np.abs(u.download_level(0)[0][0] - ref).sum() * h2)
+    u.close()
+    # adaptive
+    na = count_steps_to_end(adaptive, t_end)
+    a = adaptive()
+    st0 = a.stats()
+    ms_a = timed_steps(a, na, torch, stream)
+    st1 = a.stats()
+    l1_a = float(np.abs(a.project_finest()[0] - ref).sum() * h2)
+    a.close()
+    leaves = (st1["cell_updates"] - st0["cell_updates"]) / max(1, na)
+    out.update({
+        "uniform_fine": {"steps": nu, "gpu_ms": ms_u, "l1_rho": l1_u},
+        "adaptive": {"steps": na, "gpu_ms": ms_a, "l1_rho": l1_a, "mean_leaf_cells": leaves,
+                     "mesh_compression": leaves / 1024 ** 2},
+        "accuracy_perturbation": abs(l1_u - l1_a) / l1_u,
+        "matched": abs(l1_u - l1_a) / l1_u <= 0.05,
+        "time_ratio_adaptive_over_uniform": ms_a / ms_u,
+        "overhead_per_leaf": (ms_a / max(1.0, leaves * na)) / (ms_u / (1024 ** 2 * nu)) - 1.0,
+    })
+    return out
+
+
+def blast3d(m, stream, levels, t_end, proposer=False, eps=1e-3):
+    s = m.Solver(dim=3, precision="fp32", levels=levels, base_blocks=(2, 2, 2), lo=(-1, -1, -1), hi=(1, 1, 1),
+                 adapt=levels > 1, eps=eps, cfl=0.5, t_end=t_end, stream=stream, proposer=proposer)
+    s.init_state(mi.IC_ELLIPSOID, mi.ellipsoid_params(SEED))
+    return s
+
+
+def uniform3d(m, stream, n, t_end):
+    s = m.Solver(dim=3, precision="fp32", levels=1, base_blocks=(n // 8,) * 3, lo=(-1, -1, -1), hi=(1, 1, 1),
+                 cfl=0.5, t_end=t_end, stream=stream)
+    s.init_state(mi.IC_ELLIPSOID, mi.ellipsoid_params(SEED))
+    return s
+
+
+def proposer_snapshots(m, stream, levels, t_end, nsnap):
+    """(features at t, MR flags at t + dt) pairs from the method's own run."""
+    import numpy as np
+
+    s = blast3d(m, stream, levels, t_end)
+    feats, targets = [], []
+    for _ in range(nsnap):
+        s.analyse(WL["eps"])
+        f = s.proposer_features()
+        s.step(0.0, sync=True)
+        s.analyse(WL["eps"])
+        feats.append(f)
+        targets.append(np.concatenate([s.get_flags(l)[0].ravel() for l in range(s.levels)]))
+    s.close()
+    return np.stack(feats), np.stack(targets)
+
+
+def proposer_miss_rate(m, stream, levels, t_end, w, nsteps):
+    """Run the plain MR heuristic; at every step compare the proposer's positive
+    blocks (plus the blocks the MR rule keeps without its safety zone) with the
+    blocks found significant one step later.  miss = significant later but not
+    proposed / significant later."""
+    import numpy as np
+
+    s = blast3d(m, stream, levels, t_end)
+    s.proposer_set_weights(w)
+    miss = tot = prop = 0
+    for _ in range(nsteps):
+        s.analyse(WL["eps"])
+        z = s.proposer_infer()
+        sig = np.concatenate([s.get_flags(l)[0].ravel() for l in range(s.levels)]).astype(bool)
+        ex = np.concatenate([s.get_tree(l).ravel() for l in range(s.levels)]).astype(bool)
+        keep = sig.copy()
+        # children of significant blocks (refinement by one level) are kept too
+        off = 0
+        offs = []
+        for l in range(s.levels):
+            offs.append(off)
+            off += int(np.prod(s.blocks_shape(l)))
+        for l in range(s.levels - 1):
+            sh = s.blocks_shape(l)
+            sl = sig[offs[l]:offs[l] + int(np.prod(sh))].reshape(sh)
+            ch = np.kron(sl, np.ones((2, 2, 2), bool))
+            keep[offs[l + 1]:offs[l + 1] + ch.size] |= ch.ravel()
+        proposed = (z > 0) | keep
+        s.step(0.0, sync=True)
+        s.analyse(WL["eps"])
+        sig1 = np.concatenate([s.get_flags(l)[0].ravel() for l in range(s.levels)]).astype(bool)
+        miss += int((sig1 & ~proposed).sum())
+        tot += int(sig1.sum())
+        prop += int(((z > 0) & ~ex).sum())
+    s.close()
+    return {"miss_rate": miss / max(1, tot), "significant_blocks": tot, "steps": nsteps,
+            "proposed_new_blocks_per_step": prop / max(1, nsteps)}
+
+
+def run_matched3d(args):
+    """3D ellipsoidal blast: adaptive MR (heuristic and learned proposer) against the
+    uniform solve on the finest grid, both to t_end, L1(rho) against a uniform solve
+    at twice the finest resolution restricted to it; GPU time of each."""
+    import numpy as np
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    L = args.levels3d
+    nfin = 16 << (L - 1)
+    t_end = args.t_end3d
+    h3 = (2.0 / nfin) ** 3
+    out = {"case": f"blast3d_fp32_L{L - 1}", "finest": nfin, "t_end": t_end, "eps": WL["eps"]}
+    nref = count_steps_to_end(lambda: uniform3d(m, stream, 2 * nfin, t_end), t_end)
+    r = uniform3d(m, stream, 2 * nfin, t_end)
+    for _ in range(nref):
+        r.step(0.0, sync=False)
+    rho = r.download_level(0)[0][0]
+    r.close()
+    torch.cuda.empty_cache()
+    ref = rho.reshape(nfin, 2, nfin, 2, nfin, 2).mean(axis=(1, 3, 5))
+    del rho
+    out["reference"] = {"grid": 2 * nfin, "steps": nref}
+    nu = count_steps_to_end(lambda: uniform3d(m, stream, nfin, t_end), t_end)
+    u = uniform3d(m, stream, nfin, t_end)
+    ms_u = timed_steps(u, nu, torch, stream)
+    l1_u = float(np.abs(u.download_level(0)[0][0] - ref).sum() * h3)
+    u.close()
+    torch.cuda.empty_cache()
+    out["uniform_fine"] = {"steps": nu, "gpu_ms": ms_u, "l1_rho": l1_u}
+    # learned proposer: trained on snapshots of a coarser run (one level less)
+    feats, targets = proposer_snapshots(m, stream, L - 1, t_end, args.snapshots)
+    tr = blast3d(m, stream, L - 1, t_end)
+    rng = np.random.default_rng(0)
+    w0 = (rng.normal(0, 1, m.PROPOSER_NWEIGHTS) * 0.05).astype(np.float32)
+    tr.proposer_set_weights(w0)
+    t0 = time.perf_counter()
+    loss0 = tr.proposer_train(feats, targets, steps=1, lr=3e-3)
+    loss1 = tr.proposer_train(feats, targets, steps=args.train_steps, lr=3e-3)
+    train_s = time.perf_counter() - t0
+    w = tr.proposer_get_weights()
+    tr.close()
+    out["proposer_training"] = {"snapshots": int(feats.shape[0]), "levels": L - 1, "adam_steps": args.train_steps,
+                                "loss_first": loss0, "loss_last": loss1, "seconds": train_s}
+    out["proposer_eval"] = proposer_miss_rate(m, stream, L, t_end, w, min(args.snapshots, 40))
+    for name, prop in (("adaptive", False), ("adaptive_proposer", True)):
+        def mk2(p=prop):
+            s = blast3d(m, stream, L, t_end, proposer=p)
+            if p:
+                s.proposer_set_weights(w)
+            return s
+
+        na = count_steps_to_end(mk2, t_end)
+        a = mk2()
+        st0 = a.stats()
+        ms_a = timed_steps(a, na, torch, stream)
+        st1 = a.stats()
+        l1_a = float(np.abs(a.project_finest()[0] - ref).sum() * h3)
+        a.close()
+        torch.cuda.empty_cache()
+        leaves = (st1["cell_updates"] - st0["cell_updates"]) / max(1, na)
+        out[name] = {"steps": na, "gpu_ms": ms_a, "l1_rho": l1_a, "mean_leaf_cells": leaves,
+                     "mesh_compression": leaves / nfin ** 3,
+                     "accuracy_perturbation": abs(l1_u - l1_a) / l1_u,
+                     "time_ratio_over_uniform": ms_a / ms_u}
+    print(json.dumps(out), flush=True)
+
+
 def oracle_sample(budget_s: float, max_steps: int = 50):
     """Oracle (FP64 C, one host thread) on the same workload from t = 0."""
     import oracle
@@ -271,6 +494,10 @@ def run_ours(args):
             roof_u = {"error": str(e)}
         # end to end through the C interface: host initial state in, host state out
         e2e = run_e2e(m, torch, stream, args.steps)
+        try:
+            matched = matched_l1_2d(m, torch, stream)
+        except Exception as e:  # noqa: BLE001
+            matched = {"error": str(e)}
         # CPU baseline: the oracle on a bounded sample of the same workload
         ob, osteps, osec = oracle_sample(budget_s=float(os.environ.get("MRFV_ORACLE_BUDGET", "15")))
         result = {
@@ -286,6 +513,7 @@ def run_ours(args):
             "cpu_baseline": {"value": ob, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                              "sample": f"{osteps} FP64 oracle steps of the same workload from t=0 ({osec:.1f} s)"},
             "e2e": e2e,
+            "matched_l1": matched,
             "gpu_launches": launches,
             "clocks": clk,
         }
@@ -366,8 +594,13 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default="adaptive", choices=["adaptive", "uniform"],
-                    help="uniform: only the stage kernel on an n^d grid (profiling workload)")
+    ap.add_argument("--case", default="adaptive", choices=["adaptive", "uniform", "matched3d"],
+                    help="uniform: only the stage kernel on an n^d grid (profiling workload); "
+                         "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
+    ap.add_argument("--levels3d", type=int, default=5)
+    ap.add_argument("--t-end3d", dest="t_end3d", type=float, default=0.1)
+    ap.add_argument("--snapshots", type=int, default=60)
+    ap.add_argument("--train-steps", dest="train_steps", type=int, default=300)
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--precision", default="fp32")
@@ -376,6 +609,8 @@ def main():
         args.warmup = 3
     if args.case == "uniform":
         run_case(args)
+    elif args.case == "matched3d":
+        run_matched3d(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -184,6 +184,12 @@ int mrfv_download_level(mrfv_ctx *ctx, int level, double *host, int64_t n, uint8
 /* Write host[nv * cells(l)] into the existing blocks of level l. */
 int mrfv_upload_level(mrfv_ctx *ctx, int level, const double *host, int64_t n);
 
+/* Leaf representation projected to the finest level (Section 3, error
+   assessment for MR): existing cells as stored, every other cell predicted
+   (third order) from the level below, level by level; host[nv * cells(L)]
+   (double, dense layout as above). */
+int mrfv_project_finest(mrfv_ctx *ctx, double *host, int64_t n);
+
 /* Block map of level l (1 = block exists). */
 int mrfv_get_tree(mrfv_ctx *ctx, int level, uint8_t *exist, int64_t n);
 /* Replace the tree: exist_all = the block maps of levels 0..L concatenated.

@@ -84,6 +84,7 @@ SIGNATURES = {
     "mrfv_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "mrfv_download_level": (_I, [_P, _I, _DP, _I64, _U8]),
     "mrfv_upload_level": (_I, [_P, _I, _DP, _I64]),
+    "mrfv_project_finest": (_I, [_P, _DP, _I64]),
     "mrfv_get_tree": (_I, [_P, _I, _U8, _I64]),
     "mrfv_set_tree": (_I, [_P, _U8, _I64]),
     "mrfv_get_flags": (_I, [_P, _I, _U8, _DP, _I64]),
@@ -268,6 +269,11 @@ class Solver:
     def upload_level(self, level: int, data) -> None:
         a = np.ascontiguousarray(data, dtype=np.float64)
         self._check(self.lib.mrfv_upload_level(self._h, level, _dp(a), a.size))
+
+    def project_finest(self) -> np.ndarray:
+        out = np.empty((self.nv,) + self.cells_shape(self.L), dtype=np.float64)
+        self._check(self.lib.mrfv_project_finest(self._h, _dp(out), out.size))
+        return out
 
     def get_tree(self, level: int) -> np.ndarray:
         ex = np.empty(self.blocks_shape(level), dtype=np.uint8)

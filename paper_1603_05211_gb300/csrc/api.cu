@@ -173,7 +173,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t opf = L.take(3 * maptotal * 4), opl = L.take(maptotal * 4), opa0 = L.take(3 * maptotal * 2);
   size_t opa1 = L.take(16 * maptotal * 2), opa2 = L.take(16 * maptotal * 2);
   size_t opw1 = L.take(16 * 96 * 2), opw2 = L.take(16 * 432 * 2), opw3 = L.take(16 * 432 * 2);
-  size_t opb = L.take(3 * 16 * 4), opblob = L.take(4 * NW * 4), opwork = L.take(50 * maptotal * 4), oploss = L.take(8);
+  size_t opb = L.take(3 * 16 * 4), opblob = L.take(4 * NW * 4), opwork = L.take((size_t)kPropWorkPerPos * maptotal * 4), oploss = L.take(8);
   if (c) {
     char *a = c->arena;
     c->U = a + oU; c->Us = a + oUs; c->U0 = a + oU0; c->G = a + oG; c->FR = a + oFR;
@@ -799,6 +799,30 @@ int mrfv_upload_level(mrfv_ctx *c, int level, const double *host, int64_t n) {
   int rc = check_launch(c, "mrfv_upload_level");
   if (rc == MRFV_OK) rc = check_device(c, "mrfv_upload_level");
   cudaFree(buf);
+  return rc;
+}
+
+int mrfv_project_finest(mrfv_ctx *c, double *host, int64_t n) {
+  if (!c || !host) return fail(c, MRFV_ERR_ARG, "project_finest: arguments");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "project_finest before init");
+  const int L = c->g.L;
+  if (n != level_cells(c->g, L) * c->g.nv) return fail(c, MRFV_ERR_ARG, "project_finest: n = nv * cells(finest)");
+  double *bufs[2] = {nullptr, nullptr};
+  size_t big = (size_t)n * 8;
+  if (cudaMalloc(&bufs[0], big) != cudaSuccess || cudaMalloc(&bufs[1], big) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(bufs[0]);
+    return fail(c, MRFV_ERR_CUDA, "project_finest: staging allocation");
+  }
+  for (int l = 0; l <= L; l++) {
+    double *out = bufs[l & 1], *coarse = l > 0 ? bufs[(l - 1) & 1] : nullptr;
+    dispatch(c, [&](auto &s) { launch_project_level(c->g, l, s.U(), coarse, out, c->st); });
+  }
+  int rc = check_launch(c, "mrfv_project_finest");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_project_finest");
+  if (rc == MRFV_OK) cudaMemcpy(host, bufs[L & 1], big, cudaMemcpyDeviceToHost);
+  cudaFree(bufs[0]);
+  cudaFree(bufs[1]);
   return rc;
 }
 

@@ -62,6 +62,10 @@ struct FVArgs {
   unsigned long long *bytes;  // optional: += algorithmic bytes of this launch
 };
 
+// training scratch of the learned proposer, in floats per block position:
+// h1, h2 (16 channels each), logits z, dL/dz, and the two 16-channel gradients
+constexpr long long kPropWorkPerPos = 16 + 16 + 1 + 1 + 16 + 16;
+
 // rows of the per-level step table (see FVArgs::lev): stage 0 has coef 1/2, stage 1 coef 1
 __host__ __device__ inline int lev_index(int stage, int l, int k) { return (stage * MAXL + l) * 4 + k; }
 

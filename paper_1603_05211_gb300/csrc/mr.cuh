@@ -360,6 +360,42 @@ __global__ void k_scatter_level(Geo g, int l, const double *__restrict__ in, T *
   }
 }
 
+// ---------------------------------------------------------------- projection to the finest level
+// Dense level-l array of the leaf representation (Section 3, error assessment
+// for MR): existing cells from the pool, every other cell predicted (third
+// order, in double) from the dense level l-1 array built the same way.
+template <typename T, int D>
+__global__ void k_project_level(Geo g, int l, const T *__restrict__ A, const double *__restrict__ coarse,
+                                double *__restrict__ out) {
+  constexpr int B = (D == 2) ? 64 : 512;
+  const long long n0 = (long long)g.nb[l][0] * 8, n1 = (long long)g.nb[l][1] * 8;
+  const long long n2 = (D == 3) ? (long long)g.nb[l][2] * 8 : 1;
+  const long long nc = n0 * n1 * n2;
+  const long long c0 = n0 / 2, c1 = n1 / 2, c2 = (D == 3) ? n2 / 2 : 1, ncc = c0 * c1 * c2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % n0), j = (int)((t / n0) % n1), k = (int)(t / (n0 * n1));
+    int32_t s = g.idx[map_index(g, l, i >> 3, j >> 3, k >> 3)];
+    if (s >= 0) {
+      int c = (i & 7) + 8 * (j & 7) + ((D == 3) ? 64 * (k & 7) : 0);
+      for (int v = 0; v < D + 2; v++) out[(long long)v * nc + t] = (double)A[((long long)v * g.cap + s) * B + c];
+      continue;
+    }
+    // 3^d coarse stencil around the parent cell (boundary rule at level l-1)
+    double Pch[27];
+    for (int v = 0; v < D + 2; v++) {
+      for (int cz = 0; cz < ((D == 3) ? 3 : 1); cz++)
+        for (int cy = 0; cy < 3; cy++)
+          for (int cx = 0; cx < 3; cx++) {
+            int x = bc_cell(g, l - 1, 0, (i >> 1) + cx - 1), y = bc_cell(g, l - 1, 1, (j >> 1) + cy - 1);
+            int z = (D == 3) ? bc_cell(g, l - 1, 2, (k >> 1) + cz - 1) : 0;
+            Pch[cx + 3 * (cy + 3 * cz)] = coarse[(long long)v * ncc + x + c0 * (y + c1 * z)];
+          }
+      double si = (i & 1) ? -1.0 : 1.0, sj = (j & 1) ? -1.0 : 1.0, sk = (k & 1) ? -1.0 : 1.0;
+      out[(long long)v * nc + t] = predict<double, D, 3>(Pch, 1, 1, (D == 3) ? 1 : 0, si, sj, sk);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- totals
 template <typename T, int D>
 __global__ void k_totals(Geo g, const T *__restrict__ A, double *out) {

@@ -77,6 +77,12 @@ void launch_gradflags(const Geo &g, const T *A, double epsw, uint8_t *gflag, int
   else k_gradflags<T, 3><<<grid, 256, 0, st>>>(g, A, T(epsw), gflag);
 }
 
+template <typename T>
+void launch_project_level(const Geo &g, int l, const T *A, const double *coarse, double *out, cudaStream_t st) {
+  if (g.dim == 2) k_project_level<T, 2><<<1024, 256, 0, st>>>(g, l, A, coarse, out);
+  else k_project_level<T, 3><<<1024, 256, 0, st>>>(g, l, A, coarse, out);
+}
+
 #define MRFV_INSTANTIATE_MR(T)                                                                              \
   template void launch_restrict<T>(const Geo &, int, T *, int, cudaStream_t);                               \
   template void launch_scales<T>(const Geo &, const T *, unsigned long long *, T *, int, cudaStream_t);     \
@@ -90,6 +96,7 @@ void launch_gradflags(const Geo &g, const T *A, double epsw, uint8_t *gflag, int
   template void launch_totals<T>(const Geo &, const T *, double *, int, cudaStream_t);                      \
   template void launch_reflux<T>(const Geo &, int, int, T *, const T *, int, cudaStream_t);                 \
   template void launch_copy_level<T>(const Geo &, int, const T *, T *, int, cudaStream_t);                  \
-  template void launch_gradflags<T>(const Geo &, const T *, double, uint8_t *, int, cudaStream_t);
+  template void launch_gradflags<T>(const Geo &, const T *, double, uint8_t *, int, cudaStream_t);         \
+  template void launch_project_level<T>(const Geo &, int, const T *, const double *, double *, cudaStream_t);
 
 }  // namespace mrfv

@@ -491,7 +491,7 @@ void launch_pack_weights(const float *blob, __nv_bfloat16 *w1, float *b1, __nv_b
 
 // One Adam step on a batch of snapshots: forward in FP32 with the BF16-rounded
 // weights' master copy, BCE loss, backward, update.  feat: [ns][3][n] floats,
-// target: [ns][n] bytes (device).  work: scratch of 2*(3+16+16+1)*n floats.
+// target: [ns][n] bytes (device).  work: scratch of kPropWorkPerPos * n floats.
 void launch_prop_train_step(const Geo &g, const float *feat, const uint8_t *target, int ns, float *blob, float *grad,
                             float *m1, float *m2, int t, float lr, float *work, double *loss, cudaStream_t st) {
   long long n = g.mapoff[g.L + 1];

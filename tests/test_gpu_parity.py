@@ -129,6 +129,15 @@ def test_adaptive_mr_fp64(mrfv, seed):
     assert len([x for x in st["leaves"] if x]) >= 2
 
 
+def test_project_finest_matches_oracle(mrfv):
+    s, o = pair(mrfv, 2, 5, (1, 1, 1), adapt=True, params=mi.quadrant_params(8))
+    run_pair(s, o, 10, adapt_crit=oracle.CRIT_MR)
+    assert_same_tree(s, o)
+    g = s.project_finest()
+    r = o.project_finest()
+    assert np.abs(g - r).max() <= REL64 * np.abs(r).max()
+
+
 def test_adaptive_mr_fp64_periodic_conservation(mrfv):
     s, o = pair(mrfv, 2, 5, (1, 1, 1), bc=1, adapt=True, params=mi.quadrant_params(5))
     T0 = s.totals()
