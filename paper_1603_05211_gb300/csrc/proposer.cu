@@ -59,7 +59,10 @@ __global__ void k_prop_features(Geo g, const T *__restrict__ U, const double *__
   const long long cap = g.cap;
   const float srho = (float)scale[0], sp = (float)((g.gamma - 1.0) * (double)scale[D + 1]);
   const float gm1 = (float)(g.gamma - 1.0);
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  // one warp per position: the lanes share the block's cells, then reduce
+  for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nwarp) {
     int l = pos_level(g, p);
     long long u = p - g.mapoff[l];
     int bx = (int)(u % g.nb[l][0]), by = (int)((u / g.nb[l][0]) % g.nb[l][1]);
@@ -77,31 +80,37 @@ __global__ void k_prop_features(Geo g, const T *__restrict__ U, const double *__
       float m = (float)(maxdet[p] / eps);
       f2 = fminf(m, 8.f) / 8.f;
     }
-    float f0 = 0.f, f1 = 0.f;
+    float sr = 0.f, spp = 0.f;
+    const int ncell = (D == 3) ? ext * ext * ext : ext * ext;
     if (s >= 0) {
-      double sr = 0.0, spp = 0.0;
-      int kz = (D == 3) ? ext : 1;
-      for (int k = 0; k < kz; k++)
-        for (int j = 0; j < ext; j++)
-          for (int i = 0; i < ext; i++) {
-            int c = (c0[0] + i) + 8 * (c0[1] + j) + ((D == 3) ? 64 * (c0[2] + k) : 0);
-            float rho = (float)U[((long long)0 * cap + s) * B + c];
-            float vv = 0.f;
-            for (int d = 0; d < D; d++) {
-              float m = (float)U[((long long)(1 + d) * cap + s) * B + c];
-              vv += m * m;
-            }
-            float E = (float)U[((long long)(D + 1) * cap + s) * B + c];
-            sr += rho;
-            spp += gm1 * (E - 0.5f * vv / rho);
-          }
-      double cnt = (double)(ext * ext * ((D == 3) ? ext : 1));
-      f0 = (float)(sr / cnt) / srho;
-      f1 = (float)(spp / cnt) / sp;
+      for (int q = lane; q < ncell; q += 32) {
+        int i = q % ext, j = (q / ext) % ext, k = q / (ext * ext);
+        int c = (c0[0] + i) + 8 * (c0[1] + j) + ((D == 3) ? 64 * (c0[2] + k) : 0);
+        float rho = (float)U[((long long)0 * cap + s) * B + c];
+        float vv = 0.f;
+        for (int d = 0; d < D; d++) {
+          float m = (float)U[((long long)(1 + d) * cap + s) * B + c];
+          vv += m * m;
+        }
+        float E = (float)U[((long long)(D + 1) * cap + s) * B + c];
+        sr += rho;
+        spp += gm1 * (E - 0.5f * vv / rho);
+      }
     }
-    feat[p] = f0;
-    feat[n + p] = f1;
-    feat[2 * n + p] = f2;
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      spp += __shfl_xor_sync(0xffffffffu, spp, o);
+    }
+    if (lane == 0) {
+      float f0 = 0.f, f1 = 0.f;
+      if (s >= 0) {
+        f0 = (sr / (float)ncell) / srho;
+        f1 = (spp / (float)ncell) / sp;
+      }
+      feat[p] = f0;
+      feat[n + p] = f1;
+      feat[2 * n + p] = f2;
+    }
   }
 }
 
@@ -170,6 +179,7 @@ __global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16
   unsigned char *sB = sm + M * KP * 2;          // N x KP bf16
   uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + (M + N) * KP * 2);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+  int32_t *nbq = reinterpret_cast<int32_t *>(mbar + 2);  // [M][27] neighbour positions of the tile rows
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long npos = g.mapoff[g.L + 1];
   const int dim3d = g.dim == 3;
@@ -201,18 +211,23 @@ __global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16
 
   const long long ntiles = (npos + M - 1) / M;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    // neighbour positions of the tile rows (-1: outside the level or beyond npos)
+    for (int i = tid; i < M * 27; i += blockDim.x) {
+      int m = i / 27, t = i % 27;
+      long long p = tile * M + m;
+      int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+      long long q = -1;
+      if (p < npos && (dim3d || dz == 0)) q = pos_neighbour(g, pos_level(g, p), p, dx, dy, dz);
+      nbq[i] = (int32_t)q;
+    }
+    __syncthreads();
     // im2col rows of this tile -> shared
     for (int i = tid; i < M * KP; i += blockDim.x) {
       int m = i / KP, k = i % KP;
-      long long p = tile * M + m;
       __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-      if (p < npos && k < KREAL) {
-        int ci = k / 27, t = k % 27;
-        int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-        if (dim3d || dz == 0) {
-          long long q = pos_neighbour(g, pos_level(g, p), p, dx, dy, dz);
-          if (q >= 0) v = in[(long long)ci * npos + q];
-        }
+      if (k < KREAL) {
+        int q = nbq[m * 27 + k % 27];
+        if (q >= 0) v = in[(long long)(k / 27) * npos + q];
       }
       *reinterpret_cast<__nv_bfloat16 *>(sA + cm_offset(m, k, KP)) = v;
     }
@@ -276,7 +291,7 @@ __global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16
 
 template <int KP>
 constexpr size_t conv_smem() {
-  return (size_t)(128 + 16) * KP * 2 + 16;
+  return (size_t)(128 + 16) * KP * 2 + 16 + 128 * 27 * 4;
 }
 
 // ---------------------------------------------------------------- marking
@@ -451,8 +466,8 @@ __global__ void k_pack_weights(const float *__restrict__ blob, __nv_bfloat16 *w1
 template <typename T>
 void launch_prop_features(const Geo &g, const T *U, const double *maxdet, const T *scale, double eps, float *feat,
                           int grid, cudaStream_t st) {
-  if (g.dim == 2) k_prop_features<T, 2><<<grid, 128, 0, st>>>(g, U, maxdet, scale, eps, feat);
-  else k_prop_features<T, 3><<<grid, 128, 0, st>>>(g, U, maxdet, scale, eps, feat);
+  if (g.dim == 2) k_prop_features<T, 2><<<grid, 256, 0, st>>>(g, U, maxdet, scale, eps, feat);
+  else k_prop_features<T, 3><<<grid, 256, 0, st>>>(g, U, maxdet, scale, eps, feat);
 }
 template void launch_prop_features<float>(const Geo &, const float *, const double *, const float *, double, float *,
                                           int, cudaStream_t);
