@@ -26,6 +26,8 @@ BC_TRANSMISSIVE = 0
 BC_PERIODIC = 1
 CRIT_MR = 0
 CRIT_GRAD = 1
+SCHEME_MUSCL_RK2 = 0  # MUSCL / van Albada / AUSM+ / explicit midpoint RK2 (the MR scheme, Section 2)
+SCHEME_HANCOCK = 1    # MUSCL-Hancock / Minmod / AUSMDV (the AMR scheme, Section 2)
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +74,8 @@ def _load():
             "orc_project_finest": (None, [P, dp]),
             "orc_flux": (None, [P, I, dp, dp, dp]),
             "orc_physical_flux": (None, [P, I, dp, dp]),
+            "orc_flux_ausmdv": (None, [P, I, dp, dp, dp]),
+            "orc_set_scheme": (I, [P, I]),
             "orc_predict": (D, [P, I, dp, I, I, I, I]),
         }
         for name, (res, args) in sig.items():
@@ -95,7 +99,7 @@ class Oracle:
     ``base_blocks * 2^l`` blocks of 8 cells per dimension."""
 
     def __init__(self, dim: int, levels: int, base_blocks, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
-                 gamma: float = 1.4, bc: int = BC_TRANSMISSIVE):
+                 gamma: float = 1.4, bc: int = BC_TRANSMISSIVE, scheme: int = SCHEME_MUSCL_RK2):
         lib = _load()
         nb = (ctypes.c_int * 3)(*[int(b) for b in (list(base_blocks) + [1, 1, 1])[:3]])
         lo3 = (ctypes.c_double * 3)(*[float(x) for x in (list(lo) + [0.0] * 3)[:3]])
@@ -104,6 +108,9 @@ class Oracle:
         if not self._h:
             raise ValueError("oracle: bad configuration")
         self.lib = lib
+        if lib.orc_set_scheme(self._h, scheme) != 0:
+            raise ValueError("oracle: bad scheme")
+        self.scheme = scheme
         self.dim, self.levels, self.L, self.nv = dim, levels, levels - 1, dim + 2
         self.base_blocks = tuple(int(b) for b in (list(base_blocks) + [1, 1, 1])[:3])
         self.lo = tuple(float(x) for x in (list(lo) + [0.0] * 3)[:3])
@@ -202,6 +209,12 @@ class Oracle:
         a = np.zeros(5); b = np.zeros(5); F = np.zeros(5)
         a[: self.nv] = ql; b[: self.nv] = qr
         self.lib.orc_flux(self._h, nd, _dp(a), _dp(b), _dp(F))
+        return F[: self.nv]
+
+    def flux_ausmdv(self, nd: int, ql, qr) -> np.ndarray:
+        a = np.zeros(5); b = np.zeros(5); F = np.zeros(5)
+        a[: self.nv] = ql; b[: self.nv] = qr
+        self.lib.orc_flux_ausmdv(self._h, nd, _dp(a), _dp(b), _dp(F))
         return F[: self.nv]
 
     def physical_flux(self, nd: int, q) -> np.ndarray:

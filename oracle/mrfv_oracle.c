@@ -17,6 +17,7 @@
  *   - Euler equations, ideal gas, gamma = 1.4 .............. Section 2, Eqs. 2.1-2.3
  *   - cell averages, dQ/dt = -F(Q) ........................ Section 2 (FV semi-discretisation)
  *   - MUSCL, van Albada limiter, AUSM+ flux, RK2 midpoint .. Section 2 (MR scheme paragraph)
+ *   - MUSCL-Hancock, Minmod, AUSMDV flux (scheme 1) ....... Section 2 (AMR scheme paragraph), Sec. 4.2
  *   - projection / 3rd-order prediction / details / eps ... Section 2.1
  *   - refinement by one level, gradedness, coarsening ..... Section 2.1 (three basic operations)
  *   - virtual leaves / conservative coarse-fine fluxes ..... Section 2.1, Fig. 1
@@ -39,8 +40,11 @@ enum { O_CRIT_MR = 0, O_CRIT_GRAD = 1 };
 enum { O_IC_QUADRANTS = 0, O_IC_ELLIPSOID = 1, O_IC_SHOCKTUBE = 2, O_IC_UNIFORM = 3,
        O_IC_WAVE = 4, O_IC_ROTATED_ELLIPSOID = 5 };
 
+enum { O_SCHEME_MUSCL_RK2 = 0, O_SCHEME_HANCOCK = 1 };
+
 typedef struct {
   int dim, nv, L, bc;
+  int scheme;         /* O_SCHEME_*: the MR scheme (default) or the AMR scheme of Section 2 */
   double gamma;
   double lo[3], hi[3];
   int nb[OMAXL][3];   /* blocks per dimension (1 in unused dimensions) */
@@ -186,6 +190,121 @@ static void physical_flux(const orc *o, int nd, const double *Q, double *F) {
   F[0] = Q[0] * vn;
   for (int d = 0; d < o->dim; d++) F[1 + d] = Q[1 + d] * vn + (d == nd ? w[4] : 0.0);
   F[o->dim + 1] = (Q[o->dim + 1] + w[4]) * vn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The AMR scheme of Section 2 (scheme 1): MUSCL-Hancock with the Minmod limiter
+   in the primitive variables rho, v, p (Section 4.2) and the AUSMDV flux of
+   Wada and Liou (1997).  The step is one stage: face states are advanced half
+   a step with the exact flux before the numerical flux is taken, which makes
+   the update second order in time like the midpoint rule.
+   Reading (the paper says "unsplit" and "second order"): the cell's
+   extrapolated states are all advanced by the same half-step increment
+   dQ = sum_m (dt/2)/dx_m (f_m(Q^{-m}) - f_m(Q^{+m})) over every direction m,
+   the unsplit MUSCL-Hancock predictor; a predictor that used only the face's
+   own direction would be first order in time for oblique flow.  So the states
+   of a face need the slopes of its two cells in every direction, i.e. the cells
+   diagonally next to the face (the halo corners).
+   Reading: AUSMDV without the entropy and shock fixes, K = 10 in the blend. */
+
+static double minmod(double a, double b) {
+  if ((a * b) > 0.0) return fabs(a) < fabs(b) ? a : b;
+  return 0.0;
+}
+
+/* exact flux f_n of Eq. 2.2 at primitive state w with conservative state Q */
+static void exact_flux_prim(const orc *o, int nd, const double *w, const double *Q, double *F) {
+  double vn = w[1 + nd], p = w[4];
+  F[0] = Q[0] * vn;
+  for (int d = 0; d < o->dim; d++) {
+    double f = Q[1 + d] * vn;
+    if (d == nd) f = f + p;
+    F[1 + d] = f;
+  }
+  F[o->dim + 1] = (Q[o->dim + 1] + p) * vn;
+}
+
+/* Hancock face state: cell primitive state w with Minmod slopes s[m][.] in every
+   direction m; the extrapolated states w -/+ s[m]/2 give the half-step increment
+   dQ = sum over m (in direction order) of h_m (f_m(Q^{-m}) - f_m(Q^{+m})),
+   h_m = (dt/2)/dx_m; returns the primitive state of Q^{side,nd} + dQ
+   (side = +1: the state on the cell's high face in direction nd, -1: low face). */
+static void hancock_state(const orc *o, int l, const double *w, double s[3][5], double dt, int nd, int side,
+                          double *wout) {
+  double dQ[5] = {0, 0, 0, 0, 0};
+  double Qf[5] = {0, 0, 0, 0, 0};
+  for (int m = 0; m < o->dim; m++) {
+    double wm[5], wp[5], Qm[5], Qp[5], Fm[5], Fp[5];
+    for (int k = 0; k < 5; k++) {
+      wm[k] = w[k] - (0.5 * s[m][k]);
+      wp[k] = w[k] + (0.5 * s[m][k]);
+    }
+    prim_to_cons(o, wm, Qm);
+    prim_to_cons(o, wp, Qp);
+    exact_flux_prim(o, m, wm, Qm, Fm);
+    exact_flux_prim(o, m, wp, Qp, Fp);
+    double h = (0.5 * dt) / o->dx[l][m];
+    for (int v = 0; v < o->nv; v++) {
+      double inc = h * (Fm[v] - Fp[v]);
+      dQ[v] = (m == 0) ? inc : dQ[v] + inc;
+    }
+    if (m == nd)
+      for (int v = 0; v < o->nv; v++) Qf[v] = side > 0 ? Qp[v] : Qm[v];
+  }
+  double Qb[5];
+  for (int v = 0; v < o->nv; v++) Qb[v] = Qf[v] + dQ[v];
+  cons_to_prim(o, Qb, wout);
+  if (o->dim == 2) wout[3] = 0.0;
+}
+
+/* AUSMDV flux across a face with normal nd from primitive face states wl | wr:
+   c_m = max(c_L, c_R); pressure-weighted split velocities; split pressures;
+   normal momentum flux blended between AUSMV and AUSMD by
+   s = min(1, K |p_R - p_L| / min(p_L, p_R)) / 2; tangential momentum and
+   enthalpy upwinded by the mass flux. */
+static void ausmdv(const orc *o, int nd, const double *wl, const double *wr, double *F) {
+  double g = o->gamma;
+  double rl = wl[0], rr = wr[0], pl = wl[4], pr = wr[4];
+  double ul = wl[1 + nd], ur = wr[1 + nd];
+  double cl = sqrt((g * pl) / rl), cr = sqrt((g * pr) / rr);
+  double cm = cl > cr ? cl : cr;
+  double pol = pl / rl, por = pr / rr;
+  double al = (2.0 * pol) / (pol + por), ar = (2.0 * por) / (pol + por);
+  double upl = 0.5 * (ul + fabs(ul)), umr = 0.5 * (ur - fabs(ur));
+  double ulp, urm, plp, prm;
+  if (fabs(ul) <= cm) {
+    double t = ul + cm;
+    ulp = (al * (((t * t) / (4.0 * cm)) - upl)) + upl;
+    plp = pl * (((t * t) * (2.0 - (ul / cm))) / (4.0 * (cm * cm)));
+  } else {
+    ulp = upl;
+    plp = ul > 0.0 ? pl : 0.0;
+  }
+  if (fabs(ur) <= cm) {
+    double t = ur - cm;
+    urm = (ar * ((-((t * t) / (4.0 * cm))) - umr)) + umr;
+    prm = pr * (((t * t) * (2.0 + (ur / cm))) / (4.0 * (cm * cm)));
+  } else {
+    urm = umr;
+    prm = ur < 0.0 ? pr : 0.0;
+  }
+  double mdot = (ulp * rl) + (urm * rr);
+  double am = fabs(mdot);
+  double ph = plp + prm;
+  double pmin = pl < pr ? pl : pr;
+  double sw = 0.5 * fmin(1.0, (10.0 * fabs(pr - pl)) / pmin);
+  double fv = (ulp * (rl * ul)) + (urm * (rr * ur));
+  double fd = 0.5 * ((mdot * (ul + ur)) - (am * (ur - ul)));
+  double fn = ((0.5 + sw) * fv) + ((0.5 - sw) * fd);
+  F[0] = mdot;
+  for (int d = 0; d < o->dim; d++) {
+    if (d == nd) F[1 + d] = fn + ph;
+    else F[1 + d] = 0.5 * ((mdot * (wl[1 + d] + wr[1 + d])) - (am * (wr[1 + d] - wl[1 + d])));
+  }
+  double vvl = ((wl[1] * wl[1]) + (wl[2] * wl[2])) + (wl[3] * wl[3]);
+  double vvr = ((wr[1] * wr[1]) + (wr[2] * wr[2])) + (wr[3] * wr[3]);
+  double hl = ((g / (g - 1.0)) * pol) + (0.5 * vvl), hr = ((g / (g - 1.0)) * por) + (0.5 * vvr);
+  F[o->dim + 1] = 0.5 * ((mdot * (hl + hr)) - (am * (hr - hl)));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -359,8 +478,9 @@ static double *build_ext(const orc *o, int l, const double *src, const double *c
 
 /* ------------------------------------------------------------------------ */
 /* numerical flux across the face between cell a = (i,j,k) and a + e_nd,
-   computed from the level array E (with boundary handling of indices)        */
-static void face_flux(const orc *o, int l, const double *E, int nd, int i, int j, int k, double *F) {
+   computed from the level array E (with boundary handling of indices); dt is
+   the step the face states are advanced over (scheme 1 only) */
+static void face_flux(const orc *o, int l, const double *E, int nd, int i, int j, int k, double dt, double *F) {
   int c4[4][3];
   for (int s = 0; s < 4; s++) {
     int p[3] = {i, j, k};
@@ -374,6 +494,38 @@ static void face_flux(const orc *o, int l, const double *E, int nd, int i, int j
     cons_to_prim(o, Q, w[s]);
   }
   double wl[5], wr[5];
+  if (o->scheme == O_SCHEME_HANCOCK) {
+    /* the two cells of the face, their slopes in every direction */
+    double sl[3][5], sr[3][5];
+    for (int side = 0; side < 2; side++) {
+      int c[3] = {i, j, k};
+      c[nd] += side;
+      double (*sp)[5] = side ? sr : sl;
+      for (int m = 0; m < 3; m++)
+        for (int q = 0; q < 5; q++) sp[m][q] = 0.0;
+      for (int m = 0; m < o->dim; m++) {
+        double wn[3][5];
+        for (int t = 0; t < 3; t++) {
+          int p[3] = {c[0], c[1], c[2]};
+          p[m] += t - 1;
+          double Q[5];
+          get_cell(o, l, E, cidx(o, l, bc_cell(o, l, 0, p[0]), bc_cell(o, l, 1, p[1]), bc_cell(o, l, 2, p[2])), Q);
+          cons_to_prim(o, Q, wn[t]);
+        }
+        for (int q = 0; q < 5; q++) {
+          if (q >= 1 + o->dim && q < 4) continue;
+          sp[m][q] = minmod(wn[1][q] - wn[0][q], wn[2][q] - wn[1][q]);
+        }
+      }
+    }
+    double wa[5], wb[5];
+    for (int q = 0; q < 5; q++) { wa[q] = w[1][q]; wb[q] = w[2][q]; }
+    if (o->dim == 2) { wa[3] = 0.0; wb[3] = 0.0; }
+    hancock_state(o, l, wa, sl, dt, nd, +1, wl); /* high face of cell a */
+    hancock_state(o, l, wb, sr, dt, nd, -1, wr); /* low face of cell a + e */
+    ausmdv(o, nd, wl, wr, F);
+    return;
+  }
   for (int m = 0; m < 5; m++) {
     if (m >= 1 + o->dim && m < 4) { wl[m] = 0.0; wr[m] = 0.0; continue; }
     double sa = van_albada(w[1][m] - w[0][m], w[2][m] - w[1][m]);
@@ -408,8 +560,8 @@ static void fv_level(orc *o, int l, const double *E, const double *q0, double *o
               for (int d = 0; d < o->dim; d++) {
                 int a[3] = {i, j, k};
                 a[d] -= 1;
-                face_flux(o, l, E, d, a[0], a[1], a[2], Fm[d]);
-                face_flux(o, l, E, d, i, j, k, Fp[d]);
+                face_flux(o, l, E, d, a[0], a[1], a[2], dt, Fm[d]);
+                face_flux(o, l, E, d, i, j, k, dt, Fp[d]);
               }
               for (int v = 0; v < o->nv; v++) {
                 double r = lam[0] * (Fp[0][v] - Fm[0][v]);
@@ -684,6 +836,23 @@ double orc_dt(const orc *o, double cfl, int lts) {
    are corrected as in Fig. 2. */
 static void step_global(orc *o, double dt) {
   int L = o->L;
+  if (o->scheme == O_SCHEME_HANCOCK) {
+    /* one MUSCL-Hancock stage from Q^n, fluxes recorded for the correction */
+    double *qn[OMAXL];
+    for (int l = 0; l <= L; l++) {
+      qn[l] = alloc_level(o, l);
+      double *E = build_ext(o, l, o->q[l], l > 0 ? o->q[l - 1] : NULL);
+      fv_level(o, l, E, o->q[l], qn[l], 1.0, dt, 0, 1, 0);
+      free(E);
+    }
+    for (int l = 0; l <= L; l++) {
+      copy_blocks(o, l, qn[l], o->q[l], 1);
+      free(qn[l]);
+    }
+    for (int l = 0; l < L; l++) reflux_level(o, l, o->q[l]);
+    restrict_all(o, o->q);
+    return;
+  }
   /* stage 1 */
   for (int l = 0; l <= L; l++) {
     double *E = build_ext(o, l, o->q[l], l > 0 ? o->q[l - 1] : NULL);
@@ -734,13 +903,19 @@ static void advance_level(orc *o, int l, int sub, double dtL) {
   copy_blocks(o, l, o->q[l], o->q0[l], 0);
   double *C1 = l > 0 ? time_interp(o, l - 1, th1) : NULL;
   double *E = build_ext(o, l, o->q[l], C1);
-  fv_level(o, l, E, o->q[l], o->qs[l], 0.5, dtl, 1, 0, 0);
-  free(E); free(C1);
-  double *C2 = l > 0 ? time_interp(o, l - 1, th2) : NULL;
-  E = build_ext(o, l, o->qs[l], C2);
   double *qn = alloc_level(o, l);
-  fv_level(o, l, E, o->q[l], qn, 1.0, dtl, 1, 1, sub == 1);
-  free(E); free(C2);
+  if (o->scheme == O_SCHEME_HANCOCK) {
+    /* one stage from the sub-step start, ghosts at its start time */
+    fv_level(o, l, E, o->q[l], qn, 1.0, dtl, 1, 1, sub == 1);
+    free(E); free(C1);
+  } else {
+    fv_level(o, l, E, o->q[l], o->qs[l], 0.5, dtl, 1, 0, 0);
+    free(E); free(C1);
+    double *C2 = l > 0 ? time_interp(o, l - 1, th2) : NULL;
+    E = build_ext(o, l, o->qs[l], C2);
+    fv_level(o, l, E, o->q[l], qn, 1.0, dtl, 1, 1, sub == 1);
+    free(E); free(C2);
+  }
   copy_blocks(o, l, qn, o->q[l], 0);
   free(qn);
   if (l < L && level_has_blocks(o, l + 1)) {
@@ -1063,6 +1238,23 @@ void orc_flux(orc *o, int nd, const double *Ql, const double *Qr, double *F) {
   ausm_plus(o, nd, wl, wr, F);
 }
 void orc_physical_flux(orc *o, int nd, const double *Q, double *F) { physical_flux(o, nd, Q, F); }
+
+/* AUSMDV flux of two conservative states (checks of the scheme-1 flux) */
+void orc_flux_ausmdv(orc *o, int nd, const double *Ql, const double *Qr, double *F) {
+  double wl[5], wr[5];
+  cons_to_prim(o, Ql, wl);
+  cons_to_prim(o, Qr, wr);
+  if (o->dim == 2) { wl[3] = 0.0; wr[3] = 0.0; }
+  ausmdv(o, nd, wl, wr, F);
+}
+
+/* select the finite-volume scheme: 0 = MUSCL / van Albada / AUSM+ / RK2 midpoint
+   (the MR scheme), 1 = MUSCL-Hancock / Minmod / AUSMDV (the AMR scheme) */
+int orc_set_scheme(orc *o, int scheme) {
+  if (scheme != O_SCHEME_MUSCL_RK2 && scheme != O_SCHEME_HANCOCK) return -1;
+  o->scheme = scheme;
+  return 0;
+}
 
 /* one cell's prediction from a given coarse level array (tests of the operator) */
 double orc_predict(orc *o, int lf, const double *coarse, int v, int i, int j, int k) {
