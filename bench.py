@@ -568,11 +568,13 @@ def run_case(args):
     m.load()
     nb = args.n // 8
     prec = args.precision
+    cfl = 0.4 if args.scheme == "hancock" else 0.5
     if args.dim == 2:
-        s = m.Solver(dim=2, precision=prec, levels=1, base_blocks=(nb, nb, 1), cfl=0.5)
+        s = m.Solver(dim=2, precision=prec, levels=1, base_blocks=(nb, nb, 1), cfl=cfl, scheme=args.scheme)
         s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(SEED))
     else:
-        s = m.Solver(dim=3, precision=prec, levels=1, base_blocks=(nb, nb, nb), lo=(-1, -1, -1), hi=(1, 1, 1), cfl=0.5)
+        s = m.Solver(dim=3, precision=prec, levels=1, base_blocks=(nb, nb, nb), lo=(-1, -1, -1), hi=(1, 1, 1), cfl=cfl,
+                     scheme=args.scheme)
         s.init_state(mi.IC_ELLIPSOID, mi.ellipsoid_params(SEED))
     for _ in range(args.warmup):
         s.step(0.0, sync=False)
@@ -583,7 +585,7 @@ def run_case(args):
     hbm_peak, _ = measured_peaks()
     ach = p["fv_bytes"] / (p["fv_ms"] * 1e-3) / 1e9
     cells = args.n ** args.dim * args.steps
-    print(json.dumps({"case": f"uniform{args.dim}d_{prec}_{args.n}", "fv_launches": p["fv_launches"],
+    print(json.dumps({"case": f"uniform{args.dim}d_{prec}_{args.n}", "scheme": args.scheme, "fv_launches": p["fv_launches"],
                       "fv_avg_ms": p["fv_ms"] / max(1, p["fv_launches"]), "fv_GBps": ach,
                       "fv_frac_hbm": ach / hbm_peak, "cell_updates_per_s_fv_only": cells / (p["fv_ms"] * 1e-3)}))
 
@@ -604,6 +606,8 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--scheme", default="muscl_rk2", choices=["muscl_rk2", "hancock"],
+                    help="finite-volume scheme of the uniform case")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

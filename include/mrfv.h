@@ -63,6 +63,14 @@ enum {
   MRFV_IC_ROTATED_ELLIPSOID = 5  /* 10: a, b, c, r_c, theta, phi, rho_in, rhoe_in, rho_out, rhoe_out */
 };
 
+/* Finite-volume schemes of Section 2.  MUSCL_RK2: MUSCL reconstruction of the
+   primitive variables with the van Albada limiter, AUSM+ flux, explicit
+   midpoint rule (two stages per step; the scheme of the paper's MR method).
+   HANCOCK: unsplit MUSCL-Hancock, Minmod limiter on rho, v, p, AUSMDV flux (one
+   stage per step: face states advanced half a step with the exact flux of every
+   direction; the scheme of the paper's AMR method). */
+enum { MRFV_SCHEME_MUSCL_RK2 = 0, MRFV_SCHEME_HANCOCK = 1 };
+
 #define MRFV_MAX_LEVELS 12
 
 /* Solver configuration; plain data, copied by mrfv_create. */
@@ -90,6 +98,7 @@ typedef struct {
                            CUDA graph (on a private stream) and every step replays it on `stream` */
   int proposer;         /* 1: MR adaptation takes the learned proposer's blocks instead of the safety
                            zone, once weights are set (mrfv_proposer_set_weights) */
+  int scheme;           /* MRFV_SCHEME_MUSCL_RK2 (default) or MRFV_SCHEME_HANCOCK (Section 2) */
 } mrfv_config;
 
 typedef struct {
@@ -165,7 +174,9 @@ int mrfv_fill_ghosts(mrfv_ctx *ctx, int level, int buffer);
 int mrfv_step(mrfv_ctx *ctx, double dt, double *dt_out);
 
 /* The level recursion of Fig. 2 from level l (levels l..L advance by one step
-   of level l, dt_l = 2^(L-l) dt_finest), without adaptation. */
+   of level l, dt_l = 2^(L-l) dt_finest), without adaptation.  Needs cfg.lts
+   (only then does the arena hold the level-step start states): MRFV_ERR_STATE
+   otherwise. */
 int mrfv_step_level(mrfv_ctx *ctx, int level, double dt_finest);
 
 /* Projection (Section 2.1) of level fine_level onto the refined blocks of
@@ -223,6 +234,15 @@ typedef struct {
 int mrfv_profile_enable(mrfv_ctx *ctx, int enable);
 /* Read the counters (synchronises the stream). */
 int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
+
+/* Launch shape (no counterpart in the paper): CTAs per SM of the persistent
+   grids, for the grid-stride kernels (256-thread CTAs), the kernels that take
+   one block per CTA, and the finite-volume stage kernel.  0 keeps the default
+   (the stage kernel's default is its occupancy limit); each value is 0..32,
+   else MRFV_ERR_ARG.  Every kernel loops over its device-resident work list,
+   so any shape gives the same results; captured step graphs are dropped and
+   re-captured at the next step. */
+int mrfv_set_launch_shape(mrfv_ctx *ctx, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm);
 
 /* Learned refinement proposer (no counterpart in the paper, which refines by
    the heuristic of Section 2.1): a 3-layer 3D convolutional net (16 channels,

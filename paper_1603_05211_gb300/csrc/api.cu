@@ -16,13 +16,20 @@
 
 using namespace mrfv;
 
+// Default persistent-grid sizes, CTAs per SM: `grid` for the grid-stride kernels
+// (256-thread CTAs), `bgrid` for the kernels that take one block per CTA.
+// Dispatching a CTA costs time even when it finds no work, so these stay small;
+// mrfv_set_launch_shape overrides them.
+constexpr int kGridCtasPerSm = 8;
+constexpr int kBlockCtasPerSm = 16;
+
 struct mrfv_ctx {
   mrfv_config cfg;
   Geo g;
   int prec;         // MRFV_FP64 / MRFV_FP32
   size_t tsize;     // bytes per state value
   cudaStream_t st;
-  int nsm, grid, bgrid, fvgrid;
+  int nsm, grid, bgrid, fvgrid, fv_occupancy, fvhgrid, fvh_occupancy;
   char *arena;
   size_t arena_bytes;
   bool own_arena;
@@ -157,7 +164,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   int nv = g.nv, B = block_cells(g.dim), TF = face_cells(g.dim);
   Layout L;
   size_t state = (size_t)nv * cap * B * ts;
-  size_t oU = L.take(state), oUs = L.take(state), oU0 = L.take(state);
+  size_t oU = L.take(state), oUs = L.take(state), oU0 = L.take(cfg->lts ? state : 0);  // U0: level-step start states (LTS)
   size_t oG = L.take((size_t)nv * cap * 2 * g.dim * 2 * TF * ts);
   size_t oFR = L.take((size_t)nv * cap * 2 * g.dim * TF * ts);
   size_t oidx = L.take(maptotal * 4), olev = L.take(cap * 4), ocoord = L.take(cap * 12), onbr = L.take(cap * 24);
@@ -170,9 +177,9 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t obyt = L.take(8), olevp = L.take(2 * MAXL * 4 * 8), olevf = L.take(2 * MAXL * 4 * 4);
   size_t odone = L.take(8);
   const size_t NW = MRFV_PROPOSER_NWEIGHTS;
-  size_t opf = L.take(3 * maptotal * 4), opl = L.take(maptotal * 4), opa0 = L.take(3 * maptotal * 2);
+  size_t opf = L.take(3 * maptotal * 4), opl = L.take(maptotal * 4), opa0 = L.take(8 * maptotal * 2);
   size_t opa1 = L.take(16 * maptotal * 2), opa2 = L.take(16 * maptotal * 2);
-  size_t opw1 = L.take(16 * 96 * 2), opw2 = L.take(16 * 432 * 2), opw3 = L.take(16 * 432 * 2);
+  size_t opw1 = L.take(16 * 224 * 2), opw2 = L.take(16 * 432 * 2), opw3 = L.take(16 * 432 * 2);
   size_t opb = L.take(3 * 16 * 4), opblob = L.take(4 * NW * 4), opwork = L.take((size_t)kPropWorkPerPos * maptotal * 4), oploss = L.take(8);
   if (c) {
     char *a = c->arena;
@@ -220,6 +227,15 @@ long long capacity_of(const mrfv_config *cfg, long long full) {
 int ntiles_of(long long mtotal) { return (int)((mtotal + scan_tile_entries() - 1) / scan_tile_entries()); }
 
 long long level_blocks(const Geo &g, int l) { return g.mapoff[l + 1] - g.mapoff[l]; }
+// captured step graphs hold kernel arguments and launch shapes: drop them when either changes
+void drop_graphs(mrfv_ctx *c) {
+  for (int v = 0; v < 2; v++)
+    if (c->gexec[v]) {
+      cudaGraphExecDestroy(c->gexec[v]);
+      c->gexec[v] = nullptr;
+    }
+}
+
 int grid_for(long long items, int per_cta, int cap_grid) {
   long long n = (items + per_cta - 1) / per_cta;
   if (n < 1) n = 1;
@@ -251,6 +267,23 @@ struct Seq {
     (void)lts;
     a.stage = coef == 0.5 ? 0 : 1;
     a.words = (coef == 0.5 ? 2 : 3) * c->g.nv;
+    a.C = nullptr; a.C0 = nullptr; a.theta = 0.0;
+    timed_fv(a, false);
+  }
+  // one MUSCL-Hancock stage (Section 2, AMR scheme): Uout = Uin - dt F(Uin); halo
+  // edges that need prediction read level l-1 of Uin (or its time interpolation
+  // from C0 at theta)
+  void fvh(int kind, int l0, int l1, const T *Uin, T *Uout, const T *C0, double theta, int record) {
+    FVArgs<T> a;
+    a.Uin = Uin; a.U0 = Uin; a.Uout = Uout; a.G = G(); a.FR = FR();
+    a.kind = kind; a.l0 = l0; a.l1 = l1; a.coef = 1.0; a.lev = c->lev; a.levf = c->levf; a.record = record;
+    a.stage = 1;
+    a.words = 2 * c->g.nv;
+    a.C = Uin; a.C0 = C0; a.theta = theta;
+    timed_fv(a, true);
+  }
+  // launch a finite-volume stage kernel, bracketed by events when profiling
+  void timed_fv(FVArgs<T> &a, bool hancock) {
     a.bytes = c->prof ? c->dbytes : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->prof) {
@@ -266,7 +299,8 @@ struct Seq {
       c->ev_used += 2;
       cudaEventRecord(e0, c->st);
     }
-    launch_fv<T>(c->g, a, c->fvgrid, c->st);
+    if (hancock) launch_fvh<T>(c->g, a, c->fvhgrid, c->st);
+    else launch_fv<T>(c->g, a, c->fvgrid, c->st);
     if (c->prof) cudaEventRecord(e1, c->st);
     c->nlaunch += 1;
   }
@@ -278,6 +312,19 @@ struct Seq {
   // one midpoint-RK2 step of every leaf with the same dt (Section 2)
   void step_global() {
     int L = c->g.L;
+    if (c->cfg.scheme == MRFV_SCHEME_HANCOCK) {
+      // one stage into Us, leaves copied back, then the correction and projection
+      ghost(1, L, U(), nullptr, 0.0);
+      fvh(LK_LEAF, 0, L, U(), Us(), nullptr, 0.0, 1);
+      launch_copy_level<T>(c->g, LK_LEAF, 0, L, Us(), U(), c->grid, c->st);
+      c->nlaunch += 1;
+      if (L > 0) {
+        launch_reflux<T>(c->g, 0, L - 1, U(), FR(), c->grid, c->st);
+        c->nlaunch += 1;
+      }
+      restrict_all(U());
+      return;
+    }
     ghost(1, L, U(), nullptr, 0.0);
     fv(LK_LEAF, 0, L, U(), U(), Us(), 0.5, 0, 0);
     restrict_all(Us());
@@ -294,12 +341,19 @@ struct Seq {
   void advance(int l, int sub) {
     int L = c->g.L;
     double th1 = 0.5 * sub, th2 = th1 + 0.25;
-    launch_copy_level<T>(c->g, l, U(), U0(), c->grid, c->st);
+    launch_copy_level<T>(c->g, LK_EXIST, l, l, U(), U0(), c->grid, c->st);
     c->nlaunch += 1;
     if (l >= 1) ghost(l, l, U(), U0(), th1);
-    fv(LK_EXIST, l, l, U(), U(), Us(), 0.5, 1, 0);
-    if (l >= 1) ghost(l, l, U(), U0(), th2);
-    fv(LK_EXIST, l, l, Us(), U(), U(), 1.0, 1, sub == 1 ? 2 : 1);
+    if (c->cfg.scheme == MRFV_SCHEME_HANCOCK) {
+      // one stage from the sub-step start, halo at its start time
+      fvh(LK_EXIST, l, l, U(), Us(), U0(), th1, sub == 1 ? 2 : 1);
+      launch_copy_level<T>(c->g, LK_EXIST, l, l, Us(), U(), c->grid, c->st);
+      c->nlaunch += 1;
+    } else {
+      fv(LK_EXIST, l, l, U(), U(), Us(), 0.5, 1, 0);
+      if (l >= 1) ghost(l, l, U(), U0(), th2);
+      fv(LK_EXIST, l, l, Us(), U(), U(), 1.0, 1, sub == 1 ? 2 : 1);
+    }
     if (l < L) {
       advance(l + 1, 0);
       advance(l + 1, 1);
@@ -474,6 +528,8 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   if (cfg->criterion != MRFV_CRIT_MR && cfg->criterion != MRFV_CRIT_GRAD) return fail(nullptr, MRFV_ERR_ARG, "criterion");
   if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0)) return fail(nullptr, MRFV_ERR_ARG, "gamma/cfl");
   if (cfg->pool_blocks < 0) return fail(nullptr, MRFV_ERR_ARG, "pool_blocks");
+  if (cfg->scheme != MRFV_SCHEME_MUSCL_RK2 && cfg->scheme != MRFV_SCHEME_HANCOCK)
+    return fail(nullptr, MRFV_ERR_ARG, "scheme");
   {
     Geo gg;
     long long a, b, f;
@@ -522,9 +578,12 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
-  c->grid = c->nsm * 8;
-  c->bgrid = c->nsm * 16;
-  c->fvgrid = c->nsm * (c->prec == MRFV_FP32 ? fv_ctas_per_sm<float>(cfg->dim) : fv_ctas_per_sm<double>(cfg->dim));
+  c->fv_occupancy = c->prec == MRFV_FP32 ? fv_ctas_per_sm<float>(cfg->dim) : fv_ctas_per_sm<double>(cfg->dim);
+  c->grid = c->nsm * kGridCtasPerSm;
+  c->bgrid = c->nsm * kBlockCtasPerSm;
+  c->fvgrid = c->nsm * c->fv_occupancy;
+  c->fvh_occupancy = c->prec == MRFV_FP32 ? fvh_ctas_per_sm<float>(cfg->dim) : fvh_ctas_per_sm<double>(cfg->dim);
+  c->fvhgrid = c->nsm * c->fvh_occupancy;
   cudaMemsetAsync(c->g.idx, 0xff, c->maptotal * 4, c->st);
   cudaMemsetAsync(c->g.slot_level, 0xff, c->g.cap * 4, c->st);
   cudaMemsetAsync(c->g.loff, 0, LK_NUM * (MAXL + 2) * 4, c->st);
@@ -718,6 +777,7 @@ int mrfv_step(mrfv_ctx *c, double dt, double *dt_out) {
 int mrfv_step_level(mrfv_ctx *c, int level, double dt) {
   if (!c || level < 0 || level > c->g.L || !(dt > 0.0)) return fail(c, MRFV_ERR_ARG, "step_level: arguments");
   if (!c->initialized) return fail(c, MRFV_ERR_STATE, "step_level before init");
+  if (!c->cfg.lts) return fail(c, MRFV_ERR_STATE, "step_level needs cfg.lts (the level-step start states)");
   launch_set_double(c->dsc, dt, c->st);
   launch_level_params(c->g, c->dsc, 1, c->lev, c->levf, c->st);
   c->nlaunch += 2;
@@ -876,12 +936,7 @@ int mrfv_proposer_set_weights(mrfv_ctx *c, const float *w, int64_t n) {
   if (rc == MRFV_OK) {
     c->has_weights = true;
     c->adam_t = 0;
-    // a captured step graph does not contain the proposer path yet
-    for (int v = 0; v < 2; v++)
-      if (c->gexec[v]) {
-        cudaGraphExecDestroy(c->gexec[v]);
-        c->gexec[v] = nullptr;
-      }
+    drop_graphs(c);  // a captured step graph does not contain the proposer path yet
   }
   return rc;
 }
@@ -947,6 +1002,21 @@ int mrfv_proposer_train(mrfv_ctx *c, const float *feat, const uint8_t *target, i
   cudaFree(dt);
   if (loss) *loss = last;
   return rc;
+}
+
+int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm) {
+  if (!c) return MRFV_ERR_ARG;
+  if (grid_ctas_per_sm < 0 || grid_ctas_per_sm > 32 || block_ctas_per_sm < 0 || block_ctas_per_sm > 32 ||
+      fv_ctas_per_sm < 0 || fv_ctas_per_sm > 32)
+    return fail(c, MRFV_ERR_ARG, "set_launch_shape: CTAs per SM outside 0..32");
+  int rc = check_device(c, "mrfv_set_launch_shape");
+  if (rc != MRFV_OK) return rc;
+  c->grid = c->nsm * (grid_ctas_per_sm ? grid_ctas_per_sm : kGridCtasPerSm);
+  c->bgrid = c->nsm * (block_ctas_per_sm ? block_ctas_per_sm : kBlockCtasPerSm);
+  c->fvgrid = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fv_occupancy);
+  c->fvhgrid = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fvh_occupancy);
+  drop_graphs(c);
+  return MRFV_OK;
 }
 
 int mrfv_profile_enable(mrfv_ctx *c, int enable) {

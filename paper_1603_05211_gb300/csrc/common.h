@@ -60,6 +60,11 @@ struct FVArgs {
   int record;     // 0: no registers; 1: store dt_l F on marked faces; 2: add on fine-role faces
   int words;      // algorithmic state words moved per cell (for the byte counter)
   unsigned long long *bytes;  // optional: += algorithmic bytes of this launch
+  // coarse source of halo cells predicted inside the MUSCL-Hancock kernel: level
+  // l-1 of C, or C0 + theta (C - C0) with level-dependent steps (C0 null: C)
+  const T *C;
+  const T *C0;
+  double theta;
 };
 
 // training scratch of the learned proposer, in floats per block position:

@@ -485,17 +485,17 @@ __global__ void k_reflux(Geo g, int l0, int l1, T *__restrict__ A, const T *__re
   }
 }
 
-// copy the blocks of level l (every existing block) from src to dst
+// copy the blocks of list `kind` on levels l0..l1 from src to dst
 template <typename T, int D>
-__global__ void k_copy_level(Geo g, int l, const T *__restrict__ src, T *__restrict__ dst) {
+__global__ void k_copy_level(Geo g, int kind, int l0, int l1, const T *__restrict__ src, T *__restrict__ dst) {
   constexpr int B = (D == 2) ? 64 : 512;
   int b, e;
-  list_range(g, LK_EXIST, l, l, b, e);
+  list_range(g, kind, l0, l1, b, e);
   const long long cap = g.cap;
   for (long long t = (long long)b * B + blockIdx.x * blockDim.x + threadIdx.x; t < (long long)e * B;
        t += (long long)gridDim.x * blockDim.x) {
     int i = (int)(t / B), c = (int)(t % B);
-    int s = g.lists[LK_EXIST * cap + i];
+    int s = g.lists[kind * cap + i];
     for (int v = 0; v < D + 2; v++) {
       long long o = ((long long)v * cap + s) * B + c;
       dst[o] = src[o];

@@ -67,9 +67,9 @@ void launch_reflux(const Geo &g, int l0, int l1, T *A, const T *FR, int grid, cu
   else k_reflux<T, 3><<<grid, 256, 0, st>>>(g, l0, l1, A, FR);
 }
 template <typename T>
-void launch_copy_level(const Geo &g, int l, const T *src, T *dst, int grid, cudaStream_t st) {
-  if (g.dim == 2) k_copy_level<T, 2><<<grid, 256, 0, st>>>(g, l, src, dst);
-  else k_copy_level<T, 3><<<grid, 256, 0, st>>>(g, l, src, dst);
+void launch_copy_level(const Geo &g, int kind, int l0, int l1, const T *src, T *dst, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_copy_level<T, 2><<<grid, 256, 0, st>>>(g, kind, l0, l1, src, dst);
+  else k_copy_level<T, 3><<<grid, 256, 0, st>>>(g, kind, l0, l1, src, dst);
 }
 template <typename T>
 void launch_gradflags(const Geo &g, const T *A, double epsw, uint8_t *gflag, int grid, cudaStream_t st) {
@@ -95,7 +95,7 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
   template void launch_scatter<T>(const Geo &, int, const double *, T *, cudaStream_t);                     \
   template void launch_totals<T>(const Geo &, const T *, double *, int, cudaStream_t);                      \
   template void launch_reflux<T>(const Geo &, int, int, T *, const T *, int, cudaStream_t);                 \
-  template void launch_copy_level<T>(const Geo &, int, const T *, T *, int, cudaStream_t);                  \
+  template void launch_copy_level<T>(const Geo &, int, int, int, const T *, T *, int, cudaStream_t);                  \
   template void launch_gradflags<T>(const Geo &, const T *, double, uint8_t *, int, cudaStream_t);         \
   template void launch_project_level<T>(const Geo &, int, const T *, const double *, double *, cudaStream_t);
 

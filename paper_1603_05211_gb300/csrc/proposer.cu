@@ -114,9 +114,13 @@ __global__ void k_prop_features(Geo g, const T *__restrict__ U, const double *__
   }
 }
 
-__global__ void k_to_bf16(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = __float2bfloat16_rn(in[i]);
+// features (FP32 [3][n]) -> layer-1 input rows (BF16 [n][8], channels 3..7 zero)
+__global__ void k_feat_rows(const float *__restrict__ feat, uint4 *__restrict__ rows, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(feat[p], feat[n + p]);
+    __nv_bfloat162 c = __floats2bfloat162_rn(feat[2 * n + p], 0.f);
+    rows[p] = make_uint4(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&c), 0u, 0u);
+  }
 }
 
 // ---------------------------------------------------------------- tcgen05 helpers
@@ -163,26 +167,36 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 }
 
 // ---------------------------------------------------------------- convolution layer on tensor cores
-// in: BF16 [CIN][npos]; W: BF16 [16][KP] (row = output channel, K index
-// cin*27 + tap, tap = (dz+1)*9 + (dy+1)*3 + (dx+1), zero padded); bias FP32 [16].
-// LAST: logits[p] = acc[0] + bias[0]; otherwise out[n][p] = bf16(relu(acc + bias)).
+// Activations are channel-last BF16 rows, one per position: the layer-1 input
+// has 8 channels (the 3 features, zero padded; 16 B per position), the hidden
+// layers 16 (32 B).  The GEMM's K index is tap-major, k = tap * CIN + channel
+// (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)), so one tap of one row is one or two
+// 16-byte rows of core matrices and is gathered with vector loads.
+// Wcm: the 16 x KP BF16 weight operand, already in the shared-memory
+// core-matrix byte order (k_pack_weights); bias FP32 [16].
+// LAST: logits[p] = acc[0] + bias[0]; otherwise out[p][n] = bf16(relu(acc + bias)).
+constexpr int kConvThreads = 256;  // two threads per tile row: taps 0..13 and 14..26
+
 template <int CIN, int KP, bool LAST>
-__global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16 *__restrict__ in,
-                                                      const __nv_bfloat16 *__restrict__ W,
-                                                      const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out,
-                                                      float *__restrict__ logits) {
+__global__ void __launch_bounds__(kConvThreads) k_prop_conv_tc(Geo g, const __nv_bfloat16 *__restrict__ in,
+                                                               const uint4 *__restrict__ Wcm,
+                                                               const float *__restrict__ bias,
+                                                               __nv_bfloat16 *__restrict__ out,
+                                                               float *__restrict__ logits) {
   constexpr int M = 128, N = 16;
   constexpr int KREAL = CIN * 27;
-  static_assert(KP % 16 == 0 && KP >= KREAL, "K padding");
+  static_assert(CIN == 8 || CIN == 16, "channel-last rows of 16 or 32 bytes");
+  static_assert(KP % 16 == 0 && KP >= KREAL && KP - KREAL < 16, "K padding");
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char *sA = sm;                       // M x KP bf16
   unsigned char *sB = sm + M * KP * 2;          // N x KP bf16
   uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + (M + N) * KP * 2);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
-  int32_t *nbq = reinterpret_cast<int32_t *>(mbar + 2);  // [M][27] neighbour positions of the tile rows
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & (M - 1), half = tid >> 7;
+  const int t0 = half ? 14 : 0, t1 = half ? 27 : 14;
   const long long npos = g.mapoff[g.L + 1];
-  const int dim3d = g.dim == 3;
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -193,11 +207,11 @@ __global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
   }
-  // weights -> shared (core-matrix layout)
-  for (int i = tid; i < N * KP; i += blockDim.x) {
-    int n = i / KP, k = i % KP;
-    *reinterpret_cast<__nv_bfloat16 *>(sB + cm_offset(n, k, KP)) = W[i];
-  }
+  for (int i = tid; i < N * KP * 2 / 16; i += kConvThreads) reinterpret_cast<uint4 *>(sB)[i] = Wcm[i];
+  if (KP > KREAL && half == 0) *reinterpret_cast<uint4 *>(sA + cm_offset(row, KREAL, KP)) = zero;
+  float b[8];
+#pragma unroll
+  for (int n = 0; n < 8; n++) b[n] = bias[8 * (warp >> 2) + n];
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -211,25 +225,45 @@ __global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16
 
   const long long ntiles = (npos + M - 1) / M;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // neighbour positions of the tile rows (-1: outside the level or beyond npos)
-    for (int i = tid; i < M * 27; i += blockDim.x) {
-      int m = i / 27, t = i % 27;
-      long long p = tile * M + m;
-      int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-      long long q = -1;
-      if (p < npos && (dim3d || dz == 0)) q = pos_neighbour(g, pos_level(g, p), p, dx, dy, dz);
-      nbq[i] = (int32_t)q;
+    // this row's position, level and block coordinates
+    const long long p = tile * M + row;
+    int x = 0, y = 0, z = 0, nx = 0, ny = 0, nz = 0;
+    long long base = 0;
+    if (p < npos) {
+      int l = pos_level(g, p);
+      long long u = p - g.mapoff[l];
+      nx = g.nb[l][0];
+      ny = g.nb[l][1];
+      nz = g.nb[l][2];
+      x = (int)(u % nx);
+      y = (int)((u / nx) % ny);
+      z = (int)(u / ((long long)nx * ny));
+      base = g.mapoff[l];
     }
-    __syncthreads();
-    // im2col rows of this tile -> shared
-    for (int i = tid; i < M * KP; i += blockDim.x) {
-      int m = i / KP, k = i % KP;
-      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-      if (k < KREAL) {
-        int q = nbq[m * 27 + k % 27];
-        if (q >= 0) v = in[(long long)(k / 27) * npos + q];
+    // im2col of this row's taps (zero outside the level), in batches of 7 taps
+#pragma unroll 1
+    for (int tb = t0; tb < t1; tb += 7) {
+      uint4 v[7][CIN / 8];
+#pragma unroll
+      for (int j = 0; j < 7; j++) {
+        int t = tb + j;
+        int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        int xx = x + dx, yy = y + dy, zz = z + dz;
+        bool inside = t < t1 && xx >= 0 && yy >= 0 && zz >= 0 && xx < nx && yy < ny && zz < nz;
+        long long qn = inside ? base + xx + (long long)nx * (yy + (long long)ny * zz) : 0;
+        const uint4 *src = reinterpret_cast<const uint4 *>(in) + qn * (CIN / 8);
+#pragma unroll
+        for (int h = 0; h < CIN / 8; h++) v[j][h] = inside ? src[h] : zero;
       }
-      *reinterpret_cast<__nv_bfloat16 *>(sA + cm_offset(m, k, KP)) = v;
+#pragma unroll
+      for (int j = 0; j < 7; j++) {
+        int t = tb + j;
+        if (t < t1) {
+#pragma unroll
+          for (int h = 0; h < CIN / 8; h++)
+            *reinterpret_cast<uint4 *>(sA + cm_offset(row, t * CIN + 8 * h, KP)) = v[j][h];
+        }
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -258,25 +292,25 @@ __global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16
       if (tid == 0) atomicOr(g.err, EB_TIMEOUT);
       break;
     }
-    // accumulator rows 32*warp .. 32*warp+31 (one per lane), 16 columns
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+    // warp w reads accumulator lanes 32*(w%4) .. +31 (one row per lane), columns 8*(w/4) .. +7
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(8 * (warp >> 2))));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    long long p = tile * M + 32 * warp + lane;
-    if (p < npos) {
+    const long long q = tile * M + 32 * (warp & 3) + lane;
+    if (q < npos) {
       if (LAST) {
-        logits[p] = __uint_as_float(r[0]) + bias[0];
+        if (warp < 4) logits[q] = __uint_as_float(r[0]) + b[0];
       } else {
+        uint32_t pk[4];
 #pragma unroll
-        for (int n = 0; n < N; n++) {
-          float v = __uint_as_float(r[n]) + bias[n];
-          out[(long long)n * npos + p] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+        for (int n = 0; n < 4; n++) {
+          float lo = __uint_as_float(r[2 * n]) + b[2 * n], hi = __uint_as_float(r[2 * n + 1]) + b[2 * n + 1];
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(lo > 0.f ? lo : 0.f, hi > 0.f ? hi : 0.f);
+          pk[n] = *reinterpret_cast<uint32_t *>(&h2);
         }
+        reinterpret_cast<uint4 *>(out)[q * 2 + (warp >> 2)] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -291,8 +325,10 @@ __global__ void __launch_bounds__(128) k_prop_conv_tc(Geo g, const __nv_bfloat16
 
 template <int KP>
 constexpr size_t conv_smem() {
-  return (size_t)(128 + 16) * KP * 2 + 16 + 128 * 27 * 4;
+  return (size_t)(128 + 16) * KP * 2 + 16;
 }
+constexpr int kKP1 = 224;  // layer 1: 27 taps x 8 channels = 216, padded to a multiple of 16
+constexpr int kKP2 = 432;  // layers 2, 3: 27 taps x 16 channels
 
 // ---------------------------------------------------------------- marking
 // Positions of level >= 1 whose parent exists and whose logit is positive are
@@ -442,18 +478,22 @@ __global__ void k_adam(float *__restrict__ w, const float *__restrict__ grad, fl
   }
 }
 
-// FP32 master weights (host blob order) -> BF16 GEMM operands [16][KP] and FP32 biases [16]
+// FP32 master weights (host blob order, [co][ci][tap]) -> the BF16 weight operands
+// in shared-memory core-matrix byte order with the tap-major K index of
+// k_prop_conv_tc (layer 1: 16 x kKP1, channels padded to 8; layers 2, 3:
+// 16 x kKP2, layer 3's output channels 1..15 zero) and FP32 biases [16].
 __global__ void k_pack_weights(const float *__restrict__ blob, __nv_bfloat16 *w1, float *b1, __nv_bfloat16 *w2,
                                float *b2, __nv_bfloat16 *w3, float *b3) {
   const float *W1 = blob, *B1 = W1 + 16 * 81, *W2 = B1 + 16, *B2 = W2 + 16 * 432, *W3 = B2 + 16, *B3 = W3 + 432;
-  for (int i = threadIdx.x; i < 16 * 96; i += blockDim.x) {
-    int n = i / 96, k = i % 96;
-    w1[i] = __float2bfloat16_rn(k < 81 ? W1[n * 81 + k] : 0.f);
+  for (int i = threadIdx.x; i < 16 * kKP1; i += blockDim.x) {
+    int n = i / kKP1, k = i % kKP1, t = k / 8, ci = k % 8;
+    float v = (t < 27 && ci < 3) ? W1[(n * 3 + ci) * 27 + t] : 0.f;
+    w1[cm_offset(n, k, kKP1) / 2] = __float2bfloat16_rn(v);
   }
-  for (int i = threadIdx.x; i < 16 * 432; i += blockDim.x) {
-    w2[i] = __float2bfloat16_rn(W2[i]);
-    int n = i / 432, k = i % 432;
-    w3[i] = __float2bfloat16_rn(n == 0 ? W3[k] : 0.f);
+  for (int i = threadIdx.x; i < 16 * kKP2; i += blockDim.x) {
+    int n = i / kKP2, k = i % kKP2, t = k / 16, ci = k % 16;
+    w2[cm_offset(n, k, kKP2) / 2] = __float2bfloat16_rn(W2[(n * 16 + ci) * 27 + t]);
+    w3[cm_offset(n, k, kKP2) / 2] = __float2bfloat16_rn(n == 0 ? W3[ci * 27 + t] : 0.f);
   }
   for (int i = threadIdx.x; i < 16; i += blockDim.x) {
     b1[i] = B1[i];
@@ -475,24 +515,31 @@ template void launch_prop_features<double>(const Geo &, const double *, const do
                                            float *, int, cudaStream_t);
 
 void prop_setup() {
-  cudaFuncSetAttribute(k_prop_conv_tc<3, 96, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<96>());
-  cudaFuncSetAttribute(k_prop_conv_tc<16, 432, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)conv_smem<432>());
-  cudaFuncSetAttribute(k_prop_conv_tc<16, 432, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)conv_smem<432>());
+  cudaFuncSetAttribute(k_prop_conv_tc<8, kKP1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)conv_smem<kKP1>());
+  cudaFuncSetAttribute(k_prop_conv_tc<16, kKP2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)conv_smem<kKP2>());
+  cudaFuncSetAttribute(k_prop_conv_tc<16, kKP2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)conv_smem<kKP2>());
 }
 
-// features (float [3][n]) -> logits (float [n]) through the three layers on tensor cores
+// features (float [3][n]) -> logits (float [n]) through the three layers on tensor
+// cores; a0: BF16 [n][8], a1, a2: BF16 [n][16]
 void launch_prop_infer(const Geo &g, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
                        const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
                        const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaStream_t st) {
   long long n = g.mapoff[g.L + 1];
   long long tiles = (n + 127) / 128;
-  int grid = (int)(tiles < nsm ? tiles : nsm);
-  k_to_bf16<<<256, 256, 0, st>>>(feat, a0, 3 * n);
-  k_prop_conv_tc<3, 96, false><<<grid, 128, conv_smem<96>(), st>>>(g, a0, w1, b1, a1, nullptr);
-  k_prop_conv_tc<16, 432, false><<<grid, 128, conv_smem<432>(), st>>>(g, a1, w2, b2, a2, nullptr);
-  k_prop_conv_tc<16, 432, true><<<grid, 128, conv_smem<432>(), st>>>(g, a2, w3, b3, nullptr, logits);
+  // layer 1 fits three CTAs per SM in shared memory, layers 2 and 3 one
+  int grid1 = (int)(tiles < 3 * nsm ? tiles : 3 * nsm), grid2 = (int)(tiles < nsm ? tiles : nsm);
+  long long fb = (n + 255) / 256;
+  k_feat_rows<<<(int)(fb < 4 * nsm ? fb : 4 * nsm), 256, 0, st>>>(feat, reinterpret_cast<uint4 *>(a0), n);
+  k_prop_conv_tc<8, kKP1, false><<<grid1, kConvThreads, conv_smem<kKP1>(), st>>>(
+      g, a0, reinterpret_cast<const uint4 *>(w1), b1, a1, nullptr);
+  k_prop_conv_tc<16, kKP2, false><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
+      g, a1, reinterpret_cast<const uint4 *>(w2), b2, a2, nullptr);
+  k_prop_conv_tc<16, kKP2, true><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
+      g, a2, reinterpret_cast<const uint4 *>(w3), b3, nullptr, logits);
 }
 
 void launch_prop_mark(const Geo &g, const float *logits, uint8_t *need, int grid, cudaStream_t st) {

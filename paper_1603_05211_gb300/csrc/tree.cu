@@ -403,28 +403,37 @@ __global__ void k_advance(Geo g, double *t, const double *dt, double factor, lon
 }
 
 // ---------------------------------------------------------------- launchers
+// The tree kernels loop over fixed domains (the dense block maps, the Morton
+// positions, the scan tiles): a grid larger than the domain only adds CTAs that
+// find no work, and dispatching them costs time.
+static int fit(long long items, int per_cta, int grid) {
+  long long n = (items + per_cta - 1) / per_cta;
+  if (n < 1) n = 1;
+  return (int)(n < grid ? n : grid);
+}
+
 void launch_need_mark(const Geo &g, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t st) {
-  k_need_mark<<<grid, 256, 0, st>>>(g, sig, need, crit);
+  k_need_mark<<<fit(g.mapoff[g.L + 1], 256, grid), 256, 0, st>>>(g, sig, need, crit);
 }
 void launch_need_close(const Geo &g, int l, uint8_t *need, int grid, cudaStream_t st) {
   k_need_close<<<grid, 256, 0, st>>>(g, l, need);
 }
 void launch_free(const Geo &g, const uint8_t *need, int32_t *fs, int *ft, int grid, cudaStream_t st) {
-  k_free<<<grid, 256, 0, st>>>(g, need, fs, ft);
+  k_free<<<fit(g.mapoff[g.L + 1], 256, grid), 256, 0, st>>>(g, need, fs, ft);
 }
 void launch_alloc(const Geo &g, const uint8_t *need, int32_t *fs, int *ft, int32_t *nl, int *nn, int grid,
                   cudaStream_t st) {
-  k_alloc<<<grid, 256, 0, st>>>(g, need, fs, ft, nl, nn);
+  k_alloc<<<fit(g.mapoff[g.L + 1], 256, grid), 256, 0, st>>>(g, need, fs, ft, nl, nn);
 }
 void launch_init_freestack(int32_t *fs, int *ft, long long cap, int grid, cudaStream_t st) {
   k_init_freestack<<<grid, 256, 0, st>>>(fs, ft, cap);
 }
 void launch_rebuild_lists(const Geo &g, uint8_t *kbits, int32_t *tcount, int32_t *toff, int ntiles, int grid,
                           cudaStream_t st) {
-  k_classify<<<grid, 256, 0, st>>>(g, kbits);
-  k_tile_count<<<grid, SCAN_NT, 0, st>>>(g, kbits, tcount, ntiles);
+  k_classify<<<fit(g.moff[g.L + 1], 256, grid), 256, 0, st>>>(g, kbits);
+  k_tile_count<<<fit(ntiles, 1, grid), SCAN_NT, 0, st>>>(g, kbits, tcount, ntiles);
   k_tile_scan<<<1, 1024, 0, st>>>(g, tcount, toff, ntiles);
-  k_scatter<<<grid, SCAN_NT, 0, st>>>(g, kbits, toff, ntiles);
+  k_scatter<<<fit(ntiles, 1, grid), SCAN_NT, 0, st>>>(g, kbits, toff, ntiles);
 }
 int scan_tile_entries() { return SCAN_TILE; }
 

@@ -283,3 +283,88 @@ def test_errors_are_reported(mrfv):
     with pytest.raises(mrfv.MRFVError) as e:
         s.set_tree(bad)
     assert e.value.code == mrfv.ERR_ARG
+
+
+def test_state_pool_and_nonphysical_errors(mrfv):
+    # level-recursion step without the LTS start-state buffer
+    s = mrfv.Solver(dim=2, levels=2, base_blocks=(1, 1, 1))
+    s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(0))
+    with pytest.raises(mrfv.MRFVError) as e:
+        s.step_level(0, 1e-4)
+    assert e.value.code == mrfv.ERR_STATE
+    # a pool smaller than the full tree cannot be initialised
+    p = mrfv.Solver(dim=2, levels=3, base_blocks=(2, 2, 1), pool_blocks=4)
+    with pytest.raises(mrfv.MRFVError) as e:
+        p.init_state(mi.IC_QUADRANTS, mi.quadrant_params(0))
+    assert e.value.code == mrfv.ERR_POOL_FULL
+    # a cell with negative density is reported by the CFL reduction
+    for prec in ("fp64", "fp32"):
+        u = mrfv.Solver(dim=2, precision=prec, levels=1, base_blocks=(2, 2, 1))
+        u.init_state(mi.IC_QUADRANTS, mi.quadrant_params(0))
+        q, _ = u.download_level(0)
+        q[0, 5, 7] = -1.0
+        u.upload_level(0, q)
+        with pytest.raises(mrfv.MRFVError) as e:
+            u.step(0.0)
+        assert e.value.code == mrfv.ERR_NONPHYSICAL
+
+
+def _finest_rel_l1(s, o, make_oracle):
+    """Relative L1 of the finest-level projection of the GPU state against the
+    oracle's, with the GPU tree and data loaded into a fresh oracle."""
+    o2 = make_oracle()
+    for l in range(o.levels):
+        o2.set_exist(l, s.get_tree(l))
+    for l in range(o.levels):
+        o2.set_level(l, s.download_level(l)[0])
+    fg = o2.project_finest()[0]
+    fo = o.project_finest()[0]
+    return np.abs(fg - fo).sum() / np.abs(fo).sum()
+
+
+def test_amr2d_fp32_base128_levels4_lts_full_size_steps(mrfv):
+    """The gradient-flagged AMR workload (base 128^2, 4 levels, local time
+    stepping) at full size, two coarse steps (16 finest sub-steps)."""
+    P = mi.quadrant_params(0)
+    kw = dict(dim=2, precision="fp32", levels=4, base_blocks=(16, 16, 1), adapt=True, criterion="grad", lts=True)
+    s = mrfv.Solver(**kw)
+    s.init_state(mi.IC_QUADRANTS, P)
+
+    def make():
+        o = oracle.Oracle(2, 4, (16, 16, 1))
+        o.init(mi.IC_QUADRANTS, P)
+        return o
+
+    o = make()
+    o.adapt(oracle.CRIT_GRAD, precision=1)
+    T0 = o.totals()
+    for _ in range(2):
+        dt = o.dt(0.5, True)
+        s.step(dt)
+        o.step(dt, True)
+        o.adapt(oracle.CRIT_GRAD, precision=1)
+    assert _finest_rel_l1(s, o, make) <= 2e-4
+    assert np.all(np.abs(s.totals() - o.totals()) <= 1e-6 * np.abs(T0).max())
+
+
+def test_blast3d_fp32_levels5_full_size_step(mrfv):
+    """The 3D ellipsoidal blast (5 levels, 256^3 finest) at full size, one step."""
+    P = mi.ellipsoid_params(0)
+    lo, hi = (-1, -1, -1), (1, 1, 1)
+    s = mrfv.Solver(dim=3, precision="fp32", levels=5, base_blocks=(2, 2, 2), lo=lo, hi=hi, adapt=True, eps=1e-3)
+    s.init_state(mi.IC_ELLIPSOID, P)
+
+    def make():
+        o = oracle.Oracle(3, 5, (2, 2, 2), lo=lo, hi=hi)
+        o.init(mi.IC_ELLIPSOID, P)
+        return o
+
+    o = make()
+    o.adapt(oracle.CRIT_MR, 1e-3, precision=1)
+    T0 = o.totals()
+    dt = o.dt(0.5)
+    s.step(dt)
+    o.step(dt)
+    o.adapt(oracle.CRIT_MR, 1e-3, precision=1)
+    assert _finest_rel_l1(s, o, make) <= 2e-4
+    assert np.all(np.abs(s.totals() - o.totals()) <= 1e-6 * np.abs(T0).max())
