@@ -28,6 +28,8 @@ CRIT_MR = 0
 CRIT_GRAD = 1
 SCHEME_MUSCL_RK2 = 0  # MUSCL / van Albada / AUSM+ / explicit midpoint RK2 (the MR scheme, Section 2)
 SCHEME_HANCOCK = 1    # MUSCL-Hancock / Minmod / AUSMDV (the AMR scheme, Section 2)
+CLUSTER_ROWS = 0      # gradient flags clustered in runs along the first direction
+CLUSTER_BR = 1        # Berger-Rigoutsos clustering into boxes (Section 2.2)
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +78,8 @@ def _load():
             "orc_physical_flux": (None, [P, I, dp, dp]),
             "orc_flux_ausmdv": (None, [P, I, dp, dp, dp]),
             "orc_set_scheme": (I, [P, I]),
+            "orc_set_clustering": (I, [P, I]),
+            "orc_br_cluster": (None, [P, I, u8, D, u8]),
             "orc_predict": (D, [P, I, dp, I, I, I, I]),
         }
         for name, (res, args) in sig.items():
@@ -99,7 +103,8 @@ class Oracle:
     ``base_blocks * 2^l`` blocks of 8 cells per dimension."""
 
     def __init__(self, dim: int, levels: int, base_blocks, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
-                 gamma: float = 1.4, bc: int = BC_TRANSMISSIVE, scheme: int = SCHEME_MUSCL_RK2):
+                 gamma: float = 1.4, bc: int = BC_TRANSMISSIVE, scheme: int = SCHEME_MUSCL_RK2,
+                 clustering: int = CLUSTER_ROWS):
         lib = _load()
         nb = (ctypes.c_int * 3)(*[int(b) for b in (list(base_blocks) + [1, 1, 1])[:3]])
         lo3 = (ctypes.c_double * 3)(*[float(x) for x in (list(lo) + [0.0] * 3)[:3]])
@@ -111,6 +116,8 @@ class Oracle:
         if lib.orc_set_scheme(self._h, scheme) != 0:
             raise ValueError("oracle: bad scheme")
         self.scheme = scheme
+        if lib.orc_set_clustering(self._h, clustering) != 0:
+            raise ValueError("oracle: bad clustering")
         self.dim, self.levels, self.L, self.nv = dim, levels, levels - 1, dim + 2
         self.base_blocks = tuple(int(b) for b in (list(base_blocks) + [1, 1, 1])[:3])
         self.lo = tuple(float(x) for x in (list(lo) + [0.0] * 3)[:3])
@@ -216,6 +223,14 @@ class Oracle:
         a[: self.nv] = ql; b[: self.nv] = qr
         self.lib.orc_flux_ausmdv(self._h, nd, _dp(a), _dp(b), _dp(F))
         return F[: self.nv]
+
+    def br_cluster(self, l: int, flags, eta: float) -> np.ndarray:
+        """Berger-Rigoutsos boxes of a block flag map of level l (shape blocks_shape(l))."""
+        fl = np.ascontiguousarray(flags, dtype=np.uint8)
+        assert fl.shape == self.blocks_shape(l)
+        out = np.zeros_like(fl)
+        self.lib.orc_br_cluster(self._h, l, _u8(fl), eta, _u8(out))
+        return out
 
     def physical_flux(self, nd: int, q) -> np.ndarray:
         a = np.zeros(5); F = np.zeros(5)

@@ -41,10 +41,12 @@ enum { O_IC_QUADRANTS = 0, O_IC_ELLIPSOID = 1, O_IC_SHOCKTUBE = 2, O_IC_UNIFORM 
        O_IC_WAVE = 4, O_IC_ROTATED_ELLIPSOID = 5 };
 
 enum { O_SCHEME_MUSCL_RK2 = 0, O_SCHEME_HANCOCK = 1 };
+enum { O_CLUSTER_ROWS = 0, O_CLUSTER_BR = 1 };
 
 typedef struct {
   int dim, nv, L, bc;
   int scheme;         /* O_SCHEME_*: the MR scheme (default) or the AMR scheme of Section 2 */
+  int clustering;     /* O_CLUSTER_*: clustering of gradient flags (Section 2.2) */
   double gamma;
   double lo[3], hi[3];
   int nb[OMAXL][3];   /* blocks per dimension (1 in unused dimensions) */
@@ -1053,6 +1055,132 @@ static int grad_flag_cell(const orc *o, int l, const double *E, int i, int j, in
   return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Berger-Rigoutsos clustering (Section 2.2, as in AMROC; Berger and Rigoutsos
+   1991) of the flagged blocks fl of level l into boxes of blocks; every block of
+   an accepted box is flagged for refinement in o->sig[l].  Reading on the block
+   grid (the paper gives no details):
+     - a box is first shrunk to the bounding box of its flagged blocks (dropped
+       when it holds none);
+     - it is accepted when flagged/volume >= eta and no side exceeds
+       O_BR_MAX_SIDE blocks (64 cells, the largest patch side of the AMR
+       workload);
+     - an efficient box that is too long is bisected across its longest side;
+     - otherwise it is cut at a hole (a slice with no flag) of the signatures
+       (the counts of flags per slice along each direction): the first direction,
+       in order, that has one, at the hole nearest the middle; else at the
+       strongest inflection of the signatures (where the second difference
+       changes sign, strength = the jump of the second difference), ties to the
+       lower direction, then nearer the middle, then lower index; else the
+       longest side (ties: lower direction) is bisected;
+     - a cut at slice i gives [lo, i] and [i+1, hi]; both parts are clustered
+       again. */
+#define O_BR_MAX_SIDE 8
+typedef struct { int lo[3], hi[3]; } obox;
+
+static long br_flags_in(const orc *o, int l, const uint8_t *fl, const obox *b, obox *bb) {
+  long cnt = 0;
+  for (int d = 0; d < 3; d++) { bb->lo[d] = b->hi[d] + 1; bb->hi[d] = b->lo[d] - 1; }
+  for (int k = b->lo[2]; k <= b->hi[2]; k++)
+    for (int j = b->lo[1]; j <= b->hi[1]; j++)
+      for (int i = b->lo[0]; i <= b->hi[0]; i++) {
+        if (!fl[bidx(o, l, i, j, k)]) continue;
+        int c[3] = {i, j, k};
+        cnt++;
+        for (int d = 0; d < 3; d++) {
+          if (c[d] < bb->lo[d]) bb->lo[d] = c[d];
+          if (c[d] > bb->hi[d]) bb->hi[d] = c[d];
+        }
+      }
+  return cnt;
+}
+
+/* flags in slice s of box b along direction d */
+static long br_slice(const orc *o, int l, const uint8_t *fl, const obox *b, int d, int s) {
+  obox t = *b;
+  t.lo[d] = s;
+  t.hi[d] = s;
+  long cnt = 0;
+  for (int k = t.lo[2]; k <= t.hi[2]; k++)
+    for (int j = t.lo[1]; j <= t.hi[1]; j++)
+      for (int i = t.lo[0]; i <= t.hi[0]; i++) cnt += fl[bidx(o, l, i, j, k)] ? 1 : 0;
+  return cnt;
+}
+
+static void br_box(orc *o, int l, const uint8_t *fl, obox b, double eta) {
+  obox bb;
+  long cnt = br_flags_in(o, l, fl, &b, &bb);
+  if (cnt == 0) return;
+  b = bb;
+  long vol = 1;
+  int longest = 0, big = 0;
+  for (int d = 0; d < o->dim; d++) {
+    int side = b.hi[d] - b.lo[d] + 1;
+    vol *= side;
+    if (side > O_BR_MAX_SIDE) big = 1;
+    if (side > b.hi[longest] - b.lo[longest] + 1) longest = d;
+  }
+  int efficient = (double)cnt >= eta * (double)vol;
+  if (efficient && !big) {
+    for (int k = b.lo[2]; k <= b.hi[2]; k++)
+      for (int j = b.lo[1]; j <= b.hi[1]; j++)
+        for (int i = b.lo[0]; i <= b.hi[0]; i++) o->sig[l][bidx(o, l, i, j, k)] = 1;
+    return;
+  }
+  int cd = -1, cut = 0;
+  if (!efficient) {
+    /* holes */
+    for (int d = 0; d < o->dim && cd < 0; d++) {
+      int best = -1;
+      for (int s = b.lo[d] + 1; s < b.hi[d]; s++) {
+        if (br_slice(o, l, fl, &b, d, s) != 0) continue;
+        if (best < 0 || abs(2 * s - (b.lo[d] + b.hi[d])) < abs(2 * best - (b.lo[d] + b.hi[d]))) best = s;
+      }
+      if (best >= 0) { cd = d; cut = best; }
+    }
+    /* inflections */
+    if (cd < 0) {
+      long bstr = 0;
+      for (int d = 0; d < o->dim; d++) {
+        int n = b.hi[d] - b.lo[d] + 1;
+        if (n < 4) continue;
+        long *S = (long *)malloc(sizeof(long) * (size_t)n);
+        for (int s = 0; s < n; s++) S[s] = br_slice(o, l, fl, &b, d, b.lo[d] + s);
+        for (int s = 1; s + 2 < n; s++) {
+          long l1 = S[s - 1] - 2 * S[s] + S[s + 1];
+          long l2 = S[s] - 2 * S[s + 1] + S[s + 2];
+          if (!((l1 < 0 && l2 > 0) || (l1 > 0 && l2 < 0))) continue;
+          long str = labs(l2 - l1);
+          int pos = b.lo[d] + s; /* cut between s and s + 1 */
+          int better = 0;
+          if (cd < 0 || str > bstr) better = 1;
+          else if (str == bstr && d == cd) {
+            int dm = abs(2 * pos + 1 - (b.lo[d] + b.hi[d])), cm = abs(2 * cut + 1 - (b.lo[d] + b.hi[d]));
+            if (dm < cm) better = 1;
+          }
+          if (better) { cd = d; cut = pos; bstr = str; }
+        }
+        free(S);
+      }
+    }
+  }
+  if (cd < 0) {
+    cd = longest;
+    cut = (b.lo[cd] + b.hi[cd]) / 2;
+  }
+  obox a = b, c = b;
+  a.hi[cd] = cut;
+  c.lo[cd] = cut + 1;
+  br_box(o, l, fl, a, eta);
+  br_box(o, l, fl, c, eta);
+}
+
+static void br_cluster_level(orc *o, int l, const uint8_t *fl, double eta) {
+  obox b;
+  for (int d = 0; d < 3; d++) { b.lo[d] = 0; b.hi[d] = o->nb[l][d] - 1; }
+  br_box(o, l, fl, b, eta);
+}
+
 static void grad_flags(orc *o, double epsw, double eta) {
   int L = o->L, dim = o->dim;
   for (int l = 0; l <= L; l++) { memset(o->sig[l], 0, (size_t)o->nblk[l]); }
@@ -1078,6 +1206,12 @@ static void grad_flags(orc *o, double epsw, double eta) {
               }
           fl[bidx(o, l, bi, bj, bk)] = (uint8_t)hit;
         }
+    if (o->clustering == O_CLUSTER_BR) {
+      br_cluster_level(o, l, fl, eta);
+      free(fl);
+      free(E);
+      continue;
+    }
     /* row clustering along the first direction */
     for (int bk = 0; bk < o->nb[l][2]; bk++)
       for (int bj = 0; bj < o->nb[l][1]; bj++) {
@@ -1246,6 +1380,21 @@ void orc_flux_ausmdv(orc *o, int nd, const double *Ql, const double *Qr, double 
   cons_to_prim(o, Qr, wr);
   if (o->dim == 2) { wl[3] = 0.0; wr[3] = 0.0; }
   ausmdv(o, nd, wl, wr, F);
+}
+
+/* Berger-Rigoutsos clustering of a given flag map of level l (tests of the
+   clustering alone): out = the blocks of the accepted boxes */
+void orc_br_cluster(orc *o, int l, const uint8_t *fl, double eta, uint8_t *out) {
+  memset(o->sig[l], 0, (size_t)o->nblk[l]);
+  br_cluster_level(o, l, fl, eta);
+  memcpy(out, o->sig[l], (size_t)o->nblk[l]);
+}
+
+/* clustering of gradient flags: 0 = runs along the first direction, 1 = Berger-Rigoutsos */
+int orc_set_clustering(orc *o, int mode) {
+  if (mode != O_CLUSTER_ROWS && mode != O_CLUSTER_BR) return -1;
+  o->clustering = mode;
+  return 0;
 }
 
 /* select the finite-volume scheme: 0 = MUSCL / van Albada / AUSM+ / RK2 midpoint
