@@ -56,6 +56,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_bf16_tflops():
+    """Burst bf16 tensor peak (a kernel timed alone), measured, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -117,10 +126,12 @@ def make_solver(m, stream=None):
     return s
 
 
-def uniform_roofline(m, torch, hbm_peak, steps=6):
+def uniform_roofline(m, torch, hbm_peak, steps=6, scheme="muscl_rk2"):
     """Stage kernel alone on a uniform 8192^2 single-precision grid (state 1 GB per
-    buffer, far above L2): algorithmic bytes per launch / CUDA-event duration."""
-    s = m.Solver(dim=2, precision="fp32", levels=1, base_blocks=(1024, 1024, 1), cfl=0.5)
+    buffer, far above L2): algorithmic bytes per launch / CUDA-event duration.
+    MUSCL-Hancock: one stage per step, 2 nv words per cell."""
+    s = m.Solver(dim=2, precision="fp32", levels=1, base_blocks=(1024, 1024, 1), cfl=0.4 if scheme == "hancock" else 0.5,
+                 scheme=scheme)
     s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(SEED))
     for _ in range(2):
         s.step(0.0, sync=False)
@@ -130,26 +141,33 @@ def uniform_roofline(m, torch, hbm_peak, steps=6):
     p = s.profile_read()
     s.profile_enable(False)
     achieved = p["fv_bytes"] / (p["fv_ms"] * 1e-3) / 1e9
-    out = {"workload": "uniform2d_fp32_8192", "bound": "hbm", "achieved": round(achieved, 1),
+    out = {"workload": "uniform2d_fp32_8192", "scheme": scheme, "bound": "hbm", "achieved": round(achieved, 1),
            "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
            "launches": p["fv_launches"], "avg_launch_ms": round(p["fv_ms"] / max(1, p["fv_launches"]), 4),
-           "cell_updates_per_s": 8192 * 8192 * steps / (p["fv_ms"] * 1e-3)}
+           "cell_updates_per_s": 8192 * 8192 * steps / (p["fv_ms"] * 1e-3),
+           "kernel": "k_fvs<float,2,true> (MUSCL-Hancock stage)" if scheme == "hancock" else "k_fv<float,2> (pencil)"}
     s.close()
     del s
     torch.cuda.empty_cache()
     return out
 
 
-def timed_steps(s, n: int, torch, stream) -> float:
-    """GPU time (ms) of n asynchronous steps, CUDA events on the solver's stream."""
+def timed_steps(s, n: int, torch, stream, dt: float = 0.0) -> float:
+    """GPU time (ms) of n asynchronous steps (dt <= 0: CFL steps), CUDA events on
+    the solver's stream.  The first step (which captures the step graph on the
+    host) runs untimed and counts as the mean of the others."""
+    if n <= 1:
+        s.step(dt, sync=True)
+        return 0.0
+    s.step(dt, sync=False)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(stream)
-    for _ in range(n):
-        s.step(0.0, sync=False)
+    for _ in range(n - 1):
+        s.step(dt, sync=False)
     b.record(stream)
     torch.cuda.synchronize()
-    return a.elapsed_time(b)
+    return a.elapsed_time(b) * n / (n - 1)
 
 
 def count_steps_to_end(make, t_end: float) -> int:
@@ -492,6 +510,10 @@ def run_ours(args):
             roof_u = uniform_roofline(m, torch, hbm_peak)
         except Exception as e:  # noqa: BLE001
             roof_u = {"error": str(e)}
+        try:
+            roof_h = uniform_roofline(m, torch, hbm_peak, steps=4, scheme="hancock")
+        except Exception as e:  # noqa: BLE001
+            roof_h = {"error": str(e)}
         # end to end through the C interface: host initial state in, host state out
         e2e = run_e2e(m, torch, stream, args.steps)
         try:
@@ -509,7 +531,7 @@ def run_ours(args):
                        "ic": "seeded four-quadrant Riemann (seed 0)", "l2": "flushed between timed steps",
                        "leaves_per_step": cells / args.steps / 64, "parallelism": f"replicas x{world}"},
             "roofline": roof,
-            "roofline_uniform": roof_u,
+            "roofline_uniform": roof_u, "roofline_hancock": roof_h,
             "cpu_baseline": {"value": ob, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                              "sample": f"{osteps} FP64 oracle steps of the same workload from t=0 ({osec:.1f} s)"},
             "e2e": e2e,
@@ -558,6 +580,139 @@ def run_e2e(m, torch, stream, steps):
             "d2h_bytes_per_step": (out_bytes + 8 * steps) / steps}
 
 
+def run_proposer(args):
+    """The learned proposer's tensor-core convolution on the 3D blast hierarchy
+    (levels3d levels, every block position of every level): CUDA-event time of the
+    three tcgen05 layers per inference, algorithmic flops, fraction of the measured
+    bf16 peak.  The GEMMs are 128 positions x 16 channels x K in {216, 432}: the
+    kernel is bound by gathering its im2col rows, not by the tensor pipe."""
+    import numpy as np
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    L = args.levels3d
+    s = blast3d(m, stream, L, 1.0, proposer=False)
+    for _ in range(5):
+        s.step(0.0, sync=False)
+    s.analyse(WL["eps"])
+    rng = np.random.default_rng(0)
+    s.proposer_set_weights((rng.normal(0, 1, m.PROPOSER_NWEIGHTS) * 0.05).astype(np.float32))
+    for _ in range(max(3, args.warmup)):
+        s.proposer_infer()
+    s.profile_enable(True)
+    n = max(1, args.steps)
+    for _ in range(n):
+        s.proposer_infer()
+    p = s.profile_read()
+    s.profile_enable(False)
+    peak, kind = measured_bf16_tflops()
+    tf = p["prop_flops"] / (p["prop_ms"] * 1e-3) / 1e12
+    npos = s.positions
+    print(json.dumps({"case": f"proposer_conv_blast3d_L{L - 1}", "positions": npos, "inferences": n,
+                      "conv_us_per_inference": 1000.0 * p["prop_ms"] / n,
+                      "roofline": {"bound": "tensor", "achieved": round(tf, 3), "peak": peak, "unit": "TFLOP/s",
+                                   "frac": round(tf / peak, 6), "peak_kind": kind,
+                                   "kernel": "k_prop_conv_tc (tcgen05.mma kind::f16, 3 layers)"}}), flush=True)
+    s.close()
+
+
+def run_laxliu(args):
+    """The paper's 2D benchmark (Section 4.1, Tables 2-4): Lax-Liu configuration 6
+    on [0,1]^2 to t_e = 0.25 with N_I = 160 * 2^(L-7) fixed steps at scale levels
+    L = 7..10 (finest 2^L cells per side), single precision on the GPU.
+    FV: uniform 2^L grid (MR scheme: van Albada / AUSM+ / RK2; AMR scheme:
+    MUSCL-Hancock / Minmod / AUSMDV).  MR, MRLT: eps = 0.0023; AMR, AMRLT:
+    density-gradient flags eps_rho = 0.05 clustered by Berger-Rigoutsos
+    (eta 0.8), the AMR scheme.  Reference: the AMR scheme on a uniform 4096^2
+    grid, 5120 steps, restricted by cell means.  Reports L1(rho), rates,
+    perturbation, accumulated cells and leaves (with compression), GPU time and
+    time compression against the FV run of the same scheme."""
+    import numpy as np
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    P = mi.laxliu6_params()
+    te = 0.25
+    Ls = [int(x) for x in args.laxliu_levels.split(",")]
+
+    def solver(n_cells, levels, scheme, adapt=False, lts=False, crit="mr", eps=0.0023):
+        return m.Solver(dim=2, precision="fp32", levels=levels, base_blocks=(n_cells // (8 << (levels - 1)),) * 2 + (1,),
+                        adapt=adapt, lts=lts, criterion=crit, eps=eps, eps_w=0.05, eta_tol=0.8, cfl=0.5,
+                        stream=stream, scheme=scheme, clustering="br")
+
+    # reference: the AMR scheme on 4096^2, 5120 steps
+    nref = args.laxliu_ref
+    r = solver(nref, 1, "hancock")
+    r.init_state(mi.IC_QUADRANTS, P)
+    nr_steps = 5120 * nref // 4096
+    for _ in range(nr_steps):
+        r.step(te / nr_steps, sync=False)
+    rho_ref = r.download_level(0)[0][0]
+    r.close()
+    torch.cuda.empty_cache()
+    out = {"case": "laxliu6", "t_end": te, "reference": {"grid": nref, "steps": nr_steps, "scheme": "hancock"},
+           "rows": []}
+
+    def l1_at(rho, n):
+        k = nref // n
+        ref = rho_ref.reshape(n, k, n, k).mean(axis=(1, 3))
+        return float(np.abs(rho - ref).sum() / (n * n))
+
+    for L in Ls:
+        n = 1 << L
+        NI = 160 << (L - 7)
+        dt = te / NI
+        levels = L - 2  # blocks of 8 cells: level 0 has one block
+        row = {"L": L, "N": n, "N_I": NI}
+        for scheme, fvname in (("muscl_rk2", "FV_MR"), ("hancock", "FV_AMR")):
+            u = solver(n, 1, scheme)
+            u.init_state(mi.IC_QUADRANTS, P)
+            ms = timed_steps(u, NI, torch, stream, dt=dt)
+            row[fvname] = {"l1_rho": l1_at(u.download_level(0)[0][0], n), "gpu_ms": ms}
+            u.close()
+        variants = (("MR", "muscl_rk2", False, "mr", "FV_MR"), ("MRLT", "muscl_rk2", True, "mr", "FV_MR"),
+                    ("AMR", "hancock", False, "grad", "FV_AMR"), ("AMRLT", "hancock", True, "grad", "FV_AMR"))
+        for name, scheme, lts, crit, fvname in variants:
+            steps = NI >> (levels - 1) if lts else NI
+            # counting run: accumulated cells and leaves per finest step
+            a = solver(n, levels, scheme, adapt=True, lts=lts, crit=crit)
+            a.init_state(mi.IC_QUADRANTS, P)
+            C = Lf = 0
+            for _ in range(steps):
+                st = a.stats()
+                mult = (1 << (levels - 1)) if lts else 1
+                C += st["total_blocks"] * 64 * mult
+                Lf += st["total_leaves"] * 64 * mult
+                a.step(dt, sync=True)
+            l1 = l1_at(a.project_finest()[0], n)
+            a.close()
+            # timed run
+            a = solver(n, levels, scheme, adapt=True, lts=lts, crit=crit)
+            a.init_state(mi.IC_QUADRANTS, P)
+            ms = timed_steps(a, steps, torch, stream, dt=dt)
+            a.close()
+            fv = row[fvname]
+            row[name] = {"l1_rho": l1, "perturbation_pct": 100.0 * abs(l1 - fv["l1_rho"]) / fv["l1_rho"],
+                         "cells_1e6": C / 1e6, "cell_compression_pct": 100.0 * C / (NI * n * n),
+                         "leaves_1e6": Lf / 1e6, "leaf_compression_pct": 100.0 * Lf / (NI * n * n),
+                         "gpu_ms": ms, "time_compression_pct": 100.0 * ms / fv["gpu_ms"]}
+            torch.cuda.empty_cache()
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+    for key in ("FV_MR", "FV_AMR", "MR", "MRLT", "AMR", "AMRLT"):
+        e = [r_[key]["l1_rho"] for r_ in out["rows"]]
+        out.setdefault("rates", {})[key] = [float(np.log2(e[i] / e[i + 1])) for i in range(len(e) - 1)]
+    print(json.dumps(out), flush=True)
+
+
 def run_case(args):
     """Single uniform-grid case (the profiling workload): levels=1, n^d cells, CFL steps only."""
     import torch
@@ -576,6 +731,8 @@ def run_case(args):
         s = m.Solver(dim=3, precision=prec, levels=1, base_blocks=(nb, nb, nb), lo=(-1, -1, -1), hi=(1, 1, 1), cfl=cfl,
                      scheme=args.scheme)
         s.init_state(mi.IC_ELLIPSOID, mi.ellipsoid_params(SEED))
+    if args.stage_kernel:
+        s.set_launch_shape(stage_kernel=args.stage_kernel)
     for _ in range(args.warmup):
         s.step(0.0, sync=False)
     s.profile_enable(True)
@@ -596,7 +753,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default="adaptive", choices=["adaptive", "uniform", "matched3d"],
+    ap.add_argument("--case", default="adaptive", choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu"],
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
@@ -604,10 +761,14 @@ def main():
     ap.add_argument("--snapshots", type=int, default=60)
     ap.add_argument("--train-steps", dest="train_steps", type=int, default=300)
     ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--laxliu-levels", dest="laxliu_levels", default="7,8,9,10")
+    ap.add_argument("--laxliu-ref", dest="laxliu_ref", type=int, default=4096, help="reference grid of --case laxliu")
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--scheme", default="muscl_rk2", choices=["muscl_rk2", "hancock"],
                     help="finite-volume scheme of the uniform case")
+    ap.add_argument("--stage-kernel", dest="stage_kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="uniform case: 0 by leaf count, 1 pencil kernel, 2 staged kernel")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -615,6 +776,10 @@ def main():
         run_case(args)
     elif args.case == "matched3d":
         run_matched3d(args)
+    elif args.case == "proposer":
+        run_proposer(args)
+    elif args.case == "laxliu":
+        run_laxliu(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

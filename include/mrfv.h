@@ -71,6 +71,14 @@ enum {
    direction; the scheme of the paper's AMR method). */
 enum { MRFV_SCHEME_MUSCL_RK2 = 0, MRFV_SCHEME_HANCOCK = 1 };
 
+/* Clustering of the gradient flags into the blocks to refine (Section 2.2).
+   ROWS: runs of at most 8 blocks along the first direction whose flagged
+   fraction stays >= eta_tol.  BR: Berger-Rigoutsos boxes (AMROC's clustering):
+   a box shrunk to its flags is accepted at efficiency >= eta_tol with sides of
+   at most 8 blocks, else cut at a hole of the flag signatures, else at their
+   strongest inflection, else bisected across its longest side. */
+enum { MRFV_CLUSTER_ROWS = 0, MRFV_CLUSTER_BR = 1 };
+
 #define MRFV_MAX_LEVELS 12
 
 /* Solver configuration; plain data, copied by mrfv_create. */
@@ -99,6 +107,7 @@ typedef struct {
   int proposer;         /* 1: MR adaptation takes the learned proposer's blocks instead of the safety
                            zone, once weights are set (mrfv_proposer_set_weights) */
   int scheme;           /* MRFV_SCHEME_MUSCL_RK2 (default) or MRFV_SCHEME_HANCOCK (Section 2) */
+  int clustering;       /* gradient criterion: MRFV_CLUSTER_ROWS (default) or MRFV_CLUSTER_BR */
 } mrfv_config;
 
 typedef struct {
@@ -227,6 +236,9 @@ typedef struct {
   double fv_bytes;      /* algorithmic bytes of those launches: per cell, stage 1 reads
                            Q^n and writes Q* (2 nv words), stage 2 reads Q^n and Q* and
                            writes Q^{n+1} (3 nv words) */
+  int64_t prop_launches; /* tensor-core convolution launches of the proposer timed (3 per inference) */
+  double prop_ms;        /* their CUDA-event time */
+  double prop_flops;     /* their algorithmic flops: 2 x positions x (16*81 + 16*432 + 432) per inference */
 } mrfv_profile;
 /* enable != 0: reset the counters and bracket every finite-volume stage launch
    with CUDA events on the context stream (steps then launch eagerly instead of
@@ -237,12 +249,15 @@ int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
 
 /* Launch shape (no counterpart in the paper): CTAs per SM of the persistent
    grids, for the grid-stride kernels (256-thread CTAs), the kernels that take
-   one block per CTA, and the finite-volume stage kernel.  0 keeps the default
-   (the stage kernel's default is its occupancy limit); each value is 0..32,
-   else MRFV_ERR_ARG.  Every kernel loops over its device-resident work list,
-   so any shape gives the same results; captured step graphs are dropped and
-   re-captured at the next step. */
-int mrfv_set_launch_shape(mrfv_ctx *ctx, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm);
+   one block per CTA, and the finite-volume stage kernels.  0 keeps the default
+   (the stage kernels' default is their occupancy limit); each value is 0..32.
+   stage_kernel picks the MR-scheme stage kernel: 0 by leaf count, 1 the pencil
+   kernel (one thread per line of cells), 2 the staged kernel (one thread per
+   face).  Out-of-range values give MRFV_ERR_ARG.  Every kernel loops over its
+   device-resident work list, so any shape gives the same results; captured
+   step graphs are dropped and re-captured at the next step. */
+int mrfv_set_launch_shape(mrfv_ctx *ctx, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm,
+                          int stage_kernel);
 
 /* Learned refinement proposer (no counterpart in the paper, which refines by
    the heuristic of Section 2.1): a 3-layer 3D convolutional net (16 channels,

@@ -24,6 +24,7 @@ FP64, FP32 = 0, 1
 BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
 CRIT_MR, CRIT_GRAD = 0, 1
 SCHEME_MUSCL_RK2, SCHEME_HANCOCK = 0, 1
+CLUSTER_ROWS, CLUSTER_BR = 0, 1
 MAX_LEVELS = 12
 
 
@@ -44,6 +45,7 @@ class Config(ctypes.Structure):
         ("lts", ctypes.c_int), ("pool_blocks", ctypes.c_int64),
         ("stream", ctypes.c_void_p), ("device_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
         ("use_graph", ctypes.c_int), ("proposer", ctypes.c_int), ("scheme", ctypes.c_int),
+        ("clustering", ctypes.c_int),
     ]
 
 
@@ -59,7 +61,8 @@ class Stats(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("fv_launches", ctypes.c_int64),
-                ("fv_ms", ctypes.c_double), ("fv_bytes", ctypes.c_double)]
+                ("fv_ms", ctypes.c_double), ("fv_bytes", ctypes.c_double),
+                ("prop_launches", ctypes.c_int64), ("prop_ms", ctypes.c_double), ("prop_flops", ctypes.c_double)]
 
 
 # exported symbols of include/mrfv.h with their ctypes signatures
@@ -92,7 +95,7 @@ SIGNATURES = {
     "mrfv_synchronize": (_I, [_P]),
     "mrfv_profile_enable": (_I, [_P, _I]),
     "mrfv_profile_read": (_I, [_P, ctypes.POINTER(Profile)]),
-    "mrfv_set_launch_shape": (_I, [_P, _I, _I, _I]),
+    "mrfv_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
     "mrfv_cfl_dt_noalloc": (_I, [_I, _I, _P, _I64, _I64, _I64, _DP, _D, _D, _P, _P]),
     "mrfv_proposer_set_weights": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I64]),
     "mrfv_proposer_get_weights": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I64]),
@@ -146,7 +149,7 @@ class Solver:
     def __init__(self, dim=2, precision="fp64", levels=1, base_blocks=(1, 1, 1), lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), bc=BC_TRANSMISSIVE, gamma=1.4, cfl=0.5, t_end=0.0, adapt=False,
                  criterion="mr", eps=1e-3, eps_w=0.05, eta_tol=0.8, lts=False, pool_blocks=0, stream=None,
-                 use_graph=True, proposer=False, scheme="muscl_rk2"):
+                 use_graph=True, proposer=False, scheme="muscl_rk2", clustering="rows"):
         import torch
 
         if not torch.cuda.is_available():
@@ -173,6 +176,7 @@ class Solver:
         cfg.use_graph = int(bool(use_graph))
         cfg.proposer = int(bool(proposer))
         cfg.scheme = SCHEME_HANCOCK if str(scheme).lower() in ("hancock", "1") else SCHEME_MUSCL_RK2
+        cfg.clustering = CLUSTER_BR if str(clustering).lower() in ("br", "berger-rigoutsos", "1") else CLUSTER_ROWS
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         cfg.stream = self.stream.cuda_stream
         nbytes = lib.mrfv_arena_bytes(ctypes.byref(cfg))
@@ -338,10 +342,13 @@ class Solver:
     def profile_enable(self, enable: bool = True) -> None:
         self._check(self.lib.mrfv_profile_enable(self._h, int(bool(enable))))
 
-    def set_launch_shape(self, grid_ctas_per_sm: int = 0, block_ctas_per_sm: int = 0, fv_ctas_per_sm: int = 0) -> None:
-        self._check(self.lib.mrfv_set_launch_shape(self._h, grid_ctas_per_sm, block_ctas_per_sm, fv_ctas_per_sm))
+    def set_launch_shape(self, grid_ctas_per_sm: int = 0, block_ctas_per_sm: int = 0, fv_ctas_per_sm: int = 0,
+                         stage_kernel: int = 0) -> None:
+        self._check(self.lib.mrfv_set_launch_shape(self._h, grid_ctas_per_sm, block_ctas_per_sm, fv_ctas_per_sm,
+                                                   stage_kernel))
 
     def profile_read(self) -> dict:
         p = Profile()
         self._check(self.lib.mrfv_profile_read(self._h, ctypes.byref(p)))
-        return dict(launches=p.launches, fv_launches=p.fv_launches, fv_ms=p.fv_ms, fv_bytes=p.fv_bytes)
+        return dict(launches=p.launches, fv_launches=p.fv_launches, fv_ms=p.fv_ms, fv_bytes=p.fv_bytes,
+                    prop_launches=p.prop_launches, prop_ms=p.prop_ms, prop_flops=p.prop_flops)

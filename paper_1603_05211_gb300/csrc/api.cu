@@ -22,6 +22,12 @@ using namespace mrfv;
 // mrfv_set_launch_shape overrides them.
 constexpr int kGridCtasPerSm = 8;
 constexpr int kBlockCtasPerSm = 16;
+// Below these leaf counts the MR-scheme stage runs in the staged (thread per
+// face) kernel.  Measured on GB300 (FP32, uniform grids): staged 11.7 vs pencil
+// 13.0 us at 1024 2D blocks, 22.9 vs 19.7 us at 4096; in 3D the pencil kernel
+// is faster from 512 blocks up (21 vs 34 us), so 3D always takes it.
+constexpr long long kStagedBelow2D = 2048;
+constexpr long long kStagedBelow3D = 0;
 
 struct mrfv_ctx {
   mrfv_config cfg;
@@ -29,7 +35,9 @@ struct mrfv_ctx {
   int prec;         // MRFV_FP64 / MRFV_FP32
   size_t tsize;     // bytes per state value
   cudaStream_t st;
-  int nsm, grid, bgrid, fvgrid, fv_occupancy, fvhgrid, fvh_occupancy;
+  int nsm, grid, bgrid, fvgrid, fv_occupancy;
+  int fvs_occupancy[2], fvsgrid[2];  // staged stage kernel: [0] MR scheme, [1] MUSCL-Hancock
+  int stage_kernel;                  // 0 by leaf count, 1 pencil, 2 staged (MR scheme)
   char *arena;
   size_t arena_bytes;
   bool own_arena;
@@ -53,6 +61,8 @@ struct mrfv_ctx {
   bool prof;
   std::vector<cudaEvent_t> evs;  // start/end pairs of timed stage launches
   size_t ev_used;
+  std::vector<cudaEvent_t> pevs;  // start/end pairs around the proposer's convolution launches
+  size_t pev_used;
   unsigned long long *dbytes;
   unsigned *done;  // last-CTA counter of the CFL reduction
   // learned proposer
@@ -65,6 +75,16 @@ struct mrfv_ctx {
   cudaStream_t cap_st;
   cudaGraphExec_t gexec[2];
   long long glaunch[2];  // kernels in each captured step
+  // Launch sizing: the list offsets the current launch shapes were chosen for
+  // (snap), and host-mapped memory into which every step copies the current
+  // offsets (pub_host, written by the GPU through pub_dev).
+  int32_t snap[LK_NUM * (MAXL + 2)];
+  bool snap_valid;
+  int32_t *pub_host, *pub_dev;
+  int fv_bpc, fvs_bpc;  // blocks per CTA iteration of the pencil and the staged kernels
+  void *brscratch;      // Berger-Rigoutsos boxes and signatures
+  unsigned *rctl;       // [3]: CTAs done of the scale reduction
+  int br_maxside;       // longest side, in blocks, of the levels that are clustered
 };
 
 static thread_local std::string g_create_error;
@@ -181,7 +201,13 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t opa1 = L.take(16 * maptotal * 2), opa2 = L.take(16 * maptotal * 2);
   size_t opw1 = L.take(16 * 224 * 2), opw2 = L.take(16 * 432 * 2), opw3 = L.take(16 * 432 * 2);
   size_t opb = L.take(3 * 16 * 4), opblob = L.take(4 * NW * 4), opwork = L.take((size_t)kPropWorkPerPos * maptotal * 4), oploss = L.take(8);
+  int maxside = 1;
+  if (g.L >= 1)
+    for (int d = 0; d < g.dim; d++) maxside = g.nb[g.L - 1][d] > maxside ? g.nb[g.L - 1][d] : maxside;
+  size_t obr = L.take(br_scratch_bytes(g, maptotal, maxside));
+  size_t orctl = L.take(4 * 4);
   if (c) {
+    c->br_maxside = maxside;
     char *a = c->arena;
     c->U = a + oU; c->Us = a + oUs; c->U0 = a + oU0; c->G = a + oG; c->FR = a + oFR;
     c->g.idx = (int32_t *)(a + oidx); c->g.slot_level = (int32_t *)(a + olev);
@@ -216,6 +242,8 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->pm2 = c->pm1 + NW;
     c->pwork = (float *)(a + opwork);
     c->ploss = (double *)(a + oploss);
+    c->brscratch = a + obr;
+    c->rctl = (unsigned *)(a + orctl);
   }
   return L.off + 256;
 }
@@ -242,6 +270,52 @@ int grid_for(long long items, int per_cta, int cap_grid) {
   return (int)(n < cap_grid ? n : cap_grid);
 }
 
+// Exact list offsets (synchronises the stream); used when a step graph is
+// captured and after explicit tree changes.
+void snapshot_exact(mrfv_ctx *c) {
+  cudaStreamSynchronize(c->st);
+  if (cudaMemcpy(c->snap, c->g.loff, sizeof(c->snap), cudaMemcpyDeviceToHost) == cudaSuccess) {
+    c->snap_valid = true;
+    if (c->pub_host) memcpy(c->pub_host, c->snap, sizeof(c->snap));  // nothing in flight writes it now
+  } else {
+    cudaGetLastError();
+  }
+}
+// The offsets the last finished step published (no synchronisation; at most a
+// step old).
+void snapshot_published(mrfv_ctx *c) {
+  if (!c->pub_host) return;
+  memcpy(c->snap, (const void *)c->pub_host, sizeof(c->snap));
+  c->snap_valid = true;
+}
+long long list_count(const mrfv_ctx *c, const int32_t *off, int kind, int l0, int l1) {
+  return (long long)off[kind * (MAXL + 2) + l1 + 1] - off[kind * (MAXL + 2) + l0];
+}
+// CTAs for a kernel that loops over list `kind` on levels l0..l1: twice the
+// snapshot's count (per_item work units per listed block, per_cta units per CTA
+// iteration), at least one CTA per SM (launching up to that many costs no more
+// than launching one), at most cap.  Every kernel loops over the device-resident
+// list, so any size is correct; the size only decides how fast.
+int sized(const mrfv_ctx *c, int kind, int l0, int l1, long long per_item, long long per_cta, int cap) {
+  if (!c->snap_valid) return cap;
+  long long n = list_count(c, c->snap, kind, l0, l1);
+  long long want = (2 * n * per_item + per_cta - 1) / per_cta;
+  if (want < c->nsm) want = c->nsm;
+  return (int)(want < cap ? want : cap);
+}
+// A captured graph keeps its launch shapes; re-capture when the tree the shapes
+// were sized for has grown past the headroom or shrunk well below it.
+bool shapes_stale(const mrfv_ctx *c) {
+  if (!c->pub_host || !c->snap_valid) return false;
+  const int kinds[3] = {LK_LEAF, LK_EXIST, LK_GHOST};
+  for (int k : kinds) {
+    long long was = list_count(c, c->snap, k, 0, c->g.L);
+    long long now = list_count(c, (const int32_t *)c->pub_host, k, 0, c->g.L);
+    if (now > (was * 3) / 2 + 16 || (was > 64 && now < was / 3)) return true;
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------- typed sequencing
 template <typename T>
 struct Seq {
@@ -254,8 +328,11 @@ struct Seq {
 
   void restrict_level(int l, T *A) {
     // at most the blocks of level l are refined
-    launch_restrict<T>(c->g, l, A, grid_for(level_blocks(c->g, l), c->g.dim == 2 ? 4 : 1, c->grid), c->st);
+    int dense = grid_for(level_blocks(c->g, l), c->g.dim == 2 ? 4 : 1, c->grid);
+    launch_restrict<T>(c->g, l, A, sized(c, LK_INTERNAL, l, l, 1, c->g.dim == 2 ? 4 : 1, dense), c->st);
   }
+  // every level, finest first, one launch per level: a launch boundary costs
+  // less than the in-kernel waits of a single all-levels launch (measured)
   void restrict_all(T *A) {
     for (int l = c->g.L - 1; l >= 0; l--) restrict_level(l, A);
     c->nlaunch += c->g.L;
@@ -282,6 +359,14 @@ struct Seq {
     a.C = Uin; a.C0 = C0; a.theta = theta;
     timed_fv(a, true);
   }
+  // MR-scheme stage: the pencil kernel, or the staged kernel while the list is
+  // too short for the pencil kernel's one thread per line to fill the GPU
+  bool use_staged(const FVArgs<T> &a) const {
+    if (c->stage_kernel != 0) return c->stage_kernel == 2;
+    if (!c->snap_valid) return false;
+    long long n = list_count(c, c->snap, a.kind, a.l0, a.l1);
+    return n < (c->g.dim == 2 ? kStagedBelow2D : kStagedBelow3D);
+  }
   // launch a finite-volume stage kernel, bracketed by events when profiling
   void timed_fv(FVArgs<T> &a, bool hancock) {
     a.bytes = c->prof ? c->dbytes : nullptr;
@@ -299,14 +384,19 @@ struct Seq {
       c->ev_used += 2;
       cudaEventRecord(e0, c->st);
     }
-    if (hancock) launch_fvh<T>(c->g, a, c->fvhgrid, c->st);
-    else launch_fv<T>(c->g, a, c->fvgrid, c->st);
+    if (hancock || use_staged(a)) {
+      int h = hancock ? 1 : 0;
+      launch_fvs<T>(c->g, a, hancock, sized(c, a.kind, a.l0, a.l1, 1, c->fvs_bpc, c->fvsgrid[h]), c->st);
+    } else {
+      launch_fv<T>(c->g, a, sized(c, a.kind, a.l0, a.l1, 1, c->fv_bpc, c->fvgrid), c->st);
+    }
     if (c->prof) cudaEventRecord(e1, c->st);
     c->nlaunch += 1;
   }
   void ghost(int l0, int l1, const T *A, const T *A0, double theta) {
     if (l1 < 1) return;
-    launch_ghost<T>(c->g, l0 < 1 ? 1 : l0, l1, A, A0, theta, G(), c->bgrid, c->st);
+    int a0 = l0 < 1 ? 1 : l0;
+    launch_ghost<T>(c->g, a0, l1, A, A0, theta, G(), sized(c, LK_GHOST, a0, l1, 1, 1, c->bgrid), c->st);
     c->nlaunch += 1;
   }
   // one midpoint-RK2 step of every leaf with the same dt (Section 2)
@@ -316,10 +406,10 @@ struct Seq {
       // one stage into Us, leaves copied back, then the correction and projection
       ghost(1, L, U(), nullptr, 0.0);
       fvh(LK_LEAF, 0, L, U(), Us(), nullptr, 0.0, 1);
-      launch_copy_level<T>(c->g, LK_LEAF, 0, L, Us(), U(), c->grid, c->st);
+      launch_copy_level<T>(c->g, LK_LEAF, 0, L, Us(), U(), sized(c, LK_LEAF, 0, L, block_cells(c->g.dim), 256, c->grid), c->st);
       c->nlaunch += 1;
       if (L > 0) {
-        launch_reflux<T>(c->g, 0, L - 1, U(), FR(), c->grid, c->st);
+        launch_reflux<T>(c->g, 0, L - 1, U(), FR(), sized(c, LK_REFLUX, 0, L - 1, block_cells(c->g.dim), 256, c->grid), c->st);
         c->nlaunch += 1;
       }
       restrict_all(U());
@@ -331,7 +421,7 @@ struct Seq {
     ghost(1, L, Us(), nullptr, 0.0);
     fv(LK_LEAF, 0, L, Us(), U(), U(), 1.0, 0, 1);
     if (L > 0) {
-      launch_reflux<T>(c->g, 0, L - 1, U(), FR(), c->grid, c->st);
+      launch_reflux<T>(c->g, 0, L - 1, U(), FR(), sized(c, LK_REFLUX, 0, L - 1, block_cells(c->g.dim), 256, c->grid), c->st);
       c->nlaunch += 1;
     }
     restrict_all(U());
@@ -341,13 +431,13 @@ struct Seq {
   void advance(int l, int sub) {
     int L = c->g.L;
     double th1 = 0.5 * sub, th2 = th1 + 0.25;
-    launch_copy_level<T>(c->g, LK_EXIST, l, l, U(), U0(), c->grid, c->st);
+    launch_copy_level<T>(c->g, LK_EXIST, l, l, U(), U0(), sized(c, LK_EXIST, l, l, block_cells(c->g.dim), 256, c->grid), c->st);
     c->nlaunch += 1;
     if (l >= 1) ghost(l, l, U(), U0(), th1);
     if (c->cfg.scheme == MRFV_SCHEME_HANCOCK) {
       // one stage from the sub-step start, halo at its start time
       fvh(LK_EXIST, l, l, U(), Us(), U0(), th1, sub == 1 ? 2 : 1);
-      launch_copy_level<T>(c->g, LK_EXIST, l, l, Us(), U(), c->grid, c->st);
+      launch_copy_level<T>(c->g, LK_EXIST, l, l, Us(), U(), sized(c, LK_EXIST, l, l, block_cells(c->g.dim), 256, c->grid), c->st);
       c->nlaunch += 1;
     } else {
       fv(LK_EXIST, l, l, U(), U(), Us(), 0.5, 1, 0);
@@ -358,26 +448,29 @@ struct Seq {
       advance(l + 1, 0);
       advance(l + 1, 1);
       restrict_level(l, U());
-      launch_reflux<T>(c->g, l, l, U(), FR(), c->grid, c->st);
+      launch_reflux<T>(c->g, l, l, U(), FR(), sized(c, LK_REFLUX, l, l, block_cells(c->g.dim), 256, c->grid), c->st);
       c->nlaunch += 2;
     }
   }
   void analyse(double eps) {
-    launch_scales<T>(c->g, U(), c->red + 0, (T *)c->scale,
+    launch_scales<T>(c->g, U(), c->red + 0, c->rctl + 3, (T *)c->scale,
                      grid_for(level_blocks(c->g, 0) * block_cells(c->g.dim), 256, c->grid), c->st);
     cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
     cudaMemsetAsync(c->maxdet, 0, c->maptotal * 8, c->st);
-    launch_details<T>(c->g, U(), (const T *)c->scale, eps, c->sig, c->maxdet, c->bgrid, c->st);
-    c->nlaunch += 3;
+    launch_details<T>(c->g, U(), (const T *)c->scale, eps, c->sig, c->maxdet,
+                      sized(c, LK_EXIST, 1, c->g.L, 1, 1, c->bgrid), c->st);
+    c->nlaunch += 2;
   }
   void prolong_new() {
     for (int l = 1; l <= c->g.L; l++)
-      launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(), grid_for(level_blocks(c->g, l), 1, c->bgrid), c->st);
+      launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(),
+                        sized(c, LK_EXIST, l, l, 1, 1, grid_for(level_blocks(c->g, l), 1, c->bgrid)), c->st);
     c->nlaunch += c->g.L;
   }
   // CFL reduction; its last CTA sets dt and the per-level step table
   void compute_dt(int lts) {
-    launch_dt<T>(c->g, U(), lts, c->red + 3, c->done, c->cfg.cfl, c->cfg.t_end, c->dsc, c->lev, c->levf, c->grid,
+    launch_dt<T>(c->g, U(), lts, c->red + 3, c->done, c->cfg.cfl, c->cfg.t_end, c->dsc, c->lev, c->levf,
+                 sized(c, LK_LEAF, 0, c->g.L, block_cells(c->g.dim), 256, c->grid),
                  c->st);
     c->nlaunch += 1;
   }
@@ -394,7 +487,10 @@ struct Seq {
     cudaMemsetAsync(c->gflag, 0, c->maptotal, c->st);
     cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
     launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->gflag, c->bgrid, c->st);
-    launch_cluster(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->grid, c->st);
+    if (c->cfg.clustering == MRFV_CLUSTER_BR)
+      launch_br(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
+    else
+      launch_cluster(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->grid, c->st);
     c->nlaunch += 2;
   }
 };
@@ -421,8 +517,20 @@ void apply_need(mrfv_ctx *c, bool prolong) {
 }
 
 void prop_infer(mrfv_ctx *c) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->prof) {
+    if (c->pev_used + 2 > c->pevs.size())
+      for (int k = 0; k < 16; k++) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->pevs.push_back(e);
+      }
+    e0 = c->pevs[c->pev_used];
+    e1 = c->pevs[c->pev_used + 1];
+    c->pev_used += 2;
+  }
   launch_prop_infer(c->g, c->pfeat, c->pa0, c->pa1, c->pa2, c->pw1, c->pb1, c->pw2, c->pb2, c->pw3, c->pb3, c->plogit,
-                    c->nsm, c->st);
+                    c->nsm, e0, e1, c->st);
   c->nlaunch += 4;
 }
 
@@ -530,6 +638,8 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   if (cfg->pool_blocks < 0) return fail(nullptr, MRFV_ERR_ARG, "pool_blocks");
   if (cfg->scheme != MRFV_SCHEME_MUSCL_RK2 && cfg->scheme != MRFV_SCHEME_HANCOCK)
     return fail(nullptr, MRFV_ERR_ARG, "scheme");
+  if (cfg->clustering != MRFV_CLUSTER_ROWS && cfg->clustering != MRFV_CLUSTER_BR)
+    return fail(nullptr, MRFV_ERR_ARG, "clustering");
   {
     Geo gg;
     long long a, b, f;
@@ -582,14 +692,32 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   c->grid = c->nsm * kGridCtasPerSm;
   c->bgrid = c->nsm * kBlockCtasPerSm;
   c->fvgrid = c->nsm * c->fv_occupancy;
-  c->fvh_occupancy = c->prec == MRFV_FP32 ? fvh_ctas_per_sm<float>(cfg->dim) : fvh_ctas_per_sm<double>(cfg->dim);
-  c->fvhgrid = c->nsm * c->fvh_occupancy;
+  for (int h = 0; h < 2; h++) {
+    c->fvs_occupancy[h] =
+        c->prec == MRFV_FP32 ? fvs_ctas_per_sm<float>(cfg->dim, h == 1) : fvs_ctas_per_sm<double>(cfg->dim, h == 1);
+    c->fvsgrid[h] = c->nsm * c->fvs_occupancy[h];
+  }
+  c->stage_kernel = 0;
+  c->fv_bpc = c->prec == MRFV_FP32 ? fv_blocks_per_cta<float>(cfg->dim, false) : fv_blocks_per_cta<double>(cfg->dim, false);
+  c->fvs_bpc = c->prec == MRFV_FP32 ? fv_blocks_per_cta<float>(cfg->dim, true) : fv_blocks_per_cta<double>(cfg->dim, true);
+  c->snap_valid = false;
+  c->pub_host = c->pub_dev = nullptr;
+  if (cudaHostAlloc((void **)&c->pub_host, sizeof(c->snap), cudaHostAllocMapped) == cudaSuccess) {
+    memset(c->pub_host, 0, sizeof(c->snap));
+    if (cudaHostGetDevicePointer((void **)&c->pub_dev, c->pub_host, 0) != cudaSuccess) {
+      cudaFreeHost(c->pub_host);
+      c->pub_host = c->pub_dev = nullptr;
+    }
+  }
+  cudaGetLastError();  // without mapped memory the shapes are sized from exact snapshots only
   cudaMemsetAsync(c->g.idx, 0xff, c->maptotal * 4, c->st);
   cudaMemsetAsync(c->g.slot_level, 0xff, c->g.cap * 4, c->st);
   cudaMemsetAsync(c->g.loff, 0, LK_NUM * (MAXL + 2) * 4, c->st);
   cudaMemsetAsync(c->g.err, 0, 4, c->st);
   cudaMemsetAsync(c->dsc, 0, 4 * 8, c->st);
   cudaMemsetAsync(c->counter, 0, 2 * 8, c->st);
+  cudaMemsetAsync(c->rctl, 0, 4 * 4, c->st);
+  cudaMemsetAsync(c->red, 0, 4 * 8, c->st);
   launch_init_freestack(c->freestack, c->freetop, c->g.cap, c->grid, c->st);
   if (cfg->use_graph && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) c->cap_st = nullptr;
   prop_setup();
@@ -608,9 +736,11 @@ int mrfv_destroy(mrfv_ctx *c) {
   if (!c) return MRFV_OK;
   cudaStreamSynchronize(c->st);
   for (cudaEvent_t e : c->evs) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->pevs) cudaEventDestroy(e);
   for (int v = 0; v < 2; v++)
     if (c->gexec[v]) cudaGraphExecDestroy(c->gexec[v]);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
+  if (c->pub_host) cudaFreeHost(c->pub_host);
   if (c->own_arena && c->arena) cudaFree(c->arena);
   delete c;
   return MRFV_OK;
@@ -625,6 +755,8 @@ int mrfv_init_state(mrfv_ctx *c, int kind, const double *params, int n) {
   memset(&ic, 0, sizeof(ic));
   ic.kind = kind;
   for (int i = 0; i < n; i++) ic.p[i] = params[i];
+  drop_graphs(c);
+  c->snap_valid = false;
   cudaMemsetAsync(c->need, 1, c->maptotal, c->st);
   apply_need(c, false);
   dispatch(c, [&](auto &s) { s.init_level(ic); });
@@ -634,6 +766,7 @@ int mrfv_init_state(mrfv_ctx *c, int kind, const double *params, int n) {
   int rc = check_launch(c, "mrfv_init_state");
   if (rc == MRFV_OK) rc = check_device(c, "mrfv_init_state");
   c->initialized = rc == MRFV_OK;
+  if (rc == MRFV_OK) snapshot_exact(c);
   return rc;
 }
 
@@ -667,6 +800,7 @@ int mrfv_adapt(mrfv_ctx *c, int use_proposer, int64_t *n_blocks) {
   c->cfg.proposer = saved;
   int rc = check_launch(c, "mrfv_adapt");
   if (rc != MRFV_OK) return rc;
+  snapshot_exact(c);
   if (n_blocks) {
     rc = check_device(c, "mrfv_adapt");
     if (rc != MRFV_OK) return rc;
@@ -711,7 +845,7 @@ void issue_step(mrfv_ctx *c, bool preset) {
     if (lts) s.advance(0, 0);
     else s.step_global();
   });
-  launch_advance(c->g, c->dsc + 1, c->dsc, lts ? ldexp(1.0, c->g.L) : 1.0, c->counter, lts, c->st);
+  launch_advance(c->g, c->dsc + 1, c->dsc, lts ? ldexp(1.0, c->g.L) : 1.0, c->counter, lts, c->pub_dev, c->st);
   c->nlaunch += 1;
   if (c->cfg.adapt) adapt_tree(c);
 }
@@ -720,6 +854,7 @@ void issue_step(mrfv_ctx *c, bool preset) {
 // is a fixed device pointer or a configuration constant, and every work-list
 // length is read on the device).
 int capture_step(mrfv_ctx *c, int v) {
+  snapshot_exact(c);  // the graph's launch shapes are sized for the tree of now
   cudaStream_t user = c->st;
   c->st = c->cap_st;
   long long before = c->nlaunch;
@@ -755,6 +890,7 @@ int mrfv_step(mrfv_ctx *c, double dt, double *dt_out) {
   }
   if (c->cfg.use_graph && c->cap_st && !c->prof) {
     int v = preset ? 1 : 0;
+    if (shapes_stale(c)) drop_graphs(c);
     if (!c->gexec[v]) {
       int rc = capture_step(c, v);
       if (rc != MRFV_OK) return rc;
@@ -762,6 +898,7 @@ int mrfv_step(mrfv_ctx *c, double dt, double *dt_out) {
     if (cudaGraphLaunch(c->gexec[v], c->st) != cudaSuccess) return check_launch(c, "mrfv_step: graph launch");
     c->nlaunch += c->glaunch[v];
   } else {
+    snapshot_published(c);
     issue_step(c, preset);
   }
   int rc = check_launch(c, "mrfv_step");
@@ -902,10 +1039,13 @@ int mrfv_set_tree(mrfv_ctx *c, const uint8_t *ex, int64_t n) {
   if (!c || !ex || n != c->maptotal) return fail(c, MRFV_ERR_ARG, "set_tree: n must be the total number of block positions");
   if (!c->initialized) return fail(c, MRFV_ERR_STATE, "set_tree before init");
   if (!valid_tree(c, ex)) return fail(c, MRFV_ERR_ARG, "set_tree: tree is not complete, nested and graded");
+  drop_graphs(c);
+  c->snap_valid = false;
   cudaMemcpyAsync(c->need, ex, n, cudaMemcpyHostToDevice, c->st);
   apply_need(c, true);
   int rc = check_launch(c, "mrfv_set_tree");
   if (rc == MRFV_OK) rc = check_device(c, "mrfv_set_tree");
+  if (rc == MRFV_OK) snapshot_exact(c);
   return rc;
 }
 
@@ -1004,8 +1144,10 @@ int mrfv_proposer_train(mrfv_ctx *c, const float *feat, const uint8_t *target, i
   return rc;
 }
 
-int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm) {
+int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm,
+                          int stage_kernel) {
   if (!c) return MRFV_ERR_ARG;
+  if (stage_kernel < 0 || stage_kernel > 2) return fail(c, MRFV_ERR_ARG, "set_launch_shape: stage_kernel is 0, 1 or 2");
   if (grid_ctas_per_sm < 0 || grid_ctas_per_sm > 32 || block_ctas_per_sm < 0 || block_ctas_per_sm > 32 ||
       fv_ctas_per_sm < 0 || fv_ctas_per_sm > 32)
     return fail(c, MRFV_ERR_ARG, "set_launch_shape: CTAs per SM outside 0..32");
@@ -1014,7 +1156,8 @@ int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_
   c->grid = c->nsm * (grid_ctas_per_sm ? grid_ctas_per_sm : kGridCtasPerSm);
   c->bgrid = c->nsm * (block_ctas_per_sm ? block_ctas_per_sm : kBlockCtasPerSm);
   c->fvgrid = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fv_occupancy);
-  c->fvhgrid = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fvh_occupancy);
+  for (int h = 0; h < 2; h++) c->fvsgrid[h] = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fvs_occupancy[h]);
+  c->stage_kernel = stage_kernel;
   drop_graphs(c);
   return MRFV_OK;
 }
@@ -1025,6 +1168,7 @@ int mrfv_profile_enable(mrfv_ctx *c, int enable) {
   if (rc != MRFV_OK) return rc;
   c->prof = enable != 0;
   c->ev_used = 0;
+  c->pev_used = 0;
   c->nlaunch = 0;
   cudaMemsetAsync(c->dbytes, 0, 8, c->st);
   return check_launch(c, "mrfv_profile_enable");
@@ -1046,6 +1190,14 @@ int mrfv_profile_read(mrfv_ctx *c, mrfv_profile *o) {
   unsigned long long b = 0;
   cudaMemcpy(&b, c->dbytes, 8, cudaMemcpyDeviceToHost);
   o->fv_bytes = (double)b;
+  double pms = 0.0;
+  for (size_t k = 0; k + 1 < c->pev_used; k += 2) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->pevs[k], c->pevs[k + 1]) == cudaSuccess) pms += t;
+  }
+  o->prop_launches = (int64_t)(3 * (c->pev_used / 2));
+  o->prop_ms = pms;
+  o->prop_flops = (double)(c->pev_used / 2) * 2.0 * (double)c->maptotal * (16.0 * 81 + 16.0 * 432 + 432.0);
   return check_launch(c, "mrfv_profile_read");
 }
 

@@ -428,14 +428,18 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
     }
   }
   if (bad) set_err(g, EB_NONPHYS);
+  // warp minima, then the CTA minimum: one atomic per CTA on the shared word
+  __shared__ T wmin[32];
   for (int o = 16; o > 0; o >>= 1) {
     T x = __shfl_xor_sync(0xffffffffu, best, o);
     if (x < best) best = x;
   }
-  if ((threadIdx.x & 31) == 0 && best < T(INFINITY))
-    atomicMin(red, (unsigned long long)__double_as_longlong((double)best));
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = best;
   __syncthreads();
   if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+      if (wmin[w] < best) best = wmin[w];
+    if (best < T(INFINITY)) atomicMin(red, (unsigned long long)__double_as_longlong((double)best));
     __threadfence();
     if (atomicAdd(done, 1u) == gridDim.x - 1) {
       __threadfence();

@@ -35,26 +35,39 @@ int fv_ctas_per_sm(int dim) {
   return n > 0 ? n : 1;
 }
 
+// staged stage kernel (fvh.cuh): the MUSCL-Hancock stage, or the MR-scheme
+// stage in the thread-per-face form
 template <typename T>
-void launch_fvh(const Geo &g, const FVArgs<T> &a, int grid, cudaStream_t st) {
-  if (g.dim == 2) k_fvh<T, 2><<<grid, FVH<T, 2>::NT, fvh_smem_bytes<T, 2>(), st>>>(g, a);
-  else k_fvh<T, 3><<<grid, FVH<T, 3>::NT, fvh_smem_bytes<T, 3>(), st>>>(g, a);
+void launch_fvs(const Geo &g, const FVArgs<T> &a, bool hancock, int grid, cudaStream_t st) {
+  if (g.dim == 2) {
+    if (hancock) k_fvs<T, 2, true><<<grid, FVS<T, 2, true>::NT, fvs_smem_bytes<T, 2, true>(), st>>>(g, a);
+    else k_fvs<T, 2, false><<<grid, FVS<T, 2, false>::NT, fvs_smem_bytes<T, 2, false>(), st>>>(g, a);
+  } else {
+    if (hancock) k_fvs<T, 3, true><<<grid, FVS<T, 3, true>::NT, fvs_smem_bytes<T, 3, true>(), st>>>(g, a);
+    else k_fvs<T, 3, false><<<grid, FVS<T, 3, false>::NT, fvs_smem_bytes<T, 3, false>(), st>>>(g, a);
+  }
 }
 
-// the same for the MUSCL-Hancock stage kernel
-template <typename T>
-int fvh_ctas_per_sm(int dim) {
+template <typename T, int D, bool H>
+int fvs_occupancy() {
   int n = 0;
-  if (dim == 2) {
-    constexpr size_t sm = fvh_smem_bytes<T, 2>();
-    cudaFuncSetAttribute(k_fvh<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fvh<T, 2>, FVH<T, 2>::NT, sm);
-  } else {
-    constexpr size_t sm = fvh_smem_bytes<T, 3>();
-    cudaFuncSetAttribute(k_fvh<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fvh<T, 3>, FVH<T, 3>::NT, sm);
-  }
+  constexpr size_t sm = fvs_smem_bytes<T, D, H>();
+  cudaFuncSetAttribute(k_fvs<T, D, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fvs<T, D, H>, FVS<T, D, H>::NT, sm);
   return n > 0 ? n : 1;
+}
+// the same for the staged kernel
+template <typename T>
+int fvs_ctas_per_sm(int dim, bool hancock) {
+  if (dim == 2) return hancock ? fvs_occupancy<T, 2, true>() : fvs_occupancy<T, 2, false>();
+  return hancock ? fvs_occupancy<T, 3, true>() : fvs_occupancy<T, 3, false>();
+}
+
+// blocks one CTA takes per iteration: pencil kernel, or the staged kernel
+template <typename T>
+int fv_blocks_per_cta(int dim, bool staged) {
+  if (staged) return dim == 2 ? FVS<T, 2, true>::BPC : FVS<T, 3, true>::BPC;
+  return dim == 2 ? FVShape<T, 2>::BPC : FVShape<T, 3>::BPC;
 }
 
 template <typename T>
@@ -69,8 +82,9 @@ void launch_dt(const Geo &g, const T *A, int lts, unsigned long long *red, unsig
 #define MRFV_INSTANTIATE_FV(T)                                                                  \
   template void launch_fv<T>(const Geo &, const FVArgs<T> &, int, cudaStream_t);                \
   template int fv_ctas_per_sm<T>(int);                                                          \
-  template void launch_fvh<T>(const Geo &, const FVArgs<T> &, int, cudaStream_t);               \
-  template int fvh_ctas_per_sm<T>(int);                                                         \
+  template void launch_fvs<T>(const Geo &, const FVArgs<T> &, bool, int, cudaStream_t);         \
+  template int fvs_ctas_per_sm<T>(int, bool);                                                   \
+  template int fv_blocks_per_cta<T>(int, bool);                                                 \
   template void launch_dt<T>(const Geo &, const T *, int, unsigned long long *, unsigned *, double, double, double *, \
                              double *, float *, int, cudaStream_t);
 

@@ -12,7 +12,8 @@ namespace mrfv {
 
 // multiresolution / bookkeeping kernels (mr_f32.cu, mr_f64.cu)
 template <typename T> void launch_restrict(const Geo &, int l, T *A, int grid, cudaStream_t);
-template <typename T> void launch_scales(const Geo &, const T *A, unsigned long long *red, T *scale, int grid, cudaStream_t);
+template <typename T> void launch_scales(const Geo &, const T *A, unsigned long long *red, unsigned *done, T *scale,
+                                         int grid, cudaStream_t);
 template <typename T> void launch_details(const Geo &, const T *A, const T *scale, double eps, uint8_t *sig, double *maxdet, int grid, cudaStream_t);
 template <typename T> void launch_prolong(const Geo &, int l, const int32_t *newlist, const int *nnew, T *A, int grid, cudaStream_t);
 template <typename T> void launch_ghost(const Geo &, int l0, int l1, const T *A, const T *A0, double theta, T *G, int grid, cudaStream_t);
@@ -27,8 +28,9 @@ template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw
 template <typename T> void launch_project_level(const Geo &, int l, const T *A, const double *coarse, double *out, cudaStream_t);
 // finite-volume stage and CFL reduction (fv_f32.cu, fv_f64.cu)
 template <typename T> void launch_fv(const Geo &, const FVArgs<T> &, int grid, cudaStream_t);
-template <typename T> void launch_fvh(const Geo &, const FVArgs<T> &, int grid, cudaStream_t);
-template <typename T> int fvh_ctas_per_sm(int dim);
+template <typename T> void launch_fvs(const Geo &, const FVArgs<T> &, bool hancock, int grid, cudaStream_t);
+template <typename T> int fvs_ctas_per_sm(int dim, bool hancock);
+template <typename T> int fv_blocks_per_cta(int dim, bool staged);
 template <typename T> void launch_dt(const Geo &, const T *A, int lts, unsigned long long *red, unsigned *done, double cfl,
                                      double t_end, double *dsc, double *lev, float *levf, int grid, cudaStream_t);
 template <typename T> int fv_ctas_per_sm(int dim);
@@ -42,9 +44,13 @@ void launch_init_freestack(int32_t *fs, int *ft, long long cap, int grid, cudaSt
 void launch_rebuild_lists(const Geo &, uint8_t *kbits, int32_t *tcount, int32_t *toff, int ntiles, int grid, cudaStream_t);
 int scan_tile_entries();
 void launch_cluster(const Geo &, const uint8_t *gflag, uint8_t *sig, double eta, int grid, cudaStream_t);
+size_t br_scratch_bytes(const Geo &, long long maptotal, int maxside);
+void launch_br(const Geo &, const uint8_t *gflag, uint8_t *sig, double eta, void *scratch, long long maptotal,
+               int maxside, cudaStream_t);
 void launch_set_double(double *p, double v, cudaStream_t);
 void launch_level_params(const Geo &, const double *dt, int lts, double *lev, float *levf, cudaStream_t);
-void launch_advance(const Geo &, double *t, const double *dt, double factor, long long *counter, int lts, cudaStream_t);
+void launch_advance(const Geo &, double *t, const double *dt, double factor, long long *counter, int lts,
+                    int32_t *pub, cudaStream_t);
 
 // learned refinement proposer (proposer.cu)
 template <typename T> void launch_prop_features(const Geo &, const T *U, const double *maxdet, const T *scale, double eps,
@@ -52,7 +58,8 @@ template <typename T> void launch_prop_features(const Geo &, const T *U, const d
 void prop_setup();
 void launch_prop_infer(const Geo &, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
                        const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
-                       const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaStream_t);
+                       const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaEvent_t conv_begin,
+                       cudaEvent_t conv_end, cudaStream_t);
 void launch_prop_mark(const Geo &, const float *logits, uint8_t *need, int grid, cudaStream_t);
 void launch_pack_weights(const float *blob, __nv_bfloat16 *w1, float *b1, __nv_bfloat16 *w2, float *b2,
                          __nv_bfloat16 *w3, float *b3, cudaStream_t);

@@ -95,8 +95,26 @@ __device__ __forceinline__ void scale_max_dev(const Geo &g, const T *__restrict_
 }
 
 template <typename T, int D>
-__global__ void k_scale_max(Geo g, const T *__restrict__ A, unsigned long long *red) {
+__device__ __forceinline__ void scale_final_dev(const unsigned long long *red, T *scale);
+
+// maxima of level 0, then (last CTA) the scales; the last CTA also clears the
+// maxima and its counter for the next launch
+template <typename T, int D>
+__global__ void k_scale_max(Geo g, const T *__restrict__ A, unsigned long long *red, unsigned *done, T *scale) {
   scale_max_dev<T, D>(g, A, red);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(done, 1u) == gridDim.x - 1) {
+      __threadfence();
+      unsigned long long r[3];
+      for (int k = 0; k < 3; k++) r[k] = atomicAdd(red + k, 0ull);
+      scale_final_dev<T, D>(r, scale);
+      for (int k = 0; k < 3; k++) red[k] = 0ull;
+      *done = 0u;
+      __threadfence();
+    }
+  }
 }
 
 // s_rho = max|rho|, s_E = max|rho e|, s_m = max|rho| * max|v_n|, each at least

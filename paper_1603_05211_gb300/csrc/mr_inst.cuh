@@ -13,14 +13,12 @@ void launch_restrict(const Geo &g, int l, T *A, int grid, cudaStream_t st) {
   else k_restrict<T, 3><<<grid, 512, 0, st>>>(g, l, A);
 }
 template <typename T>
-void launch_scales(const Geo &g, const T *A, unsigned long long *red, T *scale, int grid, cudaStream_t st) {
-  cudaMemsetAsync(red, 0, 3 * sizeof(unsigned long long), st);
+void launch_scales(const Geo &g, const T *A, unsigned long long *red, unsigned *done, T *scale, int grid,
+                   cudaStream_t st) {
   if (g.dim == 2) {
-    k_scale_max<T, 2><<<grid, 256, 0, st>>>(g, A, red);
-    k_scale_final<T, 2><<<1, 1, 0, st>>>(red, scale);
+    k_scale_max<T, 2><<<grid, 256, 0, st>>>(g, A, red, done, scale);
   } else {
-    k_scale_max<T, 3><<<grid, 256, 0, st>>>(g, A, red);
-    k_scale_final<T, 3><<<1, 1, 0, st>>>(red, scale);
+    k_scale_max<T, 3><<<grid, 256, 0, st>>>(g, A, red, done, scale);
   }
 }
 template <typename T>
@@ -85,7 +83,7 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
 
 #define MRFV_INSTANTIATE_MR(T)                                                                              \
   template void launch_restrict<T>(const Geo &, int, T *, int, cudaStream_t);                               \
-  template void launch_scales<T>(const Geo &, const T *, unsigned long long *, T *, int, cudaStream_t);     \
+  template void launch_scales<T>(const Geo &, const T *, unsigned long long *, unsigned *, T *, int, cudaStream_t); \
   template void launch_details<T>(const Geo &, const T *, const T *, double, uint8_t *, double *, int,      \
                                   cudaStream_t);                                                            \
   template void launch_prolong<T>(const Geo &, int, const int32_t *, const int *, T *, int, cudaStream_t);  \

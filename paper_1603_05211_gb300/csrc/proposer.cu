@@ -527,19 +527,22 @@ void prop_setup() {
 // cores; a0: BF16 [n][8], a1, a2: BF16 [n][16]
 void launch_prop_infer(const Geo &g, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
                        const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
-                       const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaStream_t st) {
+                       const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaEvent_t conv_begin,
+                       cudaEvent_t conv_end, cudaStream_t st) {
   long long n = g.mapoff[g.L + 1];
   long long tiles = (n + 127) / 128;
   // layer 1 fits three CTAs per SM in shared memory, layers 2 and 3 one
   int grid1 = (int)(tiles < 3 * nsm ? tiles : 3 * nsm), grid2 = (int)(tiles < nsm ? tiles : nsm);
   long long fb = (n + 255) / 256;
   k_feat_rows<<<(int)(fb < 4 * nsm ? fb : 4 * nsm), 256, 0, st>>>(feat, reinterpret_cast<uint4 *>(a0), n);
+  if (conv_begin) cudaEventRecord(conv_begin, st);
   k_prop_conv_tc<8, kKP1, false><<<grid1, kConvThreads, conv_smem<kKP1>(), st>>>(
       g, a0, reinterpret_cast<const uint4 *>(w1), b1, a1, nullptr);
   k_prop_conv_tc<16, kKP2, false><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
       g, a1, reinterpret_cast<const uint4 *>(w2), b2, a2, nullptr);
   k_prop_conv_tc<16, kKP2, true><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
       g, a2, reinterpret_cast<const uint4 *>(w3), b3, nullptr, logits);
+  if (conv_end) cudaEventRecord(conv_end, st);
 }
 
 void launch_prop_mark(const Geo &g, const float *logits, uint8_t *need, int grid, cudaStream_t st) {

@@ -4,6 +4,7 @@
 // prefix-scan compaction that rebuilds the neighbour tables and the work lists
 // in level-major Morton order.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 
 #include "common.h"
@@ -380,6 +381,197 @@ __global__ void k_cluster(Geo g, const uint8_t *gflag, uint8_t *sig, double eta)
   }
 }
 
+// ---------------------------------------------------------------- Berger-Rigoutsos clustering
+// The boxes of Berger and Rigoutsos (Section 2.2, the AMROC clustering) over the
+// flagged blocks of each level l < L, one CTA per level.  Each box is shrunk to
+// its flags; accepted at efficiency >= eta with no side above kBrMaxSide blocks
+// (every block of it flagged in sig); else an efficient box is bisected across
+// its longest side, and an inefficient one is cut at a hole of its signatures
+// (flags per slice; first direction with one, the hole nearest the middle), else
+// at the strongest inflection of the signatures (sign change of the second
+// difference; ties: lower direction, nearer the middle, lower index), else
+// bisected; a cut at slice i gives [lo, i] and [i+1, hi].  Boxes are processed
+// breadth-first, one warp per box: the union of accepted boxes does not depend
+// on the order, so it equals the depth-first recursion's.
+constexpr int kBrMaxSide = 8;
+constexpr int kBrMaxRounds = 4096;  // bound on the breadth-first rounds (error bit past it)
+constexpr int kBrThreads = 1024;
+
+struct BrBox {
+  int lo[3], hi[3];
+};
+
+__device__ __forceinline__ int br_flag(const Geo &g, const uint8_t *gflag, int l, int x, int y, int z) {
+  return gflag[map_index(g, l, x, y, z)] ? 1 : 0;
+}
+
+// one warp: shrink, decide, mark or push the two parts; sigs: 3 x maxside ints
+__device__ void br_warp_box(const Geo &g, int l, const uint8_t *gflag, uint8_t *sig, double eta, BrBox b,
+                            BrBox *next, int *nnext, int cap, int *sigs, int maxside) {
+  const int lane = threadIdx.x & 31;
+  const int D = g.dim;
+  int ext[3] = {b.hi[0] - b.lo[0] + 1, b.hi[1] - b.lo[1] + 1, b.hi[2] - b.lo[2] + 1};
+  long long vol = (long long)ext[0] * ext[1] * ext[2];
+  int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+  long long cnt = 0;
+  for (long long t = lane; t < vol; t += 32) {
+    int c[3] = {b.lo[0] + (int)(t % ext[0]), b.lo[1] + (int)((t / ext[0]) % ext[1]),
+                b.lo[2] + (int)(t / ((long long)ext[0] * ext[1]))};
+    if (!br_flag(g, gflag, l, c[0], c[1], c[2])) continue;
+    cnt++;
+    for (int d = 0; d < 3; d++) {
+      mn[d] = min(mn[d], c[d]);
+      mx[d] = max(mx[d], c[d]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    for (int d = 0; d < 3; d++) {
+      mn[d] = min(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+      mx[d] = max(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+    }
+  }
+  if (cnt == 0) return;
+  for (int d = 0; d < 3; d++) {
+    b.lo[d] = mn[d];
+    b.hi[d] = mx[d];
+    ext[d] = mx[d] - mn[d] + 1;
+  }
+  vol = (long long)ext[0] * ext[1] * ext[2];
+  int longest = 0;
+  bool big = false;
+  for (int d = 0; d < D; d++) {
+    if (ext[d] > kBrMaxSide) big = true;
+    if (ext[d] > ext[longest]) longest = d;
+  }
+  const bool efficient = (double)cnt >= eta * (double)vol;
+  if (efficient && !big) {
+    for (long long t = lane; t < vol; t += 32) {
+      int x = b.lo[0] + (int)(t % ext[0]), y = b.lo[1] + (int)((t / ext[0]) % ext[1]);
+      int z = b.lo[2] + (int)(t / ((long long)ext[0] * ext[1]));
+      sig[map_index(g, l, x, y, z)] = 1;
+    }
+    return;
+  }
+  int cd = -1, cut = 0;
+  if (!efficient) {
+    // signatures: flags per slice along each direction (lanes over slices)
+    for (int d = 0; d < D; d++) {
+      const int a1 = (d == 0) ? 1 : 0, a2 = (d == 2) ? 1 : 2;
+      for (int sl = lane; sl < ext[d]; sl += 32) {
+        int n = 0;
+        for (int j = 0; j < ext[a2]; j++)
+          for (int i = 0; i < ext[a1]; i++) {
+            int c[3];
+            c[d] = b.lo[d] + sl;
+            c[a1] = b.lo[a1] + i;
+            c[a2] = b.lo[a2] + j;
+            n += br_flag(g, gflag, l, c[0], c[1], c[2]);
+          }
+        sigs[d * maxside + sl] = n;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      // holes: first direction with one, nearest the middle, lower index on ties
+      for (int d = 0; d < D && cd < 0; d++) {
+        int best = -1;
+        for (int sidx = 1; sidx + 1 < ext[d]; sidx++) {
+          if (sigs[d * maxside + sidx] != 0) continue;
+          int s = b.lo[d] + sidx;
+          if (best < 0 || abs(2 * s - (b.lo[d] + b.hi[d])) < abs(2 * best - (b.lo[d] + b.hi[d]))) best = s;
+        }
+        if (best >= 0) {
+          cd = d;
+          cut = best;
+        }
+      }
+      // inflections of the signatures
+      if (cd < 0) {
+        long long bstr = 0;
+        for (int d = 0; d < D; d++) {
+          const int n = ext[d];
+          if (n < 4) continue;
+          const int *S = sigs + d * maxside;
+          for (int sidx = 1; sidx + 2 < n; sidx++) {
+            long long l1 = (long long)S[sidx - 1] - 2LL * S[sidx] + S[sidx + 1];
+            long long l2 = (long long)S[sidx] - 2LL * S[sidx + 1] + S[sidx + 2];
+            if (!((l1 < 0 && l2 > 0) || (l1 > 0 && l2 < 0))) continue;
+            long long str = l2 - l1 < 0 ? l1 - l2 : l2 - l1;
+            int pos = b.lo[d] + sidx;
+            bool better = false;
+            if (cd < 0 || str > bstr) better = true;
+            else if (str == bstr && d == cd) {
+              int dm = abs(2 * pos + 1 - (b.lo[d] + b.hi[d])), cm = abs(2 * cut + 1 - (b.lo[d] + b.hi[d]));
+              if (dm < cm) better = true;
+            }
+            if (better) {
+              cd = d;
+              cut = pos;
+              bstr = str;
+            }
+          }
+        }
+      }
+    }
+    cd = __shfl_sync(0xffffffffu, cd, 0);
+    cut = __shfl_sync(0xffffffffu, cut, 0);
+    __syncwarp();
+  }
+  if (cd < 0) {
+    cd = longest;
+    cut = (b.lo[cd] + b.hi[cd]) / 2;
+  }
+  if (lane == 0) {
+    BrBox a = b, c = b;
+    a.hi[cd] = cut;
+    c.lo[cd] = cut + 1;
+    int k = atomicAdd(nnext, 2);
+    if (k + 1 < cap) {
+      next[k] = a;
+      next[k + 1] = c;
+    } else {
+      set_err(g, EB_TREE);  // cannot happen: live boxes are disjoint and each holds a flag
+    }
+  }
+}
+
+// boxes: per level 2 lists of cap_l boxes (cap_l = blocks of the level), at
+// boxes + 2 * mapoff[l]; sigs: per level and warp 3 * maxside ints
+__global__ void __launch_bounds__(kBrThreads) k_br(Geo g, const uint8_t *gflag, uint8_t *sig, double eta, BrBox *boxes,
+                                                   int *sigs, int maxside) {
+  const int l = blockIdx.x;
+  if (l >= g.L) return;
+  __shared__ int ncur, nnext;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int cap = (int)(g.mapoff[l + 1] - g.mapoff[l]);
+  BrBox *A = boxes + 2 * g.mapoff[l], *B = A + cap;
+  int *wsig = sigs + ((long long)l * nwarps + warp) * 3 * maxside;
+  if (threadIdx.x == 0) {
+    BrBox w;
+    for (int d = 0; d < 3; d++) {
+      w.lo[d] = 0;
+      w.hi[d] = g.nb[l][d] - 1;
+    }
+    A[0] = w;
+    ncur = 1;
+  }
+  __syncthreads();
+  int round = 0;
+  for (; round < kBrMaxRounds && ncur > 0; round++) {
+    if (threadIdx.x == 0) nnext = 0;
+    __syncthreads();
+    for (int i = warp; i < ncur; i += nwarps) br_warp_box(g, l, gflag, sig, eta, A[i], B, &nnext, cap, wsig, maxside);
+    __syncthreads();
+    BrBox *t = A;
+    A = B;
+    B = t;
+    if (threadIdx.x == 0) ncur = nnext < cap ? nnext : cap;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && ncur > 0) set_err(g, EB_TREE);
+}
+
 // ---------------------------------------------------------------- scalars
 __global__ void k_set_double(double *p, double v) { *p = v; }
 
@@ -389,8 +581,12 @@ __global__ void k_level_params(Geo g, const double *dt, int lts, double *lev, fl
 }
 
 // t += factor * dt; cell-update counter += leaf cells (weighted per level for
-// level-dependent steps: a leaf of level l takes 2^l steps per coarse step)
-__global__ void k_advance(Geo g, double *t, const double *dt, double factor, long long *counter, int lts) {
+// level-dependent steps: a leaf of level l takes 2^l steps per coarse step);
+// the list offsets are copied to `pub` (host-mapped memory) when it is set
+__global__ void k_advance(Geo g, double *t, const double *dt, double factor, long long *counter, int lts,
+                          int32_t *pub) {
+  if (pub)
+    for (int i = 0; i < LK_NUM * (MAXL + 2); i++) pub[i] = g.loff[i];
   *t = *t + factor * *dt;
   long long cells = 0;
   int B = block_cells(g.dim);
@@ -440,13 +636,25 @@ int scan_tile_entries() { return SCAN_TILE; }
 void launch_cluster(const Geo &g, const uint8_t *gflag, uint8_t *sig, double eta, int grid, cudaStream_t st) {
   k_cluster<<<grid, 128, 0, st>>>(g, gflag, sig, eta);
 }
+// scratch of the Berger-Rigoutsos clustering: 2 boxes per block position, and
+// 3 * maxside signature counts per warp and level
+size_t br_scratch_bytes(const Geo &g, long long maptotal, int maxside) {
+  return (size_t)2 * maptotal * sizeof(BrBox) + (size_t)(g.L + 1) * (kBrThreads / 32) * 3 * maxside * sizeof(int) + 256;
+}
+void launch_br(const Geo &g, const uint8_t *gflag, uint8_t *sig, double eta, void *scratch, long long maptotal,
+               int maxside, cudaStream_t st) {
+  if (g.L < 1) return;
+  BrBox *boxes = reinterpret_cast<BrBox *>(scratch);
+  int *sigs = reinterpret_cast<int *>(boxes + 2 * maptotal);
+  k_br<<<g.L, kBrThreads, 0, st>>>(g, gflag, sig, eta, boxes, sigs, maxside);
+}
 void launch_set_double(double *p, double v, cudaStream_t st) { k_set_double<<<1, 1, 0, st>>>(p, v); }
 void launch_level_params(const Geo &g, const double *dt, int lts, double *lev, float *levf, cudaStream_t st) {
   k_level_params<<<1, 32, 0, st>>>(g, dt, lts, lev, levf);
 }
 void launch_advance(const Geo &g, double *t, const double *dt, double factor, long long *counter, int lts,
-                    cudaStream_t st) {
-  k_advance<<<1, 1, 0, st>>>(g, t, dt, factor, counter, lts);
+                    int32_t *pub, cudaStream_t st) {
+  k_advance<<<1, 1, 0, st>>>(g, t, dt, factor, counter, lts, pub);
 }
 
 }  // namespace mrfv

@@ -1,0 +1,88 @@
+"""Berger-Rigoutsos clustering of gradient flags (Section 2.2) on the GPU
+against the oracle: the trees (integer work) bit-exact after every step, the
+FP64 state within 1e-12."""
+import numpy as np
+import pytest
+
+import mrfv_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrfv():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    return m
+
+
+def _pair(m, levels, base, lts, seed, bc=0, dim=2, ic=mi.IC_QUADRANTS, params=None, lo=(0, 0, 0), hi=(1, 1, 1)):
+    params = params if params is not None else mi.quadrant_params(seed)
+    s = m.Solver(dim=dim, levels=levels, base_blocks=base, adapt=True, criterion="grad", lts=lts, bc=bc, lo=lo, hi=hi,
+                 clustering="br")
+    s.init_state(ic, params)
+    o = oracle.Oracle(dim, levels, base, bc=bc, lo=lo, hi=hi, clustering=oracle.CLUSTER_BR)
+    o.init(ic, params)
+    o.adapt(oracle.CRIT_GRAD)
+    return s, o
+
+
+def _same(s, o):
+    for l in range(o.levels):
+        assert np.array_equal(s.get_tree(l), o.get_exist(l)), f"tree differs on level {l}"
+
+
+def _close(s, o):
+    for l in range(o.levels):
+        g, r = s.download_level(l)[0], o.get_level(l)
+        assert np.array_equal(np.isnan(g), np.isnan(r))
+        m = ~np.isnan(r)
+        if m.any():
+            assert np.abs(g[m] - r[m]).max() <= 1e-12 * np.abs(r[m]).max()
+
+
+@pytest.mark.parametrize("lts", [False, True])
+@pytest.mark.parametrize("seed", [3, 7])
+def test_br_amr_matches_oracle(mrfv, lts, seed):
+    s, o = _pair(mrfv, 3, (8, 8, 1), lts, seed)
+    _same(s, o)
+    for l in range(2):
+        assert np.array_equal(s.get_flags(l)[0], o.get_sig(l)[0])
+    for _ in range(3):
+        dt = o.dt(0.5, lts)
+        assert s.step(0.0) == dt
+        o.step(dt, lts)
+        o.adapt(oracle.CRIT_GRAD)
+        _same(s, o)
+    _close(s, o)
+
+
+def test_br_amr_base128_levels4_flags(mrfv):
+    """The AMR workload's geometry (base 128^2, 4 levels): the clustered flags of
+    every level after initialisation and after two steps."""
+    s, o = _pair(mrfv, 4, (16, 16, 1), True, 0)
+    _same(s, o)
+    for _ in range(2):
+        dt = o.dt(0.5, True)
+        s.step(0.0)
+        o.step(dt, True)
+        o.adapt(oracle.CRIT_GRAD)
+        _same(s, o)
+
+
+def test_br_3d_matches_oracle(mrfv):
+    s, o = _pair(mrfv, 3, (2, 2, 2), False, 0, dim=3, ic=mi.IC_SHOCKTUBE, params=mi.sod_params(1, 0.4))
+    _same(s, o)
+    for _ in range(2):
+        dt = o.dt(0.5)
+        assert s.step(0.0) == dt
+        o.step(dt)
+        o.adapt(oracle.CRIT_GRAD)
+        _same(s, o)
+    _close(s, o)

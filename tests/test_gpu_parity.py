@@ -368,3 +368,28 @@ def test_blast3d_fp32_levels5_full_size_step(mrfv):
     o.adapt(oracle.CRIT_MR, 1e-3, precision=1)
     assert _finest_rel_l1(s, o, make) <= 2e-4
     assert np.all(np.abs(s.totals() - o.totals()) <= 1e-6 * np.abs(T0).max())
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("case", ["uniform", "adaptive", "mrlt", "adaptive3d"])
+def test_both_stage_kernels_match_oracle(mrfv, kernel, case):
+    """The MR-scheme stage in the pencil kernel (1) and in the staged kernel (2),
+    each forced, against the oracle (the default picks one by leaf count)."""
+    if case == "uniform":
+        s, o = pair(mrfv, 2, 1, (3, 5, 1), params=mi.quadrant_params(5))
+        steps, lts, crit = 30, False, None
+    elif case == "adaptive":
+        s, o = pair(mrfv, 2, 5, (1, 1, 1), adapt=True, params=mi.quadrant_params(1))
+        steps, lts, crit = 15, False, oracle.CRIT_MR
+    elif case == "mrlt":
+        s, o = pair(mrfv, 2, 4, (2, 2, 1), adapt=True, lts=True, params=mi.quadrant_params(3))
+        steps, lts, crit = 2, True, oracle.CRIT_MR
+    else:
+        s, o = pair(mrfv, 3, 3, (2, 2, 2), lo=(-1, -1, -1), hi=(1, 1, 1), adapt=True, ic=mi.IC_ELLIPSOID,
+                    params=mi.ellipsoid_params(4))
+        steps, lts, crit = 3, False, oracle.CRIT_MR
+    s.set_launch_shape(stage_kernel=kernel)
+    for _ in range(steps):
+        run_pair(s, o, 1, lts=lts, adapt_crit=crit)
+        assert_same_tree(s, o)
+    assert_levels_close(s, o)
