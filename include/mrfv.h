@@ -253,7 +253,8 @@ int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
    (the stage kernels' default is their occupancy limit); each value is 0..32.
    stage_kernel picks the MR-scheme stage kernel: 0 by leaf count, 1 the pencil
    kernel (one thread per line of cells), 2 the staged kernel (one thread per
-   face).  Out-of-range values give MRFV_ERR_ARG.  Every kernel loops over its
+   face), 3 the pencil kernel with two threads per line.  Out-of-range values
+   give MRFV_ERR_ARG.  Every kernel loops over its
    device-resident work list, so any shape gives the same results; captured
    step graphs are dropped and re-captured at the next step. */
 int mrfv_set_launch_shape(mrfv_ctx *ctx, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm,

@@ -28,6 +28,12 @@ constexpr int kBlockCtasPerSm = 16;
 // is faster from 512 blocks up (21 vs 34 us), so 3D always takes it.
 constexpr long long kStagedBelow2D = 2048;
 constexpr long long kStagedBelow3D = 0;
+// Below these the pencil kernel runs with two threads per line (each half a
+// line).  Measured (FP32 uniform, one / two threads per line): 2D 4096 blocks
+// 19.9 / 16.8 us, 16384 blocks 36.4 / 36.1 us, 65536 blocks 123 / 140 us; 3D 512
+// blocks 21.1 / 22.9 us.
+constexpr long long kSplitBelow2D = 8192;
+constexpr long long kSplitBelow3D = 0;
 
 struct mrfv_ctx {
   mrfv_config cfg;
@@ -35,9 +41,9 @@ struct mrfv_ctx {
   int prec;         // MRFV_FP64 / MRFV_FP32
   size_t tsize;     // bytes per state value
   cudaStream_t st;
-  int nsm, grid, bgrid, fvgrid, fv_occupancy;
+  int nsm, grid, bgrid, fvgrid[2], fv_occupancy[2];  // pencil kernel: [0] one thread per line, [1] two
   int fvs_occupancy[2], fvsgrid[2];  // staged stage kernel: [0] MR scheme, [1] MUSCL-Hancock
-  int stage_kernel;                  // 0 by leaf count, 1 pencil, 2 staged (MR scheme)
+  int stage_kernel;                  // 0 by leaf count, 1 pencil, 2 staged, 3 split pencil (MR scheme)
   char *arena;
   size_t arena_bytes;
   bool own_arena;
@@ -367,6 +373,13 @@ struct Seq {
     long long n = list_count(c, c->snap, a.kind, a.l0, a.l1);
     return n < (c->g.dim == 2 ? kStagedBelow2D : kStagedBelow3D);
   }
+  // pencil kernel with two threads per line while the list is short
+  bool use_split(const FVArgs<T> &a) const {
+    if (c->stage_kernel != 0) return c->stage_kernel == 3;
+    if (!c->snap_valid) return false;
+    long long n = list_count(c, c->snap, a.kind, a.l0, a.l1);
+    return n < (c->g.dim == 2 ? kSplitBelow2D : kSplitBelow3D);
+  }
   // launch a finite-volume stage kernel, bracketed by events when profiling
   void timed_fv(FVArgs<T> &a, bool hancock) {
     a.bytes = c->prof ? c->dbytes : nullptr;
@@ -388,7 +401,8 @@ struct Seq {
       int h = hancock ? 1 : 0;
       launch_fvs<T>(c->g, a, hancock, sized(c, a.kind, a.l0, a.l1, 1, c->fvs_bpc, c->fvsgrid[h]), c->st);
     } else {
-      launch_fv<T>(c->g, a, sized(c, a.kind, a.l0, a.l1, 1, c->fv_bpc, c->fvgrid), c->st);
+      int sp = use_split(a) ? 1 : 0;
+      launch_fv<T>(c->g, a, sp == 1, sized(c, a.kind, a.l0, a.l1, 1, c->fv_bpc, c->fvgrid[sp]), c->st);
     }
     if (c->prof) cudaEventRecord(e1, c->st);
     c->nlaunch += 1;
@@ -512,7 +526,7 @@ void apply_need(mrfv_ctx *c, bool prolong) {
   launch_free(c->g, c->need, c->freestack, c->freetop, c->grid, c->st);
   launch_alloc(c->g, c->need, c->freestack, c->freetop, c->newlist, c->nnew, c->grid, c->st);
   launch_rebuild_lists(c->g, c->kbits, c->tcount, c->toff, c->ntiles, c->grid, c->st);
-  c->nlaunch += 6;
+  c->nlaunch += 2 + rebuild_launches(c->ntiles);
   if (prolong) dispatch(c, [&](auto &s) { s.prolong_new(); });
 }
 
@@ -688,10 +702,12 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
-  c->fv_occupancy = c->prec == MRFV_FP32 ? fv_ctas_per_sm<float>(cfg->dim) : fv_ctas_per_sm<double>(cfg->dim);
+  for (int sp = 0; sp < 2; sp++)
+    c->fv_occupancy[sp] =
+        c->prec == MRFV_FP32 ? fv_ctas_per_sm<float>(cfg->dim, sp == 1) : fv_ctas_per_sm<double>(cfg->dim, sp == 1);
   c->grid = c->nsm * kGridCtasPerSm;
   c->bgrid = c->nsm * kBlockCtasPerSm;
-  c->fvgrid = c->nsm * c->fv_occupancy;
+  for (int sp = 0; sp < 2; sp++) c->fvgrid[sp] = c->nsm * c->fv_occupancy[sp];
   for (int h = 0; h < 2; h++) {
     c->fvs_occupancy[h] =
         c->prec == MRFV_FP32 ? fvs_ctas_per_sm<float>(cfg->dim, h == 1) : fvs_ctas_per_sm<double>(cfg->dim, h == 1);
@@ -1147,7 +1163,7 @@ int mrfv_proposer_train(mrfv_ctx *c, const float *feat, const uint8_t *target, i
 int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm,
                           int stage_kernel) {
   if (!c) return MRFV_ERR_ARG;
-  if (stage_kernel < 0 || stage_kernel > 2) return fail(c, MRFV_ERR_ARG, "set_launch_shape: stage_kernel is 0, 1 or 2");
+  if (stage_kernel < 0 || stage_kernel > 3) return fail(c, MRFV_ERR_ARG, "set_launch_shape: stage_kernel is 0..3");
   if (grid_ctas_per_sm < 0 || grid_ctas_per_sm > 32 || block_ctas_per_sm < 0 || block_ctas_per_sm > 32 ||
       fv_ctas_per_sm < 0 || fv_ctas_per_sm > 32)
     return fail(c, MRFV_ERR_ARG, "set_launch_shape: CTAs per SM outside 0..32");
@@ -1155,7 +1171,7 @@ int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_
   if (rc != MRFV_OK) return rc;
   c->grid = c->nsm * (grid_ctas_per_sm ? grid_ctas_per_sm : kGridCtasPerSm);
   c->bgrid = c->nsm * (block_ctas_per_sm ? block_ctas_per_sm : kBlockCtasPerSm);
-  c->fvgrid = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fv_occupancy);
+  for (int sp = 0; sp < 2; sp++) c->fvgrid[sp] = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fv_occupancy[sp]);
   for (int h = 0; h < 2; h++) c->fvsgrid[h] = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fvs_occupancy[h]);
   c->stage_kernel = stage_kernel;
   drop_graphs(c);

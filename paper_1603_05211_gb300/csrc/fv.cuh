@@ -149,7 +149,7 @@ __device__ __forceinline__ void cons_to_prim(const L *Q, L gm1, L *w) {
 #ifndef MRFV_FV_PPT32
 #define MRFV_FV_PPT32 0
 #endif
-template <typename T, int D>
+template <typename T, int D, int SPLIT = 1>
 struct FVShape {
   static constexpr int B = (D == 2) ? 64 : 512;        // interior cells
   static constexpr int TF = (D == 2) ? 8 : 64;         // cells of one face layer = pencils per direction
@@ -157,8 +157,9 @@ struct FVShape {
   static constexpr int STRIP = 2 * D * 2 * TF;         // ghost cells (two layers per face)
   static constexpr int P = MRFV_FV_PPT32 && sizeof(T) == 4 ? 2 : 1;  // pencils per thread
   static constexpr int BPC = (D == 2) ? (P == 2 ? 32 : 16) : (P == 2 ? 2 : 1);  // blocks per CTA
-  static constexpr int TPD = TF / P;                   // threads per block and direction
-  static constexpr int NT = D * TPD * BPC;             // threads per CTA
+  static constexpr int TPD = TF / P;                   // pencil groups per block and direction
+  static constexpr int NT = D * TPD * BPC * SPLIT;     // threads per CTA (SPLIT threads per pencil group)
+  static constexpr int NK = SPLIT == 1 ? 9 : 5;        // faces per thread (the middle face twice when split)
   static constexpr int PY = (D == 2) ? 9 : 8;          // padded shared-memory cell index x + PY y + PZ z
   static constexpr int PZ = (D == 2) ? 0 : 69;         // (bank-conflict free pencil stores in 2D, 2-way in 3D)
   static constexpr int RS = (D == 2) ? 74 : 552;       // padded cells per (block, variable) in shared memory
@@ -183,9 +184,9 @@ __device__ __forceinline__ T lev_at(const FVArgs<T> &a, int i) {
   else return a.lev[i];
 }
 
-template <typename T, int D>
+template <typename T, int D, int SPLIT = 1>
 constexpr size_t fv_smem_bytes() {
-  using S = FVShape<T, D>;
+  using S = FVShape<T, D, SPLIT>;
   return (size_t)D * S::BPC * S::NV * S::RS * sizeof(T);
 }
 
@@ -253,17 +254,23 @@ __device__ __forceinline__ void pencil_load(const Geo &g, const T *__restrict__ 
   }
 }
 
-// One thread per group of P pencils: the 12 cells of a line along direction n (two
-// beyond each face of the block) are converted to primitives in a sliding window;
-// each cell's limited slope is formed once, then the two face states and the
-// AUSM+ flux of each of the 9 faces, and the flux difference F_{k+1} - F_k of every
+// One thread per group of P pencils (SPLIT = 1) or two threads per group, each
+// taking one half of the line (SPLIT = 2: faces 0..4 and 4..8, the middle face
+// evaluated by both; twice the threads and half the dependency chain, for
+// hierarchies too small to fill the GPU).  The cells of a line along direction n
+// (two beyond each face of the block) are converted to primitives in a sliding
+// window; each cell's limited slope is formed once, then the two face states
+// and the AUSM+ flux of each face, and the flux difference F_{k+1} - F_k of every
 // interior cell goes to shared memory.  A second pass applies
 // Q_out = Q_0 - (lambda_1 dF_1 + lambda_2 dF_2 [+ lambda_3 dF_3]), summed in
 // direction order, to every cell.
-template <typename T, int D>
-__global__ void __launch_bounds__(FVShape<T, D>::NT, FVMinBlocks<T>::value) k_fv(Geo g, FVArgs<T> a) {
-  using S = FVShape<T, D>;
+template <typename T, int D, int SPLIT>
+__global__ void __launch_bounds__(FVShape<T, D, SPLIT>::NT,
+                                  (FVMinBlocks<T>::value / SPLIT > 0 ? FVMinBlocks<T>::value / SPLIT : 1))
+    k_fv(Geo g, FVArgs<T> a) {
+  using S = FVShape<T, D, SPLIT>;
   constexpr int B = S::B, TF = S::TF, NV = S::NV, BPC = S::BPC, RS = S::RS, NT = S::NT, P = S::P, TPD = S::TPD;
+  constexpr int NK = S::NK;
   using L = typename Lane<T, P>::type;
   extern __shared__ unsigned char smem_raw[];
   T *dFs = reinterpret_cast<T *>(smem_raw);  // [dir][block][v][RS]
@@ -271,9 +278,11 @@ __global__ void __launch_bounds__(FVShape<T, D>::NT, FVMinBlocks<T>::value) k_fv
   const L gam = L(T(g.gamma)), gm1 = L(T(g.gamma - 1.0)), goverg1 = L(T(g.gamma / (g.gamma - 1.0)));
   const int stage = a.stage;
   // pencil group of this thread: direction-major so a warp shares one direction
-  const int n = threadIdx.x / (TPD * BPC);
-  const int j = (threadIdx.x / TPD) % BPC;
+  const int n = threadIdx.x / (TPD * BPC * SPLIT);
+  const int j = (threadIdx.x / (TPD * SPLIT)) % BPC;
+  const int half = (threadIdx.x / TPD) % SPLIT;
   const int t0 = (threadIdx.x % TPD) * P;
+  const int kb = half * 4;  // first face of this thread
   int lb, le;
   list_range(g, a.kind, a.l0, a.l1, lb, le);
   if (a.bytes && blockIdx.x == 0 && threadIdx.x == 0)
@@ -287,8 +296,8 @@ __global__ void __launch_bounds__(FVShape<T, D>::NT, FVMinBlocks<T>::value) k_fv
         const int s = g.lists[a.kind * cap + i];
         const int l = g.slot_level[s];
         const int nb_lo = g.nbr[6 * s + 2 * n], nb_hi = g.nbr[6 * s + 2 * n + 1];
-        const bool rec_lo = a.record && (nb_lo == NBR_MISSING || ((g.cmask[s] >> (2 * n)) & 1));
-        const bool rec_hi = a.record && (nb_hi == NBR_MISSING || ((g.cmask[s] >> (2 * n + 1)) & 1));
+        const bool rec_lo = a.record && kb == 0 && (nb_lo == NBR_MISSING || ((g.cmask[s] >> (2 * n)) & 1));
+        const bool rec_hi = a.record && kb + NK == 9 && (nb_hi == NBR_MISSING || ((g.cmask[s] >> (2 * n + 1)) & 1));
         const bool add_lo = a.record == 2 && nb_lo == NBR_MISSING;
         const bool add_hi = a.record == 2 && nb_hi == NBR_MISSING;
         const T dtT = lev_at(a, lev_index(stage, l, 3));
@@ -303,18 +312,19 @@ __global__ void __launch_bounds__(FVShape<T, D>::NT, FVMinBlocks<T>::value) k_fv
         L wb[NV], wc[NV], slo[NV], Fprev[NV];
         {
           L Q[NV], wa[NV];
-          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, -2, Q);
+          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, kb - 2, Q);
           cons_to_prim<L, D>(Q, gm1, wa);
-          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, -1, Q);
+          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, kb - 1, Q);
           cons_to_prim<L, D>(Q, gm1, wb);
-          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, 0, Q);
+          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, kb, Q);
           cons_to_prim<L, D>(Q, gm1, wc);
-          // slope of cell -1
+          // slope of cell kb - 1
 #pragma unroll
           for (int v = 0; v < NV; v++) slo[v] = van_albada<L>(wb[v] - wa[v], wc[v] - wb[v]);
         }
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
+        for (int kk = 0; kk < NK; kk++) {
+          const int k = kb + kk;
           L wd[NV], wl[NV], wr[NV], shi[NV], F[NV];
           {
             L Q[NV];
@@ -345,7 +355,7 @@ __global__ void __launch_bounds__(FVShape<T, D>::NT, FVMinBlocks<T>::value) k_fv
               }
             }
           }
-          if (k > 0) {
+          if (kk > 0) {
 #pragma unroll
             for (int v = 0; v < NV; v++) {
               L d = F[v] - Fprev[v];

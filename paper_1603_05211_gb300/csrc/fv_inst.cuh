@@ -7,32 +7,36 @@
 
 namespace mrfv {
 
+template <typename T, int D, int SPLIT>
+void launch_fv_shape(const Geo &g, const FVArgs<T> &a, int grid, cudaStream_t st) {
+  constexpr size_t sm = fv_smem_bytes<T, D, SPLIT>();
+  k_fv<T, D, SPLIT><<<grid, FVShape<T, D, SPLIT>::NT, sm, st>>>(g, a);
+}
 template <typename T>
-void launch_fv(const Geo &g, const FVArgs<T> &a, int grid, cudaStream_t st) {
+void launch_fv(const Geo &g, const FVArgs<T> &a, bool split, int grid, cudaStream_t st) {
   if (g.dim == 2) {
-    constexpr size_t sm = fv_smem_bytes<T, 2>();
-    k_fv<T, 2><<<grid, FVShape<T, 2>::NT, sm, st>>>(g, a);
+    if (split) launch_fv_shape<T, 2, 2>(g, a, grid, st);
+    else launch_fv_shape<T, 2, 1>(g, a, grid, st);
   } else {
-    constexpr size_t sm = fv_smem_bytes<T, 3>();
-    k_fv<T, 3><<<grid, FVShape<T, 3>::NT, sm, st>>>(g, a);
+    if (split) launch_fv_shape<T, 3, 2>(g, a, grid, st);
+    else launch_fv_shape<T, 3, 1>(g, a, grid, st);
   }
 }
 
-// Opt in to the dynamic shared memory the stage kernel needs and report how
-// many CTAs fit on one SM (sizes the persistent grid).
-template <typename T>
-int fv_ctas_per_sm(int dim) {
+// Opt in to the dynamic shared memory the pencil kernel needs and report how many
+// CTAs fit on one SM (sizes the persistent grid).
+template <typename T, int D, int SPLIT>
+int fv_occupancy_of() {
   int n = 0;
-  if (dim == 2) {
-    constexpr size_t sm = fv_smem_bytes<T, 2>();
-    cudaFuncSetAttribute(k_fv<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, 2>, FVShape<T, 2>::NT, sm);
-  } else {
-    constexpr size_t sm = fv_smem_bytes<T, 3>();
-    cudaFuncSetAttribute(k_fv<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, 3>, FVShape<T, 3>::NT, sm);
-  }
+  constexpr size_t sm = fv_smem_bytes<T, D, SPLIT>();
+  cudaFuncSetAttribute(k_fv<T, D, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fv<T, D, SPLIT>, FVShape<T, D, SPLIT>::NT, sm);
   return n > 0 ? n : 1;
+}
+template <typename T>
+int fv_ctas_per_sm(int dim, bool split) {
+  if (dim == 2) return split ? fv_occupancy_of<T, 2, 2>() : fv_occupancy_of<T, 2, 1>();
+  return split ? fv_occupancy_of<T, 3, 2>() : fv_occupancy_of<T, 3, 1>();
 }
 
 // staged stage kernel (fvh.cuh): the MUSCL-Hancock stage, or the MR-scheme
@@ -80,8 +84,8 @@ void launch_dt(const Geo &g, const T *A, int lts, unsigned long long *red, unsig
 }
 
 #define MRFV_INSTANTIATE_FV(T)                                                                  \
-  template void launch_fv<T>(const Geo &, const FVArgs<T> &, int, cudaStream_t);                \
-  template int fv_ctas_per_sm<T>(int);                                                          \
+  template void launch_fv<T>(const Geo &, const FVArgs<T> &, bool, int, cudaStream_t);          \
+  template int fv_ctas_per_sm<T>(int, bool);                                                    \
   template void launch_fvs<T>(const Geo &, const FVArgs<T> &, bool, int, cudaStream_t);         \
   template int fvs_ctas_per_sm<T>(int, bool);                                                   \
   template int fv_blocks_per_cta<T>(int, bool);                                                 \

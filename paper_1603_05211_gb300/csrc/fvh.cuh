@@ -1,9 +1,10 @@
-// MUSCL-Hancock stage: the finite-volume scheme of the paper's AMR method
-// (arXiv:1603.05211, Section 2: unsplit MUSCL with the Minmod limiter in the
-// primitive variables rho, v, p (Section 4.2), Hancock's half-step predictor
-// with the exact flux, AUSMDV numerical flux of Wada and Liou 1997).  One stage
-// per step: Q^{n+1} = Q^n - dt sum_n (F_{n,+} - F_{n,-}) / dx_n.
+// Staged finite-volume stage kernel: one thread per cell or face of a block held
+// in shared memory, for two schemes of arXiv:1603.05211 Section 2.
 //
+// HANCOCK = true: the scheme of the paper's AMR method: unsplit MUSCL with the
+// Minmod limiter in the primitive variables rho, v, p (Section 4.2), Hancock's
+// half-step predictor with the exact flux, AUSMDV numerical flux (Wada and Liou
+// 1997).  One stage per step: Q^{n+1} = Q^n - dt sum_n (F_{n,+} - F_{n,-}) / dx_n.
 // The predictor is unsplit: every cell's extrapolated face states w +/- s_m/2
 // are advanced by one common increment
 //   dQ = sum_m (dt/2)/dx_m (f_m(Q^{-m}) - f_m(Q^{+m}))     (direction order)
@@ -13,11 +14,17 @@
 // where it is absent, from the third-order prediction of the coarser level
 // evaluated here (the same formula and inputs as the ghost strips).
 //
+// HANCOCK = false: one stage of the MR scheme (van Albada MUSCL, AUSM+, stage
+// of the explicit midpoint rule), the same arithmetic as the pencil kernel k_fv
+// in the same order.  It trades the pencil kernel's reuse of primitives and
+// slopes along a line for many more threads with short dependency chains, which
+// wins when the hierarchy has few leaves (the launch is latency-bound).
+//
 // A CTA takes BPC blocks.  Phase 1 stages primitives of the interior, the two
-// face-halo layers and the halo edges (a 12^d tile); phase 2 forms dQ for the
-// interior and the ring of face-halo cells next to it (a 10^d tile); phase 3
-// evaluates AUSMDV once per face; phase 4 applies the update in the oracle's
-// summation order.
+// face-halo layers (and for HANCOCK the halo edges) in a 12^d tile; phase 2
+// (HANCOCK) forms dQ for the interior and the ring of face-halo cells next to it
+// (a 10^d tile); phase 3 evaluates the numerical flux once per face; phase 4
+// applies the update in the oracle's summation order.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -29,23 +36,24 @@
 
 namespace mrfv {
 
-template <typename T, int D>
-struct FVH {
+template <typename T, int D, bool HANCOCK>
+struct FVS {
   static constexpr int NV = D + 2;
   static constexpr int B = (D == 2) ? 64 : 512;      // interior cells
   static constexpr int TF = (D == 2) ? 8 : 64;       // cells of one face layer
   static constexpr int STRIP = 2 * D * 2 * TF;       // ghost-strip cells per block
   static constexpr int NE = (D == 2) ? 144 : 1728;   // staged tile: 12^d cells
-  static constexpr int NR = (D == 2) ? 100 : 1000;   // predictor tile: 10^d cells
+  static constexpr int NR = HANCOCK ? ((D == 2) ? 100 : 1000) : 0;  // predictor tile: 10^d cells
   static constexpr int NF = 9 * TF;                  // faces per direction
   static constexpr int BPC = (D == 2) ? 4 : 1;       // blocks per CTA
   static constexpr int NT = (D == 2) ? 256 : 512;    // threads per CTA
+  static constexpr int MINB = (D == 2 && sizeof(T) == 4) ? 4 : 1;  // CTAs per SM the registers must allow
   static constexpr int PER = (NE + NR) * NV + D * NF * NV;  // shared values per block
 };
 
-template <typename T, int D>
-constexpr size_t fvh_smem_bytes() {
-  return (size_t)FVH<T, D>::BPC * FVH<T, D>::PER * sizeof(T);
+template <typename T, int D, bool HANCOCK>
+constexpr size_t fvs_smem_bytes() {
+  return (size_t)FVS<T, D, HANCOCK>::BPC * FVS<T, D, HANCOCK>::PER * sizeof(T);
 }
 
 // index of cell (x, y, z) (relative to the block origin) in the staged 12^d tile
@@ -170,9 +178,9 @@ __device__ void ext_cell(const Geo &g, int l, int gx, int gy, int gz, const T *_
   for (int v = 0; v < NV; v++) Q[v] = predict<T, D, 3>(patch + v * NP, 1, 1, 1, si, sj, sk);
 }
 
-template <typename T, int D>
-__global__ void __launch_bounds__(FVH<T, D>::NT) k_fvh(Geo g, FVArgs<T> a) {
-  using S = FVH<T, D>;
+template <typename T, int D, bool HANCOCK>
+__global__ void __launch_bounds__(FVS<T, D, HANCOCK>::NT, FVS<T, D, HANCOCK>::MINB) k_fvs(Geo g, FVArgs<T> a) {
+  using S = FVS<T, D, HANCOCK>;
   constexpr int NV = S::NV, B = S::B, TF = S::TF, NE = S::NE, NR = S::NR, NF = S::NF, BPC = S::BPC, NT = S::NT;
   extern __shared__ unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
@@ -223,7 +231,7 @@ __global__ void __launch_bounds__(FVH<T, D>::NT) k_fvh(Geo g, FVArgs<T> a) {
 #pragma unroll
           for (int v = 0; v < NV; v++) Q[v] = a.Uin[((long long)v * cap + from) * B + c];
         }
-      } else if (nout == 2 && edge) {
+      } else if (HANCOCK && nout == 2 && edge) {
         const int l = g.slot_level[s];
         const int bx = g.slot_coord[3 * s], by = g.slot_coord[3 * s + 1], bz = g.slot_coord[3 * s + 2];
         ext_cell<T, D>(g, l, 8 * bx + c3[0], 8 * by + c3[1], 8 * bz + c3[2], a.Uin, a.C, a.C0, theta, Q);
@@ -236,7 +244,8 @@ __global__ void __launch_bounds__(FVH<T, D>::NT) k_fvh(Geo g, FVArgs<T> a) {
       for (int v = 0; v < NV; v++) sm[jj * S::PER + v * NE + e] = w[v];
     }
     __syncthreads();
-    // ---------------- phase 2: half-step increment of the interior and the ring
+    // ---------------- phase 2 (HANCOCK): half-step increment of the interior and the ring
+    if constexpr (HANCOCK)
     for (int q = threadIdx.x; q < BPC * NR; q += NT) {
       const int jj = q / NR, r = q % NR;
       const int i = i0 + jj;
@@ -276,15 +285,20 @@ __global__ void __launch_bounds__(FVH<T, D>::NT) k_fvh(Geo g, FVArgs<T> a) {
 #pragma unroll
       for (int v = 0; v < NV; v++) sm[jj * S::PER + NV * NE + v * NR + r] = dQ[v];
     }
-    __syncthreads();
-    // ---------------- phase 3: AUSMDV on every face
+    if (HANCOCK) __syncthreads();
+    // ---------------- phase 3: the numerical flux of every face
     for (int q = threadIdx.x; q < BPC * D * NF; q += NT) {
-      const int jj = q / (D * NF), rem = q % (D * NF), n = rem / NF, fi = rem % NF;
+      const int jj = q / (D * NF), rem = q % (D * NF), n = rem / NF, u = rem % NF;
       const int i = i0 + jj;
       if (i >= le) break;
       const int s = g.lists[a.kind * cap + i];
       const int l = g.slot_level[s];
-      const int f = fi % 9, t = fi / 9, ta = t & 7, tb = t >> 3;
+      // consecutive threads take neighbouring faces along x: unit-stride tile reads;
+      // the flux of face f (position along n) and tangential index t is stored at
+      // f + 9 t (stride 9 between threads for n >= 1: no bank conflicts)
+      const int f = (n == 0) ? u % 9 : (u >> 3) % 9;
+      const int t = (n == 0) ? u / 9 : (u & 7) + 8 * (u / 72);
+      const int fi = f + 9 * t, ta = t & 7, tb = t >> 3;
       const int t1 = (n == 0) ? 1 : 0, t2 = (n == 2) ? 1 : 2;
       int cl[3] = {0, 0, 0};
       cl[n] = f - 1;
@@ -295,8 +309,19 @@ __global__ void __launch_bounds__(FVH<T, D>::NT) k_fvh(Geo g, FVArgs<T> a) {
       const T *DQ = W + NV * NE;
       const int el = fvh_te<D>(cl[0], cl[1], cl[2]), er = el + st;
       const int rl = fvh_tr<D>(cl[0], cl[1], cl[2]), rr = rl + ((n == 0) ? 1 : (n == 1 ? 10 : 100));
-      T wl[NV], wr[NV];
-      {
+      T wl[NV], wr[NV], F[NV];
+      if constexpr (!HANCOCK) {
+        // van Albada slopes of the two cells along n, face states, AUSM+
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          T wa = W[v * NE + el], wb = W[v * NE + er];
+          T sa = van_albada<T>(wa - W[v * NE + el - st], wb - wa);
+          T sb = van_albada<T>(wb - wa, W[v * NE + er + st] - wb);
+          wl[v] = lfma(T(0.5), sa, wa);
+          wr[v] = wb - T(0.5) * sb;
+        }
+        ausm_plus<T, D>(n, wl, wr, gam, goverg1, F);
+      } else {
         T wq[NV], Qf[NV];
         // high face of the left cell
 #pragma unroll
@@ -320,9 +345,8 @@ __global__ void __launch_bounds__(FVH<T, D>::NT) k_fvh(Geo g, FVArgs<T> a) {
 #pragma unroll
         for (int v = 0; v < NV; v++) Qf[v] = Qf[v] + DQ[v * NR + rr];
         cons_to_prim<T, D>(Qf, gm1, wr);
+        ausmdv<T, D>(n, wl, wr, gam, goverg1, F);
       }
-      T F[NV];
-      ausmdv<T, D>(n, wl, wr, gam, goverg1, F);
       T *FS = sm + jj * S::PER + NV * (NE + NR);
 #pragma unroll
       for (int v = 0; v < NV; v++) FS[(n * NV + v) * NF + fi] = F[v];
@@ -332,7 +356,7 @@ __global__ void __launch_bounds__(FVH<T, D>::NT) k_fvh(Geo g, FVArgs<T> a) {
         const bool rec = nb == NBR_MISSING || ((g.cmask[s] >> (2 * n + side)) & 1);
         if (rec) {
           const bool add = a.record == 2 && nb == NBR_MISSING;
-          const T dtT = lev_at(a, lev_index(1, l, 3));
+          const T dtT = lev_at(a, lev_index(a.stage, l, 3));
 #pragma unroll
           for (int v = 0; v < NV; v++) {
             T *R = a.FR + ((long long)v * cap + s) * (2 * D * TF) + (2 * n + side) * TF + t;
@@ -353,8 +377,8 @@ __global__ void __launch_bounds__(FVH<T, D>::NT) k_fvh(Geo g, FVArgs<T> a) {
       const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
       const T *FS = sm + jj * S::PER + NV * (NE + NR);
       const int f0 = x + 9 * (y + 8 * z), f1 = y + 9 * (x + 8 * z), f2 = z + 9 * (x + 8 * y);
-      const T lam0 = lev_at(a, lev_index(1, l, 0)), lam1 = lev_at(a, lev_index(1, l, 1));
-      const T lam2 = lev_at(a, lev_index(1, l, 2));
+      const T lam0 = lev_at(a, lev_index(a.stage, l, 0)), lam1 = lev_at(a, lev_index(a.stage, l, 1));
+      const T lam2 = lev_at(a, lev_index(a.stage, l, 2));
 #pragma unroll
       for (int v = 0; v < NV; v++) {
         T r = lam0 * (FS[(0 * NV + v) * NF + f0 + 1] - FS[(0 * NV + v) * NF + f0]);

@@ -27,13 +27,13 @@ template <typename T> void launch_copy_level(const Geo &, int kind, int l0, int 
 template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw, uint8_t *gflag, int grid, cudaStream_t);
 template <typename T> void launch_project_level(const Geo &, int l, const T *A, const double *coarse, double *out, cudaStream_t);
 // finite-volume stage and CFL reduction (fv_f32.cu, fv_f64.cu)
-template <typename T> void launch_fv(const Geo &, const FVArgs<T> &, int grid, cudaStream_t);
+template <typename T> void launch_fv(const Geo &, const FVArgs<T> &, bool split, int grid, cudaStream_t);
 template <typename T> void launch_fvs(const Geo &, const FVArgs<T> &, bool hancock, int grid, cudaStream_t);
 template <typename T> int fvs_ctas_per_sm(int dim, bool hancock);
 template <typename T> int fv_blocks_per_cta(int dim, bool staged);
 template <typename T> void launch_dt(const Geo &, const T *A, int lts, unsigned long long *red, unsigned *done, double cfl,
                                      double t_end, double *dsc, double *lev, float *levf, int grid, cudaStream_t);
-template <typename T> int fv_ctas_per_sm(int dim);
+template <typename T> int fv_ctas_per_sm(int dim, bool split);
 
 // integer tree work (tree.cu)
 void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t);
@@ -43,6 +43,7 @@ void launch_alloc(const Geo &, const uint8_t *need, int32_t *fs, int *ft, int32_
 void launch_init_freestack(int32_t *fs, int *ft, long long cap, int grid, cudaStream_t);
 void launch_rebuild_lists(const Geo &, uint8_t *kbits, int32_t *tcount, int32_t *toff, int ntiles, int grid, cudaStream_t);
 int scan_tile_entries();
+int rebuild_launches(int ntiles);  // kernels launch_rebuild_lists issues
 void launch_cluster(const Geo &, const uint8_t *gflag, uint8_t *sig, double eta, int grid, cudaStream_t);
 size_t br_scratch_bytes(const Geo &, long long maptotal, int maxside);
 void launch_br(const Geo &, const uint8_t *gflag, uint8_t *sig, double eta, void *scratch, long long maptotal,
