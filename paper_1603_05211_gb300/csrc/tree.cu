@@ -161,9 +161,8 @@ __device__ __forceinline__ bool has_children(const Geo &g, int l, int bx, int by
 // One thread per Morton position of every level: kind bits of the block there
 // (exist / leaf / refined / needs ghost strips / needs flux correction), its face
 // neighbour table and its refined-neighbour mask.
-__device__ __forceinline__ void k_classify_dev(Geo g, uint8_t *kbits) {
-  long long total = g.moff[g.L + 1];
-  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < total; m += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ uint8_t classify_position(const Geo &g, long long m) {
+  {
     int l, bx, by, bz;
     uint8_t bits = 0;
     if (morton_block(g, m, l, bx, by, bz)) {
@@ -200,13 +199,19 @@ __device__ __forceinline__ void k_classify_dev(Geo g, uint8_t *kbits) {
         if (leaf && cm) bits |= 1u << LK_REFLUX;
       }
     }
-    kbits[m] = bits;
+    return bits;
   }
+}
+__device__ __forceinline__ void k_classify_dev(Geo g, uint8_t *kbits) {
+  long long total = g.moff[g.L + 1];
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < total; m += (long long)gridDim.x * blockDim.x)
+    kbits[m] = classify_position(g, m);
 }
 
 constexpr int SCAN_NT = 256;
 constexpr int SCAN_PER = 8;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_PER;
+constexpr int kFusedScanTiles = 1024;  // up to this many tiles each scatter CTA sums the counts before it
 
 // per tile: number of entries of each kind
 __device__ __forceinline__ void k_tile_count_dev(Geo g, const uint8_t *kbits, int32_t *tcount, int ntiles) {
@@ -232,6 +237,37 @@ __device__ __forceinline__ void k_tile_count_dev(Geo g, const uint8_t *kbits, in
       int s = 0;
       for (int w = 0; w < SCAN_NT / 32; w++) s += red[threadIdx.x][w];
       tcount[threadIdx.x * ntiles + tile] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Classification and tile counts in one pass (each thread classifies its
+// SCAN_PER consecutive Morton positions, then the CTA counts the tile).
+__global__ void k_classify_count(Geo g, uint8_t *kbits, int32_t *tcount, int ntiles) {
+  __shared__ int32_t red[LK_NUM][SCAN_NT / 32];
+  long long total = g.moff[g.L + 1];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int cnt[LK_NUM] = {0, 0, 0, 0, 0};
+    long long base = (long long)tile * SCAN_TILE + threadIdx.x * SCAN_PER;
+    for (int j = 0; j < SCAN_PER; j++) {
+      long long m = base + j;
+      if (m < total) {
+        uint8_t b = classify_position(g, m);
+        kbits[m] = b;
+        for (int k = 0; k < LK_NUM; k++) cnt[k] += (b >> k) & 1;
+      }
+    }
+    for (int k = 0; k < LK_NUM; k++) {
+      int c = cnt[k];
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < LK_NUM) {
+      int sum = 0;
+      for (int w = 0; w < SCAN_NT / 32; w++) sum += red[threadIdx.x][w];
+      tcount[threadIdx.x * ntiles + tile] = sum;
     }
     __syncthreads();
   }
@@ -281,8 +317,12 @@ __device__ __forceinline__ void k_tile_scan_dev(Geo g, const int32_t *tcount, in
 }
 
 // per tile: local exclusive scan, scatter slots into the lists; the thread that
-// owns the first Morton position of a level writes that level's list offsets
-__device__ __forceinline__ void k_scatter_dev(Geo g, const uint8_t *kbits, const int32_t *toff, int ntiles) {
+// owns the first Morton position of a level writes that level's list offsets.
+// toff == null: each CTA forms its tile's exclusive prefix from the tile counts
+// itself (few tiles), and CTA 0 writes the totals.
+__device__ __forceinline__ void k_scatter_dev(Geo g, const uint8_t *kbits, const int32_t *toff, int ntiles,
+                                             const int32_t *tcount = nullptr) {
+  __shared__ int32_t pre[LK_NUM][SCAN_NT / 32], alls[LK_NUM][SCAN_NT / 32];
   __shared__ int32_t wsum[LK_NUM][SCAN_NT / 32];
   long long total = g.moff[g.L + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -305,9 +345,41 @@ __device__ __forceinline__ void k_scatter_dev(Geo g, const uint8_t *kbits, const
       if (lane == 31) wsum[k][warp] = x;
       excl[k] = x - cnt[k];
     }
+    if (!toff) {
+      // counts of the tiles before this one (and, for tile 0, of all tiles)
+      int part[LK_NUM] = {0, 0, 0, 0, 0}, all[LK_NUM] = {0, 0, 0, 0, 0};
+      for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+        for (int k = 0; k < LK_NUM; k++) {
+          int c = tcount[k * ntiles + t];
+          if (t < tile) part[k] += c;
+          all[k] += c;
+        }
+      for (int k = 0; k < LK_NUM; k++) {
+        for (int o = 16; o > 0; o >>= 1) {
+          part[k] += __shfl_xor_sync(0xffffffffu, part[k], o);
+          all[k] += __shfl_xor_sync(0xffffffffu, all[k], o);
+        }
+      }
+      if (lane == 0)
+        for (int k = 0; k < LK_NUM; k++) {
+          pre[k][warp] = part[k];
+          alls[k][warp] = all[k];
+        }
+      __syncthreads();
+      if (tile == 0 && threadIdx.x < LK_NUM) {  // the totals of every kind
+        int sum = 0;
+        for (int w = 0; w < SCAN_NT / 32; w++) sum += alls[threadIdx.x][w];
+        g.loff[threadIdx.x * (MAXL + 2) + g.L + 1] = sum;
+      }
+    }
     __syncthreads();
     for (int k = 0; k < LK_NUM; k++) {
-      int add = toff[k * ntiles + tile];
+      int add = 0;
+      if (toff) {
+        add = toff[k * ntiles + tile];
+      } else {
+        for (int w = 0; w < SCAN_NT / 32; w++) add += pre[k][w];
+      }
       for (int w = 0; w < warp; w++) add += wsum[k][w];
       excl[k] += add;
     }
@@ -345,6 +417,9 @@ __global__ void k_tile_scan(Geo g, const int32_t *tcount, int32_t *toff, int nti
 }
 __global__ void k_scatter(Geo g, const uint8_t *kbits, const int32_t *toff, int ntiles) {
   k_scatter_dev(g, kbits, toff, ntiles);
+}
+__global__ void k_scatter_prefix(Geo g, const uint8_t *kbits, const int32_t *tcount, int ntiles) {
+  k_scatter_dev(g, kbits, nullptr, ntiles, tcount);
 }
 
 // ---------------------------------------------------------------- gradient flags: row clustering
@@ -626,12 +701,19 @@ void launch_init_freestack(int32_t *fs, int *ft, long long cap, int grid, cudaSt
 }
 void launch_rebuild_lists(const Geo &g, uint8_t *kbits, int32_t *tcount, int32_t *toff, int ntiles, int grid,
                           cudaStream_t st) {
+  if (ntiles <= kFusedScanTiles) {
+    // few tiles: classification fused with the counts, each scatter CTA forms its prefix
+    k_classify_count<<<fit(ntiles, 1, grid), SCAN_NT, 0, st>>>(g, kbits, tcount, ntiles);
+    k_scatter_prefix<<<fit(ntiles, 1, grid), SCAN_NT, 0, st>>>(g, kbits, tcount, ntiles);
+    return;
+  }
   k_classify<<<fit(g.moff[g.L + 1], 256, grid), 256, 0, st>>>(g, kbits);
   k_tile_count<<<fit(ntiles, 1, grid), SCAN_NT, 0, st>>>(g, kbits, tcount, ntiles);
   k_tile_scan<<<1, 1024, 0, st>>>(g, tcount, toff, ntiles);
   k_scatter<<<fit(ntiles, 1, grid), SCAN_NT, 0, st>>>(g, kbits, toff, ntiles);
 }
 int scan_tile_entries() { return SCAN_TILE; }
+int rebuild_launches(int ntiles) { return ntiles <= kFusedScanTiles ? 2 : 4; }
 
 void launch_cluster(const Geo &g, const uint8_t *gflag, uint8_t *sig, double eta, int grid, cudaStream_t st) {
   k_cluster<<<grid, 128, 0, st>>>(g, gflag, sig, eta);
