@@ -309,10 +309,57 @@ def proposer_miss_rate(m, stream, levels, t_end, w, nsteps):
             "proposed_new_blocks_per_step": prop / max(1, nsteps)}
 
 
+def shock_stop_time(m, stream, levels, frac=0.8, max_steps=20000):
+    """Stop rule of the 3D blast workload: the time at which the shock reaches frac
+    of the domain half-width, taken as the outer face of the outermost block of
+    the finest level that the MR analysis finds significant (run of the plain MR
+    heuristic, CFL steps)."""
+    import numpy as np
+
+    s = blast3d(m, stream, levels, 0.0)
+    nb = 2 << (levels - 1)  # finest blocks per side of [-1, 1]^3
+    t = 0.0
+    for _ in range(max_steps):
+        s.step(0.0, sync=True)
+        t = s.stats()["t"]
+        f = s.get_flags(levels - 1)[0]
+        idx = np.nonzero(f)
+        if idx[0].size:
+            r = max(float(np.max(np.maximum(np.abs(i / (nb / 2) - 1), np.abs((i + 1) / (nb / 2) - 1))))
+                    for i in idx)
+            if r >= frac:
+                break
+    s.close()
+    return t
+
+
+def run_to_end(s, t_end, torch, stream, max_steps=100000):
+    """Steps to t_end (CFL steps clipped to end there) with CUDA events around each
+    step: (steps, GPU ms).  The first step, which captures the step graph on the
+    host, counts as the mean of the others."""
+    ev = []
+    n = 0
+    while n < max_steps:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.step(0.0, sync=False)
+        b.record(stream)
+        ev.append((a, b))
+        n += 1
+        torch.cuda.synchronize()
+        if s.stats()["t"] >= t_end * (1 - 1e-12):
+            break
+    times = [x.elapsed_time(y) for x, y in ev]
+    if len(times) > 1:
+        times[0] = sum(times[1:]) / (len(times) - 1)
+    return n, float(sum(times))
+
+
 def run_matched3d(args):
     """3D ellipsoidal blast: adaptive MR (heuristic and learned proposer) against the
-    uniform solve on the finest grid, both to t_end, L1(rho) against a uniform solve
-    at twice the finest resolution restricted to it; GPU time of each."""
+    uniform solve on the finest grid, all to the stop rule of the workload (the
+    shock at 0.8 of the half-width) unless --t-end3d is given, L1(rho) against a
+    uniform solve at twice the finest resolution averaged onto it; GPU time of each."""
     import numpy as np
     import torch
 
@@ -323,23 +370,23 @@ def run_matched3d(args):
     stream = torch.cuda.current_stream()
     L = args.levels3d
     nfin = 16 << (L - 1)
-    t_end = args.t_end3d
+    t_end = args.t_end3d if args.t_end3d > 0 else shock_stop_time(m, stream, L)
     h3 = (2.0 / nfin) ** 3
-    out = {"case": f"blast3d_fp32_L{L - 1}", "finest": nfin, "t_end": t_end, "eps": WL["eps"]}
-    nref = count_steps_to_end(lambda: uniform3d(m, stream, 2 * nfin, t_end), t_end)
+    out = {"case": f"blast3d_fp32_L{L - 1}", "finest": nfin, "t_end": t_end,
+           "t_end_rule": "given" if args.t_end3d > 0 else "shock at 0.8 of the half-width", "eps": WL["eps"]}
+    # reference: uniform at twice the finest resolution, density averaged onto the finest grid
     r = uniform3d(m, stream, 2 * nfin, t_end)
-    for _ in range(nref):
-        r.step(0.0, sync=False)
-    rho = r.download_level(0)[0][0]
+    nref = 0
+    while r.stats()["t"] < t_end * (1 - 1e-12):
+        r.step(0.0, sync=True)
+        nref += 1
+    ref = r.download_var(0, 0, 2)
     r.close()
     torch.cuda.empty_cache()
-    ref = rho.reshape(nfin, 2, nfin, 2, nfin, 2).mean(axis=(1, 3, 5))
-    del rho
     out["reference"] = {"grid": 2 * nfin, "steps": nref}
-    nu = count_steps_to_end(lambda: uniform3d(m, stream, nfin, t_end), t_end)
     u = uniform3d(m, stream, nfin, t_end)
-    ms_u = timed_steps(u, nu, torch, stream)
-    l1_u = float(np.abs(u.download_level(0)[0][0] - ref).sum() * h3)
+    nu, ms_u = run_to_end(u, t_end, torch, stream)
+    l1_u = float(np.abs(u.download_var(0, 0, 1) - ref).sum() * h3)
     u.close()
     torch.cuda.empty_cache()
     out["uniform_fine"] = {"steps": nu, "gpu_ms": ms_u, "l1_rho": l1_u}
@@ -359,16 +406,11 @@ def run_matched3d(args):
                                 "loss_first": loss0, "loss_last": loss1, "seconds": train_s}
     out["proposer_eval"] = proposer_miss_rate(m, stream, L, t_end, w, min(args.snapshots, 40))
     for name, prop in (("adaptive", False), ("adaptive_proposer", True)):
-        def mk2(p=prop):
-            s = blast3d(m, stream, L, t_end, proposer=p)
-            if p:
-                s.proposer_set_weights(w)
-            return s
-
-        na = count_steps_to_end(mk2, t_end)
-        a = mk2()
+        a = blast3d(m, stream, L, t_end, proposer=prop)
+        if prop:
+            a.proposer_set_weights(w)
         st0 = a.stats()
-        ms_a = timed_steps(a, na, torch, stream)
+        na, ms_a = run_to_end(a, t_end, torch, stream)
         st1 = a.stats()
         l1_a = float(np.abs(a.project_finest()[0] - ref).sum() * h3)
         a.close()
@@ -757,7 +799,8 @@ def main():
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
-    ap.add_argument("--t-end3d", dest="t_end3d", type=float, default=0.1)
+    ap.add_argument("--t-end3d", dest="t_end3d", type=float, default=0.0,
+                    help="end time of --case matched3d; 0: the workload's stop rule (shock at 0.8 of the half-width)")
     ap.add_argument("--snapshots", type=int, default=60)
     ap.add_argument("--train-steps", dest="train_steps", type=int, default=300)
     ap.add_argument("--n", type=int, default=4096)

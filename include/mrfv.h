@@ -201,6 +201,12 @@ int mrfv_get_stats(mrfv_ctx *ctx, mrfv_stats *out);
 /* Dense copy of level l into host[nv * cells(l)] (double; NaN in absent
    blocks); exist (may be NULL) receives the block map of level l. */
 int mrfv_download_level(mrfv_ctx *ctx, int level, double *host, int64_t n, uint8_t *exist);
+/* One conserved variable of a dense level, averaged over cubes of coarsen^d
+   cells (coarsen 1, 2, 4 or 8; cell means, as the projection of Section 2.1);
+   host[(k*n1 + j)*n0 + i] with n = cells(level) / coarsen^d; NaN where a block is
+   absent.  For measuring errors against a fine reference without moving every
+   variable of it (no counterpart in the paper). */
+int mrfv_download_var(mrfv_ctx *ctx, int level, int var, int coarsen, double *host, int64_t n);
 /* Write host[nv * cells(l)] into the existing blocks of level l. */
 int mrfv_upload_level(mrfv_ctx *ctx, int level, const double *host, int64_t n);
 

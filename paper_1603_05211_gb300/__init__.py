@@ -87,6 +87,7 @@ SIGNATURES = {
     "mrfv_conserved_totals": (_I, [_P, _DP, _I]),
     "mrfv_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "mrfv_download_level": (_I, [_P, _I, _DP, _I64, _U8]),
+    "mrfv_download_var": (_I, [_P, _I, _I, _I, _DP, _I64]),
     "mrfv_upload_level": (_I, [_P, _I, _DP, _I64]),
     "mrfv_project_finest": (_I, [_P, _DP, _I64]),
     "mrfv_get_tree": (_I, [_P, _I, _U8, _I64]),
@@ -272,6 +273,13 @@ class Solver:
         ex = np.empty(self.blocks_shape(level), dtype=np.uint8)
         self._check(self.lib.mrfv_download_level(self._h, level, _dp(out), out.size, _u8(ex)))
         return out, ex
+
+    def download_var(self, level: int, var: int = 0, coarsen: int = 1) -> np.ndarray:
+        """One variable of a dense level, averaged over coarsen^d-cell cubes (NaN where absent)."""
+        shape = tuple(n // coarsen for n in self.cells_shape(level))
+        out = np.empty(shape, dtype=np.float64)
+        self._check(self.lib.mrfv_download_var(self._h, level, var, coarsen, _dp(out), out.size))
+        return out
 
     def upload_level(self, level: int, data) -> None:
         a = np.ascontiguousarray(data, dtype=np.float64)

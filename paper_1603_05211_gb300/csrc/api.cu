@@ -1001,6 +1001,24 @@ int mrfv_download_level(mrfv_ctx *c, int level, double *host, int64_t n, uint8_t
   return rc;
 }
 
+int mrfv_download_var(mrfv_ctx *c, int level, int var, int coarsen, double *host, int64_t n) {
+  if (!c || level < 0 || level > c->g.L || !host || var < 0 || var >= c->g.nv)
+    return fail(c, MRFV_ERR_ARG, "download_var: arguments");
+  if (coarsen != 1 && coarsen != 2 && coarsen != 4 && coarsen != 8)
+    return fail(c, MRFV_ERR_ARG, "download_var: coarsen is 1, 2, 4 or 8");
+  long long nc = level_cells(c->g, level);
+  long long per = c->g.dim == 3 ? (long long)coarsen * coarsen * coarsen : (long long)coarsen * coarsen;
+  if (n != nc / per) return fail(c, MRFV_ERR_ARG, "download_var: n must be cells(level) / coarsen^d");
+  double *buf = nullptr;
+  if (cudaMalloc(&buf, n * 8) != cudaSuccess) return fail(c, MRFV_ERR_CUDA, "download_var: staging allocation");
+  dispatch(c, [&](auto &s) { launch_gather_var(c->g, level, var, coarsen, s.U(), buf, c->st); });
+  int rc = check_launch(c, "mrfv_download_var");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_download_var");
+  if (rc == MRFV_OK) cudaMemcpy(host, buf, n * 8, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  return rc;
+}
+
 int mrfv_upload_level(mrfv_ctx *c, int level, const double *host, int64_t n) {
   if (!c || level < 0 || level > c->g.L || !host) return fail(c, MRFV_ERR_ARG, "upload: arguments");
   long long nc = level_cells(c->g, level);

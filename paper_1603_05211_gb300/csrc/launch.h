@@ -19,6 +19,7 @@ template <typename T> void launch_prolong(const Geo &, int l, const int32_t *new
 template <typename T> void launch_ghost(const Geo &, int l0, int l1, const T *A, const T *A0, double theta, T *G, int grid, cudaStream_t);
 template <typename T> void launch_init(const Geo &, const ICParams &, const double *hi, T *A, int grid, cudaStream_t);
 template <typename T> void launch_gather(const Geo &, int l, const T *A, double *out, cudaStream_t);
+template <typename T> void launch_gather_var(const Geo &, int l, int v, int f, const T *A, double *out, cudaStream_t);
 template <typename T> void launch_scatter(const Geo &, int l, const double *in, T *A, cudaStream_t);
 template <typename T> void launch_totals(const Geo &, const T *A, double *out, int grid, cudaStream_t);
 template <typename T> void launch_reflux(const Geo &, int l0, int l1, T *A, const T *FR, int grid, cudaStream_t);

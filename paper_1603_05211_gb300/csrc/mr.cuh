@@ -364,6 +364,35 @@ __global__ void k_gather_level(Geo g, int l, const T *__restrict__ A, double *__
   }
 }
 
+// one variable of level l, averaged over cubes of f^d cells (x fastest within
+// the cube, then y, then z); NaN where the block is absent
+template <typename T, int D>
+__global__ void k_gather_var(Geo g, int l, int v, int f, const T *__restrict__ A, double *__restrict__ out) {
+  constexpr int B = (D == 2) ? 64 : 512;
+  long long n0 = (long long)g.nb[l][0] * 8 / f, n1 = (long long)g.nb[l][1] * 8 / f;
+  long long n2 = (D == 3) ? (long long)g.nb[l][2] * 8 / f : 1;
+  long long nc = n0 * n1 * n2;
+  const double w = 1.0 / (double)(D == 3 ? f * f * f : f * f);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc; t += (long long)gridDim.x * blockDim.x) {
+    int i0 = (int)(t % n0) * f, j0 = (int)((t / n0) % n1) * f, k0 = (D == 3) ? (int)(t / (n0 * n1)) * f : 0;
+    double sum = 0.0;
+    bool absent = false;
+    for (int c3 = 0; c3 < (D == 3 ? f : 1); c3++)
+      for (int b = 0; b < f; b++)
+        for (int a = 0; a < f; a++) {
+          int i = i0 + a, j = j0 + b, k = k0 + c3;
+          int32_t s = g.idx[map_index(g, l, i >> 3, j >> 3, k >> 3)];
+          if (s < 0) {
+            absent = true;
+            continue;
+          }
+          int c = (i & 7) + 8 * (j & 7) + ((D == 3) ? 64 * (k & 7) : 0);
+          sum = sum + (double)A[((long long)v * g.cap + s) * B + c];
+        }
+    out[t] = absent ? (double)nan_val<T>() : sum * w;
+  }
+}
+
 template <typename T, int D>
 __global__ void k_scatter_level(Geo g, int l, const double *__restrict__ in, T *__restrict__ A) {
   constexpr int B = (D == 2) ? 64 : 512;

@@ -13,6 +13,11 @@ void launch_restrict(const Geo &g, int l, T *A, int grid, cudaStream_t st) {
   else k_restrict<T, 3><<<grid, 512, 0, st>>>(g, l, A);
 }
 template <typename T>
+void launch_gather_var(const Geo &g, int l, int v, int f, const T *A, double *out, cudaStream_t st) {
+  if (g.dim == 2) k_gather_var<T, 2><<<1024, 256, 0, st>>>(g, l, v, f, A, out);
+  else k_gather_var<T, 3><<<1024, 256, 0, st>>>(g, l, v, f, A, out);
+}
+template <typename T>
 void launch_scales(const Geo &g, const T *A, unsigned long long *red, unsigned *done, T *scale, int grid,
                    cudaStream_t st) {
   if (g.dim == 2) {
@@ -93,6 +98,7 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
   template void launch_scatter<T>(const Geo &, int, const double *, T *, cudaStream_t);                     \
   template void launch_totals<T>(const Geo &, const T *, double *, int, cudaStream_t);                      \
   template void launch_reflux<T>(const Geo &, int, int, T *, const T *, int, cudaStream_t);                 \
+  template void launch_gather_var<T>(const Geo &, int, int, int, const T *, double *, cudaStream_t);        \
   template void launch_copy_level<T>(const Geo &, int, int, int, const T *, T *, int, cudaStream_t);                  \
   template void launch_gradflags<T>(const Geo &, const T *, double, uint8_t *, int, cudaStream_t);         \
   template void launch_project_level<T>(const Geo &, int, const T *, const double *, double *, cudaStream_t);

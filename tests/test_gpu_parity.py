@@ -394,3 +394,24 @@ def test_both_stage_kernels_match_oracle(mrfv, kernel, case):
         run_pair(s, o, 1, lts=lts, adapt_crit=crit)
         assert_same_tree(s, o)
     assert_levels_close(s, o)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_download_var_coarsened_means(mrfv, dim):
+    """One variable averaged over coarsen^d cells equals the mean of the full download."""
+    if dim == 2:
+        s = mrfv.Solver(dim=2, levels=1, base_blocks=(3, 2, 1))
+        s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(1))
+    else:
+        s = mrfv.Solver(dim=3, levels=1, base_blocks=(2, 1, 2), lo=(-1, -1, -1), hi=(1, 1, 1))
+        s.init_state(mi.IC_ELLIPSOID, mi.ellipsoid_params(1))
+    s.step(0.0)
+    full = s.download_level(0)[0]
+    for var in range(dim + 2):
+        assert np.array_equal(s.download_var(0, var, 1), full[var])
+        for f in (2, 4):
+            g = s.download_var(0, var, f)
+            sh = full[var].shape
+            blocks = full[var].reshape(*[x for n in sh for x in (n // f, f)])
+            want = blocks.mean(axis=tuple(range(1, 2 * len(sh), 2)))
+            assert np.allclose(g, want, rtol=1e-14, atol=1e-14)
