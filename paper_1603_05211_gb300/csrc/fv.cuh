@@ -1,15 +1,15 @@
-// Fused finite-volume stage kernel: MUSCL reconstruction with the van Albada
-// limiter, the AUSM+ flux and the conservative RK2 stage update
-// (arXiv:1603.05211, Section 2), one flux per face of each 8^d block, plus the
-// CFL time-step reduction.
+// Finite-volume stage kernel of the MR scheme: MUSCL reconstruction of the
+// primitive variables with the van Albada limiter, the AUSM+ flux and the
+// conservative stage update of the explicit midpoint rule (arXiv:1603.05211,
+// Section 2), one flux per face of each 8^d block; and the CFL time-step
+// reduction.
 //
-// A CTA stages BPC blocks in shared memory: each block's interior and the two
-// cell layers beyond each face, read straight from the same-level neighbour's
-// interior (nbr >= 0), from the block's ghost strip (coarse-fine face, filled by
-// the prediction kernel) or, at a transmissive wall, from the block's own edge
-// cells.  Conservative -> primitive once per staged cell; then, direction by
-// direction: limited slopes -> face states, AUSM+ on every face, and the
-// residual of each interior cell accumulates in registers.
+// A CTA takes BPC blocks.  Each thread walks one line of cells of a block along
+// one direction (the direction is a compile-time parameter of the walk), with
+// the two cells beyond each face read from the same-level neighbour, the ghost
+// strip of a coarse-fine face or, at a transmissive wall, the block's own edge
+// cell; the flux differences of the lines go to shared memory, and a second
+// pass sums them per cell in direction order into the update.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -21,41 +21,17 @@
 namespace mrfv {
 
 
-// ---------------------------------------------------------------- lanes
-// The stage arithmetic is written once for a "lane" type L: a scalar (float,
-// double: one pencil per thread) or vf2 (two single-precision pencils per
-// thread in the packed FP32x2 instructions of sm_100+).  Branches are written as
-// selects of both sides, which gives the same values as the branches.
-struct vf2 {
-  float2 v;
-  __device__ __forceinline__ vf2() {}
-  __device__ __forceinline__ vf2(float a) : v(make_float2(a, a)) {}
-  __device__ __forceinline__ vf2(float a, float b) : v(make_float2(a, b)) {}
-  __device__ __forceinline__ explicit vf2(float2 x) : v(x) {}
-};
-struct mask2 {
-  bool x, y;
-};
-__device__ __forceinline__ vf2 operator+(vf2 a, vf2 b) { return vf2(__fadd2_rn(a.v, b.v)); }
-__device__ __forceinline__ vf2 operator-(vf2 a, vf2 b) { return vf2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))); }
-__device__ __forceinline__ vf2 operator*(vf2 a, vf2 b) { return vf2(__fmul2_rn(a.v, b.v)); }
-__device__ __forceinline__ vf2 operator/(vf2 a, vf2 b) { return vf2(a.v.x / b.v.x, a.v.y / b.v.y); }
-__device__ __forceinline__ mask2 operator>(vf2 a, vf2 b) { return {a.v.x > b.v.x, a.v.y > b.v.y}; }
-__device__ __forceinline__ mask2 operator>=(vf2 a, vf2 b) { return {a.v.x >= b.v.x, a.v.y >= b.v.y}; }
-__device__ __forceinline__ mask2 operator<(vf2 a, vf2 b) { return {a.v.x < b.v.x, a.v.y < b.v.y}; }
-__device__ __forceinline__ vf2 lsel(mask2 m, vf2 a, vf2 b) { return vf2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y); }
-__device__ __forceinline__ vf2 labs(vf2 a) { return vf2(fabsf(a.v.x), fabsf(a.v.y)); }
-__device__ __forceinline__ vf2 lsqrt(vf2 a) { return vf2(sqrtf(a.v.x), sqrtf(a.v.y)); }
-// a * b + c: fused for vf2; for scalars written as the product then the sum (the
-// double-precision unit is built without contraction, so it rounds both)
-__device__ __forceinline__ vf2 lfma(vf2 a, vf2 b, vf2 c) { return vf2(__ffma2_rn(a.v, b.v, c.v)); }
-
+// ---------------------------------------------------------------- arithmetic helpers
+// Branches of the flux functions are written as selects of both sides, which
+// give the same values as the branches.
 template <typename L>
 __device__ __forceinline__ L lsel(bool m, L a, L b) { return m ? a : b; }
 __device__ __forceinline__ float labs(float a) { return fabsf(a); }
 __device__ __forceinline__ double labs(double a) { return fabs(a); }
 __device__ __forceinline__ float lsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double lsqrt(double a) { return sqrt(a); }
+// a * b + c written as the product then the sum (the double-precision units are
+// compiled without contraction, so both round as the oracle's expression does)
 template <typename L>
 __device__ __forceinline__ L lfma(L a, L b, L c) { return (a * b) + c; }
 
@@ -142,22 +118,17 @@ __device__ __forceinline__ void cons_to_prim(const L *Q, L gm1, L *w) {
   w[D + 1] = gm1 * (Q[D + 1] - ((L(0.5f) * rho) * vv));
 }
 
-// Launch shape of the stage kernel for state type T in dimension D: P pencils per
-// thread, BPC blocks per CTA.  Two single-precision pencils per thread in packed
-// FP32x2 lanes (MRFV_FV_PPT32=1) measured slower on GB300 than one pencil per
-// thread (fewer warps to hide latency), so one is the default.
-#ifndef MRFV_FV_PPT32
-#define MRFV_FV_PPT32 0
-#endif
+// Launch shape of the stage kernel for state type T in dimension D: BPC blocks per
+// CTA, one thread per line of a block along each direction (SPLIT threads per
+// line).
 template <typename T, int D, int SPLIT = 1>
 struct FVShape {
   static constexpr int B = (D == 2) ? 64 : 512;        // interior cells
   static constexpr int TF = (D == 2) ? 8 : 64;         // cells of one face layer = pencils per direction
   static constexpr int NV = D + 2;
   static constexpr int STRIP = 2 * D * 2 * TF;         // ghost cells (two layers per face)
-  static constexpr int P = MRFV_FV_PPT32 && sizeof(T) == 4 ? 2 : 1;  // pencils per thread
-  static constexpr int BPC = (D == 2) ? (P == 2 ? 32 : 16) : (P == 2 ? 2 : 1);  // blocks per CTA
-  static constexpr int TPD = TF / P;                   // pencil groups per block and direction
+  static constexpr int BPC = (D == 2) ? 16 : 1;       // blocks per CTA
+  static constexpr int TPD = TF;                       // lines per block and direction
   static constexpr int NT = D * TPD * BPC * SPLIT;     // threads per CTA (SPLIT threads per pencil group)
   static constexpr int NK = SPLIT == 1 ? 9 : 5;        // faces per thread (the middle face twice when split)
   static constexpr int PY = (D == 2) ? 9 : 8;          // padded shared-memory cell index x + PY y + PZ z
@@ -190,99 +161,149 @@ constexpr size_t fv_smem_bytes() {
   return (size_t)D * S::BPC * S::NV * S::RS * sizeof(T);
 }
 
-template <typename T, int P>
-struct Lane;
-template <typename T>
-struct Lane<T, 1> {
-  using type = T;
-};
-template <>
-struct Lane<float, 2> {
-  using type = vf2;
-};
-
-// Conservative state of pencil position p (-2..9) of the P pencils (n, t0 .. t0+P-1)
-// of block s: own cells, the same-level neighbour's cells, the ghost strip, or the
-// block's own edge cell at a transmissive wall.
-template <typename T, int D, int P>
-__device__ __forceinline__ void pencil_load(const Geo &g, const T *__restrict__ U, const T *__restrict__ G, int s,
-                                            int n, int t0, int nb_lo, int nb_hi, int p,
-                                            typename Lane<T, P>::type *Q) {
-  using S = FVShape<T, D>;
-  constexpr int B = S::B, TF = S::TF, NV = S::NV;
+// One pencil pass along direction N (compile-time: strides and the normal
+// component are constants) for half HALF of the line (SPLIT = 2: faces 0..4 or
+// 4..8, the middle face evaluated by both halves) or the whole line (SPLIT = 1).
+// The line's cells come from the block itself, from beyond each face the
+// same-level neighbour's cells, the ghost strip (coarse-fine face) or, at a
+// transmissive wall, the block's own edge cell; each source is resolved once per
+// line.  Primitives move through a sliding window; each cell's limited slope is
+// formed once, then the two face states and the AUSM+ flux of each face; the
+// flux difference F_{k+1} - F_k of every interior cell goes to shared memory
+// (and dt_l F to the flux registers on the faces the correction needs).
+template <typename T, int D, int SPLIT, int N, int HALF>
+__device__ __forceinline__ void fv_pencil(const Geo &g, const FVArgs<T> &a, int s, int l, int t0, T *dF, T gam,
+                                          T gm1, T goverg1) {
+  using S = FVShape<T, D, SPLIT>;
+  constexpr int B = S::B, TF = S::TF, NV = S::NV, RS = S::RS, NK = S::NK;
+  constexpr int KB = HALF * 4;                                        // first face of this thread
+  constexpr int STRIDE = (N == 0) ? 1 : (N == 1 ? 8 : 64);            // cell stride along N
+  constexpr int SSTR = (N == 0) ? 1 : (N == 1 ? S::PY : S::PZ);       // shared-memory stride along N
   const long long cap = g.cap;
-  const int stride = (n == 0) ? 1 : (n == 1 ? 8 : 64);
+  const long long vsU = cap * B, vsG = cap * S::STRIP;
   const int t1 = t0 & 7, t2 = t0 >> 3;
-  // cell index of tangential position t0 with coordinate 0 along n; the next
-  // pencil of the thread is one cell further in the first tangential direction
-  const int base = (n == 0) ? (8 * t1 + 64 * t2) : (n == 1 ? (t1 + 64 * t2) : (t1 + 8 * t2));
-  const int tstep = (n == 0) ? 8 : 1;
-  int from = s, c;
-  if (p >= 0 && p <= 7) {
-    c = base + p * stride;
+  const int base = (N == 0) ? (8 * t1 + 64 * t2) : (N == 1 ? (t1 + 64 * t2) : (t1 + 8 * t2));
+  const int sbase = (N == 0) ? (S::PY * t1 + S::PZ * t2) : (N == 1 ? (t1 + S::PZ * t2) : (t1 + S::PY * t2));
+  const int nb_lo = g.nbr[6 * s + 2 * N], nb_hi = g.nbr[6 * s + 2 * N + 1];
+  // sources: position p in 0..7 at mid + p STRIDE; position -1-dd at lo + dd lo_step;
+  // position 8+dd at hi + dd hi_step (variable v one plane stride further)
+  const T *mid = a.Uin + (long long)s * B + base;
+  const T *lo, *hi;
+  long long lo_vs = vsU, hi_vs = vsU;
+  int lo_step, hi_step;
+  if (nb_lo == NBR_MISSING) {
+    lo = a.G + (long long)s * S::STRIP + (2 * N) * 2 * TF + t0;
+    lo_vs = vsG;
+    lo_step = TF;
+  } else if (nb_lo >= 0) {
+    lo = a.Uin + (long long)nb_lo * B + base + 7 * STRIDE;
+    lo_step = -STRIDE;
   } else {
-    const int side = p > 7 ? 1 : 0;
-    const int dd = side ? p - 8 : -1 - p;  // 0 touches the block
-    const int nb = side ? nb_hi : nb_lo;
-    if (nb == NBR_MISSING) {
-      const T *Gp = G + (long long)s * S::STRIP + (2 * n + side) * 2 * TF + dd * TF + t0;
+    lo = mid;
+    lo_step = 0;
+  }
+  if (nb_hi == NBR_MISSING) {
+    hi = a.G + (long long)s * S::STRIP + (2 * N + 1) * 2 * TF + t0;
+    hi_vs = vsG;
+    hi_step = TF;
+  } else if (nb_hi >= 0) {
+    hi = a.Uin + (long long)nb_hi * B + base;
+    hi_step = STRIDE;
+  } else {
+    hi = mid + 7 * STRIDE;
+    hi_step = 0;
+  }
+  auto load = [&](int p, T *w) {
+    const T *q;
+    long long vs;
+    if (p < 0) {
+      q = lo + (-1 - p) * lo_step;
+      vs = lo_vs;
+    } else if (p > 7) {
+      q = hi + (p - 8) * hi_step;
+      vs = hi_vs;
+    } else {
+      q = mid + p * STRIDE;
+      vs = vsU;
+    }
+    T Q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) Q[v] = q[v * vs];
+    cons_to_prim<T, D>(Q, gm1, w);
+  };
+  const bool rec_lo = a.record && KB == 0 && (nb_lo == NBR_MISSING || ((g.cmask[s] >> (2 * N)) & 1));
+  const bool rec_hi = a.record && KB + NK == 9 && (nb_hi == NBR_MISSING || ((g.cmask[s] >> (2 * N + 1)) & 1));
+  const bool add_lo = a.record == 2 && nb_lo == NBR_MISSING;
+  const bool add_hi = a.record == 2 && nb_hi == NBR_MISSING;
+  const T dtT = lev_at(a, lev_index(a.stage, l, 3));
+  // sliding window of primitives: wb = cell k-1, wc = cell k (face k lies between them)
+  T wb[NV], wc[NV], slo[NV], Fprev[NV];
+  {
+    T wa[NV];
+    load(KB - 2, wa);
+    load(KB - 1, wb);
+    load(KB, wc);
+#pragma unroll
+    for (int v = 0; v < NV; v++) slo[v] = van_albada<T>(wb[v] - wa[v], wc[v] - wb[v]);
+  }
+#pragma unroll
+  for (int kk = 0; kk < NK; kk++) {
+    const int k = KB + kk;
+    T wd[NV], wl[NV], wr[NV], shi[NV], F[NV];
+    load(k + 1, wd);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      shi[v] = van_albada<T>(wc[v] - wb[v], wd[v] - wc[v]);
+      wl[v] = lfma(T(0.5), slo[v], wb[v]);
+      wr[v] = wc[v] - T(0.5) * shi[v];
+    }
+    ausm_plus<T, D>(N, wl, wr, gam, goverg1, F);
+    if ((k == 0 && rec_lo) || (k == 8 && rec_hi)) {
+      const int side = k == 8 ? 1 : 0;
+      const bool add = side ? add_hi : add_lo;
+      T *R = a.FR + (long long)s * (2 * D * TF) + (2 * N + side) * TF + t0;
+      const long long vsR = cap * (2 * D * TF);
 #pragma unroll
       for (int v = 0; v < NV; v++) {
-        const T *q = Gp + (long long)v * cap * S::STRIP;
-        if constexpr (P == 2) Q[v] = vf2(*reinterpret_cast<const float2 *>(q));
-        else Q[v] = q[0];
+        T val = dtT * F[v];
+        R[v * vsR] = add ? R[v * vsR] + val : val;
       }
-      return;
     }
-    if (nb >= 0) {
-      from = nb;
-      c = base + (side ? dd : 7 - dd) * stride;
-    } else {
-      c = base + (side ? 7 : 0) * stride;
-    }
-  }
-  const T *Up = U + (long long)from * B + c;
+    if (kk > 0) {
 #pragma unroll
-  for (int v = 0; v < NV; v++) {
-    const T *q = Up + (long long)v * cap * B;
-    if constexpr (P == 2) {
-      if (tstep == 1) Q[v] = vf2(*reinterpret_cast<const float2 *>(q));
-      else Q[v] = vf2(q[0], q[8]);
-    } else {
-      Q[v] = q[0];
+      for (int v = 0; v < NV; v++) dF[v * RS + sbase + (k - 1) * SSTR] = F[v] - Fprev[v];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      Fprev[v] = F[v];
+      slo[v] = shi[v];
+      wb[v] = wc[v];
+      wc[v] = wd[v];
     }
   }
 }
 
-// One thread per group of P pencils (SPLIT = 1) or two threads per group, each
-// taking one half of the line (SPLIT = 2: faces 0..4 and 4..8, the middle face
-// evaluated by both; twice the threads and half the dependency chain, for
-// hierarchies too small to fill the GPU).  The cells of a line along direction n
-// (two beyond each face of the block) are converted to primitives in a sliding
-// window; each cell's limited slope is formed once, then the two face states
-// and the AUSM+ flux of each face, and the flux difference F_{k+1} - F_k of every
-// interior cell goes to shared memory.  A second pass applies
-// Q_out = Q_0 - (lambda_1 dF_1 + lambda_2 dF_2 [+ lambda_3 dF_3]), summed in
-// direction order, to every cell.
+// Finite-volume stage over the blocks of a work list: one thread per line of a
+// block along each direction (SPLIT = 2: two threads per line), then a second
+// pass applies Q_out = Q_0 - (lambda_1 dF_1 + lambda_2 dF_2 [+ lambda_3 dF_3]),
+// summed in direction order, to every cell.
 template <typename T, int D, int SPLIT>
 __global__ void __launch_bounds__(FVShape<T, D, SPLIT>::NT,
                                   (FVMinBlocks<T>::value / SPLIT > 0 ? FVMinBlocks<T>::value / SPLIT : 1))
     k_fv(Geo g, FVArgs<T> a) {
   using S = FVShape<T, D, SPLIT>;
-  constexpr int B = S::B, TF = S::TF, NV = S::NV, BPC = S::BPC, RS = S::RS, NT = S::NT, P = S::P, TPD = S::TPD;
-  constexpr int NK = S::NK;
-  using L = typename Lane<T, P>::type;
+  constexpr int B = S::B, NV = S::NV, BPC = S::BPC, RS = S::RS, NT = S::NT, TPD = S::TPD;
   extern __shared__ unsigned char smem_raw[];
   T *dFs = reinterpret_cast<T *>(smem_raw);  // [dir][block][v][RS]
+  __shared__ int sslot[BPC];
+  __shared__ T slam[BPC][3];
   const long long cap = g.cap;
-  const L gam = L(T(g.gamma)), gm1 = L(T(g.gamma - 1.0)), goverg1 = L(T(g.gamma / (g.gamma - 1.0)));
-  const int stage = a.stage;
-  // pencil group of this thread: direction-major so a warp shares one direction
+  const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
+  // line of this thread: direction-major so a warp shares one direction
   const int n = threadIdx.x / (TPD * BPC * SPLIT);
   const int j = (threadIdx.x / (TPD * SPLIT)) % BPC;
   const int half = (threadIdx.x / TPD) % SPLIT;
-  const int t0 = (threadIdx.x % TPD) * P;
-  const int kb = half * 4;  // first face of this thread
+  const int t0 = threadIdx.x % TPD;
   int lb, le;
   list_range(g, a.kind, a.l0, a.l1, lb, le);
   if (a.bytes && blockIdx.x == 0 && threadIdx.x == 0)
@@ -295,107 +316,40 @@ __global__ void __launch_bounds__(FVShape<T, D, SPLIT>::NT,
       if (i < le) {
         const int s = g.lists[a.kind * cap + i];
         const int l = g.slot_level[s];
-        const int nb_lo = g.nbr[6 * s + 2 * n], nb_hi = g.nbr[6 * s + 2 * n + 1];
-        const bool rec_lo = a.record && kb == 0 && (nb_lo == NBR_MISSING || ((g.cmask[s] >> (2 * n)) & 1));
-        const bool rec_hi = a.record && kb + NK == 9 && (nb_hi == NBR_MISSING || ((g.cmask[s] >> (2 * n + 1)) & 1));
-        const bool add_lo = a.record == 2 && nb_lo == NBR_MISSING;
-        const bool add_hi = a.record == 2 && nb_hi == NBR_MISSING;
-        const T dtT = lev_at(a, lev_index(stage, l, 3));
-        // padded shared-memory index of the first pencil's position 0, stride along n,
-        // step to the next pencil of the thread
-        const int t1 = t0 & 7, t2 = t0 >> 3;
-        const int base = (n == 0) ? (S::PY * t1 + S::PZ * t2) : (n == 1 ? (t1 + S::PZ * t2) : (t1 + S::PY * t2));
-        const int stride = (n == 0) ? 1 : (n == 1 ? S::PY : S::PZ);
-        const int pstep = (n == 0) ? S::PY : 1;
-        T *dF = dFs + ((size_t)(n * BPC + j) * NV) * RS;
-        // sliding window of primitives: wb = cell k-1, wc = cell k (face k lies between them)
-        L wb[NV], wc[NV], slo[NV], Fprev[NV];
-        {
-          L Q[NV], wa[NV];
-          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, kb - 2, Q);
-          cons_to_prim<L, D>(Q, gm1, wa);
-          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, kb - 1, Q);
-          cons_to_prim<L, D>(Q, gm1, wb);
-          pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, kb, Q);
-          cons_to_prim<L, D>(Q, gm1, wc);
-          // slope of cell kb - 1
+        if (n == 0 && half == 0 && t0 == 0) {
+          sslot[j] = s;
 #pragma unroll
-          for (int v = 0; v < NV; v++) slo[v] = van_albada<L>(wb[v] - wa[v], wc[v] - wb[v]);
+          for (int d = 0; d < 3; d++) slam[j][d] = lev_at(a, lev_index(a.stage, l, d));
         }
-#pragma unroll
-        for (int kk = 0; kk < NK; kk++) {
-          const int k = kb + kk;
-          L wd[NV], wl[NV], wr[NV], shi[NV], F[NV];
-          {
-            L Q[NV];
-            pencil_load<T, D, P>(g, a.Uin, a.G, s, n, t0, nb_lo, nb_hi, k + 1, Q);
-            cons_to_prim<L, D>(Q, gm1, wd);
-          }
-#pragma unroll
-          for (int v = 0; v < NV; v++) {
-            shi[v] = van_albada<L>(wc[v] - wb[v], wd[v] - wc[v]);
-            wl[v] = lfma(L(T(0.5)), slo[v], wb[v]);
-            wr[v] = wc[v] - L(T(0.5)) * shi[v];
-          }
-          ausm_plus<L, D>(n, wl, wr, gam, goverg1, F);
-          if ((k == 0 && rec_lo) || (k == 8 && rec_hi)) {
-            const int side = k == 8 ? 1 : 0;
-            const bool add = side ? add_hi : add_lo;
-#pragma unroll
-            for (int v = 0; v < NV; v++) {
-              T *R = a.FR + ((long long)v * cap + s) * (2 * D * TF) + (2 * n + side) * TF + t0;
-              if constexpr (P == 2) {
-                float2 val = __fmul2_rn(make_float2(dtT, dtT), F[v].v);
-                float2 *R2 = reinterpret_cast<float2 *>(R);
-                if (add) val = __fadd2_rn(*R2, val);
-                *R2 = val;
-              } else {
-                T val = dtT * F[v];
-                *R = add ? *R + val : val;
-              }
-            }
-          }
-          if (kk > 0) {
-#pragma unroll
-            for (int v = 0; v < NV; v++) {
-              L d = F[v] - Fprev[v];
-              T *dst = dF + v * RS + base + (k - 1) * stride;
-              if constexpr (P == 2) {
-                dst[0] = d.v.x;
-                dst[pstep] = d.v.y;
-              } else {
-                dst[0] = d;
-              }
-            }
-          }
-#pragma unroll
-          for (int v = 0; v < NV; v++) {
-            Fprev[v] = F[v];
-            slo[v] = shi[v];
-            wb[v] = wc[v];
-            wc[v] = wd[v];
-          }
+        T *dF = dFs + ((size_t)(n * BPC + j) * NV) * RS;
+        if (n == 0) {
+          if (SPLIT == 2 && half) fv_pencil<T, D, SPLIT, 0, (SPLIT == 2 ? 1 : 0)>(g, a, s, l, t0, dF, gam, gm1, goverg1);
+          else fv_pencil<T, D, SPLIT, 0, 0>(g, a, s, l, t0, dF, gam, gm1, goverg1);
+        } else if (n == 1) {
+          if (SPLIT == 2 && half) fv_pencil<T, D, SPLIT, 1, (SPLIT == 2 ? 1 : 0)>(g, a, s, l, t0, dF, gam, gm1, goverg1);
+          else fv_pencil<T, D, SPLIT, 1, 0>(g, a, s, l, t0, dF, gam, gm1, goverg1);
+        } else if constexpr (D == 3) {
+          if (SPLIT == 2 && half) fv_pencil<T, D, SPLIT, 2, (SPLIT == 2 ? 1 : 0)>(g, a, s, l, t0, dF, gam, gm1, goverg1);
+          else fv_pencil<T, D, SPLIT, 2, 0>(g, a, s, l, t0, dF, gam, gm1, goverg1);
         }
       }
     }
     __syncthreads();
     // ---------------- update pass
+    const long long vsU = cap * B;
     for (int q = threadIdx.x; q < BPC * B; q += NT) {
       const int jj = q / B, c = q % B;
-      const int i = i0 + jj;
-      if (i >= le) break;
-      const int s = g.lists[a.kind * cap + i];
-      const int l = g.slot_level[s];
+      if (i0 + jj >= le) break;
+      const int s = sslot[jj];
       const int cp = (c & 7) + S::PY * ((c >> 3) & 7) + S::PZ * (c >> 6);
-      const T lam0 = lev_at(a, lev_index(stage, l, 0)), lam1 = lev_at(a, lev_index(stage, l, 1));
-      const T lam2 = lev_at(a, lev_index(stage, l, 2));
+      const T lam0 = slam[jj][0], lam1 = slam[jj][1], lam2 = slam[jj][2];
+      const long long o = (long long)s * B + c;
 #pragma unroll
       for (int v = 0; v < NV; v++) {
         T r = lam0 * dFs[((size_t)(0 * BPC + jj) * NV + v) * RS + cp];
         r = r + lam1 * dFs[((size_t)(1 * BPC + jj) * NV + v) * RS + cp];
         if (D == 3) r = r + lam2 * dFs[((size_t)(2 * BPC + jj) * NV + v) * RS + cp];
-        long long o = ((long long)v * cap + s) * B + c;
-        a.Uout[o] = a.U0[o] - r;
+        a.Uout[o + v * vsU] = a.U0[o + v * vsU] - r;
       }
     }
     __syncthreads();

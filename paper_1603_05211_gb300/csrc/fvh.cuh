@@ -286,9 +286,12 @@ __global__ void __launch_bounds__(FVS<T, D, HANCOCK>::NT, FVS<T, D, HANCOCK>::MI
       for (int v = 0; v < NV; v++) sm[jj * S::PER + NV * NE + v * NR + r] = dQ[v];
     }
     if (HANCOCK) __syncthreads();
-    // ---------------- phase 3: the numerical flux of every face
-    for (int q = threadIdx.x; q < BPC * D * NF; q += NT) {
-      const int jj = q / (D * NF), rem = q % (D * NF), n = rem / NF, u = rem % NF;
+    // ---------------- phase 3: the numerical flux of every face, one direction at a
+    // time (the direction is a constant in each copy of the loop body)
+#pragma unroll
+    for (int n = 0; n < D; n++)
+    for (int q = threadIdx.x; q < BPC * NF; q += NT) {
+      const int jj = q / NF, u = q % NF;
       const int i = i0 + jj;
       if (i >= le) break;
       const int s = g.lists[a.kind * cap + i];
