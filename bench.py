@@ -755,6 +755,110 @@ def run_laxliu(args):
     print(json.dumps(out), flush=True)
 
 
+def run_paper3d(args):
+    """The paper's 3D benchmark (Section 4.2, Tables 6-8): the rotated ellipsoid on
+    [-2,2]^3 to t_e = 0.28 with N_I = 16 * 2^(L-5) fixed steps at scale levels
+    L = 5..8 (finest 2^L cells per side, level 0 one block of 8^3, the paper's
+    8^3 base mesh), single precision on the GPU.  FV: uniform 2^L grid of each
+    scheme.  MR, MRLT: eps = 0.013; AMR, AMRLT: density and pressure gradient
+    flags (eps_rho = eps_p = 0.05) clustered by Berger-Rigoutsos (eta 0.8), the
+    AMR scheme.  Reference: the AMR scheme on a uniform 1024^3 grid with CFL 0.4
+    steps to t_e, cell means onto each level.  L1(rho) = sum |rho - rho_ref| h^3.
+    Reports L1, rates, perturbation, accumulated cells and leaves (with
+    compression), GPU time and time compression against the FV run of the same
+    scheme."""
+    import numpy as np
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    P = mi.paper3d_params()
+    te = 0.28
+    Ls = [int(x) for x in args.paper3d_levels.split(",")]
+    lo, hi = (-2.0, -2.0, -2.0), (2.0, 2.0, 2.0)
+
+    def solver(n_cells, levels, scheme, adapt=False, lts=False, crit="mr", cfl=0.4, t_end=0.0):
+        nb = n_cells // (8 << (levels - 1))
+        return m.Solver(dim=3, precision="fp32", levels=levels, base_blocks=(nb, nb, nb), lo=lo, hi=hi,
+                        adapt=adapt, lts=lts, criterion=crit, eps=0.013, eps_w=0.05, eps_p=0.05, eta_tol=0.8,
+                        cfl=cfl, t_end=t_end, stream=stream, scheme=scheme, clustering="br")
+
+    nref = args.paper3d_ref
+    r = solver(nref, 1, "hancock", t_end=te)
+    r.init_state(mi.IC_ROTATED_ELLIPSOID, P)
+    nr_steps = 0
+    t0 = time.perf_counter()
+    while r.stats()["t"] < te * (1 - 1e-12) and nr_steps < 100000:
+        r.step(0.0, sync=True)
+        nr_steps += 1
+    ref_s = time.perf_counter() - t0
+    # cell means of the reference on each level: coarsened on the device to the
+    # finest level asked for (a factor of at most 8), then on the host
+    Lmax = max(Ls)
+    base = r.download_var(0, 0, nref >> Lmax)
+    refs = {}
+    for L in Ls:
+        k = 1 << (Lmax - L)
+        n = 1 << L
+        refs[L] = base.reshape(n, k, n, k, n, k).mean(axis=(1, 3, 5))
+    r.close()
+    torch.cuda.empty_cache()
+    out = {"case": "paper3d_rotated_ellipsoid", "t_end": te,
+           "reference": {"grid": nref, "steps": nr_steps, "cfl": 0.4, "scheme": "hancock", "wall_s": ref_s},
+           "rows": []}
+
+    def l1_at(rho, L):
+        n = 1 << L
+        return float(np.abs(rho - refs[L]).sum() * (4.0 / n) ** 3)
+
+    for L in Ls:
+        n = 1 << L
+        NI = 16 << (L - 5)
+        dt = te / NI
+        levels = L - 2  # blocks of 8 cells: level 0 has one block
+        row = {"L": L, "N": n, "N_I": NI}
+        for scheme, fvname in (("muscl_rk2", "FV_MR"), ("hancock", "FV_AMR")):
+            u = solver(n, 1, scheme)
+            u.init_state(mi.IC_ROTATED_ELLIPSOID, P)
+            ms = timed_steps(u, NI, torch, stream, dt=dt)
+            row[fvname] = {"l1_rho": l1_at(u.download_var(0, 0, 1), L), "gpu_ms": ms}
+            u.close()
+        variants = (("MR", "muscl_rk2", False, "mr", "FV_MR"), ("MRLT", "muscl_rk2", True, "mr", "FV_MR"),
+                    ("AMR", "hancock", False, "grad", "FV_AMR"), ("AMRLT", "hancock", True, "grad", "FV_AMR"))
+        for name, scheme, lts, crit, fvname in variants:
+            steps = NI >> (levels - 1) if lts else NI
+            a = solver(n, levels, scheme, adapt=True, lts=lts, crit=crit)
+            a.init_state(mi.IC_ROTATED_ELLIPSOID, P)
+            C = Lf = 0
+            mult = (1 << (levels - 1)) if lts else 1
+            for _ in range(steps):
+                st = a.stats()
+                C += st["total_blocks"] * 512 * mult
+                Lf += st["total_leaves"] * 512 * mult
+                a.step(dt, sync=True)
+            l1 = l1_at(a.project_finest()[0], L)
+            a.close()
+            a = solver(n, levels, scheme, adapt=True, lts=lts, crit=crit)
+            a.init_state(mi.IC_ROTATED_ELLIPSOID, P)
+            ms = timed_steps(a, steps, torch, stream, dt=dt)
+            a.close()
+            fv = row[fvname]
+            row[name] = {"l1_rho": l1, "perturbation_pct": 100.0 * abs(l1 - fv["l1_rho"]) / fv["l1_rho"],
+                         "cells_1e6": C / 1e6, "cell_compression_pct": 100.0 * C / (NI * n ** 3),
+                         "leaves_1e6": Lf / 1e6, "leaf_compression_pct": 100.0 * Lf / (NI * n ** 3),
+                         "gpu_ms": ms, "time_compression_pct": 100.0 * ms / fv["gpu_ms"]}
+            torch.cuda.empty_cache()
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+    for key in ("FV_MR", "FV_AMR", "MR", "MRLT", "AMR", "AMRLT"):
+        e = [r_[key]["l1_rho"] for r_ in out["rows"]]
+        out.setdefault("rates", {})[key] = [float(np.log2(e[i] / e[i + 1])) for i in range(len(e) - 1)]
+    print(json.dumps(out), flush=True)
+
+
 def run_case(args):
     """Single uniform-grid case (the profiling workload): levels=1, n^d cells, CFL steps only."""
     import torch
@@ -795,7 +899,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default="adaptive", choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu"],
+    ap.add_argument("--case", default="adaptive",
+                    choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d"],
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
@@ -806,12 +911,15 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--laxliu-levels", dest="laxliu_levels", default="7,8,9,10")
     ap.add_argument("--laxliu-ref", dest="laxliu_ref", type=int, default=4096, help="reference grid of --case laxliu")
+    ap.add_argument("--paper3d-levels", dest="paper3d_levels", default="5,6,7,8")
+    ap.add_argument("--paper3d-ref", dest="paper3d_ref", type=int, default=1024, help="reference grid of --case paper3d")
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--scheme", default="muscl_rk2", choices=["muscl_rk2", "hancock"],
                     help="finite-volume scheme of the uniform case")
-    ap.add_argument("--stage-kernel", dest="stage_kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="uniform case: 0 by leaf count, 1 pencil kernel, 2 staged kernel")
+    ap.add_argument("--stage-kernel", dest="stage_kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="uniform case: 0 by leaf count, 1 pencil kernel, 2 staged kernel, "
+                         "3 split pencil kernel, 4 pencil kernel on staged primitives")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -823,6 +931,8 @@ def main():
         run_proposer(args)
     elif args.case == "laxliu":
         run_laxliu(args)
+    elif args.case == "paper3d":
+        run_paper3d(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -93,7 +93,8 @@ typedef struct {
   double cfl;           /* CFL number of the time-step rule */
   double t_end;         /* > 0: steps with a CFL-computed dt are clipped to end at t_end */
   int adapt;            /* 1: analyse and adapt the tree after every (coarse) step */
-  int criterion;        /* MRFV_CRIT_MR (details vs eps) or MRFV_CRIT_GRAD (density gradient vs eps_w) */
+  int criterion;        /* MRFV_CRIT_MR (details vs eps) or MRFV_CRIT_GRAD (density gradient vs eps_w,
+                           and pressure gradient vs eps_p when eps_p > 0) */
   double eps;           /* MR threshold, the same on every level (Section 2.1) */
   double eps_w;         /* gradient threshold (Section 2.2) */
   double eta_tol;       /* clustering efficiency (Section 2.2) */
@@ -108,6 +109,9 @@ typedef struct {
                            zone, once weights are set (mrfv_proposer_set_weights) */
   int scheme;           /* MRFV_SCHEME_MUSCL_RK2 (default) or MRFV_SCHEME_HANCOCK (Section 2) */
   int clustering;       /* gradient criterion: MRFV_CLUSTER_ROWS (default) or MRFV_CLUSTER_BR */
+  double eps_p;         /* gradient criterion: > 0 also flags |p(Q_{i+alpha}) - p(Q_i)| > eps_p, with p from
+                           the cell's (predicted, where its block is absent) conserved state; 0 (default):
+                           density only.  The 3D case of Section 4.2 tests density and pressure. */
 } mrfv_config;
 
 typedef struct {
@@ -259,8 +263,9 @@ int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
    (the stage kernels' default is their occupancy limit); each value is 0..32.
    stage_kernel picks the MR-scheme stage kernel: 0 by leaf count, 1 the pencil
    kernel (one thread per line of cells), 2 the staged kernel (one thread per
-   face), 3 the pencil kernel with two threads per line.  Out-of-range values
-   give MRFV_ERR_ARG.  Every kernel loops over its
+   face), 3 the pencil kernel with two threads per line, 4 the pencil kernel
+   reading primitives staged in shared memory.  Out-of-range values give
+   MRFV_ERR_ARG.  Every kernel loops over its
    device-resident work list, so any shape gives the same results; captured
    step graphs are dropped and re-captured at the next step. */
 int mrfv_set_launch_shape(mrfv_ctx *ctx, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm,

@@ -79,6 +79,7 @@ def _load():
             "orc_flux_ausmdv": (None, [P, I, dp, dp, dp]),
             "orc_set_scheme": (I, [P, I]),
             "orc_set_clustering": (I, [P, I]),
+            "orc_set_eps_p": (I, [P, D]),
             "orc_br_cluster": (None, [P, I, u8, D, u8]),
             "orc_predict": (D, [P, I, dp, I, I, I, I]),
         }
@@ -199,7 +200,10 @@ class Oracle:
         return n.value
 
     def adapt(self, criterion: int = CRIT_MR, eps: float = 1e-3, eps_w: float = 0.05,
-              eta_tol: float = 0.8, precision: int = 0) -> None:
+              eta_tol: float = 0.8, precision: int = 0, eps_p: float = 0.0) -> None:
+        """eps_p > 0: the gradient criterion also tests pressure against eps_p."""
+        if self.lib.orc_set_eps_p(self._h, eps_p) != 0:
+            raise ValueError("oracle: bad eps_p")
         self.lib.orc_adapt(self._h, criterion, eps, eps_w, eta_tol, precision)
 
     def totals(self) -> np.ndarray:

@@ -47,6 +47,7 @@ typedef struct {
   int dim, nv, L, bc;
   int scheme;         /* O_SCHEME_*: the MR scheme (default) or the AMR scheme of Section 2 */
   int clustering;     /* O_CLUSTER_*: clustering of gradient flags (Section 2.2) */
+  double eps_p;       /* > 0: the gradient criterion also tests pressure (Section 4.2) */
   double gamma;
   double lo[3], hi[3];
   int nb[OMAXL][3];   /* blocks per dimension (1 in unused dimensions) */
@@ -1036,13 +1037,23 @@ int orc_analyse(orc *o, double eps, int precision, long *n_sig) {
 /* ------------------------------------------------------------------------ */
 /* scaled-gradient refinement flags with a one-cell buffer (Section 2.2):
    cell i is flagged when |rho(Q_{i+alpha}) - rho(Q_i)| > eps_w for some
-   alpha in {0,1}^d \ {0} (reading: unscaled, density only); a block of level
+   alpha in {0,1}^d \ {0} (reading: unscaled), or, with eps_p > 0 (the 3D case
+   of Section 4.2 tests density and pressure), |p(Q_{i+alpha}) - p(Q_i)| > eps_p,
+   p taken from the cell's conserved state (predicted from level l-1 where the
+   cell's block is absent); a block of level
    l < L is flagged when a flagged cell lies within one cell of it.  Blocks are
    then grouped per row of the level's block grid into runs of at most 8 blocks
    (64 cells) whose flagged fraction stays >= eta_tol (reading of the
    clustering step); every block of a run is flagged for refinement. */
+static double ext_pressure(const orc *o, int l, const double *E, long c) {
+  double Q[5], w[5];
+  get_cell(o, l, E, c, Q);
+  cons_to_prim(o, Q, w);
+  return w[4];
+}
 static int grad_flag_cell(const orc *o, int l, const double *E, int i, int j, int k, double epsw) {
   double r0 = E[cidx(o, l, i, j, k)];
+  double p0 = o->eps_p > 0.0 ? ext_pressure(o, l, E, cidx(o, l, i, j, k)) : 0.0;
   int kz = o->dim == 3 ? 2 : 1;
   for (int c = 0; c < kz; c++)
     for (int b = 0; b < 2; b++)
@@ -1051,6 +1062,7 @@ static int grad_flag_cell(const orc *o, int l, const double *E, int i, int j, in
         int ii = bc_cell(o, l, 0, i + a), jj = bc_cell(o, l, 1, j + b), kk = bc_cell(o, l, 2, k + c);
         double r1 = E[cidx(o, l, ii, jj, kk)];
         if (fabs(r1 - r0) > epsw) return 1;
+        if (o->eps_p > 0.0 && fabs(ext_pressure(o, l, E, cidx(o, l, ii, jj, kk)) - p0) > o->eps_p) return 1;
       }
   return 0;
 }
@@ -1394,6 +1406,13 @@ void orc_br_cluster(orc *o, int l, const uint8_t *fl, double eta, uint8_t *out) 
 int orc_set_clustering(orc *o, int mode) {
   if (mode != O_CLUSTER_ROWS && mode != O_CLUSTER_BR) return -1;
   o->clustering = mode;
+  return 0;
+}
+
+/* pressure threshold of the gradient criterion (0: density only) */
+int orc_set_eps_p(orc *o, double eps_p) {
+  if (!(eps_p >= 0.0)) return -1;
+  o->eps_p = eps_p;
   return 0;
 }
 

@@ -34,6 +34,10 @@ constexpr long long kStagedBelow3D = 0;
 // blocks 21.1 / 22.9 us.
 constexpr long long kSplitBelow2D = 8192;
 constexpr long long kSplitBelow3D = 0;
+// From these leaf counts on, the pencil kernel reads primitives staged in shared
+// memory (set from measurement; at or above the largest count: never).
+constexpr long long kStagedPrimAbove2D = 1LL << 40;
+constexpr long long kStagedPrimAbove3D = 1LL << 40;
 
 struct mrfv_ctx {
   mrfv_config cfg;
@@ -43,7 +47,8 @@ struct mrfv_ctx {
   cudaStream_t st;
   int nsm, grid, bgrid, fvgrid[2], fv_occupancy[2];  // pencil kernel: [0] one thread per line, [1] two
   int fvs_occupancy[2], fvsgrid[2];  // staged stage kernel: [0] MR scheme, [1] MUSCL-Hancock
-  int stage_kernel;                  // 0 by leaf count, 1 pencil, 2 staged, 3 split pencil (MR scheme)
+  int stage_kernel;                  // 0 by leaf count, 1 pencil, 2 staged, 3 split pencil, 4 pencil on staged primitives
+  int fvpgrid, fvp_occupancy, fvp_bpc;
   char *arena;
   size_t arena_bytes;
   bool own_arena;
@@ -373,6 +378,13 @@ struct Seq {
     long long n = list_count(c, c->snap, a.kind, a.l0, a.l1);
     return n < (c->g.dim == 2 ? kStagedBelow2D : kStagedBelow3D);
   }
+  // pencil kernel reading primitives staged in shared memory
+  bool use_fvp(const FVArgs<T> &a) const {
+    if (c->stage_kernel != 0) return c->stage_kernel == 4;
+    if (!c->snap_valid) return false;
+    long long n = list_count(c, c->snap, a.kind, a.l0, a.l1);
+    return n >= (c->g.dim == 2 ? kStagedPrimAbove2D : kStagedPrimAbove3D);
+  }
   // pencil kernel with two threads per line while the list is short
   bool use_split(const FVArgs<T> &a) const {
     if (c->stage_kernel != 0) return c->stage_kernel == 3;
@@ -397,7 +409,9 @@ struct Seq {
       c->ev_used += 2;
       cudaEventRecord(e0, c->st);
     }
-    if (hancock || use_staged(a)) {
+    if (!hancock && use_fvp(a)) {
+      launch_fvp<T>(c->g, a, sized(c, a.kind, a.l0, a.l1, 1, c->fvp_bpc, c->fvpgrid), c->st);
+    } else if (hancock || use_staged(a)) {
       int h = hancock ? 1 : 0;
       launch_fvs<T>(c->g, a, hancock, sized(c, a.kind, a.l0, a.l1, 1, c->fvs_bpc, c->fvsgrid[h]), c->st);
     } else {
@@ -500,7 +514,7 @@ struct Seq {
   void gradflags() {
     cudaMemsetAsync(c->gflag, 0, c->maptotal, c->st);
     cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
-    launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->gflag, c->bgrid, c->st);
+    launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, c->bgrid, c->st);
     if (c->cfg.clustering == MRFV_CLUSTER_BR)
       launch_br(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
     else
@@ -654,6 +668,7 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
     return fail(nullptr, MRFV_ERR_ARG, "scheme");
   if (cfg->clustering != MRFV_CLUSTER_ROWS && cfg->clustering != MRFV_CLUSTER_BR)
     return fail(nullptr, MRFV_ERR_ARG, "clustering");
+  if (!(cfg->eps_p >= 0.0)) return fail(nullptr, MRFV_ERR_ARG, "eps_p");
   {
     Geo gg;
     long long a, b, f;
@@ -714,6 +729,9 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
     c->fvsgrid[h] = c->nsm * c->fvs_occupancy[h];
   }
   c->stage_kernel = 0;
+  c->fvp_occupancy = c->prec == MRFV_FP32 ? fvp_ctas_per_sm<float>(cfg->dim) : fvp_ctas_per_sm<double>(cfg->dim);
+  c->fvpgrid = c->nsm * c->fvp_occupancy;
+  c->fvp_bpc = c->prec == MRFV_FP32 ? fvp_blocks_per_cta<float>(cfg->dim) : fvp_blocks_per_cta<double>(cfg->dim);
   c->fv_bpc = c->prec == MRFV_FP32 ? fv_blocks_per_cta<float>(cfg->dim, false) : fv_blocks_per_cta<double>(cfg->dim, false);
   c->fvs_bpc = c->prec == MRFV_FP32 ? fv_blocks_per_cta<float>(cfg->dim, true) : fv_blocks_per_cta<double>(cfg->dim, true);
   c->snap_valid = false;
@@ -1181,7 +1199,7 @@ int mrfv_proposer_train(mrfv_ctx *c, const float *feat, const uint8_t *target, i
 int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm,
                           int stage_kernel) {
   if (!c) return MRFV_ERR_ARG;
-  if (stage_kernel < 0 || stage_kernel > 3) return fail(c, MRFV_ERR_ARG, "set_launch_shape: stage_kernel is 0..3");
+  if (stage_kernel < 0 || stage_kernel > 4) return fail(c, MRFV_ERR_ARG, "set_launch_shape: stage_kernel is 0..4");
   if (grid_ctas_per_sm < 0 || grid_ctas_per_sm > 32 || block_ctas_per_sm < 0 || block_ctas_per_sm > 32 ||
       fv_ctas_per_sm < 0 || fv_ctas_per_sm > 32)
     return fail(c, MRFV_ERR_ARG, "set_launch_shape: CTAs per SM outside 0..32");
@@ -1192,6 +1210,7 @@ int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_
   for (int sp = 0; sp < 2; sp++) c->fvgrid[sp] = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fv_occupancy[sp]);
   for (int h = 0; h < 2; h++) c->fvsgrid[h] = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fvs_occupancy[h]);
   c->stage_kernel = stage_kernel;
+  c->fvpgrid = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fvp_occupancy);
   drop_graphs(c);
   return MRFV_OK;
 }

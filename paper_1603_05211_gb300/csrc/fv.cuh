@@ -356,6 +356,259 @@ __global__ void __launch_bounds__(FVShape<T, D, SPLIT>::NT,
   }
 }
 
+// ---------------------------------------------------------------- staged-primitive pencil kernel
+// The same stage with the primitives staged first: all threads of a CTA load the
+// interiors and the face halos of its blocks (independent, coalesced loads; one
+// conversion per cell) into a 12^d tile per block in shared memory, then each
+// thread walks one line per direction out of shared memory, and a last pass
+// applies the update.  Same arithmetic, so the same results as k_fv.
+template <typename T, int D>
+struct FVPShape {
+  static constexpr int NV = D + 2;
+  static constexpr int B = (D == 2) ? 64 : 512;
+  static constexpr int TF = (D == 2) ? 8 : 64;
+  static constexpr int STRIP = 2 * D * 2 * TF;
+  static constexpr int BPC = (D == 2) ? 8 : 1;        // blocks per CTA
+  static constexpr int NT = D * TF * BPC;              // one thread per line and direction
+  static constexpr int WX = 13;                         // padded row of the 12-wide tile
+  static constexpr int WY = 12 * WX;
+  static constexpr int WN = (D == 2) ? WY : 12 * WY;    // tile values per variable
+  static constexpr int PY = FVShape<T, D, 1>::PY, PZ = FVShape<T, D, 1>::PZ, RS = FVShape<T, D, 1>::RS;
+  // CTAs per SM the shared memory allows in single precision (the register budget
+  // is set to match)
+  static constexpr int MINB = sizeof(T) == 4 ? (D == 2 ? 5 : 3) : 1;
+};
+template <typename T, int D>
+constexpr size_t fvp_smem_bytes() {
+  using S = FVPShape<T, D>;
+  return (size_t)S::BPC * S::NV * (S::WN + D * S::RS) * sizeof(T);
+}
+// index of cell (x, y, z) (-2..9 each, relative to the block) in the padded tile
+template <int D>
+__device__ __forceinline__ int fvp_tile(int x, int y, int z) {
+  return (D == 2) ? (x + 2) + 13 * (y + 2) : (x + 2) + 13 * ((y + 2) + 12 * (z + 2));
+}
+
+template <typename T, int D, int N>
+__device__ __forceinline__ void fvp_line(const FVArgs<T> &a, int s, int l, int nb_lo, int nb_hi, int cm, int t0,
+                                         long long cap, const T *W, T *dF, T gam, T goverg1) {
+  using S = FVPShape<T, D>;
+  constexpr int NV = S::NV, RS = S::RS, TF = S::TF;
+  constexpr int SW = (N == 0) ? 1 : (N == 1 ? S::WX : S::WY);   // tile stride along N
+  constexpr int SSTR = (N == 0) ? 1 : (N == 1 ? S::PY : S::PZ);  // dF stride along N
+  const int t1 = t0 & 7, t2 = t0 >> 3;
+  // tile index of position 0 of the line; dF index of its cell 0
+  const int wbase = (N == 0) ? fvp_tile<D>(0, t1, t2) : (N == 1 ? fvp_tile<D>(t1, 0, t2) : fvp_tile<D>(t1, t2, 0));
+  const int sbase = (N == 0) ? (S::PY * t1 + S::PZ * t2) : (N == 1 ? (t1 + S::PZ * t2) : (t1 + S::PY * t2));
+  auto load = [&](int p, T *w) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) w[v] = W[v * S::WN + wbase + p * SW];
+  };
+  const bool rec_lo = a.record && (nb_lo == NBR_MISSING || ((cm >> (2 * N)) & 1));
+  const bool rec_hi = a.record && (nb_hi == NBR_MISSING || ((cm >> (2 * N + 1)) & 1));
+  const bool add_lo = a.record == 2 && nb_lo == NBR_MISSING;
+  const bool add_hi = a.record == 2 && nb_hi == NBR_MISSING;
+  const T dtT = lev_at(a, lev_index(a.stage, l, 3));
+  T wb[NV], wc[NV], slo[NV], Fprev[NV];
+  {
+    T wa[NV];
+    load(-2, wa);
+    load(-1, wb);
+    load(0, wc);
+#pragma unroll
+    for (int v = 0; v < NV; v++) slo[v] = van_albada<T>(wb[v] - wa[v], wc[v] - wb[v]);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    T wd[NV], wl[NV], wr[NV], shi[NV], F[NV];
+    load(k + 1, wd);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      shi[v] = van_albada<T>(wc[v] - wb[v], wd[v] - wc[v]);
+      wl[v] = lfma(T(0.5), slo[v], wb[v]);
+      wr[v] = wc[v] - T(0.5) * shi[v];
+    }
+    ausm_plus<T, D>(N, wl, wr, gam, goverg1, F);
+    if ((k == 0 && rec_lo) || (k == 8 && rec_hi)) {
+      const int side = k == 8 ? 1 : 0;
+      const bool add = side ? add_hi : add_lo;
+      T *R = a.FR + (long long)s * (2 * D * TF) + (2 * N + side) * TF + t0;
+      const long long vsR = cap * (2 * D * TF);
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        T val = dtT * F[v];
+        R[v * vsR] = add ? R[v * vsR] + val : val;
+      }
+    }
+    if (k > 0) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) dF[v * RS + sbase + (k - 1) * SSTR] = F[v] - Fprev[v];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      Fprev[v] = F[v];
+      slo[v] = shi[v];
+      wb[v] = wc[v];
+      wc[v] = wd[v];
+    }
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(FVPShape<T, D>::NT, FVPShape<T, D>::MINB) k_fvp(Geo g, FVArgs<T> a) {
+  using S = FVPShape<T, D>;
+  constexpr int B = S::B, TF = S::TF, NV = S::NV, BPC = S::BPC, NT = S::NT, RS = S::RS;
+  constexpr int NH = 2 * D * 2 * TF;                  // halo cells per block
+  constexpr int NI = (BPC * B + NT - 1) / NT;         // interior cells per thread
+  constexpr int NHT = (BPC * NH + NT - 1) / NT;       // halo cells per thread
+  extern __shared__ unsigned char smem_raw[];
+  T *Wt = reinterpret_cast<T *>(smem_raw);               // [block][v][WN] primitives
+  T *dFs = Wt + (size_t)BPC * NV * S::WN;                // [dir][block][v][RS]
+  __shared__ int sslot[BPC], slev[BPC], scm[BPC], snb[BPC][6];
+  __shared__ T slam[BPC][3];
+  const long long cap = g.cap, vsU = cap * B, vsG = cap * S::STRIP;
+  const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
+  const int tid = threadIdx.x;
+  int lb, le;
+  list_range(g, a.kind, a.l0, a.l1, lb, le);
+  if (a.bytes && blockIdx.x == 0 && tid == 0)
+    atomicAdd(a.bytes, (unsigned long long)(le - lb) * B * a.words * sizeof(T));
+  // slot of this thread's block in the next iteration (threads < BPC), read one
+  // iteration ahead
+  int s_next = -1;
+  if (tid < BPC && lb + (int)blockIdx.x * BPC + tid < le) s_next = g.lists[a.kind * cap + lb + blockIdx.x * BPC + tid];
+  for (int i0 = lb + blockIdx.x * BPC; i0 < le; i0 += gridDim.x * BPC) {
+    if (tid < BPC) {
+      const int s = s_next;
+      const int in = i0 + gridDim.x * BPC + tid;
+      s_next = in < le ? g.lists[a.kind * cap + in] : -1;
+      if (i0 + tid < le) {
+        const int l = g.slot_level[s];
+        sslot[tid] = s;
+        slev[tid] = l;
+        scm[tid] = g.cmask[s];
+#pragma unroll
+        for (int f = 0; f < 2 * D; f++) snb[tid][f] = g.nbr[6 * s + f];
+#pragma unroll
+        for (int d = 0; d < 3; d++) slam[tid][d] = lev_at(a, lev_index(a.stage, l, d));
+      }
+    }
+    __syncthreads();
+    // ---------------- staging: all loads of this thread first, then the conversions
+    {
+      T Qi[NI][NV], Qh[NHT][NV];
+      int ti[NI], th[NHT];
+#pragma unroll
+      for (int it = 0; it < NI; it++) {
+        const int q = tid + it * NT;
+        const int jj = q / B, c = q % B;
+        const bool ok = q < BPC * B && i0 + jj < le;
+        const T *src = a.Uin + (long long)sslot[ok ? jj : 0] * B + c;
+        ti[it] = ok ? jj * NV * S::WN + fvp_tile<D>(c & 7, (c >> 3) & 7, c >> 6) : -1;
+#pragma unroll
+        for (int v = 0; v < NV; v++) Qi[it][v] = ok ? src[v * vsU] : T(1);
+      }
+#pragma unroll
+      for (int it = 0; it < NHT; it++) {
+        const int q = tid + it * NT;
+        const int jj = q / NH, r = q % NH;
+        const bool ok = q < BPC * NH && i0 + jj < le;
+        const int j = ok ? jj : 0;
+        const int s = sslot[j];
+        const int f = r / (2 * TF), dd = (r / TF) & 1, t = r % TF;  // face, depth (0 touches), tangential
+        const int n = f >> 1, side = f & 1;
+        const int t1 = n == 0 ? 1 : 0, t2 = n == 2 ? 1 : 2;
+        int cc[3] = {0, 0, 0};
+        cc[t1] = t & 7;
+        cc[t2] = (D == 3) ? t >> 3 : 0;
+        int pc[3] = {cc[0], cc[1], cc[2]};
+        pc[n] = side ? 8 + dd : -1 - dd;
+        const int nb = snb[j][f];
+        const T *src;
+        long long vs = vsU;
+        if (nb == NBR_MISSING) {
+          src = a.G + (long long)s * S::STRIP + f * 2 * TF + dd * TF + t;
+          vs = vsG;
+        } else {
+          int from = s;
+          if (nb >= 0) {
+            from = nb;
+            cc[n] = side ? dd : 7 - dd;
+          } else {
+            cc[n] = side ? 7 : 0;
+          }
+          src = a.Uin + (long long)from * B + cc[0] + 8 * cc[1] + 64 * cc[2];
+        }
+        th[it] = ok ? j * NV * S::WN + fvp_tile<D>(pc[0], pc[1], (D == 3) ? pc[2] : 0) : -1;
+#pragma unroll
+        for (int v = 0; v < NV; v++) Qh[it][v] = ok ? src[v * vs] : T(1);
+      }
+#pragma unroll
+      for (int it = 0; it < NI; it++) {
+        T w[NV];
+        cons_to_prim<T, D>(Qi[it], gm1, w);
+        if (ti[it] >= 0) {
+#pragma unroll
+          for (int v = 0; v < NV; v++) Wt[ti[it] + v * S::WN] = w[v];
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < NHT; it++) {
+        T w[NV];
+        cons_to_prim<T, D>(Qh[it], gm1, w);
+        if (th[it] >= 0) {
+#pragma unroll
+          for (int v = 0; v < NV; v++) Wt[th[it] + v * S::WN] = w[v];
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- lines
+    {
+      const int n = tid / (TF * BPC), j = (tid / TF) % BPC, t0 = tid % TF;
+      if (i0 + j < le) {
+        const int s = sslot[j], l = slev[j], cm = scm[j];
+        const T *W = Wt + (size_t)j * NV * S::WN;
+        T *dF = dFs + ((size_t)(n * BPC + j) * NV) * RS;
+        if (n == 0) fvp_line<T, D, 0>(a, s, l, snb[j][0], snb[j][1], cm, t0, cap, W, dF, gam, goverg1);
+        else if (n == 1) fvp_line<T, D, 1>(a, s, l, snb[j][2], snb[j][3], cm, t0, cap, W, dF, gam, goverg1);
+        else if constexpr (D == 3) fvp_line<T, D, 2>(a, s, l, snb[j][4], snb[j][5], cm, t0, cap, W, dF, gam, goverg1);
+      }
+    }
+    __syncthreads();
+    // ---------------- update: the old states of this thread's cells first, then the stores
+    {
+      T Q0[NI][NV];
+      long long o[NI];
+#pragma unroll
+      for (int it = 0; it < NI; it++) {
+        const int q = tid + it * NT;
+        const int jj = q / B, c = q % B;
+        const bool ok = q < BPC * B && i0 + jj < le;
+        o[it] = ok ? (long long)sslot[jj] * B + c : -1;
+#pragma unroll
+        for (int v = 0; v < NV; v++) Q0[it][v] = ok ? a.U0[o[it] + v * vsU] : T(0);
+      }
+#pragma unroll
+      for (int it = 0; it < NI; it++) {
+        if (o[it] < 0) continue;
+        const int q = tid + it * NT;
+        const int jj = q / B, c = q % B;
+        const int cp = (c & 7) + S::PY * ((c >> 3) & 7) + S::PZ * (c >> 6);
+        const T lam0 = slam[jj][0], lam1 = slam[jj][1], lam2 = slam[jj][2];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          T r = lam0 * dFs[((size_t)(0 * BPC + jj) * NV + v) * RS + cp];
+          r = r + lam1 * dFs[((size_t)(1 * BPC + jj) * NV + v) * RS + cp];
+          if (D == 3) r = r + lam2 * dFs[((size_t)(2 * BPC + jj) * NV + v) * RS + cp];
+          a.Uout[o[it] + v * vsU] = Q0[it][v] - r;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // CFL limit over the leaves: min over cells and directions of dx_{l,n} / (|v_n| + c),
 // scaled by 2^(l-L) with level-dependent steps; rho <= 0, p <= 0 or NaN flags an
 // error.  The last CTA to finish sets dt = cfl * min (clipped to t_end - t) and

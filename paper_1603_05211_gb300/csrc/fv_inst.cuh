@@ -39,6 +39,25 @@ int fv_ctas_per_sm(int dim, bool split) {
   return split ? fv_occupancy_of<T, 3, 2>() : fv_occupancy_of<T, 3, 1>();
 }
 
+// pencil kernel reading primitives staged in shared memory
+template <typename T>
+void launch_fvp(const Geo &g, const FVArgs<T> &a, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_fvp<T, 2><<<grid, FVPShape<T, 2>::NT, fvp_smem_bytes<T, 2>(), st>>>(g, a);
+  else k_fvp<T, 3><<<grid, FVPShape<T, 3>::NT, fvp_smem_bytes<T, 3>(), st>>>(g, a);
+}
+template <typename T, int D>
+int fvp_occupancy_of() {
+  int n = 0;
+  constexpr size_t sm = fvp_smem_bytes<T, D>();
+  cudaFuncSetAttribute(k_fvp<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fvp<T, D>, FVPShape<T, D>::NT, sm);
+  return n > 0 ? n : 1;
+}
+template <typename T>
+int fvp_ctas_per_sm(int dim) { return dim == 2 ? fvp_occupancy_of<T, 2>() : fvp_occupancy_of<T, 3>(); }
+template <typename T>
+int fvp_blocks_per_cta(int dim) { return dim == 2 ? FVPShape<T, 2>::BPC : FVPShape<T, 3>::BPC; }
+
 // staged stage kernel (fvh.cuh): the MUSCL-Hancock stage, or the MR-scheme
 // stage in the thread-per-face form
 template <typename T>
@@ -87,6 +106,9 @@ void launch_dt(const Geo &g, const T *A, int lts, unsigned long long *red, unsig
   template void launch_fv<T>(const Geo &, const FVArgs<T> &, bool, int, cudaStream_t);          \
   template int fv_ctas_per_sm<T>(int, bool);                                                    \
   template void launch_fvs<T>(const Geo &, const FVArgs<T> &, bool, int, cudaStream_t);         \
+  template void launch_fvp<T>(const Geo &, const FVArgs<T> &, int, cudaStream_t);               \
+  template int fvp_ctas_per_sm<T>(int);                                                         \
+  template int fvp_blocks_per_cta<T>(int);                                                      \
   template int fvs_ctas_per_sm<T>(int, bool);                                                   \
   template int fv_blocks_per_cta<T>(int, bool);                                                 \
   template void launch_dt<T>(const Geo &, const T *, int, unsigned long long *, unsigned *, double, double, double *, \

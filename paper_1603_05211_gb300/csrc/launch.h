@@ -25,13 +25,17 @@ template <typename T> void launch_totals(const Geo &, const T *A, double *out, i
 template <typename T> void launch_reflux(const Geo &, int l0, int l1, T *A, const T *FR, int grid, cudaStream_t);
 template <typename T> void launch_copy_level(const Geo &, int kind, int l0, int l1, const T *src, T *dst, int grid,
                                              cudaStream_t);
-template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw, uint8_t *gflag, int grid, cudaStream_t);
+template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw, double epsp, uint8_t *gflag, int grid,
+                                           cudaStream_t);
 template <typename T> void launch_project_level(const Geo &, int l, const T *A, const double *coarse, double *out, cudaStream_t);
 // finite-volume stage and CFL reduction (fv_f32.cu, fv_f64.cu)
 template <typename T> void launch_fv(const Geo &, const FVArgs<T> &, bool split, int grid, cudaStream_t);
 template <typename T> void launch_fvs(const Geo &, const FVArgs<T> &, bool hancock, int grid, cudaStream_t);
 template <typename T> int fvs_ctas_per_sm(int dim, bool hancock);
 template <typename T> int fv_blocks_per_cta(int dim, bool staged);
+template <typename T> void launch_fvp(const Geo &, const FVArgs<T> &, int grid, cudaStream_t);
+template <typename T> int fvp_ctas_per_sm(int dim);
+template <typename T> int fvp_blocks_per_cta(int dim);
 template <typename T> void launch_dt(const Geo &, const T *A, int lts, unsigned long long *red, unsigned *done, double cfl,
                                      double t_end, double *dsc, double *lev, float *levf, int grid, cudaStream_t);
 template <typename T> int fv_ctas_per_sm(int dim, bool split);

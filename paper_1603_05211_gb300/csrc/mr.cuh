@@ -554,8 +554,9 @@ __global__ void k_copy_level(Geo g, int kind, int l0, int l1, const T *__restric
 // density of level l at global cell (i, j, k) (already inside the domain):
 // the block's value, or the prediction from level l-1 when the block is absent
 template <typename T, int D>
-__device__ T rho_ext(const Geo &g, int l, const T *__restrict__ A, int i, int j, int k) {
+__device__ T var_ext(const Geo &g, int l, const T *__restrict__ A0, int v, int i, int j, int k) {
   constexpr int B = (D == 2) ? 64 : 512;
+  const T *__restrict__ A = A0 + (long long)v * g.cap * B;
   int32_t s = g.idx[map_index(g, l, i >> 3, j >> 3, k >> 3)];
   if (s >= 0) return A[(long long)s * B + (i & 7) + 8 * (j & 7) + ((D == 3) ? 64 * (k & 7) : 0)];
   if (l == 0) {
@@ -582,15 +583,28 @@ __device__ T rho_ext(const Geo &g, int l, const T *__restrict__ A, int i, int j,
   T si = (i & 1) ? T(-1) : T(1), sj = (j & 1) ? T(-1) : T(1), sk = (k & 1) ? T(-1) : T(1);
   return predict<T, D, 3>(P, 1, 1, (D == 3) ? 1 : 0, si, sj, sk);
 }
+// pressure of the same (possibly predicted) conserved state
+template <typename T, int D>
+__device__ T pres_ext(const Geo &g, int l, const T *__restrict__ A, int i, int j, int k) {
+  T Q[D + 2];
+  for (int v = 0; v < D + 2; v++) Q[v] = var_ext<T, D>(g, l, A, v, i, j, k);
+  const T rho = Q[0];
+  T vel[3] = {T(0), T(0), T(0)};
+  for (int d = 0; d < D; d++) vel[d] = Q[1 + d] / rho;
+  const T vv = ((vel[0] * vel[0]) + (vel[1] * vel[1])) + (vel[2] * vel[2]);
+  return T(g.gamma - 1.0) * (Q[D + 1] - ((T(0.5) * rho) * vv));
+}
 
 // Block flag (before clustering) of every existing block of level l < L: a cell
 // within one cell of the block (and inside the domain) has
-// |rho(Q_{i+alpha}) - rho(Q_i)| > eps_w for some alpha in {0,1}^d \ {0}.
+// |rho(Q_{i+alpha}) - rho(Q_i)| > eps_w, or with eps_p > 0
+// |p(Q_{i+alpha}) - p(Q_i)| > eps_p, for some alpha in {0,1}^d \ {0}.
 template <typename T, int D>
-__global__ void k_gradflags(Geo g, const T *__restrict__ A, T epsw, uint8_t *gflag) {
+__global__ void k_gradflags(Geo g, const T *__restrict__ A, T epsw, T epsp, uint8_t *gflag) {
   constexpr int EXT = 11;  // relative cells -1 .. 9
   constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
-  __shared__ T rp[NP];
+  __shared__ T rp[NP], pp[NP];
+  const bool use_p = epsp > T(0);
   int b, e;
   if (g.L < 1) return;
   list_range(g, LK_EXIST, 0, g.L - 1, b, e);
@@ -604,7 +618,8 @@ __global__ void k_gradflags(Geo g, const T *__restrict__ A, T epsw, uint8_t *gfl
       int r[3] = {p % EXT - 1, (p / EXT) % EXT - 1, (D == 3) ? p / (EXT * EXT) - 1 : 0};
       int gc[3];
       for (int d = 0; d < 3; d++) gc[d] = (d < D) ? bc_cell(g, l, d, 8 * bc3[d] + r[d]) : 0;
-      rp[p] = rho_ext<T, D>(g, l, A, gc[0], gc[1], gc[2]);
+      rp[p] = var_ext<T, D>(g, l, A, 0, gc[0], gc[1], gc[2]);
+      if (use_p) pp[p] = pres_ext<T, D>(g, l, A, gc[0], gc[1], gc[2]);
     }
     __syncthreads();
     int hit = 0;
@@ -622,6 +637,7 @@ __global__ void k_gradflags(Geo g, const T *__restrict__ A, T epsw, uint8_t *gfl
       for (int al = 1; al < (1 << D); al++) {
         int pa = p0 + (al & 1) + EXT * (((al >> 1) & 1) + ((D == 3) ? EXT * ((al >> 2) & 1) : 0));
         if (fabs(rp[pa] - r0) > epsw) hit = 1;
+        if (use_p && fabs(pp[pa] - pp[p0]) > epsp) hit = 1;
       }
     }
     hit = __syncthreads_or(hit);

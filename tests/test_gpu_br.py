@@ -86,3 +86,48 @@ def test_br_3d_matches_oracle(mrfv):
         o.adapt(oracle.CRIT_GRAD)
         _same(s, o)
     _close(s, o)
+
+
+def _pair_p(m, dim, levels, base, lts, ic, params, clustering, scheme="muscl_rk2", lo=(0, 0, 0), hi=(1, 1, 1),
+            cfl=0.5):
+    """Gradient criterion on density and pressure (eps_w = eps_p = 0.05)."""
+    s = m.Solver(dim=dim, levels=levels, base_blocks=base, adapt=True, criterion="grad", lts=lts, lo=lo, hi=hi,
+                 clustering=clustering, eps_w=0.05, eps_p=0.05, scheme=scheme, cfl=cfl)
+    s.init_state(ic, params)
+    o = oracle.Oracle(dim, levels, base, lo=lo, hi=hi,
+                      clustering=oracle.CLUSTER_BR if clustering == "br" else oracle.CLUSTER_ROWS,
+                      scheme=oracle.SCHEME_HANCOCK if scheme == "hancock" else oracle.SCHEME_MUSCL_RK2)
+    o.init(ic, params)
+    o.adapt(oracle.CRIT_GRAD, eps_w=0.05, eps_p=0.05)
+    return s, o
+
+
+@pytest.mark.parametrize("clustering", ["rows", "br"])
+def test_pressure_gradient_flags_2d(mrfv, clustering):
+    s, o = _pair_p(mrfv, 2, 3, (4, 4, 1), False, mi.IC_QUADRANTS, mi.quadrant_params(5), clustering)
+    _same(s, o)
+    for _ in range(3):
+        dt = o.dt(0.5)
+        assert s.step(0.0) == dt
+        o.step(dt)
+        o.adapt(oracle.CRIT_GRAD, eps_w=0.05, eps_p=0.05)
+        for l in range(2):
+            assert np.array_equal(s.get_flags(l)[0], o.get_sig(l)[0])
+        _same(s, o)
+    _close(s, o)
+
+
+def test_pressure_gradient_rotated_ellipsoid_3d_hancock_lts(mrfv):
+    """The 3D case of Section 4.2 at small size: rotated ellipsoid on [-2,2]^3,
+    AMR scheme, density and pressure flags clustered by Berger-Rigoutsos,
+    level-dependent steps."""
+    s, o = _pair_p(mrfv, 3, 3, (2, 2, 2), True, mi.IC_ROTATED_ELLIPSOID, mi.paper3d_params(), "br",
+                   scheme="hancock", lo=(-2, -2, -2), hi=(2, 2, 2), cfl=0.4)
+    _same(s, o)
+    for _ in range(2):
+        dt = o.dt(0.4, True)
+        assert s.step(0.0) == dt
+        o.step(dt, True)
+        o.adapt(oracle.CRIT_GRAD, eps_w=0.05, eps_p=0.05)
+        _same(s, o)
+    _close(s, o)

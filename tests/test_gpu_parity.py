@@ -370,12 +370,13 @@ def test_blast3d_fp32_levels5_full_size_step(mrfv):
     assert np.all(np.abs(s.totals() - o.totals()) <= 1e-6 * np.abs(T0).max())
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
 @pytest.mark.parametrize("case", ["uniform", "adaptive", "mrlt", "adaptive3d"])
 def test_both_stage_kernels_match_oracle(mrfv, kernel, case):
-    """The MR-scheme stage in the pencil kernel (1), the staged kernel (2) and the
-    pencil kernel with two threads per line (3), each forced, against the oracle
-    (the default picks one by leaf count)."""
+    """The MR-scheme stage in the pencil kernel (1), the staged kernel (2), the
+    pencil kernel with two threads per line (3) and the pencil kernel reading
+    primitives staged in shared memory (4), each forced, against the oracle (the
+    default picks one by leaf count)."""
     if case == "uniform":
         s, o = pair(mrfv, 2, 1, (3, 5, 1), params=mi.quadrant_params(5))
         steps, lts, crit = 30, False, None
