@@ -209,7 +209,7 @@ __device__ __forceinline__ void k_classify_dev(Geo g, uint8_t *kbits) {
 }
 
 constexpr int SCAN_NT = 256;
-constexpr int SCAN_PER = 8;
+constexpr int SCAN_PER = 1;  // one Morton position per thread: no serial chain of table reads per thread
 constexpr int SCAN_TILE = SCAN_NT * SCAN_PER;
 constexpr int kFusedScanTiles = 1024;  // up to this many tiles each scatter CTA sums the counts before it
 
