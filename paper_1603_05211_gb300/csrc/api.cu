@@ -480,11 +480,14 @@ struct Seq {
       c->nlaunch += 2;
     }
   }
-  void analyse(double eps) {
+  // cleared: the maps were cleared by the adaptation's first kernel
+  void analyse(double eps, bool cleared = false) {
     launch_scales<T>(c->g, U(), c->red + 0, c->rctl + 3, (T *)c->scale,
                      grid_for(level_blocks(c->g, 0) * block_cells(c->g.dim), 256, c->grid), c->st);
-    cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
-    cudaMemsetAsync(c->maxdet, 0, c->maptotal * 8, c->st);
+    if (!cleared) {
+      cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
+      cudaMemsetAsync(c->maxdet, 0, c->maptotal * 8, c->st);
+    }
     launch_details<T>(c->g, U(), (const T *)c->scale, eps, c->sig, c->maxdet,
                       sized(c, LK_EXIST, 1, c->g.L, 1, 1, c->bgrid), c->st);
     c->nlaunch += 2;
@@ -511,9 +514,11 @@ struct Seq {
     launch_prop_features<T>(c->g, U(), c->maxdet, (const T *)c->scale, c->cfg.eps, c->pfeat, c->grid, c->st);
     c->nlaunch += 1;
   }
-  void gradflags() {
-    cudaMemsetAsync(c->gflag, 0, c->maptotal, c->st);
-    cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
+  void gradflags(bool cleared = false) {
+    if (!cleared) {
+      cudaMemsetAsync(c->gflag, 0, c->maptotal, c->st);
+      cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
+    }
     launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, c->bgrid, c->st);
     if (c->cfg.clustering == MRFV_CLUSTER_BR)
       launch_br(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
@@ -535,8 +540,8 @@ void dispatch(mrfv_ctx *c, F f) {
 }
 
 // free, allocate, rebuild neighbour tables and lists, optionally predict new blocks
-void apply_need(mrfv_ctx *c, bool prolong) {
-  cudaMemsetAsync(c->nnew, 0, MAXL * sizeof(int), c->st);
+void apply_need(mrfv_ctx *c, bool prolong, bool cleared = false) {
+  if (!cleared) cudaMemsetAsync(c->nnew, 0, MAXL * sizeof(int), c->st);
   launch_free(c->g, c->need, c->freestack, c->freetop, c->grid, c->st);
   launch_alloc(c->g, c->need, c->freestack, c->freetop, c->newlist, c->nnew, c->grid, c->st);
   launch_rebuild_lists(c->g, c->kbits, c->tcount, c->toff, c->ntiles, c->grid, c->st);
@@ -563,17 +568,20 @@ void prop_infer(mrfv_ctx *c) {
 }
 
 // analysis / flags -> needed blocks -> closure -> apply
-void adapt_tree(mrfv_ctx *c) {
+// (step: the first kernel also does the step's time and counter bookkeeping)
+void adapt_tree(mrfv_ctx *c, bool step = false) {
   const Geo &g = c->g;
   bool use_prop = c->cfg.proposer && c->has_weights && c->cfg.criterion == MRFV_CRIT_MR;
-  if (c->cfg.criterion == MRFV_CRIT_MR) dispatch(c, [&](auto &s) { s.analyse(c->cfg.eps); });
-  else dispatch(c, [&](auto &s) { s.gradflags(); });
+  const int lts = c->cfg.lts;
+  launch_adapt_begin(g, c->maptotal, c->sig, c->maxdet, c->gflag, c->need, c->nnew, step ? c->dsc + 1 : nullptr,
+                     c->dsc, lts ? ldexp(1.0, g.L) : 1.0, c->counter, lts, c->pub_dev, c->grid, c->st);
+  c->nlaunch += 1;
+  if (c->cfg.criterion == MRFV_CRIT_MR) dispatch(c, [&](auto &s) { s.analyse(c->cfg.eps, true); });
+  else dispatch(c, [&](auto &s) { s.gradflags(true); });
   if (use_prop) {
     dispatch(c, [&](auto &s) { s.prop_features(); });
     prop_infer(c);
   }
-  cudaMemsetAsync(c->need, 0, c->maptotal, c->st);
-  cudaMemsetAsync(c->need, 1, g.mapoff[1], c->st);
   launch_need_mark(g, c->sig, c->need, use_prop ? 2 : c->cfg.criterion, c->grid, c->st);
   if (use_prop) {
     launch_prop_mark(g, c->plogit, c->need, c->grid, c->st);
@@ -581,7 +589,7 @@ void adapt_tree(mrfv_ctx *c) {
   }
   for (int l = g.L; l >= 1; l--) launch_need_close(g, l, c->need, grid_for(level_blocks(g, l), 256, c->grid), c->st);
   c->nlaunch += 1 + g.L;
-  apply_need(c, true);
+  apply_need(c, true, true);
 }
 
 bool valid_tree(const mrfv_ctx *c, const uint8_t *ex) {
@@ -752,6 +760,8 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   cudaMemsetAsync(c->counter, 0, 2 * 8, c->st);
   cudaMemsetAsync(c->rctl, 0, 4 * 4, c->st);
   cudaMemsetAsync(c->red, 0, 4 * 8, c->st);
+  cudaMemsetAsync(c->red + 3, 0x7f, 8, c->st);  // the CFL minimum's start value, a huge positive double
+  cudaMemsetAsync(c->done, 0, 4, c->st);
   launch_init_freestack(c->freestack, c->freetop, c->g.cap, c->grid, c->st);
   if (cfg->use_graph && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) c->cap_st = nullptr;
   prop_setup();
@@ -879,9 +889,12 @@ void issue_step(mrfv_ctx *c, bool preset) {
     if (lts) s.advance(0, 0);
     else s.step_global();
   });
-  launch_advance(c->g, c->dsc + 1, c->dsc, lts ? ldexp(1.0, c->g.L) : 1.0, c->counter, lts, c->pub_dev, c->st);
-  c->nlaunch += 1;
-  if (c->cfg.adapt) adapt_tree(c);
+  if (c->cfg.adapt) {
+    adapt_tree(c, true);
+  } else {
+    launch_advance(c->g, c->dsc + 1, c->dsc, lts ? ldexp(1.0, c->g.L) : 1.0, c->counter, lts, c->pub_dev, c->st);
+    c->nlaunch += 1;
+  }
 }
 
 // Capture one step into graph variant v (once per context: every kernel argument

@@ -661,6 +661,9 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
     if (atomicAdd(done, 1u) == gridDim.x - 1) {
       __threadfence();
       double m = __longlong_as_double((long long)atomicAdd(red, 0ull));
+      // ready for the next reduction (no memset before each launch)
+      atomicExch(red, 0x7f7f7f7f7f7f7f7full);
+      atomicExch(done, 0u);
       double d = cfl * m;
       if (t_end > 0.0) {
         double rest = t_end - dsc[1];

@@ -96,8 +96,8 @@ int fv_blocks_per_cta(int dim, bool staged) {
 template <typename T>
 void launch_dt(const Geo &g, const T *A, int lts, unsigned long long *red, unsigned *done, double cfl, double t_end,
                double *dsc, double *lev, float *levf, int grid, cudaStream_t st) {
-  cudaMemsetAsync(red, 0x7f, sizeof(unsigned long long), st);  // a huge positive double
-  cudaMemsetAsync(done, 0, sizeof(unsigned), st);
+  // red (a huge positive double) and done are set at context creation and reset
+  // by the reduction's last CTA
   if (g.dim == 2) k_dt<T, 2><<<grid, 256, 0, st>>>(g, A, lts, red, done, cfl, t_end, dsc, lev, levf);
   else k_dt<T, 3><<<grid, 256, 0, st>>>(g, A, lts, red, done, cfl, t_end, dsc, lev, levf);
 }

@@ -43,6 +43,9 @@ template <typename T> int fv_ctas_per_sm(int dim, bool split);
 // integer tree work (tree.cu)
 void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t);
 void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t);
+void launch_adapt_begin(const Geo &, long long total, uint8_t *sig, double *maxdet, uint8_t *gflag, uint8_t *need,
+                        int *nnew, double *t, const double *dt, double factor, long long *counter, int lts,
+                        int32_t *pub, int grid, cudaStream_t);
 void launch_free(const Geo &, const uint8_t *need, int32_t *fs, int *ft, int grid, cudaStream_t);
 void launch_alloc(const Geo &, const uint8_t *need, int32_t *fs, int *ft, int32_t *nl, int *nn, int grid, cudaStream_t);
 void launch_init_freestack(int32_t *fs, int *ft, long long cap, int grid, cudaStream_t);

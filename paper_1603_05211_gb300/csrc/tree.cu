@@ -673,6 +673,38 @@ __global__ void k_advance(Geo g, double *t, const double *dt, double factor, lon
   counter[1] += 1;
 }
 
+// Start of an adaptation: significance, gradient-flag and detail maps cleared,
+// the needed map set to level 0 alone, the new-block counts zeroed.  With t set,
+// CTA 0 also does the step's bookkeeping of k_advance (one launch instead of
+// that kernel and five memsets).
+__global__ void k_adapt_begin(Geo g, long long total, uint8_t *sig, double *maxdet, uint8_t *gflag, uint8_t *need,
+                              int *nnew, double *t, const double *dt, double factor, long long *counter, int lts,
+                              int32_t *pub) {
+  const long long lvl0 = g.mapoff[1];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    sig[i] = 0;
+    if (maxdet) maxdet[i] = 0.0;
+    if (gflag) gflag[i] = 0;
+    need[i] = i < lvl0 ? 1 : 0;
+  }
+  if (blockIdx.x != 0) return;
+  if (threadIdx.x < MAXL) nnew[threadIdx.x] = 0;
+  if (!t) return;
+  if (pub)
+    for (int i = threadIdx.x; i < LK_NUM * (MAXL + 2); i += blockDim.x) pub[i] = g.loff[i];
+  if (threadIdx.x == 0) {
+    *t = *t + factor * *dt;
+    long long cells = 0;
+    int B = block_cells(g.dim);
+    for (int l = 0; l <= g.L; l++) {
+      long long nl = g.loff[LK_LEAF * (MAXL + 2) + l + 1] - g.loff[LK_LEAF * (MAXL + 2) + l];
+      cells += (lts ? (nl << l) : nl) * B;
+    }
+    counter[0] += cells;
+    counter[1] += 1;
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 // The tree kernels loop over fixed domains (the dense block maps, the Morton
 // positions, the scan tiles): a grid larger than the domain only adds CTAs that
@@ -733,6 +765,12 @@ void launch_br(const Geo &g, const uint8_t *gflag, uint8_t *sig, double eta, voi
 void launch_set_double(double *p, double v, cudaStream_t st) { k_set_double<<<1, 1, 0, st>>>(p, v); }
 void launch_level_params(const Geo &g, const double *dt, int lts, double *lev, float *levf, cudaStream_t st) {
   k_level_params<<<1, 32, 0, st>>>(g, dt, lts, lev, levf);
+}
+void launch_adapt_begin(const Geo &g, long long total, uint8_t *sig, double *maxdet, uint8_t *gflag, uint8_t *need,
+                        int *nnew, double *t, const double *dt, double factor, long long *counter, int lts,
+                        int32_t *pub, int grid, cudaStream_t st) {
+  k_adapt_begin<<<fit(total, 256, grid), 256, 0, st>>>(g, total, sig, maxdet, gflag, need, nnew, t, dt, factor,
+                                                       counter, lts, pub);
 }
 void launch_advance(const Geo &g, double *t, const double *dt, double factor, long long *counter, int lts,
                     int32_t *pub, cudaStream_t st) {
