@@ -199,7 +199,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t oG = L.take((size_t)nv * cap * 2 * g.dim * 2 * TF * ts);
   size_t oFR = L.take((size_t)nv * cap * 2 * g.dim * TF * ts);
   size_t oidx = L.take(maptotal * 4), olev = L.take(cap * 4), ocoord = L.take(cap * 12), onbr = L.take(cap * 24);
-  size_t ocm = L.take(cap), oloff = L.take(LK_NUM * (MAXL + 2) * 4), olists = L.take((size_t)LK_NUM * cap * 4);
+  size_t ocm = L.take(cap), okids = L.take(cap * 32), oloff = L.take(LK_NUM * (MAXL + 2) * 4), olists = L.take((size_t)LK_NUM * cap * 4);
   size_t oerr = L.take(4);
   size_t osig = L.take(maptotal), oneed = L.take(maptotal), ogf = L.take(maptotal), omd = L.take(maptotal * 8);
   size_t okb = L.take(mtotal), otc = L.take((size_t)LK_NUM * ntiles * 4), oto = L.take((size_t)LK_NUM * ntiles * 4);
@@ -223,7 +223,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->U = a + oU; c->Us = a + oUs; c->U0 = a + oU0; c->G = a + oG; c->FR = a + oFR;
     c->g.idx = (int32_t *)(a + oidx); c->g.slot_level = (int32_t *)(a + olev);
     c->g.slot_coord = (int32_t *)(a + ocoord); c->g.nbr = (int32_t *)(a + onbr);
-    c->g.cmask = (uint8_t *)(a + ocm); c->g.loff = (int32_t *)(a + oloff); c->g.lists = (int32_t *)(a + olists);
+    c->g.cmask = (uint8_t *)(a + ocm); c->g.kids = (int32_t *)(a + okids); c->g.loff = (int32_t *)(a + oloff); c->g.lists = (int32_t *)(a + olists);
     c->g.err = (int *)(a + oerr);
     c->sig = (uint8_t *)(a + osig); c->need = (uint8_t *)(a + oneed); c->gflag = (uint8_t *)(a + ogf);
     c->maxdet = (double *)(a + omd); c->kbits = (uint8_t *)(a + okb);
@@ -501,7 +501,7 @@ struct Seq {
   // CFL reduction; its last CTA sets dt and the per-level step table
   void compute_dt(int lts) {
     launch_dt<T>(c->g, U(), lts, c->red + 3, c->done, c->cfg.cfl, c->cfg.t_end, c->dsc, c->lev, c->levf,
-                 sized(c, LK_LEAF, 0, c->g.L, block_cells(c->g.dim), 256, c->grid),
+                 sized(c, LK_LEAF, 0, c->g.L, block_cells(c->g.dim), 1024, c->grid),
                  c->st);
     c->nlaunch += 1;
   }

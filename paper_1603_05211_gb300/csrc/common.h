@@ -39,6 +39,8 @@ struct Geo {
   int32_t *slot_coord;      // [slot*3 + d]
   int32_t *nbr;             // [slot*6 + face], face = 2*dir + side
   uint8_t *cmask;           // [slot]: bit f = neighbour across face f exists and is refined
+  int32_t *kids;            // [slot*8 + q]: slots of a refined block's children, q = x + 2y + 4z
+                            // (child offsets); written with the lists, read only for refined blocks
   int32_t *loff;            // [kind*(MAXL+2) + l] start of level l in list kind; [L+1] = end
   int32_t *lists;           // [kind*cap + i]
   int *err;                 // error bits (ErrBits)

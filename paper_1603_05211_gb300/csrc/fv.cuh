@@ -623,8 +623,7 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
   const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0);
   T best = T(INFINITY);
   bool bad = false;
-  for (long long t = (long long)b * B + blockIdx.x * blockDim.x + threadIdx.x; t < (long long)e * B;
-       t += (long long)gridDim.x * blockDim.x) {
+  auto cell = [&](long long t) {
     int i = (int)(t / B), c = (int)(t % B);
     int s = g.lists[LK_LEAF * cap + i];
     int l = g.slot_level[s];
@@ -634,7 +633,7 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
     cons_to_prim<T, D>(Q, gm1, w);
     if (!(w[0] > T(0)) || !(w[D + 1] > T(0))) {
       bad = true;
-      continue;
+      return;
     }
     T cs = sqrt((gam * w[D + 1]) / w[0]);
 #pragma unroll
@@ -643,6 +642,12 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
       if (lts) rr = ldexp(rr, l - g.L);
       if (rr < best) best = rr;
     }
+  };
+  // two cells per pass, so their reads are in flight together
+  const long long stride = (long long)gridDim.x * blockDim.x, end = (long long)e * B;
+  for (long long t = (long long)b * B + blockIdx.x * blockDim.x + threadIdx.x; t < end; t += 2 * stride) {
+    cell(t);
+    if (t + stride < end) cell(t + stride);
   }
   if (bad) set_err(g, EB_NONPHYS);
   // warp minima, then the CTA minimum: one atomic per CTA on the shared word

@@ -30,8 +30,7 @@ __device__ __forceinline__ void restrict_level_dev(const Geo &g, int l, T *__res
   const long long cap = g.cap;
   for (int i = b + blockIdx.x * BPC + sub; i < e; i += gridDim.x * BPC) {
     int s = g.lists[LK_INTERNAL * cap + i];
-    int bx = g.slot_coord[3 * s], by = g.slot_coord[3 * s + 1], bz = g.slot_coord[3 * s + 2];
-    int cs = g.idx[map_index(g, l + 1, 2 * bx + (x >> 2), 2 * by + (y >> 2), (D == 3) ? 2 * bz + (z >> 2) : 0)];
+    int cs = g.kids[8 * s + (x >> 2) + 2 * (y >> 2) + ((D == 3) ? 4 * (z >> 2) : 0)];
     if (cs < 0) {
       set_err(g, EB_TREE);
       continue;
@@ -496,12 +495,12 @@ __global__ void k_reflux(Geo g, int l0, int l1, T *__restrict__ A, const T *__re
       int t1 = (n == 0) ? 1 : 0, t2 = (n == 2) ? 1 : 2;
       int u = cc[t1], w = (D == 3) ? cc[t2] : 0;
       int P = g.nbr[6 * s + f];
-      int pc[3] = {g.slot_coord[3 * P], g.slot_coord[3 * P + 1], g.slot_coord[3 * P + 2]};
-      int ch[3];
-      ch[n] = 2 * pc[n] + (side ? 0 : 1);
-      ch[t1] = 2 * pc[t1] + (u >> 2);
-      ch[t2] = (D == 3) ? 2 * pc[t2] + (w >> 2) : 0;
-      int fs = g.idx[map_index(g, l + 1, ch[0], ch[1], ch[2])];
+      // the child of the refined neighbour P that touches this face
+      int ch[3] = {0, 0, 0};
+      ch[n] = side ? 0 : 1;
+      ch[t1] = u >> 2;
+      if (D == 3) ch[t2] = w >> 2;
+      int fs = g.kids[8 * P + ch[0] + 2 * ch[1] + 4 * ch[2]];
       if (fs < 0) {
         set_err(g, EB_TREE);
         continue;

@@ -171,6 +171,12 @@ __device__ __forceinline__ uint8_t classify_position(const Geo &g, long long m) 
         bits = 1u << LK_EXIST;
         bool leaf = !has_children(g, l, bx, by, bz);
         bits |= leaf ? (1u << LK_LEAF) : (1u << LK_INTERNAL);
+        if (!leaf) {
+          const int nk = g.dim == 3 ? 8 : 4;
+          for (int q = 0; q < nk; q++)
+            g.kids[8 * s + q] =
+                g.idx[map_index(g, l + 1, 2 * bx + (q & 1), 2 * by + ((q >> 1) & 1), g.dim == 3 ? 2 * bz + (q >> 2) : 0)];
+        }
         uint8_t cm = 0;
         bool missing = false;
         for (int f = 0; f < 2 * g.dim; f++) {
