@@ -152,6 +152,16 @@ def uniform_roofline(m, torch, hbm_peak, steps=6, scheme="muscl_rk2"):
     return out
 
 
+STAGE_KERNELS = ((1, "k_fv (pencil)"), (2, "k_fvs (staged)"), (4, "k_fv (pencil, two threads per line)"),
+                 (8, "k_fvp (pencil on staged primitives)"), (16, "k_fvs (staged MUSCL-Hancock)"))
+
+
+def stage_kernel_names(mask: int) -> str:
+    """Names of the fused reconstruct-flux-update stage kernels a profile saw."""
+    names = [n for bit, n in STAGE_KERNELS if mask & bit]
+    return " + ".join(names) if names else "stage kernel"
+
+
 def timed_steps(s, n: int, torch, stream, dt: float = 0.0) -> float:
     """GPU time (ms) of n asynchronous steps (dt <= 0: CFL steps), CUDA events on
     the solver's stream.  The first step (which captures the step graph on the
@@ -543,7 +553,7 @@ def run_ours(args):
         fv_ach = prof["fv_bytes"] / (prof["fv_ms"] * 1e-3) / 1e9 if prof["fv_ms"] > 0 else 0.0
         roof = {"bound": "hbm", "achieved": round(fv_ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(fv_ach / hbm_peak, 4), "traffic": None,
-                "kernel": "k_fv (fused reconstruct-flux-update stage)", "peak_kind": peak_kind,
+                "kernel": stage_kernel_names(prof.get("fv_kernels", 0)), "peak_kind": peak_kind,
                 "timing": "CUDA events around each stage launch, same workload and step count, eager launches",
                 "launches": prof["fv_launches"],
                 "avg_launch_us": round(prof["fv_ms"] * 1e3 / max(1, prof["fv_launches"]), 2),

@@ -249,6 +249,9 @@ typedef struct {
   int64_t prop_launches; /* tensor-core convolution launches of the proposer timed (3 per inference) */
   double prop_ms;        /* their CUDA-event time */
   double prop_flops;     /* their algorithmic flops: 2 x positions x (16*81 + 16*432 + 432) per inference */
+  int fv_kernels;        /* stage kernels those launches used (bit mask): 1 pencil, 2 staged (MR scheme),
+                            4 pencil with two threads per line, 8 pencil on staged primitives,
+                            16 staged MUSCL-Hancock */
 } mrfv_profile;
 /* enable != 0: reset the counters and bracket every finite-volume stage launch
    with CUDA events on the context stream (steps then launch eagerly instead of

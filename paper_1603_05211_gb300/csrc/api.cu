@@ -49,6 +49,7 @@ struct mrfv_ctx {
   int fvs_occupancy[2], fvsgrid[2];  // staged stage kernel: [0] MR scheme, [1] MUSCL-Hancock
   int stage_kernel;                  // 0 by leaf count, 1 pencil, 2 staged, 3 split pencil, 4 pencil on staged primitives
   int fvpgrid, fvp_occupancy, fvp_bpc;
+  int fv_kinds;                      // stage kernels launched since profiling was enabled (bit mask)
   char *arena;
   size_t arena_bytes;
   bool own_arena;
@@ -411,12 +412,15 @@ struct Seq {
     }
     if (!hancock && use_fvp(a)) {
       launch_fvp<T>(c->g, a, sized(c, a.kind, a.l0, a.l1, 1, c->fvp_bpc, c->fvpgrid), c->st);
+      c->fv_kinds |= 8;
     } else if (hancock || use_staged(a)) {
       int h = hancock ? 1 : 0;
       launch_fvs<T>(c->g, a, hancock, sized(c, a.kind, a.l0, a.l1, 1, c->fvs_bpc, c->fvsgrid[h]), c->st);
+      c->fv_kinds |= hancock ? 16 : 2;
     } else {
       int sp = use_split(a) ? 1 : 0;
       launch_fv<T>(c->g, a, sp == 1, sized(c, a.kind, a.l0, a.l1, 1, c->fv_bpc, c->fvgrid[sp]), c->st);
+      c->fv_kinds |= sp ? 4 : 1;
     }
     if (c->prof) cudaEventRecord(e1, c->st);
     c->nlaunch += 1;
@@ -737,6 +741,7 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
     c->fvsgrid[h] = c->nsm * c->fvs_occupancy[h];
   }
   c->stage_kernel = 0;
+  c->fv_kinds = 0;
   c->fvp_occupancy = c->prec == MRFV_FP32 ? fvp_ctas_per_sm<float>(cfg->dim) : fvp_ctas_per_sm<double>(cfg->dim);
   c->fvpgrid = c->nsm * c->fvp_occupancy;
   c->fvp_bpc = c->prec == MRFV_FP32 ? fvp_blocks_per_cta<float>(cfg->dim) : fvp_blocks_per_cta<double>(cfg->dim);
@@ -1236,6 +1241,7 @@ int mrfv_profile_enable(mrfv_ctx *c, int enable) {
   c->ev_used = 0;
   c->pev_used = 0;
   c->nlaunch = 0;
+  c->fv_kinds = 0;
   cudaMemsetAsync(c->dbytes, 0, 8, c->st);
   return check_launch(c, "mrfv_profile_enable");
 }
@@ -1264,6 +1270,7 @@ int mrfv_profile_read(mrfv_ctx *c, mrfv_profile *o) {
   o->prop_launches = (int64_t)(3 * (c->pev_used / 2));
   o->prop_ms = pms;
   o->prop_flops = (double)(c->pev_used / 2) * 2.0 * (double)c->maptotal * (16.0 * 81 + 16.0 * 432 + 432.0);
+  o->fv_kernels = c->fv_kinds;
   return check_launch(c, "mrfv_profile_read");
 }
 
