@@ -80,6 +80,7 @@ def _load():
             "orc_set_scheme": (I, [P, I]),
             "orc_set_clustering": (I, [P, I]),
             "orc_set_eps_p": (I, [P, D]),
+            "orc_set_lts_remesh": (I, [P, I, D, D]),
             "orc_br_cluster": (None, [P, I, u8, D, u8]),
             "orc_predict": (D, [P, I, dp, I, I, I, I]),
         }
@@ -205,6 +206,14 @@ class Oracle:
         if self.lib.orc_set_eps_p(self._h, eps_p) != 0:
             raise ValueError("oracle: bad eps_p")
         self.lib.orc_adapt(self._h, criterion, eps, eps_w, eta_tol, precision)
+
+    def set_lts_remesh(self, on: bool = True, eps_w: float = 0.05, eta_tol: float = 0.8,
+                       eps_p: float = 0.0) -> None:
+        """Remesh the finer levels inside the level recursion (Fig. 2) when stepping
+        with level-dependent steps and the gradient criterion."""
+        if self.lib.orc_set_eps_p(self._h, eps_p) != 0 or \
+                self.lib.orc_set_lts_remesh(self._h, int(bool(on)), eps_w, eta_tol) != 0:
+            raise ValueError("oracle: bad remesh parameters")
 
     def totals(self) -> np.ndarray:
         out = np.zeros(5)

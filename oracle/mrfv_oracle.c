@@ -48,6 +48,9 @@ typedef struct {
   int scheme;         /* O_SCHEME_*: the MR scheme (default) or the AMR scheme of Section 2 */
   int clustering;     /* O_CLUSTER_*: clustering of gradient flags (Section 2.2) */
   double eps_p;       /* > 0: the gradient criterion also tests pressure (Section 4.2) */
+  int lts_remesh;     /* level-dependent steps with the gradient criterion: remesh the finer levels
+                         inside the recursion (Fig. 2), with these flag parameters */
+  double rm_epsw, rm_eta;
   double gamma;
   double lo[3], hi[3];
   int nb[OMAXL][3];   /* blocks per dimension (1 in unused dimensions) */
@@ -83,6 +86,9 @@ static int bc_cell(const orc *o, int l, int d, int i) {
   return i < 0 ? 0 : (i >= N ? N - 1 : i);
 }
 /* neighbouring block coordinate, or -1 when it lies outside a transmissive domain */
+static void apply_need(orc *o, uint8_t **need, int lfrom);
+static void remesh_amr(orc *o, int l0, double th);
+
 static int bc_block(const orc *o, int l, int d, int b) {
   int N = o->nb[l][d];
   if (d >= o->dim) return b == 0 ? 0 : -1;
@@ -901,6 +907,9 @@ static int level_has_blocks(const orc *o, int l) {
    get the flux correction. */
 static void advance_level(orc *o, int l, int sub, double dtL) {
   int L = o->L;
+  /* Fig. 2: Remesh(l) before the update; at the first sub-step it would repeat
+     the parent's Remesh(l-1), which regenerated these levels from the same data */
+  if (o->lts_remesh && sub == 1 && l >= 1 && l < L) remesh_amr(o, l, 0.5);
   double dtl = ldexp(dtL, L - l);
   double th1 = 0.5 * (double)sub, th2 = th1 + 0.25;
   copy_blocks(o, l, o->q[l], o->q0[l], 0);
@@ -1193,11 +1202,17 @@ static void br_cluster_level(orc *o, int l, const uint8_t *fl, double eta) {
   br_box(o, l, fl, b, eta);
 }
 
-static void grad_flags(orc *o, double epsw, double eta) {
+/* flags of levels l0..L-1 (sig of every other level cleared); with th >= 0 the
+   absent cells of level l0 are predicted from level l0-1 interpolated in time
+   (th between its step's start and end), as its ghost cells are */
+static void grad_flags_range(orc *o, double epsw, double eta, int l0, double th) {
   int L = o->L, dim = o->dim;
   for (int l = 0; l <= L; l++) { memset(o->sig[l], 0, (size_t)o->nblk[l]); }
-  for (int l = 0; l < L; l++) {
-    double *E = build_ext(o, l, o->q[l], l > 0 ? o->q[l - 1] : NULL);
+  for (int l = l0; l < L; l++) {
+    double *C = NULL;
+    if (l > 0) C = (l == l0 && th >= 0.0) ? time_interp(o, l - 1, th) : o->q[l - 1];
+    double *E = build_ext(o, l, o->q[l], C);
+    if (C && C != o->q[l - 1]) free(C);
     uint8_t *fl = (uint8_t *)calloc((size_t)o->nblk[l], 1);
     for (int bk = 0; bk < o->nb[l][2]; bk++)
       for (int bj = 0; bj < o->nb[l][1]; bj++)
@@ -1246,6 +1261,7 @@ static void grad_flags(orc *o, double epsw, double eta) {
     free(E);
   }
 }
+static void grad_flags(orc *o, double epsw, double eta) { grad_flags_range(o, epsw, eta, 0, -1.0); }
 
 /* ------------------------------------------------------------------------ */
 /* tree update (Section 2.1 refinement / coarsening, gradedness).  Block reading
@@ -1311,8 +1327,80 @@ int orc_adapt(orc *o, int crit, double eps, double epsw, double eta, int precisi
           need[l - 1][bidx(o, l - 1, pi, pj, pk)] = 1;
           mark_nbrs(o, need, l - 1, pi, pj, pk);
         }
-  /* apply, coarse to fine: drop, then predict new blocks from the level below */
-  for (int l = 1; l <= L; l++) {
+  apply_need(o, need, 1);
+  for (int l = 0; l <= L; l++) free(need[l]);
+  return 0;
+}
+
+/* Remesh(l0) of Fig. 2 (AMR with level-dependent steps): at the start of a
+   sub-step of level l0, with every level >= l0 at the same time, the levels
+   above l0 are regenerated from the gradient flags of levels l0..L-1 (level
+   l0's absent cells predicted from level l0-1 interpolated in time, th); the
+   tree of levels <= l0 is kept.  Reading of the nesting rule: the closure adds
+   blocks above l0 only, and a block of level l0+1 or finer survives only where
+   its parent and the parent's 3^d-1 neighbours are in the tree (finest last,
+   so an unsupported block takes its descendants along). */
+static void remesh_amr(orc *o, int l0, double th) {
+  int L = o->L, dim = o->dim;
+  grad_flags_range(o, o->rm_epsw, o->rm_eta, l0, th);
+  uint8_t *need[OMAXL] = {0};
+  for (int l = 0; l <= L; l++) {
+    need[l] = (uint8_t *)calloc((size_t)o->nblk[l], 1);
+    if (l <= l0) memcpy(need[l], o->ex[l], (size_t)o->nblk[l]);
+  }
+  int kz = dim == 3 ? 2 : 1;
+  for (int l = l0; l < L; l++)
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++)
+        for (int bi = 0; bi < o->nb[l][0]; bi++) {
+          long b = bidx(o, l, bi, bj, bk);
+          if (!o->ex[l][b] || !o->sig[l][b]) continue;
+          for (int c = 0; c < kz; c++)
+            for (int bb = 0; bb < 2; bb++)
+              for (int a = 0; a < 2; a++)
+                need[l + 1][bidx(o, l + 1, 2 * bi + a, 2 * bj + bb, dim == 3 ? 2 * bk + c : 0)] = 1;
+        }
+  for (int l = L; l > l0; l--)
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++)
+        for (int bi = 0; bi < o->nb[l][0]; bi++) {
+          if (!need[l][bidx(o, l, bi, bj, bk)]) continue;
+          int pi = bi >> 1, pj = bj >> 1, pk = bk >> 1;
+          for (int c = 0; c < kz; c++)
+            for (int bb = 0; bb < 2; bb++)
+              for (int a = 0; a < 2; a++)
+                need[l][bidx(o, l, 2 * pi + a, 2 * pj + bb, dim == 3 ? 2 * pk + c : 0)] = 1;
+          if (l - 1 > l0) {
+            need[l - 1][bidx(o, l - 1, pi, pj, pk)] = 1;
+            mark_nbrs(o, need, l - 1, pi, pj, pk);
+          }
+        }
+  for (int l = l0 + 1; l <= L; l++)
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++)
+        for (int bi = 0; bi < o->nb[l][0]; bi++) {
+          long b = bidx(o, l, bi, bj, bk);
+          if (!need[l][b]) continue;
+          int pi = bi >> 1, pj = bj >> 1, pk = bk >> 1, ok = need[l - 1][bidx(o, l - 1, pi, pj, pk)] != 0;
+          for (int c = (dim == 3 ? -1 : 0); c <= (dim == 3 ? 1 : 0) && ok; c++)
+            for (int bb = -1; bb <= 1 && ok; bb++)
+              for (int a = -1; a <= 1 && ok; a++) {
+                int x = bc_block(o, l - 1, 0, pi + a), y = bc_block(o, l - 1, 1, pj + bb),
+                    z = bc_block(o, l - 1, 2, pk + c);
+                if (x < 0 || y < 0 || z < 0) continue;
+                if (!need[l - 1][bidx(o, l - 1, x, y, z)]) ok = 0;
+              }
+          if (!ok) need[l][b] = 0;
+        }
+  apply_need(o, need, l0 + 1);
+  for (int l = 0; l <= L; l++) free(need[l]);
+}
+
+/* apply a needed-block map to levels lfrom..L, coarse to fine: drop, then
+   predict new blocks from the level below */
+static void apply_need(orc *o, uint8_t **need, int lfrom) {
+  int L = o->L;
+  for (int l = lfrom; l <= L; l++) {
     long nc = o->ncell[l];
     uint8_t *old = (uint8_t *)malloc((size_t)o->nblk[l]);
     memcpy(old, o->ex[l], (size_t)o->nblk[l]);
@@ -1329,8 +1417,6 @@ int orc_adapt(orc *o, int crit, double eps, double epsw, double eta, int precisi
         }
     free(old);
   }
-  for (int l = 0; l <= L; l++) free(need[l]);
-  return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1406,6 +1492,16 @@ void orc_br_cluster(orc *o, int l, const uint8_t *fl, double eta, uint8_t *out) 
 int orc_set_clustering(orc *o, int mode) {
   if (mode != O_CLUSTER_ROWS && mode != O_CLUSTER_BR) return -1;
   o->clustering = mode;
+  return 0;
+}
+
+/* Remesh(l) inside the level recursion (Fig. 2) for the gradient criterion
+   with level-dependent steps: on with these flag parameters, or off */
+int orc_set_lts_remesh(orc *o, int on, double epsw, double eta) {
+  if (on != 0 && on != 1) return -1;
+  o->lts_remesh = on;
+  o->rm_epsw = epsw;
+  o->rm_eta = eta;
   return 0;
 }
 
