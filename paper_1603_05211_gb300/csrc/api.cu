@@ -462,6 +462,10 @@ struct Seq {
   // then level l+1 two steps, then projection and flux correction of level l.
   void advance(int l, int sub) {
     int L = c->g.L;
+    // Fig. 2: Remesh(l) before the update; at the first sub-step it would repeat
+    // the parent's Remesh(l-1), which regenerated these levels from the same data
+    if (sub == 1 && l >= 1 && l < L && c->cfg.adapt && c->cfg.lts_remesh && c->cfg.criterion == MRFV_CRIT_GRAD)
+      remesh(l);
     double th1 = 0.5 * sub, th2 = th1 + 0.25;
     launch_copy_level<T>(c->g, LK_EXIST, l, l, U(), U0(), sized(c, LK_EXIST, l, l, block_cells(c->g.dim), 256, c->grid), c->st);
     c->nlaunch += 1;
@@ -518,12 +522,17 @@ struct Seq {
     launch_prop_features<T>(c->g, U(), c->maxdet, (const T *)c->scale, c->cfg.eps, c->pfeat, c->grid, c->st);
     c->nlaunch += 1;
   }
+  // Remesh(l0) of Fig. 2 at the second sub-step of level l0: flags of levels
+  // l0..L-1 (level l0's absent cells from level l0-1 halfway through its step),
+  // clustering, children of flagged blocks, closure above l0 only, nesting, then
+  // the tree update of the levels above l0
+  void remesh(int l0);
   void gradflags(bool cleared = false) {
     if (!cleared) {
       cudaMemsetAsync(c->gflag, 0, c->maptotal, c->st);
       cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
     }
-    launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, c->bgrid, c->st);
+    launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, 0, (const T *)nullptr, 0.0, c->bgrid, c->st);
     if (c->cfg.clustering == MRFV_CLUSTER_BR)
       launch_br(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
     else
@@ -551,6 +560,24 @@ void apply_need(mrfv_ctx *c, bool prolong, bool cleared = false) {
   launch_rebuild_lists(c->g, c->kbits, c->tcount, c->toff, c->ntiles, c->grid, c->st);
   c->nlaunch += 2 + rebuild_launches(c->ntiles);
   if (prolong) dispatch(c, [&](auto &s) { s.prolong_new(); });
+}
+
+template <typename T>
+void Seq<T>::remesh(int l0) {
+  const Geo &g = c->g;
+  const int L = g.L;
+  launch_remesh_begin(g, c->maptotal, c->sig, c->gflag, c->need, c->nnew, l0, c->grid, c->st);
+  launch_gradflags<T>(g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, l0, U0(), 0.5, c->bgrid, c->st);
+  if (c->cfg.clustering == MRFV_CLUSTER_BR)
+    launch_br(g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
+  else
+    launch_cluster(g, c->gflag, c->sig, c->cfg.eta_tol, c->grid, c->st);
+  launch_need_mark(g, c->sig, c->need, MRFV_CRIT_GRAD, c->grid, c->st);
+  for (int m = L; m >= l0 + 1; m--)
+    launch_need_close(g, m, c->need, grid_for(level_blocks(g, m), 256, c->grid), c->st, m - 1 > l0);
+  for (int m = l0 + 1; m <= L; m++) launch_need_prune(g, m, c->need, c->grid, c->st);
+  c->nlaunch += 5 + 2 * (L - l0);
+  apply_need(c, true, true);
 }
 
 void prop_infer(mrfv_ctx *c) {
@@ -657,6 +684,7 @@ int mrfv_config_default(mrfv_config *cfg) {
   cfg->eps_w = 0.05;
   cfg->eta_tol = 0.8;
   cfg->use_graph = 1;
+  cfg->lts_remesh = 1;
   return MRFV_OK;
 }
 
@@ -681,6 +709,7 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   if (cfg->clustering != MRFV_CLUSTER_ROWS && cfg->clustering != MRFV_CLUSTER_BR)
     return fail(nullptr, MRFV_ERR_ARG, "clustering");
   if (!(cfg->eps_p >= 0.0)) return fail(nullptr, MRFV_ERR_ARG, "eps_p");
+  if (cfg->lts_remesh != 0 && cfg->lts_remesh != 1) return fail(nullptr, MRFV_ERR_ARG, "lts_remesh");
   {
     Geo gg;
     long long a, b, f;

@@ -25,8 +25,8 @@ template <typename T> void launch_totals(const Geo &, const T *A, double *out, i
 template <typename T> void launch_reflux(const Geo &, int l0, int l1, T *A, const T *FR, int grid, cudaStream_t);
 template <typename T> void launch_copy_level(const Geo &, int kind, int l0, int l1, const T *src, T *dst, int grid,
                                              cudaStream_t);
-template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw, double epsp, uint8_t *gflag, int grid,
-                                           cudaStream_t);
+template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw, double epsp, uint8_t *gflag, int l0,
+                                           const T *A0, double theta, int grid, cudaStream_t);
 template <typename T> void launch_project_level(const Geo &, int l, const T *A, const double *coarse, double *out, cudaStream_t);
 // finite-volume stage and CFL reduction (fv_f32.cu, fv_f64.cu)
 template <typename T> void launch_fv(const Geo &, const FVArgs<T> &, bool split, int grid, cudaStream_t);
@@ -42,7 +42,10 @@ template <typename T> int fv_ctas_per_sm(int dim, bool split);
 
 // integer tree work (tree.cu)
 void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t);
-void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t);
+void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t, bool parents = true);
+void launch_remesh_begin(const Geo &, long long total, uint8_t *sig, uint8_t *gflag, uint8_t *need, int *nnew, int l0,
+                         int grid, cudaStream_t);
+void launch_need_prune(const Geo &, int l, uint8_t *need, int grid, cudaStream_t);
 void launch_adapt_begin(const Geo &, long long total, uint8_t *sig, double *maxdet, uint8_t *gflag, uint8_t *need,
                         int *nnew, double *t, const double *dt, double factor, long long *counter, int lts,
                         int32_t *pub, int grid, cudaStream_t);

@@ -553,9 +553,10 @@ __global__ void k_copy_level(Geo g, int kind, int l0, int l1, const T *__restric
 // density of level l at global cell (i, j, k) (already inside the domain):
 // the block's value, or the prediction from level l-1 when the block is absent
 template <typename T, int D>
-__device__ T var_ext(const Geo &g, int l, const T *__restrict__ A0, int v, int i, int j, int k) {
+__device__ T var_ext(const Geo &g, int l, const T *__restrict__ Abase, int v, int i, int j, int k,
+                     const T *__restrict__ C0base = nullptr, T theta = T(0)) {
   constexpr int B = (D == 2) ? 64 : 512;
-  const T *__restrict__ A = A0 + (long long)v * g.cap * B;
+  const T *__restrict__ A = Abase + (long long)v * g.cap * B;
   int32_t s = g.idx[map_index(g, l, i >> 3, j >> 3, k >> 3)];
   if (s >= 0) return A[(long long)s * B + (i & 7) + 8 * (j & 7) + ((D == 3) ? 64 * (k & 7) : 0)];
   if (l == 0) {
@@ -575,7 +576,12 @@ __device__ T var_ext(const Geo &g, int l, const T *__restrict__ A0, int v, int i
           set_err(g, EB_TREE);
           val = nan_val<T>();
         } else {
-          val = A[(long long)cs * B + (x & 7) + 8 * (y & 7) + ((D == 3) ? 64 * (z & 7) : 0)];
+          const long long off = (long long)cs * B + (x & 7) + 8 * (y & 7) + ((D == 3) ? 64 * (z & 7) : 0);
+          val = A[off];
+          if (C0base) {  // level l-1 interpolated in time, as for ghost cells
+            const T a0 = C0base[(long long)v * g.cap * B + off];
+            val = a0 + theta * (val - a0);
+          }
         }
         P[a + 3 * (bb + 3 * c)] = val;
       }
@@ -584,9 +590,10 @@ __device__ T var_ext(const Geo &g, int l, const T *__restrict__ A0, int v, int i
 }
 // pressure of the same (possibly predicted) conserved state
 template <typename T, int D>
-__device__ T pres_ext(const Geo &g, int l, const T *__restrict__ A, int i, int j, int k) {
+__device__ T pres_ext(const Geo &g, int l, const T *__restrict__ A, int i, int j, int k,
+                      const T *__restrict__ C0 = nullptr, T theta = T(0)) {
   T Q[D + 2];
-  for (int v = 0; v < D + 2; v++) Q[v] = var_ext<T, D>(g, l, A, v, i, j, k);
+  for (int v = 0; v < D + 2; v++) Q[v] = var_ext<T, D>(g, l, A, v, i, j, k, C0, theta);
   const T rho = Q[0];
   T vel[3] = {T(0), T(0), T(0)};
   for (int d = 0; d < D; d++) vel[d] = Q[1 + d] / rho;
@@ -599,14 +606,18 @@ __device__ T pres_ext(const Geo &g, int l, const T *__restrict__ A, int i, int j
 // |rho(Q_{i+alpha}) - rho(Q_i)| > eps_w, or with eps_p > 0
 // |p(Q_{i+alpha}) - p(Q_i)| > eps_p, for some alpha in {0,1}^d \ {0}.
 template <typename T, int D>
-__global__ void k_gradflags(Geo g, const T *__restrict__ A, T epsw, T epsp, uint8_t *gflag) {
+// Levels l0..L-1 only; with A0 set, the absent cells of level l0 are predicted
+// from level l0-1 interpolated in time, A0 + theta (A - A0) (a remesh inside the
+// level recursion, where level l0-1 is at another time).
+__global__ void k_gradflags(Geo g, const T *__restrict__ A, T epsw, T epsp, uint8_t *gflag, int l0,
+                            const T *__restrict__ A0, T theta) {
   constexpr int EXT = 11;  // relative cells -1 .. 9
   constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
   __shared__ T rp[NP], pp[NP];
   const bool use_p = epsp > T(0);
   int b, e;
-  if (g.L < 1) return;
-  list_range(g, LK_EXIST, 0, g.L - 1, b, e);
+  if (g.L < 1 || l0 > g.L - 1) return;
+  list_range(g, LK_EXIST, l0, g.L - 1, b, e);
   const long long cap = g.cap;
   for (int it = b + blockIdx.x; it < e; it += gridDim.x) {
     int s = g.lists[LK_EXIST * cap + it];
@@ -617,8 +628,9 @@ __global__ void k_gradflags(Geo g, const T *__restrict__ A, T epsw, T epsp, uint
       int r[3] = {p % EXT - 1, (p / EXT) % EXT - 1, (D == 3) ? p / (EXT * EXT) - 1 : 0};
       int gc[3];
       for (int d = 0; d < 3; d++) gc[d] = (d < D) ? bc_cell(g, l, d, 8 * bc3[d] + r[d]) : 0;
-      rp[p] = var_ext<T, D>(g, l, A, 0, gc[0], gc[1], gc[2]);
-      if (use_p) pp[p] = pres_ext<T, D>(g, l, A, gc[0], gc[1], gc[2]);
+      const T *C0 = (l == l0) ? A0 : nullptr;
+      rp[p] = var_ext<T, D>(g, l, A, 0, gc[0], gc[1], gc[2], C0, theta);
+      if (use_p) pp[p] = pres_ext<T, D>(g, l, A, gc[0], gc[1], gc[2], C0, theta);
     }
     __syncthreads();
     int hit = 0;

@@ -75,9 +75,10 @@ void launch_copy_level(const Geo &g, int kind, int l0, int l1, const T *src, T *
   else k_copy_level<T, 3><<<grid, 256, 0, st>>>(g, kind, l0, l1, src, dst);
 }
 template <typename T>
-void launch_gradflags(const Geo &g, const T *A, double epsw, double epsp, uint8_t *gflag, int grid, cudaStream_t st) {
-  if (g.dim == 2) k_gradflags<T, 2><<<grid, 128, 0, st>>>(g, A, T(epsw), T(epsp), gflag);
-  else k_gradflags<T, 3><<<grid, 256, 0, st>>>(g, A, T(epsw), T(epsp), gflag);
+void launch_gradflags(const Geo &g, const T *A, double epsw, double epsp, uint8_t *gflag, int l0, const T *A0,
+                      double theta, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_gradflags<T, 2><<<grid, 128, 0, st>>>(g, A, T(epsw), T(epsp), gflag, l0, A0, T(theta));
+  else k_gradflags<T, 3><<<grid, 256, 0, st>>>(g, A, T(epsw), T(epsp), gflag, l0, A0, T(theta));
 }
 
 template <typename T>
@@ -100,7 +101,8 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
   template void launch_reflux<T>(const Geo &, int, int, T *, const T *, int, cudaStream_t);                 \
   template void launch_gather_var<T>(const Geo &, int, int, int, const T *, double *, cudaStream_t);        \
   template void launch_copy_level<T>(const Geo &, int, int, int, const T *, T *, int, cudaStream_t);                  \
-  template void launch_gradflags<T>(const Geo &, const T *, double, double, uint8_t *, int, cudaStream_t);         \
+  template void launch_gradflags<T>(const Geo &, const T *, double, double, uint8_t *, int, const T *, double, int, \
+                                    cudaStream_t);         \
   template void launch_project_level<T>(const Geo &, int, const T *, const double *, double *, cudaStream_t);
 
 }  // namespace mrfv

@@ -75,7 +75,7 @@ __device__ __forceinline__ void k_need_mark_dev(Geo g, const uint8_t *sig, uint8
 
 // Closure on level l (run from the finest level down): a needed block needs its
 // siblings, its parent and the 3^d-1 neighbours of its parent (gradedness).
-__device__ __forceinline__ void k_need_close_dev(Geo g, int l, uint8_t *need) {
+__device__ __forceinline__ void k_need_close_dev(Geo g, int l, uint8_t *need, int parents) {
   long long n = g.mapoff[l + 1] - g.mapoff[l];
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
     long long t = g.mapoff[l] + u;
@@ -84,6 +84,7 @@ __device__ __forceinline__ void k_need_close_dev(Geo g, int l, uint8_t *need) {
     map_coords(g, l, t, bx, by, bz);
     int px = bx >> 1, py = by >> 1, pz = bz >> 1;
     mark_children(g, need, l - 1, px, py, pz);  // siblings (children of the parent)
+    if (!parents) continue;                     // remesh: level l-1 is kept as it is
     need[map_index(g, l - 1, px, py, pz)] = 1;
     mark_nbrs(g, need, l - 1, px, py, pz);
   }
@@ -409,7 +410,44 @@ __device__ __forceinline__ void k_scatter_dev(Geo g, const uint8_t *kbits, const
 
 // ---------------------------------------------------------------- kernels
 __global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit) { k_need_mark_dev(g, sig, need, crit); }
-__global__ void k_need_close(Geo g, int l, uint8_t *need) { k_need_close_dev(g, l, need); }
+__global__ void k_need_close(Geo g, int l, uint8_t *need, int parents) { k_need_close_dev(g, l, need, parents); }
+
+// Remesh(l0) inside the level recursion (Fig. 2): flags cleared, the tree of
+// levels <= l0 kept as needed, the levels above it to be rebuilt from flags.
+__global__ void k_remesh_begin(Geo g, long long total, uint8_t *sig, uint8_t *gflag, uint8_t *need, int *nnew,
+                               int l0) {
+  const long long keep = g.mapoff[l0 + 1];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    sig[t] = 0;
+    gflag[t] = 0;
+    need[t] = (t < keep && g.idx[t] >= 0) ? 1 : 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < MAXL) nnew[threadIdx.x] = 0;
+}
+
+// Nesting of a remesh: a needed block of level l stays only where its parent and
+// the parent's 3^d-1 neighbours are needed (run coarse to fine, so a dropped
+// block takes its descendants along).
+__global__ void k_need_prune(Geo g, int l, uint8_t *need) {
+  long long n = g.mapoff[l + 1] - g.mapoff[l];
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+    long long t = g.mapoff[l] + u;
+    if (!need[t]) continue;
+    int bx, by, bz;
+    map_coords(g, l, t, bx, by, bz);
+    const int px = bx >> 1, py = by >> 1, pz = bz >> 1;
+    bool ok = need[map_index(g, l - 1, px, py, pz)] != 0;
+    const int z0 = g.dim == 3 ? -1 : 0, z1 = g.dim == 3 ? 1 : 0;
+    for (int c = z0; c <= z1 && ok; c++)
+      for (int b = -1; b <= 1 && ok; b++)
+        for (int a = -1; a <= 1 && ok; a++) {
+          int x = bc_block(g, l - 1, 0, px + a), y = bc_block(g, l - 1, 1, py + b), z = bc_block(g, l - 1, 2, pz + c);
+          if (x < 0 || y < 0 || z < 0) continue;
+          if (!need[map_index(g, l - 1, x, y, z)]) ok = false;
+        }
+    if (!ok) need[t] = 0;
+  }
+}
 __global__ void k_free(Geo g, const uint8_t *need, int32_t *fs, int *ft) { k_free_dev(g, need, fs, ft); }
 __global__ void k_alloc(Geo g, const uint8_t *need, int32_t *fs, int *ft, int32_t *nl, int *nn) {
   k_alloc_dev(g, need, fs, ft, nl, nn);
@@ -724,8 +762,15 @@ static int fit(long long items, int per_cta, int grid) {
 void launch_need_mark(const Geo &g, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t st) {
   k_need_mark<<<fit(g.mapoff[g.L + 1], 256, grid), 256, 0, st>>>(g, sig, need, crit);
 }
-void launch_need_close(const Geo &g, int l, uint8_t *need, int grid, cudaStream_t st) {
-  k_need_close<<<grid, 256, 0, st>>>(g, l, need);
+void launch_need_close(const Geo &g, int l, uint8_t *need, int grid, cudaStream_t st, bool parents) {
+  k_need_close<<<grid, 256, 0, st>>>(g, l, need, parents ? 1 : 0);
+}
+void launch_remesh_begin(const Geo &g, long long total, uint8_t *sig, uint8_t *gflag, uint8_t *need, int *nnew, int l0,
+                         int grid, cudaStream_t st) {
+  k_remesh_begin<<<fit(total, 256, grid), 256, 0, st>>>(g, total, sig, gflag, need, nnew, l0);
+}
+void launch_need_prune(const Geo &g, int l, uint8_t *need, int grid, cudaStream_t st) {
+  k_need_prune<<<fit(g.mapoff[l + 1] - g.mapoff[l], 256, grid), 256, 0, st>>>(g, l, need);
 }
 void launch_free(const Geo &g, const uint8_t *need, int32_t *fs, int *ft, int grid, cudaStream_t st) {
   k_free<<<fit(g.mapoff[g.L + 1], 256, grid), 256, 0, st>>>(g, need, fs, ft);

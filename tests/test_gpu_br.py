@@ -30,6 +30,8 @@ def _pair(m, levels, base, lts, seed, bc=0, dim=2, ic=mi.IC_QUADRANTS, params=No
     o = oracle.Oracle(dim, levels, base, bc=bc, lo=lo, hi=hi, clustering=oracle.CLUSTER_BR)
     o.init(ic, params)
     o.adapt(oracle.CRIT_GRAD)
+    if lts:
+        o.set_lts_remesh(True, 0.05, 0.8)  # the solver's default (Fig. 2)
     return s, o
 
 
@@ -99,6 +101,8 @@ def _pair_p(m, dim, levels, base, lts, ic, params, clustering, scheme="muscl_rk2
                       scheme=oracle.SCHEME_HANCOCK if scheme == "hancock" else oracle.SCHEME_MUSCL_RK2)
     o.init(ic, params)
     o.adapt(oracle.CRIT_GRAD, eps_w=0.05, eps_p=0.05)
+    if lts:
+        o.set_lts_remesh(True, 0.05, 0.8, eps_p=0.05)
     return s, o
 
 
@@ -131,3 +135,31 @@ def test_pressure_gradient_rotated_ellipsoid_3d_hancock_lts(mrfv):
         o.adapt(oracle.CRIT_GRAD, eps_w=0.05, eps_p=0.05)
         _same(s, o)
     _close(s, o)
+
+
+@pytest.mark.parametrize("scheme", ["muscl_rk2", "hancock"])
+def test_lts_remesh_inside_the_recursion_matches_oracle(mrfv, scheme):
+    """Remesh(l) at the sub-steps (Fig. 2) on a moving shock whose waves leave
+    the refined region within a coarse step: trees after every coarse step and the
+    FP64 state against the oracle; the same run with the remesh switched off on
+    both sides differs (the rule is exercised)."""
+    def run(remesh):
+        s = mrfv.Solver(dim=2, levels=5, base_blocks=(2, 1, 1), adapt=True, criterion="grad", lts=True,
+                        clustering="br", scheme=scheme, cfl=0.4, lts_remesh=remesh)
+        s.init_state(mi.IC_SHOCKTUBE, mi.sod_params(0, 0.3))
+        o = oracle.Oracle(2, 5, (2, 1, 1), clustering=oracle.CLUSTER_BR,
+                          scheme=oracle.SCHEME_HANCOCK if scheme == "hancock" else oracle.SCHEME_MUSCL_RK2)
+        o.init(mi.IC_SHOCKTUBE, mi.sod_params(0, 0.3))
+        o.adapt(oracle.CRIT_GRAD)
+        o.set_lts_remesh(remesh, 0.05, 0.8)
+        _same(s, o)
+        for _ in range(3):
+            dt = o.dt(0.4, True)
+            assert s.step(0.0) == dt
+            o.step(dt, True)
+            o.adapt(oracle.CRIT_GRAD)
+            _same(s, o)
+        _close(s, o)
+        return s
+    a, b = run(True), run(False)
+    assert any(not np.array_equal(a.download_level(l)[0], b.download_level(l)[0], equal_nan=True) for l in range(5))

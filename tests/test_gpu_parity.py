@@ -39,6 +39,8 @@ def pair(m, dim, levels, base, lo=(0, 0, 0), hi=(1, 1, 1), bc=0, precision="fp64
     if adapt:
         o.adapt(oracle.CRIT_GRAD if criterion == "grad" else oracle.CRIT_MR, eps=eps,
                 precision=1 if precision == "fp32" else 0)
+    if adapt and criterion == "grad" and lts:
+        o.set_lts_remesh(True, 0.05, 0.8)  # the solver's default (Fig. 2)
     return s, o
 
 
@@ -333,6 +335,7 @@ def test_amr2d_fp32_base128_levels4_lts_full_size_steps(mrfv):
     def make():
         o = oracle.Oracle(2, 4, (16, 16, 1))
         o.init(mi.IC_QUADRANTS, P)
+        o.set_lts_remesh(True, 0.05, 0.8)
         return o
 
     o = make()
