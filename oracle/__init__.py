@@ -80,7 +80,7 @@ def _load():
             "orc_set_scheme": (I, [P, I]),
             "orc_set_clustering": (I, [P, I]),
             "orc_set_eps_p": (I, [P, D]),
-            "orc_set_lts_remesh": (I, [P, I, D, D]),
+            "orc_set_lts_remesh": (I, [P, I, I, D, D, D, I]),
             "orc_br_cluster": (None, [P, I, u8, D, u8]),
             "orc_predict": (D, [P, I, dp, I, I, I, I]),
         }
@@ -208,11 +208,14 @@ class Oracle:
         self.lib.orc_adapt(self._h, criterion, eps, eps_w, eta_tol, precision)
 
     def set_lts_remesh(self, on: bool = True, eps_w: float = 0.05, eta_tol: float = 0.8,
-                       eps_p: float = 0.0) -> None:
+                       eps_p: float = 0.0, criterion: int = CRIT_GRAD, eps: float = 1e-3,
+                       precision: int = 0) -> None:
         """Remesh the finer levels inside the level recursion (Fig. 2) when stepping
-        with level-dependent steps and the gradient criterion."""
+        with level-dependent steps, with the gradient (eps_w, eta_tol, eps_p) or
+        the MR criterion (eps, decided in single precision with precision 1)."""
         if self.lib.orc_set_eps_p(self._h, eps_p) != 0 or \
-                self.lib.orc_set_lts_remesh(self._h, int(bool(on)), eps_w, eta_tol) != 0:
+                self.lib.orc_set_lts_remesh(self._h, int(bool(on)), criterion, eps, eps_w, eta_tol,
+                                            precision) != 0:
             raise ValueError("oracle: bad remesh parameters")
 
     def totals(self) -> np.ndarray:

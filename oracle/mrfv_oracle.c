@@ -48,9 +48,10 @@ typedef struct {
   int scheme;         /* O_SCHEME_*: the MR scheme (default) or the AMR scheme of Section 2 */
   int clustering;     /* O_CLUSTER_*: clustering of gradient flags (Section 2.2) */
   double eps_p;       /* > 0: the gradient criterion also tests pressure (Section 4.2) */
-  int lts_remesh;     /* level-dependent steps with the gradient criterion: remesh the finer levels
-                         inside the recursion (Fig. 2), with these flag parameters */
-  double rm_epsw, rm_eta;
+  int lts_remesh;     /* level-dependent steps: remesh the finer levels inside the recursion (Fig. 2)
+                         with this criterion and these parameters */
+  int rm_crit, rm_precision;
+  double rm_eps, rm_epsw, rm_eta;
   double gamma;
   double lo[3], hi[3];
   int nb[OMAXL][3];   /* blocks per dimension (1 in unused dimensions) */
@@ -88,6 +89,8 @@ static int bc_cell(const orc *o, int l, int d, int i) {
 /* neighbouring block coordinate, or -1 when it lies outside a transmissive domain */
 static void apply_need(orc *o, uint8_t **need, int lfrom);
 static void remesh_amr(orc *o, int l0, double th);
+static void remesh_mr(orc *o, int l0, double th);
+static void close_and_nest(orc *o, uint8_t **need, int l0);
 
 static int bc_block(const orc *o, int l, int d, int b) {
   int N = o->nb[l][d];
@@ -909,7 +912,10 @@ static void advance_level(orc *o, int l, int sub, double dtL) {
   int L = o->L;
   /* Fig. 2: Remesh(l) before the update; at the first sub-step it would repeat
      the parent's Remesh(l-1), which regenerated these levels from the same data */
-  if (o->lts_remesh && sub == 1 && l >= 1 && l < L) remesh_amr(o, l, 0.5);
+  if (o->lts_remesh && sub == 1 && l >= 1 && l < L) {
+    if (o->rm_crit == O_CRIT_GRAD) remesh_amr(o, l, 0.5);
+    else remesh_mr(o, l, 0.5);
+  }
   double dtl = ldexp(dtL, L - l);
   double th1 = 0.5 * (double)sub, th2 = th1 + 0.25;
   copy_blocks(o, l, o->q[l], o->q0[l], 0);
@@ -953,9 +959,15 @@ void orc_step(orc *o, double dt, int lts) {
    level-0 field): s_rho = max|rho|, s_E = max|E|, s_m = max|rho| * max|v_n|,
    each at least 1e-14 * max|rho|.  precision 1: the state is rounded to single
    precision and the whole decision is taken in single precision. */
-int orc_analyse(orc *o, double eps, int precision, long *n_sig) {
+/* analysis of levels l0..L (significance of the others cleared); with th >= 0
+   the details of level l0 are taken against the prediction from level l0-1
+   interpolated in time (a remesh inside the level recursion) */
+static int analyse_range(orc *o, double eps, int precision, long *n_sig, int l0, double th);
+int orc_analyse(orc *o, double eps, int precision, long *n_sig) { return analyse_range(o, eps, precision, n_sig, 1, -1.0); }
+static int analyse_range(orc *o, double eps, int precision, long *n_sig, int l0, double th) {
   int L = o->L, nv = o->nv, dim = o->dim;
   long total = 0;
+  if (l0 < 1) l0 = 1;
   /* scales */
   double mr = 0.0, mE = 0.0, mv = 0.0;
   float fr = 0.0f, fE = 0.0f, fv = 0.0f;
@@ -1004,8 +1016,31 @@ int orc_analyse(orc *o, double eps, int precision, long *n_sig) {
       qf[l] = (float *)malloc(sizeof(float) * (size_t)nv * (size_t)o->ncell[l]);
       for (long m = 0; m < (long)nv * o->ncell[l]; m++) qf[l][m] = (float)o->q[l][m];
     }
-  for (int l = 1; l <= L; l++) {
+  for (int l = 1; l < l0 && l <= L; l++) {
+    memset(o->sig[l], 0, (size_t)o->nblk[l]);
+    for (long b = 0; b < o->nblk[l]; b++) o->maxdet[l][b] = 0.0;
+  }
+  for (int l = l0; l <= L; l++) {
     long nc = o->ncell[l];
+    const double *P = o->q[l - 1];
+    const float *Pf = precision == 1 ? qf[l - 1] : NULL;
+    double *Pi = NULL;
+    float *Pfi = NULL;
+    if (l == l0 && th >= 0.0) {
+      long n = (long)nv * o->ncell[l - 1];
+      if (precision == 0) {
+        Pi = time_interp(o, l - 1, th);
+        P = Pi;
+      } else {
+        Pfi = (float *)malloc(sizeof(float) * (size_t)n);
+        const float thf = (float)th;
+        for (long m = 0; m < n; m++) {
+          float a0 = (float)o->q0[l - 1][m];
+          Pfi[m] = a0 + thf * ((float)o->q[l - 1][m] - a0);
+        }
+        Pf = Pfi;
+      }
+    }
     for (int bk = 0; bk < o->nb[l][2]; bk++)
       for (int bj = 0; bj < o->nb[l][1]; bj++)
         for (int bi = 0; bi < o->nb[l][0]; bi++) {
@@ -1023,11 +1058,11 @@ int orc_analyse(orc *o, double eps, int precision, long *n_sig) {
                 long c = cidx(o, l, i, j, k);
                 for (int v = 0; v < nv; v++) {
                   if (precision == 0) {
-                    double d = o->q[l][(long)v * nc + c] - predict_cell(o, l, o->q[l - 1], v, i, j, k);
+                    double d = o->q[l][(long)v * nc + c] - predict_cell(o, l, P, v, i, j, k);
                     double r = fabs(d) / s[v];
                     if (r > md) md = r;
                   } else {
-                    float d = qf[l][(long)v * nc + c] - predict_cell_f(o, l, qf[l - 1], v, i, j, k);
+                    float d = qf[l][(long)v * nc + c] - predict_cell_f(o, l, Pf, v, i, j, k);
                     float r = fabsf(d) / sf[v];
                     if (r > mdf) mdf = r;
                   }
@@ -1037,6 +1072,8 @@ int orc_analyse(orc *o, double eps, int precision, long *n_sig) {
           else { o->maxdet[l][b] = (double)mdf; o->sig[l][b] = mdf > (float)eps; }
           total += o->sig[l][b];
         }
+    free(Pi);
+    free(Pfi);
   }
   for (int l = 0; l <= L; l++) free(qf[l]);
   if (n_sig) *n_sig = total;
@@ -1360,6 +1397,16 @@ static void remesh_amr(orc *o, int l0, double th) {
               for (int a = 0; a < 2; a++)
                 need[l + 1][bidx(o, l + 1, 2 * bi + a, 2 * bj + bb, dim == 3 ? 2 * bk + c : 0)] = 1;
         }
+  close_and_nest(o, need, l0);
+  apply_need(o, need, l0 + 1);
+  for (int l = 0; l <= L; l++) free(need[l]);
+}
+
+/* closure above l0 (siblings; parents and their neighbours only above l0), then
+   nesting: a block above l0 stays only where its parent and the parent's
+   neighbours are needed (coarse to fine) */
+static void close_and_nest(orc *o, uint8_t **need, int l0) {
+  int L = o->L, dim = o->dim, kz = dim == 3 ? 2 : 1;
   for (int l = L; l > l0; l--)
     for (int bk = 0; bk < o->nb[l][2]; bk++)
       for (int bj = 0; bj < o->nb[l][1]; bj++)
@@ -1392,6 +1439,39 @@ static void remesh_amr(orc *o, int l0, double th) {
               }
           if (!ok) need[l][b] = 0;
         }
+}
+
+/* Remesh(l0) with the MR criterion, the same way as remesh_amr (the paper does
+   not say when its MR code adapts inside the recursion; reading): details of
+   levels l0..L from data at one time (level l0's against level l0-1
+   interpolated in time, th); a significant block above l0 is kept with its
+   neighbours and refined, a significant block of level l0 is refined; levels
+   <= l0 are kept; closure and nesting above l0. */
+static void remesh_mr(orc *o, int l0, double th) {
+  int L = o->L, dim = o->dim, kz = dim == 3 ? 2 : 1;
+  analyse_range(o, o->rm_eps, o->rm_precision, NULL, l0, th);
+  uint8_t *need[OMAXL] = {0};
+  for (int l = 0; l <= L; l++) {
+    need[l] = (uint8_t *)calloc((size_t)o->nblk[l], 1);
+    if (l <= l0) memcpy(need[l], o->ex[l], (size_t)o->nblk[l]);
+  }
+  for (int l = l0; l <= L; l++)
+    for (int bk = 0; bk < o->nb[l][2]; bk++)
+      for (int bj = 0; bj < o->nb[l][1]; bj++)
+        for (int bi = 0; bi < o->nb[l][0]; bi++) {
+          long b = bidx(o, l, bi, bj, bk);
+          if (!o->ex[l][b] || !o->sig[l][b]) continue;
+          if (l > l0) {
+            need[l][b] = 1;
+            mark_nbrs(o, need, l, bi, bj, bk);
+          }
+          if (l < L)
+            for (int c = 0; c < kz; c++)
+              for (int bb = 0; bb < 2; bb++)
+                for (int a = 0; a < 2; a++)
+                  need[l + 1][bidx(o, l + 1, 2 * bi + a, 2 * bj + bb, dim == 3 ? 2 * bk + c : 0)] = 1;
+        }
+  close_and_nest(o, need, l0);
   apply_need(o, need, l0 + 1);
   for (int l = 0; l <= L; l++) free(need[l]);
 }
@@ -1497,11 +1577,15 @@ int orc_set_clustering(orc *o, int mode) {
 
 /* Remesh(l) inside the level recursion (Fig. 2) for the gradient criterion
    with level-dependent steps: on with these flag parameters, or off */
-int orc_set_lts_remesh(orc *o, int on, double epsw, double eta) {
-  if (on != 0 && on != 1) return -1;
+int orc_set_lts_remesh(orc *o, int on, int crit, double eps, double epsw, double eta, int precision) {
+  if ((on != 0 && on != 1) || (crit != O_CRIT_MR && crit != O_CRIT_GRAD) || (precision != 0 && precision != 1))
+    return -1;
   o->lts_remesh = on;
+  o->rm_crit = crit;
+  o->rm_eps = eps;
   o->rm_epsw = epsw;
   o->rm_eta = eta;
+  o->rm_precision = precision;
   return 0;
 }
 

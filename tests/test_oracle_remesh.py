@@ -100,3 +100,61 @@ def test_remesh_tracks_the_uniform_fine_solution_better(scheme):
     ea = np.abs(runs[0][0].project_finest()[0] - ref).mean()
     eb = np.abs(runs[1][0].project_finest()[0] - ref).mean()
     assert eb < 0.8 * ea, (ea, eb)
+
+
+# ---------------------------------------------------------------- MR criterion
+def _mrlt(levels, base, seed, remesh, eps=1e-3, scheme=oracle.SCHEME_MUSCL_RK2, steps=3, bc=oracle.BC_PERIODIC):
+    o = oracle.Oracle(2, levels, base, bc=bc, scheme=scheme)
+    o.init(mi.IC_QUADRANTS, mi.quadrant_params(seed))
+    o.adapt(oracle.CRIT_MR, eps=eps)
+    if remesh:
+        o.set_lts_remesh(True, criterion=oracle.CRIT_MR, eps=eps)
+    T0 = o.totals()
+    for _ in range(steps):
+        o.step(o.dt(0.4, True), True)
+        _tree_rules(o)
+        o.adapt(oracle.CRIT_MR, eps=eps)
+    return o, T0
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_MUSCL_RK2, oracle.SCHEME_HANCOCK])
+def test_mr_remesh_conserves_and_keeps_the_tree_rules(scheme):
+    o, T0 = _mrlt(4, (2, 2, 1), 2, True, scheme=scheme)
+    assert np.all(np.abs(o.totals() - T0) <= 1e-12 * np.abs(T0).max())
+
+
+def test_mr_remesh_changes_nothing_when_everything_is_significant():
+    a, _ = _mrlt(3, (2, 2, 1), 1, False, eps=-1.0)
+    b, _ = _mrlt(3, (2, 2, 1), 1, True, eps=-1.0)
+    for l in range(3):
+        assert np.array_equal(a.get_exist(l), b.get_exist(l))
+        x, y = a.get_level(l), b.get_level(l)
+        m = ~np.isnan(x)
+        assert np.array_equal(np.isnan(x), np.isnan(y)) and np.array_equal(x[m], y[m])
+
+
+def test_mr_remesh_tracks_the_uniform_fine_solution_better():
+    levels = 5
+    runs = []
+    for remesh in (False, True):
+        o = oracle.Oracle(2, levels, (2, 1, 1))
+        o.init(mi.IC_SHOCKTUBE, mi.sod_params(0, 0.3))
+        o.adapt(oracle.CRIT_MR, eps=1e-3)
+        if remesh:
+            o.set_lts_remesh(True, criterion=oracle.CRIT_MR, eps=1e-3)
+        dts = []
+        for _ in range(3):
+            dt = o.dt(0.4, True)
+            dts.append(dt)
+            o.step(dt, True)
+            o.adapt(oracle.CRIT_MR, eps=1e-3)
+        runs.append((o, dts))
+    u = oracle.Oracle(2, 1, (32, 16, 1))
+    u.init(mi.IC_SHOCKTUBE, mi.sod_params(0, 0.3))
+    for dt in runs[1][1]:
+        for _ in range(1 << (levels - 1)):
+            u.step(dt)
+    ref = u.get_level(0)[0]
+    ea = np.abs(runs[0][0].project_finest()[0] - ref).mean()
+    eb = np.abs(runs[1][0].project_finest()[0] - ref).mean()
+    assert eb < 0.5 * ea, (ea, eb)
