@@ -112,9 +112,10 @@ typedef struct {
   double eps_p;         /* gradient criterion: > 0 also flags |p(Q_{i+alpha}) - p(Q_i)| > eps_p, with p from
                            the cell's (predicted, where its block is absent) conserved state; 0 (default):
                            density only.  The 3D case of Section 4.2 tests density and pressure. */
-  int lts_remesh;       /* with adapt, lts and the gradient criterion: 1 (default) regenerates the levels
-                           above l at the second sub-step of every level l >= 1 inside the level recursion
-                           (Remesh(l) of Fig. 2, flags from data at one time); 0 adapts once per coarse step */
+  int lts_remesh;       /* with adapt and lts: 1 (default) regenerates the levels above l at the second
+                           sub-step of every level l >= 1 inside the level recursion (Remesh(l) of Fig. 2,
+                           with the configured criterion on data at one time; the MR criterion uses its
+                           safety zone there, not the proposer); 0 adapts once per coarse step */
 } mrfv_config;
 
 typedef struct {

@@ -464,8 +464,7 @@ struct Seq {
     int L = c->g.L;
     // Fig. 2: Remesh(l) before the update; at the first sub-step it would repeat
     // the parent's Remesh(l-1), which regenerated these levels from the same data
-    if (sub == 1 && l >= 1 && l < L && c->cfg.adapt && c->cfg.lts_remesh && c->cfg.criterion == MRFV_CRIT_GRAD)
-      remesh(l);
+    if (sub == 1 && l >= 1 && l < L && c->cfg.adapt && c->cfg.lts_remesh) remesh(l);
     double th1 = 0.5 * sub, th2 = th1 + 0.25;
     launch_copy_level<T>(c->g, LK_EXIST, l, l, U(), U0(), sized(c, LK_EXIST, l, l, block_cells(c->g.dim), 256, c->grid), c->st);
     c->nlaunch += 1;
@@ -488,16 +487,18 @@ struct Seq {
       c->nlaunch += 2;
     }
   }
-  // cleared: the maps were cleared by the adaptation's first kernel
-  void analyse(double eps, bool cleared = false) {
+  // cleared: the maps were cleared by the adaptation's first kernel; l0, A0: a
+  // remesh's analysis of levels l0..L, level l0 against level l0-1 halfway
+  // through its step (A0 + (A - A0)/2)
+  void analyse(double eps, bool cleared = false, int l0 = 1, const T *A0 = nullptr) {
     launch_scales<T>(c->g, U(), c->red + 0, c->rctl + 3, (T *)c->scale,
                      grid_for(level_blocks(c->g, 0) * block_cells(c->g.dim), 256, c->grid), c->st);
     if (!cleared) {
       cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
       cudaMemsetAsync(c->maxdet, 0, c->maptotal * 8, c->st);
     }
-    launch_details<T>(c->g, U(), (const T *)c->scale, eps, c->sig, c->maxdet,
-                      sized(c, LK_EXIST, 1, c->g.L, 1, 1, c->bgrid), c->st);
+    launch_details<T>(c->g, U(), (const T *)c->scale, eps, c->sig, c->maxdet, l0, A0, 0.5,
+                      sized(c, LK_EXIST, l0, c->g.L, 1, 1, c->bgrid), c->st);
     c->nlaunch += 2;
   }
   void prolong_new() {
@@ -522,10 +523,12 @@ struct Seq {
     launch_prop_features<T>(c->g, U(), c->maxdet, (const T *)c->scale, c->cfg.eps, c->pfeat, c->grid, c->st);
     c->nlaunch += 1;
   }
-  // Remesh(l0) of Fig. 2 at the second sub-step of level l0: flags of levels
-  // l0..L-1 (level l0's absent cells from level l0-1 halfway through its step),
-  // clustering, children of flagged blocks, closure above l0 only, nesting, then
-  // the tree update of the levels above l0
+  // Remesh(l0) of Fig. 2 at the second sub-step of level l0: gradient flags of
+  // levels l0..L-1 (level l0's absent cells from level l0-1 halfway through its
+  // step) and clustering, or the MR analysis of levels l0..L (level l0 against
+  // level l0-1 halfway through its step); the marks above l0 (children of
+  // flagged or significant blocks, the safety zone above l0), closure above l0
+  // only, nesting, then the tree update of the levels above l0
   void remesh(int l0);
   void gradflags(bool cleared = false) {
     if (!cleared) {
@@ -567,12 +570,17 @@ void Seq<T>::remesh(int l0) {
   const Geo &g = c->g;
   const int L = g.L;
   launch_remesh_begin(g, c->maptotal, c->sig, c->gflag, c->need, c->nnew, l0, c->grid, c->st);
-  launch_gradflags<T>(g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, l0, U0(), 0.5, c->bgrid, c->st);
-  if (c->cfg.clustering == MRFV_CLUSTER_BR)
-    launch_br(g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
-  else
-    launch_cluster(g, c->gflag, c->sig, c->cfg.eta_tol, c->grid, c->st);
-  launch_need_mark(g, c->sig, c->need, MRFV_CRIT_GRAD, c->grid, c->st);
+  if (c->cfg.criterion == MRFV_CRIT_GRAD) {
+    launch_gradflags<T>(g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, l0, U0(), 0.5, c->bgrid, c->st);
+    if (c->cfg.clustering == MRFV_CLUSTER_BR)
+      launch_br(g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
+    else
+      launch_cluster(g, c->gflag, c->sig, c->cfg.eta_tol, c->grid, c->st);
+  } else {
+    // the MR analysis of levels l0..L (the safety zone, not the proposer, inside the recursion)
+    analyse(c->cfg.eps, true, l0, U0());
+  }
+  launch_need_mark(g, c->sig, c->need, c->cfg.criterion, c->grid, c->st, l0);
   for (int m = L; m >= l0 + 1; m--)
     launch_need_close(g, m, c->need, grid_for(level_blocks(g, m), 256, c->grid), c->st, m - 1 > l0);
   for (int m = l0 + 1; m <= L; m++) launch_need_prune(g, m, c->need, c->grid, c->st);

@@ -14,7 +14,8 @@ namespace mrfv {
 template <typename T> void launch_restrict(const Geo &, int l, T *A, int grid, cudaStream_t);
 template <typename T> void launch_scales(const Geo &, const T *A, unsigned long long *red, unsigned *done, T *scale,
                                          int grid, cudaStream_t);
-template <typename T> void launch_details(const Geo &, const T *A, const T *scale, double eps, uint8_t *sig, double *maxdet, int grid, cudaStream_t);
+template <typename T> void launch_details(const Geo &, const T *A, const T *scale, double eps, uint8_t *sig, double *maxdet,
+                                         int l0, const T *A0, double theta, int grid, cudaStream_t);
 template <typename T> void launch_prolong(const Geo &, int l, const int32_t *newlist, const int *nnew, T *A, int grid, cudaStream_t);
 template <typename T> void launch_ghost(const Geo &, int l0, int l1, const T *A, const T *A0, double theta, T *G, int grid, cudaStream_t);
 template <typename T> void launch_init(const Geo &, const ICParams &, const double *hi, T *A, int grid, cudaStream_t);
@@ -41,7 +42,7 @@ template <typename T> void launch_dt(const Geo &, const T *A, int lts, unsigned 
 template <typename T> int fv_ctas_per_sm(int dim, bool split);
 
 // integer tree work (tree.cu)
-void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t);
+void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t, int lkeep = 0);
 void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t, bool parents = true);
 void launch_remesh_begin(const Geo &, long long total, uint8_t *sig, uint8_t *gflag, uint8_t *need, int *nnew, int l0,
                          int grid, cudaStream_t);

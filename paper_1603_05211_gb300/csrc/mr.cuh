@@ -139,12 +139,15 @@ __global__ void k_scale_final(const unsigned long long *red, T *scale) {
 // its parent level; block flag = max over cells and variables of |d_v|/s_v > eps.
 template <typename T, int D>
 __device__ __forceinline__ void details_dev(const Geo &g, const T *__restrict__ A, const T *__restrict__ scale,
-                                            T eps, uint8_t *sig, double *maxdet, T *patch, T *wmax) {
+                                            T eps, uint8_t *sig, double *maxdet, T *patch, T *wmax, int l0,
+                                            const T *__restrict__ A0, T theta) {
   constexpr int B = (D == 2) ? 64 : 512;
   constexpr int EXT = 6;
   constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
   int b, e;
-  list_range(g, LK_EXIST, 1, g.L, b, e);
+  if (l0 < 1) l0 = 1;
+  if (l0 > g.L) return;
+  list_range(g, LK_EXIST, l0, g.L, b, e);
   const long long cap = g.cap;
   const int c = threadIdx.x;
   const int x = c & 7, y = (c >> 3) & 7, z = (D == 3) ? (c >> 6) : 0;
@@ -155,7 +158,9 @@ __device__ __forceinline__ void details_dev(const Geo &g, const T *__restrict__ 
     int l = g.slot_level[s];
     int bx = g.slot_coord[3 * s], by = g.slot_coord[3 * s + 1], bz = g.slot_coord[3 * s + 2];
     __syncthreads();
-    gather_patch<T, D, EXT>(g, l - 1, A, (const T *)nullptr, T(0), 4 * bx - 1, 4 * by - 1, 4 * bz - 1, patch, c, B);
+    // (level l0 of a remesh: the parent level interpolated in time)
+    gather_patch<T, D, EXT>(g, l - 1, A, l == l0 ? A0 : (const T *)nullptr, theta, 4 * bx - 1, 4 * by - 1, 4 * bz - 1,
+                            patch, c, B);
     __syncthreads();
     // this cell's parent inside the patch and its child signs
     int px = (x >> 1) + 1, py = (y >> 1) + 1, pz = (D == 3) ? (z >> 1) + 1 : 0;
@@ -186,10 +191,10 @@ __device__ __forceinline__ void details_dev(const Geo &g, const T *__restrict__ 
 
 template <typename T, int D>
 __global__ void k_details(Geo g, const T *__restrict__ A, const T *__restrict__ scale, T eps, uint8_t *sig,
-                          double *maxdet) {
+                          double *maxdet, int l0, const T *__restrict__ A0, T theta) {
   __shared__ T patch[(D + 2) * ((D == 2) ? 36 : 216)];
   __shared__ T wmax[32];
-  details_dev<T, D>(g, A, scale, eps, sig, maxdet, patch, wmax);
+  details_dev<T, D>(g, A, scale, eps, sig, maxdet, patch, wmax, l0, A0, theta);
 }
 
 // ---------------------------------------------------------------- prediction of new blocks

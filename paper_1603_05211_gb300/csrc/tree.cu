@@ -58,7 +58,9 @@ __device__ void mark_children(const Geo &g, uint8_t *need, int l, int bx, int by
 // below the finest level, its children are added.  GRAD: the children of every
 // flagged block are added.  MR with the proposer (crit 2): as MR without the
 // neighbours.
-__device__ __forceinline__ void k_need_mark_dev(Geo g, const uint8_t *sig, uint8_t *need, int crit) {
+// lkeep: a remesh keeps the levels <= lkeep as they are, so a significant block
+// there only asks for its children.
+__device__ __forceinline__ void k_need_mark_dev(Geo g, const uint8_t *sig, uint8_t *need, int crit, int lkeep) {
   long long total = g.mapoff[g.L + 1];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     if (g.idx[t] < 0 || !sig[t]) continue;
@@ -66,8 +68,10 @@ __device__ __forceinline__ void k_need_mark_dev(Geo g, const uint8_t *sig, uint8
     map_coords(g, l, t, bx, by, bz);
     if (crit == 0 || crit == 2) {  // MR (crit 2: without the safety zone, which the proposer replaces)
       if (l == 0) continue;
-      need[t] = 1;
-      if (crit == 0) mark_nbrs(g, need, l, bx, by, bz);
+      if (l > lkeep) {
+        need[t] = 1;
+        if (crit == 0) mark_nbrs(g, need, l, bx, by, bz);
+      }
     }
     if (l < g.L) mark_children(g, need, l, bx, by, bz);
   }
@@ -409,7 +413,9 @@ __device__ __forceinline__ void k_scatter_dev(Geo g, const uint8_t *kbits, const
 }
 
 // ---------------------------------------------------------------- kernels
-__global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit) { k_need_mark_dev(g, sig, need, crit); }
+__global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit, int lkeep) {
+  k_need_mark_dev(g, sig, need, crit, lkeep);
+}
 __global__ void k_need_close(Geo g, int l, uint8_t *need, int parents) { k_need_close_dev(g, l, need, parents); }
 
 // Remesh(l0) inside the level recursion (Fig. 2): flags cleared, the tree of
@@ -759,8 +765,8 @@ static int fit(long long items, int per_cta, int grid) {
   return (int)(n < grid ? n : grid);
 }
 
-void launch_need_mark(const Geo &g, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t st) {
-  k_need_mark<<<fit(g.mapoff[g.L + 1], 256, grid), 256, 0, st>>>(g, sig, need, crit);
+void launch_need_mark(const Geo &g, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t st, int lkeep) {
+  k_need_mark<<<fit(g.mapoff[g.L + 1], 256, grid), 256, 0, st>>>(g, sig, need, crit, lkeep);
 }
 void launch_need_close(const Geo &g, int l, uint8_t *need, int grid, cudaStream_t st, bool parents) {
   k_need_close<<<grid, 256, 0, st>>>(g, l, need, parents ? 1 : 0);

@@ -41,8 +41,9 @@ def pair(m, dim, levels, base, lo=(0, 0, 0), hi=(1, 1, 1), bc=0, precision="fp64
     if adapt:
         o.adapt(oracle.CRIT_GRAD if criterion == "grad" else oracle.CRIT_MR, eps=eps,
                 precision=1 if precision == "fp32" else 0)
-    if adapt and criterion == "grad" and lts:
-        o.set_lts_remesh(True, 0.05, 0.8)  # the solver's default (Fig. 2)
+    if adapt and lts:  # the solver's default: Remesh(l) inside the recursion (Fig. 2)
+        o.set_lts_remesh(True, 0.05, 0.8, criterion=oracle.CRIT_GRAD if criterion == "grad" else oracle.CRIT_MR,
+                         eps=eps, precision=1 if precision == "fp32" else 0)
     return s, o
 
 
