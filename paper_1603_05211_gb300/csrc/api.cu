@@ -779,6 +779,7 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   }
   c->stage_kernel = 0;
   c->fv_kinds = 0;
+  prepare_br();
   c->fvp_occupancy = c->prec == MRFV_FP32 ? fvp_ctas_per_sm<float>(cfg->dim) : fvp_ctas_per_sm<double>(cfg->dim);
   c->fvpgrid = c->nsm * c->fvp_occupancy;
   c->fvp_bpc = c->prec == MRFV_FP32 ? fvp_blocks_per_cta<float>(cfg->dim) : fvp_blocks_per_cta<double>(cfg->dim);

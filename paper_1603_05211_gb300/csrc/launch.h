@@ -43,6 +43,7 @@ template <typename T> int fv_ctas_per_sm(int dim, bool split);
 
 // integer tree work (tree.cu)
 void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t, int lkeep = 0);
+void prepare_br();
 void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t, bool parents = true);
 void launch_remesh_begin(const Geo &, long long total, uint8_t *sig, uint8_t *gflag, uint8_t *need, int *nnew, int l0,
                          int grid, cudaStream_t);

@@ -4,6 +4,8 @@
 // prefix-scan compaction that rebuilds the neighbour tables and the work lists
 // in level-major Morton order.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <limits.h>
 #include <stdint.h>
 
@@ -521,17 +523,19 @@ __global__ void k_cluster(Geo g, const uint8_t *gflag, uint8_t *sig, double eta)
 constexpr int kBrMaxSide = 8;
 constexpr int kBrMaxRounds = 4096;  // bound on the breadth-first rounds (error bit past it)
 constexpr int kBrThreads = 1024;
+constexpr int kBrSmemFlags = 160 * 1024;  // flags of a level held in shared memory up to this size
 
 struct BrBox {
   int lo[3], hi[3];
 };
 
-__device__ __forceinline__ int br_flag(const Geo &g, const uint8_t *gflag, int l, int x, int y, int z) {
-  return gflag[map_index(g, l, x, y, z)] ? 1 : 0;
+// F: the level's flags in map order (shared memory when they fit)
+__device__ __forceinline__ int br_flag(const Geo &g, const uint8_t *F, int l, int x, int y, int z) {
+  return F[x + (long long)g.nb[l][0] * (y + (long long)g.nb[l][1] * z)] ? 1 : 0;
 }
 
 // one warp: shrink, decide, mark or push the two parts; sigs: 3 x maxside ints
-__device__ void br_warp_box(const Geo &g, int l, const uint8_t *gflag, uint8_t *sig, double eta, BrBox b,
+__device__ void br_warp_box(const Geo &g, int l, const uint8_t *F, uint8_t *sig, double eta, BrBox b,
                             BrBox *next, int *nnext, int cap, int *sigs, int maxside) {
   const int lane = threadIdx.x & 31;
   const int D = g.dim;
@@ -542,7 +546,7 @@ __device__ void br_warp_box(const Geo &g, int l, const uint8_t *gflag, uint8_t *
   for (long long t = lane; t < vol; t += 32) {
     int c[3] = {b.lo[0] + (int)(t % ext[0]), b.lo[1] + (int)((t / ext[0]) % ext[1]),
                 b.lo[2] + (int)(t / ((long long)ext[0] * ext[1]))};
-    if (!br_flag(g, gflag, l, c[0], c[1], c[2])) continue;
+    if (!br_flag(g, F, l, c[0], c[1], c[2])) continue;
     cnt++;
     for (int d = 0; d < 3; d++) {
       mn[d] = min(mn[d], c[d]);
@@ -591,56 +595,83 @@ __device__ void br_warp_box(const Geo &g, int l, const uint8_t *gflag, uint8_t *
             c[d] = b.lo[d] + sl;
             c[a1] = b.lo[a1] + i;
             c[a2] = b.lo[a2] + j;
-            n += br_flag(g, gflag, l, c[0], c[1], c[2]);
+            n += br_flag(g, F, l, c[0], c[1], c[2]);
           }
         sigs[d * maxside + sl] = n;
       }
     }
     __syncwarp();
-    if (lane == 0) {
-      // holes: first direction with one, nearest the middle, lower index on ties
-      for (int d = 0; d < D && cd < 0; d++) {
-        int best = -1;
-        for (int sidx = 1; sidx + 1 < ext[d]; sidx++) {
-          if (sigs[d * maxside + sidx] != 0) continue;
-          int s = b.lo[d] + sidx;
-          if (best < 0 || abs(2 * s - (b.lo[d] + b.hi[d])) < abs(2 * best - (b.lo[d] + b.hi[d]))) best = s;
-        }
-        if (best >= 0) {
-          cd = d;
-          cut = best;
+    // holes: the first direction with one, the one nearest the middle, the lower
+    // index on ties (lanes over slices, then a warp reduction of (distance, index))
+    for (int d = 0; d < D && cd < 0; d++) {
+      const int mid2 = b.lo[d] + b.hi[d];
+      int bd = INT_MAX, bs = INT_MAX;
+      for (int sidx = 1 + lane; sidx + 1 < ext[d]; sidx += 32) {
+        if (sigs[d * maxside + sidx] != 0) continue;
+        const int s = b.lo[d] + sidx, dist = abs(2 * s - mid2);
+        if (dist < bd || (dist == bd && s < bs)) {
+          bd = dist;
+          bs = s;
         }
       }
-      // inflections of the signatures
-      if (cd < 0) {
-        long long bstr = 0;
-        for (int d = 0; d < D; d++) {
-          const int n = ext[d];
-          if (n < 4) continue;
-          const int *S = sigs + d * maxside;
-          for (int sidx = 1; sidx + 2 < n; sidx++) {
-            long long l1 = (long long)S[sidx - 1] - 2LL * S[sidx] + S[sidx + 1];
-            long long l2 = (long long)S[sidx] - 2LL * S[sidx + 1] + S[sidx + 2];
-            if (!((l1 < 0 && l2 > 0) || (l1 > 0 && l2 < 0))) continue;
-            long long str = l2 - l1 < 0 ? l1 - l2 : l2 - l1;
-            int pos = b.lo[d] + sidx;
-            bool better = false;
-            if (cd < 0 || str > bstr) better = true;
-            else if (str == bstr && d == cd) {
-              int dm = abs(2 * pos + 1 - (b.lo[d] + b.hi[d])), cm = abs(2 * cut + 1 - (b.lo[d] + b.hi[d]));
-              if (dm < cm) better = true;
-            }
-            if (better) {
-              cd = d;
-              cut = pos;
-              bstr = str;
-            }
+      for (int o = 16; o > 0; o >>= 1) {
+        const int od = __shfl_xor_sync(0xffffffffu, bd, o), os = __shfl_xor_sync(0xffffffffu, bs, o);
+        if (od < bd || (od == bd && os < bs)) {
+          bd = od;
+          bs = os;
+        }
+      }
+      if (bs != INT_MAX) {
+        cd = d;
+        cut = bs;
+      }
+    }
+    // inflections of the signatures: the strongest change of sign of the second
+    // difference, then the lower direction, the cut nearer the middle, the lower
+    // position (the order a scan by direction and position keeps)
+    if (cd < 0) {
+      long long bstr = -1;
+      int bdir = INT_MAX, bdm = INT_MAX, bpos = INT_MAX;
+      auto better = [](long long s1, int d1, int m1, int p1, long long s2, int d2, int m2, int p2) {
+        if (s1 != s2) return s1 > s2;
+        if (d1 != d2) return d1 < d2;
+        if (m1 != m2) return m1 < m2;
+        return p1 < p2;
+      };
+      for (int d = 0; d < D; d++) {
+        const int n = ext[d];
+        if (n < 4) continue;
+        const int *S = sigs + d * maxside;
+        for (int sidx = 1 + lane; sidx + 2 < n; sidx += 32) {
+          long long l1 = (long long)S[sidx - 1] - 2LL * S[sidx] + S[sidx + 1];
+          long long l2 = (long long)S[sidx] - 2LL * S[sidx + 1] + S[sidx + 2];
+          if (!((l1 < 0 && l2 > 0) || (l1 > 0 && l2 < 0))) continue;
+          long long str = l2 - l1 < 0 ? l1 - l2 : l2 - l1;
+          int pos = b.lo[d] + sidx, dm = abs(2 * pos + 1 - (b.lo[d] + b.hi[d]));
+          if (better(str, d, dm, pos, bstr, bdir, bdm, bpos)) {
+            bstr = str;
+            bdir = d;
+            bdm = dm;
+            bpos = pos;
           }
         }
       }
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long os = __shfl_xor_sync(0xffffffffu, bstr, o);
+        const int od = __shfl_xor_sync(0xffffffffu, bdir, o), om = __shfl_xor_sync(0xffffffffu, bdm, o),
+                  op = __shfl_xor_sync(0xffffffffu, bpos, o);
+        if (better(os, od, om, op, bstr, bdir, bdm, bpos)) {
+          bstr = os;
+          bdir = od;
+          bdm = om;
+          bpos = op;
+        }
+      }
+      if (bstr >= 0) {
+        cd = bdir;
+        cut = bpos;
+      }
     }
-    cd = __shfl_sync(0xffffffffu, cd, 0);
-    cut = __shfl_sync(0xffffffffu, cut, 0);
     __syncwarp();
   }
   if (cd < 0) {
@@ -664,10 +695,19 @@ __device__ void br_warp_box(const Geo &g, int l, const uint8_t *gflag, uint8_t *
 // boxes: per level 2 lists of cap_l boxes (cap_l = blocks of the level), at
 // boxes + 2 * mapoff[l]; sigs: per level and warp 3 * maxside ints
 __global__ void __launch_bounds__(kBrThreads) k_br(Geo g, const uint8_t *gflag, uint8_t *sig, double eta, BrBox *boxes,
-                                                   int *sigs, int maxside) {
+                                                   int *sigs, int maxside, int smem_flags) {
   const int l = blockIdx.x;
   if (l >= g.L) return;
   __shared__ int ncur, nnext;
+  // the level's flags, read by every round of box splitting: in shared memory when they fit
+  extern __shared__ uint8_t sflags[];
+  const long long nlev = g.mapoff[l + 1] - g.mapoff[l];
+  const uint8_t *F = gflag + g.mapoff[l];
+  if (nlev <= smem_flags) {
+    for (long long t = threadIdx.x; t < nlev; t += blockDim.x) sflags[t] = F[t];
+    __syncthreads();
+    F = sflags;
+  }
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int cap = (int)(g.mapoff[l + 1] - g.mapoff[l]);
   BrBox *A = boxes + 2 * g.mapoff[l], *B = A + cap;
@@ -686,7 +726,7 @@ __global__ void __launch_bounds__(kBrThreads) k_br(Geo g, const uint8_t *gflag, 
   for (; round < kBrMaxRounds && ncur > 0; round++) {
     if (threadIdx.x == 0) nnext = 0;
     __syncthreads();
-    for (int i = warp; i < ncur; i += nwarps) br_warp_box(g, l, gflag, sig, eta, A[i], B, &nnext, cap, wsig, maxside);
+    for (int i = warp; i < ncur; i += nwarps) br_warp_box(g, l, F, sig, eta, A[i], B, &nnext, cap, wsig, maxside);
     __syncthreads();
     BrBox *t = A;
     A = B;
@@ -812,12 +852,18 @@ void launch_cluster(const Geo &g, const uint8_t *gflag, uint8_t *sig, double eta
 size_t br_scratch_bytes(const Geo &g, long long maptotal, int maxside) {
   return (size_t)2 * maptotal * sizeof(BrBox) + (size_t)(g.L + 1) * (kBrThreads / 32) * 3 * maxside * sizeof(int) + 256;
 }
+// opt in to the clustering kernel's shared memory (once per context, outside any capture)
+void prepare_br() { cudaFuncSetAttribute(k_br, cudaFuncAttributeMaxDynamicSharedMemorySize, kBrSmemFlags); }
 void launch_br(const Geo &g, const uint8_t *gflag, uint8_t *sig, double eta, void *scratch, long long maptotal,
                int maxside, cudaStream_t st) {
   if (g.L < 1) return;
   BrBox *boxes = reinterpret_cast<BrBox *>(scratch);
   int *sigs = reinterpret_cast<int *>(boxes + 2 * maptotal);
-  k_br<<<g.L, kBrThreads, 0, st>>>(g, gflag, sig, eta, boxes, sigs, maxside);
+  // shared memory for the largest level's flags, up to 160 KB
+  long long most = 0;
+  for (int l = 0; l < g.L; l++) most = std::max(most, g.mapoff[l + 1] - g.mapoff[l]);
+  const int smem = (int)std::min<long long>(most, kBrSmemFlags);
+  k_br<<<g.L, kBrThreads, smem, st>>>(g, gflag, sig, eta, boxes, sigs, maxside, smem);
 }
 void launch_set_double(double *p, double v, cudaStream_t st) { k_set_double<<<1, 1, 0, st>>>(p, v); }
 void launch_level_params(const Geo &g, const double *dt, int lts, double *lev, float *levf, cudaStream_t st) {
