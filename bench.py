@@ -47,6 +47,22 @@ def dist_info():
     return rank, world, local
 
 
+def aggregate_ranks(ms: float, cells: float, world: int, dev) -> tuple:
+    """Whole-job throughput of N replicas: the slowest rank's time (max over
+    ranks) and the cell-updates of all ranks (sum), over the default process
+    group when world > 1.  Returns (max ms, cell-updates/s)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    c = torch.tensor([float(cells)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return ms_max, float(c.item()) / (ms_max * 1e-3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -539,13 +555,7 @@ def run_ours(args):
         s.step(0.0, sync=False)
     prof = s.profile_read()
     s.profile_enable(False)
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    c_all = torch.tensor([float(cells)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        dist.all_reduce(c_all, op=dist.ReduceOp.SUM)
-    ms_max = float(t_local.item())
-    value = float(c_all.item()) / (ms_max * 1e-3)
+    ms_max, value = aggregate_ranks(ms, cells, world, dev)
     hbm_peak, peak_kind = measured_peaks()
 
     result = None
