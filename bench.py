@@ -775,6 +775,79 @@ def run_laxliu(args):
     print(json.dumps(out), flush=True)
 
 
+def run_epssweep(args):
+    """The threshold study of Section 4.1: Lax-Liu configuration 6 at scale level
+    L (default 10), MR and MRLT with eps in {0.0005, 0.0008, 0.0010, 0.0023,
+    0.0025, 0.0028} (the paper's values, sorted), against the uniform FV-MR run
+    and the 4096^2 AMR-scheme reference of --case laxliu: L1(rho), perturbation,
+    accumulated cells and leaves, GPU time."""
+    import numpy as np
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    P = mi.laxliu6_params()
+    te = 0.25
+    L = args.eps_level
+    n = 1 << L
+    NI = 160 << (L - 7)
+    dt = te / NI
+    levels = L - 2
+    nref = args.laxliu_ref
+
+    def solver(n_cells, lv, adapt=False, lts=False, eps=0.0023, scheme="muscl_rk2"):
+        return m.Solver(dim=2, precision="fp32", levels=lv, base_blocks=(n_cells // (8 << (lv - 1)),) * 2 + (1,),
+                        adapt=adapt, lts=lts, criterion="mr", eps=eps, cfl=0.5, stream=stream, scheme=scheme)
+
+    r = solver(nref, 1, scheme="hancock")
+    r.init_state(mi.IC_QUADRANTS, P)
+    nr_steps = 5120 * nref // 4096
+    for _ in range(nr_steps):
+        r.step(te / nr_steps, sync=False)
+    rho_ref = r.download_level(0)[0][0]
+    r.close()
+    torch.cuda.empty_cache()
+    k = nref // n
+    ref = rho_ref.reshape(n, k, n, k).mean(axis=(1, 3))
+    u = solver(n, 1)
+    u.init_state(mi.IC_QUADRANTS, P)
+    ms_fv = timed_steps(u, NI, torch, stream, dt=dt)
+    l1_fv = float(np.abs(u.download_level(0)[0][0] - ref).sum() / (n * n))
+    u.close()
+    out = {"case": "epssweep_laxliu6", "L": L, "N_I": NI, "reference": {"grid": nref, "steps": nr_steps},
+           "FV_MR": {"l1_rho": l1_fv, "gpu_ms": ms_fv}, "rows": []}
+    for eps in (0.0005, 0.0008, 0.0010, 0.0023, 0.0025, 0.0028):
+        row = {"eps": eps}
+        for name, lts in (("MR", False), ("MRLT", True)):
+            steps = NI >> (levels - 1) if lts else NI
+            a = solver(n, levels, adapt=True, lts=lts, eps=eps)
+            a.init_state(mi.IC_QUADRANTS, P)
+            C = Lf = 0
+            mult = (1 << (levels - 1)) if lts else 1
+            for _ in range(steps):
+                st = a.stats()
+                C += st["total_blocks"] * 64 * mult
+                Lf += st["total_leaves"] * 64 * mult
+                a.step(dt, sync=True)
+            l1 = float(np.abs(a.project_finest()[0] - ref).sum() / (n * n))
+            a.close()
+            a = solver(n, levels, adapt=True, lts=lts, eps=eps)
+            a.init_state(mi.IC_QUADRANTS, P)
+            ms = timed_steps(a, steps, torch, stream, dt=dt)
+            a.close()
+            row[name] = {"l1_rho": l1, "perturbation_pct": 100.0 * abs(l1 - l1_fv) / l1_fv,
+                         "cell_compression_pct": 100.0 * C / (NI * n * n),
+                         "leaf_compression_pct": 100.0 * Lf / (NI * n * n),
+                         "gpu_ms": ms, "time_compression_pct": 100.0 * ms / ms_fv}
+            torch.cuda.empty_cache()
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def run_paper3d(args):
     """The paper's 3D benchmark (Section 4.2, Tables 6-8): the rotated ellipsoid on
     [-2,2]^3 to t_e = 0.28 with N_I = 16 * 2^(L-5) fixed steps at scale levels
@@ -920,7 +993,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="adaptive",
-                    choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d"],
+                    choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d", "epssweep"],
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
@@ -932,6 +1005,7 @@ def main():
     ap.add_argument("--laxliu-levels", dest="laxliu_levels", default="7,8,9,10")
     ap.add_argument("--laxliu-ref", dest="laxliu_ref", type=int, default=4096, help="reference grid of --case laxliu")
     ap.add_argument("--paper3d-levels", dest="paper3d_levels", default="5,6,7,8")
+    ap.add_argument("--eps-level", dest="eps_level", type=int, default=10, help="scale level L of --case epssweep")
     ap.add_argument("--paper3d-ref", dest="paper3d_ref", type=int, default=1024, help="reference grid of --case paper3d")
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--precision", default="fp32")
@@ -953,6 +1027,8 @@ def main():
         run_laxliu(args)
     elif args.case == "paper3d":
         run_paper3d(args)
+    elif args.case == "epssweep":
+        run_epssweep(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
