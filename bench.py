@@ -168,6 +168,13 @@ def uniform_roofline(m, torch, hbm_peak, steps=6, scheme="muscl_rk2"):
     return out
 
 
+# DRAM bytes (read + write) per stage launch measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, -k regex:k_fvs -s 60 -c 4 on the
+# default command: stage-1 and stage-2 launches of the timed graph steps,
+# averaged); the writes stay in L2 within the launch.  Re-measure when the
+# kernel changes.
+MEASURED_TRAFFIC = {(WORKLOAD, "k_fvs (staged)"): (2453760 + 3950080 + 2450432 + 3949056) / 4.0}
+
 STAGE_KERNELS = ((1, "k_fv (pencil)"), (2, "k_fvs (staged)"), (4, "k_fv (pencil, two threads per line)"),
                  (8, "k_fvp (pencil on staged primitives)"), (16, "k_fvs (staged MUSCL-Hancock)"))
 
@@ -544,26 +551,34 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    launches = s.profile_read()["launches"]
+    prof_g = s.profile_read()
+    launches = prof_g["launches"]
     st1 = s.stats()
     cells = st1["cell_updates"] - st0["cell_updates"]
     # the same steps once more with every stage launch bracketed by CUDA events
-    # (eager launches: events cannot be read per replay inside a graph)
+    # (eager launches: events cannot be read per replay inside a graph), in the
+    # stage kernel the captured step graph uses
+    graph_stage = {1: 1, 2: 2, 4: 3, 8: 4}.get(prof_g.get("graph_fv_kernels", 0), 0)
+    if graph_stage:
+        s.set_launch_shape(stage_kernel=graph_stage)
     s.profile_enable(True)
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
         s.step(0.0, sync=False)
     prof = s.profile_read()
     s.profile_enable(False)
+    if graph_stage:
+        s.set_launch_shape(stage_kernel=0)
     ms_max, value = aggregate_ranks(ms, cells, world, dev)
     hbm_peak, peak_kind = measured_peaks()
 
     result = None
     if rank == 0:
         fv_ach = prof["fv_bytes"] / (prof["fv_ms"] * 1e-3) / 1e9 if prof["fv_ms"] > 0 else 0.0
+        kname = stage_kernel_names(prof.get("fv_kernels", 0))
         roof = {"bound": "hbm", "achieved": round(fv_ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(fv_ach / hbm_peak, 4), "traffic": None,
-                "kernel": stage_kernel_names(prof.get("fv_kernels", 0)), "peak_kind": peak_kind,
+                "frac": round(fv_ach / hbm_peak, 4), "traffic": MEASURED_TRAFFIC.get((WORKLOAD, kname)),
+                "kernel": kname, "peak_kind": peak_kind,
                 "timing": "CUDA events around each stage launch, same workload and step count, eager launches",
                 "launches": prof["fv_launches"],
                 "avg_launch_us": round(prof["fv_ms"] * 1e3 / max(1, prof["fv_launches"]), 2),

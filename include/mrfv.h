@@ -256,6 +256,7 @@ typedef struct {
   int fv_kernels;        /* stage kernels those launches used (bit mask): 1 pencil, 2 staged (MR scheme),
                             4 pencil with two threads per line, 8 pencil on staged primitives,
                             16 staged MUSCL-Hancock */
+  int graph_fv_kernels;  /* the same bit mask for the stage kernels in the step graphs captured now */
 } mrfv_profile;
 /* enable != 0: reset the counters and bracket every finite-volume stage launch
    with CUDA events on the context stream (steps then launch eagerly instead of

@@ -50,6 +50,7 @@ struct mrfv_ctx {
   int stage_kernel;                  // 0 by leaf count, 1 pencil, 2 staged, 3 split pencil, 4 pencil on staged primitives
   int fvpgrid, fvp_occupancy, fvp_bpc;
   int fv_kinds;                      // stage kernels launched since profiling was enabled (bit mask)
+  int gkinds[2];                     // stage kernels in each captured step graph (bit mask)
   char *arena;
   size_t arena_bytes;
   bool own_arena;
@@ -779,6 +780,7 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   }
   c->stage_kernel = 0;
   c->fv_kinds = 0;
+  c->gkinds[0] = c->gkinds[1] = 0;
   prepare_br();
   c->fvp_occupancy = c->prec == MRFV_FP32 ? fvp_ctas_per_sm<float>(cfg->dim) : fvp_ctas_per_sm<double>(cfg->dim);
   c->fvpgrid = c->nsm * c->fvp_occupancy;
@@ -950,10 +952,14 @@ int capture_step(mrfv_ctx *c, int v) {
   long long before = c->nlaunch;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal);
+  const int kinds = c->fv_kinds;
+  c->fv_kinds = 0;
   if (e == cudaSuccess) {
     issue_step(c, v == 1);
     e = cudaStreamEndCapture(c->cap_st, &graph);
   }
+  c->gkinds[v] = c->fv_kinds;
+  c->fv_kinds = kinds;
   c->st = user;
   c->glaunch[v] = c->nlaunch - before;
   c->nlaunch = before;
@@ -1309,6 +1315,7 @@ int mrfv_profile_read(mrfv_ctx *c, mrfv_profile *o) {
   o->prop_ms = pms;
   o->prop_flops = (double)(c->pev_used / 2) * 2.0 * (double)c->maptotal * (16.0 * 81 + 16.0 * 432 + 432.0);
   o->fv_kernels = c->fv_kinds;
+  o->graph_fv_kernels = (c->gexec[0] ? c->gkinds[0] : 0) | (c->gexec[1] ? c->gkinds[1] : 0);
   return check_launch(c, "mrfv_profile_read");
 }
 
