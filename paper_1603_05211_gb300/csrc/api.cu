@@ -86,6 +86,9 @@ struct mrfv_ctx {
   int adam_t;
   // CUDA graph of one step: [0] with the CFL reduction, [1] with a preset dt
   cudaStream_t cap_st;
+  // second branch of a step: work that only reads the state runs beside the main chain
+  cudaStream_t st2;
+  cudaEvent_t ev_step, ev_dt, ev_ghost, ev_begin;
   cudaGraphExec_t gexec[2];
   long long glaunch[2];  // kernels in each captured step
   // Launch sizing: the list offsets the current launch shapes were chosen for
@@ -433,11 +436,12 @@ struct Seq {
     c->nlaunch += 1;
   }
   // one midpoint-RK2 step of every leaf with the same dt (Section 2)
-  void step_global() {
+  // (ghost_done: the first ghost strips were filled on the step's second branch)
+  void step_global(bool ghost_done = false) {
     int L = c->g.L;
     if (c->cfg.scheme == MRFV_SCHEME_HANCOCK) {
       // one stage into Us, leaves copied back, then the correction and projection
-      ghost(1, L, U(), nullptr, 0.0);
+      if (!ghost_done) ghost(1, L, U(), nullptr, 0.0);
       fvh(LK_LEAF, 0, L, U(), Us(), nullptr, 0.0, 1);
       launch_copy_level<T>(c->g, LK_LEAF, 0, L, Us(), U(), sized(c, LK_LEAF, 0, L, block_cells(c->g.dim), 256, c->grid), c->st);
       c->nlaunch += 1;
@@ -448,7 +452,7 @@ struct Seq {
       restrict_all(U());
       return;
     }
-    ghost(1, L, U(), nullptr, 0.0);
+    if (!ghost_done) ghost(1, L, U(), nullptr, 0.0);
     fv(LK_LEAF, 0, L, U(), U(), Us(), 0.5, 0, 0);
     restrict_all(Us());
     ghost(1, L, Us(), nullptr, 0.0);
@@ -608,14 +612,18 @@ void prop_infer(mrfv_ctx *c) {
 }
 
 // analysis / flags -> needed blocks -> closure -> apply
-// (step: the first kernel also does the step's time and counter bookkeeping)
-void adapt_tree(mrfv_ctx *c, bool step = false) {
+// the first kernel of an adaptation (step: with the step's time and counter bookkeeping)
+void adapt_begin(mrfv_ctx *c, bool step) {
+  const int lts = c->cfg.lts;
+  launch_adapt_begin(c->g, c->maptotal, c->sig, c->maxdet, c->gflag, c->need, c->nnew, step ? c->dsc + 1 : nullptr,
+                     c->dsc, lts ? ldexp(1.0, c->g.L) : 1.0, c->counter, lts, c->pub_dev, c->grid, c->st);
+  c->nlaunch += 1;
+}
+// (begun: adapt_begin already ran, on the step's second branch)
+void adapt_tree(mrfv_ctx *c, bool step = false, bool begun = false) {
   const Geo &g = c->g;
   bool use_prop = c->cfg.proposer && c->has_weights && c->cfg.criterion == MRFV_CRIT_MR;
-  const int lts = c->cfg.lts;
-  launch_adapt_begin(g, c->maptotal, c->sig, c->maxdet, c->gflag, c->need, c->nnew, step ? c->dsc + 1 : nullptr,
-                     c->dsc, lts ? ldexp(1.0, g.L) : 1.0, c->counter, lts, c->pub_dev, c->grid, c->st);
-  c->nlaunch += 1;
+  if (!begun) adapt_begin(c, step);
   if (c->cfg.criterion == MRFV_CRIT_MR) dispatch(c, [&](auto &s) { s.analyse(c->cfg.eps, true); });
   else dispatch(c, [&](auto &s) { s.gradflags(true); });
   if (use_prop) {
@@ -809,6 +817,9 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   cudaMemsetAsync(c->done, 0, 4, c->st);
   launch_init_freestack(c->freestack, c->freetop, c->g.cap, c->grid, c->st);
   if (cfg->use_graph && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) c->cap_st = nullptr;
+  if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess) c->st2 = nullptr;
+  for (cudaEvent_t *e : {&c->ev_step, &c->ev_dt, &c->ev_ghost, &c->ev_begin})
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) *e = nullptr;
   prop_setup();
   int rc = check_launch(c, "mrfv_create");
   if (rc == MRFV_OK) rc = check_device(c, "mrfv_create");
@@ -829,6 +840,9 @@ int mrfv_destroy(mrfv_ctx *c) {
   for (int v = 0; v < 2; v++)
     if (c->gexec[v]) cudaGraphExecDestroy(c->gexec[v]);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
+  if (c->st2) cudaStreamDestroy(c->st2);
+  for (cudaEvent_t e : {c->ev_step, c->ev_dt, c->ev_ghost, c->ev_begin})
+    if (e) cudaEventDestroy(e);
   if (c->pub_host) cudaFreeHost(c->pub_host);
   if (c->own_arena && c->arena) cudaFree(c->arena);
   delete c;
@@ -924,18 +938,43 @@ namespace {
 // nothing here synchronises, so the sequence can be captured into a graph.
 void issue_step(mrfv_ctx *c, bool preset) {
   int lts = c->cfg.lts;
+  // With global steps two branches: the first ghost strips and, once dt is known,
+  // the adaptation's first kernel (it clears maps the stages do not touch) run
+  // beside the CFL reduction and the stages.
+  const bool fork = !lts && c->st2 && c->ev_step && c->ev_dt && c->ev_ghost && c->ev_begin;
+  const bool fork_begin = fork && c->cfg.adapt;
   dispatch(c, [&](auto &s) {
+    if (fork) {
+      cudaEventRecord(c->ev_step, c->st);
+      cudaStreamWaitEvent(c->st2, c->ev_step, 0);
+      cudaStream_t main = c->st;
+      c->st = c->st2;
+      s.ghost(1, c->g.L, s.U(), nullptr, 0.0);
+      c->st = main;
+      cudaEventRecord(c->ev_ghost, c->st2);
+    }
     if (!preset) {
       s.compute_dt(lts);
     } else {
       launch_level_params(c->g, c->dsc, lts, c->lev, c->levf, c->st);
       c->nlaunch += 1;
     }
+    if (fork_begin) {
+      cudaEventRecord(c->ev_dt, c->st);
+      cudaStreamWaitEvent(c->st2, c->ev_dt, 0);
+      cudaStream_t main = c->st;
+      c->st = c->st2;
+      adapt_begin(c, true);
+      c->st = main;
+      cudaEventRecord(c->ev_begin, c->st2);
+    }
+    if (fork) cudaStreamWaitEvent(c->st, c->ev_ghost, 0);
     if (lts) s.advance(0, 0);
-    else s.step_global();
+    else s.step_global(fork);
   });
+  if (fork_begin) cudaStreamWaitEvent(c->st, c->ev_begin, 0);
   if (c->cfg.adapt) {
-    adapt_tree(c, true);
+    adapt_tree(c, true, fork_begin);
   } else {
     launch_advance(c->g, c->dsc + 1, c->dsc, lts ? ldexp(1.0, c->g.L) : 1.0, c->counter, lts, c->pub_dev, c->st);
     c->nlaunch += 1;
