@@ -633,7 +633,13 @@ def run_e2e(m, torch, stream, steps):
     L = WL["levels"] - 1
     ref = m.Solver(dim=2, precision="fp32", levels=WL["levels"], base_blocks=(1, 1, 1), adapt=False)
     ref.init_state(mi.IC_QUADRANTS, mi.quadrant_params(SEED + 1))
-    host_in = ref.download_level(L)[0]
+
+    def pinned(shape):
+        return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+
+    host_in = pinned((s.nv,) + s.cells_shape(L))
+    ref.download_level(L, out=host_in)
+    host_out = [pinned((s.nv,) + s.cells_shape(l)) for l in range(WL["levels"])]
     full = [np.ones(s.blocks_shape(l), np.uint8) for l in range(WL["levels"])]
     ref.close()
     st0 = s.stats()
@@ -647,7 +653,7 @@ def run_e2e(m, torch, stream, steps):
         s.step(0.0, sync=True)
     out_bytes = 0
     for l in range(WL["levels"]):
-        a, _ = s.download_level(l)
+        a, _ = s.download_level(l, out=host_out[l])
         out_bytes += a.nbytes
     el = time.perf_counter() - t0
     st1 = s.stats()

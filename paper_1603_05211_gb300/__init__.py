@@ -271,8 +271,15 @@ class Solver:
                     pool_capacity=s.pool_capacity, t=s.t, last_dt=s.last_dt, steps=s.steps,
                     cell_updates=s.cell_updates)
 
-    def download_level(self, level: int):
-        out = np.empty((self.nv,) + self.cells_shape(level), dtype=np.float64)
+    def download_level(self, level: int, out=None):
+        """Dense level (nv, ...) with NaN where absent, and the block existence map.
+        out: optional float64 C-contiguous array of that shape to fill (for
+        example a view of pinned host memory)."""
+        shape = (self.nv,) + self.cells_shape(level)
+        if out is None:
+            out = np.empty(shape, dtype=np.float64)
+        elif out.shape != shape or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("download_level: out must be a C-contiguous float64 array of shape %s" % (shape,))
         ex = np.empty(self.blocks_shape(level), dtype=np.uint8)
         self._check(self.lib.mrfv_download_level(self._h, level, _dp(out), out.size, _u8(ex)))
         return out, ex
