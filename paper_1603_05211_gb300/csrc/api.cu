@@ -506,11 +506,12 @@ struct Seq {
                       sized(c, LK_EXIST, l0, c->g.L, 1, 1, c->bgrid), c->st);
     c->nlaunch += 2;
   }
-  void prolong_new() {
-    for (int l = 1; l <= c->g.L; l++)
+  // new blocks of levels lfrom..L (a remesh above l0 creates none below l0+1)
+  void prolong_new(int lfrom = 1) {
+    for (int l = lfrom; l <= c->g.L; l++)
       launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(),
                         sized(c, LK_EXIST, l, l, 1, 1, grid_for(level_blocks(c->g, l), 1, c->bgrid)), c->st);
-    c->nlaunch += c->g.L;
+    c->nlaunch += c->g.L - lfrom + 1;
   }
   // CFL reduction; its last CTA sets dt and the per-level step table
   void compute_dt(int lts) {
@@ -561,13 +562,13 @@ void dispatch(mrfv_ctx *c, F f) {
 }
 
 // free, allocate, rebuild neighbour tables and lists, optionally predict new blocks
-void apply_need(mrfv_ctx *c, bool prolong, bool cleared = false) {
+void apply_need(mrfv_ctx *c, bool prolong, bool cleared = false, int lfrom = 1) {
   if (!cleared) cudaMemsetAsync(c->nnew, 0, MAXL * sizeof(int), c->st);
   launch_free(c->g, c->need, c->freestack, c->freetop, c->grid, c->st);
   launch_alloc(c->g, c->need, c->freestack, c->freetop, c->newlist, c->nnew, c->grid, c->st);
   launch_rebuild_lists(c->g, c->kbits, c->tcount, c->toff, c->ntiles, c->grid, c->st);
   c->nlaunch += 2 + rebuild_launches(c->ntiles);
-  if (prolong) dispatch(c, [&](auto &s) { s.prolong_new(); });
+  if (prolong) dispatch(c, [&](auto &s) { s.prolong_new(lfrom); });
 }
 
 template <typename T>
@@ -590,7 +591,7 @@ void Seq<T>::remesh(int l0) {
     launch_need_close(g, m, c->need, grid_for(level_blocks(g, m), 256, c->grid), c->st, m - 1 > l0);
   for (int m = l0 + 1; m <= L; m++) launch_need_prune(g, m, c->need, c->grid, c->st);
   c->nlaunch += 5 + 2 * (L - l0);
-  apply_need(c, true, true);
+  apply_need(c, true, true, l0 + 1);
 }
 
 void prop_infer(mrfv_ctx *c) {
