@@ -420,3 +420,22 @@ def test_download_var_coarsened_means(mrfv, dim):
             blocks = full[var].reshape(*[x for n in sh for x in (n // f, f)])
             want = blocks.mean(axis=tuple(range(1, 2 * len(sh), 2)))
             assert np.allclose(g, want, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("lts", [False, True])
+@pytest.mark.parametrize("eps", [1e9, -1.0])
+def test_degenerate_thresholds(mrfv, eps, lts):
+    """The two ends of the MR threshold: eps so large that nothing is significant
+    (the tree collapses to level 0 and stays there) and eps < 0 (every block
+    significant: the full tree), with global and level-dependent steps; trees and
+    FP64 states against the oracle."""
+    s, o = pair(mrfv, 2, 4, (2, 2, 1), adapt=True, lts=lts, eps=eps, params=mi.quadrant_params(4))
+    assert_same_tree(s, o)
+    for _ in range(3 if lts else 6):
+        run_pair(s, o, 1, lts=lts, adapt_crit=oracle.CRIT_MR, eps=eps)
+        assert_same_tree(s, o)
+    if eps > 1:
+        assert all(not s.get_tree(l).any() for l in range(1, 4))
+    else:
+        assert all(s.get_tree(l).all() for l in range(4))
+    assert_levels_close(s, o)
