@@ -534,16 +534,47 @@ __device__ __forceinline__ int br_flag(const Geo &g, const uint8_t *F, int l, in
   return F[x + (long long)g.nb[l][0] * (y + (long long)g.nb[l][1] * z)] ? 1 : 0;
 }
 
-// one warp: shrink, decide, mark or push the two parts; sigs: 3 x maxside ints
-__device__ void br_warp_box(const Geo &g, int l, const uint8_t *F, uint8_t *sig, double eta, BrBox b,
-                            BrBox *next, int *nnext, int cap, int *sigs, int maxside) {
-  const int lane = threadIdx.x & 31;
+// Shared partial results of the warps of a CTA, reduced per group of warps.
+struct BrShared {
+  long long cnt[32];
+  int mn[32][3], mx[32][3];
+  int hd[32][3], hs[32][3];                 // best hole per direction: distance, position
+  long long istr[32];                       // best inflection: strength, direction, distance, position
+  int idir[32], idm[32], ipos[32];
+};
+
+// barrier of a box step: the CTA when groups span several warps, else the warp
+// (the group size is the same for every thread of a round)
+__device__ __forceinline__ void br_sync(int G) {
+  if (G > 1) __syncthreads();
+  else __syncwarp();
+}
+
+__device__ __forceinline__ bool br_better(long long s1, int d1, int m1, int p1, long long s2, int d2, int m2, int p2) {
+  if (s1 != s2) return s1 > s2;
+  if (d1 != d2) return d1 < d2;
+  if (m1 != m2) return m1 < m2;
+  return p1 < p2;
+}
+
+// One box of the round, processed by a group of G warps (warps gw0..gw0+G-1;
+// tg = thread index in the group): shrink to its flags, then mark it (efficient
+// and no side above kBrMaxSide) or cut it in two (a hole of the signatures, the
+// strongest inflection, else the middle of the longest side) and push the parts.
+// Every thread of the CTA calls this with the same control flow (the barriers);
+// a group without a box passes active = false.  The decisions do not depend on
+// the group size: integer counts and a total order on the candidate cuts.
+__device__ void br_group_box(const Geo &g, int l, const uint8_t *F, uint8_t *sig, double eta, BrBox b, bool active,
+                             int gw0, int G, int tg, BrBox *next, int *nnext, int cap, int *sigs, int maxside,
+                             BrShared &sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, GT = 32 * G;
   const int D = g.dim;
   int ext[3] = {b.hi[0] - b.lo[0] + 1, b.hi[1] - b.lo[1] + 1, b.hi[2] - b.lo[2] + 1};
-  long long vol = (long long)ext[0] * ext[1] * ext[2];
+  long long vol = active ? (long long)ext[0] * ext[1] * ext[2] : 0;
+  // ---- shrink: count and bounding box of the flags
   int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
   long long cnt = 0;
-  for (long long t = lane; t < vol; t += 32) {
+  for (long long t = tg; t < vol; t += GT) {
     int c[3] = {b.lo[0] + (int)(t % ext[0]), b.lo[1] + (int)((t / ext[0]) % ext[1]),
                 b.lo[2] + (int)(t / ((long long)ext[0] * ext[1]))};
     if (!br_flag(g, F, l, c[0], c[1], c[2])) continue;
@@ -560,34 +591,56 @@ __device__ void br_warp_box(const Geo &g, int l, const uint8_t *F, uint8_t *sig,
       mx[d] = max(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
     }
   }
-  if (cnt == 0) return;
+  if (lane == 0) {
+    sh.cnt[warp] = cnt;
+    for (int d = 0; d < 3; d++) {
+      sh.mn[warp][d] = mn[d];
+      sh.mx[warp][d] = mx[d];
+    }
+  }
+  br_sync(G);
+  cnt = 0;
   for (int d = 0; d < 3; d++) {
-    b.lo[d] = mn[d];
-    b.hi[d] = mx[d];
-    ext[d] = mx[d] - mn[d] + 1;
+    mn[d] = INT_MAX;
+    mx[d] = INT_MIN;
   }
-  vol = (long long)ext[0] * ext[1] * ext[2];
+  for (int w = gw0; w < gw0 + G; w++) {
+    cnt += sh.cnt[w];
+    for (int d = 0; d < 3; d++) {
+      mn[d] = min(mn[d], sh.mn[w][d]);
+      mx[d] = max(mx[d], sh.mx[w][d]);
+    }
+  }
+  const bool live = active && cnt > 0;
   int longest = 0;
-  bool big = false;
-  for (int d = 0; d < D; d++) {
-    if (ext[d] > kBrMaxSide) big = true;
-    if (ext[d] > ext[longest]) longest = d;
+  bool big = false, efficient = false;
+  if (live) {
+    for (int d = 0; d < 3; d++) {
+      b.lo[d] = mn[d];
+      b.hi[d] = mx[d];
+      ext[d] = mx[d] - mn[d] + 1;
+    }
+    vol = (long long)ext[0] * ext[1] * ext[2];
+    for (int d = 0; d < D; d++) {
+      if (ext[d] > kBrMaxSide) big = true;
+      if (ext[d] > ext[longest]) longest = d;
+    }
+    efficient = (double)cnt >= eta * (double)vol;
   }
-  const bool efficient = (double)cnt >= eta * (double)vol;
-  if (efficient && !big) {
-    for (long long t = lane; t < vol; t += 32) {
+  const bool mark = live && efficient && !big;
+  if (mark) {
+    for (long long t = tg; t < vol; t += GT) {
       int x = b.lo[0] + (int)(t % ext[0]), y = b.lo[1] + (int)((t / ext[0]) % ext[1]);
       int z = b.lo[2] + (int)(t / ((long long)ext[0] * ext[1]));
       sig[map_index(g, l, x, y, z)] = 1;
     }
-    return;
   }
-  int cd = -1, cut = 0;
-  if (!efficient) {
-    // signatures: flags per slice along each direction (lanes over slices)
+  const bool split = live && !mark, search = split && !efficient;
+  // ---- signatures: flags per slice along each direction (the group's threads over slices)
+  if (search) {
     for (int d = 0; d < D; d++) {
       const int a1 = (d == 0) ? 1 : 0, a2 = (d == 2) ? 1 : 2;
-      for (int sl = lane; sl < ext[d]; sl += 32) {
+      for (int sl = tg; sl < ext[d]; sl += GT) {
         int n = 0;
         for (int j = 0; j < ext[a2]; j++)
           for (int i = 0; i < ext[a1]; i++) {
@@ -600,85 +653,108 @@ __device__ void br_warp_box(const Geo &g, int l, const uint8_t *F, uint8_t *sig,
         sigs[d * maxside + sl] = n;
       }
     }
-    __syncwarp();
-    // holes: the first direction with one, the one nearest the middle, the lower
-    // index on ties (lanes over slices, then a warp reduction of (distance, index))
-    for (int d = 0; d < D && cd < 0; d++) {
-      const int mid2 = b.lo[d] + b.hi[d];
-      int bd = INT_MAX, bs = INT_MAX;
-      for (int sidx = 1 + lane; sidx + 1 < ext[d]; sidx += 32) {
-        if (sigs[d * maxside + sidx] != 0) continue;
-        const int s = b.lo[d] + sidx, dist = abs(2 * s - mid2);
-        if (dist < bd || (dist == bd && s < bs)) {
-          bd = dist;
-          bs = s;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const int od = __shfl_xor_sync(0xffffffffu, bd, o), os = __shfl_xor_sync(0xffffffffu, bs, o);
-        if (od < bd || (od == bd && os < bs)) {
-          bd = od;
-          bs = os;
-        }
-      }
-      if (bs != INT_MAX) {
-        cd = d;
-        cut = bs;
-      }
-    }
-    // inflections of the signatures: the strongest change of sign of the second
-    // difference, then the lower direction, the cut nearer the middle, the lower
-    // position (the order a scan by direction and position keeps)
-    if (cd < 0) {
-      long long bstr = -1;
-      int bdir = INT_MAX, bdm = INT_MAX, bpos = INT_MAX;
-      auto better = [](long long s1, int d1, int m1, int p1, long long s2, int d2, int m2, int p2) {
-        if (s1 != s2) return s1 > s2;
-        if (d1 != d2) return d1 < d2;
-        if (m1 != m2) return m1 < m2;
-        return p1 < p2;
-      };
-      for (int d = 0; d < D; d++) {
-        const int n = ext[d];
-        if (n < 4) continue;
-        const int *S = sigs + d * maxside;
-        for (int sidx = 1 + lane; sidx + 2 < n; sidx += 32) {
-          long long l1 = (long long)S[sidx - 1] - 2LL * S[sidx] + S[sidx + 1];
-          long long l2 = (long long)S[sidx] - 2LL * S[sidx + 1] + S[sidx + 2];
-          if (!((l1 < 0 && l2 > 0) || (l1 > 0 && l2 < 0))) continue;
-          long long str = l2 - l1 < 0 ? l1 - l2 : l2 - l1;
-          int pos = b.lo[d] + sidx, dm = abs(2 * pos + 1 - (b.lo[d] + b.hi[d]));
-          if (better(str, d, dm, pos, bstr, bdir, bdm, bpos)) {
-            bstr = str;
-            bdir = d;
-            bdm = dm;
-            bpos = pos;
-          }
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long os = __shfl_xor_sync(0xffffffffu, bstr, o);
-        const int od = __shfl_xor_sync(0xffffffffu, bdir, o), om = __shfl_xor_sync(0xffffffffu, bdm, o),
-                  op = __shfl_xor_sync(0xffffffffu, bpos, o);
-        if (better(os, od, om, op, bstr, bdir, bdm, bpos)) {
-          bstr = os;
-          bdir = od;
-          bdm = om;
-          bpos = op;
-        }
-      }
-      if (bstr >= 0) {
-        cd = bdir;
-        cut = bpos;
-      }
-    }
-    __syncwarp();
   }
-  if (cd < 0) {
-    cd = longest;
-    cut = (b.lo[cd] + b.hi[cd]) / 2;
+  br_sync(G);
+  // ---- candidate cuts of this thread: per direction the hole nearest the middle
+  // (lower index on ties); the strongest inflection (then lower direction, cut
+  // nearer the middle, lower position)
+  int bd[3] = {INT_MAX, INT_MAX, INT_MAX}, bs[3] = {INT_MAX, INT_MAX, INT_MAX};
+  long long bstr = -1;
+  int bdir = INT_MAX, bdm = INT_MAX, bpos = INT_MAX;
+  if (search) {
+    for (int d = 0; d < D; d++) {
+      const int mid2 = b.lo[d] + b.hi[d];
+      const int *S = sigs + d * maxside;
+      for (int sidx = 1 + tg; sidx + 1 < ext[d]; sidx += GT) {
+        if (S[sidx] != 0) continue;
+        const int s = b.lo[d] + sidx, dist = abs(2 * s - mid2);
+        if (dist < bd[d] || (dist == bd[d] && s < bs[d])) {
+          bd[d] = dist;
+          bs[d] = s;
+        }
+      }
+      const int n = ext[d];
+      if (n < 4) continue;
+      for (int sidx = 1 + tg; sidx + 2 < n; sidx += GT) {
+        long long l1 = (long long)S[sidx - 1] - 2LL * S[sidx] + S[sidx + 1];
+        long long l2 = (long long)S[sidx] - 2LL * S[sidx + 1] + S[sidx + 2];
+        if (!((l1 < 0 && l2 > 0) || (l1 > 0 && l2 < 0))) continue;
+        long long str = l2 - l1 < 0 ? l1 - l2 : l2 - l1;
+        int pos = b.lo[d] + sidx, dm = abs(2 * pos + 1 - mid2);
+        if (br_better(str, d, dm, pos, bstr, bdir, bdm, bpos)) {
+          bstr = str;
+          bdir = d;
+          bdm = dm;
+          bpos = pos;
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int d = 0; d < 3; d++) {
+      const int od = __shfl_xor_sync(0xffffffffu, bd[d], o), os = __shfl_xor_sync(0xffffffffu, bs[d], o);
+      if (od < bd[d] || (od == bd[d] && os < bs[d])) {
+        bd[d] = od;
+        bs[d] = os;
+      }
+    }
+    const long long ostr = __shfl_xor_sync(0xffffffffu, bstr, o);
+    const int odir = __shfl_xor_sync(0xffffffffu, bdir, o), odm = __shfl_xor_sync(0xffffffffu, bdm, o),
+              opos = __shfl_xor_sync(0xffffffffu, bpos, o);
+    if (br_better(ostr, odir, odm, opos, bstr, bdir, bdm, bpos)) {
+      bstr = ostr;
+      bdir = odir;
+      bdm = odm;
+      bpos = opos;
+    }
   }
   if (lane == 0) {
+    for (int d = 0; d < 3; d++) {
+      sh.hd[warp][d] = bd[d];
+      sh.hs[warp][d] = bs[d];
+    }
+    sh.istr[warp] = bstr;
+    sh.idir[warp] = bdir;
+    sh.idm[warp] = bdm;
+    sh.ipos[warp] = bpos;
+  }
+  br_sync(G);
+  if (split && tg == 0) {
+    int cd = -1, cut = 0;
+    if (search) {
+      // holes: the first direction with one
+      for (int d = 0; d < D && cd < 0; d++) {
+        int hd = INT_MAX, hs = INT_MAX;
+        for (int w = gw0; w < gw0 + G; w++)
+          if (sh.hd[w][d] < hd || (sh.hd[w][d] == hd && sh.hs[w][d] < hs)) {
+            hd = sh.hd[w][d];
+            hs = sh.hs[w][d];
+          }
+        if (hs != INT_MAX) {
+          cd = d;
+          cut = hs;
+        }
+      }
+      if (cd < 0) {
+        long long s1 = -1;
+        int d1 = INT_MAX, m1 = INT_MAX, p1 = INT_MAX;
+        for (int w = gw0; w < gw0 + G; w++)
+          if (br_better(sh.istr[w], sh.idir[w], sh.idm[w], sh.ipos[w], s1, d1, m1, p1)) {
+            s1 = sh.istr[w];
+            d1 = sh.idir[w];
+            m1 = sh.idm[w];
+            p1 = sh.ipos[w];
+          }
+        if (s1 >= 0) {
+          cd = d1;
+          cut = p1;
+        }
+      }
+    }
+    if (cd < 0) {
+      cd = longest;
+      cut = (b.lo[cd] + b.hi[cd]) / 2;
+    }
     BrBox a = b, c = b;
     a.hi[cd] = cut;
     c.lo[cd] = cut + 1;
@@ -690,6 +766,7 @@ __device__ void br_warp_box(const Geo &g, int l, const uint8_t *F, uint8_t *sig,
       set_err(g, EB_TREE);  // cannot happen: live boxes are disjoint and each holds a flag
     }
   }
+  br_sync(G);
 }
 
 // boxes: per level 2 lists of cap_l boxes (cap_l = blocks of the level), at
@@ -708,10 +785,10 @@ __global__ void __launch_bounds__(kBrThreads) k_br(Geo g, const uint8_t *gflag, 
     __syncthreads();
     F = sflags;
   }
+  __shared__ BrShared sh;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int cap = (int)(g.mapoff[l + 1] - g.mapoff[l]);
   BrBox *A = boxes + 2 * g.mapoff[l], *B = A + cap;
-  int *wsig = sigs + ((long long)l * nwarps + warp) * 3 * maxside;
   if (threadIdx.x == 0) {
     BrBox w;
     for (int d = 0; d < 3; d++) {
@@ -726,7 +803,19 @@ __global__ void __launch_bounds__(kBrThreads) k_br(Geo g, const uint8_t *gflag, 
   for (; round < kBrMaxRounds && ncur > 0; round++) {
     if (threadIdx.x == 0) nnext = 0;
     __syncthreads();
-    for (int i = warp; i < ncur; i += nwarps) br_warp_box(g, l, F, sig, eta, A[i], B, &nnext, cap, wsig, maxside);
+    // groups of G warps per box while there are fewer boxes than warps (G a power
+    // of two dividing the warp count), one warp per box after that
+    const int n = ncur;
+    int G = 1;
+    while (2 * G <= nwarps && 2 * G * n <= nwarps) G *= 2;
+    const int ngroups = nwarps / G, gid = warp / G, gw0 = gid * G, tg = threadIdx.x - 32 * gw0;
+    int *gsig = sigs + ((long long)l * nwarps + gw0) * 3 * maxside;
+    const int iters = (n + ngroups - 1) / ngroups;
+    for (int it = 0; it < iters; it++) {
+      const int i = gid + it * ngroups;
+      const bool active = i < n;
+      br_group_box(g, l, F, sig, eta, A[active ? i : 0], active, gw0, G, tg, B, &nnext, cap, gsig, maxside, sh);
+    }
     __syncthreads();
     BrBox *t = A;
     A = B;
