@@ -169,11 +169,10 @@ def uniform_roofline(m, torch, hbm_peak, steps=6, scheme="muscl_rk2"):
 
 
 # DRAM bytes (read + write) per stage launch measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum, -k regex:k_fvs -s 60 -c 4 on the
-# default command: stage-1 and stage-2 launches of the timed graph steps,
-# averaged); the writes stay in L2 within the launch.  Re-measure when the
-# kernel changes.
-MEASURED_TRAFFIC = {(WORKLOAD, "k_fvs (staged)"): (2453760 + 3950080 + 2450432 + 3949056) / 4.0}
+# (dram__bytes_read.sum + dram__bytes_write.sum, -k regex:k_fvs -s 150 -c 6 on the
+# default command: stage-1 and stage-2 launches of the roofline pass, averaged);
+# the writes stay in L2 within the launch.  Re-measure when the kernel changes.
+MEASURED_TRAFFIC = {(WORKLOAD, "k_fvs (staged)"): (2449408 + 3944192 + 2447360 + 3944704 + 2448128 + 3945984) / 6.0}
 
 STAGE_KERNELS = ((1, "k_fv (pencil)"), (2, "k_fvs (staged)"), (4, "k_fv (pencil, two threads per line)"),
                  (8, "k_fvp (pencil on staged primitives)"), (16, "k_fvs (staged MUSCL-Hancock)"))
