@@ -169,10 +169,14 @@ def uniform_roofline(m, torch, hbm_peak, steps=6, scheme="muscl_rk2"):
 
 
 # DRAM bytes (read + write) per stage launch measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum, -k regex:k_fvs -s 150 -c 6 on the
-# default command: stage-1 and stage-2 launches of the roofline pass, averaged);
-# the writes stay in L2 within the launch.  Re-measure when the kernel changes.
-MEASURED_TRAFFIC = {(WORKLOAD, "k_fvs (staged)"): (2449408 + 3944192 + 2447360 + 3944704 + 2448128 + 3945984) / 6.0}
+# (dram__bytes_read.sum + dram__bytes_write.sum on the default command, -s 150
+# -c 6 with -k regex:'^k_fv$' or regex:k_fvs: stage-1 and stage-2 launches of the
+# roofline pass, averaged); the writes stay in L2 within the launch.
+# Re-measure when the kernel changes.
+MEASURED_TRAFFIC = {
+    (WORKLOAD, "k_fv (pencil)"): (3929600 + 6949632 + 4017920 + 7129088 + 4108544 + 7308032) / 6.0,
+    (WORKLOAD, "k_fvs (staged)"): (2449408 + 3944192 + 2447360 + 3944704 + 2448128 + 3945984) / 6.0,
+}
 
 STAGE_KERNELS = ((1, "k_fv (pencil)"), (2, "k_fvs (staged)"), (4, "k_fv (pencil, two threads per line)"),
                  (8, "k_fvp (pencil on staged primitives)"), (16, "k_fvs (staged MUSCL-Hancock)"))

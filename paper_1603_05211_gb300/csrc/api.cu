@@ -23,16 +23,19 @@ using namespace mrfv;
 constexpr int kGridCtasPerSm = 8;
 constexpr int kBlockCtasPerSm = 16;
 // Below these leaf counts the MR-scheme stage runs in the staged (thread per
-// face) kernel.  Measured on GB300 (FP32, uniform grids): staged 11.7 vs pencil
-// 13.0 us at 1024 2D blocks, 22.9 vs 19.7 us at 4096; in 3D the pencil kernel
-// is faster from 512 blocks up (21 vs 34 us), so 3D always takes it.
-constexpr long long kStagedBelow2D = 2048;
+// face) kernel.  Measured on GB300 (FP32): per launch on uniform grids staged
+// 11.7 vs pencil 13.0 us at 1024 2D blocks, 22.9 vs 19.7 us at 4096; but inside
+// the adaptive 2D step (1400-3000 leaf blocks, the graph keeps the kernel of its
+// capture) the pencil kernel gives the shortest step (0.152 ms against 0.157
+// staged and 0.156 with two threads per line); in 3D the pencil kernel is
+// faster from 512 blocks up (21 vs 34 us).  So both take the pencil kernel.
+constexpr long long kStagedBelow2D = 0;
 constexpr long long kStagedBelow3D = 0;
 // Below these the pencil kernel runs with two threads per line (each half a
 // line).  Measured (FP32 uniform, one / two threads per line): 2D 4096 blocks
 // 19.9 / 16.8 us, 16384 blocks 36.4 / 36.1 us, 65536 blocks 123 / 140 us; 3D 512
 // blocks 21.1 / 22.9 us.
-constexpr long long kSplitBelow2D = 8192;
+constexpr long long kSplitBelow2D = 0;
 constexpr long long kSplitBelow3D = 0;
 // From these leaf counts on, the pencil kernel reads primitives staged in shared
 // memory (set from measurement; at or above the largest count: never).
