@@ -17,8 +17,9 @@
 // HANCOCK = false: one stage of the MR scheme (van Albada MUSCL, AUSM+, stage
 // of the explicit midpoint rule), the same arithmetic as the pencil kernel k_fv
 // in the same order.  It trades the pencil kernel's reuse of primitives and
-// slopes along a line for many more threads with short dependency chains, which
-// wins when the hierarchy has few leaves (the launch is latency-bound).
+// slopes along a line for many more threads with short dependency chains; a
+// single launch on a few thousand blocks is faster than the pencil kernel's, but
+// the adaptive step as a whole is not, so it is a selectable alternative.
 //
 // A CTA takes BPC blocks.  Phase 1 stages primitives of the interior, the two
 // face-halo layers (and for HANCOCK the halo edges) in a 12^d tile; phase 2
