@@ -80,6 +80,9 @@ def _load():
             "orc_set_scheme": (I, [P, I]),
             "orc_set_clustering": (I, [P, I]),
             "orc_set_eps_p": (I, [P, D]),
+            "orc_set_eps_r": (I, [P, D]),
+            "orc_rich_bad": (L, [P]),
+            "orc_rich_tau": (L, [P, I, D, dp]),
             "orc_set_lts_remesh": (I, [P, I, I, D, D, D, I]),
             "orc_br_cluster": (None, [P, I, u8, D, u8]),
             "orc_predict": (D, [P, I, dp, I, I, I, I]),
@@ -121,6 +124,7 @@ class Oracle:
         if lib.orc_set_clustering(self._h, clustering) != 0:
             raise ValueError("oracle: bad clustering")
         self.dim, self.levels, self.L, self.nv = dim, levels, levels - 1, dim + 2
+        self.bc = bc
         self.base_blocks = tuple(int(b) for b in (list(base_blocks) + [1, 1, 1])[:3])
         self.lo = tuple(float(x) for x in (list(lo) + [0.0] * 3)[:3])
         self.hi = tuple(float(x) for x in (list(hi) + [1.0] * 3)[:3])
@@ -201,22 +205,37 @@ class Oracle:
         return n.value
 
     def adapt(self, criterion: int = CRIT_MR, eps: float = 1e-3, eps_w: float = 0.05,
-              eta_tol: float = 0.8, precision: int = 0, eps_p: float = 0.0) -> None:
-        """eps_p > 0: the gradient criterion also tests pressure against eps_p."""
-        if self.lib.orc_set_eps_p(self._h, eps_p) != 0:
-            raise ValueError("oracle: bad eps_p")
+              eta_tol: float = 0.8, precision: int = 0, eps_p: float = 0.0, eps_r: float = 0.0) -> None:
+        """eps_p > 0: the gradient criterion also tests pressure against eps_p;
+        eps_r > 0: it also flags by the Richardson estimate of density."""
+        if self.lib.orc_set_eps_p(self._h, eps_p) != 0 or self.lib.orc_set_eps_r(self._h, eps_r) != 0:
+            raise ValueError("oracle: bad eps_p / eps_r")
         self.lib.orc_adapt(self._h, criterion, eps, eps_w, eta_tol, precision)
 
     def set_lts_remesh(self, on: bool = True, eps_w: float = 0.05, eta_tol: float = 0.8,
                        eps_p: float = 0.0, criterion: int = CRIT_GRAD, eps: float = 1e-3,
-                       precision: int = 0) -> None:
+                       precision: int = 0, eps_r: float = 0.0) -> None:
         """Remesh the finer levels inside the level recursion (Fig. 2) when stepping
-        with level-dependent steps, with the gradient (eps_w, eta_tol, eps_p) or
+        with level-dependent steps, with the gradient (eps_w, eta_tol, eps_p, eps_r) or
         the MR criterion (eps, decided in single precision with precision 1)."""
-        if self.lib.orc_set_eps_p(self._h, eps_p) != 0 or \
+        if self.lib.orc_set_eps_p(self._h, eps_p) != 0 or self.lib.orc_set_eps_r(self._h, eps_r) != 0 or \
                 self.lib.orc_set_lts_remesh(self._h, int(bool(on)), criterion, eps, eps_w, eta_tol,
                                             precision) != 0:
             raise ValueError("oracle: bad remesh parameters")
+
+    def rich_tau(self, l: int, dt: float):
+        """Richardson estimate of density of level l with level step dt on the
+        current state: (tau on the level's grid coarsened by 2, numpy order, and
+        the number of non-finite estimates on coarse cells of existing blocks)."""
+        shape = tuple(n // 2 for n in self.cells_shape(l))
+        tau = np.empty(shape, dtype=np.float64)
+        bad = self.lib.orc_rich_tau(self._h, l, dt, _dp(tau))
+        return tau, int(bad)
+
+    @property
+    def rich_bad(self) -> int:
+        """Richardson estimates on existing blocks that came out non-finite so far."""
+        return int(self.lib.orc_rich_bad(self._h))
 
     def totals(self) -> np.ndarray:
         out = np.zeros(5)

@@ -24,6 +24,7 @@
  *   - level-dependent time steps, time interpolation ....... Section 2.1 (MRLT), Section 2.2, Fig. 2
  *   - flux correction at refinement boundaries ............. Section 2.2, Fig. 2
  *   - scaled-gradient flags + one-cell buffer, clustering .. Section 2.2 (refinement indicators)
+ *   - Richardson estimate as an additional indicator ....... Section 2.2 (refinement indicators)
  *   - L1 error by projection to the finest level .......... Section 3
  * Readings where the paper is silent are stated beside the code that takes them.
  */
@@ -34,6 +35,7 @@
 
 #define OMAXL 12
 #define OB 8 /* cells per block edge */
+#define OG OMAXL /* geometry slot of the scratch grid */
 
 enum { O_BC_TRANSMISSIVE = 0, O_BC_PERIODIC = 1 };
 enum { O_CRIT_MR = 0, O_CRIT_GRAD = 1 };
@@ -52,12 +54,18 @@ typedef struct {
                          with this criterion and these parameters */
   int rm_crit, rm_precision;
   double rm_eps, rm_epsw, rm_eta;
+  double eps_r;       /* > 0: the gradient criterion also flags by the Richardson estimate (Section 2.2) */
+  double rich_dt;     /* step of the last orc_step (finest-level step when rich_lts) */
+  int rich_lts;
+  long rich_bad;      /* Richardson estimates on existing blocks that came out non-finite */
   double gamma;
   double lo[3], hi[3];
-  int nb[OMAXL][3];   /* blocks per dimension (1 in unused dimensions) */
-  int n[OMAXL][3];    /* cells per dimension */
-  long ncell[OMAXL], nblk[OMAXL];
-  double dx[OMAXL][3];
+  /* geometry; entry OG (= OMAXL) describes a scratch grid (the level coarsened by 2
+     of the Richardson estimate) so that the level functions run on it too */
+  int nb[OMAXL + 1][3];   /* blocks per dimension (1 in unused dimensions) */
+  int n[OMAXL + 1][3];    /* cells per dimension */
+  long ncell[OMAXL + 1], nblk[OMAXL + 1];
+  double dx[OMAXL + 1][3];
   uint8_t *ex[OMAXL]; /* block exists */
   double *q[OMAXL];   /* state Q^n, [v][cell] */
   double *qs[OMAXL];  /* RK stage state Q* */
@@ -947,6 +955,8 @@ static void advance_level(orc *o, int l, int sub, double dtL) {
 /* one time step: global (lts = 0, dt for every leaf) or one coarse step of
    the level recursion (lts = 1, dt = finest-level step) */
 void orc_step(orc *o, double dt, int lts) {
+  o->rich_dt = dt; /* the step the Richardson estimate of the next flags takes */
+  o->rich_lts = lts;
   if (lts) advance_level(o, 0, 0, dt);
   else step_global(o, dt);
 }
@@ -1113,6 +1123,132 @@ static int grad_flag_cell(const orc *o, int l, const double *E, int i, int j, in
   return 0;
 }
 
+
+/* ------------------------------------------------------------------------ */
+/* Richardson estimate (Section 2.2: the heuristic local error indicator AMROC
+   can add to the gradient flags; the estimate of Berger and Oliger 1984 and
+   Berger and Colella 1989).  Reading (the paper gives no formula): with H_dt
+   one step of the configured scheme over every cell of a uniform grid (the MR
+   scheme: both stages of the midpoint rule; the AMR scheme: its one stage), R
+   the mean of the 2^d children, E the level-l array the scheme sees and dt_l
+   the step of level l in the last time step,
+       tau = ( R H_dt(H_dt(E)) - H_2dt(R E) ) / (2^(o+1) - 2),   o = 2,
+   on the level-l grid coarsened by 2, which keeps the boundary rule.  Only the
+   density component is used. */
+
+/* one stage over every cell of the grid of geometry slot gl:
+   out = q0 - coef*dt * sum_n (F_{n,+} - F_{n,-}) / dx_n, directions in order */
+static void grid_stage(const orc *o, int gl, const double *E, const double *q0, double *out, double coef,
+                       double dt) {
+  long nc = o->ncell[gl];
+  double lam[3];
+  for (int d = 0; d < 3; d++) lam[d] = (coef * dt) / o->dx[gl][d];
+  for (int k = 0; k < o->n[gl][2]; k++)
+    for (int j = 0; j < o->n[gl][1]; j++)
+      for (int i = 0; i < o->n[gl][0]; i++) {
+        long c = cidx(o, gl, i, j, k);
+        double Fm[3][5], Fp[3][5];
+        for (int d = 0; d < o->dim; d++) {
+          int a[3] = {i, j, k};
+          a[d] -= 1;
+          face_flux(o, gl, E, d, a[0], a[1], a[2], dt, Fm[d]);
+          face_flux(o, gl, E, d, i, j, k, dt, Fp[d]);
+        }
+        for (int v = 0; v < o->nv; v++) {
+          double r = lam[0] * (Fp[0][v] - Fm[0][v]);
+          r = r + lam[1] * (Fp[1][v] - Fm[1][v]);
+          if (o->dim == 3) r = r + lam[2] * (Fp[2][v] - Fm[2][v]);
+          out[(long)v * nc + c] = q0[(long)v * nc + c] - r;
+        }
+      }
+}
+
+/* H_dt on the grid of slot gl */
+static void grid_scheme_step(const orc *o, int gl, const double *E, double *out, double dt) {
+  if (o->scheme == O_SCHEME_HANCOCK) {
+    grid_stage(o, gl, E, E, out, 1.0, dt);
+    return;
+  }
+  double *S = alloc_level(o, gl);
+  grid_stage(o, gl, E, E, S, 0.5, dt);
+  grid_stage(o, gl, S, E, out, 1.0, dt);
+  free(S);
+}
+
+/* tau (density) of level l on its grid coarsened by 2, which this sets up in the
+   scratch geometry slot OG; tau has ncell[OG] entries */
+static void rich_tau(orc *o, int l, const double *E, double dtl, double *tau) {
+  o->ncell[OG] = 1;
+  for (int d = 0; d < 3; d++) {
+    o->n[OG][d] = d < o->dim ? o->n[l][d] / 2 : 1;
+    o->nb[OG][d] = 0; /* no block structure */
+    o->dx[OG][d] = d < o->dim ? 2.0 * o->dx[l][d] : 1.0;
+    o->ncell[OG] *= o->n[OG][d];
+  }
+  long ncg = o->ncell[OG];
+  double *F1 = alloc_level(o, l), *F2 = alloc_level(o, l);
+  grid_scheme_step(o, l, E, F1, dtl);
+  grid_scheme_step(o, l, F1, F2, dtl);
+  double *RE = alloc_level(o, OG), *C1 = alloc_level(o, OG);
+  for (int k = 0; k < o->n[OG][2]; k++)
+    for (int j = 0; j < o->n[OG][1]; j++)
+      for (int i = 0; i < o->n[OG][0]; i++)
+        for (int v = 0; v < o->nv; v++) RE[(long)v * ncg + cidx(o, OG, i, j, k)] = project_cell(o, l, E, v, i, j, k);
+  grid_scheme_step(o, OG, RE, C1, 2.0 * dtl);
+  for (int k = 0; k < o->n[OG][2]; k++)
+    for (int j = 0; j < o->n[OG][1]; j++)
+      for (int i = 0; i < o->n[OG][0]; i++) {
+        long c = cidx(o, OG, i, j, k);
+        tau[c] = (project_cell(o, l, F2, 0, i, j, k) - C1[c]) / 6.0;
+      }
+  free(F1); free(F2); free(RE); free(C1);
+}
+
+/* coarse-cell flags |tau| > eps_r of the existing blocks of level l (OG set up by
+   rich_tau), the largest |tau| of each block into maxdet[l].  The estimate of a
+   block's coarse cells depends on E only within 8 fine cells of the block (two
+   fine steps of at most two stages, each reaching 2 cells; one coarse step, 2
+   coarse cells per stage); a block whose estimate is not finite, or whose E is
+   not finite there, is counted (the limiters turn some absent, NaN, values
+   into a zero slope, so the box is checked as well). */
+static uint8_t *rich_flags(orc *o, int l, const double *E, double dtl) {
+  long ncg = 1;
+  for (int d = 0; d < o->dim; d++) ncg *= o->n[l][d] / 2;
+  double *tau = (double *)malloc(sizeof(double) * (size_t)ncg);
+  rich_tau(o, l, E, dtl, tau);
+  uint8_t *rfl = (uint8_t *)calloc((size_t)ncg, 1);
+  int kz = o->dim == 3 ? OB / 2 : 1;
+  for (int bk = 0; bk < o->nb[l][2]; bk++)
+    for (int bj = 0; bj < o->nb[l][1]; bj++)
+      for (int bi = 0; bi < o->nb[l][0]; bi++) {
+        long b = bidx(o, l, bi, bj, bk);
+        if (!o->ex[l][b]) continue;
+        int bad = 0;
+        int z0 = o->dim == 3 ? bk * OB - OB : 0, z1 = o->dim == 3 ? bk * OB + 2 * OB : 1;
+        for (int k = z0; k < z1; k++)
+          for (int j = bj * OB - OB; j < bj * OB + 2 * OB; j++)
+            for (int i = bi * OB - OB; i < bi * OB + 2 * OB; i++) {
+              long c = cidx(o, l, bc_cell(o, l, 0, i), bc_cell(o, l, 1, j), bc_cell(o, l, 2, k));
+              for (int v = 0; v < o->nv; v++)
+                if (!isfinite(E[(long)v * o->ncell[l] + c])) bad = 1;
+            }
+        double m = 0.0;
+        for (int c = 0; c < kz; c++)
+          for (int bb = 0; bb < OB / 2; bb++)
+            for (int a = 0; a < OB / 2; a++) {
+              long q = cidx(o, OG, bi * (OB / 2) + a, bj * (OB / 2) + bb, o->dim == 3 ? bk * (OB / 2) + c : 0);
+              double t = fabs(tau[q]);
+              if (!isfinite(t)) bad = 1;
+              if (t > o->eps_r) rfl[q] = 1;
+              if (t > m) m = t;
+            }
+        o->maxdet[l][b] = m;
+        o->rich_bad += bad;
+      }
+  free(tau);
+  return rfl;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Berger-Rigoutsos clustering (Section 2.2, as in AMROC; Berger and Rigoutsos
    1991) of the flagged blocks fl of level l into boxes of blocks; every block of
@@ -1244,12 +1380,18 @@ static void br_cluster_level(orc *o, int l, const uint8_t *fl, double eta) {
    (th between its step's start and end), as its ghost cells are */
 static void grad_flags_range(orc *o, double epsw, double eta, int l0, double th) {
   int L = o->L, dim = o->dim;
-  for (int l = 0; l <= L; l++) { memset(o->sig[l], 0, (size_t)o->nblk[l]); }
+  for (int l = 0; l <= L; l++) {
+    memset(o->sig[l], 0, (size_t)o->nblk[l]);
+    memset(o->maxdet[l], 0, sizeof(double) * (size_t)o->nblk[l]);
+  }
   for (int l = l0; l < L; l++) {
     double *C = NULL;
     if (l > 0) C = (l == l0 && th >= 0.0) ? time_interp(o, l - 1, th) : o->q[l - 1];
     double *E = build_ext(o, l, o->q[l], C);
     if (C && C != o->q[l - 1]) free(C);
+    /* Richardson flags of level l (coarse cells of its grid coarsened by 2) */
+    uint8_t *rfl = NULL;
+    if (o->eps_r > 0.0) rfl = rich_flags(o, l, E, o->rich_lts ? ldexp(o->rich_dt, L - l) : o->rich_dt);
     uint8_t *fl = (uint8_t *)calloc((size_t)o->nblk[l], 1);
     for (int bk = 0; bk < o->nb[l][2]; bk++)
       for (int bj = 0; bj < o->nb[l][1]; bj++)
@@ -1267,9 +1409,11 @@ static void grad_flags_range(orc *o, double epsw, double eta, int l0, double th)
                   }
                 }
                 if (ok && grad_flag_cell(o, l, E, id[0], id[1], id[2], epsw)) hit = 1;
+                if (ok && rfl && rfl[cidx(o, OG, id[0] >> 1, id[1] >> 1, id[2] >> 1)]) hit = 1;
               }
           fl[bidx(o, l, bi, bj, bk)] = (uint8_t)hit;
         }
+    free(rfl);
     if (o->clustering == O_CLUSTER_BR) {
       br_cluster_level(o, l, fl, eta);
       free(fl);
@@ -1587,6 +1731,32 @@ int orc_set_lts_remesh(orc *o, int on, int crit, double eps, double epsw, double
   o->rm_eta = eta;
   o->rm_precision = precision;
   return 0;
+}
+
+/* Richardson threshold added to the gradient criterion (0: off) */
+int orc_set_eps_r(orc *o, double eps_r) {
+  if (!(eps_r >= 0.0)) return -1;
+  o->eps_r = eps_r;
+  return 0;
+}
+long orc_rich_bad(const orc *o) { return o->rich_bad; }
+
+/* Richardson estimate of density of level l with level step dt on the current
+   state (absent cells predicted from level l-1): tau on the level's grid
+   coarsened by 2 ([cell] layout, n_l/2 cells per dimension); returns the number
+   of coarse cells of existing blocks whose estimate is not finite */
+long orc_rich_tau(orc *o, int l, double dt, double *tau) {
+  if (l < 0 || l > o->L) return -1;
+  double *E = build_ext(o, l, o->q[l], l > 0 ? o->q[l - 1] : NULL);
+  rich_tau(o, l, E, dt, tau);
+  free(E);
+  long bad = 0;
+  int kz = o->dim == 3 ? o->n[OG][2] : 1;
+  for (int k = 0; k < kz; k++)
+    for (int j = 0; j < o->n[OG][1]; j++)
+      for (int i = 0; i < o->n[OG][0]; i++)
+        if (cell_block_exists(o, l, 2 * i, 2 * j, 2 * k) && !isfinite(tau[cidx(o, OG, i, j, k)])) bad++;
+  return bad;
 }
 
 /* pressure threshold of the gradient criterion (0: density only) */
