@@ -116,6 +116,14 @@ typedef struct {
                            sub-step of every level l >= 1 inside the level recursion (Remesh(l) of Fig. 2,
                            with the configured criterion on data at one time; the MR criterion uses its
                            safety zone there, not the proposer); 0 adapts once per coarse step */
+  double eps_r;         /* gradient criterion: > 0 also flags by the Richardson estimate (Section 2.2: the local
+                           error indicator AMROC can add; Berger-Oliger 1984, Berger-Colella 1989):
+                           tau = (R H_dt(H_dt(E)) - H_2dt(R E)) / 6 on each level l < L coarsened by 2, H one
+                           step of the configured scheme over the level's uniform grid (absent cells predicted),
+                           R the mean of the 2^d children, dt the level's step in the last time step (zero
+                           before the first step); a block is flagged when |tau| of density exceeds eps_r on
+                           a coarse cell of an existing block within one fine cell of it.  0 (default): off.
+                           With the MR criterion it must be 0. */
 } mrfv_config;
 
 typedef struct {
@@ -234,7 +242,9 @@ int mrfv_set_tree(mrfv_ctx *ctx, const uint8_t *exist_all, int64_t n);
 
 /* Last analysis of level l: flags[b] = 1 when block b was significant (MR) or
    flagged for refinement (GRAD); maxdet[b] (may be NULL) = its largest
-   normalised detail, in the state precision widened to double. */
+   normalised detail (MR) or, with eps_r > 0, its largest |tau| of the Richardson
+   estimate (GRAD, levels below the finest), in the state precision widened to
+   double. */
 int mrfv_get_flags(mrfv_ctx *ctx, int level, uint8_t *flags, double *maxdet, int64_t n);
 
 /* Wait for all work issued on the context's stream. */

@@ -46,6 +46,7 @@ class Config(ctypes.Structure):
         ("stream", ctypes.c_void_p), ("device_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
         ("use_graph", ctypes.c_int), ("proposer", ctypes.c_int), ("scheme", ctypes.c_int),
         ("clustering", ctypes.c_int), ("eps_p", ctypes.c_double), ("lts_remesh", ctypes.c_int),
+        ("eps_r", ctypes.c_double),
     ]
 
 
@@ -152,7 +153,7 @@ class Solver:
                  hi=(1.0, 1.0, 1.0), bc=BC_TRANSMISSIVE, gamma=1.4, cfl=0.5, t_end=0.0, adapt=False,
                  criterion="mr", eps=1e-3, eps_w=0.05, eta_tol=0.8, lts=False, pool_blocks=0, stream=None,
                  use_graph=True, proposer=False, scheme="muscl_rk2", clustering="rows", eps_p=0.0,
-                 lts_remesh=True):
+                 lts_remesh=True, eps_r=0.0):
         import torch
 
         if not torch.cuda.is_available():
@@ -175,6 +176,7 @@ class Solver:
         cfg.criterion = CRIT_GRAD if str(criterion).lower() in ("grad", "1") else CRIT_MR
         cfg.eps, cfg.eps_w, cfg.eta_tol, cfg.eps_p = eps, eps_w, eta_tol, eps_p
         cfg.lts_remesh = int(bool(lts_remesh))
+        cfg.eps_r = float(eps_r)
         cfg.lts = int(bool(lts))
         cfg.pool_blocks = int(pool_blocks)
         cfg.use_graph = int(bool(use_graph))

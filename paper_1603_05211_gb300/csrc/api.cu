@@ -104,7 +104,19 @@ struct mrfv_ctx {
   void *brscratch;      // Berger-Rigoutsos boxes and signatures
   unsigned *rctl;       // [3]: CTAs done of the scale reduction
   int br_maxside;       // longest side, in blocks, of the levels that are clustered
+  unsigned long long *rmask;  // Richardson: per block position, the coarse cells with |tau| > eps_r
+  void *rscratch;       // Richardson: the patches of each CTA
+  int rich_ctas;        // CTAs of the Richardson estimate (0: off)
 };
+
+// CTAs of the Richardson estimate: a few per SM of a 152-SM part, at most one per
+// block below the finest level (each CTA holds its own scratch)
+int rich_ctas_of(const mrfv_config *cfg, const Geo &g) {
+  if (!(cfg->eps_r > 0.0) || g.L < 1) return 0;
+  long long n = g.mapoff[g.L];
+  long long want = cfg->dim == 2 ? 608 : 152;
+  return (int)(n < want ? n : want);
+}
 
 static thread_local std::string g_create_error;
 
@@ -225,6 +237,11 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     for (int d = 0; d < g.dim; d++) maxside = g.nb[g.L - 1][d] > maxside ? g.nb[g.L - 1][d] : maxside;
   size_t obr = L.take(br_scratch_bytes(g, maptotal, maxside));
   size_t orctl = L.take(4 * 4);
+  const int rctas = rich_ctas_of(cfg, g);
+  size_t ormask = L.take(rctas ? maptotal * 8 : 0);
+  size_t orscr = L.take(rctas ? (size_t)rctas * (size_t)(cfg->precision == MRFV_FP32 ? rich_scratch_bytes<float>(g.dim)
+                                                                                  : rich_scratch_bytes<double>(g.dim))
+                              : 0);
   if (c) {
     c->br_maxside = maxside;
     char *a = c->arena;
@@ -263,6 +280,9 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->ploss = (double *)(a + oploss);
     c->brscratch = a + obr;
     c->rctl = (unsigned *)(a + orctl);
+    c->rich_ctas = rctas;
+    c->rmask = rctas ? (unsigned long long *)(a + ormask) : nullptr;
+    c->rscratch = rctas ? (void *)(a + orscr) : nullptr;
   }
   return L.off + 256;
 }
@@ -545,6 +565,11 @@ struct Seq {
       cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
     }
     launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, 0, (const T *)nullptr, 0.0, c->bgrid, c->st);
+    if (c->rich_ctas) {
+      launch_rich<T>(c->g, c->cfg.scheme, U(), (const T *)nullptr, 0.0, 0, c->lev, c->cfg.eps_r, c->rmask, c->maxdet,
+                     c->gflag, (T *)c->rscratch, c->rich_ctas, c->grid, c->st);
+      c->nlaunch += 2;
+    }
     if (c->cfg.clustering == MRFV_CLUSTER_BR)
       launch_br(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
     else
@@ -581,6 +606,11 @@ void Seq<T>::remesh(int l0) {
   launch_remesh_begin(g, c->maptotal, c->sig, c->gflag, c->need, c->nnew, l0, c->grid, c->st);
   if (c->cfg.criterion == MRFV_CRIT_GRAD) {
     launch_gradflags<T>(g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, l0, U0(), 0.5, c->bgrid, c->st);
+    if (c->rich_ctas) {
+      launch_rich<T>(g, c->cfg.scheme, U(), U0(), 0.5, l0, c->lev, c->cfg.eps_r, c->rmask, c->maxdet, c->gflag,
+                     (T *)c->rscratch, c->rich_ctas, c->grid, c->st);
+      c->nlaunch += 2;
+    }
     if (c->cfg.clustering == MRFV_CLUSTER_BR)
       launch_br(g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
     else
@@ -730,6 +760,9 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   if (cfg->clustering != MRFV_CLUSTER_ROWS && cfg->clustering != MRFV_CLUSTER_BR)
     return fail(nullptr, MRFV_ERR_ARG, "clustering");
   if (!(cfg->eps_p >= 0.0)) return fail(nullptr, MRFV_ERR_ARG, "eps_p");
+  if (!(cfg->eps_r >= 0.0) || !(cfg->eps_r < INFINITY)) return fail(nullptr, MRFV_ERR_ARG, "eps_r");
+  if (cfg->eps_r > 0.0 && cfg->criterion != MRFV_CRIT_GRAD)
+    return fail(nullptr, MRFV_ERR_ARG, "eps_r: the Richardson estimate adds to the gradient criterion");
   if (cfg->lts_remesh != 0 && cfg->lts_remesh != 1) return fail(nullptr, MRFV_ERR_ARG, "lts_remesh");
   {
     Geo gg;
@@ -819,6 +852,10 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   cudaMemsetAsync(c->red, 0, 4 * 8, c->st);
   cudaMemsetAsync(c->red + 3, 0x7f, 8, c->st);  // the CFL minimum's start value, a huge positive double
   cudaMemsetAsync(c->done, 0, 4, c->st);
+  // step table zero until the first step (the Richardson estimate of an adaptation
+  // before any step is then zero)
+  cudaMemsetAsync(c->lev, 0, 2 * MAXL * 4 * 8, c->st);
+  cudaMemsetAsync(c->levf, 0, 2 * MAXL * 4 * 4, c->st);
   launch_init_freestack(c->freestack, c->freetop, c->g.cap, c->grid, c->st);
   if (cfg->use_graph && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) c->cap_st = nullptr;
   if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess) c->st2 = nullptr;

@@ -4,6 +4,7 @@
 #pragma once
 #include "launch.h"
 #include "mr.cuh"
+#include "rich.cuh"
 
 namespace mrfv {
 
@@ -82,6 +83,26 @@ void launch_gradflags(const Geo &g, const T *A, double epsw, double epsp, uint8_
 }
 
 template <typename T>
+void launch_rich(const Geo &g, int hancock, const T *A, const T *A0, double theta, int l0, const double *lev,
+                 double eps_r, unsigned long long *rmask, double *maxdet, uint8_t *gflag, T *scratch, int ctas,
+                 int grid, cudaStream_t st) {
+  const T th = T(theta);
+  if (g.dim == 2) {
+    if (hancock) k_rich<T, 2, true><<<ctas, RichShape<2>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch);
+    else k_rich<T, 2, false><<<ctas, RichShape<2>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch);
+    k_rich_flags<2><<<grid, 256, 0, st>>>(g, l0, rmask, gflag);
+  } else {
+    if (hancock) k_rich<T, 3, true><<<ctas, RichShape<3>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch);
+    else k_rich<T, 3, false><<<ctas, RichShape<3>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch);
+    k_rich_flags<3><<<grid, 256, 0, st>>>(g, l0, rmask, gflag);
+  }
+}
+template <typename T>
+long long rich_scratch_bytes(int dim) {
+  return (dim == 2 ? RichShape<2>::PER : RichShape<3>::PER) * (long long)sizeof(T);
+}
+
+template <typename T>
 void launch_project_level(const Geo &g, int l, const T *A, const double *coarse, double *out, cudaStream_t st) {
   if (g.dim == 2) k_project_level<T, 2><<<1024, 256, 0, st>>>(g, l, A, coarse, out);
   else k_project_level<T, 3><<<1024, 256, 0, st>>>(g, l, A, coarse, out);
@@ -103,6 +124,9 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
   template void launch_copy_level<T>(const Geo &, int, int, int, const T *, T *, int, cudaStream_t);                  \
   template void launch_gradflags<T>(const Geo &, const T *, double, double, uint8_t *, int, const T *, double, int, \
                                     cudaStream_t);         \
-  template void launch_project_level<T>(const Geo &, int, const T *, const double *, double *, cudaStream_t);
+  template void launch_project_level<T>(const Geo &, int, const T *, const double *, double *, cudaStream_t); \
+  template void launch_rich<T>(const Geo &, int, const T *, const T *, double, int, const double *, double,     \
+                               unsigned long long *, double *, uint8_t *, T *, int, int, cudaStream_t);        \
+  template long long rich_scratch_bytes<T>(int);
 
 }  // namespace mrfv

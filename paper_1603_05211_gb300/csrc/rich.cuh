@@ -1,0 +1,437 @@
+// Richardson error estimate, the local error indicator the AMR code of
+// arXiv:1603.05211 Section 2.2 can add to its scaled-gradient flags (the estimate
+// of Berger and Oliger 1984 and Berger and Colella 1989).  On level l, with H_dt
+// one step of the configured scheme over a uniform grid and R the mean of the
+// 2^d children:
+//     tau = (R H_dt(H_dt(E)) - H_2dt(R E)) / (2^(o+1) - 2),   o = 2,
+// on the level's grid coarsened by 2 (same boundary rule), density only; E is
+// the level as the scheme sees it (absent cells predicted from level l-1), dt the
+// level's step in the last time step.  A block is flagged when a coarse cell of
+// an existing block within one fine cell of it has |tau| > eps_r.
+//
+// One CTA per existing block of levels l0..L-1.  The estimate of the block's 4^d
+// coarse cells depends on E only within 8 fine cells of the block (each stage
+// reaches 2 cells; two fine steps, one coarse step), so the CTA gathers that
+// 24^d patch, restricts it to the 12^d coarse patch, runs the coarse step of 2 dt
+// and the two fine steps of dt, every stage on a region 2 cells narrower than its
+// input, and compares on the block.  Each stage converts its input to primitives
+// once, evaluates the numerical flux once per face of its region and applies the
+// update in the order of the cell update of the stage kernels.  At a
+// transmissive wall the reads are clamped to the domain, as the boundary rule
+// does.  Patches live in a per-CTA scratch area of global memory.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.h"
+#include "dev.cuh"
+#include "fv.cuh"
+#include "fvh.cuh"
+
+namespace mrfv {
+
+template <int D>
+struct RichShape {
+  static constexpr int NV = D + 2;
+  static constexpr int P = 24;    // fine patch edge: the block and 8 cells on each side
+  static constexpr int PC = 12;   // coarse patch edge
+  static constexpr int NP = (D == 2) ? P * P : P * P * P;
+  static constexpr int NPC = (D == 2) ? PC * PC : PC * PC * PC;
+  static constexpr int NFACE = (D == 2) ? (P + 1) * P : (P + 1) * P * P;  // faces of one direction
+  static constexpr int NT = 256;
+  // scratch values per CTA: A, S, W, DQ [NV][NP]; CA, CS [NV][NPC]; FL [D][NV][NFACE]
+  static constexpr long long PER = (long long)NV * (4 * NP + 2 * NPC) + (long long)D * NV * NFACE;
+};
+
+// A box [a, b) per dimension (unused dimensions [0, 1)) walked by the CTA's threads.
+struct RBox {
+  int a[3], b[3];
+  __device__ int count() const { return (b[0] - a[0]) * (b[1] - a[1]) * (b[2] - a[2]); }
+  __device__ void at(int q, int &x, int &y, int &z) const {
+    const int w0 = b[0] - a[0], w1 = b[1] - a[1];
+    x = a[0] + q % w0;
+    y = a[1] + (q / w0) % w1;
+    z = a[2] + q / (w0 * w1);
+  }
+};
+
+// One stage on a patch of edge E (buffers [NV][E^D]): out = q0 - sum_n lam_n (F_n(x + 1/2) - F_n(x - 1/2))
+// (directions summed in order) on the cells of `reg`, with the fluxes from the
+// stage input `in` on reg widened by 2.  dl/dh: the domain's cells of the patch
+// (reads outside are clamped into it; a periodic patch has none outside).
+// HANCOCK: the predictor advances the face states by dQ, h_m = (dt/2)/dx_m.
+template <typename T, int D, bool HANCOCK, int E>
+__device__ void rich_stage(const T *in, const T *q0, T *out, T *W, T *DQ, T *FL, const RBox &reg, const int *dl,
+                           const int *dh, const T *lam, const T *h, T gam, T gm1, T goverg1) {
+  using S = RichShape<D>;
+  constexpr int NV = S::NV, NFACE = S::NFACE, NT = S::NT;
+  constexpr int NS = (E == S::P) ? S::NP : S::NPC;  // values per variable of the patch buffers
+  auto cl = [&](int x, int d) { return x < dl[d] ? dl[d] : (x >= dh[d] ? dh[d] - 1 : x); };
+  auto pidx = [&](int x, int y, int z) { return x + E * (y + E * z); };
+  // primitives of the input on reg widened by 2, inside the domain
+  RBox wb;
+  for (int d = 0; d < 3; d++) {
+    wb.a[d] = d < D ? max(reg.a[d] - 2, dl[d]) : 0;
+    wb.b[d] = d < D ? min(reg.b[d] + 2, dh[d]) : 1;
+  }
+  for (int q = threadIdx.x; q < wb.count(); q += NT) {
+    int x, y, z;
+    wb.at(q, x, y, z);
+    const int p = pidx(x, y, z);
+    T Q[NV], w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) Q[v] = in[v * NS + p];
+    cons_to_prim<T, D>(Q, gm1, w);
+#pragma unroll
+    for (int v = 0; v < NV; v++) W[v * NS + p] = w[v];
+  }
+  __syncthreads();
+  if constexpr (HANCOCK) {
+    // half-step increment of every cell a face of reg touches (the ring of ghost
+    // cells at a wall included: their slopes come from clamped neighbours)
+    RBox qb;
+    for (int d = 0; d < 3; d++) {
+      qb.a[d] = d < D ? max(reg.a[d] - 1, dl[d] - 1) : 0;
+      qb.b[d] = d < D ? min(reg.b[d] + 1, dh[d] + 1) : 1;
+    }
+    for (int q = threadIdx.x; q < qb.count(); q += NT) {
+      int c[3];
+      qb.at(q, c[0], c[1], c[2]);
+      const int pc = pidx(cl(c[0], 0), cl(c[1], 1), D == 3 ? cl(c[2], 2) : 0);
+      T w[NV], dQ[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) w[v] = W[v * NS + pc];
+#pragma unroll
+      for (int m = 0; m < D; m++) {
+        int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+        lo[m] -= 1;
+        hi[m] += 1;
+        const int pl = pidx(cl(lo[0], 0), cl(lo[1], 1), D == 3 ? cl(lo[2], 2) : 0);
+        const int ph = pidx(cl(hi[0], 0), cl(hi[1], 1), D == 3 ? cl(hi[2], 2) : 0);
+        T wm[NV], wp[NV], Qm[NV], Qp[NV], Fm[NV], Fp[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          T sl = minmod<T>(w[v] - W[v * NS + pl], W[v * NS + ph] - w[v]);
+          wm[v] = w[v] - (T(0.5) * sl);
+          wp[v] = w[v] + (T(0.5) * sl);
+        }
+        prim_to_cons<T, D>(wm, gm1, Qm);
+        prim_to_cons<T, D>(wp, gm1, Qp);
+        exact_flux<T, D>(m, wm, Qm, Fm);
+        exact_flux<T, D>(m, wp, Qp, Fp);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          T inc = h[m] * (Fm[v] - Fp[v]);
+          dQ[v] = (m == 0) ? inc : dQ[v] + inc;
+        }
+      }
+      const int p = pidx(c[0], c[1], c[2]);
+#pragma unroll
+      for (int v = 0; v < NV; v++) DQ[v * NS + p] = dQ[v];
+    }
+    __syncthreads();
+  }
+  // numerical flux of every face of reg, all directions (face f along n lies
+  // between cells f-1 and f; stored at f + (E+1) (t1 + E t2))
+#pragma unroll
+  for (int n = 0; n < D; n++) {
+    const int t1 = (n == 0) ? 1 : 0, t2 = (n == 2) ? 1 : 2;
+    RBox fb;
+    fb.a[0] = reg.a[n];
+    fb.b[0] = reg.b[n] + 1;
+    fb.a[1] = reg.a[t1];
+    fb.b[1] = reg.b[t1];
+    fb.a[2] = D == 3 ? reg.a[t2] : 0;
+    fb.b[2] = D == 3 ? reg.b[t2] : 1;
+    for (int q = threadIdx.x; q < fb.count(); q += NT) {
+      int f, u1, u2;
+      fb.at(q, f, u1, u2);
+      int c[3];
+      c[n] = f - 1;
+      c[t1] = u1;
+      if (D == 3) c[t2] = u2;
+      else c[2] = 0;
+      T wl[NV], wr[NV], F[NV];
+      if constexpr (!HANCOCK) {
+        int cc[3] = {c[0], c[1], c[2]};
+        int pk[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          cc[n] = c[n] + k - 1;  // cells f-2, f-1, f, f+1
+          pk[k] = pidx(cl(cc[0], 0), cl(cc[1], 1), D == 3 ? cl(cc[2], 2) : 0);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          T w0 = W[v * NS + pk[0]], wa = W[v * NS + pk[1]], wb2 = W[v * NS + pk[2]], w3 = W[v * NS + pk[3]];
+          T sa = van_albada<T>(wa - w0, wb2 - wa);
+          T sb = van_albada<T>(wb2 - wa, w3 - wb2);
+          wl[v] = lfma(T(0.5), sa, wa);
+          wr[v] = wb2 - T(0.5) * sb;
+        }
+        ausm_plus<T, D>(n, wl, wr, gam, goverg1, F);
+      } else {
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+          int a[3] = {c[0], c[1], c[2]};
+          a[n] += side;  // the face's left (side 0) or right cell, unclamped
+          int am[3] = {a[0], a[1], a[2]}, ap[3] = {a[0], a[1], a[2]};
+          am[n] -= 1;
+          ap[n] += 1;
+          const int p0 = pidx(cl(a[0], 0), cl(a[1], 1), D == 3 ? cl(a[2], 2) : 0);
+          const int pm = pidx(cl(am[0], 0), cl(am[1], 1), D == 3 ? cl(am[2], 2) : 0);
+          const int pp = pidx(cl(ap[0], 0), cl(ap[1], 1), D == 3 ? cl(ap[2], 2) : 0);
+          const int pd = pidx(a[0], a[1], a[2]);
+          T wq[NV], Qf[NV];
+#pragma unroll
+          for (int v = 0; v < NV; v++) {
+            T w0 = W[v * NS + p0];
+            T sl = minmod<T>(w0 - W[v * NS + pm], W[v * NS + pp] - w0);
+            wq[v] = side == 0 ? w0 + (T(0.5) * sl) : w0 - (T(0.5) * sl);
+          }
+          prim_to_cons<T, D>(wq, gm1, Qf);
+#pragma unroll
+          for (int v = 0; v < NV; v++) Qf[v] = Qf[v] + DQ[v * NS + pd];
+          if (side == 0) cons_to_prim<T, D>(Qf, gm1, wl);
+          else cons_to_prim<T, D>(Qf, gm1, wr);
+        }
+        ausmdv<T, D>(n, wl, wr, gam, goverg1, F);
+      }
+      const int fi = f + (E + 1) * (u1 + E * u2);
+#pragma unroll
+      for (int v = 0; v < NV; v++) FL[(n * NV + v) * NFACE + fi] = F[v];
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < reg.count(); q += NT) {
+    int x, y, z;
+    reg.at(q, x, y, z);
+    const int p = pidx(x, y, z);
+    const int f0 = x + (E + 1) * (y + E * z), f1 = y + (E + 1) * (x + E * z), f2 = z + (E + 1) * (x + E * y);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      T r = lam[0] * (FL[(0 * NV + v) * NFACE + f0 + 1] - FL[(0 * NV + v) * NFACE + f0]);
+      r = r + lam[1] * (FL[(1 * NV + v) * NFACE + f1 + 1] - FL[(1 * NV + v) * NFACE + f1]);
+      if (D == 3) r = r + lam[2] * (FL[(2 * NV + v) * NFACE + f2 + 1] - FL[(2 * NV + v) * NFACE + f2]);
+      out[v * NS + p] = q0[v * NS + p] - r;
+    }
+  }
+  __syncthreads();
+}
+
+// H_dt on a patch of edge E: the stages of one step, each on the region `lo`/`hi`
+// of its row (cells per dimension, clipped to the domain).  The result is in A
+// (RK2: both stages; the second writes A in place) or, for the one Hancock stage,
+// in `res`.
+template <typename T, int D, bool HANCOCK, int E>
+__device__ void rich_step(T *A, T *Sb, T *res, T *W, T *DQ, T *FL, int lo1, int hi1, int lo2, int hi2,
+                          const int *dl, const int *dh, double dt, const double *dx, T gam, T gm1, T goverg1) {
+  T lam1[3], lam2[3], hh[3];
+  for (int d = 0; d < 3; d++) {
+    lam1[d] = T((0.5 * dt) / dx[d]);
+    lam2[d] = T((1.0 * dt) / dx[d]);
+    hh[d] = T((0.5 * dt) / dx[d]);
+  }
+  auto box = [&](int lo, int hi) {
+    RBox b;
+    for (int d = 0; d < 3; d++) {
+      b.a[d] = d < D ? max(lo, dl[d]) : 0;
+      b.b[d] = d < D ? min(hi, dh[d]) : 1;
+    }
+    return b;
+  };
+  if constexpr (HANCOCK) {
+    rich_stage<T, D, true, E>(A, A, res, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1);
+  } else {
+    rich_stage<T, D, false, E>(A, A, Sb, W, DQ, FL, box(lo1, hi1), dl, dh, lam1, hh, gam, gm1, goverg1);
+    rich_stage<T, D, false, E>(Sb, A, A, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1);
+  }
+}
+
+// Per block: rmask = bit (x + 4 y + 16 z) set for each of its coarse cells with
+// |tau| > eps_r, maxdet = the largest |tau| of its coarse cells.  Levels l0..L-1;
+// with A0 set, the absent cells of level l0 are predicted from level l0-1
+// interpolated in time, A0 + theta (A - A0) (a remesh inside the level recursion).
+template <typename T, int D, bool HANCOCK>
+__global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__restrict__ A, const T *__restrict__ A0,
+                                                           T theta, int l0, const double *__restrict__ lev,
+                                                           double eps_r, unsigned long long *rmask, double *maxdet,
+                                                           T *scratch) {
+  using S = RichShape<D>;
+  constexpr int NV = S::NV, P = S::P, PC = S::PC, NP = S::NP, NPC = S::NPC, NT = S::NT;
+  constexpr int NC = (D == 2) ? 16 : 64;  // coarse cells of a block
+  __shared__ T cc[NC], tau[NC];
+  if (g.L < 1 || l0 > g.L - 1) return;
+  int b, e;
+  list_range(g, LK_EXIST, l0, g.L - 1, b, e);
+  const long long cap = g.cap;
+  T *Ab = scratch + (long long)blockIdx.x * S::PER;
+  T *Sb = Ab + NV * NP, *Wb = Sb + NV * NP, *DQb = Wb + NV * NP;
+  T *CA = DQb + NV * NP, *CS = CA + NV * NPC, *FL = CS + NV * NPC;
+  const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
+  for (int it = b + blockIdx.x; it < e; it += gridDim.x) {
+    const int s = g.lists[LK_EXIST * cap + it];
+    const int l = g.slot_level[s];
+    const int bc3[3] = {g.slot_coord[3 * s], g.slot_coord[3 * s + 1], g.slot_coord[3 * s + 2]};
+    const double dtl = lev[lev_index(1, l, 3)];
+    // the domain's cells of the fine and coarse patches (periodic: all)
+    int dl[3], dh[3], cdl[3], cdh[3];
+    for (int d = 0; d < 3; d++) {
+      if (d >= D) {
+        dl[d] = cdl[d] = 0;
+        dh[d] = cdh[d] = 1;
+      } else if (g.bc == 1) {
+        dl[d] = cdl[d] = 0;
+        dh[d] = P;
+        cdh[d] = PC;
+      } else {
+        const int og = 8 * bc3[d] - 8, N = g.nb[l][d] * 8;
+        dl[d] = max(0, -og);
+        dh[d] = min(P, N - og);
+        cdl[d] = max(0, -og / 2);
+        cdh[d] = min(PC, N / 2 - og / 2);
+      }
+    }
+    // gather E on the fine patch (domain cells only)
+    {
+      RBox gb;
+      for (int d = 0; d < 3; d++) {
+        gb.a[d] = dl[d];
+        gb.b[d] = dh[d];
+      }
+      const T *C0 = (l == l0) ? A0 : nullptr;
+      for (int q = threadIdx.x; q < gb.count(); q += NT) {
+        int x, y, z;
+        gb.at(q, x, y, z);
+        T Q[NV];
+        ext_cell<T, D>(g, l, 8 * bc3[0] - 8 + x, 8 * bc3[1] - 8 + y, D == 3 ? 8 * bc3[2] - 8 + z : 0, A, A, C0,
+                       theta, Q);
+        const int p = x + P * (y + P * z);
+#pragma unroll
+        for (int v = 0; v < NV; v++) Ab[v * NP + p] = Q[v];
+      }
+    }
+    __syncthreads();
+    // R E on the coarse patch: children summed in lexicographic order (x fastest)
+    {
+      RBox cb;
+      for (int d = 0; d < 3; d++) {
+        cb.a[d] = cdl[d];
+        cb.b[d] = cdh[d];
+      }
+      for (int q = threadIdx.x; q < cb.count(); q += NT) {
+        int x, y, z;
+        cb.at(q, x, y, z);
+        const int pc = x + PC * (y + PC * z);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          T sum = T(0);
+#pragma unroll
+          for (int k = 0; k < (D == 3 ? 8 : 4); k++) {
+            const int p = (2 * x + (k & 1)) + P * ((2 * y + ((k >> 1) & 1)) + P * (D == 3 ? 2 * z + (k >> 2) : 0));
+            const T val = Ab[v * NP + p];
+            sum = k == 0 ? val : sum + val;
+          }
+          CA[v * NPC + pc] = sum * T(D == 3 ? 0.125 : 0.25);
+        }
+      }
+    }
+    __syncthreads();
+    // coarse step of 2 dt (cells 2..10 then 4..8 of the coarse patch)
+    double dxc[3], dxf[3];
+    for (int d = 0; d < 3; d++) {
+      dxf[d] = g.dx[l][d];
+      dxc[d] = 2.0 * g.dx[l][d];
+    }
+    rich_step<T, D, HANCOCK, PC>(CA, CS, CS, Wb, DQb, FL, 2, 10, 4, 8, cdl, cdh, 2.0 * dtl, dxc, gam, gm1, goverg1);
+    const T *Cres = HANCOCK ? CS : CA;
+    for (int q = threadIdx.x; q < NC; q += NT) {
+      const int x = q & 3, y = (q >> 2) & 3, z = q >> 4;
+      cc[q] = Cres[(4 + x) + PC * ((4 + y) + PC * (D == 3 ? 4 + z : 0))];
+    }
+    // two fine steps of dt (regions 2..22, 4..20, 6..18, 8..16; Hancock 6..18, 8..16)
+    if constexpr (HANCOCK) {
+      rich_step<T, D, true, P>(Ab, Sb, Sb, Wb, DQb, FL, 0, 0, 6, 18, dl, dh, dtl, dxf, gam, gm1, goverg1);
+      rich_step<T, D, true, P>(Sb, Ab, Ab, Wb, DQb, FL, 0, 0, 8, 16, dl, dh, dtl, dxf, gam, gm1, goverg1);
+    } else {
+      rich_step<T, D, false, P>(Ab, Sb, Ab, Wb, DQb, FL, 2, 22, 4, 20, dl, dh, dtl, dxf, gam, gm1, goverg1);
+      rich_step<T, D, false, P>(Ab, Sb, Ab, Wb, DQb, FL, 6, 18, 8, 16, dl, dh, dtl, dxf, gam, gm1, goverg1);
+    }
+    // restrict the fine result on the block and compare
+    for (int q = threadIdx.x; q < NC; q += NT) {
+      const int x = q & 3, y = (q >> 2) & 3, z = q >> 4;
+      T sum = T(0);
+#pragma unroll
+      for (int k = 0; k < (D == 3 ? 8 : 4); k++) {
+        const int p = (8 + 2 * x + (k & 1)) + P * ((8 + 2 * y + ((k >> 1) & 1)) + P * (D == 3 ? 8 + 2 * z + (k >> 2) : 0));
+        const T val = Ab[p];
+        sum = k == 0 ? val : sum + val;
+      }
+      tau[q] = (sum * T(D == 3 ? 0.125 : 0.25) - cc[q]) / T(6);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long mask = 0;
+      double m = 0.0;
+      for (int q = 0; q < NC; q++) {
+        const T t = fabs(tau[q]);
+        if (t > T(eps_r)) mask |= 1ull << q;
+        if ((double)t > m) m = (double)t;
+      }
+      const long long mi = map_index(g, l, bc3[0], bc3[1], bc3[2]);
+      rmask[mi] = mask;
+      maxdet[mi] = m;
+    }
+    __syncthreads();
+  }
+}
+
+// Richardson block flags: a block of levels l0..L-1 is flagged (gflag |= 1) when
+// its own mask or the mask of an existing same-level neighbour has a coarse cell
+// within one fine cell of it (the neighbour's coarse layer next to the shared
+// face, edge or corner).
+template <int D>
+__global__ void k_rich_flags(Geo g, int l0, const unsigned long long *__restrict__ rmask, uint8_t *gflag) {
+  if (g.L < 1 || l0 > g.L - 1) return;
+  int b, e;
+  list_range(g, LK_EXIST, l0, g.L - 1, b, e);
+  const long long cap = g.cap;
+  for (int it = b + blockIdx.x * blockDim.x + threadIdx.x; it < e; it += gridDim.x * blockDim.x) {
+    const int s = g.lists[LK_EXIST * cap + it];
+    const int l = g.slot_level[s];
+    const int bc3[3] = {g.slot_coord[3 * s], g.slot_coord[3 * s + 1], g.slot_coord[3 * s + 2]};
+    const long long self = map_index(g, l, bc3[0], bc3[1], bc3[2]);
+    bool hit = rmask[self] != 0;
+    for (int o = 0; o < (D == 3 ? 27 : 9) && !hit; o++) {
+      const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, D == 3 ? o / 9 - 1 : 0};
+      if (off[0] == 0 && off[1] == 0 && off[2] == 0) continue;
+      int nb[3];
+      bool in = true;
+      for (int d = 0; d < 3; d++) {
+        nb[d] = bc3[d] + off[d];
+        if (d >= D) continue;
+        const int N = g.nb[l][d];
+        if (nb[d] < 0 || nb[d] >= N) {
+          if (g.bc == 1) nb[d] = (nb[d] + N) % N;
+          else in = false;
+        }
+      }
+      if (!in) continue;
+      const long long mi = map_index(g, l, nb[0], nb[1], nb[2]);
+      if (g.idx[mi] < 0) continue;
+      const unsigned long long m = rmask[mi];
+      // coarse cells of the neighbour next to this block: layer 3 (neighbour below),
+      // layer 0 (above) or every layer (same position) in each direction
+      for (int q = 0; q < (D == 3 ? 64 : 16); q++) {
+        const int c[3] = {q & 3, (q >> 2) & 3, q >> 4};
+        bool adj = true;
+        for (int d = 0; d < D; d++)
+          if ((off[d] < 0 && c[d] != 3) || (off[d] > 0 && c[d] != 0)) adj = false;
+        if (adj && ((m >> q) & 1ull)) hit = true;
+      }
+    }
+    if (hit) gflag[self] = 1;
+  }
+}
+
+}  // namespace mrfv

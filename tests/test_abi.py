@@ -76,3 +76,27 @@ def test_bad_config_is_rejected(lib):
     cfg.levels = 0
     h = ctypes.c_void_p()
     assert lib.mrfv_create(ctypes.byref(cfg), ctypes.byref(h)) == m.ERR_ARG
+
+
+def test_richardson_config_is_checked_and_sized(lib):
+    """eps_r must be >= 0, only adds to the gradient criterion, and adds its mask
+    and patch scratch to the arena only when on."""
+    import paper_1603_05211_gb300 as m
+
+    cfg = m.Config()
+    lib.mrfv_config_default(ctypes.byref(cfg))
+    cfg.levels = 3
+    cfg.criterion = m.CRIT_GRAD
+    off = lib.mrfv_arena_bytes(ctypes.byref(cfg))
+    cfg.eps_r = 1e-3
+    assert lib.mrfv_arena_bytes(ctypes.byref(cfg)) > off
+    h = ctypes.c_void_p()
+    for eps_r, crit in ((-1e-3, m.CRIT_GRAD), (float("nan"), m.CRIT_GRAD), (float("inf"), m.CRIT_GRAD),
+                        (1e-3, m.CRIT_MR)):
+        cfg.eps_r, cfg.criterion = eps_r, crit
+        assert lib.mrfv_create(ctypes.byref(cfg), ctypes.byref(h)) == m.ERR_ARG
+    cfg.levels = 1  # one level: nothing below the finest, no scratch
+    cfg.criterion, cfg.eps_r = m.CRIT_GRAD, 1e-3
+    n1 = lib.mrfv_arena_bytes(ctypes.byref(cfg))
+    cfg.eps_r = 0.0
+    assert lib.mrfv_arena_bytes(ctypes.byref(cfg)) == n1
