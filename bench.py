@@ -706,6 +706,104 @@ def run_proposer(args):
     s.close()
 
 
+def laxliu_solver(m, stream, n_cells, levels, scheme, adapt=False, lts=False, crit="mr", eps=0.0023, eps_w=0.05,
+                  eps_r=0.0):
+    """Lax-Liu #6 solver on [0,1]^2, single precision, Berger-Rigoutsos clustering"""
+    return m.Solver(dim=2, precision="fp32", levels=levels, base_blocks=(n_cells // (8 << (levels - 1)),) * 2 + (1,),
+                    adapt=adapt, lts=lts, criterion=crit, eps=eps, eps_w=eps_w, eta_tol=0.8, cfl=0.5,
+                    stream=stream, scheme=scheme, clustering="br", eps_r=eps_r)
+
+
+def laxliu_reference(m, torch, stream, nref, te):
+    """density of the AMR scheme on a uniform nref^2 grid after 5120 nref/4096 steps
+    to te (the reference of Tables 2-4), and the step count"""
+    r = laxliu_solver(m, stream, nref, 1, "hancock")
+    r.init_state(mi.IC_QUADRANTS, mi.laxliu6_params())
+    nr_steps = 5120 * nref // 4096
+    for _ in range(nr_steps):
+        r.step(te / nr_steps, sync=False)
+    rho_ref = r.download_level(0)[0][0]
+    r.close()
+    torch.cuda.empty_cache()
+    return rho_ref, nr_steps
+
+
+def run_richardson(args):
+    """The Richardson estimate added to the AMR criterion (Section 2.2) on the
+    paper's 2D benchmark: Lax-Liu configuration 6 to t_e = 0.25 with N_I fixed
+    steps at scale level L, the AMR scheme, density-gradient flags eps_rho = 0.05
+    clustered by Berger-Rigoutsos, global steps, single precision.  Variants:
+    gradient flags only, gradient flags and the estimate (each eps_r), the
+    estimate alone.  Reports L1(rho) against the 4096^2 reference, accumulated
+    leaves, GPU time of the timed run, and from a profiled eager run the
+    estimate's time per launch, the blocks it estimates, and its patch stage
+    cell-updates per second next to the stage kernel's."""
+    import numpy as np
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    P = mi.laxliu6_params()
+    te = 0.25
+    nref = args.laxliu_ref
+    rho_ref, nr_steps = laxliu_reference(m, torch, stream, nref, te)
+    # patch stage cell-updates per block of the AMR scheme in 2D (blocks away from
+    # the walls): fine stages on 12^2 and 8^2 cells, the coarse stage on 4^2
+    per_block = 144 + 64 + 16
+    out = {"case": "richardson_laxliu6", "t_end": te, "scheme": "hancock",
+           "reference": {"grid": nref, "steps": nr_steps}, "rows": []}
+    for L in [int(x) for x in args.laxliu_levels.split(",")]:
+        n = 1 << L
+        NI = 160 << (L - 7)
+        dt = te / NI
+        levels = L - 2
+        k = nref // n
+        ref = rho_ref.reshape(n, k, n, k).mean(axis=(1, 3))
+        row = {"L": L, "N": n, "N_I": NI}
+        variants = [("AMR", 0.05, 0.0)] + [(f"AMR+R(eps_r={e:g})", 0.05, e) for e in (1e-2, 1e-3)] + \
+                   [("R(eps_r=1e-3)", 1e9, 1e-3)]
+        for name, eps_w, eps_r in variants:
+            a = laxliu_solver(m, stream, n, levels, "hancock", adapt=True, crit="grad", eps_w=eps_w, eps_r=eps_r)
+            a.init_state(mi.IC_QUADRANTS, P)
+            Lf = 0
+            for _ in range(NI):
+                Lf += a.stats()["total_leaves"] * 64
+                a.step(dt, sync=True)
+            l1 = float(np.abs(a.project_finest()[0] - ref).sum() / (n * n))
+            a.close()
+            a = laxliu_solver(m, stream, n, levels, "hancock", adapt=True, crit="grad", eps_w=eps_w, eps_r=eps_r)
+            a.init_state(mi.IC_QUADRANTS, P)
+            ms = timed_steps(a, NI, torch, stream, dt=dt)
+            a.close()
+            # profiled eager steps halfway through the run
+            a = laxliu_solver(m, stream, n, levels, "hancock", adapt=True, crit="grad", eps_w=eps_w, eps_r=eps_r)
+            a.init_state(mi.IC_QUADRANTS, P)
+            for _ in range(NI // 2):
+                a.step(dt, sync=False)
+            a.profile_enable(True)
+            for _ in range(20):
+                a.step(dt, sync=False)
+            p = a.profile_read()
+            a.close()
+            torch.cuda.empty_cache()
+            ent = {"l1_rho": l1, "leaves_1e6": Lf / 1e6, "leaf_compression_pct": 100.0 * Lf / (NI * n * n),
+                   "gpu_ms": ms, "ms_per_step": ms / NI,
+                   "stage_cell_updates_per_s": p["fv_bytes"] / (2 * 4 * 4) / (p["fv_ms"] * 1e-3)}
+            if p["rich_launches"]:
+                ent.update({"rich_ms_per_launch": p["rich_ms"] / p["rich_launches"],
+                            "rich_blocks_per_launch": p["rich_blocks"] / p["rich_launches"],
+                            "rich_us_per_block": 1e3 * p["rich_ms"] / max(1.0, p["rich_blocks"]),
+                            "rich_patch_cell_updates_per_s": per_block * p["rich_blocks"] / (p["rich_ms"] * 1e-3),
+                            "rich_pct_of_step": 100.0 * (p["rich_ms"] / p["rich_launches"]) / (ms / NI)})
+            row[name] = ent
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def run_laxliu(args):
     """The paper's 2D benchmark (Section 4.1, Tables 2-4): Lax-Liu configuration 6
     on [0,1]^2 to t_e = 0.25 with N_I = 160 * 2^(L-7) fixed steps at scale levels
@@ -730,20 +828,10 @@ def run_laxliu(args):
     Ls = [int(x) for x in args.laxliu_levels.split(",")]
 
     def solver(n_cells, levels, scheme, adapt=False, lts=False, crit="mr", eps=0.0023):
-        return m.Solver(dim=2, precision="fp32", levels=levels, base_blocks=(n_cells // (8 << (levels - 1)),) * 2 + (1,),
-                        adapt=adapt, lts=lts, criterion=crit, eps=eps, eps_w=0.05, eta_tol=0.8, cfl=0.5,
-                        stream=stream, scheme=scheme, clustering="br")
+        return laxliu_solver(m, stream, n_cells, levels, scheme, adapt=adapt, lts=lts, crit=crit, eps=eps)
 
-    # reference: the AMR scheme on 4096^2, 5120 steps
     nref = args.laxliu_ref
-    r = solver(nref, 1, "hancock")
-    r.init_state(mi.IC_QUADRANTS, P)
-    nr_steps = 5120 * nref // 4096
-    for _ in range(nr_steps):
-        r.step(te / nr_steps, sync=False)
-    rho_ref = r.download_level(0)[0][0]
-    r.close()
-    torch.cuda.empty_cache()
+    rho_ref, nr_steps = laxliu_reference(m, torch, stream, nref, te)
     out = {"case": "laxliu6", "t_end": te, "reference": {"grid": nref, "steps": nr_steps, "scheme": "hancock"},
            "rows": []}
 
@@ -1017,7 +1105,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="adaptive",
-                    choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d", "epssweep"],
+                    choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d", "epssweep",
+                             "richardson"],
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
@@ -1047,6 +1136,8 @@ def main():
         run_matched3d(args)
     elif args.case == "proposer":
         run_proposer(args)
+    elif args.case == "richardson":
+        run_richardson(args)
     elif args.case == "laxliu":
         run_laxliu(args)
     elif args.case == "paper3d":

@@ -267,6 +267,9 @@ typedef struct {
                             4 pencil with two threads per line, 8 pencil on staged primitives,
                             16 staged MUSCL-Hancock */
   int graph_fv_kernels;  /* the same bit mask for the stage kernels in the step graphs captured now */
+  int64_t rich_launches; /* Richardson estimates timed (the estimate and its block flags, two kernels each) */
+  double rich_ms;        /* their CUDA-event time */
+  double rich_blocks;    /* blocks they estimated */
 } mrfv_profile;
 /* enable != 0: reset the counters and bracket every finite-volume stage launch
    with CUDA events on the context stream (steps then launch eagerly instead of

@@ -64,7 +64,8 @@ class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("fv_launches", ctypes.c_int64),
                 ("fv_ms", ctypes.c_double), ("fv_bytes", ctypes.c_double),
                 ("prop_launches", ctypes.c_int64), ("prop_ms", ctypes.c_double), ("prop_flops", ctypes.c_double),
-                ("fv_kernels", ctypes.c_int), ("graph_fv_kernels", ctypes.c_int)]
+                ("fv_kernels", ctypes.c_int), ("graph_fv_kernels", ctypes.c_int),
+                ("rich_launches", ctypes.c_int64), ("rich_ms", ctypes.c_double), ("rich_blocks", ctypes.c_double)]
 
 
 # exported symbols of include/mrfv.h with their ctypes signatures
@@ -372,4 +373,5 @@ class Solver:
         self._check(self.lib.mrfv_profile_read(self._h, ctypes.byref(p)))
         return dict(launches=p.launches, fv_launches=p.fv_launches, fv_ms=p.fv_ms, fv_bytes=p.fv_bytes,
                     prop_launches=p.prop_launches, prop_ms=p.prop_ms, prop_flops=p.prop_flops,
-                    fv_kernels=p.fv_kernels, graph_fv_kernels=p.graph_fv_kernels)
+                    fv_kernels=p.fv_kernels, graph_fv_kernels=p.graph_fv_kernels,
+                    rich_launches=p.rich_launches, rich_ms=p.rich_ms, rich_blocks=p.rich_blocks)

@@ -79,6 +79,8 @@ struct mrfv_ctx {
   size_t ev_used;
   std::vector<cudaEvent_t> pevs;  // start/end pairs around the proposer's convolution launches
   size_t pev_used;
+  std::vector<cudaEvent_t> revs;  // start/end pairs around the Richardson estimate's launches
+  size_t rev_used;
   unsigned long long *dbytes;
   unsigned *done;  // last-CTA counter of the CFL reduction
   // learned proposer
@@ -106,6 +108,7 @@ struct mrfv_ctx {
   int br_maxside;       // longest side, in blocks, of the levels that are clustered
   unsigned long long *rmask;  // Richardson: per block position, the coarse cells with |tau| > eps_r
   void *rscratch;       // Richardson: the patches of each CTA
+  unsigned long long *rcount;  // Richardson: blocks estimated while profiling
   int rich_ctas;        // CTAs of the Richardson estimate (0: off)
 };
 
@@ -238,7 +241,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t obr = L.take(br_scratch_bytes(g, maptotal, maxside));
   size_t orctl = L.take(4 * 4);
   const int rctas = rich_ctas_of(cfg, g);
-  size_t ormask = L.take(rctas ? maptotal * 8 : 0);
+  size_t ormask = L.take(rctas ? maptotal * 8 : 0), orcnt = L.take(8);
   size_t orscr = L.take(rctas ? (size_t)rctas * (size_t)(cfg->precision == MRFV_FP32 ? rich_scratch_bytes<float>(g.dim)
                                                                                   : rich_scratch_bytes<double>(g.dim))
                               : 0);
@@ -283,6 +286,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->rich_ctas = rctas;
     c->rmask = rctas ? (unsigned long long *)(a + ormask) : nullptr;
     c->rscratch = rctas ? (void *)(a + orscr) : nullptr;
+    c->rcount = (unsigned long long *)(a + orcnt);
   }
   return L.off + 256;
 }
@@ -559,17 +563,34 @@ struct Seq {
   // flagged or significant blocks, the safety zone above l0), closure above l0
   // only, nesting, then the tree update of the levels above l0
   void remesh(int l0);
+  // Richardson estimate of levels l0..L-1 (level l0's absent cells from level
+  // l0-1 halfway through its step when A0 is set) and gflag |= its block flags
+  void rich(int l0, const T *A0) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+      if (c->rev_used + 2 > c->revs.size())
+        for (int k = 0; k < 16; k++) {
+          cudaEvent_t e;
+          cudaEventCreate(&e);
+          c->revs.push_back(e);
+        }
+      e0 = c->revs[c->rev_used];
+      e1 = c->revs[c->rev_used + 1];
+      c->rev_used += 2;
+      cudaEventRecord(e0, c->st);
+    }
+    launch_rich<T>(c->g, c->cfg.scheme, U(), A0, 0.5, l0, c->lev, c->cfg.eps_r, c->rmask, c->maxdet, c->gflag,
+                   (T *)c->rscratch, c->rich_ctas, c->grid, c->prof ? c->rcount : nullptr, c->st);
+    if (c->prof) cudaEventRecord(e1, c->st);
+    c->nlaunch += 2;
+  }
   void gradflags(bool cleared = false) {
     if (!cleared) {
       cudaMemsetAsync(c->gflag, 0, c->maptotal, c->st);
       cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
     }
     launch_gradflags<T>(c->g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, 0, (const T *)nullptr, 0.0, c->bgrid, c->st);
-    if (c->rich_ctas) {
-      launch_rich<T>(c->g, c->cfg.scheme, U(), (const T *)nullptr, 0.0, 0, c->lev, c->cfg.eps_r, c->rmask, c->maxdet,
-                     c->gflag, (T *)c->rscratch, c->rich_ctas, c->grid, c->st);
-      c->nlaunch += 2;
-    }
+    if (c->rich_ctas) rich(0, nullptr);
     if (c->cfg.clustering == MRFV_CLUSTER_BR)
       launch_br(c->g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
     else
@@ -606,11 +627,7 @@ void Seq<T>::remesh(int l0) {
   launch_remesh_begin(g, c->maptotal, c->sig, c->gflag, c->need, c->nnew, l0, c->grid, c->st);
   if (c->cfg.criterion == MRFV_CRIT_GRAD) {
     launch_gradflags<T>(g, U(), c->cfg.eps_w, c->cfg.eps_p, c->gflag, l0, U0(), 0.5, c->bgrid, c->st);
-    if (c->rich_ctas) {
-      launch_rich<T>(g, c->cfg.scheme, U(), U0(), 0.5, l0, c->lev, c->cfg.eps_r, c->rmask, c->maxdet, c->gflag,
-                     (T *)c->rscratch, c->rich_ctas, c->grid, c->st);
-      c->nlaunch += 2;
-    }
+    if (c->rich_ctas) rich(l0, U0());
     if (c->cfg.clustering == MRFV_CLUSTER_BR)
       launch_br(g, c->gflag, c->sig, c->cfg.eta_tol, c->brscratch, c->maptotal, c->br_maxside, c->st);
     else
@@ -878,6 +895,7 @@ int mrfv_destroy(mrfv_ctx *c) {
   cudaStreamSynchronize(c->st);
   for (cudaEvent_t e : c->evs) cudaEventDestroy(e);
   for (cudaEvent_t e : c->pevs) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->revs) cudaEventDestroy(e);
   for (int v = 0; v < 2; v++)
     if (c->gexec[v]) cudaGraphExecDestroy(c->gexec[v]);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
@@ -1364,7 +1382,9 @@ int mrfv_profile_enable(mrfv_ctx *c, int enable) {
   c->prof = enable != 0;
   c->ev_used = 0;
   c->pev_used = 0;
+  c->rev_used = 0;
   c->nlaunch = 0;
+  cudaMemsetAsync(c->rcount, 0, 8, c->st);
   c->fv_kinds = 0;
   cudaMemsetAsync(c->dbytes, 0, 8, c->st);
   return check_launch(c, "mrfv_profile_enable");
@@ -1394,6 +1414,16 @@ int mrfv_profile_read(mrfv_ctx *c, mrfv_profile *o) {
   o->prop_launches = (int64_t)(3 * (c->pev_used / 2));
   o->prop_ms = pms;
   o->prop_flops = (double)(c->pev_used / 2) * 2.0 * (double)c->maptotal * (16.0 * 81 + 16.0 * 432 + 432.0);
+  double rms = 0.0;
+  for (size_t k = 0; k + 1 < c->rev_used; k += 2) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->revs[k], c->revs[k + 1]) == cudaSuccess) rms += t;
+  }
+  o->rich_launches = (int64_t)(c->rev_used / 2);
+  o->rich_ms = rms;
+  unsigned long long rb = 0;
+  cudaMemcpy(&rb, c->rcount, 8, cudaMemcpyDeviceToHost);
+  o->rich_blocks = (double)rb;
   o->fv_kernels = c->fv_kinds;
   o->graph_fv_kernels = (c->gexec[0] ? c->gkinds[0] : 0) | (c->gexec[1] ? c->gkinds[1] : 0);
   return check_launch(c, "mrfv_profile_read");

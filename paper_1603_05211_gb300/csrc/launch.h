@@ -29,10 +29,11 @@ template <typename T> void launch_copy_level(const Geo &, int kind, int l0, int 
 template <typename T> void launch_gradflags(const Geo &, const T *A, double epsw, double epsp, uint8_t *gflag, int l0,
                                            const T *A0, double theta, int grid, cudaStream_t);
 // Richardson estimate of levels l0..L-1 (ctas CTAs, each with rich_scratch_bytes
-// of scratch), then gflag |= its block flags
+// of scratch), then gflag |= its block flags; nblk (optional) += blocks estimated
 template <typename T> void launch_rich(const Geo &, int hancock, const T *A, const T *A0, double theta, int l0,
                                        const double *lev, double eps_r, unsigned long long *rmask, double *maxdet,
-                                       uint8_t *gflag, T *scratch, int ctas, int grid, cudaStream_t);
+                                       uint8_t *gflag, T *scratch, int ctas, int grid, unsigned long long *nblk,
+                                       cudaStream_t);
 template <typename T> long long rich_scratch_bytes(int dim);
 template <typename T> void launch_project_level(const Geo &, int l, const T *A, const double *coarse, double *out, cudaStream_t);
 // finite-volume stage and CFL reduction (fv_f32.cu, fv_f64.cu)

@@ -85,15 +85,19 @@ void launch_gradflags(const Geo &g, const T *A, double epsw, double epsp, uint8_
 template <typename T>
 void launch_rich(const Geo &g, int hancock, const T *A, const T *A0, double theta, int l0, const double *lev,
                  double eps_r, unsigned long long *rmask, double *maxdet, uint8_t *gflag, T *scratch, int ctas,
-                 int grid, cudaStream_t st) {
+                 int grid, unsigned long long *nblk, cudaStream_t st) {
   const T th = T(theta);
   if (g.dim == 2) {
-    if (hancock) k_rich<T, 2, true><<<ctas, RichShape<2>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch);
-    else k_rich<T, 2, false><<<ctas, RichShape<2>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch);
+    if (hancock)
+      k_rich<T, 2, true><<<ctas, RichShape<2>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
+    else
+      k_rich<T, 2, false><<<ctas, RichShape<2>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
     k_rich_flags<2><<<grid, 256, 0, st>>>(g, l0, rmask, gflag);
   } else {
-    if (hancock) k_rich<T, 3, true><<<ctas, RichShape<3>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch);
-    else k_rich<T, 3, false><<<ctas, RichShape<3>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch);
+    if (hancock)
+      k_rich<T, 3, true><<<ctas, RichShape<3>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
+    else
+      k_rich<T, 3, false><<<ctas, RichShape<3>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
     k_rich_flags<3><<<grid, 256, 0, st>>>(g, l0, rmask, gflag);
   }
 }
@@ -126,7 +130,8 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
                                     cudaStream_t);         \
   template void launch_project_level<T>(const Geo &, int, const T *, const double *, double *, cudaStream_t); \
   template void launch_rich<T>(const Geo &, int, const T *, const T *, double, int, const double *, double,     \
-                               unsigned long long *, double *, uint8_t *, T *, int, int, cudaStream_t);        \
+                               unsigned long long *, double *, uint8_t *, T *, int, int, unsigned long long *, \
+                               cudaStream_t);                                                                   \
   template long long rich_scratch_bytes<T>(int);
 
 }  // namespace mrfv

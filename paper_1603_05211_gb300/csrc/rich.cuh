@@ -256,7 +256,7 @@ template <typename T, int D, bool HANCOCK>
 __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__restrict__ A, const T *__restrict__ A0,
                                                            T theta, int l0, const double *__restrict__ lev,
                                                            double eps_r, unsigned long long *rmask, double *maxdet,
-                                                           T *scratch) {
+                                                           T *scratch, unsigned long long *nblk) {
   using S = RichShape<D>;
   constexpr int NV = S::NV, P = S::P, PC = S::PC, NP = S::NP, NPC = S::NPC, NT = S::NT;
   constexpr int NC = (D == 2) ? 16 : 64;  // coarse cells of a block
@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
   if (g.L < 1 || l0 > g.L - 1) return;
   int b, e;
   list_range(g, LK_EXIST, l0, g.L - 1, b, e);
+  if (nblk && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nblk, (unsigned long long)(e - b));
   const long long cap = g.cap;
   T *Ab = scratch + (long long)blockIdx.x * S::PER;
   T *Sb = Ab + NV * NP, *Wb = Sb + NV * NP, *DQb = Wb + NV * NP;

@@ -34,10 +34,10 @@ def mrfv():
 
 
 def _pair(m, dim, levels, base, lts, scheme, bc=0, eps_w=0.05, eps_r=EPS_R, ic=mi.IC_QUADRANTS, params=None,
-          lo=(0, 0, 0), hi=(1, 1, 1), precision="fp64", adapt=True):
+          lo=(0, 0, 0), hi=(1, 1, 1), precision="fp64", adapt=True, cfl=0.5):
     params = params if params is not None else mi.quadrant_params(4)
     s = m.Solver(dim=dim, levels=levels, base_blocks=base, adapt=adapt, criterion="grad", lts=lts, bc=bc, lo=lo,
-                 hi=hi, eps_w=eps_w, eps_r=eps_r, scheme=scheme, precision=precision)
+                 hi=hi, eps_w=eps_w, eps_r=eps_r, scheme=scheme, precision=precision, cfl=cfl)
     s.init_state(ic, params)
     o = oracle.Oracle(dim, levels, base, bc=bc, lo=lo, hi=hi,
                       scheme=oracle.SCHEME_HANCOCK if scheme == "hancock" else oracle.SCHEME_MUSCL_RK2)
@@ -107,19 +107,28 @@ def test_richardson_alone_2d(mrfv, scheme):
     _close(s, o)
 
 
-@pytest.mark.parametrize("lts", [False, True])
-def test_richardson_3d_matches_oracle(mrfv, lts):
-    s, o = _pair(mrfv, 3, 3, (2, 2, 2), lts, "hancock" if lts else "muscl_rk2", ic=mi.IC_ELLIPSOID,
-                 params=[0.45, 0.5, 0.55, 0.3, 0.25, 0.2, 1.0, 1.0, 0.125, 0.1])
+def test_richardson_3d_sod_matches_oracle(mrfv):
+    s, o = _pair(mrfv, 3, 3, (2, 2, 2), False, "muscl_rk2", ic=mi.IC_SHOCKTUBE, params=mi.sod_params(1, 0.4))
     _same_tree(s, o)
-    _run(s, o, 2, lts, 0.05, EPS_R)
+    _run(s, o, 2, False, 0.05, EPS_R)
+    _close(s, o)
+
+
+def test_richardson_3d_rotated_ellipsoid_hancock_lts(mrfv):
+    """the 3D case of Section 4.2 at small size, level-dependent steps (remesh
+    inside the recursion with the estimate)"""
+    s, o = _pair(mrfv, 3, 3, (2, 2, 2), True, "hancock", ic=mi.IC_ROTATED_ELLIPSOID, params=mi.paper3d_params(),
+                 lo=(-2, -2, -2), hi=(2, 2, 2), cfl=0.4)
+    _same_tree(s, o)
+    _run(s, o, 2, True, 0.05, EPS_R, cfl=0.4)
     _close(s, o)
 
 
 def test_richardson_3d_periodic_alone(mrfv):
     s, o = _pair(mrfv, 3, 3, (2, 2, 2), False, "muscl_rk2", bc=1, eps_w=1e9, ic=mi.IC_ELLIPSOID,
-                 params=[0.5, 0.5, 0.5, 0.3, 0.25, 0.2, 1.0, 1.0, 0.125, 0.1])
+                 params=[0.5, 0.5, 0.5, 0.3, 0.25, 0.2, 1.0, 1.0, 0.5, 0.5])
     _run(s, o, 2, False, 1e9, EPS_R)
+    assert o.get_exist(2).any()
     _close(s, o)
 
 
