@@ -731,13 +731,13 @@ def laxliu_reference(m, torch, stream, nref, te):
 def run_richardson(args):
     """The Richardson estimate added to the AMR criterion (Section 2.2) on the
     paper's 2D benchmark: Lax-Liu configuration 6 to t_e = 0.25 with N_I fixed
-    steps at scale level L, the AMR scheme, density-gradient flags eps_rho = 0.05
-    clustered by Berger-Rigoutsos, global steps, single precision.  Variants:
-    gradient flags only, gradient flags and the estimate (each eps_r), the
-    estimate alone.  Reports L1(rho) against the 4096^2 reference, accumulated
-    leaves, GPU time of the timed run, and from a profiled eager run the
-    estimate's time per launch, the blocks it estimates, and its patch stage
-    cell-updates per second next to the stage kernel's."""
+    finest-level steps at scale level L, the AMR scheme, density-gradient flags
+    eps_rho = 0.05 clustered by Berger-Rigoutsos, single precision.  Variants, with
+    global and with level-dependent steps: gradient flags only, gradient flags and
+    the estimate (eps_r = 1e-3), the estimate alone.  Reports L1(rho) against the
+    4096^2 reference, accumulated leaves, GPU time of the timed run, and from a
+    profiled eager run the estimate's time per launch, the blocks it estimates
+    and its patch stage cell-updates per second."""
     import numpy as np
     import torch
 
@@ -763,41 +763,50 @@ def run_richardson(args):
         k = nref // n
         ref = rho_ref.reshape(n, k, n, k).mean(axis=(1, 3))
         row = {"L": L, "N": n, "N_I": NI}
-        variants = [("AMR", 0.05, 0.0)] + [(f"AMR+R(eps_r={e:g})", 0.05, e) for e in (1e-2, 1e-3)] + \
-                   [("R(eps_r=1e-3)", 1e9, 1e-3)]
-        for name, eps_w, eps_r in variants:
-            a = laxliu_solver(m, stream, n, levels, "hancock", adapt=True, crit="grad", eps_w=eps_w, eps_r=eps_r)
-            a.init_state(mi.IC_QUADRANTS, P)
+        variants = []
+        for lts in (False, True):
+            t = "LT" if lts else ""
+            variants += [(f"AMR{t}", lts, 0.05, 0.0), (f"AMR{t}+R", lts, 0.05, 1e-3), (f"R{t}", lts, 1e9, 1e-3)]
+        for name, lts, eps_w, eps_r in variants:
+            steps = NI >> (levels - 1) if lts else NI
+            mult = (1 << (levels - 1)) if lts else 1
+
+            def make():
+                a = laxliu_solver(m, stream, n, levels, "hancock", adapt=True, lts=lts, crit="grad", eps_w=eps_w,
+                                  eps_r=eps_r)
+                a.init_state(mi.IC_QUADRANTS, P)
+                return a
+
+            a = make()
             Lf = 0
-            for _ in range(NI):
-                Lf += a.stats()["total_leaves"] * 64
+            for _ in range(steps):
+                Lf += a.stats()["total_leaves"] * 64 * mult
                 a.step(dt, sync=True)
             l1 = float(np.abs(a.project_finest()[0] - ref).sum() / (n * n))
             a.close()
-            a = laxliu_solver(m, stream, n, levels, "hancock", adapt=True, crit="grad", eps_w=eps_w, eps_r=eps_r)
-            a.init_state(mi.IC_QUADRANTS, P)
-            ms = timed_steps(a, NI, torch, stream, dt=dt)
+            a = make()
+            ms = timed_steps(a, steps, torch, stream, dt=dt)
             a.close()
-            # profiled eager steps halfway through the run
-            a = laxliu_solver(m, stream, n, levels, "hancock", adapt=True, crit="grad", eps_w=eps_w, eps_r=eps_r)
-            a.init_state(mi.IC_QUADRANTS, P)
-            for _ in range(NI // 2):
+            # profiled eager steps from halfway through the run
+            a = make()
+            for _ in range(steps // 2):
                 a.step(dt, sync=False)
             a.profile_enable(True)
-            for _ in range(20):
+            nprof = max(1, min(20, steps - steps // 2))
+            for _ in range(nprof):
                 a.step(dt, sync=False)
             p = a.profile_read()
             a.close()
             torch.cuda.empty_cache()
-            ent = {"l1_rho": l1, "leaves_1e6": Lf / 1e6, "leaf_compression_pct": 100.0 * Lf / (NI * n * n),
-                   "gpu_ms": ms, "ms_per_step": ms / NI,
-                   "stage_cell_updates_per_s": p["fv_bytes"] / (2 * 4 * 4) / (p["fv_ms"] * 1e-3)}
+            ent = {"eps_w": eps_w, "eps_r": eps_r, "l1_rho": l1, "leaves_1e6": Lf / 1e6,
+                   "leaf_compression_pct": 100.0 * Lf / (NI * n * n), "gpu_ms": ms, "ms_per_step": ms / steps}
             if p["rich_launches"]:
-                ent.update({"rich_ms_per_launch": p["rich_ms"] / p["rich_launches"],
+                ent.update({"rich_launches_per_step": p["rich_launches"] / nprof,
+                            "rich_ms_per_launch": p["rich_ms"] / p["rich_launches"],
                             "rich_blocks_per_launch": p["rich_blocks"] / p["rich_launches"],
                             "rich_us_per_block": 1e3 * p["rich_ms"] / max(1.0, p["rich_blocks"]),
                             "rich_patch_cell_updates_per_s": per_block * p["rich_blocks"] / (p["rich_ms"] * 1e-3),
-                            "rich_pct_of_step": 100.0 * (p["rich_ms"] / p["rich_launches"]) / (ms / NI)})
+                            "rich_pct_of_step": 100.0 * (p["rich_ms"] / nprof) / (ms / steps)})
             row[name] = ent
         out["rows"].append(row)
         print(json.dumps(row), flush=True)

@@ -39,7 +39,7 @@ struct RichShape {
   static constexpr int NP = (D == 2) ? P * P : P * P * P;
   static constexpr int NPC = (D == 2) ? PC * PC : PC * PC * PC;
   static constexpr int NFACE = (D == 2) ? (P + 1) * P : (P + 1) * P * P;  // faces of one direction
-  static constexpr int NT = 256;
+  static constexpr int NT = (D == 2) ? 128 : 256;  // threads per CTA (2D: four CTAs per SM by registers)
   // scratch values per CTA: A, S, W, DQ [NV][NP]; CA, CS [NV][NPC]; FL [D][NV][NFACE]
   static constexpr long long PER = (long long)NV * (4 * NP + 2 * NPC) + (long long)D * NV * NFACE;
 };
@@ -371,17 +371,20 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
       tau[q] = (sum * T(D == 3 ? 0.125 : 0.25) - cc[q]) / T(6);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long mask = 0;
-      double m = 0.0;
-      for (int q = 0; q < NC; q++) {
-        const T t = fabs(tau[q]);
-        if (t > T(eps_r)) mask |= 1ull << q;
-        if ((double)t > m) m = (double)t;
+    if (threadIdx.x < 32) {  // warp 0: mask by ballot, maximum by shuffles
+      const int ln = threadIdx.x;
+      const T t0 = ln < NC ? fabs(tau[ln]) : T(0), t1 = ln + 32 < NC ? fabs(tau[ln + 32]) : T(0);
+      const unsigned lo = __ballot_sync(0xffffffffu, t0 > T(eps_r)), hi = __ballot_sync(0xffffffffu, t1 > T(eps_r));
+      double m = (double)(t0 > t1 ? t0 : t1);
+      for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_xor_sync(0xffffffffu, m, o);
+        m = u > m ? u : m;
       }
-      const long long mi = map_index(g, l, bc3[0], bc3[1], bc3[2]);
-      rmask[mi] = mask;
-      maxdet[mi] = m;
+      if (ln == 0) {
+        const long long mi = map_index(g, l, bc3[0], bc3[1], bc3[2]);
+        rmask[mi] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+        maxdet[mi] = m;
+      }
     }
     __syncthreads();
   }
