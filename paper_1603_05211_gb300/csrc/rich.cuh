@@ -39,9 +39,11 @@ struct RichShape {
   static constexpr int NP = (D == 2) ? P * P : P * P * P;
   static constexpr int NPC = (D == 2) ? PC * PC : PC * PC * PC;
   static constexpr int NFACE = (D == 2) ? (P + 1) * P : (P + 1) * P * P;  // faces of one direction
+  static constexpr int PP = 14;   // level l-1 cells the predictions of the fine patch read (per edge)
+  static constexpr int NPP = (D == 2) ? PP * PP : PP * PP * PP;
   static constexpr int NT = (D == 2) ? 128 : 256;  // threads per CTA (2D: four CTAs per SM by registers)
-  // scratch values per CTA: A, S, W, DQ [NV][NP]; CA, CS [NV][NPC]; FL [D][NV][NFACE]
-  static constexpr long long PER = (long long)NV * (4 * NP + 2 * NPC) + (long long)D * NV * NFACE;
+  // scratch values per CTA: A, S, W, DQ [NV][NP]; CA, CS [NV][NPC]; FL [D][NV][NFACE]; CP [NV][NPP]
+  static constexpr long long PER = (long long)NV * (4 * NP + 2 * NPC + NPP) + (long long)D * NV * NFACE;
 };
 
 // A box [a, b) per dimension (unused dimensions [0, 1)) walked by the CTA's threads.
@@ -61,12 +63,15 @@ struct RBox {
 // stage input `in` on reg widened by 2.  dl/dh: the domain's cells of the patch
 // (reads outside are clamped into it; a periodic patch has none outside).
 // HANCOCK: the predictor advances the face states by dQ, h_m = (dt/2)/dx_m.
-template <typename T, int D, bool HANCOCK, int E>
-__device__ void rich_stage(const T *in, const T *q0, T *out, T *W, T *DQ, T *FL, const RBox &reg, const int *dl,
-                           const int *dh, const T *lam, const T *h, T gam, T gm1, T goverg1) {
+// (E is a run-time value and the direction loop is not unrolled: one copy of the
+// stage serves both patches, which keeps the kernel's instruction footprint small.)
+template <typename T, int D, bool HANCOCK>
+__device__ __noinline__ void rich_stage(const T *in, const T *q0, T *out, T *W, T *DQ, T *FL, const RBox &reg,
+                                        const int *dl, const int *dh, const T *lam, const T *h, T gam, T gm1,
+                                        T goverg1, const int E) {
   using S = RichShape<D>;
   constexpr int NV = S::NV, NFACE = S::NFACE, NT = S::NT;
-  constexpr int NS = (E == S::P) ? S::NP : S::NPC;  // values per variable of the patch buffers
+  const int NS = (D == 2) ? E * E : E * E * E;  // values per variable of the patch buffers
   auto cl = [&](int x, int d) { return x < dl[d] ? dl[d] : (x >= dh[d] ? dh[d] - 1 : x); };
   auto pidx = [&](int x, int y, int z) { return x + E * (y + E * z); };
   // primitives of the input on reg widened by 2, inside the domain
@@ -134,7 +139,7 @@ __device__ void rich_stage(const T *in, const T *q0, T *out, T *W, T *DQ, T *FL,
   }
   // numerical flux of every face of reg, all directions (face f along n lies
   // between cells f-1 and f; stored at f + (E+1) (t1 + E t2))
-#pragma unroll
+#pragma unroll 1
   for (int n = 0; n < D; n++) {
     const int t1 = (n == 0) ? 1 : 0, t2 = (n == 2) ? 1 : 2;
     RBox fb;
@@ -223,9 +228,9 @@ __device__ void rich_stage(const T *in, const T *q0, T *out, T *W, T *DQ, T *FL,
 // of its row (cells per dimension, clipped to the domain).  The result is in A
 // (RK2: both stages; the second writes A in place) or, for the one Hancock stage,
 // in `res`.
-template <typename T, int D, bool HANCOCK, int E>
+template <typename T, int D, bool HANCOCK>
 __device__ void rich_step(T *A, T *Sb, T *res, T *W, T *DQ, T *FL, int lo1, int hi1, int lo2, int hi2,
-                          const int *dl, const int *dh, double dt, const double *dx, T gam, T gm1, T goverg1) {
+                          const int *dl, const int *dh, double dt, const double *dx, T gam, T gm1, T goverg1, int E) {
   T lam1[3], lam2[3], hh[3];
   for (int d = 0; d < 3; d++) {
     lam1[d] = T((0.5 * dt) / dx[d]);
@@ -241,10 +246,10 @@ __device__ void rich_step(T *A, T *Sb, T *res, T *W, T *DQ, T *FL, int lo1, int 
     return b;
   };
   if constexpr (HANCOCK) {
-    rich_stage<T, D, true, E>(A, A, res, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1);
+    rich_stage<T, D, true>(A, A, res, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1, E);
   } else {
-    rich_stage<T, D, false, E>(A, A, Sb, W, DQ, FL, box(lo1, hi1), dl, dh, lam1, hh, gam, gm1, goverg1);
-    rich_stage<T, D, false, E>(Sb, A, A, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1);
+    rich_stage<T, D, false>(A, A, Sb, W, DQ, FL, box(lo1, hi1), dl, dh, lam1, hh, gam, gm1, goverg1, E);
+    rich_stage<T, D, false>(Sb, A, A, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1, E);
   }
 }
 
@@ -268,7 +273,8 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
   const long long cap = g.cap;
   T *Ab = scratch + (long long)blockIdx.x * S::PER;
   T *Sb = Ab + NV * NP, *Wb = Sb + NV * NP, *DQb = Wb + NV * NP;
-  T *CA = DQb + NV * NP, *CS = CA + NV * NPC, *FL = CS + NV * NPC;
+  T *CA = DQb + NV * NP, *CS = CA + NV * NPC, *FL = CS + NV * NPC, *CP = FL + D * NV * S::NFACE;
+  constexpr int PP = S::PP, NPP = S::NPP;
   const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
   for (int it = b + blockIdx.x; it < e; it += gridDim.x) {
     const int s = g.lists[LK_EXIST * cap + it];
@@ -293,23 +299,63 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
         cdh[d] = min(PC, N / 2 - og / 2);
       }
     }
-    // gather E on the fine patch (domain cells only)
+    // gather E on the fine patch (domain cells only): the value of the cell's block,
+    // or the third-order prediction from level l-1, whose cells the patch needs
+    // (coarse cells 4 bc - 5 .. 4 bc + 8 per dimension, by the boundary rule, in
+    // time-interpolated form at level l0 with A0) are staged in CP first
     {
+      const T *C0 = (l == l0) ? A0 : nullptr;
+      if (l > 0) {
+        for (int q = threadIdx.x; q < NPP; q += NT) {
+          const int c[3] = {q % PP, (q / PP) % PP, D == 3 ? q / (PP * PP) : 0};
+          int cg[3] = {0, 0, 0};
+          for (int d = 0; d < D; d++) cg[d] = bc_cell(g, l - 1, d, 4 * bc3[d] - 5 + c[d]);
+          const int32_t sc = g.idx[map_index(g, l - 1, cg[0] >> 3, cg[1] >> 3, cg[2] >> 3)];
+          const int cc = (cg[0] & 7) + 8 * (cg[1] & 7) + (D == 3 ? 64 * (cg[2] & 7) : 0);
+#pragma unroll
+          for (int v = 0; v < NV; v++) {
+            T val = nan_val<T>();  // an absent coarse block is never read by a prediction of the tree
+            if (sc >= 0) {
+              const long long off = ((long long)v * cap + sc) * (D == 2 ? 64 : 512) + cc;
+              val = A[off];
+              if (C0) {
+                const T a0 = C0[off];
+                val = a0 + theta * (val - a0);
+              }
+            }
+            CP[v * NPP + q] = val;
+          }
+        }
+        __syncthreads();
+      }
       RBox gb;
       for (int d = 0; d < 3; d++) {
         gb.a[d] = dl[d];
         gb.b[d] = dh[d];
       }
-      const T *C0 = (l == l0) ? A0 : nullptr;
       for (int q = threadIdx.x; q < gb.count(); q += NT) {
         int x, y, z;
         gb.at(q, x, y, z);
-        T Q[NV];
-        ext_cell<T, D>(g, l, 8 * bc3[0] - 8 + x, 8 * bc3[1] - 8 + y, D == 3 ? 8 * bc3[2] - 8 + z : 0, A, A, C0,
-                       theta, Q);
+        const int u[3] = {8 * bc3[0] - 8 + x, 8 * bc3[1] - 8 + y, D == 3 ? 8 * bc3[2] - 8 + z : 0};  // unwrapped
+        int f[3] = {0, 0, 0};
+        for (int d = 0; d < D; d++) f[d] = bc_cell(g, l, d, u[d]);
+        const int32_t sf = g.idx[map_index(g, l, f[0] >> 3, f[1] >> 3, f[2] >> 3)];
         const int p = x + P * (y + P * z);
+        if (sf >= 0) {
+          const int c = (f[0] & 7) + 8 * (f[1] & 7) + (D == 3 ? 64 * (f[2] & 7) : 0);
 #pragma unroll
-        for (int v = 0; v < NV; v++) Ab[v * NP + p] = Q[v];
+          for (int v = 0; v < NV; v++) Ab[v * NP + p] = A[((long long)v * cap + sf) * (D == 2 ? 64 : 512) + c];
+        } else if (l == 0) {  // level 0 is complete: a missing block is a broken tree
+          set_err(g, EB_TREE);
+#pragma unroll
+          for (int v = 0; v < NV; v++) Ab[v * NP + p] = nan_val<T>();
+        } else {
+          // parent of the cell in CP: (u >> 1) - (4 bc - 5), i.e. 1..12
+          const int px = (x >> 1) + 1, py = (y >> 1) + 1, pz = D == 3 ? (z >> 1) + 1 : 0;
+          const T si = (f[0] & 1) ? T(-1) : T(1), sj = (f[1] & 1) ? T(-1) : T(1), sk = (f[2] & 1) ? T(-1) : T(1);
+#pragma unroll
+          for (int v = 0; v < NV; v++) Ab[v * NP + p] = predict<T, D, PP>(CP + v * NPP, px, py, pz, si, sj, sk);
+        }
       }
     }
     __syncthreads();
@@ -344,7 +390,7 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
       dxf[d] = g.dx[l][d];
       dxc[d] = 2.0 * g.dx[l][d];
     }
-    rich_step<T, D, HANCOCK, PC>(CA, CS, CS, Wb, DQb, FL, 2, 10, 4, 8, cdl, cdh, 2.0 * dtl, dxc, gam, gm1, goverg1);
+    rich_step<T, D, HANCOCK>(CA, CS, CS, Wb, DQb, FL, 2, 10, 4, 8, cdl, cdh, 2.0 * dtl, dxc, gam, gm1, goverg1, PC);
     const T *Cres = HANCOCK ? CS : CA;
     for (int q = threadIdx.x; q < NC; q += NT) {
       const int x = q & 3, y = (q >> 2) & 3, z = q >> 4;
@@ -352,11 +398,11 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
     }
     // two fine steps of dt (regions 2..22, 4..20, 6..18, 8..16; Hancock 6..18, 8..16)
     if constexpr (HANCOCK) {
-      rich_step<T, D, true, P>(Ab, Sb, Sb, Wb, DQb, FL, 0, 0, 6, 18, dl, dh, dtl, dxf, gam, gm1, goverg1);
-      rich_step<T, D, true, P>(Sb, Ab, Ab, Wb, DQb, FL, 0, 0, 8, 16, dl, dh, dtl, dxf, gam, gm1, goverg1);
+      rich_step<T, D, true>(Ab, Sb, Sb, Wb, DQb, FL, 0, 0, 6, 18, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
+      rich_step<T, D, true>(Sb, Ab, Ab, Wb, DQb, FL, 0, 0, 8, 16, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
     } else {
-      rich_step<T, D, false, P>(Ab, Sb, Ab, Wb, DQb, FL, 2, 22, 4, 20, dl, dh, dtl, dxf, gam, gm1, goverg1);
-      rich_step<T, D, false, P>(Ab, Sb, Ab, Wb, DQb, FL, 6, 18, 8, 16, dl, dh, dtl, dxf, gam, gm1, goverg1);
+      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 2, 22, 4, 20, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
+      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 6, 18, 8, 16, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
     }
     // restrict the fine result on the block and compare
     for (int q = threadIdx.x; q < NC; q += NT) {
