@@ -250,6 +250,15 @@ int mrfv_get_flags(mrfv_ctx *ctx, int level, uint8_t *flags, double *maxdet, int
 /* Wait for all work issued on the context's stream. */
 int mrfv_synchronize(mrfv_ctx *ctx);
 
+/* Failure-path self-test of the bounded device waits (no counterpart in the
+   paper).  Launches one warp that waits, with the same bounded mbarrier wait the
+   tensor-core kernels use (at most `iterations` tries, 1..2^24), on a phase that
+   completes only when `complete` = 1.  Returns MRFV_OK when the phase
+   completed, MRFV_ERR_TIMEOUT when the bound expired; either way nothing is left
+   waiting and the context stays usable.  Errors pending before the call are
+   returned first. */
+int mrfv_wait_selftest(mrfv_ctx *ctx, int64_t iterations, int complete);
+
 /* Diagnostics (no counterpart in the paper, which profiled its CPU codes with
    perf, Section 4.1 Table 5): kernel launch count and CUDA-event timing of the
    finite-volume stage launches. */

@@ -97,6 +97,7 @@ SIGNATURES = {
     "mrfv_set_tree": (_I, [_P, _U8, _I64]),
     "mrfv_get_flags": (_I, [_P, _I, _U8, _DP, _I64]),
     "mrfv_synchronize": (_I, [_P]),
+    "mrfv_wait_selftest": (_I, [_P, _I64, _I]),
     "mrfv_profile_enable": (_I, [_P, _I]),
     "mrfv_profile_read": (_I, [_P, ctypes.POINTER(Profile)]),
     "mrfv_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
@@ -320,6 +321,11 @@ class Solver:
 
     def synchronize(self) -> None:
         self._check(self.lib.mrfv_synchronize(self._h))
+
+    def wait_selftest(self, iterations: int, complete: bool) -> int:
+        """Status of one bounded device wait on a phase that completes only when
+        `complete` (OK, or ERR_TIMEOUT once `iterations` tries expired)."""
+        return int(self.lib.mrfv_wait_selftest(self._h, int(iterations), int(bool(complete))))
 
     # ------------------------------------------------------------------ learned proposer
     @property

@@ -1278,6 +1278,17 @@ int mrfv_synchronize(mrfv_ctx *c) {
   return check_device(c, "mrfv_synchronize");
 }
 
+int mrfv_wait_selftest(mrfv_ctx *c, int64_t iterations, int complete) {
+  if (!c || iterations < 1 || iterations > (1 << 24) || (complete != 0 && complete != 1))
+    return fail(c, MRFV_ERR_ARG, "wait_selftest: arguments");
+  int rc = check_device(c, "wait_selftest: before");  // earlier errors are not this test's
+  if (rc != MRFV_OK) return rc;
+  launch_wait_selftest(c->g.err, (unsigned)iterations, complete, c->st);
+  rc = check_launch(c, "mrfv_wait_selftest");
+  if (rc != MRFV_OK) return rc;
+  return check_device(c, "mrfv_wait_selftest");
+}
+
 int mrfv_proposer_set_weights(mrfv_ctx *c, const float *w, int64_t n) {
   if (!c || !w || n != MRFV_PROPOSER_NWEIGHTS) return fail(c, MRFV_ERR_ARG, "proposer_set_weights: n");
   const size_t NW = MRFV_PROPOSER_NWEIGHTS;

@@ -77,6 +77,7 @@ void launch_advance(const Geo &, double *t, const double *dt, double factor, lon
 template <typename T> void launch_prop_features(const Geo &, const T *U, const double *maxdet, const T *scale, double eps,
                                                 float *feat, int grid, cudaStream_t);
 void prop_setup();
+void launch_wait_selftest(int *err, unsigned limit, int arrive, cudaStream_t);
 void launch_prop_infer(const Geo &, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
                        const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
                        const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaEvent_t conv_begin,

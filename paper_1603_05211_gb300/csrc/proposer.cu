@@ -151,8 +151,8 @@ __device__ __forceinline__ uint32_t cm_offset(int r, int k, int KP) {
 constexpr unsigned kWaitLimit = 1u << 24;
 
 // bounded wait for the mbarrier phase `parity`; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (unsigned it = 0; it < kWaitLimit; it++) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned limit = kWaitLimit) {
+  for (unsigned it = 0; it < limit; it++) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred P;\n\t"
@@ -525,6 +525,32 @@ void prop_setup() {
 
 // features (float [3][n]) -> logits (float [n]) through the three layers on tensor
 // cores; a0: BF16 [n][8], a1, a2: BF16 [n][16]
+// Self-test of the failure path of the bounded waits: one warp initialises an
+// mbarrier expecting one arrival, arrives on it only when `arrive` is set, and
+// waits for its first phase with the tensor-core kernel's bounded wait (limit
+// iterations); an expired wait records EB_TIMEOUT, as the real kernels do.
+__global__ void k_wait_selftest(int *err, unsigned limit, int arrive) {
+  __shared__ __align__(8) uint64_t mbar;
+  const uint32_t mb = smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && arrive) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(mb) : "memory");
+    (void)state;
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(mb, 0, limit);
+  if (threadIdx.x == 0 && !ok) atomicOr(err, EB_TIMEOUT);
+}
+
+void launch_wait_selftest(int *err, unsigned limit, int arrive, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(err, limit, arrive);
+}
+
 void launch_prop_infer(const Geo &g, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
                        const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
                        const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaEvent_t conv_begin,

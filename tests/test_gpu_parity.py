@@ -439,3 +439,18 @@ def test_degenerate_thresholds(mrfv, eps, lts):
     else:
         assert all(s.get_tree(l).all() for l in range(4))
     assert_levels_close(s, o)
+
+
+def test_bounded_wait_expires_and_the_context_stays_usable(mrfv):
+    """Failure detection without a GPU fault: a bounded mbarrier wait on a phase
+    nothing completes returns ERR_TIMEOUT; the completed phase returns OK; the
+    same context then steps normally."""
+    s = mrfv.Solver(dim=2, levels=2, base_blocks=(2, 2, 1), adapt=True)
+    s.init_state(mi.IC_QUADRANTS, mi.quadrant_params(1))
+    assert s.wait_selftest(4096, True) == mrfv.OK
+    assert s.wait_selftest(4096, False) == mrfv.ERR_TIMEOUT
+    assert b"bounded device wait expired" in s.lib.mrfv_last_error(s._h)
+    assert s.wait_selftest(4096, True) == mrfv.OK
+    dt = s.step(0.0)
+    assert dt > 0.0
+    s.synchronize()
