@@ -530,7 +530,17 @@ def run_ours(args):
     m.load()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    shape, tuned = {}, None
+    if args.autotune:
+        # the launch shape from the autotuner's cache, swept and cached first when absent
+        from paper_1603_05211_gb300 import autotune
+
+        tuned = autotune.tuned_shape(lambda: make_solver(m, stream), dict(WL, criterion="mr", scheme="muscl_rk2"),
+                                     retune=args.autotune == "sweep", steps=20, warmup=5, passes=2)
+        shape = tuned["shape"]
     s = make_solver(m, stream)
+    if shape:
+        s.set_launch_shape(**shape)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         s.step(0.0, sync=False)
@@ -571,7 +581,7 @@ def run_ours(args):
     prof = s.profile_read()
     s.profile_enable(False)
     if graph_stage:
-        s.set_launch_shape(stage_kernel=0)
+        s.set_launch_shape(**dict(shape or {}, stage_kernel=(shape or {}).get("stage_kernel", 0)))
     ms_max, value = aggregate_ranks(ms, cells, world, dev)
     hbm_peak, peak_kind = measured_peaks()
 
@@ -609,7 +619,10 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "levels": 8, "finest": 1024, "eps": WL["eps"], "cfl": WL["cfl"],
                        "ic": "seeded four-quadrant Riemann (seed 0)", "l2": "flushed between timed steps",
-                       "leaves_per_step": cells / args.steps / 64, "parallelism": f"replicas x{world}"},
+                       "leaves_per_step": cells / args.steps / 64, "parallelism": f"replicas x{world}",
+                       "launch_shape": shape or "library defaults",
+                       **({"autotune": {k: tuned[k] for k in ("ms_per_step", "default_ms_per_step", "cached")
+                                        if k in tuned}} if tuned else {})},
             "roofline": roof,
             "roofline_uniform": roof_u, "roofline_hancock": roof_h,
             "cpu_baseline": {"value": ob, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
@@ -1133,6 +1146,9 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--scheme", default="muscl_rk2", choices=["muscl_rk2", "hancock"],
                     help="finite-volume scheme of the uniform case")
+    ap.add_argument("--autotune", default="", choices=["", "cache", "sweep"],
+                    help="default workload: take the launch shape from the autotuner (cache: the cached "
+                         "choice, swept first when absent; sweep: sweep again)")
     ap.add_argument("--stage-kernel", dest="stage_kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="uniform case: 0 by leaf count, 1 pencil kernel, 2 staged kernel, "
                          "3 split pencil kernel, 4 pencil kernel on staged primitives")
