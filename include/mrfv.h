@@ -208,6 +208,13 @@ int mrfv_step_level(mrfv_ctx *ctx, int level, double dt_finest);
    fine_level-1; fine_level <= 0 restricts every level, finest first. */
 int mrfv_restrict(mrfv_ctx *ctx, int fine_level);
 
+/* Prediction (Section 2.1, third order) of every existing block of level
+   coarse_level+1 from level coarse_level, overwriting those blocks (0 <=
+   coarse_level < L).  The tree's own prolongation fills only the blocks an
+   adaptation creates; this call applies the operator to a whole level (tests,
+   re-initialisation of a level from its parent). */
+int mrfv_prolong(mrfv_ctx *ctx, int coarse_level);
+
 /* Conserved totals: sum over leaf cells of Q_v times the cell volume, in double
    (nv values).  Synchronises. */
 int mrfv_conserved_totals(mrfv_ctx *ctx, double *out, int n);

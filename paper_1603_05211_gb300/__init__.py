@@ -97,6 +97,7 @@ SIGNATURES = {
     "mrfv_set_tree": (_I, [_P, _U8, _I64]),
     "mrfv_get_flags": (_I, [_P, _I, _U8, _DP, _I64]),
     "mrfv_synchronize": (_I, [_P]),
+    "mrfv_prolong": (_I, [_P, _I]),
     "mrfv_wait_selftest": (_I, [_P, _I64, _I]),
     "mrfv_profile_enable": (_I, [_P, _I]),
     "mrfv_profile_read": (_I, [_P, ctypes.POINTER(Profile)]),
@@ -261,6 +262,11 @@ class Solver:
 
     def restrict(self, fine_level: int = 0) -> None:
         self._check(self.lib.mrfv_restrict(self._h, fine_level))
+
+    def prolong(self, coarse_level: int) -> None:
+        """Overwrite every existing block of level coarse_level+1 by the
+        third-order prediction from level coarse_level."""
+        self._check(self.lib.mrfv_prolong(self._h, coarse_level))
 
     def totals(self) -> np.ndarray:
         out = np.zeros(5)

@@ -534,12 +534,12 @@ struct Seq {
                       sized(c, LK_EXIST, l0, c->g.L, 1, 1, c->bgrid), c->st);
     c->nlaunch += 2;
   }
-  // new blocks of levels lfrom..L (a remesh above l0 creates none below l0+1)
-  void prolong_new(int lfrom = 1) {
-    for (int l = lfrom; l <= c->g.L; l++)
+  // new blocks of levels lfrom..lto (default L; a remesh above l0 creates none below l0+1)
+  void prolong_new(int lfrom = 1, int lto = -1) {
+    for (int l = lfrom; l <= (lto < 0 ? c->g.L : lto); l++)
       launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(),
                         sized(c, LK_EXIST, l, l, 1, 1, grid_for(level_blocks(c->g, l), 1, c->bgrid)), c->st);
-    c->nlaunch += c->g.L - lfrom + 1;
+    c->nlaunch += (lto < 0 ? c->g.L : lto) - lfrom + 1;
   }
   // CFL reduction; its last CTA sets dt and the per-level step table
   void compute_dt(int lts) {
@@ -1125,6 +1125,19 @@ int mrfv_restrict(mrfv_ctx *c, int fine_level) {
     else s.restrict_level(fine_level - 1, s.U());
   });
   return check_launch(c, "mrfv_restrict");
+}
+
+int mrfv_prolong(mrfv_ctx *c, int coarse_level) {
+  if (!c || coarse_level < 0 || coarse_level >= c->g.L) return fail(c, MRFV_ERR_ARG, "prolong: level");
+  if (!c->initialized) return fail(c, MRFV_ERR_STATE, "prolong before init");
+  const int l = coarse_level + 1;
+  launch_list_level(c->g, l, c->newlist, c->nnew, c->grid, c->st);
+  c->nlaunch += 1;
+  dispatch(c, [&](auto &s) { s.prolong_new(l, l); });
+  cudaMemsetAsync(c->nnew, 0, MAXL * sizeof(int), c->st);  // no stale count for the next adaptation
+  int rc = check_launch(c, "mrfv_prolong");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_prolong");
+  return rc;
 }
 
 int mrfv_conserved_totals(mrfv_ctx *c, double *out, int n) {

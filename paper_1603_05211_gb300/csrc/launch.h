@@ -55,6 +55,7 @@ void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t
 void launch_remesh_begin(const Geo &, long long total, uint8_t *sig, uint8_t *gflag, uint8_t *need, int *nnew, int l0,
                          int grid, cudaStream_t);
 void launch_need_prune(const Geo &, int l, uint8_t *need, int grid, cudaStream_t);
+void launch_list_level(const Geo &, int l, int32_t *newlist, int *nnew, int grid, cudaStream_t);
 void launch_adapt_begin(const Geo &, long long total, uint8_t *sig, double *maxdet, uint8_t *gflag, uint8_t *need,
                         int *nnew, double *t, const double *dt, double factor, long long *counter, int lts,
                         int32_t *pub, int grid, cudaStream_t);

@@ -904,6 +904,19 @@ void launch_remesh_begin(const Geo &g, long long total, uint8_t *sig, uint8_t *g
                          int grid, cudaStream_t st) {
   k_remesh_begin<<<fit(total, 256, grid), 256, 0, st>>>(g, total, sig, gflag, need, nnew, l0);
 }
+// every existing block of level l into level l's segment of the new-block list
+// (the prolongation kernel's input), its count into nnew[l]
+__global__ void k_list_level(Geo g, int l, int32_t *newlist, int *nnew) {
+  int b, e;
+  list_range(g, LK_EXIST, l, l, b, e);
+  const long long cap = g.cap;
+  for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x)
+    newlist[g.mapoff[l] + (i - b)] = g.lists[LK_EXIST * cap + i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) nnew[l] = e - b;
+}
+void launch_list_level(const Geo &g, int l, int32_t *newlist, int *nnew, int grid, cudaStream_t st) {
+  k_list_level<<<grid, 256, 0, st>>>(g, l, newlist, nnew);
+}
 void launch_need_prune(const Geo &g, int l, uint8_t *need, int grid, cudaStream_t st) {
   k_need_prune<<<fit(g.mapoff[l + 1] - g.mapoff[l], 256, grid), 256, 0, st>>>(g, l, need);
 }
