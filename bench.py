@@ -826,6 +826,78 @@ def run_richardson(args):
     print(json.dumps(out), flush=True)
 
 
+def run_richardson3d(args):
+    """The Richardson estimate on the paper's 3D case (Section 4.2): the rotated
+    ellipsoid on [-2,2]^3 with N_I = 16 * 2^(L-5) fixed steps to t_e = 0.28 at
+    scale level L, the AMR scheme, density and pressure gradient flags
+    (eps_rho = eps_p = 0.05) clustered by Berger-Rigoutsos, single precision,
+    global and level-dependent steps, without and with the estimate
+    (eps_r = 1e-3).  Reports accumulated leaves, GPU time per step and the
+    estimate's time, blocks and patch stage cell-updates per second (3D AMR
+    scheme: fine stages on 12^3 and 8^3 cells, the coarse stage on 4^3)."""
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    P = mi.paper3d_params()
+    te = 0.28
+    per_block = 12 ** 3 + 8 ** 3 + 4 ** 3
+    out = {"case": "richardson_paper3d", "t_end": te, "scheme": "hancock", "rows": []}
+    for L in [int(x) for x in args.paper3d_levels.split(",")]:
+        n = 1 << L
+        NI = 16 << (L - 5)
+        dt = te / NI
+        levels = L - 2
+        row = {"L": L, "N": n, "N_I": NI}
+        for name, lts, eps_r in (("AMR", False, 0.0), ("AMR+R", False, 1e-3), ("AMRLT", True, 0.0),
+                                 ("AMRLT+R", True, 1e-3)):
+            steps = NI >> (levels - 1) if lts else NI
+            mult = (1 << (levels - 1)) if lts else 1
+
+            def make():
+                a = m.Solver(dim=3, precision="fp32", levels=levels, base_blocks=(1, 1, 1), lo=(-2.0,) * 3,
+                             hi=(2.0,) * 3, adapt=True, lts=lts, criterion="grad", eps_w=0.05, eps_p=0.05,
+                             eta_tol=0.8, cfl=0.4, stream=stream, scheme="hancock", clustering="br", eps_r=eps_r)
+                a.init_state(mi.IC_ROTATED_ELLIPSOID, P)
+                return a
+
+            a = make()
+            Lf = 0
+            for _ in range(steps):
+                Lf += a.stats()["total_leaves"] * 512 * mult
+                a.step(dt, sync=True)
+            a.close()
+            a = make()
+            ms = timed_steps(a, steps, torch, stream, dt=dt)
+            a.close()
+            a = make()
+            for _ in range(steps // 2):
+                a.step(dt, sync=False)
+            a.profile_enable(True)
+            nprof = max(1, min(10, steps - steps // 2))
+            for _ in range(nprof):
+                a.step(dt, sync=False)
+            p = a.profile_read()
+            a.close()
+            torch.cuda.empty_cache()
+            ent = {"eps_r": eps_r, "leaves_1e6": Lf / 1e6, "leaf_compression_pct": 100.0 * Lf / (NI * n ** 3),
+                   "gpu_ms": ms, "ms_per_step": ms / steps}
+            if p["rich_launches"]:
+                ent.update({"rich_launches_per_step": p["rich_launches"] / nprof,
+                            "rich_ms_per_launch": p["rich_ms"] / p["rich_launches"],
+                            "rich_blocks_per_launch": p["rich_blocks"] / p["rich_launches"],
+                            "rich_us_per_block": 1e3 * p["rich_ms"] / max(1.0, p["rich_blocks"]),
+                            "rich_patch_cell_updates_per_s": per_block * p["rich_blocks"] / (p["rich_ms"] * 1e-3),
+                            "rich_pct_of_step": 100.0 * (p["rich_ms"] / nprof) / (ms / steps)})
+            row[name] = ent
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def run_laxliu(args):
     """The paper's 2D benchmark (Section 4.1, Tables 2-4): Lax-Liu configuration 6
     on [0,1]^2 to t_e = 0.25 with N_I = 160 * 2^(L-7) fixed steps at scale levels
@@ -1162,7 +1234,10 @@ def main():
     elif args.case == "proposer":
         run_proposer(args)
     elif args.case == "richardson":
-        run_richardson(args)
+        if args.dim == 3:
+            run_richardson3d(args)
+        else:
+            run_richardson(args)
     elif args.case == "laxliu":
         run_laxliu(args)
     elif args.case == "paper3d":
