@@ -12,7 +12,8 @@
 // One CTA per existing block of levels l0..L-1.  The estimate of the block's 4^d
 // coarse cells depends on E only within 8 fine cells of the block (each stage
 // reaches 2 cells; two fine steps, one coarse step), so the CTA gathers that
-// 24^d patch, restricts it to the 12^d coarse patch, runs the coarse step of 2 dt
+// 24^d patch (absent cells predicted from the 14^d coarser cells under it, staged
+// once), restricts it to the 12^d coarse patch, runs the coarse step of 2 dt
 // and the two fine steps of dt, every stage on a region 2 cells narrower than its
 // input, and compares on the block.  Each stage converts its input to primitives
 // once, evaluates the numerical flux once per face of its region and applies the
