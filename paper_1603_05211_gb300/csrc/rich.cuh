@@ -276,6 +276,10 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
   T *Sb = Ab + NV * NP, *Wb = Sb + NV * NP, *DQb = Wb + NV * NP;
   T *CA = DQb + NV * NP, *CS = CA + NV * NPC, *FL = CS + NV * NPC, *CP = FL + D * NV * S::NFACE;
   constexpr int PP = S::PP, NPP = S::NPP;
+  // The AMR scheme's stages reach 2 cells per step, one stage each: its estimate
+  // needs only fine cells 4..20 of the patch (coarse 2..10, staged coarser cells
+  // 2..12); the MR scheme's two stages per step need the whole patch.
+  constexpr int M = HANCOCK ? 4 : 0;
   const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
   for (int it = b + blockIdx.x; it < e; it += gridDim.x) {
     const int s = g.lists[LK_EXIST * cap + it];
@@ -307,17 +311,24 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
     {
       const T *C0 = (l == l0) ? A0 : nullptr;
       if (l > 0) {
-        for (int q = threadIdx.x; q < NPP; q += NT) {
-          const int c[3] = {q % PP, (q / PP) % PP, D == 3 ? q / (PP * PP) : 0};
+        RBox pb;
+        for (int d = 0; d < 3; d++) {
+          pb.a[d] = d < D ? M / 2 : 0;
+          pb.b[d] = d < D ? PP - M / 2 : 1;
+        }
+        for (int r = threadIdx.x; r < pb.count(); r += NT) {
+          int c[3];
+          pb.at(r, c[0], c[1], c[2]);
+          const int q = c[0] + PP * (c[1] + PP * c[2]);
           int cg[3] = {0, 0, 0};
           for (int d = 0; d < D; d++) cg[d] = bc_cell(g, l - 1, d, 4 * bc3[d] - 5 + c[d]);
           const int32_t sc = g.idx[map_index(g, l - 1, cg[0] >> 3, cg[1] >> 3, cg[2] >> 3)];
-          const int cc = (cg[0] & 7) + 8 * (cg[1] & 7) + (D == 3 ? 64 * (cg[2] & 7) : 0);
+          const int cin = (cg[0] & 7) + 8 * (cg[1] & 7) + (D == 3 ? 64 * (cg[2] & 7) : 0);
 #pragma unroll
           for (int v = 0; v < NV; v++) {
             T val = nan_val<T>();  // an absent coarse block is never read by a prediction of the tree
             if (sc >= 0) {
-              const long long off = ((long long)v * cap + sc) * (D == 2 ? 64 : 512) + cc;
+              const long long off = ((long long)v * cap + sc) * (D == 2 ? 64 : 512) + cin;
               val = A[off];
               if (C0) {
                 const T a0 = C0[off];
@@ -331,8 +342,8 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
       }
       RBox gb;
       for (int d = 0; d < 3; d++) {
-        gb.a[d] = dl[d];
-        gb.b[d] = dh[d];
+        gb.a[d] = d < D ? max(dl[d], M) : 0;
+        gb.b[d] = d < D ? min(dh[d], P - M) : 1;
       }
       for (int q = threadIdx.x; q < gb.count(); q += NT) {
         int x, y, z;
@@ -364,8 +375,8 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
     {
       RBox cb;
       for (int d = 0; d < 3; d++) {
-        cb.a[d] = cdl[d];
-        cb.b[d] = cdh[d];
+        cb.a[d] = d < D ? max(cdl[d], M / 2) : 0;
+        cb.b[d] = d < D ? min(cdh[d], PC - M / 2) : 1;
       }
       for (int q = threadIdx.x; q < cb.count(); q += NT) {
         int x, y, z;
