@@ -113,12 +113,12 @@ struct mrfv_ctx {
 };
 
 // CTAs of the Richardson estimate: about the CTAs a 152-SM part keeps resident (2D:
-// eight per SM; 3D: one, whose patches then fit in L2), at most one per block below
-// the finest level (each CTA holds its own scratch)
+// eight per SM, 3D: two), at most one per block below the finest level (each CTA
+// holds its own scratch)
 int rich_ctas_of(const mrfv_config *cfg, const Geo &g) {
   if (!(cfg->eps_r > 0.0) || g.L < 1) return 0;
   long long n = g.mapoff[g.L];
-  long long want = cfg->dim == 2 ? 1216 : 152;
+  long long want = cfg->dim == 2 ? 1216 : 304;
   return (int)(n < want ? n : want);
 }
 

@@ -42,9 +42,7 @@ struct RichShape {
   static constexpr int NFACE = (D == 2) ? (P + 1) * P : (P + 1) * P * P;  // faces of one direction
   static constexpr int PP = 14;   // level l-1 cells the predictions of the fine patch read (per edge)
   static constexpr int NPP = (D == 2) ? PP * PP : PP * PP * PP;
-  // threads per CTA: 2D 128 (several CTAs per SM), 3D 512 (one CTA per SM, so that
-  // the CTAs' patches stay in L2)
-  static constexpr int NT = (D == 2) ? 128 : 512;
+  static constexpr int NT = (D == 2) ? 128 : 256;  // threads per CTA (2D: eight CTAs per SM, 3D: two)
   // scratch values per CTA: A, S, W, DQ [NV][NP]; CA, CS [NV][NPC]; FL [D][NV][NFACE]; CP [NV][NPP]
   static constexpr long long PER = (long long)NV * (4 * NP + 2 * NPC + NPP) + (long long)D * NV * NFACE;
 };
