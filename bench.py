@@ -218,39 +218,46 @@ def count_steps_to_end(make, t_end: float) -> int:
     return n
 
 
-def matched_l1_2d(m, torch, stream, t_end=0.25):
-    """Adaptive MR (8 levels, 1024^2 finest) vs the uniform 1024^2 solve, both to
-    t_end, each L1(rho) measured against a uniform 2048^2 solve restricted to
-    1024^2 (Section 3); GPU time of each (CUDA events, steps counted beforehand)."""
+def matched_l1_2d(m, torch, stream, t_end=0.25, n=1024, eps=None):
+    """Adaptive MR (finest n^2, level 0 one block) vs the uniform n^2 solve, both
+    to t_end, each L1(rho) measured against a uniform (2n)^2 solve restricted to
+    n^2 (Section 3); GPU time of each (CUDA events, steps counted beforehand)."""
     import numpy as np
 
     P = mi.quadrant_params(SEED)
+    eps = WL["eps"] if eps is None else eps
+    levels = (n // 8).bit_length()  # level 0: one block of 8^2 cells
 
-    def uniform(n):
-        s = m.Solver(dim=2, precision="fp32", levels=1, base_blocks=(n // 8, n // 8, 1), cfl=0.5, t_end=t_end,
+    def uniform(k):
+        s = m.Solver(dim=2, precision="fp32", levels=1, base_blocks=(k // 8, k // 8, 1), cfl=0.5, t_end=t_end,
                      stream=stream)
         s.init_state(mi.IC_QUADRANTS, P)
         return s
 
     def adaptive():
-        s = m.Solver(dim=2, precision="fp32", levels=8, base_blocks=(1, 1, 1), adapt=True, eps=WL["eps"], cfl=0.5,
+        s = m.Solver(dim=2, precision="fp32", levels=levels, base_blocks=(1, 1, 1), adapt=True, eps=eps, cfl=0.5,
                      t_end=t_end, stream=stream)
         s.init_state(mi.IC_QUADRANTS, P)
         return s
 
-    # reference 2048^2, restricted to 1024^2
-    nref = count_steps_to_end(lambda: uniform(2048), t_end)
-    r = uniform(2048)
-    for _ in range(nref):
-        r.step(0.0, sync=False)
+    # reference (2n)^2, restricted to n^2
+    r = uniform(2 * n)
+    nref = 0
+    while nref < 1000000:
+        dt = r.step(0.0, sync=True)
+        nref += 1
+        if dt <= 0.0 or r.stats()["t"] >= t_end * (1 - 1e-12):
+            break
     rho = r.download_level(0)[0][0]
     r.close()
-    ref = rho.reshape(1024, 2, 1024, 2).mean(axis=(1, 3))
-    h2 = (1.0 / 1024) ** 2
-    out = {"t_end": t_end, "reference": "uniform 2048^2 FP32 restricted to 1024^2", "reference_steps": nref}
+    torch.cuda.empty_cache()
+    ref = rho.reshape(n, 2, n, 2).mean(axis=(1, 3))
+    h2 = (1.0 / n) ** 2
+    out = {"t_end": t_end, "finest": n, "levels": levels, "eps": eps,
+           "reference": f"uniform {2 * n}^2 FP32 restricted to {n}^2", "reference_steps": nref}
     # uniform fine
-    nu = count_steps_to_end(lambda: uniform(1024), t_end)
-    u = uniform(1024)
+    nu = count_steps_to_end(lambda: uniform(n), t_end)
+    u = uniform(n)
     ms_u = timed_steps(u, nu, torch, stream)
     l1_u = float(np.abs(u.download_level(0)[0][0] - ref).sum() * h2)
     u.close()
@@ -266,13 +273,29 @@ def matched_l1_2d(m, torch, stream, t_end=0.25):
     out.update({
         "uniform_fine": {"steps": nu, "gpu_ms": ms_u, "l1_rho": l1_u},
         "adaptive": {"steps": na, "gpu_ms": ms_a, "l1_rho": l1_a, "mean_leaf_cells": leaves,
-                     "mesh_compression": leaves / 1024 ** 2},
+                     "mesh_compression": leaves / n ** 2},
         "accuracy_perturbation": abs(l1_u - l1_a) / l1_u,
         "matched": abs(l1_u - l1_a) / l1_u <= 0.05,
         "time_ratio_adaptive_over_uniform": ms_a / ms_u,
-        "overhead_per_leaf": (ms_a / max(1.0, leaves * na)) / (ms_u / (1024 ** 2 * nu)) - 1.0,
+        "overhead_per_leaf": (ms_a / max(1.0, leaves * na)) / (ms_u / (n ** 2 * nu)) - 1.0,
     })
     return out
+
+
+def run_matched2d(args):
+    """The matched-L1 comparison in 2D at a chosen finest resolution (--finest, a
+    power of two): adaptive MR against the uniform solve at that resolution, L1
+    against the uniform solve at twice it (Section 3)."""
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    for eps in [float(x) for x in args.eps_list.split(",")]:
+        print(json.dumps({"case": f"matched2d_fp32_{args.finest}", **matched_l1_2d(m, torch, stream, n=args.finest,
+                                                                                 eps=eps)}), flush=True)
 
 
 def blast3d(m, stream, levels, t_end, proposer=False, eps=1e-3):
@@ -1200,7 +1223,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="adaptive",
                     choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d", "epssweep",
-                             "richardson"],
+                             "richardson", "matched2d"],
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
@@ -1218,6 +1241,8 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--scheme", default="muscl_rk2", choices=["muscl_rk2", "hancock"],
                     help="finite-volume scheme of the uniform case")
+    ap.add_argument("--finest", type=int, default=4096, help="finest resolution of --case matched2d")
+    ap.add_argument("--eps-list", dest="eps_list", default="1e-3", help="MR thresholds of --case matched2d")
     ap.add_argument("--autotune", default="", choices=["", "cache", "sweep"],
                     help="default workload: take the launch shape from the autotuner (cache: the cached "
                          "choice, swept first when absent; sweep: sweep again)")
@@ -1233,6 +1258,8 @@ def main():
         run_matched3d(args)
     elif args.case == "proposer":
         run_proposer(args)
+    elif args.case == "matched2d":
+        run_matched2d(args)
     elif args.case == "richardson":
         if args.dim == 3:
             run_richardson3d(args)
