@@ -218,15 +218,17 @@ def count_steps_to_end(make, t_end: float) -> int:
     return n
 
 
-def matched_l1_2d(m, torch, stream, t_end=0.25, n=1024, eps=None):
+def matched_l1_2d(m, torch, stream, t_end=0.25, n=1024, eps=None, cache=None):
     """Adaptive MR (finest n^2, level 0 one block) vs the uniform n^2 solve, both
     to t_end, each L1(rho) measured against a uniform (2n)^2 solve restricted to
-    n^2 (Section 3); GPU time of each (CUDA events, steps counted beforehand)."""
+    n^2 (Section 3); GPU time of each (CUDA events, steps counted beforehand).
+    `cache` (a dict) keeps the reference and the uniform run between calls."""
     import numpy as np
 
     P = mi.quadrant_params(SEED)
     eps = WL["eps"] if eps is None else eps
     levels = (n // 8).bit_length()  # level 0: one block of 8^2 cells
+    cache = {} if cache is None else cache
 
     def uniform(k):
         s = m.Solver(dim=2, precision="fp32", levels=1, base_blocks=(k // 8, k // 8, 1), cfl=0.5, t_end=t_end,
@@ -241,26 +243,31 @@ def matched_l1_2d(m, torch, stream, t_end=0.25, n=1024, eps=None):
         return s
 
     # reference (2n)^2, restricted to n^2
-    r = uniform(2 * n)
-    nref = 0
-    while nref < 1000000:
-        dt = r.step(0.0, sync=True)
-        nref += 1
-        if dt <= 0.0 or r.stats()["t"] >= t_end * (1 - 1e-12):
-            break
-    rho = r.download_level(0)[0][0]
-    r.close()
-    torch.cuda.empty_cache()
-    ref = rho.reshape(n, 2, n, 2).mean(axis=(1, 3))
+    if "ref" not in cache:
+        r = uniform(2 * n)
+        nref = 0
+        while nref < 1000000:
+            dt = r.step(0.0, sync=True)
+            nref += 1
+            if dt <= 0.0 or r.stats()["t"] >= t_end * (1 - 1e-12):
+                break
+        rho = r.download_level(0)[0][0]
+        r.close()
+        torch.cuda.empty_cache()
+        cache["ref"], cache["nref"] = rho.reshape(n, 2, n, 2).mean(axis=(1, 3)), nref
+    ref, nref = cache["ref"], cache["nref"]
     h2 = (1.0 / n) ** 2
     out = {"t_end": t_end, "finest": n, "levels": levels, "eps": eps,
            "reference": f"uniform {2 * n}^2 FP32 restricted to {n}^2", "reference_steps": nref}
     # uniform fine
-    nu = count_steps_to_end(lambda: uniform(n), t_end)
-    u = uniform(n)
-    ms_u = timed_steps(u, nu, torch, stream)
-    l1_u = float(np.abs(u.download_level(0)[0][0] - ref).sum() * h2)
-    u.close()
+    if "uniform" not in cache:
+        nu = count_steps_to_end(lambda: uniform(n), t_end)
+        u = uniform(n)
+        ms_u = timed_steps(u, nu, torch, stream)
+        l1_u = float(np.abs(u.download_level(0)[0][0] - ref).sum() * h2)
+        u.close()
+        cache["uniform"] = (nu, ms_u, l1_u)
+    nu, ms_u, l1_u = cache["uniform"]
     # adaptive
     na = count_steps_to_end(adaptive, t_end)
     a = adaptive()
@@ -293,9 +300,10 @@ def run_matched2d(args):
     m.build()
     m.load()
     stream = torch.cuda.current_stream()
+    cache = {}
     for eps in [float(x) for x in args.eps_list.split(",")]:
         print(json.dumps({"case": f"matched2d_fp32_{args.finest}", **matched_l1_2d(m, torch, stream, n=args.finest,
-                                                                                 eps=eps)}), flush=True)
+                                                                                 eps=eps, cache=cache)}), flush=True)
 
 
 def blast3d(m, stream, levels, t_end, proposer=False, eps=1e-3):
