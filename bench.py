@@ -218,7 +218,27 @@ def count_steps_to_end(make, t_end: float) -> int:
     return n
 
 
-def matched_l1_2d(m, torch, stream, t_end=0.25, n=1024, eps=None, cache=None):
+def train_proposer(m, make_snap, make_train, nsnap, steps, eps):
+    """Weights of the learned proposer trained on nsnap snapshots of the run
+    make_snap() builds (on a solver make_train() builds, same geometry)."""
+    import numpy as np
+
+    feats, targets = proposer_snapshots(m, None, 0, 0.0, nsnap, make=make_snap, eps=eps)
+    tr = make_train()
+    rng = np.random.default_rng(0)
+    tr.proposer_set_weights((rng.normal(0, 1, m.PROPOSER_NWEIGHTS) * 0.05).astype(np.float32))
+    t0 = time.perf_counter()
+    loss0 = tr.proposer_train(feats, targets, steps=1, lr=3e-3)
+    loss1 = tr.proposer_train(feats, targets, steps=steps, lr=3e-3)
+    sec = time.perf_counter() - t0
+    w = tr.proposer_get_weights()
+    tr.close()
+    return w, {"snapshots": int(feats.shape[0]), "adam_steps": steps, "loss_first": loss0, "loss_last": loss1,
+               "seconds": sec}
+
+
+def matched_l1_2d(m, torch, stream, t_end=0.25, n=1024, eps=None, cache=None, proposer=False, snapshots=60,
+                  train_steps=300):
     """Adaptive MR (finest n^2, level 0 one block) vs the uniform n^2 solve, both
     to t_end, each L1(rho) measured against a uniform (2n)^2 solve restricted to
     n^2 (Section 3); GPU time of each (CUDA events, steps counted beforehand).
@@ -236,10 +256,12 @@ def matched_l1_2d(m, torch, stream, t_end=0.25, n=1024, eps=None, cache=None):
         s.init_state(mi.IC_QUADRANTS, P)
         return s
 
-    def adaptive():
-        s = m.Solver(dim=2, precision="fp32", levels=levels, base_blocks=(1, 1, 1), adapt=True, eps=eps, cfl=0.5,
-                     t_end=t_end, stream=stream)
+    def adaptive(lv=levels, prop=False, w=None):
+        s = m.Solver(dim=2, precision="fp32", levels=lv, base_blocks=(1, 1, 1), adapt=True, eps=eps, cfl=0.5,
+                     t_end=t_end, stream=stream, proposer=prop)
         s.init_state(mi.IC_QUADRANTS, P)
+        if w is not None:
+            s.proposer_set_weights(w)
         return s
 
     # reference (2n)^2, restricted to n^2
@@ -286,6 +308,25 @@ def matched_l1_2d(m, torch, stream, t_end=0.25, n=1024, eps=None, cache=None):
         "time_ratio_adaptive_over_uniform": ms_a / ms_u,
         "overhead_per_leaf": (ms_a / max(1.0, leaves * na)) / (ms_u / (n ** 2 * nu)) - 1.0,
     })
+    if proposer:
+        # the learned proposer, trained on snapshots of the run one level coarser
+        w, tr = train_proposer(m, lambda: adaptive(levels - 1), lambda: adaptive(levels - 1), snapshots,
+                               train_steps, eps)
+        out["proposer_training"] = dict(tr, levels=levels - 1)
+        make = lambda: adaptive(prop=True, w=w)  # noqa: E731
+        na = count_steps_to_end(make, t_end)
+        a = make()
+        st0 = a.stats()
+        ms_p = timed_steps(a, na, torch, stream)
+        st1 = a.stats()
+        l1_p = float(np.abs(a.project_finest()[0] - ref).sum() * h2)
+        a.close()
+        lp = (st1["cell_updates"] - st0["cell_updates"]) / max(1, na)
+        out["adaptive_proposer"] = {"steps": na, "gpu_ms": ms_p, "l1_rho": l1_p, "mean_leaf_cells": lp,
+                                    "mesh_compression": lp / n ** 2,
+                                    "accuracy_perturbation": abs(l1_u - l1_p) / l1_u,
+                                    "matched": abs(l1_u - l1_p) / l1_u <= 0.05,
+                                    "time_ratio_over_uniform": ms_p / ms_u}
     return out
 
 
@@ -302,8 +343,9 @@ def run_matched2d(args):
     stream = torch.cuda.current_stream()
     cache = {}
     for eps in [float(x) for x in args.eps_list.split(",")]:
-        print(json.dumps({"case": f"matched2d_fp32_{args.finest}", **matched_l1_2d(m, torch, stream, n=args.finest,
-                                                                                 eps=eps, cache=cache)}), flush=True)
+        r = matched_l1_2d(m, torch, stream, n=args.finest, eps=eps, cache=cache, proposer=args.proposer2d,
+                          snapshots=args.snapshots, train_steps=args.train_steps)
+        print(json.dumps({"case": f"matched2d_fp32_{args.finest}", **r}), flush=True)
 
 
 def blast3d(m, stream, levels, t_end, proposer=False, eps=1e-3):
@@ -320,17 +362,19 @@ def uniform3d(m, stream, n, t_end):
     return s
 
 
-def proposer_snapshots(m, stream, levels, t_end, nsnap):
-    """(features at t, MR flags at t + dt) pairs from the method's own run."""
+def proposer_snapshots(m, stream, levels, t_end, nsnap, make=None, eps=None):
+    """(features at t, MR flags at t + dt) pairs from the method's own run (the 3D
+    blast, or the solver make() returns)."""
     import numpy as np
 
-    s = blast3d(m, stream, levels, t_end)
+    eps = WL["eps"] if eps is None else eps
+    s = make() if make is not None else blast3d(m, stream, levels, t_end)
     feats, targets = [], []
     for _ in range(nsnap):
-        s.analyse(WL["eps"])
+        s.analyse(eps)
         f = s.proposer_features()
         s.step(0.0, sync=True)
-        s.analyse(WL["eps"])
+        s.analyse(eps)
         feats.append(f)
         targets.append(np.concatenate([s.get_flags(l)[0].ravel() for l in range(s.levels)]))
     s.close()
@@ -1251,6 +1295,7 @@ def main():
                     help="finite-volume scheme of the uniform case")
     ap.add_argument("--finest", type=int, default=4096, help="finest resolution of --case matched2d")
     ap.add_argument("--eps-list", dest="eps_list", default="1e-3", help="MR thresholds of --case matched2d")
+    ap.add_argument("--proposer2d", action="store_true", help="--case matched2d: also the learned proposer")
     ap.add_argument("--autotune", default="", choices=["", "cache", "sweep"],
                     help="default workload: take the launch shape from the autotuner (cache: the cached "
                          "choice, swept first when absent; sweep: sweep again)")
