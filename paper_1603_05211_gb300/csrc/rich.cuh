@@ -139,7 +139,8 @@ __device__ __noinline__ void rich_stage(const T *in, const T *q0, T *out, T *W, 
     __syncthreads();
   }
   // numerical flux of every face of reg, all directions (face f along n lies
-  // between cells f-1 and f; stored at f + (E+1) (t1 + E t2))
+  // between cells f-1 and f; stored compactly over the region's faces,
+  // (f - a_n) + (w_n + 1) ((t1 - a_t1) + w_t1 (t2 - a_t2)), w = the region's widths)
 #pragma unroll 1
   for (int n = 0; n < D; n++) {
     const int t1 = (n == 0) ? 1 : 0, t2 = (n == 2) ? 1 : 2;
@@ -203,7 +204,7 @@ __device__ __noinline__ void rich_stage(const T *in, const T *q0, T *out, T *W, 
         }
         ausmdv<T, D>(n, wl, wr, gam, goverg1, F);
       }
-      const int fi = f + (E + 1) * (u1 + E * u2);
+      const int fi = (f - fb.a[0]) + (fb.b[0] - fb.a[0]) * ((u1 - fb.a[1]) + (fb.b[1] - fb.a[1]) * (u2 - fb.a[2]));
 #pragma unroll
       for (int v = 0; v < NV; v++) FL[(n * NV + v) * NFACE + fi] = F[v];
     }
@@ -213,7 +214,10 @@ __device__ __noinline__ void rich_stage(const T *in, const T *q0, T *out, T *W, 
     int x, y, z;
     reg.at(q, x, y, z);
     const int p = pidx(x, y, z);
-    const int f0 = x + (E + 1) * (y + E * z), f1 = y + (E + 1) * (x + E * z), f2 = z + (E + 1) * (x + E * y);
+    const int rx = x - reg.a[0], ry = y - reg.a[1], rz = z - reg.a[2];
+    const int w0 = reg.b[0] - reg.a[0], w1 = reg.b[1] - reg.a[1], w2 = reg.b[2] - reg.a[2];
+    const int f0 = rx + (w0 + 1) * (ry + w1 * rz), f1 = ry + (w1 + 1) * (rx + w0 * rz),
+              f2 = rz + (w2 + 1) * (rx + w0 * ry);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       T r = lam[0] * (FL[(0 * NV + v) * NFACE + f0 + 1] - FL[(0 * NV + v) * NFACE + f0]);
