@@ -132,6 +132,22 @@ def test_adaptive_mr_fp64(mrfv, seed):
     assert len([x for x in st["leaves"] if x]) >= 2
 
 
+@pytest.mark.parametrize("lts", [False, True])
+def test_adaptive_mr_fp64_100_steps(mrfv, lts):
+    """The FP64 bar over a long run: 100 (coarse) steps of adaptive MR on 4 levels,
+    the tree bit-exact after every step, every cell within 1e-12 at the end,
+    dt bit-exact every step."""
+    s, o = pair(mrfv, 2, 4, (2, 2, 1), adapt=True, lts=lts, params=mi.quadrant_params(5))
+    for k in range(100):
+        run_pair(s, o, 1, lts=lts, adapt_crit=oracle.CRIT_MR)
+        assert_same_tree(s, o)
+        if k % 25 == 24:
+            assert_levels_close(s, o)
+    assert_levels_close(s, o)
+    st = s.stats()
+    assert len([x for x in st["leaves"] if x]) >= 2
+
+
 def test_project_finest_matches_oracle(mrfv):
     s, o = pair(mrfv, 2, 5, (1, 1, 1), adapt=True, params=mi.quadrant_params(8))
     run_pair(s, o, 10, adapt_crit=oracle.CRIT_MR)
