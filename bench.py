@@ -14,7 +14,7 @@ write) between timed steps, outside the timed events.
 --impl reference times the CPU oracle (plain FP64 C) on the host cores, on the
 same workload, each step a full oracle step.
 
-Multi-GPU: the method has no exchange step in this build; N ranks run N
+Multi-GPU: the single-GPU path has no exchange step; N ranks run N
 independent replicas ("scaling": "weak"), no collective on the data path.
 """
 from __future__ import annotations
