@@ -973,6 +973,28 @@ def run_richardson3d(args):
     print(json.dumps(out), flush=True)
 
 
+def run_autotune(args):
+    """The launch-shape autotuner on one workload (a fresh sweep, printed with
+    every candidate's time): --dim 2, the default adaptive 2D MR workload;
+    --dim 3, the 3D blast with --levels3d levels."""
+    import torch
+
+    import paper_1603_05211_gb300 as m
+    from paper_1603_05211_gb300 import autotune
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    if args.dim == 3:
+        make = lambda: blast3d(m, stream, args.levels3d, 0.0)  # noqa: E731
+        name = f"blast3d_fp32_L{args.levels3d - 1}"
+    else:
+        make = lambda: make_solver(m, stream)  # noqa: E731
+        name = WORKLOAD
+    r = autotune.tune(make, steps=20, warmup=5, passes=2)
+    print(json.dumps({"case": "autotune", "workload": name, **r}), flush=True)
+
+
 def run_laxliu(args):
     """The paper's 2D benchmark (Section 4.1, Tables 2-4): Lax-Liu configuration 6
     on [0,1]^2 to t_e = 0.25 with N_I = 160 * 2^(L-7) fixed steps at scale levels
@@ -1275,7 +1297,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="adaptive",
                     choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d", "epssweep",
-                             "richardson", "matched2d"],
+                             "richardson", "matched2d", "autotune"],
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
@@ -1311,6 +1333,8 @@ def main():
         run_matched3d(args)
     elif args.case == "proposer":
         run_proposer(args)
+    elif args.case == "autotune":
+        run_autotune(args)
     elif args.case == "matched2d":
         run_matched2d(args)
     elif args.case == "richardson":
