@@ -973,6 +973,29 @@ def run_richardson3d(args):
     print(json.dumps(out), flush=True)
 
 
+def run_adaptive3d(args):
+    """A short adaptive MR run of the 3D blast (--levels3d levels, CFL steps):
+    --warmup untimed steps, then --steps timed steps of the captured graph (the
+    workload of the 3D launch list)."""
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    s = blast3d(m, stream, args.levels3d, 0.0)
+    for _ in range(max(1, args.warmup)):
+        s.step(0.0, sync=False)
+    st0 = s.stats()
+    ms = timed_steps(s, args.steps, torch, stream)
+    st1 = s.stats()
+    cells = st1["cell_updates"] - st0["cell_updates"]
+    print(json.dumps({"case": f"adaptive3d_fp32_L{args.levels3d - 1}", "steps": args.steps,
+                      "ms_per_step": ms / max(1, args.steps), "leaf_cells_per_step": cells / max(1, args.steps),
+                      "cell_updates_per_s": cells / (ms * 1e-3) if ms > 0 else None}), flush=True)
+
+
 def run_autotune(args):
     """The launch-shape autotuner on one workload (a fresh sweep, printed with
     every candidate's time): --dim 2, the default adaptive 2D MR workload;
@@ -1297,7 +1320,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="adaptive",
                     choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d", "epssweep",
-                             "richardson", "matched2d", "autotune"],
+                             "richardson", "matched2d", "autotune", "adaptive3d"],
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
@@ -1333,6 +1356,8 @@ def main():
         run_matched3d(args)
     elif args.case == "proposer":
         run_proposer(args)
+    elif args.case == "adaptive3d":
+        run_adaptive3d(args)
     elif args.case == "autotune":
         run_autotune(args)
     elif args.case == "matched2d":
