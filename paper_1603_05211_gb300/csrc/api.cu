@@ -243,8 +243,9 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t orctl = L.take(4 * 4);
   const int rctas = rich_ctas_of(cfg, g);
   size_t ormask = L.take(rctas ? maptotal * 8 : 0), orcnt = L.take(8);
-  size_t orscr = L.take(rctas ? (size_t)rctas * (size_t)(cfg->precision == MRFV_FP32 ? rich_scratch_bytes<float>(g.dim)
-                                                                                  : rich_scratch_bytes<double>(g.dim))
+  const int hk = cfg->scheme == MRFV_SCHEME_HANCOCK ? 1 : 0;
+  size_t orscr = L.take(rctas ? (size_t)rctas * (size_t)(cfg->precision == MRFV_FP32 ? rich_scratch_bytes<float>(g.dim, hk)
+                                                                                  : rich_scratch_bytes<double>(g.dim, hk))
                               : 0);
   if (c) {
     c->br_maxside = maxside;

@@ -89,21 +89,23 @@ void launch_rich(const Geo &g, int hancock, const T *A, const T *A0, double thet
   const T th = T(theta);
   if (g.dim == 2) {
     if (hancock)
-      k_rich<T, 2, true><<<ctas, RichShape<2>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
+      k_rich<T, 2, true><<<ctas, RichShape<2, true>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
     else
-      k_rich<T, 2, false><<<ctas, RichShape<2>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
+      k_rich<T, 2, false><<<ctas, RichShape<2, false>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
     k_rich_flags<2><<<grid, 256, 0, st>>>(g, l0, rmask, gflag);
   } else {
     if (hancock)
-      k_rich<T, 3, true><<<ctas, RichShape<3>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
+      k_rich<T, 3, true><<<ctas, RichShape<3, true>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
     else
-      k_rich<T, 3, false><<<ctas, RichShape<3>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
+      k_rich<T, 3, false><<<ctas, RichShape<3, false>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
     k_rich_flags<3><<<grid, 256, 0, st>>>(g, l0, rmask, gflag);
   }
 }
 template <typename T>
-long long rich_scratch_bytes(int dim) {
-  return (dim == 2 ? RichShape<2>::PER : RichShape<3>::PER) * (long long)sizeof(T);
+long long rich_scratch_bytes(int dim, int hancock) {
+  const long long per = dim == 2 ? (hancock ? RichShape<2, true>::PER : RichShape<2, false>::PER)
+                                 : (hancock ? RichShape<3, true>::PER : RichShape<3, false>::PER);
+  return per * (long long)sizeof(T);
 }
 
 template <typename T>
@@ -132,6 +134,6 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
   template void launch_rich<T>(const Geo &, int, const T *, const T *, double, int, const double *, double,     \
                                unsigned long long *, double *, uint8_t *, T *, int, int, unsigned long long *, \
                                cudaStream_t);                                                                   \
-  template long long rich_scratch_bytes<T>(int);
+  template long long rich_scratch_bytes<T>(int, int);
 
 }  // namespace mrfv

@@ -10,10 +10,11 @@
 // an existing block within one fine cell of it has |tau| > eps_r.
 //
 // One CTA per existing block of levels l0..L-1.  The estimate of the block's 4^d
-// coarse cells depends on E only within 8 fine cells of the block (each stage
-// reaches 2 cells; two fine steps, one coarse step), so the CTA gathers that
-// 24^d patch (absent cells predicted from the 14^d coarser cells under it, staged
-// once), restricts it to the 12^d coarse patch, runs the coarse step of 2 dt
+// coarse cells depends on E only within H fine cells of the block (each stage
+// reaches 2 cells; two fine steps and one coarse step: H = 8 for the MR scheme's
+// two-stage steps, 4 for the AMR scheme's one-stage steps), so the CTA gathers
+// that (8 + 2H)^d patch (absent cells predicted from the coarser cells under it,
+// staged once), restricts it to the coarse patch, runs the coarse step of 2 dt
 // and the two fine steps of dt, every stage on a region 2 cells narrower than its
 // input, and compares on the block.  Each stage converts its input to primitives
 // once, evaluates the numerical flux once per face of its region and applies the
@@ -32,15 +33,18 @@
 
 namespace mrfv {
 
-template <int D>
+template <int D, bool HANCOCK>
 struct RichShape {
   static constexpr int NV = D + 2;
-  static constexpr int P = 24;    // fine patch edge: the block and 8 cells on each side
-  static constexpr int PC = 12;   // coarse patch edge
+  // fine cells around the block the estimate reads: 2 per stage, four stages of
+  // the MR scheme, two of the AMR scheme
+  static constexpr int H = HANCOCK ? 4 : 8;
+  static constexpr int P = 8 + 2 * H;  // fine patch edge
+  static constexpr int PC = P / 2;     // coarse patch edge
   static constexpr int NP = (D == 2) ? P * P : P * P * P;
   static constexpr int NPC = (D == 2) ? PC * PC : PC * PC * PC;
   static constexpr int NFACE = (D == 2) ? (P + 1) * P : (P + 1) * P * P;  // faces of one direction
-  static constexpr int PP = 14;   // level l-1 cells the predictions of the fine patch read (per edge)
+  static constexpr int PP = PC + 2;  // level l-1 cells the predictions of the fine patch read (per edge)
   static constexpr int NPP = (D == 2) ? PP * PP : PP * PP * PP;
   static constexpr int NT = (D == 2) ? 128 : 256;  // threads per CTA (2D: eight CTAs per SM, 3D: two)
   // scratch values per CTA: A, S, W, DQ [NV][NP]; CA, CS [NV][NPC]; FL [D][NV][NFACE]; CP [NV][NPP]
@@ -70,7 +74,7 @@ template <typename T, int D, bool HANCOCK>
 __device__ __noinline__ void rich_stage(const T *in, const T *q0, T *out, T *W, T *DQ, T *FL, const RBox &reg,
                                         const int *dl, const int *dh, const T *lam, const T *h, T gam, T gm1,
                                         T goverg1, const int E) {
-  using S = RichShape<D>;
+  using S = RichShape<D, HANCOCK>;
   constexpr int NV = S::NV, NFACE = S::NFACE, NT = S::NT;
   const int NS = (D == 2) ? E * E : E * E * E;  // values per variable of the patch buffers
   auto cl = [&](int x, int d) { return x < dl[d] ? dl[d] : (x >= dh[d] ? dh[d] - 1 : x); };
@@ -263,12 +267,12 @@ __device__ void rich_step(T *A, T *Sb, T *res, T *W, T *DQ, T *FL, int lo1, int 
 // with A0 set, the absent cells of level l0 are predicted from level l0-1
 // interpolated in time, A0 + theta (A - A0) (a remesh inside the level recursion).
 template <typename T, int D, bool HANCOCK>
-__global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__restrict__ A, const T *__restrict__ A0,
+__global__ void __launch_bounds__(RichShape<D, HANCOCK>::NT) k_rich(Geo g, const T *__restrict__ A, const T *__restrict__ A0,
                                                            T theta, int l0, const double *__restrict__ lev,
                                                            double eps_r, unsigned long long *rmask, double *maxdet,
                                                            T *scratch, unsigned long long *nblk) {
-  using S = RichShape<D>;
-  constexpr int NV = S::NV, P = S::P, PC = S::PC, NP = S::NP, NPC = S::NPC, NT = S::NT;
+  using S = RichShape<D, HANCOCK>;
+  constexpr int NV = S::NV, P = S::P, PC = S::PC, NP = S::NP, NPC = S::NPC, NT = S::NT, H = S::H;
   constexpr int NC = (D == 2) ? 16 : 64;  // coarse cells of a block
   __shared__ T cc[NC], tau[NC];
   if (g.L < 1 || l0 > g.L - 1) return;
@@ -280,10 +284,6 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
   T *Sb = Ab + NV * NP, *Wb = Sb + NV * NP, *DQb = Wb + NV * NP;
   T *CA = DQb + NV * NP, *CS = CA + NV * NPC, *FL = CS + NV * NPC, *CP = FL + D * NV * S::NFACE;
   constexpr int PP = S::PP, NPP = S::NPP;
-  // The AMR scheme's stages reach 2 cells per step, one stage each: its estimate
-  // needs only fine cells 4..20 of the patch (coarse 2..10, staged coarser cells
-  // 2..12); the MR scheme's two stages per step need the whole patch.
-  constexpr int M = HANCOCK ? 4 : 0;
   const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0), goverg1 = T(g.gamma / (g.gamma - 1.0));
   for (int it = b + blockIdx.x; it < e; it += gridDim.x) {
     const int s = g.lists[LK_EXIST * cap + it];
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
         dh[d] = P;
         cdh[d] = PC;
       } else {
-        const int og = 8 * bc3[d] - 8, N = g.nb[l][d] * 8;
+        const int og = 8 * bc3[d] - H, N = g.nb[l][d] * 8;
         dl[d] = max(0, -og);
         dh[d] = min(P, N - og);
         cdl[d] = max(0, -og / 2);
@@ -310,22 +310,22 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
     }
     // gather E on the fine patch (domain cells only): the value of the cell's block,
     // or the third-order prediction from level l-1, whose cells the patch needs
-    // (coarse cells 4 bc - 5 .. 4 bc + 8 per dimension, by the boundary rule, in
-    // time-interpolated form at level l0 with A0) are staged in CP first
+    // (coarse cells 4 bc - H/2 - 1 .. 4 bc + 4 + H/2 per dimension, by the boundary
+    // rule, in time-interpolated form at level l0 with A0) are staged in CP first
     {
       const T *C0 = (l == l0) ? A0 : nullptr;
       if (l > 0) {
         RBox pb;
         for (int d = 0; d < 3; d++) {
-          pb.a[d] = d < D ? M / 2 : 0;
-          pb.b[d] = d < D ? PP - M / 2 : 1;
+          pb.a[d] = 0;
+          pb.b[d] = d < D ? PP : 1;
         }
         for (int r = threadIdx.x; r < pb.count(); r += NT) {
           int c[3];
           pb.at(r, c[0], c[1], c[2]);
           const int q = c[0] + PP * (c[1] + PP * c[2]);
           int cg[3] = {0, 0, 0};
-          for (int d = 0; d < D; d++) cg[d] = bc_cell(g, l - 1, d, 4 * bc3[d] - 5 + c[d]);
+          for (int d = 0; d < D; d++) cg[d] = bc_cell(g, l - 1, d, 4 * bc3[d] - H / 2 - 1 + c[d]);
           const int32_t sc = g.idx[map_index(g, l - 1, cg[0] >> 3, cg[1] >> 3, cg[2] >> 3)];
           const int cin = (cg[0] & 7) + 8 * (cg[1] & 7) + (D == 3 ? 64 * (cg[2] & 7) : 0);
 #pragma unroll
@@ -346,13 +346,13 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
       }
       RBox gb;
       for (int d = 0; d < 3; d++) {
-        gb.a[d] = d < D ? max(dl[d], M) : 0;
-        gb.b[d] = d < D ? min(dh[d], P - M) : 1;
+        gb.a[d] = dl[d];
+        gb.b[d] = dh[d];
       }
       for (int q = threadIdx.x; q < gb.count(); q += NT) {
         int x, y, z;
         gb.at(q, x, y, z);
-        const int u[3] = {8 * bc3[0] - 8 + x, 8 * bc3[1] - 8 + y, D == 3 ? 8 * bc3[2] - 8 + z : 0};  // unwrapped
+        const int u[3] = {8 * bc3[0] - H + x, 8 * bc3[1] - H + y, D == 3 ? 8 * bc3[2] - H + z : 0};  // unwrapped
         int f[3] = {0, 0, 0};
         for (int d = 0; d < D; d++) f[d] = bc_cell(g, l, d, u[d]);
         const int32_t sf = g.idx[map_index(g, l, f[0] >> 3, f[1] >> 3, f[2] >> 3)];
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
 #pragma unroll
           for (int v = 0; v < NV; v++) Ab[v * NP + p] = nan_val<T>();
         } else {
-          // parent of the cell in CP: (u >> 1) - (4 bc - 5), i.e. 1..12
+          // parent of the cell in CP: (u >> 1) - (4 bc - H/2 - 1), i.e. 1..PC
           const int px = (x >> 1) + 1, py = (y >> 1) + 1, pz = D == 3 ? (z >> 1) + 1 : 0;
           const T si = (f[0] & 1) ? T(-1) : T(1), sj = (f[1] & 1) ? T(-1) : T(1), sk = (f[2] & 1) ? T(-1) : T(1);
 #pragma unroll
@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
     {
       RBox cb;
       for (int d = 0; d < 3; d++) {
-        cb.a[d] = d < D ? max(cdl[d], M / 2) : 0;
-        cb.b[d] = d < D ? min(cdh[d], PC - M / 2) : 1;
+        cb.a[d] = cdl[d];
+        cb.b[d] = cdh[d];
       }
       for (int q = threadIdx.x; q < cb.count(); q += NT) {
         int x, y, z;
@@ -400,25 +400,27 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
       }
     }
     __syncthreads();
-    // coarse step of 2 dt (cells 2..10 then 4..8 of the coarse patch)
+    // coarse step of 2 dt (MR scheme: cells 2..PC-2 then 4..PC-4 of the coarse
+    // patch; AMR scheme: its one stage on 2..PC-2, the block's coarse cells)
     double dxc[3], dxf[3];
     for (int d = 0; d < 3; d++) {
       dxf[d] = g.dx[l][d];
       dxc[d] = 2.0 * g.dx[l][d];
     }
-    rich_step<T, D, HANCOCK>(CA, CS, CS, Wb, DQb, FL, 2, 10, 4, 8, cdl, cdh, 2.0 * dtl, dxc, gam, gm1, goverg1, PC);
+    rich_step<T, D, HANCOCK>(CA, CS, CS, Wb, DQb, FL, 2, PC - 2, HANCOCK ? 2 : 4, HANCOCK ? PC - 2 : PC - 4, cdl, cdh,
+                             2.0 * dtl, dxc, gam, gm1, goverg1, PC);
     const T *Cres = HANCOCK ? CS : CA;
     for (int q = threadIdx.x; q < NC; q += NT) {
       const int x = q & 3, y = (q >> 2) & 3, z = q >> 4;
-      cc[q] = Cres[(4 + x) + PC * ((4 + y) + PC * (D == 3 ? 4 + z : 0))];
+      cc[q] = Cres[(H / 2 + x) + PC * ((H / 2 + y) + PC * (D == 3 ? H / 2 + z : 0))];
     }
-    // two fine steps of dt (regions 2..22, 4..20, 6..18, 8..16; Hancock 6..18, 8..16)
+    // two fine steps of dt (regions 2..P-2, 4..P-4, 6..P-6, 8..P-8; AMR scheme 2..P-2, 4..P-4)
     if constexpr (HANCOCK) {
-      rich_step<T, D, true>(Ab, Sb, Sb, Wb, DQb, FL, 0, 0, 6, 18, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
-      rich_step<T, D, true>(Sb, Ab, Ab, Wb, DQb, FL, 0, 0, 8, 16, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
+      rich_step<T, D, true>(Ab, Sb, Sb, Wb, DQb, FL, 0, 0, 2, P - 2, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
+      rich_step<T, D, true>(Sb, Ab, Ab, Wb, DQb, FL, 0, 0, 4, P - 4, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
     } else {
-      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 2, 22, 4, 20, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
-      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 6, 18, 8, 16, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
+      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 2, P - 2, 4, P - 4, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
+      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 6, P - 6, 8, P - 8, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
     }
     // restrict the fine result on the block and compare
     for (int q = threadIdx.x; q < NC; q += NT) {
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(RichShape<D>::NT) k_rich(Geo g, const T *__res
       T sum = T(0);
 #pragma unroll
       for (int k = 0; k < (D == 3 ? 8 : 4); k++) {
-        const int p = (8 + 2 * x + (k & 1)) + P * ((8 + 2 * y + ((k >> 1) & 1)) + P * (D == 3 ? 8 + 2 * z + (k >> 2) : 0));
+        const int p = (H + 2 * x + (k & 1)) + P * ((H + 2 * y + ((k >> 1) & 1)) + P * (D == 3 ? H + 2 * z + (k >> 2) : 0));
         const T val = Ab[p];
         sum = k == 0 ? val : sum + val;
       }
