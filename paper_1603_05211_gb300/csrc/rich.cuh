@@ -73,30 +73,33 @@ struct RBox {
 template <typename T, int D, bool HANCOCK>
 __device__ __noinline__ void rich_stage(const T *in, const T *q0, T *out, T *W, T *DQ, T *FL, const RBox &reg,
                                         const int *dl, const int *dh, const T *lam, const T *h, T gam, T gm1,
-                                        T goverg1, const int E) {
+                                        T goverg1, const int E, const bool w_ready, const bool w_next) {
   using S = RichShape<D, HANCOCK>;
   constexpr int NV = S::NV, NFACE = S::NFACE, NT = S::NT;
   const int NS = (D == 2) ? E * E : E * E * E;  // values per variable of the patch buffers
   auto cl = [&](int x, int d) { return x < dl[d] ? dl[d] : (x >= dh[d] ? dh[d] - 1 : x); };
   auto pidx = [&](int x, int y, int z) { return x + E * (y + E * z); };
-  // primitives of the input on reg widened by 2, inside the domain
-  RBox wb;
-  for (int d = 0; d < 3; d++) {
-    wb.a[d] = d < D ? max(reg.a[d] - 2, dl[d]) : 0;
-    wb.b[d] = d < D ? min(reg.b[d] + 2, dh[d]) : 1;
-  }
-  for (int q = threadIdx.x; q < wb.count(); q += NT) {
-    int x, y, z;
-    wb.at(q, x, y, z);
-    const int p = pidx(x, y, z);
-    T Q[NV], w[NV];
+  // primitives of the input on reg widened by 2, inside the domain (unless the
+  // phase that produced the input wrote them: w_ready)
+  if (!w_ready) {
+    RBox wb;
+    for (int d = 0; d < 3; d++) {
+      wb.a[d] = d < D ? max(reg.a[d] - 2, dl[d]) : 0;
+      wb.b[d] = d < D ? min(reg.b[d] + 2, dh[d]) : 1;
+    }
+    for (int q = threadIdx.x; q < wb.count(); q += NT) {
+      int x, y, z;
+      wb.at(q, x, y, z);
+      const int p = pidx(x, y, z);
+      T Q[NV], w[NV];
 #pragma unroll
-    for (int v = 0; v < NV; v++) Q[v] = in[v * NS + p];
-    cons_to_prim<T, D>(Q, gm1, w);
+      for (int v = 0; v < NV; v++) Q[v] = in[v * NS + p];
+      cons_to_prim<T, D>(Q, gm1, w);
 #pragma unroll
-    for (int v = 0; v < NV; v++) W[v * NS + p] = w[v];
+      for (int v = 0; v < NV; v++) W[v * NS + p] = w[v];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if constexpr (HANCOCK) {
     // half-step increment of every cell a face of reg touches (the ring of ghost
     // cells at a wall included: their slopes come from clamped neighbours)
@@ -222,12 +225,20 @@ __device__ __noinline__ void rich_stage(const T *in, const T *q0, T *out, T *W, 
     const int w0 = reg.b[0] - reg.a[0], w1 = reg.b[1] - reg.a[1], w2 = reg.b[2] - reg.a[2];
     const int f0 = rx + (w0 + 1) * (ry + w1 * rz), f1 = ry + (w1 + 1) * (rx + w0 * rz),
               f2 = rz + (w2 + 1) * (rx + w0 * ry);
+    T o[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       T r = lam[0] * (FL[(0 * NV + v) * NFACE + f0 + 1] - FL[(0 * NV + v) * NFACE + f0]);
       r = r + lam[1] * (FL[(1 * NV + v) * NFACE + f1 + 1] - FL[(1 * NV + v) * NFACE + f1]);
       if (D == 3) r = r + lam[2] * (FL[(2 * NV + v) * NFACE + f2 + 1] - FL[(2 * NV + v) * NFACE + f2]);
-      out[v * NS + p] = q0[v * NS + p] - r;
+      o[v] = q0[v * NS + p] - r;
+      out[v * NS + p] = o[v];
+    }
+    if (w_next) {  // the next stage's primitives: its input region is this stage's output region
+      T w[NV];
+      cons_to_prim<T, D>(o, gm1, w);
+#pragma unroll
+      for (int v = 0; v < NV; v++) W[v * NS + p] = w[v];
     }
   }
   __syncthreads();
@@ -237,9 +248,12 @@ __device__ __noinline__ void rich_stage(const T *in, const T *q0, T *out, T *W, 
 // of its row (cells per dimension, clipped to the domain).  The result is in A
 // (RK2: both stages; the second writes A in place) or, for the one Hancock stage,
 // in `res`.
+// w_ready: W already holds the primitives of A's input region; w_next: leave the
+// primitives of the step's result in W for the next step.
 template <typename T, int D, bool HANCOCK>
 __device__ void rich_step(T *A, T *Sb, T *res, T *W, T *DQ, T *FL, int lo1, int hi1, int lo2, int hi2,
-                          const int *dl, const int *dh, double dt, const double *dx, T gam, T gm1, T goverg1, int E) {
+                          const int *dl, const int *dh, double dt, const double *dx, T gam, T gm1, T goverg1, int E,
+                          bool w_ready, bool w_next) {
   T lam1[3], lam2[3], hh[3];
   for (int d = 0; d < 3; d++) {
     lam1[d] = T((0.5 * dt) / dx[d]);
@@ -255,10 +269,13 @@ __device__ void rich_step(T *A, T *Sb, T *res, T *W, T *DQ, T *FL, int lo1, int 
     return b;
   };
   if constexpr (HANCOCK) {
-    rich_stage<T, D, true>(A, A, res, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1, E);
+    rich_stage<T, D, true>(A, A, res, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1, E, w_ready,
+                           w_next);
   } else {
-    rich_stage<T, D, false>(A, A, Sb, W, DQ, FL, box(lo1, hi1), dl, dh, lam1, hh, gam, gm1, goverg1, E);
-    rich_stage<T, D, false>(Sb, A, A, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1, E);
+    rich_stage<T, D, false>(A, A, Sb, W, DQ, FL, box(lo1, hi1), dl, dh, lam1, hh, gam, gm1, goverg1, E, w_ready,
+                            true);
+    rich_stage<T, D, false>(Sb, A, A, W, DQ, FL, box(lo2, hi2), dl, dh, lam2, hh, gam, gm1, goverg1, E, true,
+                            w_next);
   }
 }
 
@@ -386,6 +403,7 @@ __global__ void __launch_bounds__(RichShape<D, HANCOCK>::NT) k_rich(Geo g, const
         int x, y, z;
         cb.at(q, x, y, z);
         const int pc = x + PC * (y + PC * z);
+        T Q[NV], w[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
           T sum = T(0);
@@ -395,8 +413,12 @@ __global__ void __launch_bounds__(RichShape<D, HANCOCK>::NT) k_rich(Geo g, const
             const T val = Ab[v * NP + p];
             sum = k == 0 ? val : sum + val;
           }
-          CA[v * NPC + pc] = sum * T(D == 3 ? 0.125 : 0.25);
+          Q[v] = sum * T(D == 3 ? 0.125 : 0.25);
+          CA[v * NPC + pc] = Q[v];
         }
+        cons_to_prim<T, D>(Q, gm1, w);  // the first coarse stage's primitives (its input region)
+#pragma unroll
+        for (int v = 0; v < NV; v++) Wb[v * NPC + pc] = w[v];
       }
     }
     __syncthreads();
@@ -408,7 +430,7 @@ __global__ void __launch_bounds__(RichShape<D, HANCOCK>::NT) k_rich(Geo g, const
       dxc[d] = 2.0 * g.dx[l][d];
     }
     rich_step<T, D, HANCOCK>(CA, CS, CS, Wb, DQb, FL, 2, PC - 2, HANCOCK ? 2 : 4, HANCOCK ? PC - 2 : PC - 4, cdl, cdh,
-                             2.0 * dtl, dxc, gam, gm1, goverg1, PC);
+                             2.0 * dtl, dxc, gam, gm1, goverg1, PC, true, false);
     const T *Cres = HANCOCK ? CS : CA;
     for (int q = threadIdx.x; q < NC; q += NT) {
       const int x = q & 3, y = (q >> 2) & 3, z = q >> 4;
@@ -416,11 +438,15 @@ __global__ void __launch_bounds__(RichShape<D, HANCOCK>::NT) k_rich(Geo g, const
     }
     // two fine steps of dt (regions 2..P-2, 4..P-4, 6..P-6, 8..P-8; AMR scheme 2..P-2, 4..P-4)
     if constexpr (HANCOCK) {
-      rich_step<T, D, true>(Ab, Sb, Sb, Wb, DQb, FL, 0, 0, 2, P - 2, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
-      rich_step<T, D, true>(Sb, Ab, Ab, Wb, DQb, FL, 0, 0, 4, P - 4, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
+      rich_step<T, D, true>(Ab, Sb, Sb, Wb, DQb, FL, 0, 0, 2, P - 2, dl, dh, dtl, dxf, gam, gm1, goverg1, P, false,
+                            true);
+      rich_step<T, D, true>(Sb, Ab, Ab, Wb, DQb, FL, 0, 0, 4, P - 4, dl, dh, dtl, dxf, gam, gm1, goverg1, P, true,
+                            false);
     } else {
-      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 2, P - 2, 4, P - 4, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
-      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 6, P - 6, 8, P - 8, dl, dh, dtl, dxf, gam, gm1, goverg1, P);
+      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 2, P - 2, 4, P - 4, dl, dh, dtl, dxf, gam, gm1, goverg1, P,
+                             false, true);
+      rich_step<T, D, false>(Ab, Sb, Ab, Wb, DQb, FL, 6, P - 6, 8, P - 8, dl, dh, dtl, dxf, gam, gm1, goverg1, P,
+                             true, false);
     }
     // restrict the fine result on the block and compare
     for (int q = threadIdx.x; q < NC; q += NT) {
