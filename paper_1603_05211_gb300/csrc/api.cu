@@ -113,8 +113,8 @@ struct mrfv_ctx {
 };
 
 // CTAs of the Richardson estimate: about the CTAs a 152-SM part keeps resident (2D:
-// eight per SM, 3D: two), at most one per block below the finest level (each CTA
-// holds its own scratch)
+// eight per SM, patches in shared memory; 3D: two, each with its own area of the
+// global scratch), at most one per block below the finest level
 int rich_ctas_of(const mrfv_config *cfg, const Geo &g) {
   if (!(cfg->eps_r > 0.0) || g.L < 1) return 0;
   long long n = g.mapoff[g.L];
@@ -846,6 +846,10 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   c->fv_kinds = 0;
   c->gkinds[0] = c->gkinds[1] = 0;
   prepare_br();
+  if (c->rich_ctas) {
+    if (c->prec == MRFV_FP32) prepare_rich<float>();
+    else prepare_rich<double>();
+  }
   c->fvp_occupancy = c->prec == MRFV_FP32 ? fvp_ctas_per_sm<float>(cfg->dim) : fvp_ctas_per_sm<double>(cfg->dim);
   c->fvpgrid = c->nsm * c->fvp_occupancy;
   c->fvp_bpc = c->prec == MRFV_FP32 ? fvp_blocks_per_cta<float>(cfg->dim) : fvp_blocks_per_cta<double>(cfg->dim);

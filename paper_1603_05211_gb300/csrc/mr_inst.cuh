@@ -88,10 +88,11 @@ void launch_rich(const Geo &g, int hancock, const T *A, const T *A0, double thet
                  int grid, unsigned long long *nblk, cudaStream_t st) {
   const T th = T(theta);
   if (g.dim == 2) {
+    constexpr size_t sh = RichShape<2, true>::PER * sizeof(T), sm = RichShape<2, false>::PER * sizeof(T);
     if (hancock)
-      k_rich<T, 2, true><<<ctas, RichShape<2, true>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
+      k_rich<T, 2, true><<<ctas, RichShape<2, true>::NT, sh, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
     else
-      k_rich<T, 2, false><<<ctas, RichShape<2, false>::NT, 0, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
+      k_rich<T, 2, false><<<ctas, RichShape<2, false>::NT, sm, st>>>(g, A, A0, th, l0, lev, eps_r, rmask, maxdet, scratch, nblk);
     k_rich_flags<2><<<grid, 256, 0, st>>>(g, l0, rmask, gflag);
   } else {
     if (hancock)
@@ -101,11 +102,20 @@ void launch_rich(const Geo &g, int hancock, const T *A, const T *A0, double thet
     k_rich_flags<3><<<grid, 256, 0, st>>>(g, l0, rmask, gflag);
   }
 }
+// global scratch per CTA (2D patches live in shared memory: none)
 template <typename T>
 long long rich_scratch_bytes(int dim, int hancock) {
-  const long long per = dim == 2 ? (hancock ? RichShape<2, true>::PER : RichShape<2, false>::PER)
-                                 : (hancock ? RichShape<3, true>::PER : RichShape<3, false>::PER);
-  return per * (long long)sizeof(T);
+  if (dim == 2) return 0;
+  return (hancock ? RichShape<3, true>::PER : RichShape<3, false>::PER) * (long long)sizeof(T);
+}
+// the 2D estimate's dynamic shared memory above the default limit (once, before
+// any graph capture)
+template <typename T>
+void prepare_rich() {
+  cudaFuncSetAttribute(k_rich<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(RichShape<2, true>::PER * sizeof(T)));
+  cudaFuncSetAttribute(k_rich<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(RichShape<2, false>::PER * sizeof(T)));
 }
 
 template <typename T>
@@ -134,6 +144,7 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
   template void launch_rich<T>(const Geo &, int, const T *, const T *, double, int, const double *, double,     \
                                unsigned long long *, double *, uint8_t *, T *, int, int, unsigned long long *, \
                                cudaStream_t);                                                                   \
-  template long long rich_scratch_bytes<T>(int, int);
+  template long long rich_scratch_bytes<T>(int, int);                                                      \
+  template void prepare_rich<T>();
 
 }  // namespace mrfv

@@ -20,7 +20,8 @@
 // once, evaluates the numerical flux once per face of its region and applies the
 // update in the order of the cell update of the stage kernels.  At a
 // transmissive wall the reads are clamped to the domain, as the boundary rule
-// does.  Patches live in a per-CTA scratch area of global memory.
+// does.  2D patches live in shared memory, 3D ones in a per-CTA area of global
+// memory.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -297,7 +298,10 @@ __global__ void __launch_bounds__(RichShape<D, HANCOCK>::NT) k_rich(Geo g, const
   list_range(g, LK_EXIST, l0, g.L - 1, b, e);
   if (nblk && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(nblk, (unsigned long long)(e - b));
   const long long cap = g.cap;
-  T *Ab = scratch + (long long)blockIdx.x * S::PER;
+  // 2D patches fit in shared memory (dynamic, S::PER values); 3D ones use the
+  // CTA's area of the global scratch
+  extern __shared__ __align__(16) unsigned char rich_smem[];
+  T *Ab = (D == 2) ? reinterpret_cast<T *>(rich_smem) : scratch + (long long)blockIdx.x * S::PER;
   T *Sb = Ab + NV * NP, *Wb = Sb + NV * NP, *DQb = Wb + NV * NP;
   T *CA = DQb + NV * NP, *CS = CA + NV * NPC, *FL = CS + NV * NPC, *CP = FL + D * NV * S::NFACE;
   constexpr int PP = S::PP, NPP = S::NPP;
