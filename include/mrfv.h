@@ -356,7 +356,9 @@ int mrfv_proposer_train(mrfv_ctx *ctx, const float *feat, const uint8_t *target,
      stream  cudaStream_t (NULL = legacy default stream); the call only enqueues.
    The first call on a device looks up the scratch array's device address (with
    that device current) and caches it: make that first call before any stream
-   capture.  Every call shares the scratch array, which keeps the last call's
+   capture.  The cached address does not survive cudaDeviceReset or any other
+   teardown of the device's primary context: do not call this entry point after
+   one in the same process.  Every call shares the scratch array, which keeps the last call's
    contents; calls that overlap on the GPU (on different streams, or from several
    threads) race on it and must be serialised by the caller. */
 #define MRFV_NOALLOC_DT_TILE_CELLS 4096

@@ -112,9 +112,10 @@ struct mrfv_ctx {
   int rich_ctas;        // CTAs of the Richardson estimate (0: off)
 };
 
-// CTAs of the Richardson estimate: about the CTAs a 152-SM part keeps resident (2D:
-// eight per SM, patches in shared memory; 3D: two, each with its own area of the
-// global scratch), at most one per block below the finest level
+// CTAs of the Richardson estimate, at most one per block below the finest level.
+// 3D: two per SM of a 152-SM part, each with its own area of the global scratch
+// (the arena is sized for these).  2D: an upper bound here; mrfv_create lowers it
+// to the CTAs the SMs hold with the patch's shared memory.
 int rich_ctas_of(const mrfv_config *cfg, const Geo &g) {
   if (!(cfg->eps_r > 0.0) || g.L < 1) return 0;
   long long n = g.mapoff[g.L];
@@ -847,8 +848,18 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   c->gkinds[0] = c->gkinds[1] = 0;
   prepare_br();
   if (c->rich_ctas) {
-    if (c->prec == MRFV_FP32) prepare_rich<float>();
-    else prepare_rich<double>();
+    int per_sm = 0;
+    const int h = cfg->scheme == MRFV_SCHEME_HANCOCK ? 1 : 0;
+    cudaError_t e = c->prec == MRFV_FP32 ? prepare_rich<float>(cfg->dim, h, &per_sm)
+                                         : prepare_rich<double>(cfg->dim, h, &per_sm);
+    if (e != cudaSuccess) {
+      std::string msg = std::string("Richardson estimate: shared-memory set-up failed: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      mrfv_destroy(c);
+      return fail(nullptr, MRFV_ERR_CUDA, msg);
+    }
+    // 2D: the CTAs the SMs hold at once with the patch in shared memory
+    if (cfg->dim == 2 && per_sm > 0 && (long long)per_sm * c->nsm < c->rich_ctas) c->rich_ctas = per_sm * c->nsm;
   }
   c->fvp_occupancy = c->prec == MRFV_FP32 ? fvp_ctas_per_sm<float>(cfg->dim) : fvp_ctas_per_sm<double>(cfg->dim);
   c->fvpgrid = c->nsm * c->fvp_occupancy;

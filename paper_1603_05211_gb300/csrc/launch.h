@@ -35,7 +35,7 @@ template <typename T> void launch_rich(const Geo &, int hancock, const T *A, con
                                        uint8_t *gflag, T *scratch, int ctas, int grid, unsigned long long *nblk,
                                        cudaStream_t);
 template <typename T> long long rich_scratch_bytes(int dim, int hancock);
-template <typename T> void prepare_rich();
+template <typename T> cudaError_t prepare_rich(int dim, int hancock, int *per_sm);
 template <typename T> void launch_project_level(const Geo &, int l, const T *A, const double *coarse, double *out, cudaStream_t);
 // finite-volume stage and CFL reduction (fv_f32.cu, fv_f64.cu)
 template <typename T> void launch_fv(const Geo &, const FVArgs<T> &, bool split, int grid, cudaStream_t);

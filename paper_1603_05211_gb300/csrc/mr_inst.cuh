@@ -109,13 +109,24 @@ long long rich_scratch_bytes(int dim, int hancock) {
   return (hancock ? RichShape<3, true>::PER : RichShape<3, false>::PER) * (long long)sizeof(T);
 }
 // the 2D estimate's dynamic shared memory above the default limit (once, before
-// any graph capture)
+// any graph capture); *per_sm = CTAs of the scheme's 2D kernel one SM holds with
+// that shared memory (0 in 3D, whose patches live in global scratch)
 template <typename T>
-void prepare_rich() {
-  cudaFuncSetAttribute(k_rich<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(RichShape<2, true>::PER * sizeof(T)));
-  cudaFuncSetAttribute(k_rich<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(RichShape<2, false>::PER * sizeof(T)));
+cudaError_t prepare_rich(int dim, int hancock, int *per_sm) {
+  *per_sm = 0;
+  cudaError_t e = cudaFuncSetAttribute(k_rich<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(RichShape<2, true>::PER * sizeof(T)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_rich<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(RichShape<2, false>::PER * sizeof(T)));
+  if (e != cudaSuccess || dim != 2) return e;
+  if (hancock)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_rich<T, 2, true>, RichShape<2, true>::NT,
+                                                      RichShape<2, true>::PER * sizeof(T));
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_rich<T, 2, false>, RichShape<2, false>::NT,
+                                                      RichShape<2, false>::PER * sizeof(T));
+  return e;
 }
 
 template <typename T>
@@ -145,6 +156,6 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
                                unsigned long long *, double *, uint8_t *, T *, int, int, unsigned long long *, \
                                cudaStream_t);                                                                   \
   template long long rich_scratch_bytes<T>(int, int);                                                      \
-  template void prepare_rich<T>();
+  template cudaError_t prepare_rich<T>(int, int, int *);
 
 }  // namespace mrfv

@@ -13,7 +13,6 @@
 #include <math.h>
 #include <stdint.h>
 
-#include <atomic>
 #include <mutex>
 
 #include "mrfv.h"
@@ -115,7 +114,9 @@ __global__ void k_dt_tiles_final(const double *partial, int ntiles, double cfl, 
 }
 
 // Device address of g_dt_partial for the current device, looked up once per
-// device (the array's name is only a host-side stand-in in host code).
+// device (the array's name is only a host-side stand-in in host code).  The
+// cached address belongs to the device's primary context: it does not survive
+// cudaDeviceReset (or any other teardown of that context) in this process.
 int partial_for_current_device(double **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -142,7 +143,13 @@ extern "C" int mrfv_cfl_dt_noalloc(int dim, int precision, const void *state, in
   if ((dim != 2 && dim != 3) || (precision != MRFV_FP32 && precision != MRFV_FP64) || !state || !dx || !dt_out)
     return MRFV_ERR_ARG;
   if (n0 < 1 || n1 < 1 || n2 < 1 || (dim == 2 && n2 != 1) || !(gamma > 1.0) || !(cfl > 0.0)) return MRFV_ERR_ARG;
-  long long ncell = (long long)n0 * n1 * n2;
+  // the cell count, checked against the maximum before each multiply (no overflow)
+  const int64_t maxc = MRFV_NOALLOC_DT_MAX_CELLS;
+  if (n0 > maxc || n1 > maxc || n2 > maxc) return MRFV_ERR_ARG;
+  if (n1 > maxc / n0) return MRFV_ERR_ARG;
+  long long ncell = (long long)n0 * n1;
+  if (n2 > maxc / ncell) return MRFV_ERR_ARG;
+  ncell *= n2;
   long long ntiles = (ncell + kTileCells - 1) / kTileCells;
   if (ntiles > kMaxTiles) return MRFV_ERR_ARG;  // more than MRFV_NOALLOC_DT_MAX_CELLS cells
   double *partial = nullptr;

@@ -47,7 +47,8 @@ struct RichShape {
   static constexpr int NFACE = (D == 2) ? (P + 1) * P : (P + 1) * P * P;  // faces of one direction
   static constexpr int PP = PC + 2;  // level l-1 cells the predictions of the fine patch read (per edge)
   static constexpr int NPP = (D == 2) ? PP * PP : PP * PP * PP;
-  static constexpr int NT = (D == 2) ? 128 : 256;  // threads per CTA (2D: eight CTAs per SM, 3D: two)
+  static constexpr int NT = (D == 2) ? 128 : 256;  // threads per CTA (2D: as many per SM as the
+                                                   // patch's shared memory allows; 3D: two)
   // scratch values per CTA: A, S, W, DQ [NV][NP]; CA, CS [NV][NPC]; FL [D][NV][NFACE]; CP [NV][NPP]
   static constexpr long long PER = (long long)NV * (4 * NP + 2 * NPC + NPP) + (long long)D * NV * NFACE;
 };
