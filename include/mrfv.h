@@ -335,6 +335,19 @@ int mrfv_proposer_infer(mrfv_ctx *ctx, float *logits, int64_t n);
    current tree).  *loss = loss of the last step. */
 int mrfv_proposer_train(mrfv_ctx *ctx, const float *feat, const uint8_t *target, int nsnap, int steps, float lr,
                         double *loss);
+/* The gradient the next Adam step of mrfv_proposer_train would take, without
+   taking it: the same forward and backward kernels on the same snapshots
+   (feat[nsnap][3][positions], target[nsnap][positions]), the loss summed over
+   the snapshots and over the positions of level >= 1 with an existing parent
+   (current tree), divided by nsnap * (positions of levels >= 1).  grad: host,
+   n = MRFV_PROPOSER_NWEIGHTS floats in the weight layout above; *loss (host,
+   optional) its loss.  Weights and Adam state are left unchanged. */
+int mrfv_proposer_grad(mrfv_ctx *ctx, const float *feat, const uint8_t *target, int nsnap, float *grad, int64_t n,
+                       double *loss);
+/* The BF16 layer inputs of the second and third convolution of the last
+   mrfv_proposer_infer (the ReLU outputs of layers 1 and 2, rounded to
+   bfloat16), widened to float: h1, h2 host [positions][16] (n = 16 * positions). */
+int mrfv_proposer_activations(mrfv_ctx *ctx, float *h1, float *h2, int64_t n);
 
 /* Allocation-free CFL time step of a caller-owned dense array of cells (no
    counterpart in the paper).  Some callers cannot call cudaMalloc: work issued

@@ -109,6 +109,9 @@ SIGNATURES = {
     "mrfv_proposer_infer": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I64]),
     "mrfv_proposer_train": (_I, [_P, ctypes.POINTER(ctypes.c_float), _U8, _I, _I, ctypes.c_float,
                                  ctypes.POINTER(ctypes.c_double)]),
+    "mrfv_proposer_grad": (_I, [_P, ctypes.POINTER(ctypes.c_float), _U8, _I, ctypes.POINTER(ctypes.c_float), _I64,
+                                ctypes.POINTER(ctypes.c_double)]),
+    "mrfv_proposer_activations": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _I64]),
 }
 PROPOSER_NWEIGHTS = 8673
 
@@ -362,6 +365,26 @@ class Solver:
         a = np.empty(self.positions, dtype=np.float32)
         self._check(self.lib.mrfv_proposer_infer(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
         return a
+
+    def proposer_grad(self, feats, targets):
+        """(loss, gradient) of the next training step, without the step."""
+        f = np.ascontiguousarray(feats, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.uint8)
+        g = np.empty(PROPOSER_NWEIGHTS, np.float32)
+        loss = ctypes.c_double(0.0)
+        self._check(self.lib.mrfv_proposer_grad(self._h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _u8(t),
+                                                f.shape[0], g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), g.size,
+                                                ctypes.byref(loss)))
+        return loss.value, g
+
+    def proposer_activations(self):
+        """BF16 inputs of layers 2 and 3 of the last inference, [positions][16] each."""
+        n = self.positions()
+        h1 = np.empty((n, 16), np.float32)
+        h2 = np.empty((n, 16), np.float32)
+        self._check(self.lib.mrfv_proposer_activations(self._h, h1.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                       h2.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), h1.size))
+        return h1, h2
 
     def proposer_train(self, feats, targets, steps: int, lr: float) -> float:
         f = np.ascontiguousarray(feats, dtype=np.float32)

@@ -1382,7 +1382,7 @@ int mrfv_proposer_train(mrfv_ctx *c, const float *feat, const uint8_t *target, i
   for (int k = 0; k < steps && rc == MRFV_OK; k++) {
     cudaMemsetAsync(c->ploss, 0, 8, c->st);
     launch_prop_train_step(c->g, df, dt, nsnap, c->pblob, c->pgrad, c->pm1, c->pm2, ++c->adam_t, lr, c->pwork,
-                           c->ploss, c->st);
+                           c->ploss, 1, c->st);
     rc = check_launch(c, "mrfv_proposer_train");
     if (rc == MRFV_OK && k == steps - 1) {
       rc = check_device(c, "mrfv_proposer_train");
@@ -1394,6 +1394,54 @@ int mrfv_proposer_train(mrfv_ctx *c, const float *feat, const uint8_t *target, i
   cudaFree(df);
   cudaFree(dt);
   if (loss) *loss = last;
+  return rc;
+}
+
+int mrfv_proposer_grad(mrfv_ctx *c, const float *feat, const uint8_t *target, int nsnap, float *grad, int64_t n,
+                       double *loss) {
+  if (!c || !feat || !target || !grad || nsnap < 1 || n != MRFV_PROPOSER_NWEIGHTS)
+    return fail(c, MRFV_ERR_ARG, "proposer_grad: arguments");
+  if (!c->initialized || !c->has_weights) return fail(c, MRFV_ERR_STATE, "proposer_grad before init / weights");
+  long long np = c->maptotal;
+  float *df = nullptr;
+  uint8_t *dt = nullptr;
+  if (cudaMalloc(&df, (size_t)nsnap * 3 * np * 4) != cudaSuccess || cudaMalloc(&dt, (size_t)nsnap * np) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(df);
+    return fail(c, MRFV_ERR_CUDA, "proposer_grad: staging allocation");
+  }
+  cudaMemcpy(df, feat, (size_t)nsnap * 3 * np * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dt, target, (size_t)nsnap * np, cudaMemcpyHostToDevice);
+  cudaMemsetAsync(c->ploss, 0, 8, c->st);
+  launch_prop_train_step(c->g, df, dt, nsnap, c->pblob, c->pgrad, c->pm1, c->pm2, c->adam_t, 0.f, c->pwork, c->ploss,
+                         0, c->st);
+  int rc = check_launch(c, "mrfv_proposer_grad");
+  if (rc == MRFV_OK) rc = check_device(c, "mrfv_proposer_grad");
+  if (rc == MRFV_OK) {
+    cudaMemcpy(grad, c->pgrad, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    if (loss) cudaMemcpy(loss, c->ploss, 8, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(df);
+  cudaFree(dt);
+  return rc;
+}
+
+int mrfv_proposer_activations(mrfv_ctx *c, float *h1, float *h2, int64_t n) {
+  if (!c || !h1 || !h2 || n != 16 * c->maptotal) return fail(c, MRFV_ERR_ARG, "proposer_activations: n = 16 * positions");
+  if (!c->initialized || !c->has_weights) return fail(c, MRFV_ERR_STATE, "proposer_activations before init / weights");
+  int rc = check_device(c, "mrfv_proposer_activations");
+  if (rc != MRFV_OK) return rc;
+  std::vector<uint16_t> raw((size_t)n);
+  for (int k = 0; k < 2 && rc == MRFV_OK; k++) {
+    if (cudaMemcpy(raw.data(), k == 0 ? (void *)c->pa1 : (void *)c->pa2, (size_t)n * 2, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      rc = check_device(c, "mrfv_proposer_activations");
+    float *out = k == 0 ? h1 : h2;
+    for (int64_t i = 0; i < n && rc == MRFV_OK; i++) {
+      uint32_t b = (uint32_t)raw[(size_t)i] << 16;  // bfloat16 = the high half of a float
+      memcpy(out + i, &b, 4);
+    }
+  }
   return rc;
 }
 

@@ -584,7 +584,8 @@ void launch_pack_weights(const float *blob, __nv_bfloat16 *w1, float *b1, __nv_b
 // weights' master copy, BCE loss, backward, update.  feat: [ns][3][n] floats,
 // target: [ns][n] bytes (device).  work: scratch of kPropWorkPerPos * n floats.
 void launch_prop_train_step(const Geo &g, const float *feat, const uint8_t *target, int ns, float *blob, float *grad,
-                            float *m1, float *m2, int t, float lr, float *work, double *loss, cudaStream_t st) {
+                            float *m1, float *m2, int t, float lr, float *work, double *loss, int adam,
+                            cudaStream_t st) {
   long long n = g.mapoff[g.L + 1];
   const int NW = 16 * 81 + 16 + 16 * 432 + 16 + 432 + 1;
   float *W1 = blob, *B1 = W1 + 16 * 81, *W2 = B1 + 16, *B2 = W2 + 16 * 432, *W3 = B2 + 16, *B3 = W3 + 432;
@@ -609,7 +610,7 @@ void launch_prop_train_step(const Geo &g, const float *feat, const uint8_t *targ
     k_relu_back<<<grid, 256, 0, st>>>(h1, d1, 16 * n);
     k_conv_dw<<<16 * 81, 256, 0, st>>>(g, x, 3, d1, 16, gW1, gB1);
   }
-  k_adam<<<64, 256, 0, st>>>(blob, grad, m1, m2, NW, lr, t);
+  if (adam) k_adam<<<64, 256, 0, st>>>(blob, grad, m1, m2, NW, lr, t);
 }
 
 }  // namespace mrfv
