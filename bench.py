@@ -179,7 +179,8 @@ MEASURED_TRAFFIC = {
 }
 
 STAGE_KERNELS = ((1, "k_fv (pencil)"), (2, "k_fvs (staged)"), (4, "k_fv (pencil, two threads per line)"),
-                 (8, "k_fvp (pencil on staged primitives)"), (16, "k_fvs (staged MUSCL-Hancock)"))
+                 (8, "k_fvp (pencil on staged primitives)"), (16, "k_fvs (staged MUSCL-Hancock)"),
+                 (32, "k_fvt (TMA-staged, packed x/y lines)"))
 
 
 def stage_kernel_names(mask: int) -> str:
@@ -1344,7 +1345,7 @@ def main():
     ap.add_argument("--autotune", default="", choices=["", "cache", "sweep"],
                     help="default workload: take the launch shape from the autotuner (cache: the cached "
                          "choice, swept first when absent; sweep: sweep again)")
-    ap.add_argument("--stage-kernel", dest="stage_kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--stage-kernel", dest="stage_kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="uniform case: 0 by leaf count, 1 pencil kernel, 2 staged kernel, "
                          "3 split pencil kernel, 4 pencil kernel on staged primitives")
     args = ap.parse_args()

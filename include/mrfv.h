@@ -301,8 +301,12 @@ int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
    stage_kernel picks the MR-scheme stage kernel: 0 by leaf count, 1 the pencil
    kernel (one thread per line of cells), 2 the staged kernel (one thread per
    face), 3 the pencil kernel with two threads per line, 4 the pencil kernel
-   reading primitives staged in shared memory.  Out-of-range values give
-   MRFV_ERR_ARG.  Every kernel loops over its
+   reading primitives staged in shared memory, 5 the TMA-staged kernel (2D
+   single-precision state only: each block and its halo copied into shared
+   memory by the tensor memory accelerator, x and y lines walked together in
+   packed FP32x2 arithmetic; the default there).  Out-of-range values, and 5 for
+   another configuration, give MRFV_ERR_ARG.  The TMA-staged kernel holds at most
+   its occupancy limit of CTAs per SM (a larger fv_ctas_per_sm is capped).  Every kernel loops over its
    device-resident work list, so any shape gives the same results; captured
    step graphs are dropped and re-captured at the next step. */
 int mrfv_set_launch_shape(mrfv_ctx *ctx, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm,

@@ -4,7 +4,8 @@ Translation units and their floating-point flags:
   fv_f64.cu, mr_f64.cu, mr_f32.cu : -fmad=false, IEEE division and square root, so
       the double-precision step and every multiresolution operation round exactly
       where the source says (parity with the CPU oracle; bit-exact thresholding);
-  fv_f32.cu : --use_fast_math (single-precision throughput path);
+  fv_f32.cu, fvt.cu : --use_fast_math (single-precision throughput path; fvt.cu is the
+      TMA-staged 2D stage kernel with packed FP32x2 arithmetic);
   tree.cu, api.cu : integer work and host sequencing;
   noalloc.cu : -fmad=false (the allocation-free CFL reduction rounds like the
       double-precision one in fv_f64.cu);
@@ -36,6 +37,7 @@ UNITS = {
     "api.cu": [],
     "noalloc.cu": ["-fmad=false"],
     "proposer.cu": [],
+    "fvt.cu": ["--use_fast_math"],
 }
 
 

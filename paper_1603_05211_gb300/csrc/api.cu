@@ -110,6 +110,8 @@ struct mrfv_ctx {
   void *rscratch;       // Richardson: the patches of each CTA
   unsigned long long *rcount;  // Richardson: blocks estimated while profiling
   int rich_ctas;        // CTAs of the Richardson estimate (0: off)
+  FvtSet fvt;           // TMA-staged stage kernel (2D single precision): tensor maps
+  int fvtgrid;          // its persistent grid
 };
 
 // CTAs of the Richardson estimate, at most one per block below the finest level.
@@ -427,6 +429,21 @@ struct Seq {
     long long n = list_count(c, c->snap, a.kind, a.l0, a.l1);
     return n < (c->g.dim == 2 ? kSplitBelow2D : kSplitBelow3D);
   }
+  // TMA-staged stage kernel (2D single precision, every buffer of the launch mapped)
+  bool use_fvt(const FVArgs<T> &a) const {
+    if constexpr (sizeof(T) != 4) {
+      return false;
+    } else {
+      if (!c->fvt.ok) return false;
+      if (c->stage_kernel != 0 && c->stage_kernel != 5) return false;
+      bool in = false, u0 = false;
+      for (int b = 0; b < 3; b++) {
+        in = in || (c->fvt.buf[b] && c->fvt.buf[b] == (const void *)a.Uin);
+        u0 = u0 || (c->fvt.buf[b] && c->fvt.buf[b] == (const void *)a.U0);
+      }
+      return in && u0;
+    }
+  }
   // launch a finite-volume stage kernel, bracketed by events when profiling
   void timed_fv(FVArgs<T> &a, bool hancock) {
     a.bytes = c->prof ? c->dbytes : nullptr;
@@ -444,7 +461,15 @@ struct Seq {
       c->ev_used += 2;
       cudaEventRecord(e0, c->st);
     }
-    if (!hancock && use_fvp(a)) {
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (!hancock && use_fvt(a)) {
+        done = launch_fvt(c->g, a, c->fvt, sized(c, a.kind, a.l0, a.l1, 1, fvt_blocks_per_cta(), c->fvtgrid), c->st);
+        if (done) c->fv_kinds |= 32;
+      }
+    }
+    if (done) {
+    } else if (!hancock && use_fvp(a)) {
       launch_fvp<T>(c->g, a, sized(c, a.kind, a.l0, a.l1, 1, c->fvp_bpc, c->fvpgrid), c->st);
       c->fv_kinds |= 8;
     } else if (hancock || use_staged(a)) {
@@ -866,6 +891,13 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   c->fvp_bpc = c->prec == MRFV_FP32 ? fvp_blocks_per_cta<float>(cfg->dim) : fvp_blocks_per_cta<double>(cfg->dim);
   c->fv_bpc = c->prec == MRFV_FP32 ? fv_blocks_per_cta<float>(cfg->dim, false) : fv_blocks_per_cta<double>(cfg->dim, false);
   c->fvs_bpc = c->prec == MRFV_FP32 ? fv_blocks_per_cta<float>(cfg->dim, true) : fv_blocks_per_cta<double>(cfg->dim, true);
+  // the TMA-staged stage kernel for 2D single precision (tensor maps of the state
+  // buffers and the ghost strips); without it the pencil kernel runs
+  c->fvt.ok = false;
+  c->fvtgrid = 0;
+  if (c->prec == MRFV_FP32 && cfg->dim == 2 && fvt_prepare(c->fvt, c->g, c->U, c->Us, c->U0, c->G))
+    c->fvtgrid = c->nsm * c->fvt.ctas_per_sm;
+  cudaGetLastError();
   c->snap_valid = false;
   c->pub_host = c->pub_dev = nullptr;
   if (cudaHostAlloc((void **)&c->pub_host, sizeof(c->snap), cudaHostAllocMapped) == cudaSuccess) {
@@ -1448,7 +1480,9 @@ int mrfv_proposer_activations(mrfv_ctx *c, float *h1, float *h2, int64_t n) {
 int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_sm, int fv_ctas_per_sm,
                           int stage_kernel) {
   if (!c) return MRFV_ERR_ARG;
-  if (stage_kernel < 0 || stage_kernel > 4) return fail(c, MRFV_ERR_ARG, "set_launch_shape: stage_kernel is 0..4");
+  if (stage_kernel < 0 || stage_kernel > 5) return fail(c, MRFV_ERR_ARG, "set_launch_shape: stage_kernel is 0..5");
+  if (stage_kernel == 5 && !c->fvt.ok)
+    return fail(c, MRFV_ERR_ARG, "set_launch_shape: stage kernel 5 (TMA-staged) needs 2D single-precision state");
   if (grid_ctas_per_sm < 0 || grid_ctas_per_sm > 32 || block_ctas_per_sm < 0 || block_ctas_per_sm > 32 ||
       fv_ctas_per_sm < 0 || fv_ctas_per_sm > 32)
     return fail(c, MRFV_ERR_ARG, "set_launch_shape: CTAs per SM outside 0..32");
@@ -1460,6 +1494,10 @@ int mrfv_set_launch_shape(mrfv_ctx *c, int grid_ctas_per_sm, int block_ctas_per_
   for (int h = 0; h < 2; h++) c->fvsgrid[h] = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fvs_occupancy[h]);
   c->stage_kernel = stage_kernel;
   c->fvpgrid = c->nsm * (fv_ctas_per_sm ? fv_ctas_per_sm : c->fvp_occupancy);
+  if (c->fvt.ok) {
+    const int n = fv_ctas_per_sm && fv_ctas_per_sm < c->fvt.ctas_per_sm ? fv_ctas_per_sm : c->fvt.ctas_per_sm;
+    c->fvtgrid = c->nsm * n;
+  }
   drop_graphs(c);
   return MRFV_OK;
 }

@@ -1,6 +1,7 @@
 // Host-side launchers of the kernels (one definition per precision, see the
 // *_f32.cu / *_f64.cu translation units).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -48,6 +49,23 @@ template <typename T> int fvp_blocks_per_cta(int dim);
 template <typename T> void launch_dt(const Geo &, const T *A, int lts, unsigned long long *red, unsigned *done, double cfl,
                                      double t_end, double *dsc, double *lev, float *levf, int grid, cudaStream_t);
 template <typename T> int fv_ctas_per_sm(int dim, bool split);
+
+// TMA-staged stage kernel of the MR scheme, 2D single precision (fvt.cu): tensor
+// maps of the state buffers (own block, x-halo and y-halo boxes) and the ghost
+// strips, built once per context
+struct FvtMaps {
+  CUtensorMap in_own, in_xh, in_yh, u0_own, ghost;
+};
+struct FvtSet {
+  CUtensorMap own[3], xh[3], yh[3], ghost;
+  const void *buf[3];   // the state buffers the maps describe (U, Us, U0; null: none)
+  int ctas_per_sm;
+  bool ok;
+};
+bool fvt_prepare(FvtSet &, const Geo &, const void *U, const void *Us, const void *U0, const void *G);
+int fvt_blocks_per_cta();
+// false (nothing launched) when a buffer of the launch has no tensor map
+bool launch_fvt(const Geo &, const FVArgs<float> &, const FvtSet &, int grid, cudaStream_t);
 
 // integer tree work (tree.cu)
 void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t, int lkeep = 0);

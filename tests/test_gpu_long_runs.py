@@ -67,6 +67,7 @@ def _close(s, o, k):
 
 def _run_fp64(s, o, crit, steps, lts=False, cfl=0.5):
     _same_tree(s, o, 0)
+    adaptive = 0  # steps after which the leaves lie on two levels or more
     for k in range(1, steps + 1):
         dt = o.dt(cfl, lts)
         assert s.step(0.0) == dt, f"step {k}: dt differs"
@@ -75,8 +76,8 @@ def _run_fp64(s, o, crit, steps, lts=False, cfl=0.5):
         _same_tree(s, o, k)
         if k % 25 == 0:
             _close(s, o, k)
-    st = s.stats()
-    assert len([x for x in st["leaves"] if x]) >= 2, "the run must stay adaptive"
+        adaptive += len([x for x in s.stats()["leaves"] if x]) >= 2
+    assert adaptive >= steps // 4, f"the tree was adaptive after {adaptive} of {steps} steps only"
 
 
 def test_adaptive_3d_mr_fp64_100_steps(mrfv):

@@ -417,6 +417,73 @@ def test_both_stage_kernels_match_oracle(mrfv, kernel, case):
     assert_levels_close(s, o)
 
 
+@pytest.mark.parametrize("case", ["uniform", "periodic", "adaptive", "adaptive_periodic", "mrlt"])
+def test_tma_stage_kernel_fp32_matches_pencil_cell_by_cell(mrfv, case):
+    """The TMA-staged stage kernel (5) against the pencil kernel (1) in single
+    precision, every cell after two steps from the same state with the same time
+    steps: same-level halos, ghost strips of coarse-fine faces, transmissive walls,
+    periodic wrap and the flux registers (global and level-dependent steps) all
+    enter.  The two kernels round differently (packed FP32x2 arithmetic and
+    approximate reciprocals against the pencil kernel's expressions), so the bar is
+    a few units of single-precision rounding of each variable's magnitude."""
+    kw = dict(dim=2, precision="fp32")
+    if case in ("uniform", "periodic"):
+        kw.update(levels=1, base_blocks=(3, 5, 1), bc=1 if case == "periodic" else 0)
+        P = mi.quadrant_params(5)
+    else:
+        kw.update(levels=5 if case != "mrlt" else 4, base_blocks=(1, 1, 1) if case != "mrlt" else (2, 2, 1),
+                  adapt=True, eps=1e-3, lts=case == "mrlt", bc=1 if case == "adaptive_periodic" else 0)
+        P = mi.quadrant_params(1)
+    a = mrfv.Solver(**kw)
+    b = mrfv.Solver(**kw)
+    for s in (a, b):
+        s.init_state(mi.IC_QUADRANTS, P)
+    # a few steps of history on the pencil kernel so the halos and ghost strips are non-trivial
+    for s in (a, b):
+        s.set_launch_shape(stage_kernel=1)
+        for _ in range(3):
+            s.step(2e-4)
+    a.set_launch_shape(stage_kernel=5)
+    a.profile_enable(True)
+    for _ in range(2):
+        a.step(2e-4)
+        b.step(2e-4)
+    assert a.profile_read()["fv_kernels"] & 32, "the TMA-staged kernel did not run"
+    for l in range(a.levels):
+        assert np.array_equal(a.get_tree(l), b.get_tree(l))
+        ga, _ = a.download_level(l)
+        gb, _ = b.download_level(l)
+        assert np.array_equal(np.isnan(ga), np.isnan(gb))
+        m = ~np.isnan(gb[0])
+        if not m.any():
+            continue
+        for v in range(4):
+            scale = np.abs(gb[v][m]).max()
+            err = np.abs(ga[v][m] - gb[v][m]).max()
+            assert err <= 3e-6 * scale, (case, l, v, err, scale)
+
+
+def test_tma_stage_kernel_fp32_mrlt_against_oracle(mrfv):
+    """Level-dependent steps (flux registers accumulated over the fine sub-steps)
+    on the TMA-staged kernel against the FP64 oracle: 2e-4 relative L1, totals 1e-6."""
+    s, o = pair(mrfv, 2, 4, (2, 2, 1), precision="fp32", adapt=True, lts=True, params=mi.quadrant_params(3))
+    s.set_launch_shape(stage_kernel=5)
+    T0 = o.totals()
+    for _ in range(6):
+        dt = o.dt(0.5, True)
+        s.step(dt)
+        o.step(dt, True)
+        o.adapt(oracle.CRIT_MR, 1e-3, precision=1)
+    assert _finest_rel_l1(s, o, lambda: _fresh_oracle(2, 4, (2, 2, 1), mi.quadrant_params(3))) <= 2e-4
+    assert np.all(np.abs(s.totals() - o.totals()) <= 1e-6 * np.abs(T0).max())
+
+
+def _fresh_oracle(dim, levels, base, P):
+    o = oracle.Oracle(dim, levels, base)
+    o.init(mi.IC_QUADRANTS, P)
+    return o
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_download_var_coarsened_means(mrfv, dim):
     """One variable averaged over coarsen^d cells equals the mean of the full download."""
