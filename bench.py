@@ -168,15 +168,49 @@ def uniform_roofline(m, torch, hbm_peak, steps=6, scheme="muscl_rk2"):
     return out
 
 
-# DRAM bytes (read + write) per stage launch measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum on the default command, -s 150
-# -c 6 with -k regex:'^k_fv$' or regex:k_fvs: stage-1 and stage-2 launches of the
-# roofline pass, averaged); the writes stay in L2 within the launch.
-# Re-measure when the kernel changes.
-MEASURED_TRAFFIC = {
-    (WORKLOAD, "k_fv (pencil)"): (3929600 + 6949632 + 4017920 + 7129088 + 4108544 + 7308032) / 6.0,
-    (WORKLOAD, "k_fvs (staged)"): (2449408 + 3944192 + 2447360 + 3944704 + 2448128 + 3945984) / 6.0,
-}
+# DRAM traffic of the stage kernel per launch on the default workload, from an ncu
+# capture summarised under profiles/: a line
+#   bench-traffic: kernel=<name> workload=<workload> source_sha256=<hash> bytes_per_launch=<N>
+# The figure is reported only while the kernel's source still has that hash (the
+# counters describe the kernel as it was built then); otherwise traffic is null.
+KERNEL_SOURCES = {"k_fvt": ["paper_1603_05211_gb300/csrc/fvt.cu"],
+                  "k_fv": ["paper_1603_05211_gb300/csrc/fv.cuh"],
+                  "k_fvs": ["paper_1603_05211_gb300/csrc/fvh.cuh"],
+                  "k_fvp": ["paper_1603_05211_gb300/csrc/fv.cuh"]}
+
+
+def kernel_source_sha(kernel: str):
+    import hashlib
+
+    files = KERNEL_SOURCES.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_label: str, workload: str):
+    """(bytes per launch, summary file) of the ncu capture of this kernel on this
+    workload, or (None, reason) when there is none for the current source."""
+    import glob
+    import re
+
+    kernel = kernel_label.split(" ")[0]
+    sha = kernel_source_sha(kernel)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                mt = re.match(r"\s*bench-traffic: kernel=(\S+) workload=(\S+) source_sha256=(\S+) "
+                              r"bytes_per_launch=([0-9.eE+]+)", line)
+                if mt and mt.group(1) == kernel and mt.group(2) == workload:
+                    if mt.group(3) != sha:
+                        return None, f"{os.path.basename(path)}: kernel source changed since the capture"
+                    return float(mt.group(4)), os.path.basename(path)
+    return None, "no ncu capture of this kernel on this workload"
+
 
 STAGE_KERNELS = ((1, "k_fv (pencil)"), (2, "k_fvs (staged)"), (4, "k_fv (pencil, two threads per line)"),
                  (8, "k_fvp (pencil on staged primitives)"), (16, "k_fvs (staged MUSCL-Hancock)"),
@@ -467,25 +501,19 @@ def run_to_end(s, t_end, torch, stream, max_steps=100000):
     return n, float(sum(times))
 
 
-def run_matched3d(args):
-    """3D ellipsoidal blast: adaptive MR (heuristic and learned proposer) against the
-    uniform solve on the finest grid, all to the stop rule of the workload (the
-    shock at 0.8 of the half-width) unless --t-end3d is given, L1(rho) against a
-    uniform solve at twice the finest resolution averaged onto it; GPU time of each."""
+def matched_l1_3d(m, torch, stream, L, t_end=0.0, proposer=False, snapshots=60, train_steps=300):
+    """3D ellipsoidal blast: adaptive MR (and, with `proposer`, the learned
+    proposer) against the uniform solve on the finest grid, all to the stop rule
+    of the workload (the shock at 0.8 of the half-width) unless t_end > 0,
+    L1(rho) against a uniform solve at twice the finest resolution averaged onto
+    it (Section 3); GPU time of each (CUDA events around each step)."""
     import numpy as np
-    import torch
 
-    import paper_1603_05211_gb300 as m
-
-    m.build()
-    m.load()
-    stream = torch.cuda.current_stream()
-    L = args.levels3d
     nfin = 16 << (L - 1)
-    t_end = args.t_end3d if args.t_end3d > 0 else shock_stop_time(m, stream, L)
+    rule = "given" if t_end > 0 else "shock at 0.8 of the half-width"
+    t_end = t_end if t_end > 0 else shock_stop_time(m, stream, L)
     h3 = (2.0 / nfin) ** 3
-    out = {"case": f"blast3d_fp32_L{L - 1}", "finest": nfin, "t_end": t_end,
-           "t_end_rule": "given" if args.t_end3d > 0 else "shock at 0.8 of the half-width", "eps": WL["eps"]}
+    out = {"case": f"blast3d_fp32_L{L - 1}", "finest": nfin, "t_end": t_end, "t_end_rule": rule, "eps": WL["eps"]}
     # reference: uniform at twice the finest resolution, density averaged onto the finest grid
     r = uniform3d(m, stream, 2 * nfin, t_end)
     nref = 0
@@ -502,22 +530,25 @@ def run_matched3d(args):
     u.close()
     torch.cuda.empty_cache()
     out["uniform_fine"] = {"steps": nu, "gpu_ms": ms_u, "l1_rho": l1_u}
-    # learned proposer: trained on snapshots of a coarser run (one level less)
-    feats, targets = proposer_snapshots(m, stream, L - 1, t_end, args.snapshots)
-    tr = blast3d(m, stream, L - 1, t_end)
-    rng = np.random.default_rng(0)
-    w0 = (rng.normal(0, 1, m.PROPOSER_NWEIGHTS) * 0.05).astype(np.float32)
-    tr.proposer_set_weights(w0)
-    t0 = time.perf_counter()
-    loss0 = tr.proposer_train(feats, targets, steps=1, lr=3e-3)
-    loss1 = tr.proposer_train(feats, targets, steps=args.train_steps, lr=3e-3)
-    train_s = time.perf_counter() - t0
-    w = tr.proposer_get_weights()
-    tr.close()
-    out["proposer_training"] = {"snapshots": int(feats.shape[0]), "levels": L - 1, "adam_steps": args.train_steps,
-                                "loss_first": loss0, "loss_last": loss1, "seconds": train_s}
-    out["proposer_eval"] = proposer_miss_rate(m, stream, L, t_end, w, min(args.snapshots, 40))
-    for name, prop in (("adaptive", False), ("adaptive_proposer", True)):
+    runs = [("adaptive", False, None)]
+    if proposer:
+        # learned proposer: trained on snapshots of a coarser run (one level less)
+        feats, targets = proposer_snapshots(m, stream, L - 1, t_end, snapshots)
+        tr = blast3d(m, stream, L - 1, t_end)
+        rng = np.random.default_rng(0)
+        w0 = (rng.normal(0, 1, m.PROPOSER_NWEIGHTS) * 0.05).astype(np.float32)
+        tr.proposer_set_weights(w0)
+        t0 = time.perf_counter()
+        loss0 = tr.proposer_train(feats, targets, steps=1, lr=3e-3)
+        loss1 = tr.proposer_train(feats, targets, steps=train_steps, lr=3e-3)
+        train_s = time.perf_counter() - t0
+        w = tr.proposer_get_weights()
+        tr.close()
+        out["proposer_training"] = {"snapshots": int(feats.shape[0]), "levels": L - 1, "adam_steps": train_steps,
+                                    "loss_first": loss0, "loss_last": loss1, "seconds": train_s}
+        out["proposer_eval"] = proposer_miss_rate(m, stream, L, t_end, w, min(snapshots, 40))
+        runs.append(("adaptive_proposer", True, w))
+    for name, prop, w in runs:
         a = blast3d(m, stream, L, t_end, proposer=prop)
         if prop:
             a.proposer_set_weights(w)
@@ -528,10 +559,24 @@ def run_matched3d(args):
         a.close()
         torch.cuda.empty_cache()
         leaves = (st1["cell_updates"] - st0["cell_updates"]) / max(1, na)
+        pert = abs(l1_u - l1_a) / l1_u
         out[name] = {"steps": na, "gpu_ms": ms_a, "l1_rho": l1_a, "mean_leaf_cells": leaves,
-                     "mesh_compression": leaves / nfin ** 3,
-                     "accuracy_perturbation": abs(l1_u - l1_a) / l1_u,
-                     "time_ratio_over_uniform": ms_a / ms_u}
+                     "mesh_compression": leaves / nfin ** 3, "accuracy_perturbation": pert,
+                     "matched": pert <= 0.05, "time_ratio_over_uniform": ms_a / ms_u}
+    return out
+
+
+def run_matched3d(args):
+    """--case matched3d: matched_l1_3d with the learned proposer."""
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    out = matched_l1_3d(m, torch, stream, args.levels3d, t_end=args.t_end3d, proposer=True,
+                        snapshots=args.snapshots, train_steps=args.train_steps)
     print(json.dumps(out), flush=True)
 
 
@@ -553,6 +598,43 @@ def oracle_sample(budget_s: float, max_steps: int = 50):
         steps += 1
     el = time.perf_counter() - t0
     return cells / el, steps, el
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:  # noqa: BLE001
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_omp_uniform(budget_s: float, n: int = 1024, max_steps: int = 200):
+    """The oracle's OpenMP build (the same C source, its finite-volume loops over
+    blocks on every host core) on a uniform n^2 FP64 grid of the seeded
+    four-quadrant data: cell-updates/s, steps, seconds, threads."""
+    import oracle
+
+    o = oracle.Oracle(2, 1, (n // 8, n // 8, 1), openmp=True)
+    o.init(mi.IC_QUADRANTS, mi.quadrant_params(SEED))
+    o.step(o.dt(WL["cfl"]))  # warm-up (thread team, first touch)
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps and time.perf_counter() - t0 < budget_s:
+        o.step(o.dt(WL["cfl"]))
+        steps += 1
+    el = time.perf_counter() - t0
+    return n * n * steps / el, steps, el, oracle.threads(True)
 
 
 def run_reference(args):
@@ -647,7 +729,7 @@ def run_ours(args):
     # the same steps once more with every stage launch bracketed by CUDA events
     # (eager launches: events cannot be read per replay inside a graph), in the
     # stage kernel the captured step graph uses
-    graph_stage = {1: 1, 2: 2, 4: 3, 8: 4}.get(prof_g.get("graph_fv_kernels", 0), 0)
+    graph_stage = {1: 1, 2: 2, 4: 3, 8: 4, 32: 5}.get(prof_g.get("graph_fv_kernels", 0), 0)
     if graph_stage:
         s.set_launch_shape(stage_kernel=graph_stage)
     s.profile_enable(True)
@@ -665,8 +747,9 @@ def run_ours(args):
     if rank == 0:
         fv_ach = prof["fv_bytes"] / (prof["fv_ms"] * 1e-3) / 1e9 if prof["fv_ms"] > 0 else 0.0
         kname = stage_kernel_names(prof.get("fv_kernels", 0))
+        traffic, traffic_src = profiled_traffic(kname, WORKLOAD)
         roof = {"bound": "hbm", "achieved": round(fv_ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(fv_ach / hbm_peak, 4), "traffic": MEASURED_TRAFFIC.get((WORKLOAD, kname)),
+                "frac": round(fv_ach / hbm_peak, 4), "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": kname, "peak_kind": peak_kind,
                 "timing": "CUDA events around each stage launch, same workload and step count, eager launches",
                 "launches": prof["fv_launches"],
@@ -682,12 +765,35 @@ def run_ours(args):
             roof_h = {"error": str(e)}
         # end to end through the C interface: host initial state in, host state out
         e2e = run_e2e(m, torch, stream, args.steps)
+        # adaptive against uniform-fine GPU time at matched L1 (Section 3): the default
+        # workload (1024^2 finest), the same data at 4096^2 finest, and the 3D blast
+        matched = {}
         try:
-            matched = matched_l1_2d(m, torch, stream)
+            matched["2d_1024"] = matched_l1_2d(m, torch, stream)
         except Exception as e:  # noqa: BLE001
-            matched = {"error": str(e)}
+            matched["2d_1024"] = {"error": str(e)}
+        try:
+            c4096 = {}
+            matched["2d_4096"] = [matched_l1_2d(m, torch, stream, n=4096, eps=e, cache=c4096) for e in (3e-4, 2e-4)]
+            del c4096
+        except Exception as e:  # noqa: BLE001
+            matched["2d_4096"] = {"error": str(e)}
+        torch.cuda.empty_cache()
+        try:
+            matched["3d_blast_256"] = matched_l1_3d(m, torch, stream, 5)
+        except Exception as e:  # noqa: BLE001
+            matched["3d_blast_256"] = {"error": str(e)}
+        torch.cuda.empty_cache()
         # CPU baseline: the oracle on a bounded sample of the same workload
         ob, osteps, osec = oracle_sample(budget_s=float(os.environ.get("MRFV_ORACLE_BUDGET", "15")))
+        try:
+            omp_v, omp_steps, omp_s, omp_threads = oracle_omp_uniform(
+                budget_s=float(os.environ.get("MRFV_ORACLE_BUDGET", "15")) / 2)
+            omp = {"value": omp_v, "unit": "cell-updates/s", "cores": omp_threads, "kind": "oracle (OpenMP build)",
+                   "sample": f"{omp_steps} FP64 steps of the uniform 1024^2 grid of the same initial data "
+                             f"({omp_s:.1f} s)"}
+        except Exception as e:  # noqa: BLE001
+            omp = {"error": str(e)}
         result = {
             "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -702,7 +808,9 @@ def run_ours(args):
             "roofline": roof,
             "roofline_uniform": roof_u, "roofline_hancock": roof_h,
             "cpu_baseline": {"value": ob, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{osteps} FP64 oracle steps of the same workload from t=0 ({osec:.1f} s)"},
+                             "sample": f"{osteps} FP64 oracle steps of the same workload from t=0 ({osec:.1f} s)",
+                             "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
+                             "uniform_fv_all_cores": omp},
             "e2e": e2e,
             "matched_l1": matched,
             "gpu_launches": launches,

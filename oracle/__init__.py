@@ -21,6 +21,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mrfv_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# the same source built with -fopenmp: the finite-volume loops over blocks run on
+# every host core (identical results; the multi-core CPU baseline of the bench)
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 BC_TRANSMISSIVE = 0
 BC_PERIODIC = 1
@@ -32,24 +35,27 @@ CLUSTER_ROWS = 0      # gradient flags clustered in runs along the first directi
 CLUSTER_BR = 1        # Berger-Rigoutsos clustering into boxes (Section 2.2)
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so (gcc, -O2, no floating-point contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile liboracle.so (gcc, -O2, no floating-point contraction), or with
+    openmp its OpenMP build liboracle_omp.so."""
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
-                               "-fno-fast-math", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-fno-fast-math", "-shared", "-fPIC"] + (["-fopenmp"] if openmp else [])
+                              + [_SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 _lib = None
+_lib_omp = None
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
+    if (_lib_omp if openmp else _lib) is None:
+        lib = ctypes.CDLL(build(openmp=openmp))
         P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
@@ -86,13 +92,22 @@ def _load():
             "orc_set_lts_remesh": (I, [P, I, I, D, D, D, I]),
             "orc_br_cluster": (None, [P, I, u8, D, u8]),
             "orc_predict": (D, [P, I, dp, I, I, I, I]),
+            "orc_threads": (I, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
             f.restype = res
             f.argtypes = args
-        _lib = lib
-    return _lib
+        if openmp:
+            _lib_omp = lib
+        else:
+            _lib = lib
+    return _lib_omp if openmp else _lib
+
+
+def threads(openmp: bool = False) -> int:
+    """Threads of the finite-volume loops of the (OpenMP) oracle library."""
+    return int(_load(openmp).orc_threads())
 
 
 def _dp(a: np.ndarray):
@@ -109,8 +124,8 @@ class Oracle:
 
     def __init__(self, dim: int, levels: int, base_blocks, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
                  gamma: float = 1.4, bc: int = BC_TRANSMISSIVE, scheme: int = SCHEME_MUSCL_RK2,
-                 clustering: int = CLUSTER_ROWS):
-        lib = _load()
+                 clustering: int = CLUSTER_ROWS, openmp: bool = False):
+        lib = _load(openmp)
         nb = (ctypes.c_int * 3)(*[int(b) for b in (list(base_blocks) + [1, 1, 1])[:3]])
         lo3 = (ctypes.c_double * 3)(*[float(x) for x in (list(lo) + [0.0] * 3)[:3]])
         hi3 = (ctypes.c_double * 3)(*[float(x) for x in (list(hi) + [1.0] * 3)[:3]])

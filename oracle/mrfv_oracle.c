@@ -28,6 +28,9 @@
  *   - L1 error by projection to the finest level .......... Section 3
  * Readings where the paper is silent are stated beside the code that takes them.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -483,6 +486,9 @@ static float predict_cell_f(const orc *o, int lf, const float *C, int v, int I, 
    coarse values are NaN and would poison any result that used them. */
 static double *build_ext(const orc *o, int l, const double *src, const double *coarse) {
   double *e = alloc_level(o, l);
+  /* every cell is written once from its own inputs (the pragma only matters in
+     the OpenMP build of this file, used for the multi-core CPU baseline) */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < o->n[l][2]; k++)
     for (int j = 0; j < o->n[l][1]; j++)
       for (int i = 0; i < o->n[l][0]; i++) {
@@ -566,6 +572,9 @@ static void fv_level(orc *o, int l, const double *E, const double *q0, double *o
   long nc = o->ncell[l];
   double lam[3];
   for (int d = 0; d < 3; d++) lam[d] = (coef * dt) / o->dx[l][d];
+  /* blocks are independent: each cell's output and flux record is written once
+     (the pragma only matters in the OpenMP build of this file) */
+#pragma omp parallel for collapse(3) schedule(static)
   for (int bk = 0; bk < o->nb[l][2]; bk++)
     for (int bj = 0; bj < o->nb[l][1]; bj++)
       for (int bi = 0; bi < o->nb[l][0]; bi++) {
@@ -710,6 +719,16 @@ orc *orc_create(int dim, int levels, const int *nb0, const double *lo, const dou
     o->rf[l] = (double *)calloc((size_t)6 * o->nv * o->ncell[l], sizeof(double));
   }
   return o;
+}
+
+/* threads the finite-volume loops use: 1, or the OpenMP team size in the
+   OpenMP build of this file */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 void orc_destroy(orc *o) {

@@ -379,7 +379,7 @@ class Solver:
 
     def proposer_activations(self):
         """BF16 inputs of layers 2 and 3 of the last inference, [positions][16] each."""
-        n = self.positions()
+        n = self.positions
         h1 = np.empty((n, 16), np.float32)
         h2 = np.empty((n, 16), np.float32)
         self._check(self.lib.mrfv_proposer_activations(self._h, h1.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),

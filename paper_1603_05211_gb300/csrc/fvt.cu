@@ -95,23 +95,26 @@ __device__ __forceinline__ F2 van_albada2(F2 a, F2 b) {
   return num * rcp2(den);
 }
 
-// AUSM+ split Mach number and pressure of Liou (1996), beta = 1/8, alpha = 3/16,
-// for the + side (sgn = 1) and the - side (sgn = -1); |M| >= 1 takes the
-// supersonic form (max(M, 0), [M > 0]; min(M, 0), [M < 0])
+// AUSM+ split Mach number and pressure of Liou (1996), beta = 1/8, alpha = 3/16.
+// With c = clamp(M, -1, 1), the subsonic polynomials expanded in powers of c
+// give the supersonic forms as well:
+//   M4+(M) = c^4/8 + c/2 + 3/8 + max(M - 1, 0)      (= max(M, 0) when |M| >= 1)
+//   M4-(M) = -c^4/8 + c/2 - 3/8 + min(M + 1, 0)     (= min(M, 0))
+//   P5+(M) =  c (3/16 c^4 - 5/8 c^2 + 15/16) + 1/2   (= [M > 0])
+//   P5-(M) = -c (3/16 c^4 - 5/8 c^2 + 15/16) + 1/2   (= [M < 0])
+// (expanding 1/4 (M +- 1)^2 +- 1/8 (M^2 - 1)^2 and
+// 1/4 (M +- 1)^2 (2 -+ M) +- 3/16 M (M^2 - 1)^2).
 template <int SGN>
 __device__ __forceinline__ void ausm_split2(F2 M, F2 &m4, F2 &p5) {
-  const F2 s = f2s((float)SGN);
-  F2 t = M + s;                               // M +- 1
-  F2 u = fma2(M, M, f2s(-1.f));               // M^2 - 1
-  F2 tt = t * t, uu = u * u;
-  F2 A = f2s(0.25f) * tt;
-  F2 m4sub = fma2(f2s(0.125f * SGN), uu, s * A);      // +-(1/4 t^2 + 1/8 u^2)
-  F2 p5sub = fma2(A, f2s(2.f) - s * M, (f2s(0.1875f * SGN) * M) * uu);   // 1/4 t^2 (2 -+ M) +- 3/16 M u^2
-  F2 m4sup = SGN > 0 ? max02(M) : min02(M);
-  F2 p5sup = sat2(s * M);                     // [M > 0] (or [M < 0]) when |M| >= 1
-  const bool bx = fabsf(M.v.x) >= 1.f, by = fabsf(M.v.y) >= 1.f;
-  m4 = sel2(bx, by, m4sup, m4sub);
-  p5 = sel2(bx, by, p5sup, p5sub);
+  const F2 c = f2(fminf(fmaxf(M.v.x, -1.f), 1.f), fminf(fmaxf(M.v.y, -1.f), 1.f));
+  const F2 c2 = c * c;
+  const F2 lin = fma2(f2s(0.5f), c, f2s(0.375f * SGN));                 // c/2 +- 3/8
+  const F2 quart = fma2(f2s(0.125f * SGN) * c2, c2, lin);              // +-c^4/8 + ...
+  const F2 over = M - f2s((float)SGN);                                  // M -+ 1
+  const F2 sup = SGN > 0 ? max02(over) : min02(over);
+  m4 = quart + sup;
+  const F2 q = fma2(fma2(f2s(0.1875f * SGN), c2, f2s(-0.625f * SGN)), c2, f2s(0.9375f * SGN));
+  p5 = fma2(c, q, f2s(0.5f));
 }
 
 // AUSM+ flux of both lanes' faces from the left / right primitive states;
@@ -281,13 +284,21 @@ __global__ void __launch_bounds__(fvt::NT, 4) k_fvt(Geo g, FVArgs<float> a, cons
       fetch(i0 + gridDim.x * G + lane);
     }
     // ---------------- wait for the copies (bounded; one decision for the CTA)
-    const bool ok = __syncthreads_and(mbar_wait_bounded(mbar, parity) ? 1 : 0) != 0;
-    parity ^= 1u;
+    // one thread polls (bounded), the CTA learns the outcome at the barrier, then every
+    // thread observes the completed phase once (which acquires the copies' writes)
+    bool got = true;
+    if (tid == 0) got = mbar_wait_bounded(mbar, parity);
+    const bool ok = __syncthreads_and(got ? 1 : 0) != 0;
     if (!ok) {
-      if (tid == 0) atomicOr(g.err, EB_TIMEOUT);
-      __syncthreads_and(mbar_wait_bounded(mbar, parity ^ 1u) ? 1 : 0);  // copies still in flight
+      if (tid == 0) {
+        atomicOr(g.err, EB_TIMEOUT);
+        mbar_wait_bounded(mbar, parity);  // copies still in flight: wait for them (bounded) before leaving
+      }
+      __syncthreads();
       return;
     }
+    mbar_wait_bounded(mbar, parity);      // completes at once
+    parity ^= 1u;
     // ---------------- 2. primitives of each block and its halo into the tile
     {
       const int j = tid >> 4, r = tid & 15;
@@ -490,26 +501,27 @@ __global__ void __launch_bounds__(fvt::NT, 4) k_fvt(Geo g, FVArgs<float> a, cons
       }
     }
     __syncthreads();
-    // ---------------- 4. update and store
+    // ---------------- 4. update and store: each thread four cells (x0..x0+3, y) of one
+    // block, every variable: Q_out = Q_0 - lambda_x dF_x - lambda_y dF_y
     {
       const long long vsU = cap * 64;
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const int q = tid + NT * i;
-        const int j = q >> 6, c = q & 63;
-        const int s = sslot[j];
-        if (s < 0) continue;
-        const int x = c & 7, y = c >> 3;
+      const int j = tid >> 4, r = tid & 15;
+      const int s = sslot[j];
+      if (s >= 0) {
+        const int y = r >> 1, x0 = 4 * (r & 1);
         const float *dFx = reinterpret_cast<const float *>(sm + (size_t)j * ST_BYTES) + 8 * (j & 3);
         const float *dFy = dFx + 256;
         const float *Q0 = reinterpret_cast<const float *>(sm + OFF_U0 + (size_t)j * U0_BYTES);
-        const float lx = slam[j][0], ly = slam[j][1];
-        float *out = a.Uout + (long long)s * 64 + c;
+        const F2 mlx = f2s(-slam[j][0]), mly = f2s(-slam[j][1]);
+        float *out = a.Uout + (long long)s * 64 + y * 8 + x0;
 #pragma unroll
         for (int v = 0; v < 4; v++) {
-          float r = lx * dFx[v * 64 + x * 8 + y];
-          r = fmaf(ly, dFy[v * 64 + y * 8 + x], r);
-          out[v * vsU] = Q0[v * 64 + c] - r;
+          const float4 q = *reinterpret_cast<const float4 *>(Q0 + v * 64 + y * 8 + x0);
+          const float4 dy = *reinterpret_cast<const float4 *>(dFy + v * 64 + y * 8 + x0);
+          const float *dxp = dFx + v * 64 + x0 * 8 + y;   // dF_x stored [x][y]
+          F2 lo = fma2(mlx, f2(dxp[0], dxp[8]), fma2(mly, f2(dy.x, dy.y), f2(q.x, q.y)));
+          F2 hi = fma2(mlx, f2(dxp[16], dxp[24]), fma2(mly, f2(dy.z, dy.w), f2(q.z, q.w)));
+          *reinterpret_cast<float4 *>(out + v * vsU) = make_float4(lo.v.x, lo.v.y, hi.v.x, hi.v.y);
         }
       }
     }

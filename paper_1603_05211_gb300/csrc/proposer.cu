@@ -466,10 +466,12 @@ __global__ void k_conv_dx(Geo g, const float *__restrict__ dy, int cout, const f
   }
 }
 
-// Adam on the FP32 master weights (beta1 0.9, beta2 0.999, eps 1e-8), step t
+// Adam on the FP32 master weights (beta1 0.9, beta2 0.999, eps 1e-8), step t; the
+// bias corrections 1 - beta^t are formed in double precision (in single precision
+// 1 - 0.999f loses five digits to cancellation)
 __global__ void k_adam(float *__restrict__ w, const float *__restrict__ grad, float *__restrict__ m,
                        float *__restrict__ v, int n, float lr, int t) {
-  float b1t = 1.f - powf(0.9f, (float)t), b2t = 1.f - powf(0.999f, (float)t);
+  const float b1t = (float)(1.0 - pow(0.9, (double)t)), b2t = (float)(1.0 - pow(0.999, (double)t));
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float gi = grad[i];
     m[i] = 0.9f * m[i] + 0.1f * gi;

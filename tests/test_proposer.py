@@ -96,14 +96,15 @@ def _check_bf16_layer(h_gpu, pre, bound):
     pre-activations of the same inputs; bound: the FP32-accumulation error bound
     per output.  Exact equality with bf16(relu(pre)) except where pre lies
     within the bound of a rounding midpoint (or of 0), where the two
-    neighbouring bfloat16 values are both correct."""
+    neighbouring bfloat16 values are both correct.  Returns (outputs within the
+    bound of a tie, outputs)."""
     ref = P.bf16_round(np.maximum(pre, 0.0).astype(np.float32)).astype(np.float64)
     near = (_bf16_tie_distance(pre) <= bound) | (np.abs(pre) <= bound)
     exact = ~near
     assert np.array_equal(h_gpu[exact], ref[exact]), np.abs(h_gpu[exact] - ref[exact]).max()
     ulp = np.ldexp(1.0, np.frexp(np.maximum(np.abs(pre[near]) + bound[near], 1e-30))[1] - 7)
     assert np.all(np.abs(h_gpu[near] - ref[near]) <= ulp)
-    assert near.mean() < 0.01
+    return int(near.sum()), near.size
 
 
 @pytest.mark.gpu
@@ -137,21 +138,25 @@ def test_proposer_features_and_tensor_core_inference_match_oracle(mrfv, dim):
     # FP32 accumulation of K products: error below K * 2^-22 * sum |w| |x| (a factor 4 over
     # the sequential-summation bound, the tensor core's adder order being unspecified)
     off = 0
+    near = total = 0
     for sh in shapes:
         n = int(np.prod(sh))
         x = P.bf16_round(fg[:, off:off + n]).astype(np.float64).reshape((3,) + sh)
         a1 = P.conv_level(x, W1, B1)
         b1 = 224 * 2.0 ** -22 * P.conv_level(np.abs(x), np.abs(W1), np.abs(B1))
-        _check_bf16_layer(h1g[off:off + n].T.reshape((16,) + sh), a1, b1)
+        k, m = _check_bf16_layer(h1g[off:off + n].T.reshape((16,) + sh), a1, b1)
+        near, total = near + k, total + m
         h1 = h1g[off:off + n].T.reshape((16,) + sh).astype(np.float64)
         a2 = P.conv_level(h1, W2, B2)
         b2 = 432 * 2.0 ** -22 * P.conv_level(np.abs(h1), np.abs(W2), np.abs(B2))
-        _check_bf16_layer(h2g[off:off + n].T.reshape((16,) + sh), a2, b2)
+        k, m = _check_bf16_layer(h2g[off:off + n].T.reshape((16,) + sh), a2, b2)
+        near, total = near + k, total + m
         h2 = h2g[off:off + n].T.reshape((16,) + sh).astype(np.float64)
         z = P.conv_level(h2, W3, B3)[0].reshape(-1)
         bz = (432 * 2.0 ** -22 * P.conv_level(np.abs(h2), np.abs(W3), np.abs(B3)))[0].reshape(-1)
         assert np.all(np.abs(zg[off:off + n] - z) <= bz + 1e-30), np.abs(zg[off:off + n] - z).max()
         off += n
+    assert near < 0.1 * total, (near, total)   # the bound leaves most outputs decided exactly
     # end to end, the decisions agree wherever the oracle's own BF16 chain is clear of 0
     zo = P.forward(w, fg, shapes)
     clear = np.abs(zo) > 2e-3 * np.abs(zo).max()
