@@ -124,6 +124,10 @@ typedef struct {
                            before the first step); a block is flagged when |tau| of density exceeds eps_r on
                            a coarse cell of an existing block within one fine cell of it.  0 (default): off.
                            With the MR criterion it must be 0. */
+  int proposer_dense;   /* with the proposer: 0 (default) computes its convolutions only on the 128-position
+                           tiles whose logits can add a block (children of existing blocks, and the one- and
+                           two-position neighbourhoods the second and first layer feed them from); 1: on every
+                           block position of every level (the same blocks are added) */
 } mrfv_config;
 
 typedef struct {
@@ -278,10 +282,12 @@ typedef struct {
                            writes Q^{n+1} (3 nv words) */
   int64_t prop_launches; /* tensor-core convolution launches of the proposer timed (3 per inference) */
   double prop_ms;        /* their CUDA-event time */
-  double prop_flops;     /* their algorithmic flops: 2 x positions x (16*81 + 16*432 + 432) per inference */
+  double prop_flops;     /* their algorithmic flops: 2 x (16*81 + 16*432 + 432) per position covered (every
+                            position for mrfv_proposer_infer; in the adaptation, the positions of the tiles
+                            each layer needs, unless cfg.proposer_dense) */
   int fv_kernels;        /* stage kernels those launches used (bit mask): 1 pencil, 2 staged (MR scheme),
                             4 pencil with two threads per line, 8 pencil on staged primitives,
-                            16 staged MUSCL-Hancock */
+                            16 staged MUSCL-Hancock, 32 TMA-staged */
   int graph_fv_kernels;  /* the same bit mask for the stage kernels in the step graphs captured now */
   int64_t rich_launches; /* Richardson estimates timed (the estimate and its block flags, two kernels each) */
   double rich_ms;        /* their CUDA-event time */
@@ -304,7 +310,7 @@ int mrfv_profile_read(mrfv_ctx *ctx, mrfv_profile *out);
    reading primitives staged in shared memory, 5 the TMA-staged kernel (2D
    single-precision state only: each block and its halo copied into shared
    memory by the tensor memory accelerator, x and y lines walked together in
-   packed FP32x2 arithmetic; the default there).  Out-of-range values, and 5 for
+   packed FP32x2 arithmetic; the automatic choice there from 65536 leaf blocks).  Out-of-range values, and 5 for
    another configuration, give MRFV_ERR_ARG.  The TMA-staged kernel holds at most
    its occupancy limit of CTAs per SM (a larger fv_ctas_per_sm is capped).  Every kernel loops over its
    device-resident work list, so any shape gives the same results; captured
@@ -334,9 +340,12 @@ int mrfv_proposer_features(mrfv_ctx *ctx, float *feat, int64_t n);
 /* Logits of the current features (n = positions), through the tensor-core kernels. */
 int mrfv_proposer_infer(mrfv_ctx *ctx, float *logits, int64_t n);
 /* `steps` Adam steps (learning rate lr) on nsnap snapshots: feat[nsnap][3][positions],
-   target[nsnap][positions] (1 = block needed at the next step); binary
-   cross-entropy over positions of level >= 1 with an existing parent (in the
-   current tree).  *loss = loss of the last step. */
+   target[nsnap][positions] (1 = block needed at the next step, 0 = not, 255 =
+   left out of the loss); binary cross-entropy over positions of level >= 1 with
+   an existing parent (in the current tree) and a target other than 255.  With a
+   full tree (cfg.adapt = 0) the 255 entries alone select the positions, so
+   snapshots of different trees (255 where the snapshot's parent block was
+   absent) train together.  *loss = loss of the last step. */
 int mrfv_proposer_train(mrfv_ctx *ctx, const float *feat, const uint8_t *target, int nsnap, int steps, float lr,
                         double *loss);
 /* The gradient the next Adam step of mrfv_proposer_train would take, without

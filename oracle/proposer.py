@@ -170,10 +170,10 @@ def parent_mask(shapes, exist_maps) -> np.ndarray:
 def loss_and_grad(blob: np.ndarray, feats: np.ndarray, targets: np.ndarray, shapes, use: np.ndarray,
                   inv_count: float):
     """Binary cross-entropy with logits summed over the snapshots and over the
-    positions where ``use`` holds, times inv_count, and its gradient in the
-    weights (the blob's order).  feats: [nsnap][3][positions], targets:
-    [nsnap][positions] (0/1).  Master weights as given (no bfloat16 rounding),
-    float64 throughout."""
+    positions where ``use`` holds and the target is not 255, times inv_count,
+    and its gradient in the weights (the blob's order).  feats:
+    [nsnap][3][positions], targets: [nsnap][positions] (0/1, 255 = left out).
+    Master weights as given (no bfloat16 rounding), float64 throughout."""
     (W1, B1), (W2, B2), (W3, B3) = unpack(blob, np.float64)
     g = {k: 0.0 for k in ("W1", "B1", "W2", "B2", "W3", "B3")}
     loss = 0.0
@@ -182,8 +182,8 @@ def loss_and_grad(blob: np.ndarray, feats: np.ndarray, targets: np.ndarray, shap
         for sh in shapes:
             n = int(np.prod(sh))
             x = f[:, off:off + n].reshape((3,) + sh)
-            u = use[off:off + n].reshape(sh)
-            yy = (y[off:off + n].reshape(sh) != 0).astype(np.float64)
+            u = use[off:off + n].reshape(sh) & (y[off:off + n].reshape(sh) != 255)
+            yy = (y[off:off + n].reshape(sh) == 1).astype(np.float64)
             a1 = conv_level(x, W1, B1)
             h1 = np.maximum(a1, 0.0)
             a2 = conv_level(h1, W2, B2)

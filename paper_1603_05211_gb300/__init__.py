@@ -46,7 +46,7 @@ class Config(ctypes.Structure):
         ("stream", ctypes.c_void_p), ("device_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
         ("use_graph", ctypes.c_int), ("proposer", ctypes.c_int), ("scheme", ctypes.c_int),
         ("clustering", ctypes.c_int), ("eps_p", ctypes.c_double), ("lts_remesh", ctypes.c_int),
-        ("eps_r", ctypes.c_double),
+        ("eps_r", ctypes.c_double), ("proposer_dense", ctypes.c_int),
     ]
 
 
@@ -159,7 +159,7 @@ class Solver:
                  hi=(1.0, 1.0, 1.0), bc=BC_TRANSMISSIVE, gamma=1.4, cfl=0.5, t_end=0.0, adapt=False,
                  criterion="mr", eps=1e-3, eps_w=0.05, eta_tol=0.8, lts=False, pool_blocks=0, stream=None,
                  use_graph=True, proposer=False, scheme="muscl_rk2", clustering="rows", eps_p=0.0,
-                 lts_remesh=True, eps_r=0.0):
+                 lts_remesh=True, eps_r=0.0, proposer_dense=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -187,6 +187,7 @@ class Solver:
         cfg.pool_blocks = int(pool_blocks)
         cfg.use_graph = int(bool(use_graph))
         cfg.proposer = int(bool(proposer))
+        cfg.proposer_dense = int(bool(proposer_dense))
         cfg.scheme = SCHEME_HANCOCK if str(scheme).lower() in ("hancock", "1") else SCHEME_MUSCL_RK2
         cfg.clustering = CLUSTER_BR if str(clustering).lower() in ("br", "berger-rigoutsos", "1") else CLUSTER_ROWS
         self.stream = stream if stream is not None else torch.cuda.current_stream()

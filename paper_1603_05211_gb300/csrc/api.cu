@@ -41,6 +41,11 @@ constexpr long long kSplitBelow3D = 0;
 // memory (set from measurement; at or above the largest count: never).
 constexpr long long kStagedPrimAbove2D = 1LL << 40;
 constexpr long long kStagedPrimAbove3D = 1LL << 40;
+// From this leaf count on (2D single precision), the TMA-staged kernel runs.
+// Measured (FP32, CUDA events per launch, TMA-staged / pencil): uniform 4096^2
+// (262144 blocks) 0.352 / 0.371 ms, 8192^2 1.374 / 1.433 ms; the adaptive 8-level
+// workload (about 1700 leaf blocks) 14.3-15.7 / 14.0-14.2 us.
+constexpr long long kFvtAbove2D = 65536;
 
 struct mrfv_ctx {
   mrfv_config cfg;
@@ -85,6 +90,10 @@ struct mrfv_ctx {
   unsigned *done;  // last-CTA counter of the CFL reduction
   // learned proposer
   float *pfeat, *plogit, *pb1, *pb2, *pb3, *pblob, *pgrad, *pm1, *pm2, *pwork;
+  uint8_t *ptile;                 // tiles each layer needs (restricted inference), 3 x ptiles bytes
+  long long ptiles;               // 128-position tiles
+  unsigned long long *ptcount;    // tiles computed per layer while profiling
+  long long pdense;               // dense inferences while profiling
   __nv_bfloat16 *pa0, *pa1, *pa2, *pw1, *pw2, *pw3;
   double *ploss;
   bool has_weights;
@@ -239,6 +248,8 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t opa1 = L.take(16 * maptotal * 2), opa2 = L.take(16 * maptotal * 2);
   size_t opw1 = L.take(16 * 224 * 2), opw2 = L.take(16 * 432 * 2), opw3 = L.take(16 * 432 * 2);
   size_t opb = L.take(3 * 16 * 4), opblob = L.take(4 * NW * 4), opwork = L.take((size_t)kPropWorkPerPos * maptotal * 4), oploss = L.take(8);
+  const long long ptiles = (maptotal + 127) / 128;
+  size_t optile = L.take(3 * (size_t)ptiles), optc = L.take(3 * 8);
   int maxside = 1;
   if (g.L >= 1)
     for (int d = 0; d < g.dim; d++) maxside = g.nb[g.L - 1][d] > maxside ? g.nb[g.L - 1][d] : maxside;
@@ -286,6 +297,9 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->pm2 = c->pm1 + NW;
     c->pwork = (float *)(a + opwork);
     c->ploss = (double *)(a + oploss);
+    c->ptile = (uint8_t *)(a + optile);
+    c->ptiles = ptiles;
+    c->ptcount = (unsigned long long *)(a + optc);
     c->brscratch = a + obr;
     c->rctl = (unsigned *)(a + orctl);
     c->rich_ctas = rctas;
@@ -436,6 +450,10 @@ struct Seq {
     } else {
       if (!c->fvt.ok) return false;
       if (c->stage_kernel != 0 && c->stage_kernel != 5) return false;
+      if (c->stage_kernel == 0) {
+        if (!c->snap_valid) return false;
+        if (list_count(c, c->snap, a.kind, a.l0, a.l1) < kFvtAbove2D) return false;
+      }
       bool in = false, u0 = false;
       for (int b = 0; b < 3; b++) {
         in = in || (c->fvt.buf[b] && c->fvt.buf[b] == (const void *)a.Uin);
@@ -672,8 +690,16 @@ void Seq<T>::remesh(int l0) {
   apply_need(c, true, true, l0 + 1);
 }
 
-void prop_infer(mrfv_ctx *c) {
+// restricted: only the tiles whose logits can add a block (the adaptation's use);
+// otherwise every position (mrfv_proposer_infer, and cfg.proposer_dense)
+void prop_infer(mrfv_ctx *c, bool restricted) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (restricted) {
+    launch_prop_tiles(c->g, c->ptile, c->ptiles, c->prof ? c->ptcount : nullptr, c->grid, c->st);
+    c->nlaunch += c->prof ? 2 : 1;
+  } else if (c->prof) {
+    c->pdense += 1;
+  }
   if (c->prof) {
     if (c->pev_used + 2 > c->pevs.size())
       for (int k = 0; k < 16; k++) {
@@ -686,7 +712,7 @@ void prop_infer(mrfv_ctx *c) {
     c->pev_used += 2;
   }
   launch_prop_infer(c->g, c->pfeat, c->pa0, c->pa1, c->pa2, c->pw1, c->pb1, c->pw2, c->pb2, c->pw3, c->pb3, c->plogit,
-                    c->nsm, e0, e1, c->st);
+                    c->nsm, e0, e1, restricted ? c->ptile : nullptr, c->st);
   c->nlaunch += 4;
 }
 
@@ -707,7 +733,7 @@ void adapt_tree(mrfv_ctx *c, bool step = false, bool begun = false) {
   else dispatch(c, [&](auto &s) { s.gradflags(true); });
   if (use_prop) {
     dispatch(c, [&](auto &s) { s.prop_features(); });
-    prop_infer(c);
+    prop_infer(c, !c->cfg.proposer_dense);
   }
   launch_need_mark(g, c->sig, c->need, use_prop ? 2 : c->cfg.criterion, c->grid, c->st);
   if (use_prop) {
@@ -809,6 +835,7 @@ int mrfv_create(const mrfv_config *cfg, mrfv_ctx **out) {
   if (cfg->eps_r > 0.0 && cfg->criterion != MRFV_CRIT_GRAD)
     return fail(nullptr, MRFV_ERR_ARG, "eps_r: the Richardson estimate adds to the gradient criterion");
   if (cfg->lts_remesh != 0 && cfg->lts_remesh != 1) return fail(nullptr, MRFV_ERR_ARG, "lts_remesh");
+  if (cfg->proposer_dense != 0 && cfg->proposer_dense != 1) return fail(nullptr, MRFV_ERR_ARG, "proposer_dense");
   {
     Geo gg;
     long long a, b, f;
@@ -1387,7 +1414,7 @@ int mrfv_proposer_infer(mrfv_ctx *c, float *logits, int64_t n) {
   if (!c || !logits || n != c->maptotal) return fail(c, MRFV_ERR_ARG, "proposer_infer: n = positions");
   if (!c->initialized || !c->has_weights) return fail(c, MRFV_ERR_STATE, "proposer_infer before init / weights");
   dispatch(c, [&](auto &s) { s.prop_features(); });
-  prop_infer(c);
+  prop_infer(c, false);
   int rc = check_launch(c, "mrfv_proposer_infer");
   if (rc == MRFV_OK) rc = check_device(c, "mrfv_proposer_infer");
   if (rc == MRFV_OK) cudaMemcpy(logits, c->plogit, n * 4, cudaMemcpyDeviceToHost);
@@ -1512,6 +1539,8 @@ int mrfv_profile_enable(mrfv_ctx *c, int enable) {
   c->rev_used = 0;
   c->nlaunch = 0;
   cudaMemsetAsync(c->rcount, 0, 8, c->st);
+  cudaMemsetAsync(c->ptcount, 0, 3 * 8, c->st);
+  c->pdense = 0;
   c->fv_kinds = 0;
   cudaMemsetAsync(c->dbytes, 0, 8, c->st);
   return check_launch(c, "mrfv_profile_enable");
@@ -1540,7 +1569,12 @@ int mrfv_profile_read(mrfv_ctx *c, mrfv_profile *o) {
   }
   o->prop_launches = (int64_t)(3 * (c->pev_used / 2));
   o->prop_ms = pms;
-  o->prop_flops = (double)(c->pev_used / 2) * 2.0 * (double)c->maptotal * (16.0 * 81 + 16.0 * 432 + 432.0);
+  // algorithmic flops of the positions the convolutions covered: every position for a
+  // dense inference, the flagged tiles' positions for a restricted one
+  unsigned long long tc[3] = {0, 0, 0};
+  cudaMemcpy(tc, c->ptcount, sizeof(tc), cudaMemcpyDeviceToHost);
+  o->prop_flops = 2.0 * ((double)c->pdense * (double)c->maptotal * (16.0 * 81 + 16.0 * 432 + 432.0) +
+                         128.0 * ((double)tc[0] * 16.0 * 81 + (double)tc[1] * 16.0 * 432 + (double)tc[2] * 432.0));
   double rms = 0.0;
   for (size_t k = 0; k + 1 < c->rev_used; k += 2) {
     float t = 0.f;

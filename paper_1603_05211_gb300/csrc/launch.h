@@ -98,10 +98,14 @@ template <typename T> void launch_prop_features(const Geo &, const T *U, const d
                                                 float *feat, int grid, cudaStream_t);
 void prop_setup();
 void launch_wait_selftest(int *err, unsigned limit, int arrive, cudaStream_t);
+// the 128-position tiles each layer of the proposer needs (flags: 3 x ntp bytes); count
+// (optional): tiles flagged per layer are added to count[3]
+void launch_prop_tiles(const Geo &, uint8_t *flags, long long ntp, unsigned long long *count, int grid, cudaStream_t);
+// tneed: flags of launch_prop_tiles (only those tiles are computed), or null (every tile)
 void launch_prop_infer(const Geo &, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
                        const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
                        const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaEvent_t conv_begin,
-                       cudaEvent_t conv_end, cudaStream_t);
+                       cudaEvent_t conv_end, const uint8_t *tneed, cudaStream_t);
 void launch_prop_mark(const Geo &, const float *logits, uint8_t *need, int grid, cudaStream_t);
 void launch_pack_weights(const float *blob, __nv_bfloat16 *w1, float *b1, __nv_bfloat16 *w2, float *b2,
                          __nv_bfloat16 *w3, float *b3, cudaStream_t);

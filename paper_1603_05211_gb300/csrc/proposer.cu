@@ -177,12 +177,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsign
 // LAST: logits[p] = acc[0] + bias[0]; otherwise out[p][n] = bf16(relu(acc + bias)).
 constexpr int kConvThreads = 256;  // two threads per tile row: taps 0..13 and 14..26
 
+// tneed (may be null: every tile): per 128-position tile, nonzero when some position
+// of the tile is needed by the layer; other tiles are skipped (their outputs stay as
+// they were: only needed positions are read downstream).
 template <int CIN, int KP, bool LAST>
 __global__ void __launch_bounds__(kConvThreads) k_prop_conv_tc(Geo g, const __nv_bfloat16 *__restrict__ in,
                                                                const uint4 *__restrict__ Wcm,
                                                                const float *__restrict__ bias,
                                                                __nv_bfloat16 *__restrict__ out,
-                                                               float *__restrict__ logits) {
+                                                               float *__restrict__ logits,
+                                                               const uint8_t *__restrict__ tneed) {
   constexpr int M = 128, N = 16;
   constexpr int KREAL = CIN * 27;
   static_assert(CIN == 8 || CIN == 16, "channel-last rows of 16 or 32 bytes");
@@ -225,6 +229,7 @@ __global__ void __launch_bounds__(kConvThreads) k_prop_conv_tc(Geo g, const __nv
 
   const long long ntiles = (npos + M - 1) / M;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    if (tneed && !tneed[tile]) continue;  // the same decision for the whole CTA
     // this row's position, level and block coordinates
     const long long p = tile * M + row;
     int x = 0, y = 0, z = 0, nx = 0, ny = 0, nz = 0;
@@ -330,6 +335,45 @@ constexpr size_t conv_smem() {
 constexpr int kKP1 = 224;  // layer 1: 27 taps x 8 channels = 216, padded to a multiple of 16
 constexpr int kKP2 = 432;  // layers 2, 3: 27 taps x 16 channels
 
+// ---------------------------------------------------------------- tiles the marking needs
+// A logit is used only at positions of level >= 1 whose parent block exists: the
+// 2^d children positions of every existing block below the finest level.  Layer 3
+// is needed there, layer 2 within one position of them (its 3^d stencil), layer 1
+// within two.  flags[k * ntp + tile] = 1 for every 128-position tile that holds a
+// position layer k + 1 needs (k = 0: distance 2, 1: distance 1, 2: the children).
+__global__ void k_prop_tiles(Geo g, uint8_t *__restrict__ flags, long long ntp) {
+  int b, e;
+  list_range(g, LK_EXIST, 0, g.L - 1, b, e);
+  const long long cap = g.cap;
+  for (int i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
+    const int s = g.lists[LK_EXIST * cap + i];
+    const int l = g.slot_level[s] + 1;  // the children's level
+    const int c0 = 2 * g.slot_coord[3 * s], c1 = 2 * g.slot_coord[3 * s + 1], c2 = 2 * g.slot_coord[3 * s + 2];
+    const int nx = g.nb[l][0], ny = g.nb[l][1], nz = g.nb[l][2];
+    for (int k = 0; k < 3; k++) {
+      const int r = 2 - k;
+      const int x0 = max(c0 - r, 0), x1 = min(c0 + 1 + r, nx - 1);
+      const int y0 = max(c1 - r, 0), y1 = min(c1 + 1 + r, ny - 1);
+      const int z0 = g.dim == 3 ? max(c2 - r, 0) : 0, z1 = g.dim == 3 ? min(c2 + 1 + r, nz - 1) : 0;
+      for (int z = z0; z <= z1; z++)
+        for (int y = y0; y <= y1; y++) {
+          const long long row = g.mapoff[l] + (long long)nx * (y + (long long)ny * z);
+          for (long long t = (row + x0) >> 7; t <= (row + x1) >> 7; t++) flags[k * ntp + t] = 1;
+        }
+    }
+  }
+}
+// tiles flagged per layer, added to cnt[3] (profiling)
+__global__ void k_prop_tile_count(const uint8_t *__restrict__ flags, long long ntp, unsigned long long *cnt) {
+  for (int k = 0; k < 3; k++) {
+    unsigned long long c = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ntp; t += (long long)gridDim.x * blockDim.x)
+      c += flags[k * ntp + t] ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt + k, c);
+  }
+}
+
 // ---------------------------------------------------------------- marking
 // Positions of level >= 1 whose parent exists and whose logit is positive are
 // needed (the closure then adds their siblings, parents and grading).
@@ -371,7 +415,7 @@ __global__ void k_conv_fwd_f32(Geo g, const float *__restrict__ x, int cin, cons
 }
 
 // binary cross-entropy with logits, averaged over positions of level >= 1
-// whose parent exists: dL/dz = (sigmoid(z) - y) / count
+// whose parent exists and whose target is not 255 (excluded): dL/dz = (sigmoid(z) - y) / count
 __global__ void k_bce_grad(Geo g, const float *__restrict__ z, const uint8_t *__restrict__ target,
                            float *__restrict__ dz, double *loss, float inv_count) {
   const long long n = g.mapoff[g.L + 1];
@@ -379,7 +423,7 @@ __global__ void k_bce_grad(Geo g, const float *__restrict__ z, const uint8_t *__
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
     float d = 0.f;
     int l = pos_level(g, p);
-    bool use = l > 0;
+    bool use = l > 0 && target[p] != 255;
     if (use) {
       long long u = p - g.mapoff[l];
       int bx = (int)(u % g.nb[l][0]), by = (int)((u / g.nb[l][0]) % g.nb[l][1]);
@@ -553,23 +597,31 @@ void launch_wait_selftest(int *err, unsigned limit, int arrive, cudaStream_t st)
   k_wait_selftest<<<1, 32, 0, st>>>(err, limit, arrive);
 }
 
+void launch_prop_tiles(const Geo &g, uint8_t *flags, long long ntp, unsigned long long *count, int grid,
+                       cudaStream_t st) {
+  cudaMemsetAsync(flags, 0, 3 * (size_t)ntp, st);
+  if (g.L >= 1) k_prop_tiles<<<grid, 256, 0, st>>>(g, flags, ntp);
+  if (count) k_prop_tile_count<<<64, 256, 0, st>>>(flags, ntp, count);
+}
+
 void launch_prop_infer(const Geo &g, const float *feat, __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2,
                        const __nv_bfloat16 *w1, const float *b1, const __nv_bfloat16 *w2, const float *b2,
                        const __nv_bfloat16 *w3, const float *b3, float *logits, int nsm, cudaEvent_t conv_begin,
-                       cudaEvent_t conv_end, cudaStream_t st) {
+                       cudaEvent_t conv_end, const uint8_t *tneed, cudaStream_t st) {
   long long n = g.mapoff[g.L + 1];
   long long tiles = (n + 127) / 128;
+  const uint8_t *t1 = tneed, *t2 = tneed ? tneed + tiles : nullptr, *t3 = tneed ? tneed + 2 * tiles : nullptr;
   // layer 1 fits three CTAs per SM in shared memory, layers 2 and 3 one
   int grid1 = (int)(tiles < 3 * nsm ? tiles : 3 * nsm), grid2 = (int)(tiles < nsm ? tiles : nsm);
   long long fb = (n + 255) / 256;
   k_feat_rows<<<(int)(fb < 4 * nsm ? fb : 4 * nsm), 256, 0, st>>>(feat, reinterpret_cast<uint4 *>(a0), n);
   if (conv_begin) cudaEventRecord(conv_begin, st);
   k_prop_conv_tc<8, kKP1, false><<<grid1, kConvThreads, conv_smem<kKP1>(), st>>>(
-      g, a0, reinterpret_cast<const uint4 *>(w1), b1, a1, nullptr);
+      g, a0, reinterpret_cast<const uint4 *>(w1), b1, a1, nullptr, t1);
   k_prop_conv_tc<16, kKP2, false><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
-      g, a1, reinterpret_cast<const uint4 *>(w2), b2, a2, nullptr);
+      g, a1, reinterpret_cast<const uint4 *>(w2), b2, a2, nullptr, t2);
   k_prop_conv_tc<16, kKP2, true><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
-      g, a2, reinterpret_cast<const uint4 *>(w3), b3, nullptr, logits);
+      g, a2, reinterpret_cast<const uint4 *>(w3), b3, nullptr, logits, t3);
   if (conv_end) cudaEventRecord(conv_end, st);
 }
 

@@ -153,6 +153,12 @@ def test_training_loss_is_the_binary_cross_entropy():
     assert L == pytest.approx(0.5 * (2 * -np.log(s) + -np.log(1 - s)), rel=1e-14)
     # dL/db3 = inv * sum over used positions of (sigmoid(b) - y)
     assert g[-1] == pytest.approx(0.5 * ((s - 1) * 2 + s), rel=1e-14)
+    # a target of 255 leaves its position out of the loss
+    t2 = targets.copy()
+    t2[0, 2] = 255
+    L2, g2 = P.loss_and_grad(w, feats, t2, shapes, use, 0.5)
+    assert L2 == pytest.approx(0.5 * (2 * -np.log(s)), rel=1e-14)
+    assert g2[-1] == pytest.approx(0.5 * ((s - 1) * 2), rel=1e-14)
 
 
 def test_adam_closed_form():
