@@ -1196,6 +1196,51 @@ def run_adaptive3d(args):
                       "cell_updates_per_s": cells / (ms * 1e-3) if ms > 0 else None}), flush=True)
 
 
+def run_adaptive2d(args):
+    """The default workload's steps alone (no side measurements; the workload of the
+    2D launch list and of the stage kernel's traffic capture): --warmup untimed
+    steps, --steps steps of the captured graph timed with CUDA events (L2 flushed
+    before each), then the same number of eager steps with every stage launch
+    bracketed by CUDA events (the roofline pass of the default line)."""
+    import torch
+
+    import paper_1603_05211_gb300 as m
+
+    m.build()
+    m.load()
+    stream = torch.cuda.current_stream()
+    s = make_solver(m, stream)
+    if args.stage_kernel:
+        s.set_launch_shape(stage_kernel=args.stage_kernel)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        s.step(0.0, sync=False)
+    s.synchronize()
+    st0 = s.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        s.step(0.0, sync=False)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    cells = s.stats()["cell_updates"] - st0["cell_updates"]
+    s.profile_enable(True)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        s.step(0.0, sync=False)
+    p = s.profile_read()
+    hbm_peak, _ = measured_peaks()
+    ach = p["fv_bytes"] / (p["fv_ms"] * 1e-3) / 1e9 if p["fv_ms"] > 0 else 0.0
+    print(json.dumps({"case": WORKLOAD, "steps": args.steps, "ms_per_step": ms / max(1, args.steps),
+                      "cell_updates_per_s": cells / (ms * 1e-3) if ms > 0 else None,
+                      "stage_kernel": stage_kernel_names(p.get("fv_kernels", 0)),
+                      "stage_avg_us": 1e3 * p["fv_ms"] / max(1, p["fv_launches"]),
+                      "stage_bytes_per_launch": p["fv_bytes"] / max(1, p["fv_launches"]),
+                      "stage_frac_hbm": ach / hbm_peak}), flush=True)
+
+
 def run_autotune(args):
     """The launch-shape autotuner on one workload (a fresh sweep, printed with
     every candidate's time): --dim 2, the default adaptive 2D MR workload;
@@ -1520,7 +1565,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="adaptive",
                     choices=["adaptive", "uniform", "matched3d", "proposer", "laxliu", "paper3d", "epssweep",
-                             "richardson", "matched2d", "autotune", "adaptive3d"],
+                             "richardson", "matched2d", "autotune", "adaptive3d", "adaptive2d"],
                     help="uniform: only the stage kernel on an n^d grid (profiling workload); "
                          "matched3d: 3D blast, adaptive (heuristic / learned proposer) vs uniform at matched L1")
     ap.add_argument("--levels3d", type=int, default=5)
@@ -1556,6 +1601,8 @@ def main():
         run_matched3d(args)
     elif args.case == "proposer":
         run_proposer(args)
+    elif args.case == "adaptive2d":
+        run_adaptive2d(args)
     elif args.case == "adaptive3d":
         run_adaptive3d(args)
     elif args.case == "autotune":

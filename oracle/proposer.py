@@ -13,7 +13,8 @@ first two layers.
 Inference (``forward``): weights and every layer input are rounded to bfloat16
 (round to nearest, ties to even); accumulation is exact here (float64).
 
-Training (``loss_and_grad``, ``adam``): the forward pass on the unrounded
+Training (``loss_and_grad``, ``adam``; ``loss_and_grad_bf16`` adds the bfloat16
+rounding points of the tensor-core path): the forward pass on the unrounded
 master weights, the binary cross-entropy of the logits against next-step
 flags over the positions of level >= 1 whose parent block exists, normalised
 by a count given by the caller, its gradient by the chain rule through the
@@ -199,6 +200,54 @@ def loss_and_grad(blob: np.ndarray, feats: np.ndarray, targets: np.ndarray, shap
             g["W2"] = g["W2"] + conv_level_weight_grad(h1, d2)
             g["B2"] = g["B2"] + d2.sum(axis=(1, 2, 3))
             d1 = conv_level_input_grad(d2, W2) * (a1 > 0)
+            g["W1"] = g["W1"] + conv_level_weight_grad(x, d1)
+            g["B1"] = g["B1"] + d1.sum(axis=(1, 2, 3))
+            off += n
+    grad = np.concatenate([np.broadcast_to(np.asarray(g[k], dtype=np.float64), s).ravel()
+                           for k, s in (("W1", (16, 3, 27)), ("B1", (16,)), ("W2", (16, 16, 27)), ("B2", (16,)),
+                                        ("W3", (1, 16, 27)), ("B3", (1,)))])
+    return loss, grad
+
+
+def _bf16_f64(x: np.ndarray) -> np.ndarray:
+    """float64 -> float32 -> nearest bfloat16, returned as float64."""
+    return bf16_round(np.asarray(x, dtype=np.float64).astype(np.float32)).astype(np.float64)
+
+
+def loss_and_grad_bf16(blob: np.ndarray, feats: np.ndarray, targets: np.ndarray, shapes, use: np.ndarray,
+                       inv_count: float, rnd=_bf16_f64):
+    """The loss and gradient of training in bfloat16 (the tensor-core path): the
+    forward pass of ``forward`` (weights, features and hidden activations rounded
+    by ``rnd``), dL/dz of the binary cross-entropy (positions where ``use`` holds
+    and the target is not 255), the gradients of the layer inputs through the
+    rounded weights, masked by the ReLU and rounded by ``rnd`` (dL/dz itself is
+    rounded before it enters the layer-3 input gradient), and the weight
+    gradients as products of those rounded operands, accumulated exactly.  With
+    ``rnd`` the identity this is ``loss_and_grad``."""
+    (W1, B1), (W2, B2), (W3, B3) = unpack(blob, np.float64)
+    W1b, W2b, W3b = rnd(W1), rnd(W2), rnd(W3)
+    g = {k: 0.0 for k in ("W1", "B1", "W2", "B2", "W3", "B3")}
+    loss = 0.0
+    for f, y in zip(np.asarray(feats, dtype=np.float64), np.asarray(targets)):
+        off = 0
+        for sh in shapes:
+            n = int(np.prod(sh))
+            x = rnd(f[:, off:off + n]).reshape((3,) + sh)
+            u = use[off:off + n].reshape(sh) & (y[off:off + n].reshape(sh) != 255)
+            yy = (y[off:off + n].reshape(sh) == 1).astype(np.float64)
+            h1 = rnd(np.maximum(conv_level(x, W1b, B1), 0.0))
+            h2 = rnd(np.maximum(conv_level(h1, W2b, B2), 0.0))
+            z = conv_level(h2, W3b, B3)[0]
+            lz = np.maximum(z, 0.0) - z * yy + np.log1p(np.exp(-np.abs(z)))
+            loss += inv_count * float(np.sum(lz[u]))
+            dz = np.where(u, (1.0 / (1.0 + np.exp(-z)) - yy) * inv_count, 0.0)[None]
+            dzf = dz.astype(np.float32).astype(np.float64) if rnd is _bf16_f64 else dz
+            g["W3"] = g["W3"] + conv_level_weight_grad(h2, dzf)
+            g["B3"] = g["B3"] + dzf.sum(axis=(1, 2, 3))
+            d2 = rnd(conv_level_input_grad(rnd(dzf), W3b) * (h2 > 0))
+            g["W2"] = g["W2"] + conv_level_weight_grad(h1, d2)
+            g["B2"] = g["B2"] + d2.sum(axis=(1, 2, 3))
+            d1 = rnd(conv_level_input_grad(d2, W2b) * (h1 > 0))
             g["W1"] = g["W1"] + conv_level_weight_grad(x, d1)
             g["B1"] = g["B1"] + d1.sum(axis=(1, 2, 3))
             off += n

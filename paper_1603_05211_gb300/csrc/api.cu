@@ -94,7 +94,7 @@ struct mrfv_ctx {
   long long ptiles;               // 128-position tiles
   unsigned long long *ptcount;    // tiles computed per layer while profiling
   long long pdense;               // dense inferences while profiling
-  __nv_bfloat16 *pa0, *pa1, *pa2, *pw1, *pw2, *pw3;
+  __nv_bfloat16 *pa0, *pa1, *pa2, *pw1, *pw2, *pw3, *pw3t, *pw2t;
   double *ploss;
   bool has_weights;
   int adam_t;
@@ -247,6 +247,7 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
   size_t opf = L.take(3 * maptotal * 4), opl = L.take(maptotal * 4), opa0 = L.take(8 * maptotal * 2);
   size_t opa1 = L.take(16 * maptotal * 2), opa2 = L.take(16 * maptotal * 2);
   size_t opw1 = L.take(16 * 224 * 2), opw2 = L.take(16 * 432 * 2), opw3 = L.take(16 * 432 * 2);
+  size_t opw3t = L.take(16 * 224 * 2), opw2t = L.take(16 * 432 * 2);
   size_t opb = L.take(3 * 16 * 4), opblob = L.take(4 * NW * 4), opwork = L.take((size_t)kPropWorkPerPos * maptotal * 4), oploss = L.take(8);
   const long long ptiles = (maptotal + 127) / 128;
   size_t optile = L.take(3 * (size_t)ptiles), optc = L.take(3 * 8);
@@ -288,6 +289,8 @@ size_t layout(const mrfv_config *cfg, const Geo &g, long long cap, long long map
     c->pw1 = (__nv_bfloat16 *)(a + opw1);
     c->pw2 = (__nv_bfloat16 *)(a + opw2);
     c->pw3 = (__nv_bfloat16 *)(a + opw3);
+    c->pw3t = (__nv_bfloat16 *)(a + opw3t);
+    c->pw2t = (__nv_bfloat16 *)(a + opw2t);
     c->pb1 = (float *)(a + opb);
     c->pb2 = c->pb1 + 16;
     c->pb3 = c->pb2 + 16;
@@ -1441,7 +1444,8 @@ int mrfv_proposer_train(mrfv_ctx *c, const float *feat, const uint8_t *target, i
   for (int k = 0; k < steps && rc == MRFV_OK; k++) {
     cudaMemsetAsync(c->ploss, 0, 8, c->st);
     launch_prop_train_step(c->g, df, dt, nsnap, c->pblob, c->pgrad, c->pm1, c->pm2, ++c->adam_t, lr, c->pwork,
-                           c->ploss, 1, c->st);
+                           c->ploss, 1, c->pa0, c->pa1, c->pa2, c->pw1, c->pb1, c->pw2, c->pb2, c->pw3, c->pb3,
+                           c->pw3t, c->pw2t, c->nsm, c->st);
     rc = check_launch(c, "mrfv_proposer_train");
     if (rc == MRFV_OK && k == steps - 1) {
       rc = check_device(c, "mrfv_proposer_train");
@@ -1473,7 +1477,8 @@ int mrfv_proposer_grad(mrfv_ctx *c, const float *feat, const uint8_t *target, in
   cudaMemcpy(dt, target, (size_t)nsnap * np, cudaMemcpyHostToDevice);
   cudaMemsetAsync(c->ploss, 0, 8, c->st);
   launch_prop_train_step(c->g, df, dt, nsnap, c->pblob, c->pgrad, c->pm1, c->pm2, c->adam_t, 0.f, c->pwork, c->ploss,
-                         0, c->st);
+                         0, c->pa0, c->pa1, c->pa2, c->pw1, c->pb1, c->pw2, c->pb2, c->pw3, c->pb3, c->pw3t, c->pw2t,
+                         c->nsm, c->st);
   int rc = check_launch(c, "mrfv_proposer_grad");
   if (rc == MRFV_OK) rc = check_device(c, "mrfv_proposer_grad");
   if (rc == MRFV_OK) {

@@ -69,9 +69,10 @@ struct FVArgs {
   double theta;
 };
 
-// training scratch of the learned proposer, in floats per block position:
-// h1, h2 (16 channels each), logits z, dL/dz, and the two 16-channel gradients
-constexpr long long kPropWorkPerPos = 16 + 16 + 1 + 1 + 16 + 16;
+// training scratch of the learned proposer, in floats per block position: logits z
+// and dL/dz (FP32), and the BF16 rows of dL/dz (8 channels), dL/dh2 and dL/dh1 (16
+// each), i.e. 2 + 4 + 8 + 8 floats, and two for the 16-byte alignment of the rows
+constexpr long long kPropWorkPerPos = 2 + 4 + 8 + 8 + 2;
 
 // rows of the per-level step table (see FVArgs::lev): stage 0 has coef 1/2, stage 1 coef 1
 __host__ __device__ inline int lev_index(int stage, int l, int k) { return (stage * MAXL + l) * 4 + k; }

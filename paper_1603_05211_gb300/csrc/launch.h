@@ -109,8 +109,13 @@ void launch_prop_infer(const Geo &, const float *feat, __nv_bfloat16 *a0, __nv_b
 void launch_prop_mark(const Geo &, const float *logits, uint8_t *need, int grid, cudaStream_t);
 void launch_pack_weights(const float *blob, __nv_bfloat16 *w1, float *b1, __nv_bfloat16 *w2, float *b2,
                          __nv_bfloat16 *w3, float *b3, cudaStream_t);
-// adam = 0: gradient and loss only (weights and moments untouched)
+// adam = 0: gradient and loss only (weights and moments untouched); a0..a2, w1..b3:
+// the inference buffers and operands (overwritten); w3t, w2t: the mirrored-tap
+// operands of the backward-data convolutions
 void launch_prop_train_step(const Geo &, const float *feat, const uint8_t *target, int ns, float *blob, float *grad,
-                            float *m1, float *m2, int t, float lr, float *work, double *loss, int adam, cudaStream_t);
+                            float *m1, float *m2, int t, float lr, float *work, double *loss, int adam,
+                            __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2, __nv_bfloat16 *w1, float *b1,
+                            __nv_bfloat16 *w2, float *b2, __nv_bfloat16 *w3, float *b3, __nv_bfloat16 *w3t,
+                            __nv_bfloat16 *w2t, int nsm, cudaStream_t);
 
 }  // namespace mrfv

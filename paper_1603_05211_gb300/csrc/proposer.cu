@@ -17,8 +17,9 @@
 // Every wait is bounded; on expiry the kernel records EB_TIMEOUT, frees its TMEM
 // and returns.
 //
-// Training: FP32 CUDA-core kernels (direct convolution forward, binary
-// cross-entropy gradient, backward convolution for weights and inputs, Adam).
+// Training: the same tensor-core convolutions for the forward pass and, with the
+// taps mirrored, for the gradients of the layer inputs; weight gradients from the
+// BF16 rows summed in double on the CUDA cores; Adam on FP32 master weights.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -174,19 +175,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsign
 // 16-byte rows of core matrices and is gathered with vector loads.
 // Wcm: the 16 x KP BF16 weight operand, already in the shared-memory
 // core-matrix byte order (k_pack_weights); bias FP32 [16].
-// LAST: logits[p] = acc[0] + bias[0]; otherwise out[p][n] = bf16(relu(acc + bias)).
+// MODE kHidden: out[p][n] = bf16(relu(acc + bias)); kLogit: logits[p] = acc[0] + bias[0];
+// kBackData (training, the gradient of a layer input): out[p][n] = bf16(acc) where the
+// forward activation act[p][n] > 0, else 0 (the ReLU's derivative); no bias.
+constexpr int kHidden = 0, kLogit = 1, kBackData = 2;
 constexpr int kConvThreads = 256;  // two threads per tile row: taps 0..13 and 14..26
 
 // tneed (may be null: every tile): per 128-position tile, nonzero when some position
 // of the tile is needed by the layer; other tiles are skipped (their outputs stay as
 // they were: only needed positions are read downstream).
-template <int CIN, int KP, bool LAST>
+template <int CIN, int KP, int MODE>
 __global__ void __launch_bounds__(kConvThreads) k_prop_conv_tc(Geo g, const __nv_bfloat16 *__restrict__ in,
                                                                const uint4 *__restrict__ Wcm,
                                                                const float *__restrict__ bias,
                                                                __nv_bfloat16 *__restrict__ out,
                                                                float *__restrict__ logits,
-                                                               const uint8_t *__restrict__ tneed) {
+                                                               const uint8_t *__restrict__ tneed,
+                                                               const __nv_bfloat16 *__restrict__ act) {
+  constexpr bool LAST = MODE == kLogit;
   constexpr int M = 128, N = 16;
   constexpr int KREAL = CIN * 27;
   static_assert(CIN == 8 || CIN == 16, "channel-last rows of 16 or 32 bytes");
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(kConvThreads) k_prop_conv_tc(Geo g, const __nv
   if (KP > KREAL && half == 0) *reinterpret_cast<uint4 *>(sA + cm_offset(row, KREAL, KP)) = zero;
   float b[8];
 #pragma unroll
-  for (int n = 0; n < 8; n++) b[n] = bias[8 * (warp >> 2) + n];
+  for (int n = 0; n < 8; n++) b[n] = MODE == kBackData ? 0.f : bias[8 * (warp >> 2) + n];
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -307,6 +313,20 @@ __global__ void __launch_bounds__(kConvThreads) k_prop_conv_tc(Geo g, const __nv
     if (q < npos) {
       if (LAST) {
         if (warp < 4) logits[q] = __uint_as_float(r[0]) + b[0];
+      } else if (MODE == kBackData) {
+        const uint4 fa = reinterpret_cast<const uint4 *>(act)[q * 2 + (warp >> 2)];  // 8 forward activations
+        const uint32_t fw[4] = {fa.x, fa.y, fa.z, fa.w};
+        uint32_t pk[4];
+#pragma unroll
+        for (int n = 0; n < 4; n++) {
+          // a bfloat16 is positive when its sign bit is clear and it is not zero
+          const bool plo = (fw[n] & 0x8000u) == 0 && (fw[n] & 0x7FFFu) != 0;
+          const bool phi = (fw[n] & 0x80000000u) == 0 && (fw[n] & 0x7FFF0000u) != 0;
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(plo ? __uint_as_float(r[2 * n]) : 0.f,
+                                                    phi ? __uint_as_float(r[2 * n + 1]) : 0.f);
+          pk[n] = *reinterpret_cast<uint32_t *>(&h2);
+        }
+        reinterpret_cast<uint4 *>(out)[q * 2 + (warp >> 2)] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
       } else {
         uint32_t pk[4];
 #pragma unroll
@@ -391,29 +411,7 @@ __global__ void k_prop_mark(Geo g, const float *__restrict__ logits, uint8_t *ne
   }
 }
 
-// ---------------------------------------------------------------- training (FP32, CUDA cores)
-// direct convolution: y[co][p] = b[co] + sum_{ci,tap} w[co][ci][tap] * x[ci][p+tap]
-__global__ void k_conv_fwd_f32(Geo g, const float *__restrict__ x, int cin, const float *__restrict__ w,
-                               const float *__restrict__ b, int cout, float *__restrict__ y, int relu) {
-  const long long n = g.mapoff[g.L + 1];
-  const int dim3d = g.dim == 3;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n * cout;
-       idx += (long long)gridDim.x * blockDim.x) {
-    int co = (int)(idx / n);
-    long long p = idx % n;
-    int l = pos_level(g, p);
-    float acc = b[co];
-    for (int t = 0; t < 27; t++) {
-      int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-      if (!dim3d && dz != 0) continue;
-      long long q = pos_neighbour(g, l, p, dx, dy, dz);
-      if (q < 0) continue;
-      for (int ci = 0; ci < cin; ci++) acc += w[(co * cin + ci) * 27 + t] * x[(long long)ci * n + q];
-    }
-    y[(long long)co * n + p] = relu ? fmaxf(acc, 0.f) : acc;
-  }
-}
-
+// ---------------------------------------------------------------- training: loss, Adam
 // binary cross-entropy with logits, averaged over positions of level >= 1
 // whose parent exists and whose target is not 255 (excluded): dL/dz = (sigmoid(z) - y) / count
 __global__ void k_bce_grad(Geo g, const float *__restrict__ z, const uint8_t *__restrict__ target,
@@ -440,74 +438,6 @@ __global__ void k_bce_grad(Geo g, const float *__restrict__ z, const uint8_t *__
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
-}
-
-// gradient of a ReLU layer output -> pre-activation: zero where the output was 0
-__global__ void k_relu_back(const float *__restrict__ y, float *__restrict__ dy, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    if (!(y[i] > 0.f)) dy[i] = 0.f;
-}
-
-// dW[co][ci][tap] += sum_p dy[co][p] x[ci][p+tap]; db[co] += sum_p dy[co][p]
-// one CTA per (co, ci, tap) weight (+ the bias on ci == 0, tap == 13)
-__global__ void k_conv_dw(Geo g, const float *__restrict__ x, int cin, const float *__restrict__ dy, int cout,
-                          float *__restrict__ dw, float *__restrict__ db) {
-  const long long n = g.mapoff[g.L + 1];
-  const int dim3d = g.dim == 3;
-  int wi = blockIdx.x;  // (co * cin + ci) * 27 + t
-  int t = wi % 27, ci = (wi / 27) % cin, co = wi / (27 * cin);
-  int dz = t / 9 - 1, dy_ = (t / 3) % 3 - 1, dx = t % 3 - 1;
-  __shared__ double red[2][32];
-  double acc = 0.0, accb = 0.0;
-  if (dim3d || dz == 0) {
-    for (long long p = threadIdx.x; p < n; p += blockDim.x) {
-      float d = dy[(long long)co * n + p];
-      if (d == 0.f) continue;
-      long long q = pos_neighbour(g, pos_level(g, p), p, dx, dy_, dz);
-      if (q >= 0) acc += (double)d * x[(long long)ci * n + q];
-      accb += d;
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    accb += __shfl_xor_sync(0xffffffffu, accb, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = acc;
-    red[1][threadIdx.x >> 5] = accb;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0, sb = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-      s += red[0][w];
-      sb += red[1][w];
-    }
-    dw[wi] += (float)s;
-    if (ci == 0 && t == 13) db[co] += (float)sb;
-  }
-}
-
-// dx[ci][q] = sum_{co,tap} dy[co][q - tap] w[co][ci][tap]
-__global__ void k_conv_dx(Geo g, const float *__restrict__ dy, int cout, const float *__restrict__ w, int cin,
-                          float *__restrict__ dx) {
-  const long long n = g.mapoff[g.L + 1];
-  const int dim3d = g.dim == 3;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n * cin;
-       idx += (long long)gridDim.x * blockDim.x) {
-    int ci = (int)(idx / n);
-    long long q = idx % n;
-    int l = pos_level(g, q);
-    float acc = 0.f;
-    for (int t = 0; t < 27; t++) {
-      int dz = t / 9 - 1, dyy = (t / 3) % 3 - 1, dxx = t % 3 - 1;
-      if (!dim3d && dz != 0) continue;
-      long long p = pos_neighbour(g, l, q, -dxx, -dyy, -dz);
-      if (p < 0) continue;
-      for (int co = 0; co < cout; co++) acc += dy[(long long)co * n + p] * w[(co * cin + ci) * 27 + t];
-    }
-    dx[(long long)ci * n + q] = acc;
-  }
 }
 
 // Adam on the FP32 master weights (beta1 0.9, beta2 0.999, eps 1e-8), step t; the
@@ -548,6 +478,78 @@ __global__ void k_pack_weights(const float *__restrict__ blob, __nv_bfloat16 *w1
   }
 }
 
+// ---------------------------------------------------------------- training on the tensor cores
+// The gradient of a layer's input is the correlation of the output gradient with
+// the taps mirrored (tap t -> 26 - t) and the channel roles swapped:
+//   dIn[ci](q) = sum_{co,t} W[co][ci][26 - t] dOut[co](q + off(t)).
+// These operands, in the core-matrix byte order of k_prop_conv_tc: layer 3 (one
+// output channel; input rows of 8 channels, channel 0 = dz): w3t[ci][t*8 + 0] =
+// W3[0][ci][26 - t]; layer 2: w2t[ci][t*16 + co] = W2[co][ci][26 - t].
+__global__ void k_pack_weights_back(const float *__restrict__ blob, __nv_bfloat16 *w3t, __nv_bfloat16 *w2t) {
+  const float *W1 = blob, *B1 = W1 + 16 * 81, *W2 = B1 + 16, *B2 = W2 + 16 * 432, *W3 = B2 + 16;
+  for (int i = threadIdx.x; i < 16 * kKP1; i += blockDim.x) {
+    int n = i / kKP1, k = i % kKP1, t = k / 8, c = k % 8;
+    float v = (t < 27 && c == 0) ? W3[n * 27 + (26 - t)] : 0.f;
+    w3t[cm_offset(n, k, kKP1) / 2] = __float2bfloat16_rn(v);
+  }
+  for (int i = threadIdx.x; i < 16 * kKP2; i += blockDim.x) {
+    int n = i / kKP2, k = i % kKP2, t = k / 16, co = k % 16;
+    w2t[cm_offset(n, k, kKP2) / 2] = __float2bfloat16_rn(W2[(co * 16 + n) * 27 + (26 - t)]);
+  }
+}
+
+// dL/dz (FP32 [n]) -> BF16 rows [n][8], channel 0 = dz
+__global__ void k_dz_rows(const float *__restrict__ dz, uint4 *__restrict__ rows, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(dz[p], 0.f);
+    rows[p] = make_uint4(*reinterpret_cast<uint32_t *>(&a), 0u, 0u, 0u);
+  }
+}
+
+// Weight (and bias) gradient from channel-last BF16 rows: x rows [n][XS] (channels
+// 0..cin-1 used), output gradient either FP32 [n] (dzf, one channel) or BF16 rows
+// [n][16] (dyr).  dW[co][ci][t] += sum_p dy[co][p] x[ci][p + off(t)], summed in double;
+// db[co] += sum_p dy[co][p] (on ci == 0, t == 13).  One CTA per weight.
+template <int XS>
+__global__ void k_conv_dw_rows(Geo g, const __nv_bfloat16 *__restrict__ x, int cin, const float *__restrict__ dzf,
+                               const __nv_bfloat16 *__restrict__ dyr, int cout, float *__restrict__ dw,
+                               float *__restrict__ db) {
+  const long long n = g.mapoff[g.L + 1];
+  const int dim3d = g.dim == 3;
+  const int wi = blockIdx.x;  // (co * cin + ci) * 27 + t
+  const int t = wi % 27, ci = (wi / 27) % cin, co = wi / (27 * cin);
+  const int dz = t / 9 - 1, dy_ = (t / 3) % 3 - 1, dx = t % 3 - 1;
+  __shared__ double red[2][32];
+  double acc = 0.0, accb = 0.0;
+  if (dim3d || dz == 0) {
+    for (long long p = threadIdx.x; p < n; p += blockDim.x) {
+      const float d = dzf ? dzf[p] : __bfloat162float(dyr[p * 16 + co]);
+      if (d == 0.f) continue;
+      const long long q = pos_neighbour(g, pos_level(g, p), p, dx, dy_, dz);
+      if (q >= 0) acc += (double)d * (double)__bfloat162float(x[q * XS + ci]);
+      accb += d;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    accb += __shfl_xor_sync(0xffffffffu, accb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = acc;
+    red[1][threadIdx.x >> 5] = accb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sw = 0, sb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      sw += red[0][w];
+      sb += red[1][w];
+    }
+    dw[wi] += (float)sw;
+    if (ci == 0 && t == 13) db[co] += (float)sb;
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 template <typename T>
 void launch_prop_features(const Geo &g, const T *U, const double *maxdet, const T *scale, double eps, float *feat,
@@ -561,11 +563,15 @@ template void launch_prop_features<double>(const Geo &, const double *, const do
                                            float *, int, cudaStream_t);
 
 void prop_setup() {
-  cudaFuncSetAttribute(k_prop_conv_tc<8, kKP1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_prop_conv_tc<8, kKP1, kBackData>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)conv_smem<kKP1>());
-  cudaFuncSetAttribute(k_prop_conv_tc<16, kKP2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_prop_conv_tc<16, kKP2, kBackData>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)conv_smem<kKP2>());
-  cudaFuncSetAttribute(k_prop_conv_tc<16, kKP2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_prop_conv_tc<8, kKP1, kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)conv_smem<kKP1>());
+  cudaFuncSetAttribute(k_prop_conv_tc<16, kKP2, kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)conv_smem<kKP2>());
+  cudaFuncSetAttribute(k_prop_conv_tc<16, kKP2, kLogit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)conv_smem<kKP2>());
 }
 
@@ -616,12 +622,12 @@ void launch_prop_infer(const Geo &g, const float *feat, __nv_bfloat16 *a0, __nv_
   long long fb = (n + 255) / 256;
   k_feat_rows<<<(int)(fb < 4 * nsm ? fb : 4 * nsm), 256, 0, st>>>(feat, reinterpret_cast<uint4 *>(a0), n);
   if (conv_begin) cudaEventRecord(conv_begin, st);
-  k_prop_conv_tc<8, kKP1, false><<<grid1, kConvThreads, conv_smem<kKP1>(), st>>>(
-      g, a0, reinterpret_cast<const uint4 *>(w1), b1, a1, nullptr, t1);
-  k_prop_conv_tc<16, kKP2, false><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
-      g, a1, reinterpret_cast<const uint4 *>(w2), b2, a2, nullptr, t2);
-  k_prop_conv_tc<16, kKP2, true><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
-      g, a2, reinterpret_cast<const uint4 *>(w3), b3, nullptr, logits, t3);
+  k_prop_conv_tc<8, kKP1, kHidden><<<grid1, kConvThreads, conv_smem<kKP1>(), st>>>(
+      g, a0, reinterpret_cast<const uint4 *>(w1), b1, a1, nullptr, t1, nullptr);
+  k_prop_conv_tc<16, kKP2, kHidden><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
+      g, a1, reinterpret_cast<const uint4 *>(w2), b2, a2, nullptr, t2, nullptr);
+  k_prop_conv_tc<16, kKP2, kLogit><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
+      g, a2, reinterpret_cast<const uint4 *>(w3), b3, nullptr, logits, t3, nullptr);
   if (conv_end) cudaEventRecord(conv_end, st);
 }
 
@@ -634,37 +640,54 @@ void launch_pack_weights(const float *blob, __nv_bfloat16 *w1, float *b1, __nv_b
   k_pack_weights<<<1, 256, 0, st>>>(blob, w1, b1, w2, b2, w3, b3);
 }
 
-// One Adam step on a batch of snapshots: forward in FP32 with the BF16-rounded
-// weights' master copy, BCE loss, backward, update.  feat: [ns][3][n] floats,
-// target: [ns][n] bytes (device).  work: scratch of kPropWorkPerPos * n floats.
+// One Adam step on a batch of snapshots, on the tensor cores: per snapshot the
+// BF16 forward pass of inference (layer inputs rounded to BF16, FP32 accumulation),
+// the binary cross-entropy gradient dz (FP32), the gradients of the layer inputs by
+// the mirrored-tap convolutions (BF16 operands, FP32 accumulation, rounded to BF16
+// and masked by the forward ReLU), and the weight gradients from the BF16 rows
+// (summed in double on the CUDA cores); then Adam on the FP32 master weights and
+// the re-packing of the BF16 operands.  feat: [ns][3][n] floats, target: [ns][n]
+// bytes (device).  work: kPropWorkPerPos floats per position (z, dz, and the BF16
+// rows of dz, dL/dh2, dL/dh1).
 void launch_prop_train_step(const Geo &g, const float *feat, const uint8_t *target, int ns, float *blob, float *grad,
                             float *m1, float *m2, int t, float lr, float *work, double *loss, int adam,
-                            cudaStream_t st) {
+                            __nv_bfloat16 *a0, __nv_bfloat16 *a1, __nv_bfloat16 *a2, __nv_bfloat16 *w1,
+                            float *b1, __nv_bfloat16 *w2, float *b2, __nv_bfloat16 *w3, float *b3,
+                            __nv_bfloat16 *w3t, __nv_bfloat16 *w2t, int nsm, cudaStream_t st) {
   long long n = g.mapoff[g.L + 1];
   const int NW = 16 * 81 + 16 + 16 * 432 + 16 + 432 + 1;
-  float *W1 = blob, *B1 = W1 + 16 * 81, *W2 = B1 + 16, *B2 = W2 + 16 * 432, *W3 = B2 + 16, *B3 = W3 + 432;
   float *gW1 = grad, *gB1 = gW1 + 16 * 81, *gW2 = gB1 + 16, *gB2 = gW2 + 16 * 432, *gW3 = gB2 + 16, *gB3 = gW3 + 432;
-  float *h1 = work, *h2 = h1 + 16 * n, *z = h2 + 16 * n, *dz = z + n, *d2 = dz + n, *d1 = d2 + 16 * n;
+  const long long n4 = (n + 3) & ~3LL;                             // 16-byte aligned rows below
+  float *z = work, *dz = z + n4;
+  __nv_bfloat16 *dzr = reinterpret_cast<__nv_bfloat16 *>(dz + n4);  // [n][8]
+  __nv_bfloat16 *d2r = dzr + 8 * n;                                 // [n][16]
+  __nv_bfloat16 *d1r = d2r + 16 * n;                                // [n][16]
   cudaMemsetAsync(grad, 0, NW * sizeof(float), st);
-  // count of the positions entering the loss (level >= 1 with an existing parent) is
-  // approximated by the number of positions of levels >= 1 (sets the loss scale only)
+  launch_pack_weights(blob, w1, b1, w2, b2, w3, b3, st);
+  k_pack_weights_back<<<1, 256, 0, st>>>(blob, w3t, w2t);
+  // the loss is normalised by the positions of levels >= 1 times the snapshots (a
+  // fixed scale; the positions entering it are selected inside k_bce_grad)
   float inv = 1.f / (float)((n - g.mapoff[1]) * (long long)ns);
-  int grid = 1024;
+  const int grid = 1024;
+  const long long tiles = (n + 127) / 128;
+  const int grid1 = (int)(tiles < 3 * nsm ? tiles : 3 * nsm), grid2 = (int)(tiles < nsm ? tiles : nsm);
   for (int k = 0; k < ns; k++) {
     const float *x = feat + (long long)k * 3 * n;
-    k_conv_fwd_f32<<<grid, 256, 0, st>>>(g, x, 3, W1, B1, 16, h1, 1);
-    k_conv_fwd_f32<<<grid, 256, 0, st>>>(g, h1, 16, W2, B2, 16, h2, 1);
-    k_conv_fwd_f32<<<grid, 256, 0, st>>>(g, h2, 16, W3, B3, 1, z, 0);
+    launch_prop_infer(g, x, a0, a1, a2, w1, b1, w2, b2, w3, b3, z, nsm, nullptr, nullptr, nullptr, st);
     k_bce_grad<<<grid, 256, 0, st>>>(g, z, target + (long long)k * n, dz, loss, inv);
-    k_conv_dw<<<432, 256, 0, st>>>(g, h2, 16, dz, 1, gW3, gB3);
-    k_conv_dx<<<grid, 256, 0, st>>>(g, dz, 1, W3, 16, d2);
-    k_relu_back<<<grid, 256, 0, st>>>(h2, d2, 16 * n);
-    k_conv_dw<<<16 * 432, 256, 0, st>>>(g, h1, 16, d2, 16, gW2, gB2);
-    k_conv_dx<<<grid, 256, 0, st>>>(g, d2, 16, W2, 16, d1);
-    k_relu_back<<<grid, 256, 0, st>>>(h1, d1, 16 * n);
-    k_conv_dw<<<16 * 81, 256, 0, st>>>(g, x, 3, d1, 16, gW1, gB1);
+    k_dz_rows<<<grid, 256, 0, st>>>(dz, reinterpret_cast<uint4 *>(dzr), n);
+    k_conv_dw_rows<16><<<432, 256, 0, st>>>(g, a2, 16, dz, nullptr, 1, gW3, gB3);
+    k_prop_conv_tc<8, kKP1, kBackData><<<grid1, kConvThreads, conv_smem<kKP1>(), st>>>(
+        g, dzr, reinterpret_cast<const uint4 *>(w3t), nullptr, d2r, nullptr, nullptr, a2);
+    k_conv_dw_rows<16><<<16 * 432, 256, 0, st>>>(g, a1, 16, nullptr, d2r, 16, gW2, gB2);
+    k_prop_conv_tc<16, kKP2, kBackData><<<grid2, kConvThreads, conv_smem<kKP2>(), st>>>(
+        g, d2r, reinterpret_cast<const uint4 *>(w2t), nullptr, d1r, nullptr, nullptr, a1);
+    k_conv_dw_rows<8><<<16 * 81, 256, 0, st>>>(g, a0, 3, nullptr, d1r, 16, gW1, gB1);
   }
-  if (adam) k_adam<<<64, 256, 0, st>>>(blob, grad, m1, m2, NW, lr, t);
+  if (adam) {
+    k_adam<<<64, 256, 0, st>>>(blob, grad, m1, m2, NW, lr, t);
+    launch_pack_weights(blob, w1, b1, w2, b2, w3, b3, st);
+  }
 }
 
 }  // namespace mrfv

@@ -176,3 +176,20 @@ def test_adam_closed_form():
     vv = 0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2
     assert m2 == pytest.approx(mm, rel=1e-14) and v2 == pytest.approx(vv, rel=1e-14)
     assert w2 == pytest.approx(w1 - 0.01 * (mm / 0.19) / (np.sqrt(vv / (1 - 0.999 ** 2)) + 1e-8), rel=1e-13)
+
+
+@pytest.mark.parametrize("dim,levels,base", [(2, 3, (1, 2)), (3, 2, (2, 1, 2))])
+def test_bf16_training_gradient_reduces_to_the_pinned_one(dim, levels, base):
+    """With its rounding taken out, the bfloat16 training gradient is the gradient
+    pinned by finite differences above; with it, it stays close (the rounding
+    points move each operand by at most 2^-8 relative)."""
+    w, shapes, feats, targets, use = _random_case(dim, levels, base, 7 + dim)
+    inv = 1.0 / use.size
+    L, g = P.loss_and_grad(w, feats, targets, shapes, use, inv)
+    Li, gi = P.loss_and_grad_bf16(w, feats, targets, shapes, use, inv, rnd=lambda a: np.asarray(a, np.float64))
+    assert Li == pytest.approx(L, rel=1e-12)
+    assert np.allclose(gi, g, rtol=1e-10, atol=1e-14)
+    Lb, gb = P.loss_and_grad_bf16(w, feats, targets, shapes, use, inv)
+    assert Lb == pytest.approx(L, rel=0.05)
+    assert np.abs(gb - g).max() <= 0.1 * np.abs(g).max()
+    assert not np.array_equal(gb, g)

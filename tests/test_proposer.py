@@ -180,10 +180,14 @@ def _snapshots(mrfv, kw, nsnap, seed=2):
 @pytest.mark.gpu
 @pytest.mark.parametrize("dim", [2, 3])
 def test_proposer_training_gradient_and_adam_match_oracle(mrfv, dim):
-    """The training kernels (forward, BCE gradient, backward convolutions for the
-    weights and the inputs, ReLU masks) against the oracle's backward pass, layer
-    by layer; then three Adam steps against the oracle's Adam on the same
-    gradients."""
+    """The training kernels (the tensor-core forward pass, the BCE gradient, the
+    mirrored-tap tensor-core convolutions for the gradients of the layer inputs
+    with the ReLU masks, the weight gradients from the BF16 rows) against the
+    oracle's bfloat16 backward pass, layer by layer; then three Adam steps against
+    the oracle's Adam on the same gradients.  The two sides round the same values
+    to bfloat16; they differ where FP32 accumulation in a different order crosses a
+    rounding tie, so each layer's gradient must agree within 0.5 % of its largest
+    entry (a wrong tap, sign or mask changes entries by their own size)."""
     if dim == 2:
         kw = dict(dim=2, precision="fp32", levels=5, base_blocks=(2, 2, 1), adapt=True, eps=1e-3, bc=1)
     else:
@@ -213,12 +217,12 @@ def test_proposer_training_gradient_and_adam_match_oracle(mrfv, dim):
     n0 = int(np.prod(shapes[0]))
     inv = 1.0 / (feats.shape[0] * (use.size - n0))
     lg, gg = s.proposer_grad(feats, targets)
-    lo, go = P.loss_and_grad(w.astype(np.float64), feats, targets, shapes, use, inv)
-    assert lg == pytest.approx(lo, rel=1e-5)
+    lo, go = P.loss_and_grad_bf16(w.astype(np.float64), feats, targets, shapes, use, inv)
+    assert lg == pytest.approx(lo, rel=1e-4)
     o = 0
     for name, size in (("W1", 16 * 81), ("B1", 16), ("W2", 16 * 432), ("B2", 16), ("W3", 432), ("B3", 1)):
         a, b = gg[o:o + size], go[o:o + size]
-        assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max() + 1e-12, (name, np.abs(a - b).max(), np.abs(b).max())
+        assert np.abs(a - b).max() <= 5e-3 * np.abs(b).max() + 1e-12, (name, np.abs(a - b).max(), np.abs(b).max())
         o += size
     # Adam: each step applies the gradient the grad entry point reports for the current weights
     m = np.zeros(P.NWEIGHTS)
