@@ -110,16 +110,17 @@ __device__ __forceinline__ T predict(const T *P, int x, int y, int z, T si, T sj
 // Per-level step table (computed once per step, in double): dt_l = dt (global) or
 // dt * 2^(L-l) (level-dependent steps); for each stage coefficient c (1/2, 1)
 // (c dt_l) / dx_{l,n}; and its single-precision copy.
+// One entry (level l, stage st) of the table.
+__device__ inline void level_params_entry(const Geo &g, double dt, int lts, double *lev, float *levf, int l, int st) {
+  double dtl = lts ? ldexp(dt, g.L - l) : dt;
+  double coef = st == 0 ? 0.5 : 1.0;
+  for (int n = 0; n < 3; n++) lev[lev_index(st, l, n)] = (coef * dtl) / g.dx[l][n];
+  lev[lev_index(st, l, 3)] = dtl;
+  for (int k = 0; k < 4; k++) levf[lev_index(st, l, k)] = (float)lev[lev_index(st, l, k)];
+}
 __device__ inline void level_params_dev(const Geo &g, double dt, int lts, double *lev, float *levf) {
-  for (int l = 0; l <= g.L; l++) {
-    double dtl = lts ? ldexp(dt, g.L - l) : dt;
-    for (int st = 0; st < 2; st++) {
-      double coef = st == 0 ? 0.5 : 1.0;
-      for (int n = 0; n < 3; n++) lev[lev_index(st, l, n)] = (coef * dtl) / g.dx[l][n];
-      lev[lev_index(st, l, 3)] = dtl;
-      for (int k = 0; k < 4; k++) levf[lev_index(st, l, k)] = (float)lev[lev_index(st, l, k)];
-    }
-  }
+  for (int l = 0; l <= g.L; l++)
+    for (int st = 0; st < 2; st++) level_params_entry(g, dt, lts, lev, levf, l, st);
 }
 
 template <typename T>

@@ -657,13 +657,16 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
     if (x < best) best = x;
   }
   if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = best;
+  __shared__ int last;
+  __shared__ double dsh;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); w++)
       if (wmin[w] < best) best = wmin[w];
     if (best < T(INFINITY)) atomicMin(red, (unsigned long long)__double_as_longlong((double)best));
     __threadfence();
-    if (atomicAdd(done, 1u) == gridDim.x - 1) {
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+    if (last) {
       __threadfence();
       double m = __longlong_as_double((long long)atomicAdd(red, 0ull));
       // ready for the next reduction (no memset before each launch)
@@ -675,9 +678,13 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
         if (rest < d) d = rest;
       }
       dsc[0] = d;
-      level_params_dev(g, d, lts, lev, levf);
+      dsh = d;
     }
   }
+  __syncthreads();
+  // the last CTA fills the per-level step table, one (level, stage) entry per thread
+  if (last)
+    for (int k = threadIdx.x; k < 2 * (g.L + 1); k += blockDim.x) level_params_entry(g, dsh, lts, lev, levf, k >> 1, k & 1);
 }
 
 }  // namespace mrfv

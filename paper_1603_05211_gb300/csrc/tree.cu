@@ -830,8 +830,11 @@ __global__ void __launch_bounds__(kBrThreads) k_br(Geo g, const uint8_t *gflag, 
 __global__ void k_set_double(double *p, double v) { *p = v; }
 
 // per-level step table of a preset dt (the CFL path fills it in k_dt's last CTA)
+// (one (level, stage) entry per thread: a single thread's chain of double-precision
+// divisions would take microseconds on this part)
 __global__ void k_level_params(Geo g, const double *dt, int lts, double *lev, float *levf) {
-  if (threadIdx.x == 0) level_params_dev(g, *dt, lts, lev, levf);
+  const double d = *dt;
+  for (int k = threadIdx.x; k < 2 * (g.L + 1); k += blockDim.x) level_params_entry(g, d, lts, lev, levf, k >> 1, k & 1);
 }
 
 // t += factor * dt; cell-update counter += leaf cells (weighted per level for
@@ -840,7 +843,8 @@ __global__ void k_level_params(Geo g, const double *dt, int lts, double *lev, fl
 __global__ void k_advance(Geo g, double *t, const double *dt, double factor, long long *counter, int lts,
                           int32_t *pub) {
   if (pub)
-    for (int i = 0; i < LK_NUM * (MAXL + 2); i++) pub[i] = g.loff[i];
+    for (int i = threadIdx.x; i < LK_NUM * (MAXL + 2); i += blockDim.x) pub[i] = g.loff[i];
+  if (threadIdx.x != 0) return;
   *t = *t + factor * *dt;
   long long cells = 0;
   int B = block_cells(g.dim);
@@ -979,7 +983,7 @@ void launch_adapt_begin(const Geo &g, long long total, uint8_t *sig, double *max
 }
 void launch_advance(const Geo &g, double *t, const double *dt, double factor, long long *counter, int lts,
                     int32_t *pub, cudaStream_t st) {
-  k_advance<<<1, 1, 0, st>>>(g, t, dt, factor, counter, lts, pub);
+  k_advance<<<1, 32, 0, st>>>(g, t, dt, factor, counter, lts, pub);
 }
 
 }  // namespace mrfv
