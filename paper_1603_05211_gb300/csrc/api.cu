@@ -402,6 +402,14 @@ struct Seq {
     for (int l = c->g.L - 1; l >= 0; l--) restrict_level(l, A);
     c->nlaunch += c->g.L;
   }
+  // between the two stages: only the coarse cells the second stage reads
+  void restrict_edge(T *A) {
+    if (c->g.L < 1) return;
+    const int per = c->g.dim == 2 ? 16 : 4;
+    int dense = grid_for(c->g.mapoff[c->g.L + 1] - c->g.mapoff[1], per, c->grid);
+    launch_restrict_edge<T>(c->g, A, sized(c, LK_LEAF, 1, c->g.L, 1, per, dense), c->st);
+    c->nlaunch += 1;
+  }
   void fv(int kind, int l0, int l1, const T *Uin, const T *U0b, T *Uout, double coef, int lts, int record) {
     FVArgs<T> a;
     a.Uin = Uin; a.U0 = U0b; a.Uout = Uout; a.G = G(); a.FR = FR();
@@ -530,7 +538,7 @@ struct Seq {
     }
     if (!ghost_done) ghost(1, L, U(), nullptr, 0.0);
     fv(LK_LEAF, 0, L, U(), U(), Us(), 0.5, 0, 0);
-    restrict_all(Us());
+    restrict_edge(Us());
     ghost(1, L, Us(), nullptr, 0.0);
     fv(LK_LEAF, 0, L, Us(), U(), U(), 1.0, 0, 1);
     if (L > 0) {

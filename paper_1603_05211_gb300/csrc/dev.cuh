@@ -24,6 +24,18 @@ __device__ __forceinline__ int bc_cell(const Geo &g, int l, int d, int i) {
   return i < 0 ? 0 : (i >= N ? N - 1 : i);
 }
 
+// neighbouring block coordinate with the boundary rule, -1 outside a transmissive domain
+__device__ __forceinline__ int bc_block(const Geo &g, int l, int d, int b) {
+  if (d >= g.dim) return b == 0 ? 0 : -1;
+  int N = g.nb[l][d];
+  if (g.bc == 1) {
+    b %= N;
+    if (b < 0) b += N;
+    return b;
+  }
+  return (b < 0 || b >= N) ? -1 : b;
+}
+
 // Range [begin, end) of list `kind` over levels l0..l1.
 __device__ __forceinline__ void list_range(const Geo &g, int kind, int l0, int l1, int &b, int &e) {
   b = g.loff[kind * (MAXL + 2) + l0];

@@ -13,6 +13,9 @@ namespace mrfv {
 
 // multiresolution / bookkeeping kernels (mr_f32.cu, mr_f64.cu)
 template <typename T> void launch_restrict(const Geo &, int l, T *A, int grid, cudaStream_t);
+// between the stages of the MR step: the parent quadrants of the leaves next to an
+// absent block, all levels in one launch
+template <typename T> void launch_restrict_edge(const Geo &, T *A, int grid, cudaStream_t);
 template <typename T> void launch_scales(const Geo &, const T *A, unsigned long long *red, unsigned *done, T *scale,
                                          int grid, cudaStream_t);
 template <typename T> void launch_details(const Geo &, const T *A, const T *scale, double eps, uint8_t *sig, double *maxdet,

@@ -58,6 +58,66 @@ __global__ void k_restrict(Geo g, int l, T *__restrict__ A) {
   restrict_level_dev<T, D>(g, l, A);
 }
 
+// Projection between the two stages of the MR step.  Before the step's closing
+// projection, the second stage reads only two kinds of coarse cells of refined
+// blocks: the parent-level cells that the ghost-strip prediction of a block with
+// an absent same-level neighbour reads (three cells across the face, six along
+// it, around the block's quadrant), and the two cells next to a coarse-fine face
+// that the coarse side's reconstruction reads.  In a graded tree a block next to
+// an absent position (across a face, an edge or a corner) is a leaf, and every
+// such cell lies over a leaf of that kind; so projecting, on all levels at once,
+// the parent quadrant of every leaf that has an absent position among its 3^d-1
+// neighbours gives those cells the values of the full projection (one level, the
+// same sums in the same order).  Cells of refined blocks over other children keep
+// older values that nothing reads before the closing projection.
+template <typename T, int D>
+__global__ void k_restrict_edge(Geo g, T *__restrict__ A) {
+  constexpr int B = (D == 2) ? 64 : 512;
+  constexpr int Q = (D == 2) ? 16 : 64;  // cells of a parent quadrant
+  constexpr int PER = 256 / Q;           // leaves per CTA and pass
+  const int sub = threadIdx.x / Q, c = threadIdx.x % Q;
+  const int qx = c & 3, qy = (c >> 2) & 3, qz = (D == 3) ? (c >> 4) : 0;
+  const long long cap = g.cap;
+  int b, e;
+  list_range(g, LK_LEAF, 1, g.L, b, e);
+  for (int i = b + blockIdx.x * PER + sub; i < e; i += gridDim.x * PER) {
+    const int s = g.lists[LK_LEAF * cap + i];
+    const int l = g.slot_level[s];
+    const int bx = g.slot_coord[3 * s], by = g.slot_coord[3 * s + 1], bz = g.slot_coord[3 * s + 2];
+    bool edge = false;
+    for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); dz++)
+      for (int dy = -1; dy <= 1; dy++)
+        for (int dx = -1; dx <= 1; dx++) {
+          if (dx == 0 && dy == 0 && dz == 0) continue;
+          const int x = bc_block(g, l, 0, bx + dx), y = bc_block(g, l, 1, by + dy), z = bc_block(g, l, 2, bz + dz);
+          if (x < 0 || y < 0 || z < 0) continue;  // outside a transmissive domain: not an absent block
+          if (g.idx[map_index(g, l, x, y, z)] < 0) edge = true;
+        }
+    const int p = g.idx[map_index(g, l - 1, bx >> 1, by >> 1, bz >> 1)];
+    if (!edge) continue;
+    if (p < 0) {
+      set_err(g, EB_TREE);
+      continue;
+    }
+    const int pc = ((bx & 1) * 4 + qx) + 8 * ((by & 1) * 4 + qy) + ((D == 3) ? 64 * ((bz & 1) * 4 + qz) : 0);
+    const int f = 2 * qx + 16 * qy + ((D == 3) ? 128 * qz : 0);
+    for (int v = 0; v < D + 2; v++) {
+      const T *C = A + ((long long)v * cap + s) * B + f;
+      T sum = C[0];
+      sum = sum + C[1];
+      sum = sum + C[8];
+      sum = sum + C[9];
+      if (D == 3) {
+        sum = sum + C[64];
+        sum = sum + C[65];
+        sum = sum + C[72];
+        sum = sum + C[73];
+      }
+      A[((long long)v * cap + p) * B + pc] = sum * T(D == 2 ? 0.25 : 0.125);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- MR analysis
 // Normalisation maxima over level 0: |rho|, |rho e|, max_n |v_n| (as the bit
 // patterns of non-negative doubles, so atomicMax on the integer orders them).

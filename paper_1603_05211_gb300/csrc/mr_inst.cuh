@@ -14,6 +14,11 @@ void launch_restrict(const Geo &g, int l, T *A, int grid, cudaStream_t st) {
   else k_restrict<T, 3><<<grid, 512, 0, st>>>(g, l, A);
 }
 template <typename T>
+void launch_restrict_edge(const Geo &g, T *A, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_restrict_edge<T, 2><<<grid, 256, 0, st>>>(g, A);
+  else k_restrict_edge<T, 3><<<grid, 256, 0, st>>>(g, A);
+}
+template <typename T>
 void launch_gather_var(const Geo &g, int l, int v, int f, const T *A, double *out, cudaStream_t st) {
   if (g.dim == 2) k_gather_var<T, 2><<<1024, 256, 0, st>>>(g, l, v, f, A, out);
   else k_gather_var<T, 3><<<1024, 256, 0, st>>>(g, l, v, f, A, out);
@@ -137,6 +142,7 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
 
 #define MRFV_INSTANTIATE_MR(T)                                                                              \
   template void launch_restrict<T>(const Geo &, int, T *, int, cudaStream_t);                               \
+  template void launch_restrict_edge<T>(const Geo &, T *, int, cudaStream_t);                               \
   template void launch_scales<T>(const Geo &, const T *, unsigned long long *, unsigned *, T *, int, cudaStream_t); \
   template void launch_details<T>(const Geo &, const T *, const T *, double, uint8_t *, double *, int,      \
                                   const T *, double, int, cudaStream_t);                                    \

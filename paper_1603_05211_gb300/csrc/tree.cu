@@ -26,17 +26,6 @@ __device__ __forceinline__ void map_coords(const Geo &g, int l, long long t, int
   by = (int)((u / g.nb[l][0]) % g.nb[l][1]);
   bz = (int)(u / ((long long)g.nb[l][0] * g.nb[l][1]));
 }
-// neighbouring block coordinate with the boundary rule, -1 outside a transmissive domain
-__device__ __forceinline__ int bc_block(const Geo &g, int l, int d, int b) {
-  if (d >= g.dim) return b == 0 ? 0 : -1;
-  int N = g.nb[l][d];
-  if (g.bc == 1) {
-    b %= N;
-    if (b < 0) b += N;
-    return b;
-  }
-  return (b < 0 || b >= N) ? -1 : b;
-}
 
 __device__ void mark_nbrs(const Geo &g, uint8_t *need, int l, int bx, int by, int bz) {
   int z0 = g.dim == 3 ? -1 : 0, z1 = g.dim == 3 ? 1 : 0;
