@@ -22,6 +22,11 @@ using namespace mrfv;
 // mrfv_set_launch_shape overrides them.
 constexpr int kGridCtasPerSm = 8;
 constexpr int kBlockCtasPerSm = 16;
+// A level with at most this many CTAs of block positions per SM is projected by a
+// sweep of its dense maps (two independent reads before the data, against three
+// dependent ones for the list of refined blocks); a larger sweep dispatches more
+// CTAs than the list needs.
+constexpr int kRestrictPosCtasPerSm = 1;
 // Below these leaf counts the MR-scheme stage runs in the staged (thread per
 // face) kernel.  Measured on GB300 (FP32): per launch on uniform grids staged
 // 11.7 vs pencil 13.0 us at 1024 2D blocks, 22.9 vs 19.7 us at 4096; but inside
@@ -203,6 +208,7 @@ bool fill_geo(const mrfv_config *cfg, Geo &g, long long &maptotal, long long &mt
       }
       nblk *= g.nb[l][d];
     }
+    if (nblk >= (1ll << 31)) return false;  // block positions of one level are indexed in 32 bits
     g.mapoff[l] = maptotal;
     maptotal += nblk;
     g.mbits[l] = ilog2_ceil(mx);
@@ -329,6 +335,16 @@ void drop_graphs(mrfv_ctx *c) {
     }
 }
 
+// The largest level l <= lmax whose dense map holds at most max_positions block
+// positions (the levels below it hold fewer), or -1.
+int tail_level(const Geo &g, long long max_positions, int lmax) {
+  int lt = -1;
+  for (int l = 0; l <= lmax && l <= g.L; l++)
+    if (level_blocks(g, l) <= max_positions) lt = l;
+    else break;
+  return lt;
+}
+
 int grid_for(long long items, int per_cta, int cap_grid) {
   long long n = (items + per_cta - 1) / per_cta;
   if (n < 1) n = 1;
@@ -393,14 +409,26 @@ struct Seq {
 
   void restrict_level(int l, T *A) {
     // at most the blocks of level l are refined
-    int dense = grid_for(level_blocks(c->g, l), c->g.dim == 2 ? 4 : 1, c->grid);
-    launch_restrict<T>(c->g, l, A, sized(c, LK_INTERNAL, l, l, 1, c->g.dim == 2 ? 4 : 1, dense), c->st);
+    const int bpc = c->g.dim == 2 ? 4 : 1;
+    const long long pos = level_blocks(c->g, l);
+    if (pos <= (long long)kRestrictPosCtasPerSm * bpc * c->nsm) {
+      // few positions: one pass over the dense maps, a shorter chain of reads
+      launch_restrict_pos<T>(c->g, l, A, grid_for(pos, bpc, c->grid), c->st);
+      return;
+    }
+    int dense = grid_for(pos, bpc, c->grid);
+    launch_restrict<T>(c->g, l, A, sized(c, LK_INTERNAL, l, l, 1, bpc, dense), c->st);
   }
-  // every level, finest first, one launch per level: a launch boundary costs
-  // less than the in-kernel waits of a single all-levels launch (measured)
+  // every level, finest first: one launch per level, and the coarse levels whose
+  // positions one CTA covers in a pass together in one single-CTA launch
   void restrict_all(T *A) {
-    for (int l = c->g.L - 1; l >= 0; l--) restrict_level(l, A);
-    c->nlaunch += c->g.L;
+    const int lt = tail_level(c->g, kTailThreads / block_cells(c->g.dim), c->g.L - 1);
+    for (int l = c->g.L - 1; l > lt; l--) restrict_level(l, A);
+    c->nlaunch += c->g.L - 1 - lt;
+    if (lt >= 0) {
+      launch_restrict_tail<T>(c->g, lt, A, c->st);
+      c->nlaunch += 1;
+    }
   }
   // between the two stages: only the coarse cells the second stage reads
   void restrict_edge(T *A) {
@@ -592,10 +620,25 @@ struct Seq {
   }
   // new blocks of levels lfrom..lto (default L; a remesh above l0 creates none below l0+1)
   void prolong_new(int lfrom = 1, int lto = -1) {
-    for (int l = lfrom; l <= (lto < 0 ? c->g.L : lto); l++)
+    // at most two CTAs per SM: an adaptation adds few blocks per level, and a
+    // level that gets none costs the dispatch of every CTA of the grid
+    const int top = lto < 0 ? c->g.L : lto;
+    int l = lfrom;
+    if (lfrom == 1) {
+      // the coarse levels, where a new block is rare (at most 64 positions in 2D,
+      // 8 in 3D), in one single-CTA launch that takes the new blocks one by one
+      const int lt = tail_level(c->g, c->g.dim == 2 ? 64 : 8, top);
+      if (lt >= 2) {
+        launch_prolong_tail<T>(c->g, lt, c->newlist, c->nnew, U(), c->st);
+        c->nlaunch += 1;
+        l = lt + 1;
+      }
+    }
+    for (; l <= top; l++) {
       launch_prolong<T>(c->g, l, c->newlist, c->nnew, U(),
-                        sized(c, LK_EXIST, l, l, 1, 1, grid_for(level_blocks(c->g, l), 1, c->bgrid)), c->st);
-    c->nlaunch += (lto < 0 ? c->g.L : lto) - lfrom + 1;
+                        sized(c, LK_EXIST, l, l, 1, 1, grid_for(level_blocks(c->g, l), 1, 2 * c->nsm)), c->st);
+      c->nlaunch += 1;
+    }
   }
   // CFL reduction; its last CTA sets dt and the per-level step table
   void compute_dt(int lts) {
@@ -751,8 +794,17 @@ void adapt_tree(mrfv_ctx *c, bool step = false, bool begun = false) {
     launch_prop_mark(g, c->plogit, c->need, c->grid, c->st);
     c->nlaunch += 1;
   }
-  for (int l = g.L; l >= 1; l--) launch_need_close(g, l, c->need, grid_for(level_blocks(g, l), 256, c->grid), c->st);
-  c->nlaunch += 1 + g.L;
+  // finest first; the levels whose positions one CTA covers in a pass together
+  const int lt = tail_level(g, kTailThreads, g.L);
+  for (int l = g.L; l >= 1 && l > lt; l--) {
+    launch_need_close(g, l, c->need, grid_for(level_blocks(g, l), 256, c->grid), c->st);
+    c->nlaunch += 1;
+  }
+  if (lt >= 1) {
+    launch_need_close_tail(g, lt, c->need, c->st);
+    c->nlaunch += 1;
+  }
+  c->nlaunch += 1;
   apply_need(c, true, true);
 }
 

@@ -13,6 +13,15 @@ namespace mrfv {
 
 // multiresolution / bookkeeping kernels (mr_f32.cu, mr_f64.cu)
 template <typename T> void launch_restrict(const Geo &, int l, T *A, int grid, cudaStream_t);
+// the same as a sweep of the dense maps of level l (levels with few positions)
+template <typename T> void launch_restrict_pos(const Geo &, int l, T *A, int grid, cudaStream_t);
+// threads of the single-CTA kernels that take several coarse levels in one launch
+constexpr int kTailThreads = 1024;
+// levels lhi..0 in one single-CTA launch (levels whose positions one CTA covers)
+template <typename T> void launch_restrict_tail(const Geo &, int lhi, T *A, cudaStream_t);
+// new blocks of levels 1..lhi in one single-CTA launch
+template <typename T> void launch_prolong_tail(const Geo &, int lhi, const int32_t *newlist, const int *nnew, T *A,
+                                               cudaStream_t);
 // between the stages of the MR step: the parent quadrants of the leaves next to an
 // absent block, all levels in one launch
 template <typename T> void launch_restrict_edge(const Geo &, T *A, int grid, cudaStream_t);
@@ -74,6 +83,8 @@ bool launch_fvt(const Geo &, const FVArgs<float> &, const FvtSet &, int grid, cu
 void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t, int lkeep = 0);
 void prepare_br();
 void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t, bool parents = true);
+// the closure of levels lhi..1 (with parents) in one single-CTA launch
+void launch_need_close_tail(const Geo &, int lhi, uint8_t *need, cudaStream_t);
 void launch_remesh_begin(const Geo &, long long total, uint8_t *sig, uint8_t *gflag, uint8_t *need, int *nnew, int l0,
                          int grid, cudaStream_t);
 void launch_need_prune(const Geo &, int l, uint8_t *need, int grid, cudaStream_t);

@@ -58,6 +58,61 @@ __global__ void k_restrict(Geo g, int l, T *__restrict__ A) {
   restrict_level_dev<T, D>(g, l, A);
 }
 
+// The same projection as a sweep over the block positions of level l: the slots
+// of the block and of its child come from the dense maps, two independent reads,
+// where the list form reads the list offsets, the list and the child table one
+// after the other.  A position whose child is absent holds no refined block.
+template <typename T, int D>
+__device__ __forceinline__ void restrict_pos_dev(const Geo &g, int l, T *__restrict__ A) {
+  constexpr int B = (D == 2) ? 64 : 512;
+  const int BPC = blockDim.x / B;  // blocks per CTA and pass
+  const int sub = threadIdx.x / B, c = threadIdx.x % B;
+  const int x = c & 7, y = (c >> 3) & 7, z = (D == 3) ? (c >> 6) : 0;
+  const int nx = g.nb[l][0], ny = g.nb[l][1];
+  const int n = (int)(g.mapoff[l + 1] - g.mapoff[l]);
+  const long long cap = g.cap;
+  const int f = 2 * (x & 3) + 16 * (y & 3) + ((D == 3) ? 128 * (z & 3) : 0);
+  for (int u = blockIdx.x * BPC + sub; u < n; u += gridDim.x * BPC) {
+    const int r = u / nx, bx = u - r * nx, by = r % ny, bz = r / ny;
+    const int cs = g.idx[map_index(g, l + 1, 2 * bx + (x >> 2), 2 * by + (y >> 2), (D == 3) ? 2 * bz + (z >> 2) : 0)];
+    const int s = g.idx[g.mapoff[l] + u];
+    if (cs < 0) continue;
+    if (s < 0) {
+      set_err(g, EB_TREE);
+      continue;
+    }
+    for (int v = 0; v < D + 2; v++) {
+      const T *C = A + ((long long)v * cap + cs) * B + f;
+      T sum = C[0];
+      sum = sum + C[1];
+      sum = sum + C[8];
+      sum = sum + C[9];
+      if (D == 3) {
+        sum = sum + C[64];
+        sum = sum + C[65];
+        sum = sum + C[72];
+        sum = sum + C[73];
+      }
+      A[((long long)v * cap + s) * B + c] = sum * T(D == 2 ? 0.25 : 0.125);
+    }
+  }
+}
+template <typename T, int D>
+__global__ void k_restrict_pos(Geo g, int l, T *__restrict__ A) {
+  restrict_pos_dev<T, D>(g, l, A);
+}
+// Levels lhi..0 projected by one CTA, finest first, a CTA barrier between the
+// levels (the writes of a level are visible to the whole CTA after it).  For the
+// coarse levels, whose few positions one CTA covers in a pass: one launch and a
+// barrier per level instead of a launch per level.
+template <typename T, int D>
+__global__ void k_restrict_tail(Geo g, int lhi, T *__restrict__ A) {
+  for (int l = lhi; l >= 0; l--) {
+    restrict_pos_dev<T, D>(g, l, A);
+    __syncthreads();
+  }
+}
+
 // Projection between the two stages of the MR step.  Before the step's closing
 // projection, the second stage reads only two kinds of coarse cells of refined
 // blocks: the parent-level cells that the ghost-strip prediction of a block with
@@ -286,6 +341,17 @@ __global__ void k_prolong(Geo g, int l, const int32_t *__restrict__ newlist, con
                           T *__restrict__ A) {
   __shared__ T patch[(D + 2) * ((D == 2) ? 36 : 216)];
   prolong_level_dev<T, D>(g, l, newlist, nnew, A, patch);
+}
+// New blocks of levels 1..lhi predicted by one CTA, coarsest first (a new block
+// may read new blocks of the level above), a CTA barrier between the levels.
+template <typename T, int D>
+__global__ void k_prolong_tail(Geo g, int lhi, const int32_t *__restrict__ newlist, const int *__restrict__ nnew,
+                               T *__restrict__ A) {
+  __shared__ T patch[(D + 2) * ((D == 2) ? 36 : 216)];
+  for (int l = 1; l <= lhi; l++) {
+    prolong_level_dev<T, D>(g, l, newlist, nnew, A, patch);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- ghost strips

@@ -14,6 +14,21 @@ void launch_restrict(const Geo &g, int l, T *A, int grid, cudaStream_t st) {
   else k_restrict<T, 3><<<grid, 512, 0, st>>>(g, l, A);
 }
 template <typename T>
+void launch_restrict_pos(const Geo &g, int l, T *A, int grid, cudaStream_t st) {
+  if (g.dim == 2) k_restrict_pos<T, 2><<<grid, 256, 0, st>>>(g, l, A);
+  else k_restrict_pos<T, 3><<<grid, 512, 0, st>>>(g, l, A);
+}
+template <typename T>
+void launch_restrict_tail(const Geo &g, int lhi, T *A, cudaStream_t st) {
+  if (g.dim == 2) k_restrict_tail<T, 2><<<1, kTailThreads, 0, st>>>(g, lhi, A);
+  else k_restrict_tail<T, 3><<<1, kTailThreads, 0, st>>>(g, lhi, A);
+}
+template <typename T>
+void launch_prolong_tail(const Geo &g, int lhi, const int32_t *newlist, const int *nnew, T *A, cudaStream_t st) {
+  if (g.dim == 2) k_prolong_tail<T, 2><<<1, 64, 0, st>>>(g, lhi, newlist, nnew, A);
+  else k_prolong_tail<T, 3><<<1, 512, 0, st>>>(g, lhi, newlist, nnew, A);
+}
+template <typename T>
 void launch_restrict_edge(const Geo &g, T *A, int grid, cudaStream_t st) {
   if (g.dim == 2) k_restrict_edge<T, 2><<<grid, 256, 0, st>>>(g, A);
   else k_restrict_edge<T, 3><<<grid, 256, 0, st>>>(g, A);
@@ -143,6 +158,9 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
 #define MRFV_INSTANTIATE_MR(T)                                                                              \
   template void launch_restrict<T>(const Geo &, int, T *, int, cudaStream_t);                               \
   template void launch_restrict_edge<T>(const Geo &, T *, int, cudaStream_t);                               \
+  template void launch_restrict_pos<T>(const Geo &, int, T *, int, cudaStream_t);                           \
+  template void launch_restrict_tail<T>(const Geo &, int, T *, cudaStream_t);                               \
+  template void launch_prolong_tail<T>(const Geo &, int, const int32_t *, const int *, T *, cudaStream_t);  \
   template void launch_scales<T>(const Geo &, const T *, unsigned long long *, unsigned *, T *, int, cudaStream_t); \
   template void launch_details<T>(const Geo &, const T *, const T *, double, uint8_t *, double *, int,      \
                                   const T *, double, int, cudaStream_t);                                    \

@@ -20,11 +20,14 @@ __device__ __forceinline__ int level_of_map(const Geo &g, long long t) {
   while (l < g.L && t >= g.mapoff[l + 1]) l++;
   return l;
 }
+// (32-bit arithmetic: a level holds fewer than 2^31 block positions)
 __device__ __forceinline__ void map_coords(const Geo &g, int l, long long t, int &bx, int &by, int &bz) {
-  long long u = t - g.mapoff[l];
-  bx = (int)(u % g.nb[l][0]);
-  by = (int)((u / g.nb[l][0]) % g.nb[l][1]);
-  bz = (int)(u / ((long long)g.nb[l][0] * g.nb[l][1]));
+  const int u = (int)(t - g.mapoff[l]);
+  const int nx = g.nb[l][0], ny = g.nb[l][1];
+  const int r = u / nx;
+  bx = u - r * nx;
+  by = r % ny;
+  bz = r / ny;
 }
 
 __device__ void mark_nbrs(const Geo &g, uint8_t *need, int l, int bx, int by, int bz) {
@@ -408,6 +411,14 @@ __global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit, 
   k_need_mark_dev(g, sig, need, crit, lkeep);
 }
 __global__ void k_need_close(Geo g, int l, uint8_t *need, int parents) { k_need_close_dev(g, l, need, parents); }
+// Levels lhi..1 closed by one CTA, finest first, a CTA barrier between the levels
+// (a level's marks are visible to the whole CTA after it).
+__global__ void k_need_close_tail(Geo g, int lhi, uint8_t *need) {
+  for (int l = lhi; l >= 1; l--) {
+    k_need_close_dev(g, l, need, 1);
+    __syncthreads();
+  }
+}
 
 // Remesh(l0) inside the level recursion (Fig. 2): flags cleared, the tree of
 // levels <= l0 kept as needed, the levels above it to be rebuilt from flags.
@@ -889,6 +900,9 @@ static int fit(long long items, int per_cta, int grid) {
 
 void launch_need_mark(const Geo &g, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t st, int lkeep) {
   k_need_mark<<<fit(g.mapoff[g.L + 1], 256, grid), 256, 0, st>>>(g, sig, need, crit, lkeep);
+}
+void launch_need_close_tail(const Geo &g, int lhi, uint8_t *need, cudaStream_t st) {
+  k_need_close_tail<<<1, kTailThreads, 0, st>>>(g, lhi, need);
 }
 void launch_need_close(const Geo &g, int l, uint8_t *need, int grid, cudaStream_t st, bool parents) {
   k_need_close<<<grid, 256, 0, st>>>(g, l, need, parents ? 1 : 0);
