@@ -27,6 +27,9 @@ constexpr int kBlockCtasPerSm = 16;
 // dependent ones for the list of refined blocks); a larger sweep dispatches more
 // CTAs than the list needs.
 constexpr int kRestrictPosCtasPerSm = 1;
+// Up to this many level-0 cells every CTA of the details kernel computes the
+// level-0 normalisation itself (no separate reduction launch before it).
+constexpr long long kOwnScaleCells = 256;
 // Below these leaf counts the MR-scheme stage runs in the staged (thread per
 // face) kernel.  Measured on GB300 (FP32): per launch on uniform grids staged
 // 11.7 vs pencil 13.0 us at 1024 2D blocks, 22.9 vs 19.7 us at 4096; but inside
@@ -607,16 +610,24 @@ struct Seq {
   // cleared: the maps were cleared by the adaptation's first kernel; l0, A0: a
   // remesh's analysis of levels l0..L, level l0 against level l0-1 halfway
   // through its step (A0 + (A - A0)/2)
-  void analyse(double eps, bool cleared = false, int l0 = 1, const T *A0 = nullptr) {
-    launch_scales<T>(c->g, U(), c->red + 0, c->rctl + 3, (T *)c->scale,
-                     grid_for(level_blocks(c->g, 0) * block_cells(c->g.dim), 256, c->grid), c->st);
+  // marks: the MR criterion's needed-block marks made by the details kernel (the
+  // adaptation of a step, without the proposer)
+  void analyse(double eps, bool cleared = false, int l0 = 1, const T *A0 = nullptr, bool marks = false) {
+    // a level 0 of a few blocks: every details CTA computes the normalisation itself
+    const bool own = level_blocks(c->g, 0) * block_cells(c->g.dim) <= kOwnScaleCells;
+    if (!own) {
+      launch_scales<T>(c->g, U(), c->red + 0, c->rctl + 3, (T *)c->scale,
+                       grid_for(level_blocks(c->g, 0) * block_cells(c->g.dim), 256, c->grid), c->st);
+      c->nlaunch += 1;
+    }
     if (!cleared) {
       cudaMemsetAsync(c->sig, 0, c->maptotal, c->st);
       cudaMemsetAsync(c->maxdet, 0, c->maptotal * 8, c->st);
     }
     launch_details<T>(c->g, U(), (const T *)c->scale, eps, c->sig, c->maxdet, l0, A0, 0.5,
-                      sized(c, LK_EXIST, l0, c->g.L, 1, 1, c->bgrid), c->st);
-    c->nlaunch += 2;
+                      sized(c, LK_EXIST, l0, c->g.L, 1, 1, c->bgrid), c->st, own ? (T *)c->scale : nullptr,
+                      marks ? c->need : nullptr);
+    c->nlaunch += 1;
   }
   // new blocks of levels lfrom..lto (default L; a remesh above l0 creates none below l0+1)
   void prolong_new(int lfrom = 1, int lto = -1) {
@@ -783,13 +794,18 @@ void adapt_tree(mrfv_ctx *c, bool step = false, bool begun = false) {
   const Geo &g = c->g;
   bool use_prop = c->cfg.proposer && c->has_weights && c->cfg.criterion == MRFV_CRIT_MR;
   if (!begun) adapt_begin(c, step);
-  if (c->cfg.criterion == MRFV_CRIT_MR) dispatch(c, [&](auto &s) { s.analyse(c->cfg.eps, true); });
+  // MR without the proposer: the details kernel makes the needed-block marks
+  const bool fused_marks = c->cfg.criterion == MRFV_CRIT_MR && !use_prop;
+  if (c->cfg.criterion == MRFV_CRIT_MR) dispatch(c, [&](auto &s) { s.analyse(c->cfg.eps, true, 1, nullptr, fused_marks); });
   else dispatch(c, [&](auto &s) { s.gradflags(true); });
   if (use_prop) {
     dispatch(c, [&](auto &s) { s.prop_features(); });
     prop_infer(c, !c->cfg.proposer_dense);
   }
-  launch_need_mark(g, c->sig, c->need, use_prop ? 2 : c->cfg.criterion, c->grid, c->st);
+  if (!fused_marks) {
+    launch_need_mark(g, c->sig, c->need, use_prop ? 2 : c->cfg.criterion, c->grid, c->st);
+    c->nlaunch += 1;
+  }
   if (use_prop) {
     launch_prop_mark(g, c->plogit, c->need, c->grid, c->st);
     c->nlaunch += 1;
@@ -804,7 +820,6 @@ void adapt_tree(mrfv_ctx *c, bool step = false, bool begun = false) {
     launch_need_close_tail(g, lt, c->need, c->st);
     c->nlaunch += 1;
   }
-  c->nlaunch += 1;
   apply_need(c, true, true);
 }
 

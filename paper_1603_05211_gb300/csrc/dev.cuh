@@ -36,6 +36,25 @@ __device__ __forceinline__ int bc_block(const Geo &g, int l, int d, int b) {
   return (b < 0 || b >= N) ? -1 : b;
 }
 
+// needed-block marks: the 3^d-1 neighbours (boundary rule) and the children of a block
+__device__ __forceinline__ void mark_nbrs(const Geo &g, uint8_t *need, int l, int bx, int by, int bz) {
+  int z0 = g.dim == 3 ? -1 : 0, z1 = g.dim == 3 ? 1 : 0;
+  for (int c = z0; c <= z1; c++)
+    for (int b = -1; b <= 1; b++)
+      for (int a = -1; a <= 1; a++) {
+        int x = bc_block(g, l, 0, bx + a), y = bc_block(g, l, 1, by + b), z = bc_block(g, l, 2, bz + c);
+        if (x < 0 || y < 0 || z < 0) continue;
+        need[map_index(g, l, x, y, z)] = 1;
+      }
+}
+__device__ __forceinline__ void mark_children(const Geo &g, uint8_t *need, int l, int bx, int by, int bz) {
+  int kz = g.dim == 3 ? 2 : 1;
+  for (int c = 0; c < kz; c++)
+    for (int b = 0; b < 2; b++)
+      for (int a = 0; a < 2; a++)
+        need[map_index(g, l + 1, 2 * bx + a, 2 * by + b, g.dim == 3 ? 2 * bz + c : 0)] = 1;
+}
+
 // Range [begin, end) of list `kind` over levels l0..l1.
 __device__ __forceinline__ void list_range(const Geo &g, int kind, int l0, int l1, int &b, int &e) {
   b = g.loff[kind * (MAXL + 2) + l0];

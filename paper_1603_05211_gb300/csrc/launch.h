@@ -27,8 +27,12 @@ template <typename T> void launch_prolong_tail(const Geo &, int lhi, const int32
 template <typename T> void launch_restrict_edge(const Geo &, T *A, int grid, cudaStream_t);
 template <typename T> void launch_scales(const Geo &, const T *A, unsigned long long *red, unsigned *done, T *scale,
                                          int grid, cudaStream_t);
+// own_scale (optional): every CTA computes the level-0 normalisation itself and CTA
+// 0 stores it there (no k_scale_max before); need (optional): the MR criterion's
+// needed-block marks made here (no k_need_mark after)
 template <typename T> void launch_details(const Geo &, const T *A, const T *scale, double eps, uint8_t *sig, double *maxdet,
-                                         int l0, const T *A0, double theta, int grid, cudaStream_t);
+                                         int l0, const T *A0, double theta, int grid, cudaStream_t,
+                                         T *own_scale = nullptr, uint8_t *need = nullptr);
 template <typename T> void launch_prolong(const Geo &, int l, const int32_t *newlist, const int *nnew, T *A, int grid, cudaStream_t);
 template <typename T> void launch_ghost(const Geo &, int l0, int l1, const T *A, const T *A0, double theta, T *G, int grid, cudaStream_t);
 template <typename T> void launch_init(const Geo &, const ICParams &, const double *hi, T *A, int grid, cudaStream_t);

@@ -176,15 +176,19 @@ __global__ void k_restrict_edge(Geo g, T *__restrict__ A) {
 // ---------------------------------------------------------------- MR analysis
 // Normalisation maxima over level 0: |rho|, |rho e|, max_n |v_n| (as the bit
 // patterns of non-negative doubles, so atomicMax on the integer orders them).
+// This thread's maxima over the level-0 cells start, start + stride, ..., then
+// the warp's (every lane holds them).
 template <typename T, int D>
-__device__ __forceinline__ void scale_max_dev(const Geo &g, const T *__restrict__ A, unsigned long long *red) {
+__device__ __forceinline__ void level0_maxima(const Geo &g, const T *__restrict__ A, long long start, long long stride,
+                                              T &mr, T &mE, T &mv) {
   constexpr int B = (D == 2) ? 64 : 512;
   int b, e;
   list_range(g, LK_EXIST, 0, 0, b, e);
   const long long cap = g.cap;
-  T mr = 0, mE = 0, mv = 0;
-  for (long long t = (long long)b * B + blockIdx.x * blockDim.x + threadIdx.x; t < (long long)e * B;
-       t += (long long)gridDim.x * blockDim.x) {
+  mr = 0;
+  mE = 0;
+  mv = 0;
+  for (long long t = (long long)b * B + start; t < (long long)e * B; t += stride) {
     int i = (int)(t / B), c = (int)(t % B);
     int s = g.lists[LK_EXIST * cap + i];
     T rho = A[((long long)0 * cap + s) * B + c];
@@ -201,6 +205,12 @@ __device__ __forceinline__ void scale_max_dev(const Geo &g, const T *__restrict_
     mE = fmax(mE, __shfl_xor_sync(0xffffffffu, mE, o));
     mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, o));
   }
+}
+template <typename T, int D>
+__device__ __forceinline__ void scale_max_dev(const Geo &g, const T *__restrict__ A, unsigned long long *red) {
+  T mr, mE, mv;
+  level0_maxima<T, D>(g, A, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, mr,
+                      mE, mv);
   if ((threadIdx.x & 31) == 0) {
     atomicMax(red + 0, (unsigned long long)__double_as_longlong((double)mr));
     atomicMax(red + 1, (unsigned long long)__double_as_longlong((double)mE));
@@ -255,7 +265,7 @@ __global__ void k_scale_final(const unsigned long long *red, T *scale) {
 template <typename T, int D>
 __device__ __forceinline__ void details_dev(const Geo &g, const T *__restrict__ A, const T *__restrict__ scale,
                                             T eps, uint8_t *sig, double *maxdet, T *patch, T *wmax, int l0,
-                                            const T *__restrict__ A0, T theta) {
+                                            const T *__restrict__ A0, T theta, T *own_scale, uint8_t *need) {
   constexpr int B = (D == 2) ? 64 : 512;
   constexpr int EXT = 6;
   constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
@@ -267,7 +277,35 @@ __device__ __forceinline__ void details_dev(const Geo &g, const T *__restrict__ 
   const int c = threadIdx.x;
   const int x = c & 7, y = (c >> 3) & 7, z = (D == 3) ? (c >> 6) : 0;
   T sc[D + 2];
-  for (int v = 0; v < D + 2; v++) sc[v] = scale[v];
+  if (own_scale) {
+    // the normalisation of k_scale_max computed by this CTA alone (a level 0 of a
+    // few blocks): the same maxima, so the same scales; CTA 0 stores them
+    T mr, mE, mv;
+    level0_maxima<T, D>(g, A, c, B, mr, mE, mv);
+    if ((c & 31) == 0) {
+      patch[3 * (c >> 5)] = mr;
+      patch[3 * (c >> 5) + 1] = mE;
+      patch[3 * (c >> 5) + 2] = mv;
+    }
+    __syncthreads();
+    if (c == 0) {
+      for (int w = 1; w < B / 32; w++) {
+        mr = fmax(mr, patch[3 * w]);
+        mE = fmax(mE, patch[3 * w + 1]);
+        mv = fmax(mv, patch[3 * w + 2]);
+      }
+      unsigned long long r[3] = {(unsigned long long)__double_as_longlong((double)mr),
+                                 (unsigned long long)__double_as_longlong((double)mE),
+                                 (unsigned long long)__double_as_longlong((double)mv)};
+      scale_final_dev<T, D>(r, wmax);
+      if (blockIdx.x == 0)
+        for (int v = 0; v < D + 2; v++) own_scale[v] = wmax[v];
+    }
+    __syncthreads();
+    for (int v = 0; v < D + 2; v++) sc[v] = wmax[v];
+  } else {
+    for (int v = 0; v < D + 2; v++) sc[v] = scale[v];
+  }
   for (int i = b + blockIdx.x; i < e; i += gridDim.x) {
     int s = g.lists[LK_EXIST * cap + i];
     int l = g.slot_level[s];
@@ -300,16 +338,36 @@ __device__ __forceinline__ void details_dev(const Geo &g, const T *__restrict__ 
       long long mi = map_index(g, l, bx, by, bz);
       sig[mi] = (m > eps) ? 1 : 0;
       maxdet[mi] = (double)m;
+      wmax[31] = (need && m > eps) ? T(1) : T(0);
+    }
+    if (need) {
+      // the MR marks of k_need_mark for a significant block (level >= 1): the block
+      // and its 3^d-1 neighbours (one per thread), below the finest level its children
+      __syncthreads();
+      if (wmax[31] != T(0)) {
+        constexpr int NN = (D == 2) ? 9 : 27;
+        if (c < NN) {
+          const int a = c % 3 - 1, bb = (c / 3) % 3 - 1, cc = (D == 3) ? c / 9 - 1 : 0;
+          const int nx = bc_block(g, l, 0, bx + a), ny = bc_block(g, l, 1, by + bb), nz = bc_block(g, l, 2, bz + cc);
+          if (nx >= 0 && ny >= 0 && nz >= 0) need[map_index(g, l, nx, ny, nz)] = 1;
+        } else if (c < NN + (D == 2 ? 4 : 8) && l < g.L) {
+          const int q = c - NN;
+          need[map_index(g, l + 1, 2 * bx + (q & 1), 2 * by + ((q >> 1) & 1), (D == 3) ? 2 * bz + (q >> 2) : 0)] = 1;
+        }
+      }
     }
   }
 }
 
+// own_scale: compute the level-0 normalisation in every CTA (and store it there)
+// instead of reading it; need: mark the needed blocks of the MR criterion here
+// instead of in k_need_mark (the adaptation of a step)
 template <typename T, int D>
 __global__ void k_details(Geo g, const T *__restrict__ A, const T *__restrict__ scale, T eps, uint8_t *sig,
-                          double *maxdet, int l0, const T *__restrict__ A0, T theta) {
+                          double *maxdet, int l0, const T *__restrict__ A0, T theta, T *own_scale, uint8_t *need) {
   __shared__ T patch[(D + 2) * ((D == 2) ? 36 : 216)];
   __shared__ T wmax[32];
-  details_dev<T, D>(g, A, scale, eps, sig, maxdet, patch, wmax, l0, A0, theta);
+  details_dev<T, D>(g, A, scale, eps, sig, maxdet, patch, wmax, l0, A0, theta, own_scale, need);
 }
 
 // ---------------------------------------------------------------- prediction of new blocks

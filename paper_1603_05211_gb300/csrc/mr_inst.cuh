@@ -49,9 +49,11 @@ void launch_scales(const Geo &g, const T *A, unsigned long long *red, unsigned *
 }
 template <typename T>
 void launch_details(const Geo &g, const T *A, const T *scale, double eps, uint8_t *sig, double *maxdet, int l0,
-                    const T *A0, double theta, int grid, cudaStream_t st) {
-  if (g.dim == 2) k_details<T, 2><<<grid, 64, 0, st>>>(g, A, scale, T(eps), sig, maxdet, l0, A0, T(theta));
-  else k_details<T, 3><<<grid, 512, 0, st>>>(g, A, scale, T(eps), sig, maxdet, l0, A0, T(theta));
+                    const T *A0, double theta, int grid, cudaStream_t st, T *own_scale, uint8_t *need) {
+  if (g.dim == 2)
+    k_details<T, 2><<<grid, 64, 0, st>>>(g, A, scale, T(eps), sig, maxdet, l0, A0, T(theta), own_scale, need);
+  else
+    k_details<T, 3><<<grid, 512, 0, st>>>(g, A, scale, T(eps), sig, maxdet, l0, A0, T(theta), own_scale, need);
 }
 template <typename T>
 void launch_prolong(const Geo &g, int l, const int32_t *newlist, const int *nnew, T *A, int grid, cudaStream_t st) {
@@ -163,7 +165,7 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
   template void launch_prolong_tail<T>(const Geo &, int, const int32_t *, const int *, T *, cudaStream_t);  \
   template void launch_scales<T>(const Geo &, const T *, unsigned long long *, unsigned *, T *, int, cudaStream_t); \
   template void launch_details<T>(const Geo &, const T *, const T *, double, uint8_t *, double *, int,      \
-                                  const T *, double, int, cudaStream_t);                                    \
+                                  const T *, double, int, cudaStream_t, T *, uint8_t *);                    \
   template void launch_prolong<T>(const Geo &, int, const int32_t *, const int *, T *, int, cudaStream_t);  \
   template void launch_ghost<T>(const Geo &, int, int, const T *, const T *, double, T *, int, cudaStream_t); \
   template void launch_init<T>(const Geo &, const ICParams &, const double *, T *, int, cudaStream_t);      \

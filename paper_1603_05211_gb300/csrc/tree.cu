@@ -30,23 +30,6 @@ __device__ __forceinline__ void map_coords(const Geo &g, int l, long long t, int
   bz = r / ny;
 }
 
-__device__ void mark_nbrs(const Geo &g, uint8_t *need, int l, int bx, int by, int bz) {
-  int z0 = g.dim == 3 ? -1 : 0, z1 = g.dim == 3 ? 1 : 0;
-  for (int c = z0; c <= z1; c++)
-    for (int b = -1; b <= 1; b++)
-      for (int a = -1; a <= 1; a++) {
-        int x = bc_block(g, l, 0, bx + a), y = bc_block(g, l, 1, by + b), z = bc_block(g, l, 2, bz + c);
-        if (x < 0 || y < 0 || z < 0) continue;
-        need[map_index(g, l, x, y, z)] = 1;
-      }
-}
-__device__ void mark_children(const Geo &g, uint8_t *need, int l, int bx, int by, int bz) {
-  int kz = g.dim == 3 ? 2 : 1;
-  for (int c = 0; c < kz; c++)
-    for (int b = 0; b < 2; b++)
-      for (int a = 0; a < 2; a++)
-        need[map_index(g, l + 1, 2 * bx + a, 2 * by + b, g.dim == 3 ? 2 * bz + c : 0)] = 1;
-}
 
 // MR: a significant block of level >= 1 is kept with its 3^d-1 neighbours and,
 // below the finest level, its children are added.  GRAD: the children of every
