@@ -424,14 +424,38 @@ struct Seq {
   }
   // every level, finest first: one launch per level, and the coarse levels whose
   // positions one CTA covers in a pass together in one single-CTA launch
-  void restrict_all(T *A) {
-    const int lt = tail_level(c->g, kTailThreads / block_cells(c->g.dim), c->g.L - 1);
-    for (int l = c->g.L - 1; l > lt; l--) restrict_level(l, A);
-    c->nlaunch += c->g.L - 1 - lt;
+  void restrict_all(T *A) { restrict_from(c->g.L - 1, A); }
+  // levels top..0
+  void restrict_from(int top, T *A) {
+    const int lt = tail_level(c->g, kTailThreads / block_cells(c->g.dim), top);
+    for (int l = top; l > lt; l--) restrict_level(l, A);
+    if (top > lt) c->nlaunch += top - lt;
     if (lt >= 0) {
       launch_restrict_tail<T>(c->g, lt, A, c->st);
       c->nlaunch += 1;
     }
+  }
+  // end of a step: flux correction of levels 0..L-1, then the projection of every
+  // level; where level L-1 takes the list form, its projection shares the launch
+  // of the correction (neither reads what the other writes)
+  void reflux_restrict_all() {
+    const Geo &g = c->g;
+    const int L = g.L;
+    if (L < 1) return;
+    const int bpc = g.dim == 2 ? 4 : 1, nt = g.dim == 2 ? 256 : 512;
+    const long long pos = level_blocks(g, L - 1);
+    const int lt = tail_level(g, kTailThreads / block_cells(g.dim), L - 1);
+    if (L - 1 > lt && pos > (long long)kRestrictPosCtasPerSm * bpc * c->nsm) {
+      const int nr = sized(c, LK_REFLUX, 0, L - 1, block_cells(g.dim), nt, c->grid);
+      const int np = sized(c, LK_INTERNAL, L - 1, L - 1, 1, bpc, grid_for(pos, bpc, c->grid));
+      launch_reflux_restrict<T>(g, U(), FR(), nr, np, c->st);
+      c->nlaunch += 1;
+      restrict_from(L - 2, U());
+      return;
+    }
+    launch_reflux<T>(g, 0, L - 1, U(), FR(), sized(c, LK_REFLUX, 0, L - 1, block_cells(g.dim), 256, c->grid), c->st);
+    c->nlaunch += 1;
+    restrict_all(U());
   }
   // between the two stages: only the coarse cells the second stage reads
   void restrict_edge(T *A) {
@@ -560,11 +584,7 @@ struct Seq {
       fvh(LK_LEAF, 0, L, U(), Us(), nullptr, 0.0, 1);
       launch_copy_level<T>(c->g, LK_LEAF, 0, L, Us(), U(), sized(c, LK_LEAF, 0, L, block_cells(c->g.dim), 256, c->grid), c->st);
       c->nlaunch += 1;
-      if (L > 0) {
-        launch_reflux<T>(c->g, 0, L - 1, U(), FR(), sized(c, LK_REFLUX, 0, L - 1, block_cells(c->g.dim), 256, c->grid), c->st);
-        c->nlaunch += 1;
-      }
-      restrict_all(U());
+      reflux_restrict_all();
       return;
     }
     if (!ghost_done) ghost(1, L, U(), nullptr, 0.0);
@@ -572,11 +592,7 @@ struct Seq {
     restrict_edge(Us());
     ghost(1, L, Us(), nullptr, 0.0);
     fv(LK_LEAF, 0, L, Us(), U(), U(), 1.0, 0, 1);
-    if (L > 0) {
-      launch_reflux<T>(c->g, 0, L - 1, U(), FR(), sized(c, LK_REFLUX, 0, L - 1, block_cells(c->g.dim), 256, c->grid), c->st);
-      c->nlaunch += 1;
-    }
-    restrict_all(U());
+    reflux_restrict_all();
   }
   // Fig. 2 recursion: level l takes one step of dt_l = 2^(L-l) dt (all its blocks),
   // then level l+1 two steps, then projection and flux correction of level l.

@@ -17,6 +17,9 @@ template <typename T> void launch_restrict(const Geo &, int l, T *A, int grid, c
 template <typename T> void launch_restrict_pos(const Geo &, int l, T *A, int grid, cudaStream_t);
 // threads of the single-CTA kernels that take several coarse levels in one launch
 constexpr int kTailThreads = 1024;
+// flux correction of levels 0..L-1 on nr CTAs and projection of level L-1 (list
+// form) on np CTAs, in one launch
+template <typename T> void launch_reflux_restrict(const Geo &, T *A, const T *FR, int nr, int np, cudaStream_t);
 // levels lhi..0 in one single-CTA launch (levels whose positions one CTA covers)
 template <typename T> void launch_restrict_tail(const Geo &, int lhi, T *A, cudaStream_t);
 // new blocks of levels 1..lhi in one single-CTA launch

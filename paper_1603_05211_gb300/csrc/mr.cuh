@@ -20,7 +20,7 @@ namespace mrfv {
 // Parent cell = mean of its 2^d children, summed in lexicographic child order
 // (x offset fastest), on every refined block of level l.
 template <typename T, int D>
-__device__ __forceinline__ void restrict_level_dev(const Geo &g, int l, T *__restrict__ A) {
+__device__ __forceinline__ void restrict_level_dev(const Geo &g, int l, T *__restrict__ A, int cta, int ncta) {
   constexpr int B = (D == 2) ? 64 : 512;
   constexpr int BPC = (D == 2) ? 4 : 1;
   int b, e;
@@ -28,7 +28,7 @@ __device__ __forceinline__ void restrict_level_dev(const Geo &g, int l, T *__res
   const int sub = threadIdx.x / B, c = threadIdx.x % B;
   const int x = c & 7, y = (c >> 3) & 7, z = (D == 3) ? (c >> 6) : 0;
   const long long cap = g.cap;
-  for (int i = b + blockIdx.x * BPC + sub; i < e; i += gridDim.x * BPC) {
+  for (int i = b + cta * BPC + sub; i < e; i += ncta * BPC) {
     int s = g.lists[LK_INTERNAL * cap + i];
     int cs = g.kids[8 * s + (x >> 2) + 2 * (y >> 2) + ((D == 3) ? 4 * (z >> 2) : 0)];
     if (cs < 0) {
@@ -55,7 +55,7 @@ __device__ __forceinline__ void restrict_level_dev(const Geo &g, int l, T *__res
 
 template <typename T, int D>
 __global__ void k_restrict(Geo g, int l, T *__restrict__ A) {
-  restrict_level_dev<T, D>(g, l, A);
+  restrict_level_dev<T, D>(g, l, A, blockIdx.x, gridDim.x);
 }
 
 // The same projection as a sweep over the block positions of level l: the slots
@@ -663,15 +663,16 @@ __global__ void k_totals(Geo g, const T *__restrict__ A, double *out) {
 // cell applies its faces in direction order, low side first; the fine faces are
 // averaged in the order (first tangential offset fastest).
 template <typename T, int D>
-__global__ void k_reflux(Geo g, int l0, int l1, T *__restrict__ A, const T *__restrict__ FR) {
+__device__ __forceinline__ void reflux_dev(const Geo &g, int l0, int l1, T *__restrict__ A, const T *__restrict__ FR,
+                                           int cta, int ncta) {
   constexpr int B = (D == 2) ? 64 : 512;
   constexpr int TF = (D == 2) ? 8 : 64;
   constexpr int FS = 2 * D * TF;
   int b, e;
   list_range(g, LK_REFLUX, l0, l1, b, e);
   const long long cap = g.cap;
-  for (long long t = (long long)b * B + blockIdx.x * blockDim.x + threadIdx.x; t < (long long)e * B;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)b * B + cta * (long long)blockDim.x + threadIdx.x; t < (long long)e * B;
+       t += (long long)ncta * blockDim.x) {
     int i = (int)(t / B), c = (int)(t % B);
     int s = g.lists[LK_REFLUX * cap + i];
     int l = g.slot_level[s];
@@ -718,6 +719,19 @@ __global__ void k_reflux(Geo g, int l0, int l1, T *__restrict__ A, const T *__re
       }
     }
   }
+}
+template <typename T, int D>
+__global__ void k_reflux(Geo g, int l0, int l1, T *__restrict__ A, const T *__restrict__ FR) {
+  reflux_dev<T, D>(g, l0, l1, A, FR, blockIdx.x, gridDim.x);
+}
+// Flux correction of levels 0..L-1 (the first nr CTAs) beside the projection of
+// level L-1 (the others): the projection reads only leaves of level L, which the
+// correction never changes (no block of the finest level has a refined
+// neighbour), and writes only refined blocks, which the correction never reads.
+template <typename T, int D>
+__global__ void k_reflux_restrict(Geo g, int nr, T *__restrict__ A, const T *__restrict__ FR) {
+  if ((int)blockIdx.x < nr) reflux_dev<T, D>(g, 0, g.L - 1, A, FR, blockIdx.x, nr);
+  else restrict_level_dev<T, D>(g, g.L - 1, A, blockIdx.x - nr, gridDim.x - nr);
 }
 
 // copy the blocks of list `kind` on levels l0..l1 from src to dst

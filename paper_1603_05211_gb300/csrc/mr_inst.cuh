@@ -19,6 +19,11 @@ void launch_restrict_pos(const Geo &g, int l, T *A, int grid, cudaStream_t st) {
   else k_restrict_pos<T, 3><<<grid, 512, 0, st>>>(g, l, A);
 }
 template <typename T>
+void launch_reflux_restrict(const Geo &g, T *A, const T *FR, int nr, int np, cudaStream_t st) {
+  if (g.dim == 2) k_reflux_restrict<T, 2><<<nr + np, 256, 0, st>>>(g, nr, A, FR);
+  else k_reflux_restrict<T, 3><<<nr + np, 512, 0, st>>>(g, nr, A, FR);
+}
+template <typename T>
 void launch_restrict_tail(const Geo &g, int lhi, T *A, cudaStream_t st) {
   if (g.dim == 2) k_restrict_tail<T, 2><<<1, kTailThreads, 0, st>>>(g, lhi, A);
   else k_restrict_tail<T, 3><<<1, kTailThreads, 0, st>>>(g, lhi, A);
@@ -162,6 +167,7 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
   template void launch_restrict_edge<T>(const Geo &, T *, int, cudaStream_t);                               \
   template void launch_restrict_pos<T>(const Geo &, int, T *, int, cudaStream_t);                           \
   template void launch_restrict_tail<T>(const Geo &, int, T *, cudaStream_t);                               \
+  template void launch_reflux_restrict<T>(const Geo &, T *, const T *, int, int, cudaStream_t);            \
   template void launch_prolong_tail<T>(const Geo &, int, const int32_t *, const int *, T *, cudaStream_t);  \
   template void launch_scales<T>(const Geo &, const T *, unsigned long long *, unsigned *, T *, int, cudaStream_t); \
   template void launch_details<T>(const Geo &, const T *, const T *, double, uint8_t *, double *, int,      \
