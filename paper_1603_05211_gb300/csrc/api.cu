@@ -827,7 +827,9 @@ void adapt_tree(mrfv_ctx *c, bool step = false, bool begun = false) {
     c->nlaunch += 1;
   }
   // finest first; the levels whose positions one CTA covers in a pass together
-  const int lt = tail_level(g, kTailThreads, g.L);
+  // (and whose need maps fit in its shared memory)
+  int lt = tail_level(g, kTailThreads, g.L);
+  while (lt >= 1 && g.mapoff[lt + 1] > kTailNeedBytes) lt--;
   for (int l = g.L; l >= 1 && l > lt; l--) {
     launch_need_close(g, l, c->need, grid_for(level_blocks(g, l), 256, c->grid), c->st);
     c->nlaunch += 1;

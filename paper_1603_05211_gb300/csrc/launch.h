@@ -90,7 +90,9 @@ bool launch_fvt(const Geo &, const FVArgs<float> &, const FvtSet &, int grid, cu
 void launch_need_mark(const Geo &, const uint8_t *sig, uint8_t *need, int crit, int grid, cudaStream_t, int lkeep = 0);
 void prepare_br();
 void launch_need_close(const Geo &, int l, uint8_t *need, int grid, cudaStream_t, bool parents = true);
-// the closure of levels lhi..1 (with parents) in one single-CTA launch
+// the closure of levels lhi..1 (with parents) in one single-CTA launch, in shared
+// memory: the need map of levels 0..lhi must fit in kTailNeedBytes
+constexpr int kTailNeedBytes = 4096;
 void launch_need_close_tail(const Geo &, int lhi, uint8_t *need, cudaStream_t);
 void launch_remesh_begin(const Geo &, long long total, uint8_t *sig, uint8_t *gflag, uint8_t *need, int *nnew, int l0,
                          int grid, cudaStream_t);

@@ -394,13 +394,37 @@ __global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit, 
   k_need_mark_dev(g, sig, need, crit, lkeep);
 }
 __global__ void k_need_close(Geo g, int l, uint8_t *need, int parents) { k_need_close_dev(g, l, need, parents); }
-// Levels lhi..1 closed by one CTA, finest first, a CTA barrier between the levels
-// (a level's marks are visible to the whole CTA after it).
+// Levels lhi..1 closed by one CTA, finest first, with the rule of
+// k_need_close_dev (parents included): the need map of levels 0..lhi (at most
+// kTailNeedBytes) is read into shared memory once, closed there level by level
+// with a CTA barrier between the levels, and written back.
 __global__ void k_need_close_tail(Geo g, int lhi, uint8_t *need) {
+  __shared__ __align__(16) uint8_t sn[kTailNeedBytes];
+  const int total = (int)g.mapoff[lhi + 1];
+  for (int i = threadIdx.x; i < total; i += blockDim.x) sn[i] = need[i];
+  __syncthreads();
   for (int l = lhi; l >= 1; l--) {
-    k_need_close_dev(g, l, need, 1);
+    const int n = (int)(g.mapoff[l + 1] - g.mapoff[l]);
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+      if (!sn[g.mapoff[l] + u]) continue;
+      int bx, by, bz;
+      map_coords(g, l, g.mapoff[l] + u, bx, by, bz);
+      const int px = bx >> 1, py = by >> 1, pz = bz >> 1;
+      const int kz = g.dim == 3 ? 2 : 1;
+      for (int c = 0; c < kz; c++)  // the siblings
+        for (int b = 0; b < 2; b++)
+          for (int a = 0; a < 2; a++) sn[map_index(g, l, 2 * px + a, 2 * py + b, g.dim == 3 ? 2 * pz + c : 0)] = 1;
+      const int z0 = g.dim == 3 ? -1 : 0, z1 = g.dim == 3 ? 1 : 0;
+      for (int c = z0; c <= z1; c++)  // the parent and its neighbours
+        for (int b = -1; b <= 1; b++)
+          for (int a = -1; a <= 1; a++) {
+            const int x = bc_block(g, l - 1, 0, px + a), y = bc_block(g, l - 1, 1, py + b), z = bc_block(g, l - 1, 2, pz + c);
+            if (x >= 0 && y >= 0 && z >= 0) sn[map_index(g, l - 1, x, y, z)] = 1;
+          }
+    }
     __syncthreads();
   }
+  for (int i = threadIdx.x; i < total; i += blockDim.x) need[i] = sn[i];
 }
 
 // Remesh(l0) inside the level recursion (Fig. 2): flags cleared, the tree of
