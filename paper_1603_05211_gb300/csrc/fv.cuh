@@ -623,6 +623,9 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
   const T gam = T(g.gamma), gm1 = T(g.gamma - 1.0);
   T best = T(INFINITY);
   bool bad = false;
+  // the time the last CTA clips dt against, read now so it is not a read of its own
+  // at the end of the reduction (nothing writes it while this kernel runs)
+  const double tnow = (threadIdx.x == 0 && t_end > 0.0) ? dsc[1] : 0.0;
   auto cell = [&](long long t) {
     int i = (int)(t / B), c = (int)(t % B);
     int s = g.lists[LK_LEAF * cap + i];
@@ -674,7 +677,7 @@ __global__ void k_dt(Geo g, const T *__restrict__ A, int lts, unsigned long long
       atomicExch(done, 0u);
       double d = cfl * m;
       if (t_end > 0.0) {
-        double rest = t_end - dsc[1];
+        double rest = t_end - tnow;
         if (rest < d) d = rest;
       }
       dsc[0] = d;

@@ -101,14 +101,93 @@ template <typename T, int D>
 __global__ void k_restrict_pos(Geo g, int l, T *__restrict__ A) {
   restrict_pos_dev<T, D>(g, l, A);
 }
-// Levels lhi..0 projected by one CTA, finest first, a CTA barrier between the
-// levels (the writes of a level are visible to the whole CTA after it).  For the
-// coarse levels, whose few positions one CTA covers in a pass: one launch and a
-// barrier per level instead of a launch per level.
+// Levels lhi..0 projected by one CTA (the coarse levels, whose few positions one
+// CTA covers in a pass: 16 blocks of level lhi at most in 2D, 2 in 3D).  Two rounds
+// of global reads: the slots of every position of levels 0..lhi and of their
+// children, then the values of every block there (leaves final, refined blocks of
+// level lhi projected from their children of level lhi+1); the coarser levels
+// are then projected from shared memory, finest first, a CTA barrier per level.
+// Every projected block is also stored.  Same sums in the same order as
+// restrict_level_dev.
+template <int D>
+struct TailShape {
+  static constexpr int B = (D == 2) ? 64 : 512;
+  static constexpr int MAXB = (D == 2) ? 22 : 2;  // blocks of levels 0..lhi
+};
+template <typename T, int D>
+__device__ __forceinline__ T project_cell(const T *C, int cstride) {
+  T sum = C[0];
+  sum = sum + C[1];
+  sum = sum + C[8];
+  sum = sum + C[9];
+  if (D == 3) {
+    sum = sum + C[64];
+    sum = sum + C[65];
+    sum = sum + C[72];
+    sum = sum + C[73];
+  }
+  (void)cstride;
+  return sum * T(D == 2 ? 0.25 : 0.125);
+}
 template <typename T, int D>
 __global__ void k_restrict_tail(Geo g, int lhi, T *__restrict__ A) {
-  for (int l = lhi; l >= 0; l--) {
-    restrict_pos_dev<T, D>(g, l, A);
+  constexpr int B = TailShape<D>::B, MAXB = TailShape<D>::MAXB, NV = D + 2, NK = (D == 2) ? 4 : 8;
+  __shared__ T sv[MAXB * NV * B];
+  __shared__ int sslot[MAXB], skid[MAXB][NK];
+  const long long cap = g.cap;
+  const int np = (int)g.mapoff[lhi + 1];
+  // round 1: slots of the positions and of their children
+  for (int k = threadIdx.x; k < np * (NK + 1); k += blockDim.x) {
+    const int pos = k / (NK + 1), q = k % (NK + 1) - 1;
+    int l = 0;
+    while (l < lhi && pos >= g.mapoff[l + 1]) l++;
+    const int u = pos - (int)g.mapoff[l], nx = g.nb[l][0], ny = g.nb[l][1];
+    const int r = u / nx, bx = u - r * nx, by = r % ny, bz = r / ny;
+    if (q < 0) sslot[pos] = g.idx[pos];
+    else
+      skid[pos][q] = g.idx[map_index(g, l + 1, 2 * bx + (q & 1), 2 * by + ((q >> 1) & 1), (D == 3) ? 2 * bz + (q >> 2) : 0)];
+  }
+  __syncthreads();
+  // round 2: every block's values; refined blocks of level lhi from their children
+  const int p0 = (int)g.mapoff[lhi];
+  for (int k = threadIdx.x; k < np * B; k += blockDim.x) {
+    const int pos = k / B, c = k % B, s = sslot[pos];
+    if (s < 0) continue;
+    if (pos >= p0 && skid[pos][0] >= 0) {
+      const int x = c & 7, y = (c >> 3) & 7, z = (D == 3) ? (c >> 6) : 0;
+      const int cs = skid[pos][(x >> 2) + 2 * (y >> 2) + ((D == 3) ? 4 * (z >> 2) : 0)];
+      const int f = 2 * (x & 3) + 16 * (y & 3) + ((D == 3) ? 128 * (z & 3) : 0);
+      if (cs < 0) {
+        set_err(g, EB_TREE);
+        continue;
+      }
+      for (int v = 0; v < NV; v++) {
+        const T val = project_cell<T, D>(A + ((long long)v * cap + cs) * B + f, 0);
+        sv[(pos * NV + v) * B + c] = val;
+        A[((long long)v * cap + s) * B + c] = val;
+      }
+    } else {
+      for (int v = 0; v < NV; v++) sv[(pos * NV + v) * B + c] = A[((long long)v * cap + s) * B + c];
+    }
+  }
+  __syncthreads();
+  for (int l = lhi - 1; l >= 0; l--) {
+    const int b = (int)g.mapoff[l], e = (int)g.mapoff[l + 1];
+    const int nxf = g.nb[l + 1][0], nyf = g.nb[l + 1][1], nx = g.nb[l][0], ny = g.nb[l][1];
+    for (int k = threadIdx.x; k < (e - b) * B; k += blockDim.x) {
+      const int pos = b + k / B, c = k % B, s = sslot[pos];
+      if (s < 0 || skid[pos][0] < 0) continue;
+      const int u = pos - b, r = u / nx, bx = u - r * nx, by = r % ny, bz = r / ny;
+      const int x = c & 7, y = (c >> 3) & 7, z = (D == 3) ? (c >> 6) : 0;
+      // the child holding this cell's children, as a position of level l+1
+      const int cpos = (int)g.mapoff[l + 1] + (2 * bx + (x >> 2)) + nxf * ((2 * by + (y >> 2)) + nyf * ((D == 3) ? 2 * bz + (z >> 2) : 0));
+      const int f = 2 * (x & 3) + 16 * (y & 3) + ((D == 3) ? 128 * (z & 3) : 0);
+      for (int v = 0; v < NV; v++) {
+        const T val = project_cell<T, D>(sv + (cpos * NV + v) * B + f, 0);
+        sv[(pos * NV + v) * B + c] = val;
+        A[((long long)v * cap + s) * B + c] = val;
+      }
+    }
     __syncthreads();
   }
 }

@@ -394,33 +394,62 @@ __global__ void k_need_mark(Geo g, const uint8_t *sig, uint8_t *need, int crit, 
   k_need_mark_dev(g, sig, need, crit, lkeep);
 }
 __global__ void k_need_close(Geo g, int l, uint8_t *need, int parents) { k_need_close_dev(g, l, need, parents); }
-// Levels lhi..1 closed by one CTA, finest first, with the rule of
-// k_need_close_dev (parents included): the need map of levels 0..lhi (at most
-// kTailNeedBytes) is read into shared memory once, closed there level by level
-// with a CTA barrier between the levels, and written back.
+// Levels lhi..1 closed by one CTA, finest first: the need map of levels 0..lhi
+// (at most kTailNeedBytes) is read into shared memory once, closed there level by
+// level and written back.  Each level is closed by gathering instead of
+// scattering: with any(q) = "some child of q (level l-1) is needed", the rule of
+// k_need_close_dev (parents included) marks on level l every child of a q with
+// any(q), and on level l-1 every position p with any(q) for some q among p and its
+// 3^d-1 neighbours (the neighbour relation is symmetric, boundary rule included).
+// Two passes over the positions of level l-1 per level, no scattered writes.
 __global__ void k_need_close_tail(Geo g, int lhi, uint8_t *need) {
   __shared__ __align__(16) uint8_t sn[kTailNeedBytes];
+  __shared__ uint8_t anyc[kTailThreads];
   const int total = (int)g.mapoff[lhi + 1];
+#pragma unroll 4
   for (int i = threadIdx.x; i < total; i += blockDim.x) sn[i] = need[i];
   __syncthreads();
+  const bool d3 = g.dim == 3;
   for (int l = lhi; l >= 1; l--) {
-    const int n = (int)(g.mapoff[l + 1] - g.mapoff[l]);
-    for (int u = threadIdx.x; u < n; u += blockDim.x) {
-      if (!sn[g.mapoff[l] + u]) continue;
-      int bx, by, bz;
-      map_coords(g, l, g.mapoff[l] + u, bx, by, bz);
-      const int px = bx >> 1, py = by >> 1, pz = bz >> 1;
-      const int kz = g.dim == 3 ? 2 : 1;
-      for (int c = 0; c < kz; c++)  // the siblings
-        for (int b = 0; b < 2; b++)
-          for (int a = 0; a < 2; a++) sn[map_index(g, l, 2 * px + a, 2 * py + b, g.dim == 3 ? 2 * pz + c : 0)] = 1;
-      const int z0 = g.dim == 3 ? -1 : 0, z1 = g.dim == 3 ? 1 : 0;
-      for (int c = z0; c <= z1; c++)  // the parent and its neighbours
-        for (int b = -1; b <= 1; b++)
+    const int lp = l - 1;
+    const int nx = g.nb[lp][0], ny = g.nb[lp][1];
+    const int n = (int)(g.mapoff[l] - g.mapoff[lp]);  // positions of level l-1 (at most kTailThreads)
+    const int cx = g.nb[l][0], cxy = g.nb[l][0] * g.nb[l][1];
+    uint8_t *fine = sn + g.mapoff[l];
+    uint8_t *coarse = sn + g.mapoff[lp];
+    int qx = 0, qy = 0, qz = 0;
+    const int u = threadIdx.x;
+    if (u < n) {
+      qy = u / nx;
+      qx = u - qy * nx;
+      qz = qy / ny;
+      qy -= qz * ny;
+      const int f = 2 * qx + cx * (2 * qy) + cxy * (2 * qz);
+      uint8_t a = fine[f] | fine[f + 1] | fine[f + cx] | fine[f + cx + 1];
+      if (d3) a |= fine[f + cxy] | fine[f + cxy + 1] | fine[f + cxy + cx] | fine[f + cxy + cx + 1];
+      anyc[u] = a;
+    }
+    __syncthreads();
+    if (u < n) {
+      if (anyc[u]) {  // the children of q, the siblings of its needed child
+        const int f = 2 * qx + cx * (2 * qy) + cxy * (2 * qz);
+        fine[f] = fine[f + 1] = fine[f + cx] = fine[f + cx + 1] = 1;
+        if (d3) fine[f + cxy] = fine[f + cxy + 1] = fine[f + cxy + cx] = fine[f + cxy + cx + 1] = 1;
+      }
+      uint8_t m = 0;
+      for (int c = d3 ? -1 : 0; c <= (d3 ? 1 : 0); c++) {
+        const int z = bc_block(g, lp, 2, qz + c);
+        if (z < 0) continue;
+        for (int b = -1; b <= 1; b++) {
+          const int y = bc_block(g, lp, 1, qy + b);
+          if (y < 0) continue;
           for (int a = -1; a <= 1; a++) {
-            const int x = bc_block(g, l - 1, 0, px + a), y = bc_block(g, l - 1, 1, py + b), z = bc_block(g, l - 1, 2, pz + c);
-            if (x >= 0 && y >= 0 && z >= 0) sn[map_index(g, l - 1, x, y, z)] = 1;
+            const int x = bc_block(g, lp, 0, qx + a);
+            if (x >= 0) m |= anyc[x + nx * (y + ny * z)];
           }
+        }
+      }
+      if (m) coarse[u] = 1;
     }
     __syncthreads();
   }
