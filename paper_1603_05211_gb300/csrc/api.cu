@@ -459,12 +459,14 @@ struct Seq {
     c->nlaunch += 1;
     restrict_all(U());
   }
-  // between the two stages: only the coarse cells the second stage reads
-  void restrict_edge(T *A) {
+  // between the two stages: the ghost strips and the projection of restrict_edge_dev
+  // in one launch (the strips project their coarse cells on the fly)
+  void ghost_edge(T *A) {
     if (c->g.L < 1) return;
-    const int per = c->g.dim == 2 ? 16 : 4;
-    int dense = grid_for(c->g.mapoff[c->g.L + 1] - c->g.mapoff[1], per, c->grid);
-    launch_restrict_edge<T>(c->g, A, sized(c, LK_LEAF, 1, c->g.L, 1, per, dense), c->st);
+    const int ng = sized(c, LK_GHOST, 1, c->g.L, 1, 1, c->bgrid);
+    int dense = grid_for(c->g.mapoff[c->g.L + 1] - c->g.mapoff[1], 4, c->grid);
+    const int ne = sized(c, LK_LEAF, 1, c->g.L, 1, 4, dense);
+    launch_ghost_edge<T>(c->g, A, G(), ng, ne, c->st);
     c->nlaunch += 1;
   }
   void fv(int kind, int l0, int l1, const T *Uin, const T *U0b, T *Uout, double coef, int lts, int record) {
@@ -591,8 +593,7 @@ struct Seq {
     }
     if (!ghost_done) ghost(1, L, U(), nullptr, 0.0);
     fv(LK_LEAF, 0, L, U(), U(), Us(), 0.5, 0, 0);
-    restrict_edge(Us());
-    ghost(1, L, Us(), nullptr, 0.0);
+    ghost_edge(Us());
     fv(LK_LEAF, 0, L, Us(), U(), U(), 1.0, 0, 1);
     reflux_restrict_all();
   }

@@ -96,6 +96,52 @@ __device__ void gather_patch(const Geo &g, int lc, const T *__restrict__ A, cons
   }
 }
 
+// gather_patch for the ghost strips between the stages of the MR step: a coarse
+// cell whose block is refined takes the projection of its 2^d children (the sums
+// of the level projection, in its order), read from level lc+1, in place of its
+// stored value, which is projected only later.  (A coarse cell over a refined
+// child is projected from that child's stale values; the prediction never reads
+// such a cell: in a graded tree the blocks next to an absent position are leaves.)
+template <typename T, int D, int EXT>
+__device__ void gather_patch_proj(const Geo &g, int lc, const T *__restrict__ A, int o0, int o1, int o2, T *patch,
+                                  int tid, int nthr) {
+  constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
+  constexpr int NB = (D == 2) ? 64 : 512;
+  const long long cap = g.cap;
+  for (int p = tid; p < NP; p += nthr) {
+    int x = p % EXT, y = (p / EXT) % EXT, z = (D == 3) ? p / (EXT * EXT) : 0;
+    int cx = bc_cell(g, lc, 0, o0 + x), cy = bc_cell(g, lc, 1, o1 + y), cz = (D == 3) ? bc_cell(g, lc, 2, o2 + z) : 0;
+    int32_t s = g.idx[map_index(g, lc, cx >> 3, cy >> 3, cz >> 3)];
+    // the child of level lc+1 holding this cell's children (absent under a leaf)
+    int32_t cs = g.idx[map_index(g, lc + 1, cx >> 2, cy >> 2, cz >> 2)];
+    int c = (cx & 7) + 8 * (cy & 7) + (D == 3 ? 64 * (cz & 7) : 0);
+    int f = 2 * (cx & 3) + 16 * (cy & 3) + (D == 3 ? 128 * (cz & 3) : 0);
+    for (int v = 0; v < D + 2; v++) {
+      T val;
+      if (s < 0) {
+        val = T(__int_as_float(0x7fc00000));
+        if (v == 0) set_err(g, EB_TREE);
+      } else if (cs >= 0) {
+        const T *C = A + ((long long)v * cap + cs) * NB + f;
+        T sum = C[0];
+        sum = sum + C[1];
+        sum = sum + C[8];
+        sum = sum + C[9];
+        if (D == 3) {
+          sum = sum + C[64];
+          sum = sum + C[65];
+          sum = sum + C[72];
+          sum = sum + C[73];
+        }
+        val = sum * T(D == 2 ? 0.25 : 0.125);
+      } else {
+        val = A[((long long)v * cap + s) * NB + c];
+      }
+      patch[v * NP + p] = val;
+    }
+  }
+}
+
 // Third-order prediction of the fine cell whose parent is patch cell
 // (x, y, z): tensor product of the 1D rule Q_k +/- (Q_{k-1} - Q_{k+1})/8 (+ for
 // the even child).  Evaluation order: Q_k, the first-order terms in direction

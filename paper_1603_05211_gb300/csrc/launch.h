@@ -25,9 +25,11 @@ template <typename T> void launch_restrict_tail(const Geo &, int lhi, T *A, cuda
 // new blocks of levels 1..lhi in one single-CTA launch
 template <typename T> void launch_prolong_tail(const Geo &, int lhi, const int32_t *newlist, const int *nnew, T *A,
                                                cudaStream_t);
-// between the stages of the MR step: the parent quadrants of the leaves next to an
-// absent block, all levels in one launch
-template <typename T> void launch_restrict_edge(const Geo &, T *A, int grid, cudaStream_t);
+// between the stages of the MR step: the ghost strips of every level (ng CTAs, the
+// coarse cells over refined blocks projected on the fly) and the projection of
+// restrict_edge_dev (ne CTAs: the parent quadrants of the leaves next to an absent
+// block, all levels) in one launch
+template <typename T> void launch_ghost_edge(const Geo &, T *A, T *G, int ng, int ne, cudaStream_t);
 template <typename T> void launch_scales(const Geo &, const T *A, unsigned long long *red, unsigned *done, T *scale,
                                          int grid, cudaStream_t);
 // own_scale (optional): every CTA computes the level-0 normalisation itself and CTA

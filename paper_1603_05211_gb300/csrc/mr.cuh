@@ -205,16 +205,16 @@ __global__ void k_restrict_tail(Geo g, int lhi, T *__restrict__ A) {
 // same sums in the same order).  Cells of refined blocks over other children keep
 // older values that nothing reads before the closing projection.
 template <typename T, int D>
-__global__ void k_restrict_edge(Geo g, T *__restrict__ A) {
+__device__ __forceinline__ void restrict_edge_dev(const Geo &g, T *__restrict__ A, int cta, int ncta) {
   constexpr int B = (D == 2) ? 64 : 512;
   constexpr int Q = (D == 2) ? 16 : 64;  // cells of a parent quadrant
-  constexpr int PER = 256 / Q;           // leaves per CTA and pass
+  const int PER = blockDim.x / Q;        // leaves per CTA and pass
   const int sub = threadIdx.x / Q, c = threadIdx.x % Q;
   const int qx = c & 3, qy = (c >> 2) & 3, qz = (D == 3) ? (c >> 4) : 0;
   const long long cap = g.cap;
   int b, e;
   list_range(g, LK_LEAF, 1, g.L, b, e);
-  for (int i = b + blockIdx.x * PER + sub; i < e; i += gridDim.x * PER) {
+  for (int i = b + cta * PER + sub; i < e; i += ncta * PER) {
     const int s = g.lists[LK_LEAF * cap + i];
     const int l = g.slot_level[s];
     const int bx = g.slot_coord[3 * s], by = g.slot_coord[3 * s + 1], bz = g.slot_coord[3 * s + 2];
@@ -496,25 +496,27 @@ __global__ void k_prolong_tail(Geo g, int lhi, const int32_t *__restrict__ newli
 // neighbour is absent gets its two outer cell layers predicted from level l-1
 // (A, or A0 + theta (A - A0) for level-dependent steps).  Strip layout:
 // G[v][slot][face][depth][tangential], depth 0 touches the block.
-template <typename T, int D>
-__global__ void k_ghost(Geo g, int l0, int l1, const T *__restrict__ A, const T *__restrict__ A0, T theta,
-                        T *__restrict__ G) {
+template <typename T, int D, bool PROJ>
+__device__ __forceinline__ void ghost_dev(const Geo &g, int l0, int l1, const T *__restrict__ A,
+                                          const T *__restrict__ A0, T theta, T *__restrict__ G, T *patch, int cta,
+                                          int ncta) {
   constexpr int TF = (D == 2) ? 8 : 64;
   constexpr int GS = 2 * D * 2 * TF;
   constexpr int EXT = 8;
   constexpr int NP = (D == 2) ? EXT * EXT : EXT * EXT * EXT;
-  extern __shared__ unsigned char smem_raw[];
-  T *patch = reinterpret_cast<T *>(smem_raw);
   int b, e;
   list_range(g, LK_GHOST, l0, l1, b, e);
   const long long cap = g.cap;
-  for (int i = b + blockIdx.x; i < e; i += gridDim.x) {
+  for (int i = b + cta; i < e; i += ncta) {
     int s = g.lists[LK_GHOST * cap + i];
     int l = g.slot_level[s];
     int bx = g.slot_coord[3 * s], by = g.slot_coord[3 * s + 1], bz = g.slot_coord[3 * s + 2];
     __syncthreads();
-    gather_patch<T, D, EXT>(g, l - 1, A, A0, theta, 4 * bx - 2, 4 * by - 2, 4 * bz - 2, patch, threadIdx.x,
-                            blockDim.x);
+    if (PROJ)
+      gather_patch_proj<T, D, EXT>(g, l - 1, A, 4 * bx - 2, 4 * by - 2, 4 * bz - 2, patch, threadIdx.x, blockDim.x);
+    else
+      gather_patch<T, D, EXT>(g, l - 1, A, A0, theta, 4 * bx - 2, 4 * by - 2, 4 * bz - 2, patch, threadIdx.x,
+                              blockDim.x);
     __syncthreads();
     for (int q = threadIdx.x; q < GS; q += blockDim.x) {
       int f = q / (2 * TF), dd = (q / TF) & 1, t = q % TF;
@@ -533,6 +535,25 @@ __global__ void k_ghost(Geo g, int l0, int l1, const T *__restrict__ A, const T 
         G[((long long)v * cap + s) * GS + q] = predict<T, D, EXT>(patch + v * NP, px, py, pz, si, sj, sk);
     }
   }
+}
+template <typename T, int D>
+__global__ void k_ghost(Geo g, int l0, int l1, const T *__restrict__ A, const T *__restrict__ A0, T theta,
+                        T *__restrict__ G) {
+  extern __shared__ unsigned char smem_raw[];
+  ghost_dev<T, D, false>(g, l0, l1, A, A0, theta, G, reinterpret_cast<T *>(smem_raw), blockIdx.x, gridDim.x);
+}
+// Between the stages of the MR step, in one launch: the ghost strips of every
+// level (the first ng CTAs), their coarse cells over refined blocks projected on
+// the fly from the children, and the projection of restrict_edge_dev (the
+// others), which the stage's coarse-side fluxes read.  The two parts read the
+// stage state and write disjoint buffers.
+template <typename T, int D>
+__global__ void k_ghost_edge(Geo g, int ng, T *__restrict__ A, T *__restrict__ G) {
+  extern __shared__ unsigned char smem_raw[];
+  if ((int)blockIdx.x < ng)
+    ghost_dev<T, D, true>(g, 1, g.L, A, (const T *)nullptr, T(0), G, reinterpret_cast<T *>(smem_raw), blockIdx.x, ng);
+  else
+    restrict_edge_dev<T, D>(g, A, blockIdx.x - ng, gridDim.x - ng);
 }
 
 // ---------------------------------------------------------------- initial data

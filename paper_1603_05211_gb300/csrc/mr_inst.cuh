@@ -34,9 +34,9 @@ void launch_prolong_tail(const Geo &g, int lhi, const int32_t *newlist, const in
   else k_prolong_tail<T, 3><<<1, 512, 0, st>>>(g, lhi, newlist, nnew, A);
 }
 template <typename T>
-void launch_restrict_edge(const Geo &g, T *A, int grid, cudaStream_t st) {
-  if (g.dim == 2) k_restrict_edge<T, 2><<<grid, 256, 0, st>>>(g, A);
-  else k_restrict_edge<T, 3><<<grid, 256, 0, st>>>(g, A);
+void launch_ghost_edge(const Geo &g, T *A, T *G, int ng, int ne, cudaStream_t st) {
+  if (g.dim == 2) k_ghost_edge<T, 2><<<ng + ne, 64, 4 * 64 * sizeof(T), st>>>(g, ng, A, G);
+  else k_ghost_edge<T, 3><<<ng + ne, 256, 5 * 512 * sizeof(T), st>>>(g, ng, A, G);
 }
 template <typename T>
 void launch_gather_var(const Geo &g, int l, int v, int f, const T *A, double *out, cudaStream_t st) {
@@ -164,7 +164,7 @@ void launch_project_level(const Geo &g, int l, const T *A, const double *coarse,
 
 #define MRFV_INSTANTIATE_MR(T)                                                                              \
   template void launch_restrict<T>(const Geo &, int, T *, int, cudaStream_t);                               \
-  template void launch_restrict_edge<T>(const Geo &, T *, int, cudaStream_t);                               \
+  template void launch_ghost_edge<T>(const Geo &, T *, T *, int, int, cudaStream_t);                       \
   template void launch_restrict_pos<T>(const Geo &, int, T *, int, cudaStream_t);                           \
   template void launch_restrict_tail<T>(const Geo &, int, T *, cudaStream_t);                               \
   template void launch_reflux_restrict<T>(const Geo &, T *, const T *, int, int, cudaStream_t);            \
