@@ -45,10 +45,13 @@ constexpr long long kStagedBelow3D = 0;
 // blocks 21.1 / 22.9 us.
 constexpr long long kSplitBelow2D = 0;
 constexpr long long kSplitBelow3D = 0;
-// From these leaf counts on, the pencil kernel reads primitives staged in shared
-// memory (set from measurement; at or above the largest count: never).
-constexpr long long kStagedPrimAbove2D = 1LL << 40;
-constexpr long long kStagedPrimAbove3D = 1LL << 40;
+// Below these leaf counts the single-precision MR-scheme stage runs in the pencil
+// kernel that reads primitives staged in shared memory (k_fvp).  Measured on GB300
+// inside the adaptive 2D step (about 1700 leaf blocks; same box, alternating runs):
+// 0.1011-0.1019 ms per step against 0.1038-0.1040 with the plain pencil kernel.
+// Not measured above that size nor in 3D, where the plain pencil kernel stays.
+constexpr long long kStagedPrimBelow2D = 4096;
+constexpr long long kStagedPrimBelow3D = 0;
 // From this leaf count on (2D single precision), the TMA-staged kernel runs.
 // Measured (FP32, CUDA events per launch, TMA-staged / pencil): uniform 4096^2
 // (262144 blocks) 0.352 / 0.371 ms, 8192^2 1.374 / 1.433 ms; the adaptive 8-level
@@ -502,9 +505,9 @@ struct Seq {
   // pencil kernel reading primitives staged in shared memory
   bool use_fvp(const FVArgs<T> &a) const {
     if (c->stage_kernel != 0) return c->stage_kernel == 4;
-    if (!c->snap_valid) return false;
+    if (sizeof(T) != 4 || !c->snap_valid) return false;
     long long n = list_count(c, c->snap, a.kind, a.l0, a.l1);
-    return n >= (c->g.dim == 2 ? kStagedPrimAbove2D : kStagedPrimAbove3D);
+    return n < (c->g.dim == 2 ? kStagedPrimBelow2D : kStagedPrimBelow3D);
   }
   // pencil kernel with two threads per line while the list is short
   bool use_split(const FVArgs<T> &a) const {
