@@ -260,6 +260,10 @@ def test_restricted_inference_adds_the_blocks_dense_inference_adds(mrfv, dim):
         s = mrfv.Solver(proposer=True, proposer_dense=dense, **kw)
         s.init_state(ic, params)
         s.proposer_set_weights(weights)
+        # one stage kernel for every run: the automatic choice follows the leaf count,
+        # which the profiled (eager) run reads every step and a captured graph keeps
+        # from its capture, and single-precision kernels differ in the last bit
+        s.set_launch_shape(stage_kernel=1)
         if name == "restricted":
             s.profile_enable(True)
         for _ in range(4):
