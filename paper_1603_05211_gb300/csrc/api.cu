@@ -431,7 +431,7 @@ struct Seq {
   // levels top..0
   void restrict_from(int top, T *A) {
     int lt = tail_level(c->g, kTailThreads / block_cells(c->g.dim), top);
-    while (lt >= 0 && c->g.mapoff[lt + 1] > (c->g.dim == 2 ? 22 : 2)) lt--;  // the tail kernel's block limit
+    while (lt >= 0 && c->g.mapoff[lt + 1] > (c->g.dim == 2 ? kRestrictTailBlocks2D : kRestrictTailBlocks3D)) lt--;
     for (int l = top; l > lt; l--) restrict_level(l, A);
     if (top > lt) c->nlaunch += top - lt;
     if (lt >= 0) {
@@ -449,7 +449,7 @@ struct Seq {
     const int bpc = g.dim == 2 ? 4 : 1, nt = g.dim == 2 ? 256 : 512;
     const long long pos = level_blocks(g, L - 1);
     int lt = tail_level(g, kTailThreads / block_cells(g.dim), L - 1);
-    while (lt >= 0 && g.mapoff[lt + 1] > (g.dim == 2 ? 22 : 2)) lt--;
+    while (lt >= 0 && g.mapoff[lt + 1] > (g.dim == 2 ? kRestrictTailBlocks2D : kRestrictTailBlocks3D)) lt--;
     if (L - 1 > lt && pos > (long long)kRestrictPosCtasPerSm * bpc * c->nsm) {
       const int nr = sized(c, LK_REFLUX, 0, L - 1, block_cells(g.dim), nt, c->grid);
       const int np = sized(c, LK_INTERNAL, L - 1, L - 1, 1, bpc, grid_for(pos, bpc, c->grid));

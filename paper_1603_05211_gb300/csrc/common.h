@@ -17,6 +17,10 @@ namespace mrfv {
 
 constexpr int BS = 8;        // cells per block edge
 constexpr int MAXL = 12;     // maximum number of levels
+// block positions the single-CTA projection of the coarse levels holds in shared
+// memory (levels 0..lhi together), 2D and 3D
+constexpr int kRestrictTailBlocks2D = 22;
+constexpr int kRestrictTailBlocks3D = 2;
 constexpr int NBR_MISSING = -1;  // same-level neighbour absent: read the ghost strip
 constexpr int NBR_WALL = -2;     // outside a transmissive domain: zero-gradient copy
 

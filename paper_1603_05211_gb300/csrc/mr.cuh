@@ -112,10 +112,12 @@ __global__ void k_restrict_pos(Geo g, int l, T *__restrict__ A) {
 template <int D>
 struct TailShape {
   static constexpr int B = (D == 2) ? 64 : 512;
-  static constexpr int MAXB = (D == 2) ? 22 : 2;  // blocks of levels 0..lhi
+  static constexpr int MAXB = (D == 2) ? kRestrictTailBlocks2D : kRestrictTailBlocks3D;  // positions of levels 0..lhi
 };
+// the projection of one cell from its children's cells at C (C[0]: the first child
+// cell in x, y, z order), the sums of restrict_level_dev in their order
 template <typename T, int D>
-__device__ __forceinline__ T project_cell(const T *C, int cstride) {
+__device__ __forceinline__ T project_cell(const T *C) {
   T sum = C[0];
   sum = sum + C[1];
   sum = sum + C[8];
@@ -126,7 +128,6 @@ __device__ __forceinline__ T project_cell(const T *C, int cstride) {
     sum = sum + C[72];
     sum = sum + C[73];
   }
-  (void)cstride;
   return sum * T(D == 2 ? 0.25 : 0.125);
 }
 template <typename T, int D>
@@ -162,7 +163,7 @@ __global__ void k_restrict_tail(Geo g, int lhi, T *__restrict__ A) {
         continue;
       }
       for (int v = 0; v < NV; v++) {
-        const T val = project_cell<T, D>(A + ((long long)v * cap + cs) * B + f, 0);
+        const T val = project_cell<T, D>(A + ((long long)v * cap + cs) * B + f);
         sv[(pos * NV + v) * B + c] = val;
         A[((long long)v * cap + s) * B + c] = val;
       }
@@ -183,7 +184,7 @@ __global__ void k_restrict_tail(Geo g, int lhi, T *__restrict__ A) {
       const int cpos = (int)g.mapoff[l + 1] + (2 * bx + (x >> 2)) + nxf * ((2 * by + (y >> 2)) + nyf * ((D == 3) ? 2 * bz + (z >> 2) : 0));
       const int f = 2 * (x & 3) + 16 * (y & 3) + ((D == 3) ? 128 * (z & 3) : 0);
       for (int v = 0; v < NV; v++) {
-        const T val = project_cell<T, D>(sv + (cpos * NV + v) * B + f, 0);
+        const T val = project_cell<T, D>(sv + (cpos * NV + v) * B + f);
         sv[(pos * NV + v) * B + c] = val;
         A[((long long)v * cap + s) * B + c] = val;
       }
