@@ -102,7 +102,7 @@ __global__ void k_restrict_pos(Geo g, int l, T *__restrict__ A) {
   restrict_pos_dev<T, D>(g, l, A);
 }
 // Levels lhi..0 projected by one CTA (the coarse levels, whose few positions one
-// CTA covers in a pass: 16 blocks of level lhi at most in 2D, 2 in 3D).  Two rounds
+// CTA covers in a pass: 16 blocks of level lhi at most in 2D, 2 in 3D).  Two passes
 // of global reads: the slots of every position of levels 0..lhi and of their
 // children, then the values of every block there (leaves final, refined blocks of
 // level lhi projected from their children of level lhi+1); the coarser levels
@@ -137,7 +137,7 @@ __global__ void k_restrict_tail(Geo g, int lhi, T *__restrict__ A) {
   __shared__ int sslot[MAXB], skid[MAXB][NK];
   const long long cap = g.cap;
   const int np = (int)g.mapoff[lhi + 1];
-  // round 1: slots of the positions and of their children
+  // first pass of reads: slots of the positions and of their children
   for (int k = threadIdx.x; k < np * (NK + 1); k += blockDim.x) {
     const int pos = k / (NK + 1), q = k % (NK + 1) - 1;
     int l = 0;
@@ -149,7 +149,7 @@ __global__ void k_restrict_tail(Geo g, int lhi, T *__restrict__ A) {
       skid[pos][q] = g.idx[map_index(g, l + 1, 2 * bx + (q & 1), 2 * by + ((q >> 1) & 1), (D == 3) ? 2 * bz + (q >> 2) : 0)];
   }
   __syncthreads();
-  // round 2: every block's values; refined blocks of level lhi from their children
+  // second pass of reads: every block's values; refined blocks of level lhi from their children
   const int p0 = (int)g.mapoff[lhi];
   for (int k = threadIdx.x; k < np * B; k += blockDim.x) {
     const int pos = k / B, c = k % B, s = sslot[pos];
